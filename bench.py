@@ -1,0 +1,322 @@
+#!/usr/bin/env python
+"""Benchmark of the collision-operator library on B300.
+
+Workload (one "step"): the single-instance N = 128 configuration integrated in
+full: build the kernel tensor for the grid (p/m in [1e-3, 10], m = 1), then
+integrate the seeded bimodal f0 with the two freeze-in sources for the four
+cross-sections sigma in {0.1, 1, 10, 100} (a batch of 4 instances sharing the
+kernel) until each matches Maxwell-Boltzmann to 1e-3 in L1 after the sources
+are off.  Metric: collision-term evaluations per second (C_proj for one
+instance = one evaluation), with solves/s and the plain FP64 path on the same
+inputs beside it.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+(N > 1: launched by torch.distributed.run, one independent replica per rank.)
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import kx_inputs as ki  # noqa: E402
+
+METRIC = "collision-term evals/s & solves/s vs plain FP64 path; p50/p99 solve latency"
+UNIT = "evals/s"
+L2_FLUSH_BYTES = 512 << 20     # > 126 MB L2
+SOLVE = dict(t_end=1e5, h0=1e-3, rtol=1e-6, l1_tol=1e-3, check_every=10, max_attempts=2_000_000)
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            p = json.load(fh)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6400.0, "fallback"
+
+
+def workload():
+    c = ki.config2()
+    B = len(c["sigmas"])
+    f0 = np.tile(c["f0"], (B, 1))
+    atol = 1e-12 * float(c["f0"].max())
+    return c, B, f0, dict(SOLVE, atol=atol)
+
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons during a region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_id: str):
+        self.proc = None
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", gpu_id, f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except Exception:
+            self.proc.kill()
+            out = ""
+        sm, smax, reasons = [], [], set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for line in out.strip().splitlines():
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def oracle_sample(c, B, seconds: float):
+    """The oracle as it stands: RHS evaluations (tensor-form C, projection,
+    sources) of the workload's first Heun attempts, for about `seconds`."""
+    import oracle
+    q = c["q"]
+    W = oracle.kernel_tensor(q)
+    evals, t0 = 0, time.perf_counter()
+    while time.perf_counter() - t0 < seconds:
+        for b in range(B):
+            M2 = oracle.M2_from_sigma(1.0, c["sigmas"][b])
+            _, r = oracle.solve(q, W, c["f0"], M2, sources=c["sources"], t_end=1e5, h0=1e-3,
+                                rtol=1e-6, atol=1e-12 * c["f0"].max(), max_attempts=2)
+            evals += int(r["evals"])
+    dt = time.perf_counter() - t0
+    return evals, dt, oracle.num_threads()
+
+
+def run_reference(args, rank):
+    """Reference arm: the FP64 CPU oracle on this host's cores (rank 0 only)."""
+    if rank != 0:
+        return 0
+    c, B, f0, par = workload()
+    per_step = max(1.0, min(8.0, 60.0 / max(1, args.steps + args.warmup)))
+    for _ in range(args.warmup):
+        oracle_sample(c, B, per_step)
+    tot_e, tot_t, cores = 0, 0.0, 1
+    for _ in range(args.steps):
+        e, t, cores = oracle_sample(c, B, per_step)
+        tot_e += e
+        tot_t += t
+    val = tot_e / tot_t
+    sample = (f"{tot_e} RHS evaluations (tensor-form C + projection + sources, first Heun "
+              f"attempts of the 4-sigma N=128 workload) in {tot_t:.1f} s")
+    line = {"impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot_t / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": config_desc(c, B),
+            "cpu_baseline": {"value": val, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def config_desc(c, B):
+    return {"workload": "single instance N=128 full integration: kernel build + adaptive Heun "
+                        "solve with two freeze-in sources for sigma in {0.1,1,10,100} "
+                        "(batch of 4 sharing one kernel) to L1<=1e-3 vs MB",
+            "n": int(c["q"].size), "batch": B, "q_range": [1e-3, 10.0], "mass": 1.0,
+            "n_mu": 18, "path": "FP32 streaming contraction, FP64 projection/stepper",
+            "l2": "flushed between timed steps (512 MB write)"}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--fp64-steps", type=int, default=1)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        return run_reference(args, rank)
+
+    import torch
+    import paper_2607_00755_b300 as kx
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    ctx = kx.Context(local)
+    stream = torch.cuda.current_stream()
+    c, B, f0, par = workload()
+    q, sig, src = c["q"], c["sigmas"], c["sources"]
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
+
+    def one_step(precision):
+        k = ctx.build_kernel(q, precision=precision)
+        fd = torch.as_tensor(f0, device="cuda")
+        res = ctx.solve(k, fd, sig, sources=src, **par)
+        k.release()
+        return res
+
+    def barrier():
+        torch.cuda.synchronize()
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    for _ in range(args.warmup):
+        one_step(kx.FP32)
+    uuid = "GPU-" + str(torch.cuda.get_device_properties(local).uuid)
+    barrier()
+    clocks = ClockSampler(uuid)
+    launches0 = ctx.launch_count()
+    total_ms, evals, solves, results = 0.0, 0, 0, []
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    for _ in range(args.steps):
+        flush.zero_()                      # cold L2 before each step (not timed)
+        e0.record(stream)
+        res = one_step(kx.FP32)
+        e1.record(stream)
+        e1.synchronize()
+        total_ms += e0.elapsed_time(e1)
+        evals += sum(r["evals"] for r in res)
+        solves += len(res)
+        results += res
+    barrier()
+    launches = ctx.launch_count() - launches0
+    clk = clocks.stop()
+    t_local = total_ms
+    if dist is not None:
+        t = torch.tensor([total_ms], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+        cnt = torch.tensor([evals, solves], device="cuda", dtype=torch.float64)
+        dist.all_reduce(cnt)
+        evals, solves = int(cnt[0].item()), int(cnt[1].item())
+    value = evals / (total_ms / 1e3)
+    solves_per_s = solves / (total_ms / 1e3)
+    bad = [r for r in results if r["status"] != 0 or not r["converged"]]
+
+    # ---- end to end through the public API with host buffers ------------------
+    e2e_t, e2e_evals = 0.0, 0
+    h2d = q.nbytes + f0.nbytes + src["shape"].nbytes * 1
+    d2h = f0.nbytes
+    for _ in range(max(1, args.steps)):
+        flush.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        k = ctx.build_kernel(q, precision=kx.FP32)
+        fh, res = ctx.solve_host(k, f0, sig, sources=src, **par)
+        k.release()
+        torch.cuda.synchronize()
+        e2e_t += time.perf_counter() - t0
+        e2e_evals += sum(r["evals"] for r in res)
+
+    # ---- plain FP64 path on the same inputs ------------------------------------
+    fp64 = None
+    if args.fp64_steps > 0:
+        one_step(kx.FP64)
+        t64, ev64 = 0.0, 0
+        for _ in range(args.fp64_steps):
+            flush.zero_()
+            e0.record(stream)
+            res = one_step(kx.FP64)
+            e1.record(stream)
+            e1.synchronize()
+            t64 += e0.elapsed_time(e1)
+            ev64 += sum(r["evals"] for r in res)
+        fp64 = {"value": ev64 / (t64 / 1e3), "unit": UNIT, "ms_per_step": t64 / args.fp64_steps,
+                "solves_per_s": B * args.fp64_steps / (t64 / 1e3)}
+
+    # ---- roofline of the dominant kernel (FP32 contraction) --------------------
+    hbm, src_peak = peaks()
+    n = q.size
+    U = n * n * (n + 1) // 2
+    V = sum((n - a + 3) // 4 for a in range(n))
+    kk = ctx.build_kernel(q, precision=kx.FP32)
+    fdev = torch.as_tensor(f0, device="cuda")
+    ms_cold = ctx.time_contraction(kk, fdev, iters=30, flush_bytes=L2_FLUSH_BYTES)
+    ms_warm = ctx.time_contraction(kk, fdev, iters=30, flush_bytes=0)
+    kk.release()
+    alg_bytes = 8 * U + 4 * V
+    achieved = alg_bytes / (ms_cold * 1e-3) / 1e9
+    roof = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+            "frac": achieved / hbm, "traffic": None,
+            "kernel": "k_contract32<4> (N=128, 4 instances per pass)",
+            "algorithmic_bytes_per_launch": alg_bytes, "avg_launch_ms_cold_l2": ms_cold,
+            "avg_launch_ms_warm_l2": ms_warm, "peak_source": src_peak}
+    # streaming single-instance roofline at N=384 (tables 227 MB > L2)
+    q384 = ki.log_grid(384, 1e-3, 1e2)
+    k384 = ctx.build_kernel(q384, precision=kx.FP32)
+    f384 = torch.as_tensor(ki.batch_bimodal(np.random.default_rng(7), q384, 1), device="cuda")
+    ms384 = ctx.time_contraction(k384, f384, iters=30, flush_bytes=L2_FLUSH_BYTES)
+    k384.release()
+    U384 = 384 * 384 * 385 // 2
+    V384 = sum((384 - a + 3) // 4 for a in range(384))
+    b384 = 8 * U384 + 4 * V384
+    roof384 = {"bound": "hbm", "achieved": b384 / (ms384 * 1e-3) / 1e9, "peak": hbm,
+               "unit": "GB/s", "frac": b384 / (ms384 * 1e-3) / 1e9 / hbm, "traffic": None,
+               "kernel": "k_contract32<1> (N=384, single instance, cold L2)",
+               "algorithmic_bytes_per_launch": b384, "avg_launch_ms": ms384,
+               "evals_per_s": 1e3 / ms384}
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        e, t, cores = oracle_sample(c, B, 12.0)
+        cpu = {"value": e / t, "unit": UNIT, "cores": cores, "kind": "oracle",
+               "sample": f"{e} RHS evaluations (tensor-form C + projection + sources) of the "
+                         f"N=128 workload's first Heun attempts in {t:.1f} s"}
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+                "steps": args.steps, "warmup": args.warmup,
+                "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+                "data": "synthetic", "config": config_desc(c, B),
+                "solves_per_s": solves_per_s,
+                "fp64_path": fp64,
+                "speedup_vs_fp64": (value / fp64["value"]) if fp64 else None,
+                "failed_solves": len(bad),
+                "roofline": roof, "roofline_streaming_n384": roof384,
+                "cpu_baseline": cpu,
+                "e2e": {"value": e2e_evals / e2e_t, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+                        "d2h_bytes_per_step": int(d2h)},
+                "gpu_launches": int(launches), "clocks": clk}
+        print(json.dumps(line), flush=True)
+    del t_local
+    if dist is not None:
+        dist.barrier()
+        dist.destroy_process_group()
+    ctx.close()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,222 @@
+/*
+ * kx.h -- C ABI of the B300 collision-operator library (libkx.so).
+ *
+ * The library evaluates the discretised 2->2 elastic self-collision term of a
+ * dark-sector momentum distribution (arXiv 2607.00755, "KineticXGPU"):
+ *
+ *   C_i[f] = sum_{n,m} W_inm [ f_n f_m - f_i f_t(i,n,m) ]            (Sec. 4.1,
+ *            eq. discrete_collision_operator; Appendix A, eq. app_dense_collision)
+ *
+ * with the precomputed kernel tensor W (eq. discrete_weight, eq. app_F_1d), the
+ * log-energy interpolation of f at the fourth momentum (eqs. app_interp_weights,
+ * app_log_interp), the two-moment conservation projection (Appendix B,
+ * eqs. app_self_projection, app_projection_system) and the adaptive Heun time
+ * integration of df/dt = C[f] + S(t) (Sec. 4.2) in the static box (a fixed,
+ * H = 0) with synthetic freeze-in sources.
+ *
+ * Conventions for every entry point:
+ *  - Return value: KX_OK (0), KX_PENDING (1) or a negative KX_E* code.  No C++
+ *    exception crosses the ABI.  kx_strerror() names a code; kx_last_error()
+ *    returns the last detailed message of a context.
+ *  - Pointers named *_dev are device pointers owned by the caller; they must be
+ *    valid for the context's device and are used on the context's stream.
+ *    Pointers named *_host (and all struct members) are host memory, read during
+ *    the call only.  Device arrays of a batch are row-major [batch][n] FP64.
+ *  - The library owns kernels (reference counted), the context's scratch space
+ *    and the serving state.
+ *  - Units: momenta and mass in the same unit; the cross-section sigma enters
+ *    as |M|^2 = 64 pi m^2 sigma (Table 1 caption: sigma_T/m = lambda^2/(64 pi m^3)
+ *    with |M|^2 = lambda^2 for the contact interaction of Sec. 3), g_chi = 1.
+ *  - Threading: one context per host thread.  Calls on one context are not
+ *    re-entrant.  kx_submit/kx_poll may be called from the owning thread while
+ *    the serving loop runs on its own worker thread.
+ */
+#ifndef KX_H_
+#define KX_H_
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ------------------------------------------------------------ status codes */
+#define KX_OK 0
+#define KX_PENDING 1       /* kx_poll: request not finished yet */
+#define KX_EINVAL -1       /* bad argument: n < 4 or > 512, q not ascending/positive, m <= 0, ... */
+#define KX_ENOMEM -2       /* device or host allocation failed */
+#define KX_EADMIT -3       /* serving: footprint above the configured budget; retry later */
+#define KX_ENEG -4         /* fixed-step integration produced a negative f */
+#define KX_ENONFINITE -5   /* a NaN/Inf appeared in f or C */
+#define KX_ESINGULAR -6    /* projection 2x2 system singular; alpha = beta = 0 used */
+#define KX_ENOCONV -7      /* integration hit max_attempts before finishing */
+#define KX_ETIMEOUT -8     /* a bounded device or host wait expired */
+#define KX_ECUDA -9        /* a CUDA runtime/driver call failed (see kx_last_error) */
+#define KX_ENOTSUP -10     /* option not supported by this build (e.g. quantum statistics) */
+
+/* -------------------------------------------------------------- options */
+#define KX_MEASURE_ENERGY 0   /* W = dE_n dE_m F / (2 E_i g): F of eq. app_F_2d is the kernel of dE_n dE_m (default) */
+#define KX_MEASURE_LITERAL 1  /* W = Dp_n Dp_m F / (2 E_i g): eq. discrete_weight read literally */
+
+#define KX_FP64 0        /* plain FP64 path: FP64 tensor (18 B/element), FP64 contraction */
+#define KX_FP32 1        /* FP32 streaming path: FP32 W + packed (j_L, omega) (8 B/element), FP32 math, FP64 sums */
+#define KX_SPLIT_BF16 2  /* batched path: gain on tcgen05 tensor cores in split BF16, exact FP32 loss */
+
+typedef struct kx_ctx kx_ctx;
+typedef struct kx_kernel kx_kernel;
+typedef uint64_t kx_ticket;
+
+/* Momentum grid and kernel options (Appendix A).  q is the comoving momentum
+ * grid (host, length n, strictly ascending, > 0); p_i = q_i / a, E_i = sqrt(p_i^2 + m^2);
+ * widths Dq_i are the trapezoid widths in q (the paper leaves w_i unspecified).
+ * n_mu = Gauss-Legendre nodes of the mu integral of eq. app_F_1d (the paper uses 18). */
+typedef struct {
+    int n;            /* 4 <= n <= 512 */
+    const double *q;  /* host [n] */
+    double a;         /* scale factor > 0 (1 for the static box) */
+    double mass;      /* m_chi > 0 */
+    int n_mu;         /* 1 <= n_mu <= 64 */
+    int measure;      /* KX_MEASURE_ENERGY | KX_MEASURE_LITERAL */
+    int stats;        /* 0 = dilute f3 f4 - f1 f2 (eq. Lambda dilute); +-1 (quantum) -> KX_ENOTSUP */
+    int precision;    /* KX_FP64 | KX_FP32 | KX_SPLIT_BF16 */
+} kx_grid_desc;
+
+/* Synthetic freeze-in sources: S_i(t) = sum_k rate_k env_k(t) shape_k,i / sum_j h_j shape_k,j,
+ * env_k(t) = exp(-(t - t_on_k)/tau_k) for t >= t_on_k, else 0.  The library
+ * normalises each shape row so that rate_k is the number injection rate. */
+typedef struct {
+    int n_src;             /* 0..4 */
+    const double *shape;   /* host [n_src][n], >= 0 */
+    const double *rate;    /* host [n_src] */
+    const double *tau;     /* host [n_src], > 0 */
+    const double *t_on;    /* host [n_src] */
+} kx_source;
+
+/* Integration controls (Sec. 4.2 adaptive Heun; controller details are this
+ * library's reading: err = max_i |f_c - f_p| / (atol + rtol |f_c|), accept if
+ * err <= 1 and no negative stage, h <- h min(5, max(0.2, 0.9 err^-1/2)),
+ * a negative stage halves h). */
+typedef struct {
+    double t0, t_end, h0;
+    double rtol, atol;      /* typical: 1e-6, 1e-12 max f0 */
+    double h_min, h_max;
+    double l1_tol;          /* stop when sources are off and L1(f, MB fit) <= l1_tol (<= 0: run to t_end) */
+    int max_attempts;       /* accepted + rejected attempts before KX_ENOCONV */
+    int fixed_step;         /* 1: constant h = h0, always accept, negative stage -> KX_ENEG */
+    int check_every;        /* MB test every k accepted steps */
+    int project;            /* 1: use the projected operator (Appendix B) */
+} kx_solve_params;
+
+/* Projection diagnostics (Appendix B: eq. app_epsilon_definition and
+ * eq. app_projection_relative_correction). */
+typedef struct {
+    double eps_N_raw, eps_E_raw, eps_N_proj, eps_E_proj;
+    double R_N, R_E, alpha, beta;
+    double f_max;
+    int singular;   /* det guard fired (alpha = beta = 0) */
+    int status;     /* KX_OK or KX_ENONFINITE for this instance */
+} kx_diag;
+
+typedef struct {
+    double t, h, l1_to_mb, T_mb, ln_z_mb, latency_s;
+    long long steps, rejects, evals;
+    int status;       /* KX_OK, KX_ENEG, KX_ENONFINITE, KX_ENOCONV, KX_ETIMEOUT */
+    int converged;    /* stopping test met */
+} kx_result;
+
+typedef struct {
+    int n, n_mu, measure, precision;
+    long long unique_elements;   /* U = n^2 (n+1)/2 (i, n <= m) elements */
+    long long nonzero_elements;  /* elements inside the kinematic support */
+    long long tensor_bytes;      /* device bytes of the kernel tables */
+    double build_ms;             /* device time of the build */
+} kx_kernel_info;
+
+/* ------------------------------------------------------------- context */
+/* Create a context on CUDA device `device` that enqueues work on `cuda_stream`
+ * (a cudaStream_t; NULL = legacy default stream).  KX_EINVAL/KX_ECUDA on failure. */
+int kx_create(kx_ctx **out, int device, void *cuda_stream);
+void kx_destroy(kx_ctx *ctx);
+int kx_set_stream(kx_ctx *ctx, void *cuda_stream);
+const char *kx_strerror(int code);
+const char *kx_last_error(const kx_ctx *ctx);
+
+/* --------------------------------------------------------------- kernel */
+/* Build the kernel tensor of eq. discrete_weight for one grid (Appendix A):
+ * W_inm = mu_n mu_m F_inm / (2 E_i g) with |M|^2 = 1 (sigma scales it at call
+ * time), F from Gauss-Legendre over the closed-form nu integral (equal to the
+ * printed arcsin form, eq. app_I_mu), zero outside E_0 <= E_n + E_m - E_i <= E_{n-1};
+ * symmetrised over (n, m) and stored for n <= m, with the interpolation bracket
+ * j_L and weight omega per element.  Runs on the device (FP64), synchronises
+ * the stream.  The handle starts with reference count 1. */
+int kx_build_kernel(kx_ctx *ctx, const kx_grid_desc *desc, kx_kernel **out);
+void kx_kernel_retain(kx_kernel *k);
+void kx_kernel_release(kx_kernel *k);
+int kx_kernel_get_info(const kx_kernel *k, kx_kernel_info *info);
+/* Copy the grid as the library sees it (host arrays [n], any may be NULL). */
+int kx_kernel_grid(const kx_kernel *k, double *p, double *E, double *dp, double *dE, double *h);
+/* Copy the symmetrised FP64 tables of row i (host arrays [n(n+1)/2] in
+ * (n, m >= n) row-major pair order; any may be NULL).  KX_FP64 kernels only. */
+int kx_kernel_row(const kx_kernel *k, int i, double *W, int *jL, double *omega);
+
+/* ------------------------------------------------------------ collision */
+/* Evaluate C[f] for `batch` distributions sharing one kernel (eq.
+ * discrete_collision_operator, dilute), scaled by |M|^2 = 64 pi m^2 sigma_b.
+ * f_dev, C_dev: device [batch][n] FP64.  project = 1 applies the two-moment
+ * projection (Appendix B).  diag_host: NULL, or host [batch] (requires a
+ * stream synchronisation inside the call).  Without diag the call only
+ * enqueues work on the stream.  KX_ENONFINITE is reported through diag. */
+int kx_collision(kx_ctx *ctx, const kx_kernel *k, int batch, const double *sigma_host,
+                 const double *f_dev, double *C_dev, int project, kx_diag *diag_host);
+
+/* Same as kx_collision with host input/output arrays (host [batch][n]); the
+ * copies run on the context's stream; returns after C_host is written. */
+int kx_collision_host(kx_ctx *ctx, const kx_kernel *k, int batch, const double *sigma_host,
+                      const double *f_host, double *C_host, int project, kx_diag *diag_host);
+
+/* ---------------------------------------------------------- integration */
+/* One Heun attempt per instance (Sec. 4.2): k1 = RHS(f, t), f_p = f + h k1,
+ * k2 = RHS(f_p, t + h), f_c = f + h/2 (k1 + k2); accept/reject and the next h
+ * as described at kx_solve_params.  t_host, h_host: host [batch], updated.
+ * src: NULL, one source set shared by all instances (n_src_sets = 1) or one per
+ * instance (n_src_sets = batch).  res_host: host [batch] (may be NULL). */
+int kx_step(kx_ctx *ctx, const kx_kernel *k, int batch, const double *sigma_host,
+            const kx_source *src, int n_src_sets, const kx_solve_params *par,
+            double *t_host, double *h_host, double *f_dev, kx_result *res_host);
+
+/* Integrate every instance until its stopping test, t_end or max_attempts.
+ * The step loop is device resident (captured CUDA graph of Heun attempts with
+ * on-device accept/reject, step-size control and MB stopping test); the host
+ * only polls a status word.  f_dev: device [batch][n], in/out. */
+int kx_solve(kx_ctx *ctx, const kx_kernel *k, int batch, const double *sigma_host,
+             const kx_source *src, int n_src_sets, const kx_solve_params *par,
+             double *f_dev, kx_result *res_host);
+
+/* Same as kx_solve with host f (host [batch][n], in/out). */
+int kx_solve_host(kx_ctx *ctx, const kx_kernel *k, int batch, const double *sigma_host,
+                  const kx_source *src, int n_src_sets, const kx_solve_params *par,
+                  double *f_host, kx_result *res_host);
+
+/* ------------------------------------------------------------ profiling */
+/* Number of this library's kernels enqueued through `ctx` so far (a captured
+ * graph counts each of its kernel nodes at every launch). */
+long long kx_launch_count(const kx_ctx *ctx);
+
+/* Time the contraction kernel alone (eq. discrete_collision_operator, the
+ * O(N^3) step) for `batch` instances of f_dev: prepares the inputs once, then
+ * launches the contraction `iters` times on the context's stream bracketed by
+ * CUDA events and returns the mean device time per launch in *avg_ms.  If
+ * flush_bytes > 0, a device buffer of that size (allocated here) is rewritten
+ * between launches, outside the timed events, so each launch starts with a
+ * cold L2.  Synchronises the stream. */
+int kx_time_contraction(kx_ctx *ctx, const kx_kernel *k, int batch, const double *f_dev,
+                        int iters, long long flush_bytes, double *avg_ms);
+
+/* Moment-matched discrete Maxwell-Boltzmann fit used by the stopping test:
+ * out_host[batch][3] = (T, ln z, L1) with L1 = sum h |f - f_MB| / sum h f. */
+int kx_mb_fit(kx_ctx *ctx, const kx_kernel *k, int batch, const double *f_dev, double *out_host);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* KX_H_ */

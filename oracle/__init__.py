@@ -66,6 +66,7 @@ def _load():
         "oracle_mb_fit": (i, [i, vp, vp, vp, vp]),
         "oracle_solve": (i, [i, vp, d, d, vp, d, i, vp, vp, vp, vp, vp, vp, vp]),
         "oracle_M2_from_sigma": (d, [d, d]),
+        "oracle_collision_rows": (i, [i, vp, d, d, d, i, i, vp, i, vp, vp, vp, vp]),
         "oracle_num_threads": (i, []),
         "oracle_set_threads": (None, [i]),
     }
@@ -189,6 +190,18 @@ def collision_direct(q, f, a=1.0, mass=1.0, M2=1.0, n_mu=18, measure=MEASURE_ENE
     if rc:
         raise ValueError(rc)
     return C
+
+
+def collision_rows(q, f, rows, a=1.0, mass=1.0, M2=1.0, n_mu=18, measure=MEASURE_ENERGY):
+    """C_raw, G and nu of selected rows (direct form, no stored tensor)."""
+    q, f = _f64(q), _f64(f)
+    rows = np.ascontiguousarray(rows, dtype=np.int32)
+    C, G, L = (np.empty(rows.size) for _ in range(3))
+    rc = _load().oracle_collision_rows(q.size, _p(q), a, mass, M2, n_mu, measure, _p(f),
+                                       rows.size, _p(rows), _p(C), _p(G), _p(L))
+    if rc:
+        raise ValueError(rc)
+    return C, G, L
 
 
 DIAG_KEYS = ("eps_N_raw", "eps_E_raw", "eps_N_proj", "eps_E_proj", "R_N", "R_E",

@@ -708,3 +708,51 @@ out:
 double oracle_M2_from_sigma(double mass, double sigma) {
     return 64.0 * OR_PI * mass * mass * sigma;
 }
+
+/* Selected rows of C_raw (direct form, F on the fly from eq. app_F_1d with the
+ * closed-form nu integral) for sampled checks at sizes where the full N^3 tensor
+ * is too large for the oracle.  rows[nrows] are row indices; C[nrows]; the gain
+ * G and loss rate nu of those rows are returned too (may be NULL). */
+int oracle_collision_rows(int n, const double *q, double a, double mass, double M2,
+                          int n_mu, int measure, const double *f, int nrows, const int *rows,
+                          double *C, double *gain, double *loss_rate) {
+    double *p = malloc(sizeof(double) * n), *E = malloc(sizeof(double) * n);
+    double *dp = malloc(sizeof(double) * n), *dE = malloc(sizeof(double) * n);
+    double *h = malloc(sizeof(double) * n), *lf = malloc(sizeof(double) * n);
+    double *x = malloc(sizeof(double) * (n_mu > 0 ? n_mu : 1));
+    double *w = malloc(sizeof(double) * (n_mu > 0 ? n_mu : 1));
+    int rc = OR_OK;
+    if (!p || !E || !dp || !dE || !h || !lf || !x || !w) { rc = OR_ENOMEM; goto out; }
+    rc = oracle_grid(n, q, a, mass, p, E, dp, dE, h);
+    if (rc) goto out;
+    if (n_mu < 1) { rc = OR_EINVAL; goto out; }
+    oracle_gauss_legendre(n_mu, x, w);
+    for (int j = 0; j < n; ++j) lf[j] = log_floor(f[j]);
+#pragma omp parallel for schedule(dynamic)
+    for (int r = 0; r < nrows; ++r) {
+        int i = rows[r];
+        double Ci = 0.0, Gi = 0.0, Li = 0.0;
+        for (int nn = 0; nn < n; ++nn) {
+            for (int mm = 0; mm < n; ++mm) {
+                double Et = (E[nn] + E[mm]) - E[i];
+                int j;
+                double om;
+                if (!oracle_bracket(n, E, Et, &j, &om)) continue;
+                double F = oracle_F(mass, M2, p[i], p[nn], p[mm], E[i], E[nn], E[mm], n_mu, x, w, 0);
+                double mun = measure == 1 ? dp[nn] : dE[nn];
+                double mum = measure == 1 ? dp[mm] : dE[mm];
+                double Wv = mun * mum * F / (2.0 * E[i] * 1.0);
+                double ft = exp((1.0 - om) * lf[j] + om * lf[j + 1]);
+                Ci += Wv * (f[nn] * f[mm] - f[i] * ft);
+                Gi += Wv * (f[nn] * f[mm]);
+                Li += Wv * ft;
+            }
+        }
+        C[r] = Ci;
+        if (gain) gain[r] = Gi;
+        if (loss_rate) loss_rate[r] = Li;
+    }
+out:
+    free(p); free(E); free(dp); free(dE); free(h); free(lf); free(x); free(w);
+    return rc;
+}

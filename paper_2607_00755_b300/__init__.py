@@ -1,0 +1,335 @@
+"""Thin Python binding of libkx (the B300 collision-operator library).
+
+Argument marshalling only: every step of the computation runs in the CUDA
+kernels of ``libkx.so`` behind the C ABI of ``include/kx.h``.  torch is used
+for device memory and streams.  Loading fails loudly if the library has not
+been built (``python -m paper_2607_00755_b300.build``); there is no CPU path.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libkx.so")
+
+OK, PENDING = 0, 1
+EINVAL, ENOMEM, EADMIT, ENEG, ENONFINITE = -1, -2, -3, -4, -5
+ESINGULAR, ENOCONV, ETIMEOUT, ECUDA, ENOTSUP = -6, -7, -8, -9, -10
+MEASURE_ENERGY, MEASURE_LITERAL = 0, 1
+FP64, FP32, SPLIT_BF16 = 0, 1, 2
+
+EXPORTS = (
+    "kx_create", "kx_destroy", "kx_set_stream", "kx_strerror", "kx_last_error",
+    "kx_build_kernel", "kx_kernel_retain", "kx_kernel_release", "kx_kernel_get_info",
+    "kx_kernel_grid", "kx_kernel_row", "kx_collision", "kx_collision_host", "kx_step",
+    "kx_solve", "kx_solve_host", "kx_mb_fit", "kx_launch_count", "kx_time_contraction",
+)
+
+
+class GridDesc(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int), ("q", ctypes.c_void_p), ("a", ctypes.c_double),
+                ("mass", ctypes.c_double), ("n_mu", ctypes.c_int), ("measure", ctypes.c_int),
+                ("stats", ctypes.c_int), ("precision", ctypes.c_int)]
+
+
+class Source(ctypes.Structure):
+    _fields_ = [("n_src", ctypes.c_int), ("shape", ctypes.c_void_p), ("rate", ctypes.c_void_p),
+                ("tau", ctypes.c_void_p), ("t_on", ctypes.c_void_p)]
+
+
+class SolveParams(ctypes.Structure):
+    _fields_ = [("t0", ctypes.c_double), ("t_end", ctypes.c_double), ("h0", ctypes.c_double),
+                ("rtol", ctypes.c_double), ("atol", ctypes.c_double), ("h_min", ctypes.c_double),
+                ("h_max", ctypes.c_double), ("l1_tol", ctypes.c_double),
+                ("max_attempts", ctypes.c_int), ("fixed_step", ctypes.c_int),
+                ("check_every", ctypes.c_int), ("project", ctypes.c_int)]
+
+
+class Diag(ctypes.Structure):
+    _fields_ = [(k, ctypes.c_double) for k in ("eps_N_raw", "eps_E_raw", "eps_N_proj",
+                                               "eps_E_proj", "R_N", "R_E", "alpha", "beta",
+                                               "f_max")] + \
+               [("singular", ctypes.c_int), ("status", ctypes.c_int)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class Result(ctypes.Structure):
+    _fields_ = [(k, ctypes.c_double) for k in ("t", "h", "l1_to_mb", "T_mb", "ln_z_mb",
+                                               "latency_s")] + \
+               [(k, ctypes.c_longlong) for k in ("steps", "rejects", "evals")] + \
+               [("status", ctypes.c_int), ("converged", ctypes.c_int)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class KernelInfo(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int), ("n_mu", ctypes.c_int), ("measure", ctypes.c_int),
+                ("precision", ctypes.c_int), ("unique_elements", ctypes.c_longlong),
+                ("nonzero_elements", ctypes.c_longlong), ("tensor_bytes", ctypes.c_longlong),
+                ("build_ms", ctypes.c_double)]
+
+
+_lib = None
+
+
+def load_library(path: str = LIB_PATH):
+    """Load libkx.so (raises if it is missing: the product has no fallback)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"libkx.so not built at {path}; run python -m paper_2607_00755_b300.build")
+    lib = ctypes.CDLL(path)
+    i, vp, d = ctypes.c_int, ctypes.c_void_p, ctypes.c_double
+    sig = {
+        "kx_create": (i, [vp, i, vp]),
+        "kx_destroy": (None, [vp]),
+        "kx_set_stream": (i, [vp, vp]),
+        "kx_strerror": (ctypes.c_char_p, [i]),
+        "kx_last_error": (ctypes.c_char_p, [vp]),
+        "kx_build_kernel": (i, [vp, ctypes.POINTER(GridDesc), vp]),
+        "kx_kernel_retain": (None, [vp]),
+        "kx_kernel_release": (None, [vp]),
+        "kx_kernel_get_info": (i, [vp, ctypes.POINTER(KernelInfo)]),
+        "kx_kernel_grid": (i, [vp, vp, vp, vp, vp, vp]),
+        "kx_kernel_row": (i, [vp, i, vp, vp, vp]),
+        "kx_collision": (i, [vp, vp, i, vp, vp, vp, i, vp]),
+        "kx_collision_host": (i, [vp, vp, i, vp, vp, vp, i, vp]),
+        "kx_step": (i, [vp, vp, i, vp, vp, i, ctypes.POINTER(SolveParams), vp, vp, vp, vp]),
+        "kx_solve": (i, [vp, vp, i, vp, vp, i, ctypes.POINTER(SolveParams), vp, vp]),
+        "kx_solve_host": (i, [vp, vp, i, vp, vp, i, ctypes.POINTER(SolveParams), vp, vp]),
+        "kx_mb_fit": (i, [vp, vp, i, vp, vp]),
+        "kx_launch_count": (ctypes.c_longlong, [vp]),
+        "kx_time_contraction": (i, [vp, vp, i, vp, i, ctypes.c_longlong, vp]),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+class KxError(RuntimeError):
+    def __init__(self, code, msg=""):
+        self.code = code
+        super().__init__(f"kx error {code}: {msg}")
+
+
+def _np(a, dtype=np.float64):
+    return np.ascontiguousarray(a, dtype=dtype)
+
+
+def _ptr(a):
+    return ctypes.c_void_p(a.ctypes.data)
+
+
+def _dptr(t):
+    """Device pointer of a contiguous CUDA float64 torch tensor."""
+    import torch
+    if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.float64
+            and t.is_contiguous()):
+        raise TypeError("expected a contiguous CUDA float64 tensor")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+class Context:
+    """kx_ctx bound to a CUDA device and a torch stream."""
+
+    def __init__(self, device: int = 0, stream=None):
+        import torch
+        self.lib = load_library()
+        self.device = device
+        if stream is None:
+            stream = torch.cuda.current_stream(device)
+        self.stream = stream
+        h = ctypes.c_void_p()
+        rc = self.lib.kx_create(ctypes.byref(h), device, ctypes.c_void_p(stream.cuda_stream))
+        if rc:
+            raise KxError(rc, "kx_create")
+        self.h = h
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.kx_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def error(self, rc, what):
+        msg = self.lib.kx_last_error(self.h) or b""
+        return KxError(rc, f"{what}: {self.lib.kx_strerror(rc).decode()} {msg.decode()}")
+
+    # -------------------------------------------------------------- kernels
+    def build_kernel(self, q, mass=1.0, a=1.0, n_mu=18, measure=MEASURE_ENERGY,
+                     precision=FP64, stats=0):
+        q = _np(q)
+        desc = GridDesc(q.size, q.ctypes.data, a, mass, n_mu, measure, stats, precision)
+        h = ctypes.c_void_p()
+        rc = self.lib.kx_build_kernel(self.h, ctypes.byref(desc), ctypes.byref(h))
+        if rc:
+            raise self.error(rc, "kx_build_kernel")
+        return Kernel(self, h, q.size)
+
+    # ------------------------------------------------------------ collision
+    def collision(self, kernel, f, sigma=1.0, project=True, out=None, diag=False):
+        """C[f] for f of shape [B, n] (CUDA float64); returns (C, diag list|None)."""
+        import torch
+        f2 = f if f.dim() == 2 else f.view(1, -1)
+        B = f2.shape[0]
+        sig = _np(np.broadcast_to(np.asarray(sigma, dtype=np.float64), (B,)))
+        C = out if out is not None else torch.empty_like(f2)
+        dg = (Diag * B)() if diag else None
+        rc = self.lib.kx_collision(self.h, kernel.h, B, _ptr(sig), _dptr(f2), _dptr(C),
+                                   int(project), dg)
+        if rc and not (rc == ENONFINITE and diag):
+            raise self.error(rc, "kx_collision")
+        return C.view_as(f), ([x.as_dict() for x in dg] if diag else None)
+
+    def collision_host(self, kernel, f, sigma=1.0, project=True, diag=False):
+        f2 = _np(np.atleast_2d(f))
+        B = f2.shape[0]
+        sig = _np(np.broadcast_to(np.asarray(sigma, dtype=np.float64), (B,)))
+        C = np.empty_like(f2)
+        dg = (Diag * B)() if diag else None
+        rc = self.lib.kx_collision_host(self.h, kernel.h, B, _ptr(sig), _ptr(f2), _ptr(C),
+                                        int(project), dg)
+        if rc and not (rc == ENONFINITE and diag):
+            raise self.error(rc, "kx_collision_host")
+        return C.reshape(np.shape(f)), ([x.as_dict() for x in dg] if diag else None)
+
+    # ---------------------------------------------------------- integration
+    @staticmethod
+    def _sources(sources, B, n):
+        """sources: None, one dict (shared) or a list of B dicts."""
+        if sources is None:
+            return None, 0, []
+        lst = [sources] if isinstance(sources, dict) else list(sources)
+        keep = []
+        arr = (Source * len(lst))()
+        for s, src in enumerate(lst):
+            shape = _np(np.atleast_2d(src["shape"]))
+            rate, tau, t_on = (_np(src[k]) for k in ("rate", "tau", "t_on"))
+            keep += [shape, rate, tau, t_on]
+            arr[s] = Source(shape.shape[0], shape.ctypes.data, rate.ctypes.data,
+                            tau.ctypes.data, t_on.ctypes.data)
+        return arr, len(lst), keep
+
+    @staticmethod
+    def params(**kw):
+        p = dict(t0=0.0, t_end=1.0, h0=1e-3, rtol=1e-6, atol=1e-12, h_min=0.0, h_max=0.0,
+                 l1_tol=0.0, max_attempts=1_000_000, fixed_step=0, check_every=10, project=1)
+        p.update(kw)
+        return SolveParams(**{k: p[k] for k, _ in SolveParams._fields_})
+
+    def solve(self, kernel, f, sigma, sources=None, **params):
+        """Integrate f ([B, n] CUDA float64, in place).  Returns list of result dicts."""
+        f2 = f if f.dim() == 2 else f.view(1, -1)
+        B = f2.shape[0]
+        sig = _np(np.broadcast_to(np.asarray(sigma, dtype=np.float64), (B,)))
+        src, ns, keep = self._sources(sources, B, kernel.n)
+        par = self.params(**params)
+        res = (Result * B)()
+        rc = self.lib.kx_solve(self.h, kernel.h, B, _ptr(sig), src, ns, ctypes.byref(par),
+                               _dptr(f2), res)
+        del keep
+        if rc in (EINVAL, ENOMEM, ECUDA, ETIMEOUT, ENOTSUP):
+            raise self.error(rc, "kx_solve")
+        return [r.as_dict() for r in res]
+
+    def solve_host(self, kernel, f, sigma, sources=None, **params):
+        """Host-buffer variant: f numpy [B, n] copied in and out inside the call."""
+        f2 = _np(np.atleast_2d(f)).copy()
+        B = f2.shape[0]
+        sig = _np(np.broadcast_to(np.asarray(sigma, dtype=np.float64), (B,)))
+        src, ns, keep = self._sources(sources, B, kernel.n)
+        par = self.params(**params)
+        res = (Result * B)()
+        rc = self.lib.kx_solve_host(self.h, kernel.h, B, _ptr(sig), src, ns, ctypes.byref(par),
+                                    _ptr(f2), res)
+        del keep
+        if rc in (EINVAL, ENOMEM, ECUDA, ETIMEOUT, ENOTSUP):
+            raise self.error(rc, "kx_solve_host")
+        return f2, [r.as_dict() for r in res]
+
+    def step(self, kernel, f, sigma, t, h, sources=None, **params):
+        """One Heun attempt per instance; t, h numpy [B] updated in place."""
+        f2 = f if f.dim() == 2 else f.view(1, -1)
+        B = f2.shape[0]
+        sig = _np(np.broadcast_to(np.asarray(sigma, dtype=np.float64), (B,)))
+        src, ns, keep = self._sources(sources, B, kernel.n)
+        par = self.params(**params)
+        res = (Result * B)()
+        rc = self.lib.kx_step(self.h, kernel.h, B, _ptr(sig), src, ns, ctypes.byref(par),
+                              _ptr(t), _ptr(h), _dptr(f2), res)
+        del keep
+        if rc in (EINVAL, ENOMEM, ECUDA, ETIMEOUT, ENOTSUP):
+            raise self.error(rc, "kx_step")
+        return [r.as_dict() for r in res]
+
+    def launch_count(self) -> int:
+        return int(self.lib.kx_launch_count(self.h))
+
+    def time_contraction(self, kernel, f, iters=20, flush_bytes=0):
+        """Mean device time (ms) of one contraction launch for f [B, n]."""
+        f2 = f if f.dim() == 2 else f.view(1, -1)
+        ms = ctypes.c_double()
+        rc = self.lib.kx_time_contraction(self.h, kernel.h, f2.shape[0], _dptr(f2), int(iters),
+                                          int(flush_bytes), ctypes.byref(ms))
+        if rc:
+            raise self.error(rc, "kx_time_contraction")
+        return ms.value
+
+    def mb_fit(self, kernel, f):
+        f2 = f if f.dim() == 2 else f.view(1, -1)
+        out = np.empty((f2.shape[0], 3))
+        rc = self.lib.kx_mb_fit(self.h, kernel.h, f2.shape[0], _dptr(f2), _ptr(out))
+        if rc:
+            raise self.error(rc, "kx_mb_fit")
+        return out
+
+
+class Kernel:
+    """Reference-counted kernel-tensor handle (kx_kernel)."""
+
+    def __init__(self, ctx: Context, h, n: int):
+        self.ctx, self.h, self.n = ctx, h, n
+
+    def info(self):
+        inf = KernelInfo()
+        self.ctx.lib.kx_kernel_get_info(self.h, ctypes.byref(inf))
+        return {k: getattr(inf, k) for k, _ in KernelInfo._fields_}
+
+    def grid(self):
+        out = {k: np.empty(self.n) for k in ("p", "E", "dp", "dE", "h")}
+        self.ctx.lib.kx_kernel_grid(self.h, *(_ptr(out[k]) for k in ("p", "E", "dp", "dE", "h")))
+        return out
+
+    def row(self, i: int):
+        P = self.n * (self.n + 1) // 2
+        W, jl, om = np.empty(P), np.empty(P, dtype=np.int32), np.empty(P)
+        rc = self.ctx.lib.kx_kernel_row(self.h, i, _ptr(W), _ptr(jl), _ptr(om))
+        if rc:
+            raise self.ctx.error(rc, "kx_kernel_row")
+        return W, jl, om
+
+    def release(self):
+        if self.h:
+            self.ctx.lib.kx_kernel_release(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.release()
+        except Exception:
+            pass

@@ -1,0 +1,798 @@
+// kx_api.cu -- host side of the C ABI declared in include/kx.h.
+#include <math.h>
+#include <string.h>
+
+#include <algorithm>
+#include <chrono>
+#include <new>
+#include <string>
+#include <thread>
+#include <vector>
+
+#include "kx_internal.cuh"
+
+#define KX_PI_H 3.14159265358979323846
+
+int kx_set_error(kx_ctx *ctx, int code, const std::string &msg) {
+    if (ctx) ctx->last_error = msg;
+    return code;
+}
+
+extern "C" const char *kx_strerror(int code) {
+    switch (code) {
+    case KX_OK: return "ok";
+    case KX_PENDING: return "pending";
+    case KX_EINVAL: return "invalid argument";
+    case KX_ENOMEM: return "out of memory";
+    case KX_EADMIT: return "admission refused (footprint above budget)";
+    case KX_ENEG: return "negative distribution in a fixed step";
+    case KX_ENONFINITE: return "non-finite value";
+    case KX_ESINGULAR: return "singular projection system";
+    case KX_ENOCONV: return "no convergence within max_attempts";
+    case KX_ETIMEOUT: return "bounded wait expired";
+    case KX_ECUDA: return "CUDA error";
+    case KX_ENOTSUP: return "not supported";
+    default: return "unknown status";
+    }
+}
+
+extern "C" const char *kx_last_error(const kx_ctx *ctx) {
+    return ctx ? ctx->last_error.c_str() : "no context";
+}
+
+// ------------------------------------------------------------------ context
+extern "C" int kx_create(kx_ctx **out, int device, void *cuda_stream) {
+    if (!out) return KX_EINVAL;
+    *out = nullptr;
+    int count = 0;
+    if (cudaGetDeviceCount(&count) != cudaSuccess || device < 0 || device >= count)
+        return KX_ECUDA;
+    if (cudaSetDevice(device) != cudaSuccess) return KX_ECUDA;
+    kx_ctx *c = new (std::nothrow) kx_ctx();
+    if (!c) return KX_ENOMEM;
+    c->device = device;
+    c->stream = (cudaStream_t)cuda_stream;
+    c->d_arena = nullptr;
+    c->arena_bytes = 0;
+    c->h_pinned = nullptr;
+    c->pinned_bytes = 0;
+    c->launches = 0;
+    *out = c;
+    return KX_OK;
+}
+
+extern "C" void kx_destroy(kx_ctx *ctx) {
+    if (!ctx) return;
+    cudaSetDevice(ctx->device);
+    cudaStreamSynchronize(ctx->stream);
+    if (ctx->d_arena) cudaFree(ctx->d_arena);
+    if (ctx->h_pinned) cudaFreeHost(ctx->h_pinned);
+    delete ctx;
+}
+
+extern "C" int kx_set_stream(kx_ctx *ctx, void *cuda_stream) {
+    if (!ctx) return KX_EINVAL;
+    ctx->stream = (cudaStream_t)cuda_stream;
+    return KX_OK;
+}
+
+static int kx_arena_reserve(kx_ctx *ctx, size_t bytes) {
+    if (bytes <= ctx->arena_bytes) return KX_OK;
+    KX_CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
+    if (ctx->d_arena) cudaFree(ctx->d_arena);
+    ctx->d_arena = nullptr;
+    ctx->arena_bytes = 0;
+    size_t want = std::max(bytes, (size_t)1 << 20);
+    if (cudaMalloc(&ctx->d_arena, want) != cudaSuccess) {
+        cudaGetLastError();
+        return kx_set_error(ctx, KX_ENOMEM, "arena allocation failed");
+    }
+    ctx->arena_bytes = want;
+    return KX_OK;
+}
+
+static int kx_pinned_reserve(kx_ctx *ctx, size_t bytes) {
+    if (bytes <= ctx->pinned_bytes) return KX_OK;
+    KX_CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
+    if (ctx->h_pinned) cudaFreeHost(ctx->h_pinned);
+    ctx->h_pinned = nullptr;
+    ctx->pinned_bytes = 0;
+    size_t want = std::max(bytes, (size_t)1 << 16);
+    if (cudaMallocHost(&ctx->h_pinned, want) != cudaSuccess) {
+        cudaGetLastError();
+        return kx_set_error(ctx, KX_ENOMEM, "pinned allocation failed");
+    }
+    ctx->pinned_bytes = want;
+    return KX_OK;
+}
+
+static size_t kx_align(size_t x) { return (x + 255) & ~(size_t)255; }
+
+// Scratch views of one batched evaluation, carved from a base pointer.
+size_t kx_views_bytes(const kx_kernel *k, int B) {
+    const size_t n = k->n, chunks = kx_chunks_per_row(k);
+    size_t s = 0;
+    s += kx_align(sizeof(double) * B);               // fmax
+    s += kx_align(sizeof(double) * B * n);           // lf64
+    s += kx_align(sizeof(float2) * B * (n + 4));     // tl
+    s += kx_align(sizeof(float2) * B * n);           // td
+    s += kx_align(sizeof(double2) * B * n * chunks); // partial
+    s += kx_align(sizeof(int) * B);                  // flags
+    s += kx_align(sizeof(double) * B);               // M2
+    s += kx_align(sizeof(kx_diag) * B);              // diag
+    return s;
+}
+
+void kx_carve_views(const kx_kernel *k, int B, void *base, kx_batch_views *v) {
+    const size_t n = k->n;
+    const int chunks = kx_chunks_per_row(k);
+    char *p = (char *)base;
+    v->fmax = (double *)p; p += kx_align(sizeof(double) * B);
+    v->lf64 = (double *)p; p += kx_align(sizeof(double) * B * n);
+    v->tl = (float2 *)p; p += kx_align(sizeof(float2) * B * (n + 4));
+    v->td = (float2 *)p; p += kx_align(sizeof(float2) * B * n);
+    v->partial = (double2 *)p; p += kx_align(sizeof(double2) * B * n * chunks);
+    v->flags = (int *)p; p += kx_align(sizeof(int) * B);
+    v->M2 = (double *)p; p += kx_align(sizeof(double) * B);
+    v->diag = (kx_diag *)p; p += kx_align(sizeof(kx_diag) * B);
+    v->chunks = chunks;
+}
+
+// ----------------------------------------------------------------- kernel
+// Gauss-Legendre nodes on [-1, 1] (ascending): Newton's method on P_n started
+// from the Tricomi-type estimate cos(pi (4k - 1)/(4n + 2)); P_n, P_n' from the
+// Bonnet recurrence; w_k = 2 / ((1 - x_k^2) P_n'(x_k)^2).
+static void kx_gauss_legendre(int n, kx_gl_nodes *gl) {
+    for (int k = 1; k <= n; ++k) {
+        double x = cos(KX_PI_H * (4.0 * k - 1.0) / (4.0 * n + 2.0));
+        double dp = 1.0;
+        for (int it = 0; it < 64; ++it) {
+            double pkm1 = 1.0, pk = x;
+            for (int j = 2; j <= n; ++j) {
+                double pn = ((2.0 * j - 1.0) * x * pk - (j - 1.0) * pkm1) / j;
+                pkm1 = pk;
+                pk = pn;
+            }
+            if (n == 1) { pk = x; pkm1 = 1.0; }
+            dp = n * (x * pk - pkm1) / (x * x - 1.0);
+            double dx = pk / dp;
+            x -= dx;
+            if (fabs(dx) <= 1e-17) break;
+        }
+        double pkm1 = 1.0, pk = x;
+        for (int j = 2; j <= n; ++j) {
+            double pn = ((2.0 * j - 1.0) * x * pk - (j - 1.0) * pkm1) / j;
+            pkm1 = pk;
+            pk = pn;
+        }
+        if (n == 1) { pk = x; pkm1 = 1.0; }
+        dp = n * (x * pk - pkm1) / (x * x - 1.0);
+        gl->x[n - k] = x;
+        gl->w[n - k] = 2.0 / ((1.0 - x * x) * dp * dp);
+    }
+}
+
+static void kx_free_kernel(kx_kernel *k) {
+    if (!k) return;
+    cudaSetDevice(k->device);
+    void *ptrs[] = {k->d_p, k->d_E, k->d_dp, k->d_dE, k->d_h, k->d_pair, k->d_W64,
+                    k->d_om64, k->d_jl, k->d_vt, k->d_W32, k->d_pk};
+    for (void *p : ptrs)
+        if (p) cudaFree(p);
+    delete k;
+}
+
+template <typename T>
+static int kx_dev_alloc(kx_ctx *ctx, T **p, size_t count, long long *bytes) {
+    *p = nullptr;
+    if (count == 0) count = 1;
+    if (cudaMalloc((void **)p, sizeof(T) * count) != cudaSuccess) {
+        cudaGetLastError();
+        return kx_set_error(ctx, KX_ENOMEM, "kernel table allocation failed");
+    }
+    *bytes += (long long)(sizeof(T) * count);
+    return KX_OK;
+}
+
+extern "C" int kx_build_kernel(kx_ctx *ctx, const kx_grid_desc *d, kx_kernel **out) {
+    if (!ctx || !d || !out) return KX_EINVAL;
+    *out = nullptr;
+    const int n = d->n;
+    if (n < 4 || n > KX_MAX_N || !d->q) return kx_set_error(ctx, KX_EINVAL, "n must be in [4, 512]");
+    if (!(d->a > 0) || !(d->mass > 0)) return kx_set_error(ctx, KX_EINVAL, "a and mass must be > 0");
+    if (d->n_mu < 1 || d->n_mu > KX_MAX_NMU) return kx_set_error(ctx, KX_EINVAL, "n_mu in [1, 64]");
+    if (d->measure != KX_MEASURE_ENERGY && d->measure != KX_MEASURE_LITERAL)
+        return kx_set_error(ctx, KX_EINVAL, "unknown measure");
+    if (d->stats != 0) return kx_set_error(ctx, KX_ENOTSUP, "only dilute statistics are built");
+    if (d->precision != KX_FP64 && d->precision != KX_FP32)
+        return kx_set_error(ctx, KX_ENOTSUP, "precision not available in this build");
+    for (int i = 0; i < n; ++i) {
+        if (!(d->q[i] > 0) || !isfinite(d->q[i]))
+            return kx_set_error(ctx, KX_EINVAL, "q must be finite and > 0");
+        if (i && !(d->q[i] > d->q[i - 1]))
+            return kx_set_error(ctx, KX_EINVAL, "q must be strictly ascending");
+    }
+    KX_CUDA_TRY(ctx, cudaSetDevice(ctx->device));
+    kx_kernel *k = new (std::nothrow) kx_kernel();
+    if (!k) return KX_ENOMEM;
+    k->refcount = 1;
+    k->device = ctx->device;
+    k->n = n;
+    k->n_mu = d->n_mu;
+    k->measure = d->measure;
+    k->precision = d->precision;
+    k->a = d->a;
+    k->mass = d->mass;
+    k->P = (long long)n * (n + 1) / 2;
+    k->bytes = 0;
+    // grid (Appendix A; trapezoid widths in q)
+    k->q.assign(d->q, d->q + n);
+    k->p.resize(n); k->E.resize(n); k->dp.resize(n); k->dE.resize(n); k->h.resize(n);
+    for (int i = 0; i < n; ++i) {
+        double dq;
+        if (i == 0) dq = (d->q[1] - d->q[0]) / 2.0;
+        else if (i == n - 1) dq = (d->q[n - 1] - d->q[n - 2]) / 2.0;
+        else dq = (d->q[i + 1] - d->q[i - 1]) / 2.0;
+        k->p[i] = d->q[i] / d->a;
+        k->E[i] = sqrt(k->p[i] * k->p[i] + d->mass * d->mass);
+        k->dp[i] = dq / d->a;
+        k->dE[i] = k->p[i] * k->dp[i] / k->E[i];
+        k->h[i] = k->p[i] * k->p[i] * k->dp[i];
+    }
+    std::vector<uint32_t> pair;
+    pair.reserve(k->P);
+    for (int a = 0; a < n; ++a)
+        for (int b = a; b < n; ++b) pair.push_back((uint32_t)a | ((uint32_t)b << 16));
+    std::vector<uint32_t> vt;
+    for (int a = 0; a < n; ++a)
+        for (int m0 = a; m0 < n; m0 += 4) vt.push_back((uint32_t)a | ((uint32_t)m0 << 16));
+    k->V = (int)vt.size();
+
+    int rc = KX_OK;
+    long long *by = &k->bytes;
+    cudaStream_t s = ctx->stream;
+#define KX_ALLOC(ptr, cnt)                                 \
+    if ((rc = kx_dev_alloc(ctx, &ptr, cnt, by)) != KX_OK) { \
+        kx_free_kernel(k);                                  \
+        return rc;                                          \
+    }
+    KX_ALLOC(k->d_p, n); KX_ALLOC(k->d_E, n); KX_ALLOC(k->d_dp, n); KX_ALLOC(k->d_dE, n);
+    KX_ALLOC(k->d_h, n);
+    KX_ALLOC(k->d_pair, k->P);
+    KX_ALLOC(k->d_W64, (size_t)n * k->P);
+    KX_ALLOC(k->d_om64, (size_t)n * k->P);
+    KX_ALLOC(k->d_jl, (size_t)n * k->P);
+    if (k->precision == KX_FP32) {
+        KX_ALLOC(k->d_vt, k->V);
+        KX_ALLOC(k->d_W32, (size_t)n * k->V * 4);
+        KX_ALLOC(k->d_pk, (size_t)n * k->V * 4);
+    }
+#undef KX_ALLOC
+    unsigned long long *d_cnt = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    auto fail = [&](const char *what, cudaError_t e) {
+        if (d_cnt) cudaFree(d_cnt);
+        if (e0) cudaEventDestroy(e0);
+        if (e1) cudaEventDestroy(e1);
+        kx_free_kernel(k);
+        return kx_set_error(ctx, KX_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
+    };
+    cudaError_t e;
+#define KX_CHK(what, expr) \
+    if ((e = (expr)) != cudaSuccess) return fail(what, e);
+    KX_CHK("upload grid", cudaMemcpyAsync(k->d_p, k->p.data(), sizeof(double) * n, cudaMemcpyHostToDevice, s));
+    KX_CHK("upload grid", cudaMemcpyAsync(k->d_E, k->E.data(), sizeof(double) * n, cudaMemcpyHostToDevice, s));
+    KX_CHK("upload grid", cudaMemcpyAsync(k->d_dp, k->dp.data(), sizeof(double) * n, cudaMemcpyHostToDevice, s));
+    KX_CHK("upload grid", cudaMemcpyAsync(k->d_dE, k->dE.data(), sizeof(double) * n, cudaMemcpyHostToDevice, s));
+    KX_CHK("upload grid", cudaMemcpyAsync(k->d_h, k->h.data(), sizeof(double) * n, cudaMemcpyHostToDevice, s));
+    KX_CHK("upload pairs", cudaMemcpyAsync(k->d_pair, pair.data(), sizeof(uint32_t) * k->P, cudaMemcpyHostToDevice, s));
+    if (k->d_vt)
+        KX_CHK("upload vectors", cudaMemcpyAsync(k->d_vt, vt.data(), sizeof(uint32_t) * k->V, cudaMemcpyHostToDevice, s));
+    kx_gl_nodes gl;
+    memset(&gl, 0, sizeof(gl));
+    kx_gauss_legendre(k->n_mu, &gl);
+    KX_CHK("event", cudaEventCreate(&e0));
+    KX_CHK("event", cudaEventCreate(&e1));
+    KX_CHK("malloc", cudaMalloc(&d_cnt, sizeof(unsigned long long)));
+    KX_CHK("memset", cudaMemsetAsync(d_cnt, 0, sizeof(unsigned long long), s));
+    KX_CHK("event", cudaEventRecord(e0, s));
+    KX_CHK("build", kx_launch_build_fp64(k, gl, s));
+    if (k->precision == KX_FP32) KX_CHK("pack", kx_launch_pack_fp32(k, s));
+    KX_CHK("event", cudaEventRecord(e1, s));
+    KX_CHK("count", kx_launch_count_nnz(k, d_cnt, s));
+    ctx->launches += k->precision == KX_FP32 ? 3 : 2;
+    unsigned long long cnt = 0;
+    KX_CHK("copy", cudaMemcpyAsync(&cnt, d_cnt, sizeof(cnt), cudaMemcpyDeviceToHost, s));
+    KX_CHK("sync", cudaStreamSynchronize(s));
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    k->build_ms = ms;
+    k->nnz = (long long)cnt;
+    cudaFree(d_cnt);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+#undef KX_CHK
+    if (k->precision == KX_FP32) {
+        // the FP32 path streams only its own tables
+        cudaFree(k->d_W64); k->d_W64 = nullptr;
+        cudaFree(k->d_om64); k->d_om64 = nullptr;
+        cudaFree(k->d_jl); k->d_jl = nullptr;
+        k->bytes -= (long long)n * k->P * (8 + 8 + 2);
+    }
+    *out = k;
+    return KX_OK;
+}
+
+extern "C" void kx_kernel_retain(kx_kernel *k) {
+    if (k) __atomic_add_fetch(&k->refcount, 1, __ATOMIC_SEQ_CST);
+}
+
+extern "C" void kx_kernel_release(kx_kernel *k) {
+    if (!k) return;
+    if (__atomic_sub_fetch(&k->refcount, 1, __ATOMIC_SEQ_CST) == 0) kx_free_kernel(k);
+}
+
+extern "C" int kx_kernel_get_info(const kx_kernel *k, kx_kernel_info *info) {
+    if (!k || !info) return KX_EINVAL;
+    info->n = k->n;
+    info->n_mu = k->n_mu;
+    info->measure = k->measure;
+    info->precision = k->precision;
+    info->unique_elements = (long long)k->n * k->P;
+    info->nonzero_elements = k->nnz;
+    info->tensor_bytes = k->bytes;
+    info->build_ms = k->build_ms;
+    return KX_OK;
+}
+
+extern "C" int kx_kernel_grid(const kx_kernel *k, double *p, double *E, double *dp, double *dE,
+                              double *h) {
+    if (!k) return KX_EINVAL;
+    size_t b = sizeof(double) * k->n;
+    if (p) memcpy(p, k->p.data(), b);
+    if (E) memcpy(E, k->E.data(), b);
+    if (dp) memcpy(dp, k->dp.data(), b);
+    if (dE) memcpy(dE, k->dE.data(), b);
+    if (h) memcpy(h, k->h.data(), b);
+    return KX_OK;
+}
+
+extern "C" int kx_kernel_row(const kx_kernel *k, int i, double *W, int *jL, double *omega) {
+    if (!k || i < 0 || i >= k->n) return KX_EINVAL;
+    if (!k->d_W64) return KX_ENOTSUP;
+    if (cudaSetDevice(k->device) != cudaSuccess) return KX_ECUDA;
+    const size_t P = k->P;
+    if (W && cudaMemcpy(W, k->d_W64 + i * P, sizeof(double) * P, cudaMemcpyDeviceToHost) != cudaSuccess)
+        return KX_ECUDA;
+    if (omega && cudaMemcpy(omega, k->d_om64 + i * P, sizeof(double) * P, cudaMemcpyDeviceToHost) != cudaSuccess)
+        return KX_ECUDA;
+    if (jL) {
+        std::vector<uint16_t> t(P);
+        if (cudaMemcpy(t.data(), k->d_jl + i * P, sizeof(uint16_t) * P, cudaMemcpyDeviceToHost) != cudaSuccess)
+            return KX_ECUDA;
+        for (size_t e = 0; e < P; ++e) jL[e] = t[e];
+    }
+    return KX_OK;
+}
+
+// -------------------------------------------------------------- collision
+static double kx_M2(double mass, double sigma) { return 64.0 * KX_PI_H * mass * mass * sigma; }
+
+static int kx_check_batch(kx_ctx *ctx, const kx_kernel *k, int B, const double *sigma) {
+    if (!ctx || !k || B < 1 || !sigma) return kx_set_error(ctx, KX_EINVAL, "bad batch arguments");
+    if (k->device != ctx->device) return kx_set_error(ctx, KX_EINVAL, "kernel on another device");
+    for (int b = 0; b < B; ++b)
+        if (!(sigma[b] > 0) || !isfinite(sigma[b]))
+            return kx_set_error(ctx, KX_EINVAL, "sigma must be finite and > 0");
+    return KX_OK;
+}
+
+static int kx_collision_impl(kx_ctx *ctx, const kx_kernel *k, int B, const double *sigma,
+                             const double *f_dev, double *C_dev, int project, kx_diag *diag,
+                             size_t extra_offset) {
+    cudaStream_t s = ctx->stream;
+    kx_batch_views v;
+    kx_carve_views(k, B, (char *)ctx->d_arena + extra_offset, &v);
+    std::vector<double> M2(B);
+    for (int b = 0; b < B; ++b) M2[b] = kx_M2(k->mass, sigma[b]);
+    KX_CUDA_TRY(ctx, cudaMemcpyAsync(v.M2, M2.data(), sizeof(double) * B, cudaMemcpyHostToDevice, s));
+    KX_CUDA_TRY(ctx, kx_launch_prep(k, B, f_dev, v, nullptr, s));
+    KX_CUDA_TRY(ctx, kx_launch_contract(k, B, f_dev, v, nullptr, 1, s));
+    KX_CUDA_TRY(ctx, kx_launch_finalize(k, B, f_dev, v, C_dev, project, diag != nullptr, s));
+    ctx->launches += 3;
+    if (diag) {
+        KX_CUDA_TRY(ctx, cudaMemcpyAsync(diag, v.diag, sizeof(kx_diag) * B, cudaMemcpyDeviceToHost, s));
+        KX_CUDA_TRY(ctx, cudaStreamSynchronize(s));
+        for (int b = 0; b < B; ++b)
+            if (diag[b].status != KX_OK) return KX_ENONFINITE;
+    }
+    return KX_OK;
+}
+
+extern "C" int kx_collision(kx_ctx *ctx, const kx_kernel *k, int B, const double *sigma,
+                            const double *f_dev, double *C_dev, int project, kx_diag *diag) {
+    int rc = kx_check_batch(ctx, k, B, sigma);
+    if (rc) return rc;
+    if (!f_dev || !C_dev) return kx_set_error(ctx, KX_EINVAL, "null device pointer");
+    KX_CUDA_TRY(ctx, cudaSetDevice(ctx->device));
+    if ((rc = kx_arena_reserve(ctx, kx_views_bytes(k, B))) != KX_OK) return rc;
+    return kx_collision_impl(ctx, k, B, sigma, f_dev, C_dev, project, diag, 0);
+}
+
+extern "C" int kx_collision_host(kx_ctx *ctx, const kx_kernel *k, int B, const double *sigma,
+                                 const double *f_host, double *C_host, int project, kx_diag *diag) {
+    int rc = kx_check_batch(ctx, k, B, sigma);
+    if (rc) return rc;
+    if (!f_host || !C_host) return kx_set_error(ctx, KX_EINVAL, "null host pointer");
+    KX_CUDA_TRY(ctx, cudaSetDevice(ctx->device));
+    const size_t fb = kx_align(sizeof(double) * B * k->n);
+    if ((rc = kx_arena_reserve(ctx, 2 * fb + kx_views_bytes(k, B))) != KX_OK) return rc;
+    double *d_f = (double *)ctx->d_arena;
+    double *d_C = (double *)((char *)ctx->d_arena + fb);
+    cudaStream_t s = ctx->stream;
+    KX_CUDA_TRY(ctx, cudaMemcpyAsync(d_f, f_host, sizeof(double) * B * k->n, cudaMemcpyHostToDevice, s));
+    rc = kx_collision_impl(ctx, k, B, sigma, d_f, d_C, project, diag, 2 * fb);
+    if (rc && rc != KX_ENONFINITE) return rc;
+    KX_CUDA_TRY(ctx, cudaMemcpyAsync(C_host, d_C, sizeof(double) * B * k->n, cudaMemcpyDeviceToHost, s));
+    KX_CUDA_TRY(ctx, cudaStreamSynchronize(s));
+    return rc;
+}
+
+// ------------------------------------------------------------ integration
+struct kx_solve_layout {
+    size_t views, f, k1, fp, st, src, shapes, mb, total;
+};
+
+static kx_solve_layout kx_layout_solve(const kx_kernel *k, int B, int n_shape_rows, bool own_f) {
+    kx_solve_layout L;
+    size_t o = 0;
+    L.views = o; o += kx_align(kx_views_bytes(k, B));
+    L.f = o; o += own_f ? kx_align(sizeof(double) * B * k->n) : 0;
+    L.k1 = o; o += kx_align(sizeof(double) * B * k->n);
+    L.fp = o; o += kx_align(sizeof(double) * B * k->n);
+    L.st = o; o += kx_align(sizeof(kx_inst_state) * B);
+    L.src = o; o += kx_align(sizeof(kx_src_dev) * B);
+    L.shapes = o; o += kx_align(sizeof(double) * std::max(1, n_shape_rows) * k->n);
+    L.mb = o; o += kx_align(sizeof(double) * 3 * B);
+    L.total = o;
+    return L;
+}
+
+static int kx_check_params(kx_ctx *ctx, const kx_solve_params *p) {
+    if (!p) return kx_set_error(ctx, KX_EINVAL, "null params");
+    if (!(p->rtol >= 0) || !(p->atol >= 0) || !(p->rtol + p->atol > 0))
+        return kx_set_error(ctx, KX_EINVAL, "rtol/atol must be >= 0, not both 0");
+    if (!(p->h0 > 0)) return kx_set_error(ctx, KX_EINVAL, "h0 must be > 0");
+    if (p->max_attempts < 1) return kx_set_error(ctx, KX_EINVAL, "max_attempts must be >= 1");
+    return KX_OK;
+}
+
+// Normalised source shapes and per-instance source descriptors.
+static int kx_sources_host(kx_ctx *ctx, const kx_kernel *k, int B, const kx_source *src, int nsets,
+                           std::vector<kx_src_dev> &sd, std::vector<double> &shapes) {
+    sd.assign(B, kx_src_dev());
+    shapes.clear();
+    const int n = k->n;
+    if (src && nsets != 1 && nsets != B)
+        return kx_set_error(ctx, KX_EINVAL, "n_src_sets must be 1 or batch");
+    std::vector<long long> set_off;
+    for (int s = 0; src && s < nsets; ++s) {
+        const kx_source &S = src[s];
+        if (S.n_src < 0 || S.n_src > KX_MAX_SRC)
+            return kx_set_error(ctx, KX_EINVAL, "n_src must be in [0, 4]");
+        if (S.n_src && (!S.shape || !S.rate || !S.tau || !S.t_on))
+            return kx_set_error(ctx, KX_EINVAL, "null source array");
+        set_off.push_back((long long)shapes.size());
+        for (int r = 0; r < S.n_src; ++r) {
+            double norm = 0.0;
+            for (int j = 0; j < n; ++j) {
+                double v = S.shape[(size_t)r * n + j];
+                if (!(v >= 0) || !isfinite(v)) return kx_set_error(ctx, KX_EINVAL, "source shape must be >= 0");
+                norm += k->h[j] * v;
+            }
+            if (!(norm > 0) || !(S.tau[r] > 0))
+                return kx_set_error(ctx, KX_EINVAL, "source shape must have positive weight, tau > 0");
+            for (int j = 0; j < n; ++j) shapes.push_back(S.shape[(size_t)r * n + j] / norm);
+        }
+    }
+    for (int b = 0; b < B; ++b) {
+        kx_src_dev &d = sd[b];
+        d.t_off = -INFINITY;
+        if (!src) continue;
+        const int s = nsets == 1 ? 0 : b;
+        const kx_source &S = src[s];
+        d.n_src = S.n_src;
+        d.shape_off = set_off[s];
+        for (int r = 0; r < S.n_src; ++r) {
+            d.rate[r] = S.rate[r];
+            d.tau[r] = S.tau[r];
+            d.t_on[r] = S.t_on[r];
+            d.t_off = std::max(d.t_off, S.t_on[r] + S.tau[r] * log(1e12));
+        }
+    }
+    if (shapes.empty()) shapes.push_back(0.0);
+    return KX_OK;
+}
+
+struct kx_run {
+    kx_batch_views v;
+    kx_step_views sv;
+    double *mb;
+};
+
+static int kx_setup_run(kx_ctx *ctx, const kx_kernel *k, int B, const double *sigma,
+                        const kx_source *src, int nsets, const kx_solve_params *par,
+                        const double *t0, const double *h0, double *f_dev, bool own_f,
+                        kx_run *run, double **f_used) {
+    std::vector<kx_src_dev> sd;
+    std::vector<double> shapes;
+    int rc = kx_sources_host(ctx, k, B, src, nsets, sd, shapes);
+    if (rc) return rc;
+    kx_solve_layout L = kx_layout_solve(k, B, (int)(shapes.size() / k->n) + 1, own_f);
+    if ((rc = kx_arena_reserve(ctx, L.total)) != KX_OK) return rc;
+    char *base = (char *)ctx->d_arena;
+    kx_carve_views(k, B, base + L.views, &run->v);
+    kx_step_views &sv = run->sv;
+    sv.f = own_f ? (double *)(base + L.f) : f_dev;
+    sv.k1 = (double *)(base + L.k1);
+    sv.fp = (double *)(base + L.fp);
+    sv.st = (kx_inst_state *)(base + L.st);
+    sv.src = (const kx_src_dev *)(base + L.src);
+    sv.shapes = (const double *)(base + L.shapes);
+    sv.rtol = par->rtol;
+    sv.atol = par->atol;
+    sv.h_min = par->h_min;
+    sv.h_max = par->h_max > 0 ? par->h_max : INFINITY;
+    sv.l1_tol = par->l1_tol;
+    sv.max_attempts = par->max_attempts;
+    sv.fixed = par->fixed_step;
+    sv.check_every = par->check_every;
+    sv.project = par->project;
+    run->mb = (double *)(base + L.mb);
+    *f_used = sv.f;
+    std::vector<kx_inst_state> st(B);
+    std::vector<double> M2(B);
+    for (int b = 0; b < B; ++b) {
+        memset(&st[b], 0, sizeof(kx_inst_state));
+        st[b].t = t0 ? t0[b] : par->t0;
+        st[b].h = h0 ? h0[b] : par->h0;
+        st[b].t_end = par->t_end;
+        st[b].l1 = INFINITY;
+        st[b].done = !(st[b].t < st[b].t_end);
+        M2[b] = kx_M2(k->mass, sigma[b]);
+    }
+    cudaStream_t s = ctx->stream;
+    KX_CUDA_TRY(ctx, cudaMemcpyAsync(sv.st, st.data(), sizeof(kx_inst_state) * B, cudaMemcpyHostToDevice, s));
+    KX_CUDA_TRY(ctx, cudaMemcpyAsync((void *)sv.src, sd.data(), sizeof(kx_src_dev) * B, cudaMemcpyHostToDevice, s));
+    KX_CUDA_TRY(ctx, cudaMemcpyAsync((void *)sv.shapes, shapes.data(), sizeof(double) * shapes.size(), cudaMemcpyHostToDevice, s));
+    KX_CUDA_TRY(ctx, cudaMemcpyAsync(run->v.M2, M2.data(), sizeof(double) * B, cudaMemcpyHostToDevice, s));
+    return KX_OK;
+}
+
+static cudaError_t kx_enqueue_attempt(const kx_kernel *k, int B, const kx_run &r, cudaStream_t s) {
+    cudaError_t e;
+    if ((e = kx_launch_contract(k, B, r.sv.f, r.v, r.sv.st, 1, s)) != cudaSuccess) return e;
+    if ((e = kx_launch_stage(k, B, r.v, r.sv, 1, s)) != cudaSuccess) return e;
+    if ((e = kx_launch_contract(k, B, r.sv.fp, r.v, r.sv.st, 2, s)) != cudaSuccess) return e;
+    return kx_launch_stage(k, B, r.v, r.sv, 2, s);
+}
+
+static int kx_collect(kx_ctx *ctx, const kx_kernel *k, int B, const kx_run &r, kx_result *res,
+                      double *t_out, double *h_out, double latency) {
+    cudaStream_t s = ctx->stream;
+    std::vector<kx_inst_state> st(B);
+    std::vector<double> mb(3 * B);
+    KX_CUDA_TRY(ctx, kx_launch_mbfit(k, B, r.sv.f, r.mb, s));
+    ctx->launches += 1;
+    KX_CUDA_TRY(ctx, cudaMemcpyAsync(st.data(), r.sv.st, sizeof(kx_inst_state) * B, cudaMemcpyDeviceToHost, s));
+    KX_CUDA_TRY(ctx, cudaMemcpyAsync(mb.data(), r.mb, sizeof(double) * 3 * B, cudaMemcpyDeviceToHost, s));
+    KX_CUDA_TRY(ctx, cudaStreamSynchronize(s));
+    int worst = KX_OK;
+    for (int b = 0; b < B; ++b) {
+        if (t_out) t_out[b] = st[b].t;
+        if (h_out) h_out[b] = st[b].h;
+        if (res) {
+            kx_result &o = res[b];
+            o.t = st[b].t;
+            o.h = st[b].h;
+            o.T_mb = mb[3 * b];
+            o.ln_z_mb = mb[3 * b + 1];
+            o.l1_to_mb = mb[3 * b + 2];
+            o.steps = st[b].steps;
+            o.rejects = st[b].rejects;
+            o.evals = st[b].evals;
+            o.status = st[b].status;
+            o.converged = st[b].converged;
+            o.latency_s = latency;
+        }
+        if (st[b].status != KX_OK && worst == KX_OK) worst = st[b].status;
+    }
+    return worst;
+}
+
+extern "C" int kx_step(kx_ctx *ctx, const kx_kernel *k, int B, const double *sigma,
+                       const kx_source *src, int nsets, const kx_solve_params *par, double *t_host,
+                       double *h_host, double *f_dev, kx_result *res) {
+    int rc = kx_check_batch(ctx, k, B, sigma);
+    if (rc) return rc;
+    if ((rc = kx_check_params(ctx, par)) != KX_OK) return rc;
+    if (!t_host || !h_host || !f_dev) return kx_set_error(ctx, KX_EINVAL, "null t/h/f");
+    KX_CUDA_TRY(ctx, cudaSetDevice(ctx->device));
+    kx_run r;
+    double *f = nullptr;
+    if ((rc = kx_setup_run(ctx, k, B, sigma, src, nsets, par, t_host, h_host, f_dev, false, &r, &f)))
+        return rc;
+    (void)f;
+    r.sv.max_attempts = (long long)1 << 62;
+    cudaStream_t s = ctx->stream;
+    KX_CUDA_TRY(ctx, kx_launch_prep(k, B, r.sv.f, r.v, r.sv.st, s));
+    KX_CUDA_TRY(ctx, kx_enqueue_attempt(k, B, r, s));
+    ctx->launches += 5;
+    return kx_collect(ctx, k, B, r, res, t_host, h_host, 0.0);
+}
+
+// Device-resident integration: G attempts per captured graph; the host keeps
+// one graph in flight ahead of the status word it reads (bounded wall time).
+static int kx_solve_run(kx_ctx *ctx, const kx_kernel *k, int B, const kx_run &r,
+                        const kx_solve_params *par, kx_result *res) {
+    cudaStream_t s = ctx->stream;
+    const auto t_start = std::chrono::steady_clock::now();
+    KX_CUDA_TRY(ctx, kx_launch_prep(k, B, r.sv.f, r.v, r.sv.st, s));
+    ctx->launches += 1;
+    const int G = 16;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    cudaStream_t cap = nullptr;
+    int rc = KX_OK;
+    if ((rc = kx_pinned_reserve(ctx, 2 * sizeof(kx_inst_state) * (size_t)B)) != KX_OK) return rc;
+    kx_inst_state *h_st = (kx_inst_state *)ctx->h_pinned;
+    cudaError_t e = cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+        for (int a = 0; a < G && e == cudaSuccess; ++a) e = kx_enqueue_attempt(k, B, r, cap);
+        cudaError_t e2 = cudaStreamEndCapture(cap, &graph);
+        if (e == cudaSuccess) e = e2;
+    }
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&exec, graph, 0);
+    if (cap) cudaStreamDestroy(cap);
+    if (e != cudaSuccess) {
+        if (graph) cudaGraphDestroy(graph);
+        return kx_set_error(ctx, KX_ECUDA, std::string("graph capture: ") + cudaGetErrorString(e));
+    }
+    // two status buffers / events: graph g+1 runs while the host reads graph g's status
+    cudaEvent_t ev[2] = {nullptr, nullptr};
+    cudaEventCreateWithFlags(&ev[0], cudaEventDisableTiming);
+    cudaEventCreateWithFlags(&ev[1], cudaEventDisableTiming);
+    const long long max_launch = (long long)par->max_attempts / G + 2;
+    const double wall_limit = 600.0;
+    long long launched = 0;
+    auto launch_one = [&](int slot) -> cudaError_t {
+        cudaError_t x = cudaGraphLaunch(exec, s);
+        if (x == cudaSuccess)
+            x = cudaMemcpyAsync(h_st + (size_t)slot * B, r.sv.st, sizeof(kx_inst_state) * B,
+                                cudaMemcpyDeviceToHost, s);
+        if (x == cudaSuccess) x = cudaEventRecord(ev[slot], s);
+        ++launched;
+        ctx->launches += 4LL * G;
+        return x;
+    };
+    e = launch_one(0);
+    if (e == cudaSuccess && launched < max_launch) e = launch_one(1);
+    for (long long g = 0; e == cudaSuccess; ++g) {
+        const int slot = (int)(g & 1);
+        for (;;) {  // bounded wait on the status copy of graph g
+            cudaError_t q = cudaEventQuery(ev[slot]);
+            if (q == cudaSuccess) break;
+            if (q != cudaErrorNotReady) { e = q; break; }
+            double el = std::chrono::duration<double>(std::chrono::steady_clock::now() - t_start).count();
+            if (el > wall_limit) { rc = KX_ETIMEOUT; break; }
+            std::this_thread::yield();
+        }
+        if (e != cudaSuccess || rc) break;
+        bool all_done = true;
+        for (int b = 0; b < B; ++b) all_done &= h_st[(size_t)slot * B + b].done != 0;
+        if (all_done || launched >= max_launch) break;
+        e = launch_one(slot);
+    }
+    cudaStreamSynchronize(s);
+    cudaEventDestroy(ev[0]);
+    cudaEventDestroy(ev[1]);
+    cudaGraphExecDestroy(exec);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) return kx_set_error(ctx, KX_ECUDA, std::string("solve loop: ") + cudaGetErrorString(e));
+    const double latency = std::chrono::duration<double>(std::chrono::steady_clock::now() - t_start).count();
+    int worst = kx_collect(ctx, k, B, r, res, nullptr, nullptr, latency);
+    if (rc) return rc;
+    return worst;
+}
+
+extern "C" int kx_solve(kx_ctx *ctx, const kx_kernel *k, int B, const double *sigma,
+                        const kx_source *src, int nsets, const kx_solve_params *par, double *f_dev,
+                        kx_result *res) {
+    int rc = kx_check_batch(ctx, k, B, sigma);
+    if (rc) return rc;
+    if ((rc = kx_check_params(ctx, par)) != KX_OK) return rc;
+    if (!f_dev) return kx_set_error(ctx, KX_EINVAL, "null f");
+    KX_CUDA_TRY(ctx, cudaSetDevice(ctx->device));
+    kx_run r;
+    double *f = nullptr;
+    if ((rc = kx_setup_run(ctx, k, B, sigma, src, nsets, par, nullptr, nullptr, f_dev, false, &r, &f)))
+        return rc;
+    return kx_solve_run(ctx, k, B, r, par, res);
+}
+
+extern "C" int kx_solve_host(kx_ctx *ctx, const kx_kernel *k, int B, const double *sigma,
+                             const kx_source *src, int nsets, const kx_solve_params *par,
+                             double *f_host, kx_result *res) {
+    int rc = kx_check_batch(ctx, k, B, sigma);
+    if (rc) return rc;
+    if ((rc = kx_check_params(ctx, par)) != KX_OK) return rc;
+    if (!f_host) return kx_set_error(ctx, KX_EINVAL, "null f");
+    KX_CUDA_TRY(ctx, cudaSetDevice(ctx->device));
+    kx_run r;
+    double *f = nullptr;
+    if ((rc = kx_setup_run(ctx, k, B, sigma, src, nsets, par, nullptr, nullptr, nullptr, true, &r, &f)))
+        return rc;
+    cudaStream_t s = ctx->stream;
+    KX_CUDA_TRY(ctx, cudaMemcpyAsync(f, f_host, sizeof(double) * B * k->n, cudaMemcpyHostToDevice, s));
+    int rc2 = kx_solve_run(ctx, k, B, r, par, res);
+    if (rc2 == KX_ECUDA || rc2 == KX_ETIMEOUT) return rc2;
+    KX_CUDA_TRY(ctx, cudaMemcpyAsync(f_host, f, sizeof(double) * B * k->n, cudaMemcpyDeviceToHost, s));
+    KX_CUDA_TRY(ctx, cudaStreamSynchronize(s));
+    return rc2;
+}
+
+extern "C" int kx_mb_fit(kx_ctx *ctx, const kx_kernel *k, int B, const double *f_dev, double *out) {
+    if (!ctx || !k || B < 1 || !f_dev || !out) return KX_EINVAL;
+    KX_CUDA_TRY(ctx, cudaSetDevice(ctx->device));
+    int rc = kx_arena_reserve(ctx, kx_align(sizeof(double) * 3 * B));
+    if (rc) return rc;
+    double *d = (double *)ctx->d_arena;
+    KX_CUDA_TRY(ctx, kx_launch_mbfit(k, B, f_dev, d, ctx->stream));
+    ctx->launches += 1;
+    KX_CUDA_TRY(ctx, cudaMemcpyAsync(out, d, sizeof(double) * 3 * B, cudaMemcpyDeviceToHost, ctx->stream));
+    KX_CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
+    return KX_OK;
+}
+
+// ---------------------------------------------------------------- profiling
+extern "C" long long kx_launch_count(const kx_ctx *ctx) { return ctx ? ctx->launches : 0; }
+
+extern "C" int kx_time_contraction(kx_ctx *ctx, const kx_kernel *k, int B, const double *f_dev,
+                                   int iters, long long flush_bytes, double *avg_ms) {
+    if (!ctx || !k || B < 1 || !f_dev || iters < 1 || !avg_ms || flush_bytes < 0) return KX_EINVAL;
+    KX_CUDA_TRY(ctx, cudaSetDevice(ctx->device));
+    int rc = kx_arena_reserve(ctx, kx_views_bytes(k, B));
+    if (rc) return rc;
+    cudaStream_t s = ctx->stream;
+    kx_batch_views v;
+    kx_carve_views(k, B, ctx->d_arena, &v);
+    void *flush = nullptr;
+    if (flush_bytes > 0 && cudaMalloc(&flush, (size_t)flush_bytes) != cudaSuccess) {
+        cudaGetLastError();
+        return kx_set_error(ctx, KX_ENOMEM, "flush buffer");
+    }
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    cudaError_t e = kx_launch_prep(k, B, f_dev, v, nullptr, s);
+    ctx->launches += 1;
+    double total = 0.0;
+    for (int it = 0; it < iters && e == cudaSuccess; ++it) {
+        if (flush) e = cudaMemsetAsync(flush, it & 0xff, (size_t)flush_bytes, s);
+        if (e == cudaSuccess) e = cudaEventRecord(e0, s);
+        if (e == cudaSuccess) e = kx_launch_contract(k, B, f_dev, v, nullptr, 1, s);
+        ctx->launches += 1;
+        if (e == cudaSuccess) e = cudaEventRecord(e1, s);
+        if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+        float ms = 0.f;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+        total += ms;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (flush) cudaFree(flush);
+    if (e != cudaSuccess) return kx_set_error(ctx, KX_ECUDA, std::string("time contraction: ") + cudaGetErrorString(e));
+    *avg_ms = total / iters;
+    return KX_OK;
+}

@@ -1,0 +1,159 @@
+// kx_build.cu -- device build of the collision-kernel tensor (Appendix A).
+//
+// Compiled with -fmad=false: every expression below is evaluated as written,
+// operation by operation, in IEEE FP64, so that the kinematic-support and
+// Theta(K^2 + A1^2 - A0^2) decisions are reproducible bit for bit from the
+// same grid values.
+#include "kx_internal.cuh"
+
+#define KX_PI 3.14159265358979323846
+
+// Index of pair (n, n) in the row-major n <= m pair order.
+__device__ __forceinline__ long long kx_pair_base(int n, int N) {
+    return (long long)n * N - (long long)n * (n - 1) / 2;
+}
+
+// Largest j <= N-2 with E[j] <= Et, for E[0] <= Et (bisection on ascending E).
+__device__ __forceinline__ int kx_bracket(const double *E, int N, double Et) {
+    int lo = 0, hi = N - 2;
+    while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if (E[mid] <= Et) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+// Angular kernel of eq. (app_F_1d) with |M|^2 = 1:
+//   F = p_n p_m / (4 (2 pi)^4) sum_k w_k I(mu_k),
+// I(mu) = pi / sqrt(K^2 + A1^2) when K^2 + A1^2 - A0^2 >= 0 (the nu integral of
+// eq. app_I_mu over its root interval, which lies inside [-1, 1]), else 0;
+// A0, A1, K^2 as defined below eq. (app_cosphi).
+__device__ double kx_F_unit(double m, double pi, double pn, double pm, double Ei, double En,
+                            double Em, const kx_gl_nodes &gl, int n_mu) {
+    double acc = 0.0;
+    for (int k = 0; k < n_mu; ++k) {
+        double mu = gl.x[k];
+        double A0 = m * m + En * Em - En * Ei - Em * Ei + pi * pn * mu;
+        double A1 = pi * pm - pn * pm * mu;
+        double K2 = pn * pn * pm * pm * (1.0 - mu * mu);
+        double s = K2 + A1 * A1;
+        double D = s - A0 * A0;
+        if (s > 0.0 && D >= 0.0) acc += gl.w[k] * (KX_PI / sqrt(s));
+    }
+    double two_pi = 2.0 * KX_PI;
+    return 1.0 * pn * pm / (4.0 * two_pi * two_pi * two_pi * two_pi) * acc;
+}
+
+// One thread per (i, pair n <= m).  Writes the symmetrised weight
+// S_inm = W_inm + W_imn (n < m) or W_inn, the bracket j_L and omega_R of
+// eq. (app_interp_weights).  W_inm = mu_n mu_m F_inm / (2 E_i g), g = 1, with
+// mu = dE (energy measure) or Dp (literal measure).  Outside the support
+// E_0 <= E_t <= E_{N-1}, E_t = (E_n + E_m) - E_i (eq. app_fourth_momentum),
+// everything is zero.
+__global__ void k_build_fp64(int N, long long P, int n_mu, int measure, double m,
+                             const double *__restrict__ p, const double *__restrict__ E,
+                             const double *__restrict__ dp, const double *__restrict__ dE,
+                             const uint32_t *__restrict__ pair, kx_gl_nodes gl,
+                             double *__restrict__ W, double *__restrict__ om,
+                             uint16_t *__restrict__ jl) {
+    long long pidx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    int i = blockIdx.y;
+    if (pidx >= P) return;
+    uint32_t pr = pair[pidx];
+    int n = pr & 0xffff, mm = pr >> 16;
+    long long e = (long long)i * P + pidx;
+    double Et = (E[n] + E[mm]) - E[i];
+    if (!(Et >= E[0] && Et <= E[N - 1])) {
+        W[e] = 0.0;
+        om[e] = 0.0;
+        jl[e] = 0;
+        return;
+    }
+    int j = kx_bracket(E, N, Et);
+    double omega = (Et - E[j]) / (E[j + 1] - E[j]);
+    double mun = measure == KX_MEASURE_LITERAL ? dp[n] : dE[n];
+    double mum = measure == KX_MEASURE_LITERAL ? dp[mm] : dE[mm];
+    double F1 = kx_F_unit(m, p[i], p[n], p[mm], E[i], E[n], E[mm], gl, n_mu);
+    double W1 = mun * mum * F1 / (2.0 * E[i] * 1.0);
+    double S = W1;
+    if (n != mm) {
+        double F2 = kx_F_unit(m, p[i], p[mm], p[n], E[i], E[mm], E[n], gl, n_mu);
+        double W2 = mum * mun * F2 / (2.0 * E[i] * 1.0);
+        S = W1 + W2;
+    }
+    W[e] = S;
+    om[e] = omega;
+    jl[e] = (uint16_t)j;
+}
+
+cudaError_t kx_launch_build_fp64(const kx_kernel *k, const kx_gl_nodes &gl, cudaStream_t s) {
+    dim3 block(128);
+    dim3 grid((unsigned)((k->P + block.x - 1) / block.x), k->n);
+    k_build_fp64<<<grid, block, 0, s>>>(k->n, k->P, k->n_mu, k->measure, k->mass, k->d_p, k->d_E,
+                                        k->d_dp, k->d_dE, k->d_pair, gl, k->d_W64, k->d_om64,
+                                        k->d_jl);
+    return cudaGetLastError();
+}
+
+// FP32 streaming layout: row i holds V 4-element vectors; vector v covers
+// (n, m0..m0+3) of one n-segment (segments padded to a multiple of 4 with W = 0).
+// pk = j_L << 23 | round(omega 2^23) (omega quantised to 2^-23; omega that
+// rounds to 1 is stored as (j_L + 1, 0)).
+__global__ void k_pack_fp32(int N, long long P, int V, const uint32_t *__restrict__ vt,
+                            const double *__restrict__ W64, const double *__restrict__ om64,
+                            const uint16_t *__restrict__ jl, float *__restrict__ W32,
+                            uint32_t *__restrict__ pk) {
+    int v = blockIdx.x * blockDim.x + threadIdx.x;
+    int i = blockIdx.y;
+    if (v >= V) return;
+    uint32_t t = vt[v];
+    int n = t & 0xffff, m0 = t >> 16;
+    long long out = ((long long)i * V + v) * 4;
+    long long base = (long long)i * P + kx_pair_base(n, N);
+    for (int c = 0; c < 4; ++c) {
+        int m = m0 + c;
+        float w = 0.f;
+        uint32_t word = 0u;
+        if (m < N) {
+            long long e = base + (m - n);
+            double wd = W64[e];
+            if (wd != 0.0) {
+                w = (float)wd;
+                uint32_t j = jl[e];
+                double q = rint(om64[e] * 8388608.0);
+                // omega rounding to 1 is stored as the next grid point with omega = 0,
+                // so that E_t on a grid point interpolates exactly (j + 1 <= N - 1)
+                if (q >= 8388608.0) {
+                    j += 1;
+                    q = 0.0;
+                }
+                word = (j << 23) | (uint32_t)q;
+            }
+        }
+        W32[out + c] = w;
+        pk[out + c] = word;
+    }
+}
+
+cudaError_t kx_launch_pack_fp32(const kx_kernel *k, cudaStream_t s) {
+    dim3 block(128);
+    dim3 grid((unsigned)((k->V + block.x - 1) / block.x), k->n);
+    k_pack_fp32<<<grid, block, 0, s>>>(k->n, k->P, k->V, k->d_vt, k->d_W64, k->d_om64, k->d_jl,
+                                       k->d_W32, k->d_pk);
+    return cudaGetLastError();
+}
+
+__global__ void k_count_nnz(long long total, const double *__restrict__ W,
+                            unsigned long long *count) {
+    unsigned long long local = 0;
+    for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+         e += (long long)gridDim.x * blockDim.x)
+        local += W[e] != 0.0;
+    for (int off = 16; off; off >>= 1) local += __shfl_xor_sync(0xffffffffu, local, off);
+    if ((threadIdx.x & 31) == 0) atomicAdd(count, local);
+}
+
+cudaError_t kx_launch_count_nnz(const kx_kernel *k, unsigned long long *d_count, cudaStream_t s) {
+    k_count_nnz<<<592, 256, 0, s>>>((long long)k->n * k->P, k->d_W64, d_count);
+    return cudaGetLastError();
+}

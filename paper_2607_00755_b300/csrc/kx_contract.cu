@@ -1,0 +1,732 @@
+// kx_contract.cu -- evaluation of the collision term and the Heun stages.
+//
+//   C_i = sum_{n<=m} S_inm [ f_n f_m - f_i f_t(i,n,m) ]        (Sec. 4.1, dilute)
+//       = G_i - f_i L_i,   G_i = sum S f_n f_m,   L_i = sum S f_t
+//   f_t = exp((1 - omega) ln f_jL + omega ln f_jL+1)          (eq. app_log_interp)
+//
+// Work split: a row i's elements are cut into fixed chunks; each block writes
+// the chunk's (G, L) partial sums, and a per-instance block combines them in a
+// fixed order (deterministic, no atomics), then applies |M|^2, the two-moment
+// projection (Appendix B) and, in the integrator, the Heun stage (Sec. 4.2).
+#include <math.h>
+
+#include "kx_internal.cuh"
+
+// ----------------------------------------------------------------- helpers
+__device__ __forceinline__ float kx_ex2(float x) {
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+// Deterministic block reduction of K doubles (sum).  All threads receive the
+// result.  smem holds K*32 doubles.
+template <int K>
+__device__ __forceinline__ void kx_block_sum(double (&v)[K], double *smem) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+    for (int k = 0; k < K; ++k)
+#pragma unroll
+        for (int off = 16; off; off >>= 1) v[k] += __shfl_xor_sync(0xffffffffu, v[k], off);
+    if (lane == 0)
+#pragma unroll
+        for (int k = 0; k < K; ++k) smem[k * 32 + warp] = v[k];
+    __syncthreads();
+    if (warp == 0) {
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            double x = lane < nw ? smem[k * 32 + lane] : 0.0;
+#pragma unroll
+            for (int off = 16; off; off >>= 1) x += __shfl_xor_sync(0xffffffffu, x, off);
+            if (lane == 0) smem[k * 32] = x;
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < K; ++k) v[k] = smem[k * 32];
+    __syncthreads();
+}
+
+__device__ __forceinline__ double kx_block_max(double v, double *smem) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int off = 16; off; off >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, off));
+    if (lane == 0) smem[warp] = v;
+    __syncthreads();
+    if (warp == 0) {
+        double x = lane < nw ? smem[lane] : 0.0;
+        for (int off = 16; off; off >>= 1) x = fmax(x, __shfl_xor_sync(0xffffffffu, x, off));
+        if (lane == 0) smem[0] = x;
+    }
+    __syncthreads();
+    double r = smem[0];
+    __syncthreads();
+    return r;
+}
+
+__device__ __forceinline__ int kx_block_or(int v, double *smem) {
+    double r = kx_block_max((double)v, smem);
+    return r > 0.0;
+}
+
+// ------------------------------------------------------------------- prep
+// Per instance (block b, thread = grid point): f_max = max |f|, and either
+//  FP64 path: lf = ln max(f, 1e-300)
+//  FP32 path: l2_j = log2(max(f_j, 1e-300) / f_max) and its deviation
+//             delta_j = l2_j - (a0 - b0 E_j) from a log-linear (Maxwell-Boltzmann
+//             shaped) reference fitted by least squares with weights h_j f_j.
+//             The reference cancels exactly in the exponent difference of each
+//             element's gain and loss (energy conservation, eq. app_fourth_momentum,
+//             and the energy-linear interpolation, eq. app_interp_weights), so the
+//             difference is formed from the small deltas: near equilibrium the
+//             bracket keeps its relative accuracy.  The scale f_max^2 is put back
+//             in FP64 when the row sums are combined (C is bilinear in f).
+// Returns the non-finite flag (block-uniform).
+__device__ int kx_prep_block(int n, int path, const double *__restrict__ fb,
+                             const double *__restrict__ E, const double *__restrict__ h,
+                             double *fmax_out, double *lf64, float2 *tl, float2 *td,
+                             double *smem) {
+    const int i = threadIdx.x;
+    double x = i < n ? fb[i] : 0.0;
+    int bad = (i < n) && !isfinite(x);
+    double fm = kx_block_max(fabs(x), smem);
+    bad = kx_block_or(bad, smem);
+    if (threadIdx.x == 0) *fmax_out = fm;
+    if (path == KX_FP64) {
+        if (i < n) lf64[i] = log(x > KX_LOG_FLOOR ? x : KX_LOG_FLOOR);
+        return bad;
+    }
+    double *dl = smem + 64 + 32;  // deltas, n <= 512 doubles after the reduction scratch
+    const double Ei = i < n ? E[i] : 0.0;
+    double l2 = -2000.0;
+    if (i < n && fm > 0.0) l2 = log2(x > KX_LOG_FLOOR ? x : KX_LOG_FLOOR) - log2(fm);
+    const double w = (i < n && fm > 0.0 && x > 0.0) ? h[i] * (x / fm) : 0.0;
+    double s[5] = {w, w * Ei, w * Ei * Ei, w * l2, w * Ei * l2};
+    kx_block_sum<5>(s, smem);
+    double det = s[0] * s[2] - s[1] * s[1];
+    double slope = 0.0, icpt = s[0] > 0.0 ? s[3] / s[0] : 0.0;
+    if (det > 1e-12 * s[0] * s[2]) {
+        slope = (s[0] * s[4] - s[1] * s[3]) / det;
+        icpt = (s[3] - slope * s[1]) / s[0];
+    }
+    const double del = l2 - (icpt + slope * Ei);
+    if (i < n) dl[i] = del;
+    __syncthreads();
+    if (i < n) {
+        tl[i] = make_float2((float)l2, (float)del);
+        td[i] = make_float2((float)del, i + 1 < n ? (float)(dl[i + 1] - del) : 0.f);
+    }
+    if (i < 4) tl[n + i] = make_float2(-2000.f, 0.f);
+    __syncthreads();
+    return bad;
+}
+
+__global__ void __launch_bounds__(KX_FIN_THREADS)
+    k_prep(int n, int path, const double *__restrict__ f, const double *__restrict__ E,
+           const double *__restrict__ h, kx_batch_views v, const kx_inst_state *__restrict__ st) {
+    __shared__ double smem[64 + 32 + KX_MAX_N];
+    const int b = blockIdx.x;
+    if (st && st[b].done) return;
+    int bad = kx_prep_block(n, path, f + (long long)b * n, E, h, v.fmax + b,
+                            v.lf64 + (long long)b * n, v.tl + (long long)b * (n + 4),
+                            v.td + (long long)b * n, smem);
+    if (threadIdx.x == 0) v.flags[b] = bad;
+}
+
+cudaError_t kx_launch_prep(const kx_kernel *k, int B, const double *f, const kx_batch_views &v,
+                           const kx_inst_state *st, cudaStream_t s) {
+    int path = k->precision == KX_FP64 ? KX_FP64 : KX_FP32;
+    k_prep<<<B, KX_FIN_THREADS, 0, s>>>(k->n, path, f, k->d_E, k->d_h, v, st);
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------- FP64 contraction
+// Plain FP64 path: one thread per (i, pair) element, FP64 exp per element.
+__global__ void __launch_bounds__(KX_T64)
+    k_contract64(int n, long long P, int chunks, const uint32_t *__restrict__ pair,
+                 const double *__restrict__ W, const double *__restrict__ om,
+                 const uint16_t *__restrict__ jl, const double *__restrict__ f,
+                 const double *__restrict__ lf, double2 *__restrict__ partial,
+                 const kx_inst_state *__restrict__ st, int stage) {
+    const int c = blockIdx.x, i = blockIdx.y, b = blockIdx.z;
+    if (st && (st[b].done || (stage == 2 && st[b].skip2))) return;
+    __shared__ double s_f[KX_MAX_N], s_l[KX_MAX_N];
+    __shared__ double red[2 * 32];
+    for (int t = threadIdx.x; t < n; t += blockDim.x) {
+        s_f[t] = f[(long long)b * n + t];
+        s_l[t] = lf[(long long)b * n + t];
+    }
+    __syncthreads();
+    double g = 0.0, l = 0.0;
+    const long long base = (long long)i * P;
+    const long long p0 = (long long)c * KX_CH64;
+#pragma unroll 4
+    for (int e = 0; e < KX_EPT64; ++e) {
+        long long pidx = p0 + (long long)e * KX_T64 + threadIdx.x;
+        if (pidx < P) {
+            double w = W[base + pidx];
+            if (w != 0.0) {
+                uint32_t pr = pair[pidx];
+                int nn = pr & 0xffff, mm = pr >> 16;
+                int j = jl[base + pidx];
+                double o = om[base + pidx];
+                g += w * (s_f[nn] * s_f[mm]);
+                l += w * exp((1.0 - o) * s_l[j] + o * s_l[j + 1]);
+            }
+        }
+    }
+    double vals[2] = {g, l};
+    kx_block_sum<2>(vals, red);
+    if (threadIdx.x == 0)
+        partial[((long long)b * n + i) * chunks + c] = make_double2(vals[0], vals[1]);
+}
+
+// ------------------------------------------------------- FP32 contraction
+// Streaming path: 8 B per element (FP32 S, packed j_L/omega), read with 128-bit
+// coalesced loads; per element one ex2 for the log-interpolated loss and two
+// FMAs for the gain; per-thread FP32 sums, FP64 across threads/blocks.
+// BP instances sharing the kernel are evaluated from one pass over the tables.
+__device__ __forceinline__ float4 kx_ld_stream(const float4 *p) {
+    float4 r;
+    asm volatile("ld.global.nc.L1::no_allocate.v4.f32 {%0,%1,%2,%3}, [%4];"
+                 : "=f"(r.x), "=f"(r.y), "=f"(r.z), "=f"(r.w)
+                 : "l"(p));
+    return r;
+}
+__device__ __forceinline__ uint4 kx_ld_stream(const uint4 *p) {
+    uint4 r;
+    asm volatile("ld.global.nc.L1::no_allocate.v4.u32 {%0,%1,%2,%3}, [%4];"
+                 : "=r"(r.x), "=r"(r.y), "=r"(r.z), "=r"(r.w)
+                 : "l"(p));
+    return r;
+}
+
+__device__ __forceinline__ float kx_unpack_omega(uint32_t w) {
+    return __uint_as_float(0x3f800000u | (w & 0x7fffffu)) - 1.0f;
+}
+
+// 2^d - 1 for |d| < 1/4: Taylor series of expm1(x), x = d ln 2, through x^6
+// (truncation below 1e-9 relative); exact 0 at d = 0.
+__device__ __forceinline__ float kx_exp2m1_small(float d) {
+    const float c1 = 0.69314718056f, c2 = 0.24022650695f, c3 = 0.05550410866f;
+    const float c4 = 0.00961812911f, c5 = 0.00133335581f, c6 = 0.00015403530f;
+    float p = fmaf(d, c6, c5);
+    p = fmaf(d, p, c4);
+    p = fmaf(d, p, c3);
+    p = fmaf(d, p, c2);
+    p = fmaf(d, p, c1);
+    return d * p;
+}
+
+// One element's bracket f_n f_m - f_i f_t in units of f_max^2:
+//   a = l2_n + l2_m (gain exponent), d = (delta_i + delta_t) - (delta_n + delta_m)
+//   (loss minus gain exponent; the log-linear reference cancels), and
+//   f_n f_m - f_i f_t = 2^a (1 - 2^d): for |d| < 1/4 through the series above,
+//   else as 2^a - 2^(a + d) (no cancellation, no 0 * inf).
+__device__ __forceinline__ float kx_bracket_term(float a, float d) {
+    const float ea = kx_ex2(a);
+    const float near = -ea * kx_exp2m1_small(d);
+    const float far = ea - kx_ex2(a + d);
+    return fabsf(d) < 0.25f ? near : far;
+}
+
+template <int BP>
+__global__ void __launch_bounds__(KX_T32)
+    k_contract32(int n, int V, int chunks, int B, const uint32_t *__restrict__ vt,
+                 const float4 *__restrict__ W, const uint4 *__restrict__ PK,
+                 const float2 *__restrict__ tl, const float2 *__restrict__ td,
+                 double2 *__restrict__ partial, const kx_inst_state *__restrict__ st, int stage) {
+    const int c = blockIdx.x, i = blockIdx.y, b0 = blockIdx.z * BP;
+    __shared__ float2 s_l[BP][KX_MAX_N + 4];   // (l2_j, delta_j)
+    __shared__ float2 s_d[BP][KX_MAX_N];       // (delta_j, delta_{j+1} - delta_j)
+    __shared__ double red[BP * 32];
+    bool act[BP];
+    bool any = false;
+#pragma unroll
+    for (int bb = 0; bb < BP; ++bb) {
+        int b = b0 + bb;
+        act[bb] = b < B && !(st && (st[b].done || (stage == 2 && st[b].skip2)));
+        any |= act[bb];
+    }
+    if (!any) return;
+#pragma unroll
+    for (int bb = 0; bb < BP; ++bb) {
+        const int b = b0 + bb;
+        for (int t = threadIdx.x; t < n + 4; t += blockDim.x)
+            s_l[bb][t] = act[bb] ? tl[(long long)b * (n + 4) + t] : make_float2(-2000.f, 0.f);
+        for (int t = threadIdx.x; t < n; t += blockDim.x)
+            s_d[bb][t] = act[bb] ? td[(long long)b * n + t] : make_float2(0.f, 0.f);
+    }
+    __syncthreads();
+
+    float acc[BP], di[BP];
+#pragma unroll
+    for (int bb = 0; bb < BP; ++bb) {
+        acc[bb] = 0.f;
+        di[bb] = s_l[bb][i].y;
+    }
+    const float4 *Wr = W + (long long)i * V;
+    const uint4 *Pr = PK + (long long)i * V;
+    const int v0 = c * KX_CHV32 + threadIdx.x;
+    float4 w[KX_VPT32];
+    uint4 pk[KX_VPT32];
+    uint32_t nv[KX_VPT32];
+#pragma unroll
+    for (int e = 0; e < KX_VPT32; ++e) {
+        int v = v0 + e * KX_T32;
+        if (v < V) {
+            w[e] = kx_ld_stream(Wr + v);
+            pk[e] = kx_ld_stream(Pr + v);
+            nv[e] = __ldg(vt + v);
+        } else {
+            w[e] = make_float4(0.f, 0.f, 0.f, 0.f);
+            pk[e] = make_uint4(0u, 0u, 0u, 0u);
+            nv[e] = 0u;
+        }
+    }
+#pragma unroll
+    for (int e = 0; e < KX_VPT32; ++e) {
+        const int nn = nv[e] & 0xffff, m0 = nv[e] >> 16;
+        const float wk[4] = {w[e].x, w[e].y, w[e].z, w[e].w};
+        const uint32_t pw[4] = {pk[e].x, pk[e].y, pk[e].z, pk[e].w};
+#pragma unroll
+        for (int bb = 0; bb < BP; ++bb) {
+            const float2 ln = s_l[bb][nn];
+            const float dn_i = di[bb];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const float2 lm = s_l[bb][m0 + q];
+                const float2 dj = s_d[bb][pw[q] >> 23];
+                const float a = ln.x + lm.x;
+                const float d = (dn_i + fmaf(kx_unpack_omega(pw[q]), dj.y, dj.x)) - (ln.y + lm.y);
+                acc[bb] = fmaf(wk[q], kx_bracket_term(a, d), acc[bb]);
+            }
+        }
+    }
+    double vals[BP];
+#pragma unroll
+    for (int bb = 0; bb < BP; ++bb) vals[bb] = acc[bb];
+    kx_block_sum<BP>(vals, red);
+    if (threadIdx.x == 0) {
+#pragma unroll
+        for (int bb = 0; bb < BP; ++bb)
+            if (act[bb])
+                partial[((long long)(b0 + bb) * n + i) * chunks + c] = make_double2(vals[bb], 0.0);
+    }
+}
+
+int kx_chunks_per_row(const kx_kernel *k) {
+    if (k->precision == KX_FP64) return (int)((k->P + KX_CH64 - 1) / KX_CH64);
+    return (k->V + KX_CHV32 - 1) / KX_CHV32;
+}
+
+cudaError_t kx_launch_contract(const kx_kernel *k, int B, const double *f, const kx_batch_views &v,
+                               const kx_inst_state *st, int stage, cudaStream_t s) {
+    const int n = k->n, chunks = v.chunks;
+    if (k->precision == KX_FP64) {
+        dim3 grid(chunks, n, B);
+        k_contract64<<<grid, KX_T64, 0, s>>>(n, k->P, chunks, k->d_pair, k->d_W64, k->d_om64,
+                                             k->d_jl, f, v.lf64, v.partial, st, stage);
+        return cudaGetLastError();
+    }
+    const float4 *W = reinterpret_cast<const float4 *>(k->d_W32);
+    const uint4 *PK = reinterpret_cast<const uint4 *>(k->d_pk);
+    if (B >= 4) {
+        dim3 grid(chunks, n, (B + 3) / 4);
+        k_contract32<4><<<grid, KX_T32, 0, s>>>(n, k->V, chunks, B, k->d_vt, W, PK, v.tl, v.td,
+                                                v.partial, st, stage);
+    } else if (B == 2 || B == 3) {
+        dim3 grid(chunks, n, (B + 1) / 2);
+        k_contract32<2><<<grid, KX_T32, 0, s>>>(n, k->V, chunks, B, k->d_vt, W, PK, v.tl, v.td,
+                                                v.partial, st, stage);
+    } else {
+        dim3 grid(chunks, n, B);
+        k_contract32<1><<<grid, KX_T32, 0, s>>>(n, k->V, chunks, B, k->d_vt, W, PK, v.tl, v.td,
+                                                v.partial, st, stage);
+    }
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------- row combine + projection
+// Thread i of block b: C_raw_i = |M|^2 (G_i - f_i L_i) from the chunk partials
+// (fixed order), then the projection of Appendix B:
+//   xi_i = |f_i|/f_max (0 below eps_supp), A00 = sum h xi, A01 = sum h E xi,
+//   A11 = sum h E^2 xi, R0 = sum h C, R1 = sum h E C, (alpha, beta) = A^-1 R,
+//   C_proj = C - xi (alpha + beta E).
+struct kx_row_out {
+    double Craw, Cproj, alpha, beta;
+    int singular;
+};
+
+__device__ kx_row_out kx_combine_project(int n, int chunks, int path, int b, double fi, double Ei,
+                                         double hi, const kx_batch_views &v, int project,
+                                         double *smem) {
+    const int i = threadIdx.x;
+    const double fm = v.fmax[b];
+    double G = 0.0, L = 0.0;
+    if (i < n) {
+        const double2 *pp = v.partial + ((long long)b * n + i) * chunks;
+        for (int c = 0; c < chunks; ++c) {
+            double2 x = pp[c];
+            G += x.x;
+            L += x.y;
+        }
+    }
+    double Craw;
+    if (path == KX_FP64) Craw = v.M2[b] * (G - fi * L);
+    else Craw = v.M2[b] * (fm * fm * G);  // FP32 path: G holds sum S (f_n f_m - f_i f_t) / f_max^2
+    if (i >= n) Craw = 0.0;
+    kx_row_out r;
+    r.Craw = Craw;
+    r.Cproj = Craw;
+    r.alpha = r.beta = 0.0;
+    r.singular = 0;
+    if (!project) return r;
+    double xi = 0.0;
+    if (i < n && fm > 0.0) {
+        double q = fabs(fi) / fm;
+        xi = q > KX_EPS_SUPP ? q : 0.0;
+    }
+    double s[5] = {hi * xi, hi * Ei * xi, hi * Ei * Ei * xi, hi * Craw, hi * Ei * Craw};
+    kx_block_sum<5>(s, smem);
+    double det = s[0] * s[2] - s[1] * s[1];
+    if (!(det > KX_DET_GUARD * s[0] * s[2])) {
+        r.singular = 1;
+    } else {
+        r.alpha = (s[3] * s[2] - s[4] * s[1]) / det;
+        r.beta = (s[4] * s[0] - s[3] * s[1]) / det;
+    }
+    r.Cproj = Craw - xi * (r.alpha + r.beta * Ei);
+    return r;
+}
+
+__device__ void kx_write_diag(int n, double Ei, double hi, const kx_row_out &r, kx_diag *d,
+                              double fm, int bad, double *smem) {
+    const int i = threadIdx.x;
+    double C = i < n ? r.Craw : 0.0, P = i < n ? r.Cproj : 0.0;
+    double s[10] = {hi * C,         hi * Ei * C,     hi * fabs(C),    hi * Ei * fabs(C),
+                    hi * P,         hi * Ei * P,     hi * fabs(P),    hi * Ei * fabs(P),
+                    hi * fabs(P - C), hi * Ei * fabs(P - C)};
+    int nf = (i < n) && !(isfinite(C) && isfinite(P));
+    kx_block_sum<10>(s, smem);
+    nf = kx_block_or(nf, smem) || bad;
+    if (threadIdx.x == 0) {
+        d->eps_N_raw = s[2] > 0 ? s[0] / s[2] : 0.0;
+        d->eps_E_raw = s[3] > 0 ? s[1] / s[3] : 0.0;
+        d->eps_N_proj = s[6] > 0 ? s[4] / s[6] : 0.0;
+        d->eps_E_proj = s[7] > 0 ? s[5] / s[7] : 0.0;
+        d->R_N = s[2] > 0 ? s[8] / s[2] : 0.0;
+        d->R_E = s[3] > 0 ? s[9] / s[3] : 0.0;
+        d->alpha = r.alpha;
+        d->beta = r.beta;
+        d->f_max = fm;
+        d->singular = r.singular;
+        d->status = nf ? KX_ENONFINITE : KX_OK;
+    }
+}
+
+__global__ void __launch_bounds__(KX_FIN_THREADS)
+    k_finalize(int n, int chunks, int path, const double *__restrict__ f,
+               const double *__restrict__ E, const double *__restrict__ h, kx_batch_views v,
+               double *__restrict__ Cout, int project, int want_diag) {
+    __shared__ double smem[10 * 32];
+    const int b = blockIdx.x, i = threadIdx.x;
+    double fi = 0.0, Ei = 0.0, hi = 0.0;
+    if (i < n) {
+        fi = f[(long long)b * n + i];
+        Ei = E[i];
+        hi = h[i];
+    }
+    kx_row_out r = kx_combine_project(n, chunks, path, b, fi, Ei, hi, v, project, smem);
+    if (i < n) Cout[(long long)b * n + i] = project ? r.Cproj : r.Craw;
+    if (want_diag) kx_write_diag(n, Ei, hi, r, v.diag + b, v.fmax[b], v.flags[b], smem);
+}
+
+cudaError_t kx_launch_finalize(const kx_kernel *k, int B, const double *f, const kx_batch_views &v,
+                               double *C_out, int project, int want_diag, cudaStream_t s) {
+    int path = k->precision == KX_FP64 ? KX_FP64 : KX_FP32;
+    k_finalize<<<B, KX_FIN_THREADS, 0, s>>>(k->n, v.chunks, path, f, k->d_E, k->d_h, v, C_out,
+                                            project, want_diag);
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------------ MB fit -----
+// Moment-matched discrete Maxwell-Boltzmann: T solves <E>_MB(T) = sum h E f /
+// sum h f (safeguarded Newton in u = ln T inside [ln 1e-12, ln 1e12]; <E>(T) is
+// increasing with d<E>/du = Var(E)/T), z from the number moment,
+// L1 = sum h |f - f_MB| / sum h f.  Block-wide; returns (T, ln z, L1) to all threads.
+__device__ void kx_mb_fit_block(int n, double fi, double Ei, double hi, double E0, double *out,
+                                double *smem) {
+    const bool in = threadIdx.x < n;
+    double s0[2] = {in ? hi * fi : 0.0, in ? hi * Ei * fi : 0.0};
+    kx_block_sum<2>(s0, smem);
+    const double N0 = s0[0];
+    if (!(N0 > 0.0)) {
+        out[0] = 0.0;
+        out[1] = 0.0;
+        out[2] = INFINITY;
+        return;
+    }
+    const double ebar = s0[1] / N0;
+    double lo = log(1e-12), hi_u = log(1e12);
+    double T0 = (ebar - E0) / 1.5;
+    double u = T0 > 1e-12 ? log(T0) : lo;
+    if (u > hi_u) u = hi_u;
+    double T = exp(u);
+    for (int it = 0; it < 200; ++it) {
+        T = exp(u);
+        double wgt = in ? hi * exp(-(Ei - E0) / T) : 0.0;
+        double s[3] = {wgt, wgt * Ei, wgt * Ei * Ei};
+        kx_block_sum<3>(s, smem);
+        double mean = s[1] / s[0];
+        double var = s[2] / s[0] - mean * mean;
+        double g = mean - ebar;
+        if (g < 0.0) lo = u; else hi_u = u;
+        double un = (var > 0.0) ? u - g * T / var : 0.5 * (lo + hi_u);
+        if (!(un > lo && un < hi_u)) un = 0.5 * (lo + hi_u);
+        if (fabs(un - u) < 1e-14 * fmax(1.0, fabs(u)) || hi_u - lo < 1e-15) {
+            u = un;
+            break;
+        }
+        u = un;
+    }
+    T = exp(u);
+    double w = in ? exp(-(Ei - E0) / T) : 0.0;
+    double s1[1] = {in ? hi * w : 0.0};
+    kx_block_sum<1>(s1, smem);
+    double fmb = N0 * w / s1[0];
+    double s2[1] = {in ? hi * fabs(fi - fmb) : 0.0};
+    kx_block_sum<1>(s2, smem);
+    out[0] = T;
+    out[1] = log(N0 / s1[0]) + E0 / T;
+    out[2] = s2[0] / N0;
+}
+
+__global__ void __launch_bounds__(KX_FIN_THREADS)
+    k_mbfit(int n, const double *__restrict__ f, const double *__restrict__ E,
+            const double *__restrict__ h, double *__restrict__ out3) {
+    __shared__ double smem[3 * 32];
+    const int b = blockIdx.x, i = threadIdx.x;
+    double fi = i < n ? f[(long long)b * n + i] : 0.0;
+    double Ei = i < n ? E[i] : 0.0, hi = i < n ? h[i] : 0.0;
+    double o[3];
+    kx_mb_fit_block(n, fi, Ei, hi, E[0], o, smem);
+    if (threadIdx.x == 0) {
+        out3[3 * b] = o[0];
+        out3[3 * b + 1] = o[1];
+        out3[3 * b + 2] = o[2];
+    }
+}
+
+cudaError_t kx_launch_mbfit(const kx_kernel *k, int B, const double *f, double *out3,
+                            cudaStream_t s) {
+    k_mbfit<<<B, KX_FIN_THREADS, 0, s>>>(k->n, f, k->d_E, k->d_h, out3);
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------------ Heun stages
+// Source S_i(t) = sum_k rate_k env_k(t) shape_k,i (shapes pre-normalised so
+// that sum_i h_i shape_k,i = 1), env_k = exp(-(t - t_on)/tau) for t >= t_on.
+__device__ __forceinline__ double kx_source_at(const kx_src_dev &src, const double *shapes, int n,
+                                               int i, double t) {
+    double S = 0.0;
+    for (int k = 0; k < src.n_src; ++k) {
+        if (t < src.t_on[k]) continue;
+        double env = exp(-(t - src.t_on[k]) / src.tau[k]);
+        S += src.rate[k] * env * shapes[src.shape_off + (long long)k * n + i];
+    }
+    return S;
+}
+
+// stage 1: k1 = C_proj[f] + S(t); f_p = f + h k1 (Euler predictor), prep(f_p).
+// stage 2: k2 = C_proj[f_p] + S(t + h); f_c = f + h/2 (k1 + k2) (trapezoid
+//          corrector), err = max |f_c - f_p| / (atol + rtol |f_c|), accept or
+//          reject, next h, MB stopping test, prep(next f).
+__global__ void __launch_bounds__(KX_FIN_THREADS)
+    k_stage(int n, int chunks, int path, const double *__restrict__ E,
+            const double *__restrict__ h, kx_batch_views v, kx_step_views sv, int stage,
+            long long max_attempts) {
+    __shared__ double smem[64 + 32 + KX_MAX_N];
+    const int b = blockIdx.x, i = threadIdx.x;
+    kx_inst_state *st = sv.st + b;
+    if (st->done) return;
+    if (stage == 2 && st->skip2) {
+        __syncthreads();
+        if (threadIdx.x == 0) st->skip2 = 0;
+        return;
+    }
+    const bool in = i < n;
+    const double Ei = in ? E[i] : 0.0, hi = in ? h[i] : 0.0;
+    double *fb = sv.f + (long long)b * n;
+    double *k1 = sv.k1 + (long long)b * n;
+    double *fp = sv.fp + (long long)b * n;
+    const double t = st->t;
+    double htry;
+    if (stage == 1) {
+        htry = st->h;
+        if (!sv.fixed) {
+            if (htry > sv.h_max) htry = sv.h_max;
+            if (htry < sv.h_min) htry = sv.h_min;
+        }
+        int last = 0;
+        if (t + htry >= st->t_end) {
+            htry = st->t_end - t;
+            last = 1;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            st->h_try = htry;
+            st->last = last;
+        }
+    } else {
+        htry = st->h_try;
+    }
+    const double fcur = in ? (stage == 1 ? fb[i] : fp[i]) : 0.0;
+    kx_row_out r = kx_combine_project(n, chunks, path, b, fcur, Ei, hi, v, sv.project, smem);
+    const double C = sv.project ? r.Cproj : r.Craw;
+    const double tS = stage == 1 ? t : t + htry;
+    const double kv = in ? C + kx_source_at(sv.src[b], sv.shapes, n, i, tS) : 0.0;
+    const double f0 = in ? fb[i] : 0.0;
+    __syncthreads();
+    if (stage == 1) {
+        const double fpi = f0 + htry * kv;
+        int bad = in && !isfinite(fpi);
+        int neg = in && fpi < 0.0;
+        bad = kx_block_or(bad | v.flags[b], smem);
+        neg = kx_block_or(neg, smem);
+        if (bad) {
+            if (threadIdx.x == 0) {
+                st->status = KX_ENONFINITE;
+                st->done = 1;
+                st->evals += 1;
+            }
+            return;
+        }
+        if (neg) {
+            if (threadIdx.x == 0) {
+                st->evals += 1;
+                if (sv.fixed) {
+                    st->status = KX_ENEG;
+                    st->done = 1;
+                } else {
+                    st->h = 0.5 * htry;
+                    st->rejects += 1;
+                    st->skip2 = 1;
+                    if (st->steps + st->rejects >= max_attempts) {
+                        st->status = KX_ENOCONV;
+                        st->done = 1;
+                    }
+                }
+            }
+            return;
+        }
+        if (in) {
+            k1[i] = kv;
+            fp[i] = fpi;
+        }
+        if (threadIdx.x == 0) st->evals += 1;
+        __syncthreads();
+        int bad2 = kx_prep_block(n, path, fp, E, h, v.fmax + b, v.lf64 + (long long)b * n,
+                                 v.tl + (long long)b * (n + 4), v.td + (long long)b * n, smem);
+        if (threadIdx.x == 0) v.flags[b] = bad2;
+        return;
+    }
+    // stage 2
+    const double fpi = in ? fp[i] : 0.0;
+    const double fci = f0 + 0.5 * htry * ((in ? k1[i] : 0.0) + kv);
+    double e = in ? fabs(fci - fpi) / (sv.atol + sv.rtol * fabs(fci)) : 0.0;
+    int bad = in && !isfinite(fci);
+    int neg = in && fci < 0.0;
+    bad = kx_block_or(bad | v.flags[b], smem);
+    neg = kx_block_or(neg, smem);
+    double err = kx_block_max(e, smem);
+    if (bad) {
+        if (threadIdx.x == 0) {
+            st->status = KX_ENONFINITE;
+            st->done = 1;
+            st->evals += 1;
+        }
+        return;
+    }
+    int accept;
+    double hnext;
+    if (sv.fixed) {
+        if (neg) {
+            if (threadIdx.x == 0) {
+                st->status = KX_ENEG;
+                st->done = 1;
+                st->evals += 1;
+            }
+            return;
+        }
+        accept = 1;
+        hnext = htry;
+    } else if (neg) {
+        accept = 0;
+        hnext = 0.5 * htry;
+    } else {
+        double fac = err > 0.0 ? 0.9 / sqrt(err) : 5.0;
+        if (fac > 5.0) fac = 5.0;
+        if (fac < 0.2) fac = 0.2;
+        hnext = htry * fac;
+        accept = err <= 1.0;
+    }
+    double tn = t;
+    if (accept) {
+        if (in) fb[i] = fci;
+        tn = st->last ? st->t_end : t + htry;
+    }
+    __syncthreads();
+    long long steps = st->steps + (accept ? 1 : 0);
+    long long rejects = st->rejects + (accept ? 0 : 1);
+    int done = 0, converged = 0;
+    double fit[3] = {st->l1, st->T, st->lnz};
+    if (accept && sv.check_every > 0 && sv.l1_tol > 0.0 && steps % sv.check_every == 0 &&
+        tn >= sv.src[b].t_off) {
+        const double fnew = in ? fb[i] : 0.0;
+        double o[3];
+        kx_mb_fit_block(n, fnew, Ei, hi, E[0], o, smem);
+        fit[0] = o[2];
+        fit[1] = o[0];
+        fit[2] = o[1];
+        if (o[2] <= sv.l1_tol) {
+            converged = 1;
+            done = 1;
+        }
+    }
+    int status = KX_OK;
+    if (!done) {
+        if (tn >= st->t_end) done = 1;
+        else if (steps + rejects >= max_attempts) {
+            done = 1;
+            status = KX_ENOCONV;
+        }
+    }
+    if (threadIdx.x == 0) {
+        st->t = tn;
+        st->h = hnext;
+        st->err = err;
+        st->steps = steps;
+        st->rejects = rejects;
+        st->evals += 1;
+        st->l1 = fit[0];
+        st->T = fit[1];
+        st->lnz = fit[2];
+        st->converged = converged;
+        if (done) {
+            st->done = 1;
+            st->status = status;
+        }
+    }
+    // prepare the next attempt's contraction input (f_new or the restored f)
+    int bad2 = kx_prep_block(n, path, fb, E, h, v.fmax + b, v.lf64 + (long long)b * n,
+                             v.tl + (long long)b * (n + 4), v.td + (long long)b * n, smem);
+    if (threadIdx.x == 0) v.flags[b] = bad2;
+}
+
+cudaError_t kx_launch_stage(const kx_kernel *k, int B, const kx_batch_views &v,
+                            const kx_step_views &sv, int stage, cudaStream_t s) {
+    int path = k->precision == KX_FP64 ? KX_FP64 : KX_FP32;
+    k_stage<<<B, KX_FIN_THREADS, 0, s>>>(k->n, v.chunks, path, k->d_E, k->d_h, v, sv, stage,
+                                         sv.max_attempts);
+    return cudaGetLastError();
+}

@@ -1,0 +1,147 @@
+// kx_internal.cuh -- internal structures of libkx (not part of the ABI).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/kx.h"
+
+#define KX_MAX_N 512
+#define KX_MAX_NMU 64
+#define KX_MAX_SRC 4
+#define KX_LOG_FLOOR 1e-300   // floor of f inside the logarithm (Appendix A, "small positive floor")
+#define KX_EPS_SUPP 1e-12     // epsilon_supp of the projection (Appendix B)
+#define KX_DET_GUARD 1e-14    // relative guard of the 2x2 projection system
+
+// Chunking of the contraction work (elements of one row i are split in chunks
+// whose partial sums are combined in a fixed order: results are deterministic).
+#define KX_T64 256            // threads per FP64 contraction block
+#define KX_EPT64 8            // pairs per thread
+#define KX_CH64 (KX_T64 * KX_EPT64)
+#define KX_T32 256            // threads per FP32 contraction block
+#define KX_VPT32 4            // 4-element vectors per thread
+#define KX_CHV32 (KX_T32 * KX_VPT32)
+#define KX_FIN_THREADS 512    // finalize / stage kernels: one block per instance, thread = grid point
+
+struct kx_gl_nodes {
+    double x[KX_MAX_NMU];
+    double w[KX_MAX_NMU];
+};
+
+struct kx_kernel {
+    int refcount;
+    int device;
+    int n, n_mu, measure, precision;
+    double a, mass;
+    long long P;         // pairs n <= m: n(n+1)/2
+    int V;               // 4-element vectors per row (FP32 layout, segments padded to 4)
+    // grid (device, FP64)
+    double *d_p, *d_E, *d_dp, *d_dE, *d_h;
+    std::vector<double> p, E, dp, dE, h, q;
+    // FP64 tables [n][P]
+    uint32_t *d_pair;    // [P]: n | m << 16
+    double *d_W64;
+    double *d_om64;
+    uint16_t *d_jl;
+    // FP32 tables [n][4V]
+    uint32_t *d_vt;      // [V]: n | m0 << 16 (first m of the vector)
+    float *d_W32;
+    uint32_t *d_pk;      // j_L << 23 | round(omega 2^23)
+    long long nnz;
+    long long bytes;
+    double build_ms;
+};
+
+// Per-instance integration state (device resident).
+struct kx_inst_state {
+    double t, h, h_try, t_end, err;
+    double l1, T, lnz;
+    long long steps, rejects, evals;
+    int status;      // KX_OK or error
+    int done;        // 1: finished (converged, t_end, error)
+    int converged;
+    int skip2;       // stage 1 rejected: skip stage 2 of this attempt
+    int last;        // this attempt ends exactly at t_end
+    int pad;
+};
+
+struct kx_src_dev {
+    int n_src;
+    int pad;
+    double rate[KX_MAX_SRC];
+    double tau[KX_MAX_SRC];
+    double t_on[KX_MAX_SRC];
+    double t_off;            // all envelopes < 1e-12 of their peak for t >= t_off
+    long long shape_off;     // offset (doubles) of this instance's normalised shapes
+};
+
+struct kx_ctx {
+    int device;
+    cudaStream_t stream;
+    std::string last_error;
+    void *d_arena;
+    size_t arena_bytes;
+    void *h_pinned;
+    size_t pinned_bytes;
+    long long launches;      // kernels enqueued through this context
+};
+
+// error helpers ---------------------------------------------------------------
+int kx_set_error(kx_ctx *ctx, int code, const std::string &msg);
+#define KX_CUDA_TRY(ctx, expr)                                                         \
+    do {                                                                               \
+        cudaError_t _e = (expr);                                                       \
+        if (_e != cudaSuccess)                                                         \
+            return kx_set_error((ctx), KX_ECUDA, std::string(#expr) + ": " +           \
+                                                   cudaGetErrorString(_e));            \
+    } while (0)
+
+// launch wrappers (defined in the .cu files) ----------------------------------
+struct kx_batch_views {
+    // per call scratch carved from the context arena
+    double *fmax;          // [B]
+    double *lf64;          // [B][n]       FP64 path: ln max(f, floor)
+    float2 *tl;            // [B][n + 4]   FP32 path: (l2_j, delta_j), l2 = log2(max(f, floor)/f_max)
+    float2 *td;            // [B][n]       FP32 path: (delta_j, delta_{j+1} - delta_j)
+    double2 *partial;      // [B][n][chunks]
+    int *flags;            // [B] non-finite flags
+    double *M2;            // [B] |M|^2 per instance
+    kx_diag *diag;         // [B]
+    int chunks;
+};
+
+int kx_chunks_per_row(const kx_kernel *k);
+size_t kx_views_bytes(const kx_kernel *k, int B);
+void kx_carve_views(const kx_kernel *k, int B, void *base, kx_batch_views *v);
+
+cudaError_t kx_launch_build_fp64(const kx_kernel *k, const kx_gl_nodes &gl, cudaStream_t s);
+cudaError_t kx_launch_pack_fp32(const kx_kernel *k, cudaStream_t s);
+cudaError_t kx_launch_count_nnz(const kx_kernel *k, unsigned long long *d_count, cudaStream_t s);
+
+// prep: f -> (fmax, lf64 | sf, sld); mode selects path
+cudaError_t kx_launch_prep(const kx_kernel *k, int B, const double *f, const kx_batch_views &v,
+                           const kx_inst_state *st, cudaStream_t s);
+cudaError_t kx_launch_contract(const kx_kernel *k, int B, const double *f, const kx_batch_views &v,
+                               const kx_inst_state *st, int stage, cudaStream_t s);
+// finalize for kx_collision: C_out = (proj) C_raw
+cudaError_t kx_launch_finalize(const kx_kernel *k, int B, const double *f, const kx_batch_views &v,
+                               double *C_out, int project, int want_diag, cudaStream_t s);
+
+// integration stage kernels
+struct kx_step_views {
+    double *f;          // [B][n] state
+    double *k1;         // [B][n]
+    double *fp;         // [B][n] predictor
+    kx_inst_state *st;  // [B]
+    const kx_src_dev *src;   // [B]
+    const double *shapes;    // normalised source shapes
+    double rtol, atol, h_min, h_max, l1_tol;
+    long long max_attempts;
+    int fixed, check_every, project;
+};
+cudaError_t kx_launch_stage(const kx_kernel *k, int B, const kx_batch_views &v,
+                            const kx_step_views &sv, int stage, cudaStream_t s);
+cudaError_t kx_launch_mbfit(const kx_kernel *k, int B, const double *f, double *out3,
+                            cudaStream_t s);

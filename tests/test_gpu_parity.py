@@ -1,0 +1,357 @@
+"""GPU parity: the CUDA path through the C ABI against the FP64 oracle.
+
+Tolerances (max-norm relative, max_i |dC_i| / max_i |C_i|): 1e-12 for the FP64
+path, 1e-5 for the FP32 streaming path; conserved moments after an FP32-path
+integration to 1e-7 relative.  Integer and index data (support, bracket j_L)
+are compared bit-exactly.
+"""
+import numpy as np
+import pytest
+
+import kx_inputs as ki
+import oracle
+
+pytestmark = pytest.mark.gpu
+
+TOL = {0: 1e-12, 1: 1e-5}
+
+
+@pytest.fixture(scope="module")
+def kx():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    import paper_2607_00755_b300 as kxm
+    from paper_2607_00755_b300 import build
+    build.build()
+    return kxm
+
+
+@pytest.fixture(scope="module")
+def ctx(kx):
+    c = kx.Context(0)
+    yield c
+    c.close()
+
+
+def dev(a):
+    import torch
+    return torch.as_tensor(np.ascontiguousarray(a, dtype=np.float64), device="cuda")
+
+
+def sym_pairs(Wo):
+    """Oracle W[i, n, m] -> symmetrised pair layout S[i, (n <= m)]."""
+    N = Wo.shape[0]
+    iu = np.triu_indices(N)
+    S = Wo + Wo.transpose(0, 2, 1)
+    d = np.arange(N)
+    S[:, d, d] = Wo[:, d, d]
+    return S[:, iu[0], iu[1]]
+
+
+def oracle_C(q, f, sigma, project, W=None):
+    """Oracle C (rows [B, n]) with |M|^2 = 64 pi m^2 sigma_b."""
+    f = np.atleast_2d(f)
+    g = oracle.grid(q)
+    if W is None:
+        W = oracle.kernel_tensor(q)
+    out, diags = [], []
+    for b in range(f.shape[0]):
+        C = oracle.collision_tensor(q, W, f[b]) * oracle.M2_from_sigma(1.0, sigma[b])
+        if project:
+            C, d = oracle.project(g["E"], g["h"], f[b], C)
+        else:
+            _, d = oracle.project(g["E"], g["h"], f[b], C)
+        out.append(C)
+        diags.append(d)
+    return np.array(out), diags
+
+
+def relerr(a, b):
+    return np.max(np.abs(a - b)) / max(np.max(np.abs(b)), 1e-300)
+
+
+# --------------------------------------------------------------- kernel ----
+@pytest.mark.parametrize("N,measure,grid", [(24, 0, "log"), (40, 1, "log"), (37, 0, "random")])
+def test_kernel_tensor_matches_oracle(ctx, kx, N, measure, grid):
+    rng = np.random.default_rng(N)
+    q = ki.log_grid(N, 1e-3, 10.0) if grid == "log" else ki.random_grid(rng, N)
+    k = ctx.build_kernel(q, measure=measure, precision=kx.FP64)
+    g = k.grid()
+    go = oracle.grid(q)
+    for key in ("p", "E", "dp", "dE", "h"):
+        np.testing.assert_array_equal(g[key], go[key])
+    So = sym_pairs(oracle.kernel_tensor(q, measure=measure))
+    jLo, omo = oracle.bracket_tensor(q)
+    iu = np.triu_indices(N)
+    flips = 0
+    for i in range(N):
+        W, jl, om = k.row(i)
+        sup = jLo[i][iu] >= 0
+        np.testing.assert_array_equal(W[~sup], 0.0)
+        np.testing.assert_array_equal(jl[sup], jLo[i][iu][sup])
+        np.testing.assert_array_equal(om[sup], omo[i][iu][sup])
+        d = np.abs(W - So[i])
+        flips += int(np.sum(d > 1e-12 * np.abs(So[i]) + 1e-300))
+        assert np.max(d) <= 1e-13 * np.max(np.abs(So))
+    assert flips == 0, f"Theta/support flips: {flips}"
+    info = k.info()
+    assert info["nonzero_elements"] == int(np.count_nonzero(So))
+
+
+def test_build_rejects_bad_grids(ctx, kx):
+    with pytest.raises(kx.KxError):
+        ctx.build_kernel(np.array([1.0, 2.0, 3.0]))
+    with pytest.raises(kx.KxError):
+        ctx.build_kernel(np.array([1.0, 3.0, 2.0, 4.0]))
+    with pytest.raises(kx.KxError):
+        ctx.build_kernel(ki.log_grid(513, 1e-3, 10.0))
+    with pytest.raises(kx.KxError):
+        ctx.build_kernel(ki.log_grid(16, 1e-3, 10.0), mass=0.0)
+    with pytest.raises(kx.KxError):
+        ctx.build_kernel(ki.log_grid(16, 1e-3, 10.0), stats=1)
+
+
+# ------------------------------------------------------------ collision ----
+@pytest.mark.parametrize("precision", [0, 1])
+@pytest.mark.parametrize("N", [4, 17, 64, 130])
+def test_collision_matches_oracle(ctx, kx, precision, N):
+    rng = np.random.default_rng(100 + N)
+    q = ki.log_grid(N, 1e-3, 10.0 if N < 100 else 1e2)
+    f = ki.batch_bimodal(rng, q, 3)
+    sigma = np.array([1.0, 0.25, 7.0])
+    k = ctx.build_kernel(q, precision=precision)
+    W = oracle.kernel_tensor(q)
+    fd = dev(f)
+    for project in (0, 1):
+        C, diag = ctx.collision(k, fd, sigma, project=bool(project), diag=True)
+        Co, do = oracle_C(q, f, sigma, project, W)
+        C = C.cpu().numpy()
+        g = oracle.grid(q)
+        for b in range(3):
+            assert relerr(C[b], Co[b]) <= TOL[precision], (b, relerr(C[b], Co[b]))
+            assert diag[b]["status"] == 0
+            if project:
+                # the diagnostics are h- (and hE-) weighted ratios: their error is
+                # bounded by the weighted C error, not by the max-norm one
+                Craw = oracle_C(q, f[b], [sigma[b]], 0, W)[0][0]
+                for key, wgt in (("eps_N_raw", g["h"]), ("eps_E_raw", g["h"] * g["E"]),
+                                 ("R_N", g["h"]), ("R_E", g["h"] * g["E"])):
+                    bound = 4 * np.sum(wgt * np.abs(C[b] - Co[b])) / np.sum(wgt * np.abs(Craw))
+                    bound += 8 * TOL[precision] * np.max(np.abs(Craw)) * np.sum(wgt) / np.sum(wgt * np.abs(Craw))
+                    assert abs(diag[b][key] - do[b][key]) <= bound + 1e-14, (key, diag[b][key], do[b][key])
+                # projected moments vanish to rounding (Appendix B), amplified by the
+                # condition number of the 2x2 system
+                xi = np.abs(f[b]) / np.max(np.abs(f[b]))
+                xi[xi <= 1e-12] = 0.0
+                A = [np.sum(g["h"] * xi * g["E"] ** k) for k in range(3)]
+                cond = A[0] * A[2] / (A[0] * A[2] - A[1] ** 2)
+                for wgt in (g["h"], g["h"] * g["E"]):
+                    assert abs(np.sum(wgt * C[b])) <= 1e-14 * cond * np.sum(wgt * np.abs(Craw))
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_collision_full_size_sampled_rows(ctx, kx, precision):
+    """N = 384 and 512 (the maximum): every row on the GPU, sampled rows by the
+    oracle's direct per-row form."""
+    for N in (384, 512):
+        rng = np.random.default_rng(N)
+        q = ki.log_grid(N, 1e-3, 1e2)
+        f = ki.batch_bimodal(rng, q, 1)[0]
+        k = ctx.build_kernel(q, precision=precision)
+        C, _ = ctx.collision(k, dev(f[None]), 1.0, project=False)
+        C = C.cpu().numpy()[0]
+        rows = np.unique(np.concatenate([[0, 1, N // 2, N - 2, N - 1], rng.integers(0, N, 5)]))
+        Co, G, L = oracle.collision_rows(q, f, rows, M2=oracle.M2_from_sigma(1.0, 1.0))
+        scale = np.max(np.abs(C))
+        assert np.max(np.abs(C[rows] - Co)) <= TOL[precision] * scale
+        k.release()
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_collision_edge_cases(ctx, kx, precision):
+    N = 20
+    q = ki.log_grid(N, 1e-3, 10.0)
+    k = ctx.build_kernel(q, precision=precision)
+    g = oracle.grid(q)
+    # all-zero f: C = 0, projection flagged singular
+    C, d = ctx.collision(k, dev(np.zeros((1, N))), 1.0, diag=True)
+    assert np.all(C.cpu().numpy() == 0.0) and d[0]["singular"] == 1
+    # zeros inside the support (log floor) and a single populated bin
+    f = ki.bimodal(np.random.default_rng(3), q)
+    f[5:9] = 0.0
+    f1 = np.zeros(N)
+    f1[7] = 0.3
+    for fx in (f, f1):
+        C, d = ctx.collision(k, dev(fx[None]), 2.0, diag=True)
+        Co, do = oracle_C(q, fx, [2.0], 1)
+        assert relerr(C.cpu().numpy()[0], Co[0]) <= TOL[precision]
+        assert d[0]["singular"] == do[0]["singular"]
+    # Maxwell-Boltzmann fixed point (eq. app_log_interp preserves MB)
+    fm = 0.4 * np.exp(-g["E"] / 0.5)
+    C, d = ctx.collision(k, dev(fm[None]), 1.0, project=False, diag=True)
+    _, G, _ = oracle.collision_tensor(q, oracle.kernel_tensor(q), fm, parts=True)
+    assert np.max(np.abs(C.cpu().numpy())) <= (1e-13 if precision == 0 else 1e-6) * \
+        oracle.M2_from_sigma(1.0, 1.0) * np.max(G)
+    # non-finite input is reported
+    fn = f.copy()
+    fn[3] = np.nan
+    _, d = ctx.collision(k, dev(fn[None]), 1.0, diag=True)
+    assert d[0]["status"] == kx.ENONFINITE
+    # bad sigma
+    with pytest.raises(kx.KxError):
+        ctx.collision(k, dev(f[None]), -1.0)
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_batch_is_bitwise_independent_of_co_scheduling(ctx, kx, precision):
+    """Each instance's C is bit-identical alone and inside a batch."""
+    N = 48
+    q = ki.log_grid(N, 1e-3, 10.0)
+    f = ki.batch_bimodal(np.random.default_rng(9), q, 6)
+    sig = np.array([1.0, 2.0, 0.5, 3.0, 1.5, 0.1])
+    k = ctx.build_kernel(q, precision=precision)
+    Cb, _ = ctx.collision(k, dev(f), sig)
+    Cb = Cb.cpu().numpy()
+    for b in range(6):
+        Ca, _ = ctx.collision(k, dev(f[b:b + 1]), sig[b:b + 1])
+        np.testing.assert_array_equal(Ca.cpu().numpy()[0], Cb[b])
+    Ch, _ = ctx.collision_host(k, f, sig)
+    np.testing.assert_array_equal(Ch, Cb)
+
+
+# ----------------------------------------------------------- integration ---
+def test_single_heun_attempt_matches_oracle(ctx, kx):
+    N = 32
+    q = ki.log_grid(N, 1e-3, 10.0)
+    f0 = ki.bimodal(np.random.default_rng(21), q)
+    k = ctx.build_kernel(q, precision=kx.FP64)
+    W = oracle.kernel_tensor(q)
+    src = ki.two_sources(q)
+    M2 = oracle.M2_from_sigma(1.0, 1.0)
+    for h0 in (0.01, 0.5, 5.0):   # accepted, rejected by error, rejected by negativity
+        fd = dev(f0[None])
+        t = np.array([0.2])
+        h = np.array([h0])
+        res = ctx.step(k, fd, 1.0, t, h, sources=src, t_end=100.0, rtol=1e-6, atol=1e-12)
+        fo, ro = oracle.solve(q, W, f0, M2, sources=src, t0=0.2, t_end=100.0, h0=h0,
+                              max_attempts=1, rtol=1e-6, atol=1e-12)
+        assert res[0]["steps"] == ro["steps"] and res[0]["rejects"] == ro["rejects"]
+        assert abs(h[0] - ro["h"]) <= 1e-12 * ro["h"]
+        assert abs(t[0] - ro["t"]) <= 1e-15 * max(1.0, ro["t"])
+        assert relerr(fd.cpu().numpy()[0], fo) <= 1e-12
+
+
+def test_fixed_step_solve_matches_oracle_config1(ctx, kx):
+    """Configuration 1: N = 32, 100 fixed Heun steps."""
+    c = ki.config1()
+    q, f0 = c["q"], c["f0"]
+    W = oracle.kernel_tensor(q)
+    fo, ro = oracle.solve(q, W, f0, oracle.M2_from_sigma(1.0, c["sigma"]), t_end=c["n_steps"] * c["h"],
+                          h0=c["h"], fixed_step=1)
+    assert ro["status"] == 0 and ro["steps"] == c["n_steps"]
+    g = oracle.grid(q)
+    for precision in (0, 1):
+        k = ctx.build_kernel(q, precision=precision)
+        fd = dev(f0[None])
+        res = ctx.solve(k, fd, c["sigma"], t_end=c["n_steps"] * c["h"], h0=c["h"], fixed_step=1)
+        f = fd.cpu().numpy()[0]
+        assert res[0]["status"] == 0 and res[0]["steps"] == c["n_steps"]
+        assert relerr(f, fo) <= (1e-11 if precision == 0 else 1e-5)
+        n0, n1 = np.sum(g["h"] * f0), np.sum(g["h"] * f)
+        e0, e1 = np.sum(g["h"] * g["E"] * f0), np.sum(g["h"] * g["E"] * f)
+        assert abs(n1 / n0 - 1) < 1e-7 and abs(e1 / e0 - 1) < 1e-7
+
+
+def test_adaptive_solve_with_sources_matches_oracle(ctx, kx):
+    N = 40
+    q = ki.log_grid(N, 1e-3, 10.0)
+    f0 = ki.bimodal(np.random.default_rng(22), q)
+    src = ki.two_sources(q)
+    W = oracle.kernel_tensor(q)
+    par = dict(t_end=1e4, h0=1e-3, rtol=1e-6, atol=1e-12 * f0.max(), l1_tol=1e-3, check_every=5)
+    fo, ro = oracle.solve(q, W, f0, oracle.M2_from_sigma(1.0, 3.0), sources=src, **par)
+    assert ro["converged"] == 1
+    k = ctx.build_kernel(q, precision=kx.FP64)
+    fd = dev(f0[None])
+    res = ctx.solve(k, fd, 3.0, sources=src, **par)[0]
+    assert res["converged"] == 1 and res["status"] == 0
+    assert res["steps"] == ro["steps"] and res["rejects"] == ro["rejects"]
+    # the controller's err = |f_c - f_p| / (rtol |f|) is a difference of nearly
+    # equal states: a 1e-16 rounding difference becomes ~1e-16/rtol = 1e-10 in err
+    # and h, accumulating over the steps in t (not in f, which depends smoothly on h)
+    assert abs(res["t"] / ro["t"] - 1) < 1e-9
+    assert relerr(fd.cpu().numpy()[0], fo) <= 1e-10
+    assert abs(res["l1_to_mb"] - ro["l1"]) < 1e-10
+    # FP32 path: same physics within the mixed tolerances; moments exactly tracked
+    k32 = ctx.build_kernel(q, precision=kx.FP32)
+    fd32 = dev(f0[None])
+    r32 = ctx.solve(k32, fd32, 3.0, sources=src, **par)[0]
+    assert r32["converged"] == 1
+    g = oracle.grid(q)
+    f32 = fd32.cpu().numpy()[0]
+    # different step sequences integrate the decaying sources with different
+    # trapezoid errors (~1e-7 here), so only closeness is asserted; exact moment
+    # bookkeeping is tested where the quadrature is exact (next test)
+    assert np.sum(g["h"] * np.abs(f32 - fo)) / np.sum(g["h"] * fo) < 5e-3
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_moments_conserved_through_integration(ctx, kx, precision):
+    """Number and energy after an integration: without sources they stay at
+    their initial values; with a constant-rate source (trapezoid exact) they
+    grow by R t and R <E>_s t.  Tolerance 1e-7 (mixed path) / 1e-12 (FP64)."""
+    N = 48
+    q = ki.log_grid(N, 1e-3, 10.0)
+    g = oracle.grid(q)
+    f0 = ki.bimodal(np.random.default_rng(25), q)
+    k = ctx.build_kernel(q, precision=precision)
+    tol = 1e-12 if precision == 0 else 1e-7
+    fd = dev(f0[None])
+    r = ctx.solve(k, fd, 2.0, t_end=20.0, h0=1e-3, rtol=1e-6, atol=1e-12)[0]
+    f = fd.cpu().numpy()[0]
+    assert r["status"] == 0 and r["t"] == 20.0
+    for w in (g["h"], g["h"] * g["E"]):
+        assert abs(np.sum(w * f) / np.sum(w * f0) - 1) < tol
+    shape = ki.lognormal_bumps(q, (1.0,), (0.3,), (1.0,))
+    src = dict(shape=shape[None], rate=np.array([0.02]), tau=np.array([1e300]), t_on=np.array([0.0]))
+    fd = dev(f0[None])
+    r = ctx.solve(k, fd, 2.0, sources=src, t_end=10.0, h0=1e-3, rtol=1e-6, atol=1e-12)[0]
+    f = fd.cpu().numpy()[0]
+    e_s = np.sum(g["h"] * g["E"] * shape) / np.sum(g["h"] * shape)
+    assert abs(np.sum(g["h"] * f) / (np.sum(g["h"] * f0) + 0.02 * 10.0) - 1) < tol
+    assert abs(np.sum(g["h"] * g["E"] * f) / (np.sum(g["h"] * g["E"] * f0) + 0.02 * e_s * 10.0) - 1) < tol
+
+
+def test_solve_batch_of_sigmas_matches_individual(ctx, kx):
+    """Several sigmas integrated together give bit-identical results to each
+    sigma alone (no cross-instance coupling)."""
+    N = 32
+    q = ki.log_grid(N, 1e-3, 10.0)
+    f0 = ki.bimodal(np.random.default_rng(23), q)
+    sig = np.array([0.5, 1.0, 4.0])
+    par = dict(t_end=50.0, h0=1e-3, rtol=1e-6, atol=1e-12, l1_tol=1e-3, check_every=5)
+    for precision in (0, 1):
+        k = ctx.build_kernel(q, precision=precision)
+        fb = dev(np.tile(f0, (3, 1)))
+        rb = ctx.solve(k, fb, sig, **par)
+        for b in range(3):
+            fa = dev(f0[None])
+            ra = ctx.solve(k, fa, sig[b], **par)[0]
+            np.testing.assert_array_equal(fa.cpu().numpy()[0], fb.cpu().numpy()[b])
+            assert ra["steps"] == rb[b]["steps"]
+        fh, rh = ctx.solve_host(k, np.tile(f0, (3, 1)), sig, **par)
+        np.testing.assert_array_equal(fh, fb.cpu().numpy())
+
+
+def test_mb_fit_matches_oracle(ctx, kx):
+    N = 64
+    q = ki.log_grid(N, 1e-3, 10.0)
+    g = oracle.grid(q)
+    k = ctx.build_kernel(q, precision=kx.FP64)
+    fs = [0.3 * np.exp(-g["E"] / 0.7), ki.bimodal(np.random.default_rng(24), q)]
+    out = ctx.mb_fit(k, dev(np.array(fs)))
+    for b, f in enumerate(fs):
+        r = oracle.mb_fit(g["E"], g["h"], f)
+        assert abs(out[b, 0] / r["T"] - 1) < 1e-12
+        assert abs(out[b, 1] - r["ln_z"]) < 1e-10
+        assert abs(out[b, 2] - r["l1"]) < 1e-10 * max(1.0, r["l1"])
