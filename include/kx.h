@@ -174,6 +174,25 @@ int kx_collision(kx_ctx *ctx, const kx_kernel *k, int batch, const double *sigma
 int kx_collision_host(kx_ctx *ctx, const kx_kernel *k, int batch, const double *sigma_host,
                       const double *f_host, double *C_host, int project, kx_diag *diag_host);
 
+/* Allocation-free variant of kx_collision (no counterpart in the paper; it
+ * exists for callers that must not allocate GPU memory during the call, such
+ * as code running inside an allocator or memory-pool callback, or a host that
+ * reserved all device memory up front).  Same inputs, outputs and arithmetic as
+ * kx_collision without diagnostics: f_dev, C_dev are the caller's device
+ * arrays [batch][n].  Instead of the context arena it uses one scratch array
+ * of 8 MiB compiled into the library (one copy per GPU that loads it, resident
+ * until the process exits); it calls no cudaMalloc/cudaFree and no allocating
+ * library routine.  Limits: batch <= 64 and the call's scratch (per instance:
+ * the partial row sums and prepared tables) <= 8 MiB, e.g. 64 instances at
+ * n = 128 or 28 at n = 512 on the FP32 path; larger requests return KX_EINVAL
+ * with a message in kx_last_error.  The first call on a device looks up the
+ * array's device address (cudaGetSymbolAddress); make that first call outside
+ * any stream capture.  All calls share the one array: calls whose work can
+ * overlap on the GPU (other streams, other contexts on the same device) race
+ * and must be serialised by the caller.  Only enqueues work on the stream. */
+int kx_collision_noalloc(kx_ctx *ctx, const kx_kernel *k, int batch, const double *sigma_host,
+                         const double *f_dev, double *C_dev, int project);
+
 /* ---------------------------------------------------------- integration */
 /* One Heun attempt per instance (Sec. 4.2): k1 = RHS(f, t), f_p = f + h k1,
  * k2 = RHS(f_p, t + h), f_c = f + h/2 (k1 + k2); accept/reject and the next h

@@ -26,6 +26,7 @@ EXPORTS = (
     "kx_build_kernel", "kx_kernel_retain", "kx_kernel_release", "kx_kernel_get_info",
     "kx_kernel_grid", "kx_kernel_row", "kx_collision", "kx_collision_host", "kx_step",
     "kx_solve", "kx_solve_host", "kx_mb_fit", "kx_launch_count", "kx_time_contraction",
+    "kx_collision_noalloc",
 )
 
 
@@ -107,6 +108,7 @@ def load_library(path: str = LIB_PATH):
         "kx_mb_fit": (i, [vp, vp, i, vp, vp]),
         "kx_launch_count": (ctypes.c_longlong, [vp]),
         "kx_time_contraction": (i, [vp, vp, i, vp, i, ctypes.c_longlong, vp]),
+        "kx_collision_noalloc": (i, [vp, vp, i, vp, vp, vp, i]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
