@@ -142,6 +142,32 @@ def run_reference(args, rank):
     return 0
 
 
+def run_contraction_only(args):
+    """Contraction kernel alone on an n-point grid (q in [1e-3, 1e2]) for
+    `batch` seeded bimodal distributions; cold L2 before every launch."""
+    import torch
+    import paper_2607_00755_b300 as kx
+    ctx = kx.Context(0)
+    q = ki.log_grid(args.n, 1e-3, 1e2)
+    prec = kx.FP32 if args.precision == "fp32" else kx.FP64
+    k = ctx.build_kernel(q, precision=prec)
+    f = torch.as_tensor(ki.batch_bimodal(np.random.default_rng(7), q, args.batch), device="cuda")
+    ms = ctx.time_contraction(k, f, iters=args.iters, flush_bytes=L2_FLUSH_BYTES)
+    n = args.n
+    U = n * n * (n + 1) // 2
+    V = sum((n - a + 3) // 4 for a in range(n))
+    alg = (8 * U + 4 * V) if prec == kx.FP32 else 18 * U + 4 * U // n
+    hbm, src = peaks()
+    print(json.dumps({"kernel": "contraction", "n": n, "batch": args.batch,
+                      "precision": args.precision, "avg_ms": ms,
+                      "algorithmic_bytes": alg, "achieved_gbs": alg / (ms * 1e-3) / 1e9,
+                      "frac_of_" + src + "_hbm": alg / (ms * 1e-3) / 1e9 / hbm,
+                      "info": k.info()}), flush=True)
+    k.release()
+    ctx.close()
+    return 0
+
+
 def config_desc(c, B):
     return {"workload": "single instance N=128 full integration: kernel build + adaptive Heun "
                         "solve with two freeze-in sources for sigma in {0.1,1,10,100} "
@@ -159,12 +185,20 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--fp64-steps", type=int, default=1)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--only", default="", choices=["", "contraction"],
+                    help="micro-benchmark: time the contraction kernel alone (for profiling)")
+    ap.add_argument("--n", type=int, default=384)
+    ap.add_argument("--batch", type=int, default=1)
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
+    ap.add_argument("--iters", type=int, default=20)
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     if args.impl == "reference":
         return run_reference(args, rank)
+    if args.only == "contraction":
+        return run_contraction_only(args)
 
     import torch
     import paper_2607_00755_b300 as kx
@@ -270,7 +304,7 @@ def main():
     achieved = alg_bytes / (ms_cold * 1e-3) / 1e9
     roof = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
             "frac": achieved / hbm, "traffic": None,
-            "kernel": "k_contract32<4> (N=128, 4 instances per pass)",
+            "kernel": "k_stream32<4,2> (N=128, 4 instances per pass)",
             "algorithmic_bytes_per_launch": alg_bytes, "avg_launch_ms_cold_l2": ms_cold,
             "avg_launch_ms_warm_l2": ms_warm, "peak_source": src_peak}
     # streaming single-instance roofline at N=384 (tables 227 MB > L2)
@@ -284,7 +318,7 @@ def main():
     b384 = 8 * U384 + 4 * V384
     roof384 = {"bound": "hbm", "achieved": b384 / (ms384 * 1e-3) / 1e9, "peak": hbm,
                "unit": "GB/s", "frac": b384 / (ms384 * 1e-3) / 1e9 / hbm, "traffic": None,
-               "kernel": "k_contract32<1> (N=384, single instance, cold L2)",
+               "kernel": "k_stream32<1,4> (N=384, single instance, cold L2)",
                "algorithmic_bytes_per_launch": b384, "avg_launch_ms": ms384,
                "evals_per_s": 1e3 / ms384}
 

@@ -57,6 +57,7 @@ extern "C" int kx_create(kx_ctx **out, int device, void *cuda_stream) {
     c->h_pinned = nullptr;
     c->pinned_bytes = 0;
     c->launches = 0;
+    kx_contract_prepare();
     *out = c;
     return KX_OK;
 }

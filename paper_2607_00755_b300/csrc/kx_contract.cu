@@ -47,26 +47,37 @@ __device__ __forceinline__ void kx_block_sum(double (&v)[K], double *smem) {
     __syncthreads();
 }
 
+// Block maximum of non-negative doubles.  For x >= 0 the IEEE bit patterns
+// order like the values, so the reduction runs on 64-bit integers (integer
+// pipe) instead of the FP64 pipe.
 __device__ __forceinline__ double kx_block_max(double v, double *smem) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    for (int off = 16; off; off >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, off));
-    if (lane == 0) smem[warp] = v;
+    unsigned long long x = (unsigned long long)__double_as_longlong(v);
+    for (int off = 16; off; off >>= 1) {
+        unsigned long long y = __shfl_xor_sync(0xffffffffu, x, off);
+        x = y > x ? y : x;
+    }
+    unsigned long long *us = reinterpret_cast<unsigned long long *>(smem);
+    if (lane == 0) us[warp] = x;
     __syncthreads();
     if (warp == 0) {
-        double x = lane < nw ? smem[lane] : 0.0;
-        for (int off = 16; off; off >>= 1) x = fmax(x, __shfl_xor_sync(0xffffffffu, x, off));
-        if (lane == 0) smem[0] = x;
+        unsigned long long z = lane < nw ? us[lane] : 0ull;
+        for (int off = 16; off; off >>= 1) {
+            unsigned long long y = __shfl_xor_sync(0xffffffffu, z, off);
+            z = y > z ? y : z;
+        }
+        if (lane == 0) us[0] = z;
     }
     __syncthreads();
-    double r = smem[0];
+    double r = __longlong_as_double((long long)us[0]);
     __syncthreads();
     return r;
 }
 
-__device__ __forceinline__ int kx_block_or(int v, double *smem) {
-    double r = kx_block_max((double)v, smem);
-    return r > 0.0;
-}
+__device__ __forceinline__ int kx_block_or(int v, double *) { return __syncthreads_or(v) != 0; }
+
+// Threads per instance block: the grid points rounded up to whole warps.
+static inline int kx_fin_threads(int n) { return ((n + 31) / 32) * 32; }
 
 // ------------------------------------------------------------------- prep
 // Per instance (block b, thread = grid point): f_max = max |f|, and either
@@ -95,7 +106,7 @@ __device__ int kx_prep_block(int n, int path, const double *__restrict__ fb,
         if (i < n) lf64[i] = log(x > KX_LOG_FLOOR ? x : KX_LOG_FLOOR);
         return bad;
     }
-    double *dl = smem + 64 + 32;  // deltas, n <= 512 doubles after the reduction scratch
+    double *dl = smem + 64 + 32;           // deltas, n <= 512 doubles after the reduction scratch
     const double Ei = i < n ? E[i] : 0.0;
     double l2 = -2000.0;
     if (i < n && fm > 0.0) l2 = log2(x > KX_LOG_FLOOR ? x : KX_LOG_FLOOR) - log2(fm);
@@ -123,7 +134,7 @@ __device__ int kx_prep_block(int n, int path, const double *__restrict__ fb,
 __global__ void __launch_bounds__(KX_FIN_THREADS)
     k_prep(int n, int path, const double *__restrict__ f, const double *__restrict__ E,
            const double *__restrict__ h, kx_batch_views v, const kx_inst_state *__restrict__ st) {
-    __shared__ double smem[64 + 32 + KX_MAX_N];
+    __shared__ double smem[64 + 32 + 2 * KX_MAX_N];
     const int b = blockIdx.x;
     if (st && st[b].done) return;
     int bad = kx_prep_block(n, path, f + (long long)b * n, E, h, v.fmax + b,
@@ -135,7 +146,7 @@ __global__ void __launch_bounds__(KX_FIN_THREADS)
 cudaError_t kx_launch_prep(const kx_kernel *k, int B, const double *f, const kx_batch_views &v,
                            const kx_inst_state *st, cudaStream_t s) {
     int path = k->precision == KX_FP64 ? KX_FP64 : KX_FP32;
-    k_prep<<<B, KX_FIN_THREADS, 0, s>>>(k->n, path, f, k->d_E, k->d_h, v, st);
+    k_prep<<<B, kx_fin_threads(k->n), 0, s>>>(k->n, path, f, k->d_E, k->d_h, v, st);
     return cudaGetLastError();
 }
 
@@ -205,7 +216,7 @@ __device__ __forceinline__ float kx_unpack_omega(uint32_t w) {
 }
 
 // 2^d - 1 for |d| < 1/4: Taylor series of expm1(x), x = d ln 2, through x^6
-// (truncation below 1e-9 relative); exact 0 at d = 0.
+// (truncation below 1e-9 relative); exactly 0 at d = 0.
 __device__ __forceinline__ float kx_exp2m1_small(float d) {
     const float c1 = 0.69314718056f, c2 = 0.24022650695f, c3 = 0.05550410866f;
     const float c4 = 0.00961812911f, c5 = 0.00133335581f, c6 = 0.00015403530f;
@@ -224,21 +235,25 @@ __device__ __forceinline__ float kx_exp2m1_small(float d) {
 //   else as 2^a - 2^(a + d) (no cancellation, no 0 * inf).
 __device__ __forceinline__ float kx_bracket_term(float a, float d) {
     const float ea = kx_ex2(a);
-    const float near = -ea * kx_exp2m1_small(d);
-    const float far = ea - kx_ex2(a + d);
-    return fabsf(d) < 0.25f ? near : far;
+    const float nearv = -ea * kx_exp2m1_small(d);
+    const float farv = ea - kx_ex2(a + d);
+    return fabsf(d) < 0.25f ? nearv : farv;
 }
 
-template <int BP>
+// Persistent streaming contraction.  The work unit is one warp-sized slice of
+// a row: 32 x VPL consecutive 4-element vectors of row i.  Warps take units in
+// a fixed round-robin order, prefetch the next unit's tables into registers
+// while computing the current one, and reduce each unit inside the warp
+// (FP64 shuffles, no block barrier); the unit's sum is one partial of its row.
+template <int BP, int VPL>
 __global__ void __launch_bounds__(KX_T32)
-    k_contract32(int n, int V, int chunks, int B, const uint32_t *__restrict__ vt,
-                 const float4 *__restrict__ W, const uint4 *__restrict__ PK,
-                 const float2 *__restrict__ tl, const float2 *__restrict__ td,
-                 double2 *__restrict__ partial, const kx_inst_state *__restrict__ st, int stage) {
-    const int c = blockIdx.x, i = blockIdx.y, b0 = blockIdx.z * BP;
+    k_stream32(int n, int V, int upr, int B, const uint32_t *__restrict__ vt,
+               const float4 *__restrict__ W, const uint4 *__restrict__ PK,
+               const float2 *__restrict__ tl, const float2 *__restrict__ td,
+               double2 *__restrict__ partial, const kx_inst_state *__restrict__ st, int stage) {
+    const int b0 = blockIdx.y * BP;
     __shared__ float2 s_l[BP][KX_MAX_N + 4];   // (l2_j, delta_j)
     __shared__ float2 s_d[BP][KX_MAX_N];       // (delta_j, delta_{j+1} - delta_j)
-    __shared__ double red[BP * 32];
     bool act[BP];
     bool any = false;
 #pragma unroll
@@ -258,65 +273,140 @@ __global__ void __launch_bounds__(KX_T32)
     }
     __syncthreads();
 
-    float acc[BP], di[BP];
+    const int lane = threadIdx.x & 31;
+    const int wpb = blockDim.x >> 5;
+    const int total = n * upr;
+    const int stride = gridDim.x * wpb;
+    int u = blockIdx.x * wpb + (threadIdx.x >> 5);
+    float4 w[VPL];
+    uint4 pk[VPL];
+    uint32_t nv[VPL];
+    auto load_unit = [&](int uu) {
+        const int i = uu / upr, c = uu - i * upr;
+        const float4 *Wr = W + (long long)i * V;
+        const uint4 *Pr = PK + (long long)i * V;
 #pragma unroll
-    for (int bb = 0; bb < BP; ++bb) {
-        acc[bb] = 0.f;
-        di[bb] = s_l[bb][i].y;
-    }
-    const float4 *Wr = W + (long long)i * V;
-    const uint4 *Pr = PK + (long long)i * V;
-    const int v0 = c * KX_CHV32 + threadIdx.x;
-    float4 w[KX_VPT32];
-    uint4 pk[KX_VPT32];
-    uint32_t nv[KX_VPT32];
-#pragma unroll
-    for (int e = 0; e < KX_VPT32; ++e) {
-        int v = v0 + e * KX_T32;
-        if (v < V) {
-            w[e] = kx_ld_stream(Wr + v);
-            pk[e] = kx_ld_stream(Pr + v);
-            nv[e] = __ldg(vt + v);
-        } else {
-            w[e] = make_float4(0.f, 0.f, 0.f, 0.f);
-            pk[e] = make_uint4(0u, 0u, 0u, 0u);
-            nv[e] = 0u;
-        }
-    }
-#pragma unroll
-    for (int e = 0; e < KX_VPT32; ++e) {
-        const int nn = nv[e] & 0xffff, m0 = nv[e] >> 16;
-        const float wk[4] = {w[e].x, w[e].y, w[e].z, w[e].w};
-        const uint32_t pw[4] = {pk[e].x, pk[e].y, pk[e].z, pk[e].w};
-#pragma unroll
-        for (int bb = 0; bb < BP; ++bb) {
-            const float2 ln = s_l[bb][nn];
-            const float dn_i = di[bb];
-#pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                const float2 lm = s_l[bb][m0 + q];
-                const float2 dj = s_d[bb][pw[q] >> 23];
-                const float a = ln.x + lm.x;
-                const float d = (dn_i + fmaf(kx_unpack_omega(pw[q]), dj.y, dj.x)) - (ln.y + lm.y);
-                acc[bb] = fmaf(wk[q], kx_bracket_term(a, d), acc[bb]);
+        for (int e = 0; e < VPL; ++e) {
+            const int v = c * (32 * VPL) + e * 32 + lane;
+            if (v < V) {
+                w[e] = kx_ld_stream(Wr + v);
+                pk[e] = kx_ld_stream(Pr + v);
+                nv[e] = __ldg(vt + v);
+            } else {
+                w[e] = make_float4(0.f, 0.f, 0.f, 0.f);
+                pk[e] = make_uint4(0u, 0u, 0u, 0u);
+                nv[e] = 0u;
             }
         }
-    }
-    double vals[BP];
+    };
+    if (u < total) load_unit(u);
+    while (u < total) {
+        float4 wc[VPL];
+        uint4 pc[VPL];
+        uint32_t nc[VPL];
 #pragma unroll
-    for (int bb = 0; bb < BP; ++bb) vals[bb] = acc[bb];
-    kx_block_sum<BP>(vals, red);
-    if (threadIdx.x == 0) {
+        for (int e = 0; e < VPL; ++e) {
+            wc[e] = w[e];
+            pc[e] = pk[e];
+            nc[e] = nv[e];
+        }
+        const int un = u + stride;
+        if (un < total) load_unit(un);
+        const int i = u / upr, c = u - i * upr;
+        float acc[BP], di[BP];
 #pragma unroll
-        for (int bb = 0; bb < BP; ++bb)
-            if (act[bb])
-                partial[((long long)(b0 + bb) * n + i) * chunks + c] = make_double2(vals[bb], 0.0);
+        for (int bb = 0; bb < BP; ++bb) {
+            acc[bb] = 0.f;
+            di[bb] = s_l[bb][i].y;
+        }
+#pragma unroll
+        for (int e = 0; e < VPL; ++e) {
+            const int nn = nc[e] & 0xffff, m0 = nc[e] >> 16;
+            const float wk[4] = {wc[e].x, wc[e].y, wc[e].z, wc[e].w};
+            const uint32_t pw[4] = {pc[e].x, pc[e].y, pc[e].z, pc[e].w};
+#pragma unroll
+            for (int bb = 0; bb < BP; ++bb) {
+                const float2 ln = s_l[bb][nn];
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const float2 lm = s_l[bb][m0 + q];
+                    const float2 dj = s_d[bb][pw[q] >> 23];
+                    const float a = ln.x + lm.x;
+                    const float d =
+                        (di[bb] + fmaf(kx_unpack_omega(pw[q]), dj.y, dj.x)) - (ln.y + lm.y);
+                    acc[bb] = fmaf(wk[q], kx_bracket_term(a, d), acc[bb]);
+                }
+            }
+        }
+#pragma unroll
+        for (int bb = 0; bb < BP; ++bb) {
+            double x = acc[bb];
+#pragma unroll
+            for (int off = 16; off; off >>= 1) x += __shfl_xor_sync(0xffffffffu, x, off);
+            if (lane == 0 && act[bb])
+                partial[((long long)(b0 + bb) * n + i) * upr + c] = make_double2(x, 0.0);
+        }
+        u = un;
     }
 }
 
+// Vectors per lane of a streaming unit: short rows use smaller units so that
+// every SM gets work.
+static int kx_stream_vpl(int n) { return n <= 160 ? 2 : 4; }
+
 int kx_chunks_per_row(const kx_kernel *k) {
     if (k->precision == KX_FP64) return (int)((k->P + KX_CH64 - 1) / KX_CH64);
-    return (k->V + KX_CHV32 - 1) / KX_CHV32;
+    const int unit = 32 * kx_stream_vpl(k->n);
+    return (k->V + unit - 1) / unit;
+}
+
+// SM count, queried once (kx_contract_prepare) before any stream capture.
+static int g_sms;
+
+template <int BP, int VPL>
+static void kx_stream_attr() {
+    int occ = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_stream32<BP, VPL>, KX_T32, 0);
+}
+
+void kx_contract_prepare() {
+    if (g_sms) return;
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    kx_stream_attr<1, 2>();
+    kx_stream_attr<1, 4>();
+    kx_stream_attr<2, 2>();
+    kx_stream_attr<2, 4>();
+    kx_stream_attr<4, 2>();
+    kx_stream_attr<4, 4>();
+    cudaGetLastError();
+    g_sms = sms > 0 ? sms : 1;
+}
+
+template <int BP, int VPL>
+static cudaError_t kx_launch_stream(const kx_kernel *k, int B, const kx_batch_views &v,
+                                    const kx_inst_state *st, int stage, cudaStream_t s) {
+    int occ = 0;
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_stream32<BP, VPL>,
+                                                                  KX_T32, 0);
+    if (e != cudaSuccess) return e;
+    if (occ < 1) occ = 1;
+    const int sms = g_sms > 0 ? g_sms : 148;
+    const int upr = v.chunks;
+    const int total = k->n * upr;
+    const int wpb = KX_T32 / 32;
+    const int groups = (B + BP - 1) / BP;
+    int blocks = (total + wpb - 1) / wpb;
+    int cap = (occ * sms + groups - 1) / groups;
+    if (cap < sms) cap = sms;
+    if (blocks > cap) blocks = cap;
+    dim3 grid(blocks, groups);
+    const float4 *W = reinterpret_cast<const float4 *>(k->d_W32);
+    const uint4 *PK = reinterpret_cast<const uint4 *>(k->d_pk);
+    k_stream32<BP, VPL><<<grid, KX_T32, 0, s>>>(k->n, k->V, upr, B, k->d_vt, W, PK, v.tl, v.td,
+                                                v.partial, st, stage);
+    return cudaGetLastError();
 }
 
 cudaError_t kx_launch_contract(const kx_kernel *k, int B, const double *f, const kx_batch_views &v,
@@ -328,22 +418,13 @@ cudaError_t kx_launch_contract(const kx_kernel *k, int B, const double *f, const
                                              k->d_jl, f, v.lf64, v.partial, st, stage);
         return cudaGetLastError();
     }
-    const float4 *W = reinterpret_cast<const float4 *>(k->d_W32);
-    const uint4 *PK = reinterpret_cast<const uint4 *>(k->d_pk);
-    if (B >= 4) {
-        dim3 grid(chunks, n, (B + 3) / 4);
-        k_contract32<4><<<grid, KX_T32, 0, s>>>(n, k->V, chunks, B, k->d_vt, W, PK, v.tl, v.td,
-                                                v.partial, st, stage);
-    } else if (B == 2 || B == 3) {
-        dim3 grid(chunks, n, (B + 1) / 2);
-        k_contract32<2><<<grid, KX_T32, 0, s>>>(n, k->V, chunks, B, k->d_vt, W, PK, v.tl, v.td,
-                                                v.partial, st, stage);
-    } else {
-        dim3 grid(chunks, n, B);
-        k_contract32<1><<<grid, KX_T32, 0, s>>>(n, k->V, chunks, B, k->d_vt, W, PK, v.tl, v.td,
-                                                v.partial, st, stage);
-    }
-    return cudaGetLastError();
+    const bool small = kx_stream_vpl(n) == 2;
+    if (B >= 4) return small ? kx_launch_stream<4, 2>(k, B, v, st, stage, s)
+                             : kx_launch_stream<4, 4>(k, B, v, st, stage, s);
+    if (B >= 2) return small ? kx_launch_stream<2, 2>(k, B, v, st, stage, s)
+                             : kx_launch_stream<2, 4>(k, B, v, st, stage, s);
+    return small ? kx_launch_stream<1, 2>(k, B, v, st, stage, s)
+                 : kx_launch_stream<1, 4>(k, B, v, st, stage, s);
 }
 
 // ---------------------------------------------------- row combine + projection
@@ -444,7 +525,7 @@ __global__ void __launch_bounds__(KX_FIN_THREADS)
 cudaError_t kx_launch_finalize(const kx_kernel *k, int B, const double *f, const kx_batch_views &v,
                                double *C_out, int project, int want_diag, cudaStream_t s) {
     int path = k->precision == KX_FP64 ? KX_FP64 : KX_FP32;
-    k_finalize<<<B, KX_FIN_THREADS, 0, s>>>(k->n, v.chunks, path, f, k->d_E, k->d_h, v, C_out,
+    k_finalize<<<B, kx_fin_threads(k->n), 0, s>>>(k->n, v.chunks, path, f, k->d_E, k->d_h, v, C_out,
                                             project, want_diag);
     return cudaGetLastError();
 }
@@ -519,23 +600,13 @@ __global__ void __launch_bounds__(KX_FIN_THREADS)
 
 cudaError_t kx_launch_mbfit(const kx_kernel *k, int B, const double *f, double *out3,
                             cudaStream_t s) {
-    k_mbfit<<<B, KX_FIN_THREADS, 0, s>>>(k->n, f, k->d_E, k->d_h, out3);
+    k_mbfit<<<B, kx_fin_threads(k->n), 0, s>>>(k->n, f, k->d_E, k->d_h, out3);
     return cudaGetLastError();
 }
 
 // ------------------------------------------------------------ Heun stages
 // Source S_i(t) = sum_k rate_k env_k(t) shape_k,i (shapes pre-normalised so
 // that sum_i h_i shape_k,i = 1), env_k = exp(-(t - t_on)/tau) for t >= t_on.
-__device__ __forceinline__ double kx_source_at(const kx_src_dev &src, const double *shapes, int n,
-                                               int i, double t) {
-    double S = 0.0;
-    for (int k = 0; k < src.n_src; ++k) {
-        if (t < src.t_on[k]) continue;
-        double env = exp(-(t - src.t_on[k]) / src.tau[k]);
-        S += src.rate[k] * env * shapes[src.shape_off + (long long)k * n + i];
-    }
-    return S;
-}
 
 // stage 1: k1 = C_proj[f] + S(t); f_p = f + h k1 (Euler predictor), prep(f_p).
 // stage 2: k2 = C_proj[f_p] + S(t + h); f_c = f + h/2 (k1 + k2) (trapezoid
@@ -545,7 +616,7 @@ __global__ void __launch_bounds__(KX_FIN_THREADS)
     k_stage(int n, int chunks, int path, const double *__restrict__ E,
             const double *__restrict__ h, kx_batch_views v, kx_step_views sv, int stage,
             long long max_attempts) {
-    __shared__ double smem[64 + 32 + KX_MAX_N];
+    __shared__ double smem[64 + 32 + 2 * KX_MAX_N];
     const int b = blockIdx.x, i = threadIdx.x;
     kx_inst_state *st = sv.st + b;
     if (st->done) return;
@@ -584,7 +655,18 @@ __global__ void __launch_bounds__(KX_FIN_THREADS)
     kx_row_out r = kx_combine_project(n, chunks, path, b, fcur, Ei, hi, v, sv.project, smem);
     const double C = sv.project ? r.Cproj : r.Craw;
     const double tS = stage == 1 ? t : t + htry;
-    const double kv = in ? C + kx_source_at(sv.src[b], sv.shapes, n, i, tS) : 0.0;
+    // source envelopes: one exp per source, shared by the block
+    __shared__ double s_env[KX_MAX_SRC];
+    const kx_src_dev &src = sv.src[b];
+    if (threadIdx.x < src.n_src) {
+        const int k = threadIdx.x;
+        s_env[k] = tS >= src.t_on[k] ? src.rate[k] * exp(-(tS - src.t_on[k]) / src.tau[k]) : 0.0;
+    }
+    __syncthreads();
+    double Si = 0.0;
+    if (in)
+        for (int k = 0; k < src.n_src; ++k) Si += s_env[k] * sv.shapes[src.shape_off + (long long)k * n + i];
+    const double kv = in ? C + Si : 0.0;
     const double f0 = in ? fb[i] : 0.0;
     __syncthreads();
     if (stage == 1) {
@@ -726,7 +808,7 @@ __global__ void __launch_bounds__(KX_FIN_THREADS)
 cudaError_t kx_launch_stage(const kx_kernel *k, int B, const kx_batch_views &v,
                             const kx_step_views &sv, int stage, cudaStream_t s) {
     int path = k->precision == KX_FP64 ? KX_FP64 : KX_FP32;
-    k_stage<<<B, KX_FIN_THREADS, 0, s>>>(k->n, v.chunks, path, k->d_E, k->d_h, v, sv, stage,
+    k_stage<<<B, kx_fin_threads(k->n), 0, s>>>(k->n, v.chunks, path, k->d_E, k->d_h, v, sv, stage,
                                          sv.max_attempts);
     return cudaGetLastError();
 }

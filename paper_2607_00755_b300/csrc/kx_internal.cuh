@@ -21,8 +21,6 @@
 #define KX_EPT64 8            // pairs per thread
 #define KX_CH64 (KX_T64 * KX_EPT64)
 #define KX_T32 256            // threads per FP32 contraction block
-#define KX_VPT32 4            // 4-element vectors per thread
-#define KX_CHV32 (KX_T32 * KX_VPT32)
 #define KX_FIN_THREADS 512    // finalize / stage kernels: one block per instance, thread = grid point
 
 struct kx_gl_nodes {
@@ -113,6 +111,7 @@ struct kx_batch_views {
 };
 
 int kx_chunks_per_row(const kx_kernel *k);
+void kx_contract_prepare();  // one-time launch-shape queries (call outside stream capture)
 size_t kx_views_bytes(const kx_kernel *k, int B);
 void kx_carve_views(const kx_kernel *k, int B, void *base, kx_batch_views *v);
 

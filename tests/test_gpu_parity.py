@@ -113,7 +113,7 @@ def test_build_rejects_bad_grids(ctx, kx):
 
 # ------------------------------------------------------------ collision ----
 @pytest.mark.parametrize("precision", [0, 1])
-@pytest.mark.parametrize("N", [4, 17, 64, 130])
+@pytest.mark.parametrize("N", [4, 17, 64, 130, 200])
 def test_collision_matches_oracle(ctx, kx, precision, N):
     rng = np.random.default_rng(100 + N)
     q = ki.log_grid(N, 1e-3, 10.0 if N < 100 else 1e2)
@@ -203,9 +203,9 @@ def test_collision_edge_cases(ctx, kx, precision):
 
 
 @pytest.mark.parametrize("precision", [0, 1])
-def test_batch_is_bitwise_independent_of_co_scheduling(ctx, kx, precision):
+@pytest.mark.parametrize("N", [48, 200])
+def test_batch_is_bitwise_independent_of_co_scheduling(ctx, kx, precision, N):
     """Each instance's C is bit-identical alone and inside a batch."""
-    N = 48
     q = ki.log_grid(N, 1e-3, 10.0)
     f = ki.batch_bimodal(np.random.default_rng(9), q, 6)
     sig = np.array([1.0, 2.0, 0.5, 3.0, 1.5, 0.1])
