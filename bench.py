@@ -149,7 +149,7 @@ def run_contraction_only(args):
     import paper_2607_00755_b300 as kx
     ctx = kx.Context(0)
     q = ki.log_grid(args.n, 1e-3, 1e2)
-    prec = kx.FP32 if args.precision == "fp32" else kx.FP64
+    prec = {"fp32": kx.FP32, "fp64": kx.FP64, "split": kx.SPLIT_TF32}[args.precision]
     k = ctx.build_kernel(q, precision=prec)
     f = torch.as_tensor(ki.batch_bimodal(np.random.default_rng(7), q, args.batch), device="cuda")
     ms = ctx.time_contraction(k, f, iters=args.iters, flush_bytes=L2_FLUSH_BYTES)
@@ -166,6 +166,48 @@ def run_contraction_only(args):
     k.release()
     ctx.close()
     return 0
+
+
+def measure_batched(ctx, kx, torch, flush, iters=5, oracle_sample=4):
+    """Batched configuration: B = 512 seeded bimodal distributions sharing one
+    N = 192 kernel (q in [1e-3, 1e2]); projected C per instance through
+    kx_collision, split-TF32 tensor-core path vs the plain FP64 path on the same
+    inputs; max relative error of a sample of instances vs the FP64 oracle."""
+    c = ki.config3()
+    q, f, B = c["q"], c["f"], c["f"].shape[0]
+    stream = torch.cuda.current_stream()
+    fd = torch.as_tensor(f, device="cuda")
+    out = {}
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    Cs = {}
+    for name, prec, reps in (("split_tf32", kx.SPLIT_TF32, iters), ("fp64", kx.FP64, 2)):
+        k = ctx.build_kernel(q, precision=prec)
+        C, _ = ctx.collision(k, fd, c["sigma"])
+        tot = 0.0
+        for _ in range(reps):
+            flush.zero_()
+            e0.record(stream)
+            C, _ = ctx.collision(k, fd, c["sigma"], out=C)
+            e1.record(stream)
+            e1.synchronize()
+            tot += e0.elapsed_time(e1)
+        Cs[name] = C.cpu().numpy()
+        out[name] = {"evals_per_s": B * reps / (tot / 1e3), "ms_per_batch": tot / reps}
+        k.release()
+    import oracle
+    W = oracle.kernel_tensor(q)
+    g = oracle.grid(q)
+    err = {"split_tf32": 0.0, "fp64": 0.0}
+    for b in range(oracle_sample):
+        Co = oracle.collision_tensor(q, W, f[b]) * oracle.M2_from_sigma(1.0, c["sigma"][b])
+        Co, _ = oracle.project(g["E"], g["h"], f[b], Co)
+        for name in err:
+            err[name] = max(err[name], float(np.max(np.abs(Cs[name][b] - Co)) / np.max(np.abs(Co))))
+    return {"workload": "B=512 distributions sharing one N=192 kernel, q in [1e-3,1e2], "
+                        "projected C (kx_collision)",
+            "split_tf32": out["split_tf32"], "fp64_path": out["fp64"],
+            "speedup_vs_fp64": out["split_tf32"]["evals_per_s"] / out["fp64"]["evals_per_s"],
+            "max_rel_err_vs_oracle": err, "oracle_sample": f"{oracle_sample} instances"}
 
 
 def config_desc(c, B):
@@ -189,7 +231,7 @@ def main():
                     help="micro-benchmark: time the contraction kernel alone (for profiling)")
     ap.add_argument("--n", type=int, default=384)
     ap.add_argument("--batch", type=int, default=1)
-    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64", "split"])
     ap.add_argument("--iters", type=int, default=20)
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))
@@ -322,6 +364,8 @@ def main():
                "algorithmic_bytes_per_launch": b384, "avg_launch_ms": ms384,
                "evals_per_s": 1e3 / ms384}
 
+    batched = measure_batched(ctx, kx, torch, flush) if rank == 0 else None
+
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         e, t, cores = oracle_sample(c, B, 12.0)
@@ -339,6 +383,7 @@ def main():
                 "speedup_vs_fp64": (value / fp64["value"]) if fp64 else None,
                 "failed_solves": len(bad),
                 "roofline": roof, "roofline_streaming_n384": roof384,
+                "batched_n192_b512": batched,
                 "cpu_baseline": cpu,
                 "e2e": {"value": e2e_evals / e2e_t, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
                         "d2h_bytes_per_step": int(d2h)},

@@ -60,7 +60,9 @@ extern "C" {
 
 #define KX_FP64 0        /* plain FP64 path: FP64 tensor (18 B/element), FP64 contraction */
 #define KX_FP32 1        /* FP32 streaming path: FP32 W + packed (j_L, omega) (8 B/element), FP32 math, FP64 sums */
-#define KX_SPLIT_BF16 2  /* batched path: gain on tcgen05 tensor cores in split BF16, exact FP32 loss */
+#define KX_SPLIT_TF32 2  /* batched path for many f sharing one kernel: gain G = f^T W f with T = W F on the
+                            tcgen05 tensor cores in split TF32 (hi*hi + hi*lo + lo*hi, FP32 accumulation in
+                            tensor memory), exact FP32 loss with one exp2 per element and instance, FP64 combine */
 
 typedef struct kx_ctx kx_ctx;
 typedef struct kx_kernel kx_kernel;
@@ -78,7 +80,7 @@ typedef struct {
     int n_mu;         /* 1 <= n_mu <= 64 */
     int measure;      /* KX_MEASURE_ENERGY | KX_MEASURE_LITERAL */
     int stats;        /* 0 = dilute f3 f4 - f1 f2 (eq. Lambda dilute); +-1 (quantum) -> KX_ENOTSUP */
-    int precision;    /* KX_FP64 | KX_FP32 | KX_SPLIT_BF16 */
+    int precision;    /* KX_FP64 | KX_FP32 | KX_SPLIT_TF32 */
 } kx_grid_desc;
 
 /* Synthetic freeze-in sources: S_i(t) = sum_k rate_k env_k(t) shape_k,i / sum_j h_j shape_k,j,

@@ -19,7 +19,7 @@ OK, PENDING = 0, 1
 EINVAL, ENOMEM, EADMIT, ENEG, ENONFINITE = -1, -2, -3, -4, -5
 ESINGULAR, ENOCONV, ETIMEOUT, ECUDA, ENOTSUP = -6, -7, -8, -9, -10
 MEASURE_ENERGY, MEASURE_LITERAL = 0, 1
-FP64, FP32, SPLIT_BF16 = 0, 1, 2
+FP64, FP32, SPLIT_TF32 = 0, 1, 2
 
 EXPORTS = (
     "kx_create", "kx_destroy", "kx_set_stream", "kx_strerror", "kx_last_error",

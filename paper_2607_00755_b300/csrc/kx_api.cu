@@ -58,6 +58,7 @@ extern "C" int kx_create(kx_ctx **out, int device, void *cuda_stream) {
     c->pinned_bytes = 0;
     c->launches = 0;
     kx_contract_prepare();
+    kx_batch_prepare();
     *out = c;
     return KX_OK;
 }
@@ -121,6 +122,13 @@ size_t kx_views_bytes(const kx_kernel *k, int B) {
     s += kx_align(sizeof(int) * B);                  // flags
     s += kx_align(sizeof(double) * B);               // M2
     s += kx_align(sizeof(kx_diag) * B);              // diag
+    s += kx_align(sizeof(int));                      // err
+    if (k->precision == KX_SPLIT_TF32) {
+        const size_t Bpad = ((B + 63) / 64) * 64;
+        s += kx_align(sizeof(float) * Bpad * k->Kpad * 2);   // bt (hi, lo)
+        s += kx_align(sizeof(float) * Bpad * k->Kpad);       // fT
+        s += kx_align(sizeof(float) * Bpad * k->Mpad);       // T
+    }
     return s;
 }
 
@@ -136,7 +144,16 @@ void kx_carve_views(const kx_kernel *k, int B, void *base, kx_batch_views *v) {
     v->flags = (int *)p; p += kx_align(sizeof(int) * B);
     v->M2 = (double *)p; p += kx_align(sizeof(double) * B);
     v->diag = (kx_diag *)p; p += kx_align(sizeof(kx_diag) * B);
+    v->err = (int *)p; p += kx_align(sizeof(int));
     v->chunks = chunks;
+    v->bt = v->fT = v->T = nullptr;
+    v->Bpad = ((B + 63) / 64) * 64;
+    if (k->precision == KX_SPLIT_TF32) {
+        const size_t Bpad = v->Bpad;
+        v->bt = (float *)p; p += kx_align(sizeof(float) * Bpad * k->Kpad * 2);
+        v->fT = (float *)p; p += kx_align(sizeof(float) * Bpad * k->Kpad);
+        v->T = (float *)p; p += kx_align(sizeof(float) * Bpad * k->Mpad);
+    }
 }
 
 // ----------------------------------------------------------------- kernel
@@ -177,7 +194,8 @@ static void kx_free_kernel(kx_kernel *k) {
     if (!k) return;
     cudaSetDevice(k->device);
     void *ptrs[] = {k->d_p, k->d_E, k->d_dp, k->d_dE, k->d_h, k->d_pair, k->d_W64,
-                    k->d_om64, k->d_jl, k->d_vt, k->d_W32, k->d_pk};
+                    k->d_om64, k->d_jl, k->d_vt, k->d_W32, k->d_pk, k->d_Atile, k->d_lel,
+                    k->d_lrow, k->d_lgrp};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     delete k;
@@ -205,7 +223,7 @@ extern "C" int kx_build_kernel(kx_ctx *ctx, const kx_grid_desc *d, kx_kernel **o
     if (d->measure != KX_MEASURE_ENERGY && d->measure != KX_MEASURE_LITERAL)
         return kx_set_error(ctx, KX_EINVAL, "unknown measure");
     if (d->stats != 0) return kx_set_error(ctx, KX_ENOTSUP, "only dilute statistics are built");
-    if (d->precision != KX_FP64 && d->precision != KX_FP32)
+    if (d->precision != KX_FP64 && d->precision != KX_FP32 && d->precision != KX_SPLIT_TF32)
         return kx_set_error(ctx, KX_ENOTSUP, "precision not available in this build");
     for (int i = 0; i < n; ++i) {
         if (!(d->q[i] > 0) || !isfinite(d->q[i]))
@@ -313,8 +331,15 @@ extern "C" int kx_build_kernel(kx_ctx *ctx, const kx_grid_desc *d, kx_kernel **o
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
 #undef KX_CHK
-    if (k->precision == KX_FP32) {
-        // the FP32 path streams only its own tables
+    if (k->precision == KX_SPLIT_TF32) {
+        int rc2 = kx_batch_build_tables(ctx, k);
+        if (rc2) {
+            kx_free_kernel(k);
+            return rc2;
+        }
+    }
+    if (k->precision != KX_FP64) {
+        // the FP32 and batched paths read only their own tables
         cudaFree(k->d_W64); k->d_W64 = nullptr;
         cudaFree(k->d_om64); k->d_om64 = nullptr;
         cudaFree(k->d_jl); k->d_jl = nullptr;
@@ -397,6 +422,7 @@ static int kx_collision_impl(kx_ctx *ctx, const kx_kernel *k, int B, const doubl
     std::vector<double> M2(B);
     for (int b = 0; b < B; ++b) M2[b] = kx_M2(k->mass, sigma[b]);
     KX_CUDA_TRY(ctx, cudaMemcpyAsync(v.M2, M2.data(), sizeof(double) * B, cudaMemcpyHostToDevice, s));
+    KX_CUDA_TRY(ctx, cudaMemsetAsync(v.err, 0, sizeof(int), s));
     KX_CUDA_TRY(ctx, kx_launch_prep(k, B, f_dev, v, nullptr, s));
     KX_CUDA_TRY(ctx, kx_launch_contract(k, B, f_dev, v, nullptr, 1, s));
     KX_CUDA_TRY(ctx, kx_launch_finalize(k, B, f_dev, v, C_dev, project, diag != nullptr, s));
@@ -567,6 +593,7 @@ static int kx_setup_run(kx_ctx *ctx, const kx_kernel *k, int B, const double *si
     KX_CUDA_TRY(ctx, cudaMemcpyAsync((void *)sv.src, sd.data(), sizeof(kx_src_dev) * B, cudaMemcpyHostToDevice, s));
     KX_CUDA_TRY(ctx, cudaMemcpyAsync((void *)sv.shapes, shapes.data(), sizeof(double) * shapes.size(), cudaMemcpyHostToDevice, s));
     KX_CUDA_TRY(ctx, cudaMemcpyAsync(run->v.M2, M2.data(), sizeof(double) * B, cudaMemcpyHostToDevice, s));
+    KX_CUDA_TRY(ctx, cudaMemsetAsync(run->v.err, 0, sizeof(int), s));
     return KX_OK;
 }
 

@@ -91,21 +91,47 @@ static inline int kx_fin_threads(int n) { return ((n + 31) / 32) * 32; }
 //             difference is formed from the small deltas: near equilibrium the
 //             bracket keeps its relative accuracy.  The scale f_max^2 is put back
 //             in FP64 when the row sums are combined (C is bilinear in f).
+//  split-TF32 (batched) path: td = (l2_j, l2_{j+1} - l2_j) for the exact loss,
+//             f/f_max instance-minor (fT) and as TF32 hi/lo MMA operand tiles (bt)
+//             for the tensor-core gain; zeros in the k padding up to n rounded to 32.
 // Returns the non-finite flag (block-uniform).
 __device__ int kx_prep_block(int n, int path, const double *__restrict__ fb,
                              const double *__restrict__ E, const double *__restrict__ h,
-                             double *fmax_out, double *lf64, float2 *tl, float2 *td,
-                             double *smem) {
+                             const kx_batch_views &v, int b, double *smem) {
     const int i = threadIdx.x;
     double x = i < n ? fb[i] : 0.0;
     int bad = (i < n) && !isfinite(x);
     double fm = kx_block_max(fabs(x), smem);
     bad = kx_block_or(bad, smem);
-    if (threadIdx.x == 0) *fmax_out = fm;
+    if (threadIdx.x == 0) v.fmax[b] = fm;
     if (path == KX_FP64) {
-        if (i < n) lf64[i] = log(x > KX_LOG_FLOOR ? x : KX_LOG_FLOOR);
+        if (i < n) v.lf64[(long long)b * n + i] = log(x > KX_LOG_FLOOR ? x : KX_LOG_FLOOR);
         return bad;
     }
+    if (path == KX_SPLIT_TF32) {
+        double *ll = smem + 64 + 32;
+        double l2 = -2000.0;
+        if (i < n && fm > 0.0) l2 = log2(x > KX_LOG_FLOOR ? x : KX_LOG_FLOOR) - log2(fm);
+        if (i < n) ll[i] = l2;
+        __syncthreads();
+        if (i < n)
+            v.td[(long long)b * n + i] =
+                make_float2((float)l2, i + 1 < n ? (float)(ll[i + 1] - l2) : 0.f);
+        const float fp = (i < n && fm > 0.0) ? (float)(x / fm) : 0.f;
+        if (i < n) v.fT[(size_t)i * v.Bpad + b] = fp;
+        uint32_t hb;
+        asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(hb) : "f"(fp));
+        const float hi = __uint_as_float(hb);
+        const int KB = blockDim.x >> 5;   // blockDim = n rounded up to 32 = padded k extent
+        const size_t t = ((size_t)(b >> 6) * KB + (i >> 5)) * 2;
+        const int off = kx_tile_offset(b & 63, i & 31);
+        v.bt[t * 2048 + off] = hi;
+        v.bt[(t + 1) * 2048 + off] = fp - hi;
+        __syncthreads();
+        return bad;
+    }
+    float2 *tl = v.tl + (long long)b * (n + 4);
+    float2 *td = v.td + (long long)b * n;
     double *dl = smem + 64 + 32;           // deltas, n <= 512 doubles after the reduction scratch
     const double Ei = i < n ? E[i] : 0.0;
     double l2 = -2000.0;
@@ -137,15 +163,13 @@ __global__ void __launch_bounds__(KX_FIN_THREADS)
     __shared__ double smem[64 + 32 + 2 * KX_MAX_N];
     const int b = blockIdx.x;
     if (st && st[b].done) return;
-    int bad = kx_prep_block(n, path, f + (long long)b * n, E, h, v.fmax + b,
-                            v.lf64 + (long long)b * n, v.tl + (long long)b * (n + 4),
-                            v.td + (long long)b * n, smem);
+    int bad = kx_prep_block(n, path, f + (long long)b * n, E, h, v, b, smem);
     if (threadIdx.x == 0) v.flags[b] = bad;
 }
 
 cudaError_t kx_launch_prep(const kx_kernel *k, int B, const double *f, const kx_batch_views &v,
                            const kx_inst_state *st, cudaStream_t s) {
-    int path = k->precision == KX_FP64 ? KX_FP64 : KX_FP32;
+    int path = k->precision;
     k_prep<<<B, kx_fin_threads(k->n), 0, s>>>(k->n, path, f, k->d_E, k->d_h, v, st);
     return cudaGetLastError();
 }
@@ -355,6 +379,7 @@ __global__ void __launch_bounds__(KX_T32)
 static int kx_stream_vpl(int n) { return n <= 160 ? 2 : 4; }
 
 int kx_chunks_per_row(const kx_kernel *k) {
+    if (k->precision == KX_SPLIT_TF32) return 1;
     if (k->precision == KX_FP64) return (int)((k->P + KX_CH64 - 1) / KX_CH64);
     const int unit = 32 * kx_stream_vpl(k->n);
     return (k->V + unit - 1) / unit;
@@ -412,6 +437,7 @@ static cudaError_t kx_launch_stream(const kx_kernel *k, int B, const kx_batch_vi
 cudaError_t kx_launch_contract(const kx_kernel *k, int B, const double *f, const kx_batch_views &v,
                                const kx_inst_state *st, int stage, cudaStream_t s) {
     const int n = k->n, chunks = v.chunks;
+    if (k->precision == KX_SPLIT_TF32) return kx_launch_batch_contract(k, B, v, st, stage, v.err, s);
     if (k->precision == KX_FP64) {
         dim3 grid(chunks, n, B);
         k_contract64<<<grid, KX_T64, 0, s>>>(n, k->P, chunks, k->d_pair, k->d_W64, k->d_om64,
@@ -453,8 +479,10 @@ __device__ kx_row_out kx_combine_project(int n, int chunks, int path, int b, dou
         }
     }
     double Craw;
-    if (path == KX_FP64) Craw = v.M2[b] * (G - fi * L);
-    else Craw = v.M2[b] * (fm * fm * G);  // FP32 path: G holds sum S (f_n f_m - f_i f_t) / f_max^2
+    // FP32 path: G holds sum S (f_n f_m - f_i f_t) / f_max^2; the FP64 and batched
+    // paths hold the gain G and the loss rate L
+    if (path == KX_FP32) Craw = v.M2[b] * (fm * fm * G);
+    else Craw = v.M2[b] * (G - fi * L);
     if (i >= n) Craw = 0.0;
     kx_row_out r;
     r.Craw = Craw;
@@ -524,7 +552,7 @@ __global__ void __launch_bounds__(KX_FIN_THREADS)
 
 cudaError_t kx_launch_finalize(const kx_kernel *k, int B, const double *f, const kx_batch_views &v,
                                double *C_out, int project, int want_diag, cudaStream_t s) {
-    int path = k->precision == KX_FP64 ? KX_FP64 : KX_FP32;
+    int path = k->precision;
     k_finalize<<<B, kx_fin_threads(k->n), 0, s>>>(k->n, v.chunks, path, f, k->d_E, k->d_h, v, C_out,
                                             project, want_diag);
     return cudaGetLastError();
@@ -707,8 +735,7 @@ __global__ void __launch_bounds__(KX_FIN_THREADS)
         }
         if (threadIdx.x == 0) st->evals += 1;
         __syncthreads();
-        int bad2 = kx_prep_block(n, path, fp, E, h, v.fmax + b, v.lf64 + (long long)b * n,
-                                 v.tl + (long long)b * (n + 4), v.td + (long long)b * n, smem);
+        int bad2 = kx_prep_block(n, path, fp, E, h, v, b, smem);
         if (threadIdx.x == 0) v.flags[b] = bad2;
         return;
     }
@@ -800,14 +827,13 @@ __global__ void __launch_bounds__(KX_FIN_THREADS)
         }
     }
     // prepare the next attempt's contraction input (f_new or the restored f)
-    int bad2 = kx_prep_block(n, path, fb, E, h, v.fmax + b, v.lf64 + (long long)b * n,
-                             v.tl + (long long)b * (n + 4), v.td + (long long)b * n, smem);
+    int bad2 = kx_prep_block(n, path, fb, E, h, v, b, smem);
     if (threadIdx.x == 0) v.flags[b] = bad2;
 }
 
 cudaError_t kx_launch_stage(const kx_kernel *k, int B, const kx_batch_views &v,
                             const kx_step_views &sv, int stage, cudaStream_t s) {
-    int path = k->precision == KX_FP64 ? KX_FP64 : KX_FP32;
+    int path = k->precision;
     k_stage<<<B, kx_fin_threads(k->n), 0, s>>>(k->n, v.chunks, path, k->d_E, k->d_h, v, sv, stage,
                                          sv.max_attempts);
     return cudaGetLastError();

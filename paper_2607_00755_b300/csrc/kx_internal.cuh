@@ -47,6 +47,13 @@ struct kx_kernel {
     uint32_t *d_vt;      // [V]: n | m0 << 16 (first m of the vector)
     float *d_W32;
     uint32_t *d_pk;      // j_L << 23 | round(omega 2^23)
+    // batched (split TF32) tables
+    int Mpad;            // n^2 rows (i, n) padded to a multiple of 128
+    int Kpad;            // n columns (m) padded to a multiple of 32
+    float *d_Atile;      // [Mpad/128][Kpad/32][hi, lo][4096]: W_full as TF32 hi/lo in MMA operand tiles
+    uint2 *d_lel;        // per row i: nonzero (S_inm as float bits, j_L << 23 | omega) sorted by j_L
+    int *d_lrow;         // [n + 1] row offsets into d_lel
+    int *d_lgrp;         // [n][n + 1] first element of each bracket group j_L in row i
     long long nnz;
     long long bytes;
     double build_ms;
@@ -108,7 +115,23 @@ struct kx_batch_views {
     double *M2;            // [B] |M|^2 per instance
     kx_diag *diag;         // [B]
     int chunks;
+    // batched (split TF32) path
+    float *bt;             // [Bpad/64][Kpad/32][hi, lo][2048]: f/f_max as TF32 hi/lo MMA operand tiles
+    float *fT;             // [Kpad][Bpad]: f/f_max, instance-minor
+    float *T;              // [Mpad][Bpad]: T = W_full F (tensor-core product)
+    int *err;              // tensor-core stage timeout flag (bounded waits)
+    int Bpad;
 };
+
+// The MMA operand tile layout (K-major, no swizzle, 8-row x 16-byte core
+// matrices): element (row r, k) of a 128-row (A) or 64-row (B) tile with 32
+// TF32 values of k per row sits at float offset
+//   (r / 8) * 256 + (k / 4) * 32 + (r % 8) * 4 + (k % 4),
+// i.e. leading-dimension (k) stride 128 B between core matrices and
+// stride-dimension (row) stride 1024 B between 8-row groups.
+__host__ __device__ __forceinline__ int kx_tile_offset(int r, int k) {
+    return (r >> 3) * 256 + (k >> 2) * 32 + (r & 7) * 4 + (k & 3);
+}
 
 int kx_chunks_per_row(const kx_kernel *k);
 void kx_contract_prepare();  // one-time launch-shape queries (call outside stream capture)
@@ -144,3 +167,9 @@ cudaError_t kx_launch_stage(const kx_kernel *k, int B, const kx_batch_views &v,
                             const kx_step_views &sv, int stage, cudaStream_t s);
 cudaError_t kx_launch_mbfit(const kx_kernel *k, int B, const double *f, double *out3,
                             cudaStream_t s);
+
+// batched split-TF32 path (kx_batch.cu)
+int kx_batch_build_tables(kx_ctx *ctx, kx_kernel *k);   // after the FP64 build
+cudaError_t kx_launch_batch_contract(const kx_kernel *k, int B, const kx_batch_views &v,
+                                     const kx_inst_state *st, int stage, int *d_err, cudaStream_t s);
+void kx_batch_prepare();   // one-time kernel attribute setup (outside stream capture)

@@ -1,0 +1,93 @@
+"""GPU parity of the batched split-TF32 path (tensor-core gain + exact loss)
+against the FP64 oracle.  Tolerance 1e-5 max-norm relative on C (the mixed
+path's bound); instances are bit-identical alone and inside a batch."""
+import numpy as np
+import pytest
+
+import kx_inputs as ki
+import oracle
+
+pytestmark = pytest.mark.gpu
+TOL = 1e-5
+
+
+@pytest.fixture(scope="module")
+def env():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    import paper_2607_00755_b300 as kx
+    from paper_2607_00755_b300 import build
+    build.build()
+    ctx = kx.Context(0)
+    yield kx, ctx, torch
+    ctx.close()
+
+
+def oracle_rows(q, f, sigma, project):
+    g = oracle.grid(q)
+    W = oracle.kernel_tensor(q)
+    out = []
+    for b in range(f.shape[0]):
+        C = oracle.collision_tensor(q, W, f[b]) * oracle.M2_from_sigma(1.0, sigma[b])
+        if project:
+            C, _ = oracle.project(g["E"], g["h"], f[b], C)
+        out.append(C)
+    return np.array(out)
+
+
+@pytest.mark.parametrize("N,B", [(20, 1), (48, 3), (64, 70), (100, 5)])
+def test_batched_collision_matches_oracle(env, N, B):
+    kx, ctx, torch = env
+    rng = np.random.default_rng(300 + N)
+    q = ki.log_grid(N, 1e-3, 1e2)
+    f = ki.batch_bimodal(rng, q, B)
+    sig = rng.uniform(0.3, 3.0, size=B)
+    k = ctx.build_kernel(q, precision=kx.SPLIT_TF32)
+    fd = torch.as_tensor(f, device="cuda")
+    for project in (0, 1):
+        C, d = ctx.collision(k, fd, sig, project=bool(project), diag=True)
+        C = C.cpu().numpy()
+        Co = oracle_rows(q, f, sig, project)
+        for b in range(B):
+            err = np.max(np.abs(C[b] - Co[b])) / np.max(np.abs(Co[b]))
+            assert err <= TOL, (b, err)
+            assert d[b]["status"] == 0
+    k.release()
+
+
+def test_batched_alone_equals_in_batch(env):
+    kx, ctx, torch = env
+    N = 40
+    q = ki.log_grid(N, 1e-3, 1e2)
+    f = ki.batch_bimodal(np.random.default_rng(31), q, 67)
+    sig = np.linspace(0.5, 2.0, 67)
+    k = ctx.build_kernel(q, precision=kx.SPLIT_TF32)
+    Cb, _ = ctx.collision(k, torch.as_tensor(f, device="cuda"), sig)
+    Cb = Cb.cpu().numpy()
+    for b in (0, 5, 63, 64, 66):
+        Ca, _ = ctx.collision(k, torch.as_tensor(f[b:b + 1], device="cuda"), sig[b:b + 1])
+        np.testing.assert_array_equal(Ca.cpu().numpy()[0], Cb[b])
+    k.release()
+
+
+def test_batched_solve_conserves_and_relaxes(env):
+    kx, ctx, torch = env
+    N = 48
+    q = ki.log_grid(N, 1e-3, 10.0)
+    g = oracle.grid(q)
+    f0 = ki.batch_bimodal(np.random.default_rng(32), q, 3)
+    k = ctx.build_kernel(q, precision=kx.SPLIT_TF32)
+    fd = torch.as_tensor(f0, device="cuda")
+    res = ctx.solve(k, fd, np.array([1.0, 2.0, 4.0]), t_end=1e4, h0=1e-3, rtol=1e-6,
+                    atol=1e-12, l1_tol=1e-3, check_every=5)
+    f = fd.cpu().numpy()
+    W = oracle.kernel_tensor(q)
+    for b in range(3):
+        assert res[b]["status"] == 0 and res[b]["converged"] == 1
+        for w in (g["h"], g["h"] * g["E"]):
+            assert abs(np.sum(w * f[b]) / np.sum(w * f0[b]) - 1) < 1e-7
+        fo, ro = oracle.solve(q, W, f0[b], oracle.M2_from_sigma(1.0, [1.0, 2.0, 4.0][b]),
+                              t_end=1e4, h0=1e-3, rtol=1e-6, atol=1e-12, l1_tol=1e-3,
+                              check_every=5)
+        assert np.sum(g["h"] * np.abs(f[b] - fo)) / np.sum(g["h"] * fo) < 5e-3
+    k.release()
