@@ -33,6 +33,10 @@ import kx_inputs as ki  # noqa: E402
 METRIC = "collision-term evals/s & solves/s vs plain FP64 path; p50/p99 solve latency"
 UNIT = "evals/s"
 L2_FLUSH_BYTES = 512 << 20     # > 126 MB L2
+# DRAM bytes (read + write) per launch from one ncu capture of the current kernels
+# (profiles/k_stream32_n128_batch4.md, profiles/k_stream32_n384_single.md); set to
+# None whenever those kernels change.
+NCU_TRAFFIC = {"stream_n128_b4": 8.698112e6, "stream_n384": 228.958976e6 + 3.475712e6}
 SOLVE = dict(t_end=1e5, h0=1e-3, rtol=1e-6, l1_tol=1e-3, check_every=10, max_attempts=2_000_000)
 
 
@@ -227,8 +231,9 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--fp64-steps", type=int, default=1)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--only", default="", choices=["", "contraction"],
-                    help="micro-benchmark: time the contraction kernel alone (for profiling)")
+    ap.add_argument("--only", default="", choices=["", "contraction", "step"],
+                    help="contraction: time the contraction kernel alone; step: run the "
+                         "workload's steps only (no baselines), for profiling")
     ap.add_argument("--n", type=int, default=384)
     ap.add_argument("--batch", type=int, default=1)
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64", "split"])
@@ -270,6 +275,12 @@ def main():
 
     for _ in range(args.warmup):
         one_step(kx.FP32)
+    if args.only == "step":
+        for _ in range(args.steps):
+            one_step(kx.FP32)
+        torch.cuda.synchronize()
+        ctx.close()
+        return 0
     uuid = "GPU-" + str(torch.cuda.get_device_properties(local).uuid)
     barrier()
     clocks = ClockSampler(uuid)
@@ -345,7 +356,7 @@ def main():
     alg_bytes = 8 * U + 4 * V
     achieved = alg_bytes / (ms_cold * 1e-3) / 1e9
     roof = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
-            "frac": achieved / hbm, "traffic": None,
+            "frac": achieved / hbm, "traffic": NCU_TRAFFIC["stream_n128_b4"],
             "kernel": "k_stream32<4,2> (N=128, 4 instances per pass)",
             "algorithmic_bytes_per_launch": alg_bytes, "avg_launch_ms_cold_l2": ms_cold,
             "avg_launch_ms_warm_l2": ms_warm, "peak_source": src_peak}
@@ -359,7 +370,8 @@ def main():
     V384 = sum((384 - a + 3) // 4 for a in range(384))
     b384 = 8 * U384 + 4 * V384
     roof384 = {"bound": "hbm", "achieved": b384 / (ms384 * 1e-3) / 1e9, "peak": hbm,
-               "unit": "GB/s", "frac": b384 / (ms384 * 1e-3) / 1e9 / hbm, "traffic": None,
+               "unit": "GB/s", "frac": b384 / (ms384 * 1e-3) / 1e9 / hbm,
+               "traffic": NCU_TRAFFIC["stream_n384"],
                "kernel": "k_stream32<1,4> (N=384, single instance, cold L2)",
                "algorithmic_bytes_per_launch": b384, "avg_launch_ms": ms384,
                "evals_per_s": 1e3 / ms384}
