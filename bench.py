@@ -36,7 +36,7 @@ L2_FLUSH_BYTES = 512 << 20     # > 126 MB L2
 # DRAM bytes (read + write) per launch from one ncu capture of the current kernels
 # (profiles/k_stream32_n128_batch4.md, profiles/k_stream32_n384_single.md); set to
 # None whenever those kernels change.
-NCU_TRAFFIC = {"stream_n128_b4": 8.698112e6, "stream_n384": 228.958976e6 + 3.475712e6}
+NCU_TRAFFIC = {"stream_n128_b4": None, "stream_n384": None}
 SOLVE = dict(t_end=1e5, h0=1e-3, rtol=1e-6, l1_tol=1e-3, check_every=10, max_attempts=2_000_000)
 
 
@@ -214,6 +214,111 @@ def measure_batched(ctx, kx, torch, flush, iters=5, oracle_sample=4):
             "max_rel_err_vs_oracle": err, "oracle_sample": f"{oracle_sample} instances"}
 
 
+def measure_uneven(ctx, kx, t_end=5.0, fp64_per_size=4):
+    """Uneven batch: 1024 instances with N uniform over {64, 96, 128, 192, 256},
+    sigma log-uniform over [1e-3, 1], 5 shared kernel tensors, all admitted at once
+    into the solve server (one group and one captured graph of attempts per
+    kernel, groups on concurrent streams), split-TF32 tensor-core path; each
+    instance integrated to t = t_end.  The plain FP64 path is timed on a sample of
+    the same instances through the same server."""
+    c = ki.config4()
+    par = dict(rtol=1e-6, atol=1e-12, l1_tol=0.0, check_every=10, max_attempts=1_000_000)
+    out = {}
+    for name, prec, idx in (("split_tf32", kx.SPLIT_TF32, range(len(c["ns"]))),
+                            ("fp64", kx.FP64, None)):
+        if idx is None:   # a few instances of each size
+            idx = [i for n in (64, 96, 128, 192, 256)
+                   for i in np.nonzero(c["ns"] == n)[0][:fp64_per_size]]
+        srv = kx.Server(ctx, budget_bytes=64 << 30, slots_per_group=256, attempts_per_tick=8,
+                        precision=prec, **par)
+        # build the five kernels first (cold builds are reported separately)
+        tb = time.perf_counter()
+        warm = [srv.submit(c["grids"][n], c["f"][int(np.nonzero(c["ns"] == n)[0][0])], 1.0,
+                           t_end=1e-9, h0=1e-3) for n in (64, 96, 128, 192, 256)]
+        for t, n in zip(warm, (64, 96, 128, 192, 256)):
+            srv.poll(t, n, timeout=600.0)
+        t_build = time.perf_counter() - tb
+        ev0 = srv.stats()["evals"]
+        t0 = time.perf_counter()
+        tickets = [(srv.submit(c["grids"][int(c["ns"][i])], c["f"][i], float(c["sigma"][i]),
+                               t_end=t_end, h0=1e-3), int(c["ns"][i])) for i in idx]
+        ok = 0
+        for t, n in tickets:
+            rc, _, _ = srv.poll(t, n, timeout=1800.0)
+            ok += rc == kx.OK
+        dt = time.perf_counter() - t0
+        st = srv.stats()
+        srv.stop()
+        evals = st["evals"] - ev0
+        out[name] = {"instances": len(tickets), "completed": ok, "seconds": dt,
+                     "solves_per_s": ok / dt, "evals_per_s": evals / dt, "evals": evals,
+                     "kernel_build_s": t_build}
+    return {"workload": "1024 instances, N uniform over {64,96,128,192,256}, sigma logU[1e-3,1], "
+                        f"no sources, each integrated to t={t_end}; all admitted at once",
+            "split_tf32": out["split_tf32"], "fp64_path_sample": out["fp64"],
+            "speedup_vs_fp64_evals": out["split_tf32"]["evals_per_s"] / out["fp64"]["evals_per_s"]}
+
+
+def serve_stream(kx, ctx, reqs, precision, budget=96 << 30, slots=8, phases=("run",)):
+    """Submit `reqs` at their arrival times to one server; one result dict per phase
+    (the same stream again in each phase, kernels cached after the first)."""
+    par = dict(rtol=1e-6, atol=1e-12, l1_tol=1e-3, check_every=10, max_attempts=2_000_000)
+    srv = kx.Server(ctx, budget_bytes=budget, slots_per_group=slots, attempts_per_tick=8,
+                    precision=precision, **par)
+    res = {}
+    for phase in phases:
+        s0 = srv.stats()
+        t0 = time.perf_counter()
+        tickets = []
+        for r in reqs:
+            delay = r["arrival"] - reqs[0]["arrival"] - (time.perf_counter() - t0)
+            if delay > 0:
+                time.sleep(delay)
+            tickets.append((srv.submit(r["q"], r["f0"], r["sigma"], sources=r["sources"],
+                                       t_end=1e5, h0=1e-3), r["n"]))
+        lat, ok, conv = [], 0, 0
+        for t, n in tickets:
+            rc, _, rr = srv.poll(t, n, timeout=1800.0)
+            if rc == kx.OK:
+                ok += 1
+                conv += int(rr["converged"])
+                lat.append(rr["latency_s"])
+        dt = time.perf_counter() - t0
+        s1 = srv.stats()
+        res[phase] = {"requests": len(reqs), "completed": ok, "converged": conv,
+                      "failed": len(reqs) - ok, "seconds": dt, "solves_per_s": ok / dt,
+                      "evals_per_s": (s1["evals"] - s0["evals"]) / dt,
+                      "p50_latency_s": float(np.percentile(lat, 50)) if lat else None,
+                      "p99_latency_s": float(np.percentile(lat, 99)) if lat else None,
+                      "kernels_built": s1["kernels_built"] - s0["kernels_built"],
+                      "kernel_cache_hits": s1["kernel_cache_hits"] - s0["kernel_cache_hits"]}
+    srv.stop()
+    return res
+
+
+def measure_serving(ctx, kx, requests=100, fp64_requests=8):
+    """Serving: a seeded Poisson stream (mean 200 req/s) of full solves with
+    N ~ U{64..384}, sigma ~ logU[1e-2, 10], random initial and source bumps,
+    submitted at their arrival times.  FP32 path: kernel tensors built on demand
+    (cold), then the same stream with every kernel cached (warm).  The plain FP64
+    path and the FP32 path also serve the stream's first `fp64_requests` requests
+    (same inputs, cold) for the speedup."""
+    reqs = ki.config5()[:requests]
+    out = serve_stream(kx, ctx, reqs, kx.FP32, phases=("cold", "warm"))
+    sub = reqs[:fp64_requests]
+    a = serve_stream(kx, ctx, sub, kx.FP32)["run"]
+    b = serve_stream(kx, ctx, sub, kx.FP64)["run"]
+    out["same_inputs_fp32"] = a
+    out["same_inputs_fp64_path"] = b
+    out["speedup_vs_fp64_solves_per_s"] = (a["solves_per_s"] / b["solves_per_s"]
+                                           if b["solves_per_s"] > 0 else None)
+    out["workload"] = (f"{requests} requests of a Poisson stream (200 req/s), N ~ U{{64..384}}, "
+                       "sigma logU[1e-2,10], two random source bumps each, full solves to "
+                       "L1<=1e-3 after the sources are off; FP32 path, 8 slots per kernel; "
+                       f"FP32 vs FP64 path on the first {fp64_requests} requests")
+    return out
+
+
 def config_desc(c, B):
     return {"workload": "single instance N=128 full integration: kernel build + adaptive Heun "
                         "solve with two freeze-in sources for sigma in {0.1,1,10,100} "
@@ -231,13 +336,16 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--fp64-steps", type=int, default=1)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--only", default="", choices=["", "contraction", "step"],
+    ap.add_argument("--only", default="", choices=["", "contraction", "step", "uneven", "serving"],
                     help="contraction: time the contraction kernel alone; step: run the "
                          "workload's steps only (no baselines), for profiling")
     ap.add_argument("--n", type=int, default=384)
     ap.add_argument("--batch", type=int, default=1)
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64", "split"])
     ap.add_argument("--iters", type=int, default=20)
+    ap.add_argument("--requests", type=int, default=100)
+    ap.add_argument("--no-serving", action="store_true",
+                    help="skip the uneven-batch and serving measurements")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -246,6 +354,15 @@ def main():
         return run_reference(args, rank)
     if args.only == "contraction":
         return run_contraction_only(args)
+    if args.only in ("uneven", "serving"):
+        import torch
+        import paper_2607_00755_b300 as kx
+        ctx = kx.Context(0)
+        r = measure_uneven(ctx, kx) if args.only == "uneven" else measure_serving(
+            ctx, kx, requests=args.requests)
+        print(json.dumps(r), flush=True)
+        ctx.close()
+        return 0
 
     import torch
     import paper_2607_00755_b300 as kx
@@ -377,6 +494,9 @@ def main():
                "evals_per_s": 1e3 / ms384}
 
     batched = measure_batched(ctx, kx, torch, flush) if rank == 0 else None
+    uneven = measure_uneven(ctx, kx) if rank == 0 and not args.no_serving else None
+    serving = (measure_serving(ctx, kx, requests=args.requests)
+               if rank == 0 and not args.no_serving else None)
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
@@ -396,6 +516,8 @@ def main():
                 "failed_solves": len(bad),
                 "roofline": roof, "roofline_streaming_n384": roof384,
                 "batched_n192_b512": batched,
+                "uneven_batch": uneven,
+                "serving": serving,
                 "cpu_baseline": cpu,
                 "e2e": {"value": e2e_evals / e2e_t, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
                         "d2h_bytes_per_step": int(d2h)},

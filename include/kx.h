@@ -218,6 +218,56 @@ int kx_solve_host(kx_ctx *ctx, const kx_kernel *k, int batch, const double *sigm
                   const kx_source *src, int n_src_sets, const kx_solve_params *par,
                   double *f_host, kx_result *res_host);
 
+/* -------------------------------------------------------------- serving */
+/* A solve server for parameter scans (continuous batching; no counterpart in
+ * the paper, which integrates one distribution at a time): requests (grid,
+ * mass, sigma, sources, initial f) are queued by kx_submit; a worker thread
+ * owning the context's device admits them into free slots of a per-kernel
+ * group (kernel tensors are built once per grid and shared between requests,
+ * kept in an LRU cache), subject to an HBM budget for kernel tables plus
+ * per-slot state; every group integrates all its slots together with captured
+ * CUDA graphs of Heun attempts (the Sec. 4.2 step, device-resident
+ * accept/reject and stopping test), and finished requests leave their slot at
+ * the next graph boundary while new ones join.  A request's result does not
+ * depend on the other requests in flight (per-instance arithmetic is
+ * independent of co-scheduling). */
+typedef struct kx_server kx_server;
+typedef struct {
+    long long hbm_budget_bytes;  /* kernel tables + slot state admitted at once (> 0) */
+    int slots_per_group;         /* instances integrated together per kernel tensor, 1..256 */
+    int attempts_per_tick;       /* Heun attempts per captured graph launch, 1..64 */
+    int precision;               /* KX_FP32 | KX_FP64 | KX_SPLIT_TF32 for every kernel */
+    int n_mu, measure;           /* kernel options of every request */
+    kx_solve_params par;         /* integration controls of every request (t0, t_end, h0
+                                    are per request; see kx_submit) */
+} kx_server_config;
+
+typedef struct {
+    long long submitted, completed, failed, queued, active;
+    long long kernels_built, kernel_cache_hits, evictions;
+    double p50_latency_s, p99_latency_s, mean_latency_s;   /* submit -> result available */
+    double p50_wait_s;                                     /* submit -> admitted */
+    long long evals;                                       /* collision evaluations done */
+} kx_server_stats;
+
+/* Start a server on the context's device (the context's stream is not used).
+ * KX_EINVAL on a bad configuration. */
+int kx_server_start(kx_ctx *ctx, const kx_server_config *cfg, kx_server **out);
+/* Queue one solve.  grid: n, q (host, copied), a, mass (n_mu, measure and
+ * precision come from the server).  src: NULL or one source set (copied).
+ * f0_host: [n] (copied).  t0, t_end, h0: this request's interval and first
+ * step.  Returns KX_EADMIT when the request can never fit the budget. */
+int kx_submit(kx_server *srv, const kx_grid_desc *grid, double sigma, const kx_source *src,
+              double t0, double t_end, double h0, const double *f0_host, kx_ticket *ticket);
+/* Wait up to timeout_s (>= 0) for a request.  KX_OK: done, f_out_host [n]
+ * (nullable) and *res filled, ticket released; KX_PENDING: not finished;
+ * other codes: the request failed (ticket released) or the ticket is unknown. */
+int kx_poll(kx_server *srv, kx_ticket ticket, double timeout_s, double *f_out_host,
+            kx_result *res);
+int kx_server_get_stats(kx_server *srv, kx_server_stats *out);
+/* Finish the requests in flight, stop the worker and free the server. */
+void kx_server_stop(kx_server *srv);
+
 /* ------------------------------------------------------------ profiling */
 /* Number of this library's kernels enqueued through `ctx` so far (a captured
  * graph counts each of its kernel nodes at every launch). */

@@ -104,7 +104,7 @@ def config4(seed: int = 4, instances: int = 1024, sizes=(64, 96, 128, 192, 256))
 def config5(seed: int = 5, requests: int = 2000, rate_hz: float = 200.0,
             n_min: int = 64, n_max: int = 384):
     """Poisson arrival stream of full solves: arrival times, N ~ U{n_min..n_max},
-    sigma ~ logU over 3 decades, random initial bumps and source bumps."""
+    sigma ~ logU[1e-2, 10] (3 decades), random initial bumps and source bumps."""
     rng = np.random.default_rng(seed)
     gaps = rng.exponential(1.0 / rate_hz, size=requests)
     arrivals = np.cumsum(gaps)
@@ -112,7 +112,7 @@ def config5(seed: int = 5, requests: int = 2000, rate_hz: float = 200.0,
     for r in range(requests):
         n = int(rng.integers(n_min, n_max + 1))
         q = log_grid(n, 1e-3, 1e2)
-        sigma = float(np.exp(rng.uniform(np.log(1e-1), np.log(1e2))))
+        sigma = float(np.exp(rng.uniform(np.log(1e-2), np.log(10.0))))
         f0 = batch_bimodal(rng, q, 1)[0]
         c = np.exp(rng.uniform(np.log(0.02), np.log(5.0), size=2))
         w = rng.uniform(0.3, 0.5, size=2)

@@ -26,7 +26,8 @@ EXPORTS = (
     "kx_build_kernel", "kx_kernel_retain", "kx_kernel_release", "kx_kernel_get_info",
     "kx_kernel_grid", "kx_kernel_row", "kx_collision", "kx_collision_host", "kx_step",
     "kx_solve", "kx_solve_host", "kx_mb_fit", "kx_launch_count", "kx_time_contraction",
-    "kx_collision_noalloc",
+    "kx_collision_noalloc", "kx_server_start", "kx_submit", "kx_poll", "kx_server_get_stats",
+    "kx_server_stop",
 )
 
 
@@ -76,6 +77,23 @@ class KernelInfo(ctypes.Structure):
                 ("build_ms", ctypes.c_double)]
 
 
+class ServerConfig(ctypes.Structure):
+    _fields_ = [("hbm_budget_bytes", ctypes.c_longlong), ("slots_per_group", ctypes.c_int),
+                ("attempts_per_tick", ctypes.c_int), ("precision", ctypes.c_int),
+                ("n_mu", ctypes.c_int), ("measure", ctypes.c_int), ("par", SolveParams)]
+
+
+class ServerStats(ctypes.Structure):
+    _fields_ = [(k, ctypes.c_longlong) for k in ("submitted", "completed", "failed", "queued",
+                                                 "active", "kernels_built", "kernel_cache_hits",
+                                                 "evictions")] + \
+               [(k, ctypes.c_double) for k in ("p50_latency_s", "p99_latency_s", "mean_latency_s",
+                                               "p50_wait_s")] + [("evals", ctypes.c_longlong)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
 _lib = None
 
 
@@ -109,6 +127,11 @@ def load_library(path: str = LIB_PATH):
         "kx_launch_count": (ctypes.c_longlong, [vp]),
         "kx_time_contraction": (i, [vp, vp, i, vp, i, ctypes.c_longlong, vp]),
         "kx_collision_noalloc": (i, [vp, vp, i, vp, vp, vp, i]),
+        "kx_server_start": (i, [vp, ctypes.POINTER(ServerConfig), vp]),
+        "kx_submit": (i, [vp, ctypes.POINTER(GridDesc), d, vp, d, d, d, vp, vp]),
+        "kx_poll": (i, [vp, ctypes.c_uint64, d, vp, vp]),
+        "kx_server_get_stats": (i, [vp, ctypes.POINTER(ServerStats)]),
+        "kx_server_stop": (None, [vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -299,6 +322,58 @@ class Context:
         if rc:
             raise self.error(rc, "kx_mb_fit")
         return out
+
+
+class Server:
+    """Continuous-batching solve server (kx_server): submit solves, poll results."""
+
+    def __init__(self, ctx: Context, budget_bytes=8 << 30, slots_per_group=16,
+                 attempts_per_tick=8, precision=FP32, n_mu=18, measure=MEASURE_ENERGY, **params):
+        self.ctx, self.lib = ctx, ctx.lib
+        cfg = ServerConfig(int(budget_bytes), int(slots_per_group), int(attempts_per_tick),
+                           int(precision), int(n_mu), int(measure), Context.params(**params))
+        h = ctypes.c_void_p()
+        rc = self.lib.kx_server_start(ctx.h, ctypes.byref(cfg), ctypes.byref(h))
+        if rc:
+            raise ctx.error(rc, "kx_server_start")
+        self.h = h
+
+    def submit(self, q, f0, sigma, sources=None, t0=0.0, t_end=1.0, h0=1e-3, mass=1.0, a=1.0):
+        """Queue one solve; returns a ticket (int).  Raises KxError (e.g. KX_EADMIT)."""
+        q, f0 = _np(q), _np(f0)
+        desc = GridDesc(q.size, q.ctypes.data, a, mass, 0, 0, 0, 0)
+        src, ns, keep = Context._sources(sources, 1, q.size)
+        t = ctypes.c_uint64()
+        rc = self.lib.kx_submit(self.h, ctypes.byref(desc), float(sigma), src, float(t0),
+                                float(t_end), float(h0), _ptr(f0), ctypes.byref(t))
+        del keep
+        if rc:
+            raise KxError(rc, self.lib.kx_strerror(rc).decode())
+        return t.value
+
+    def poll(self, ticket, n, timeout=0.0):
+        """(status, f, result dict): status OK when done, PENDING otherwise."""
+        f = np.empty(n)
+        res = Result()
+        rc = self.lib.kx_poll(self.h, ctypes.c_uint64(ticket), float(timeout), _ptr(f),
+                              ctypes.byref(res))
+        return rc, f, res.as_dict()
+
+    def stats(self):
+        st = ServerStats()
+        self.lib.kx_server_get_stats(self.h, ctypes.byref(st))
+        return st.as_dict()
+
+    def stop(self):
+        if getattr(self, "h", None):
+            self.lib.kx_server_stop(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.stop()
+        except Exception:
+            pass
 
 
 class Kernel:

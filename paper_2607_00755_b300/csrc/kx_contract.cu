@@ -256,11 +256,15 @@ __device__ __forceinline__ float kx_exp2m1_small(float d) {
 //   a = l2_n + l2_m (gain exponent), d = (delta_i + delta_t) - (delta_n + delta_m)
 //   (loss minus gain exponent; the log-linear reference cancels), and
 //   f_n f_m - f_i f_t = 2^a (1 - 2^d): for |d| < 1/4 through the series above,
-//   else as 2^a - 2^(a + d) (no cancellation, no 0 * inf).
+//   else as 2^a - 2^(a + d).  Inside the kinematic support a + d is
+//   log2(f_i f_t / f_max^2) <= 0.  Outside it (W = 0, j and omega are
+//   placeholders) the reference line does not cancel and a + d can pass the
+//   float range for a steep f; the cap keeps W * term = 0 there instead of
+//   0 * inf, and never binds inside the support.
 __device__ __forceinline__ float kx_bracket_term(float a, float d) {
     const float ea = kx_ex2(a);
     const float nearv = -ea * kx_exp2m1_small(d);
-    const float farv = ea - kx_ex2(a + d);
+    const float farv = ea - kx_ex2(fminf(a + d, 64.f));
     return fabsf(d) < 0.25f ? nearv : farv;
 }
 
@@ -653,22 +657,29 @@ __global__ void __launch_bounds__(KX_FIN_THREADS)
         if (threadIdx.x == 0) st->skip2 = 0;
         return;
     }
+    // Every thread takes its copy of the instance state here, before the first
+    // block barrier: thread 0 rewrites the state at the end of the stage, and a
+    // warp that read it after that write could disagree with the others on
+    // block-uniform decisions (the MB check, which holds barriers).
+    const double t = st->t, t_end = st->t_end, h_state = st->h, h_try_state = st->h_try;
+    const int last_state = st->last;
+    const long long steps0 = st->steps, rejects0 = st->rejects;
+    const double l1_0 = st->l1, T0 = st->T, lnz0 = st->lnz;
     const bool in = i < n;
     const double Ei = in ? E[i] : 0.0, hi = in ? h[i] : 0.0;
     double *fb = sv.f + (long long)b * n;
     double *k1 = sv.k1 + (long long)b * n;
     double *fp = sv.fp + (long long)b * n;
-    const double t = st->t;
     double htry;
     if (stage == 1) {
-        htry = st->h;
+        htry = h_state;
         if (!sv.fixed) {
             if (htry > sv.h_max) htry = sv.h_max;
             if (htry < sv.h_min) htry = sv.h_min;
         }
         int last = 0;
-        if (t + htry >= st->t_end) {
-            htry = st->t_end - t;
+        if (t + htry >= t_end) {
+            htry = t_end - t;
             last = 1;
         }
         __syncthreads();
@@ -677,7 +688,7 @@ __global__ void __launch_bounds__(KX_FIN_THREADS)
             st->last = last;
         }
     } else {
-        htry = st->h_try;
+        htry = h_try_state;
     }
     const double fcur = in ? (stage == 1 ? fb[i] : fp[i]) : 0.0;
     kx_row_out r = kx_combine_project(n, chunks, path, b, fcur, Ei, hi, v, sv.project, smem);
@@ -782,13 +793,13 @@ __global__ void __launch_bounds__(KX_FIN_THREADS)
     double tn = t;
     if (accept) {
         if (in) fb[i] = fci;
-        tn = st->last ? st->t_end : t + htry;
+        tn = last_state ? t_end : t + htry;
     }
     __syncthreads();
-    long long steps = st->steps + (accept ? 1 : 0);
-    long long rejects = st->rejects + (accept ? 0 : 1);
+    long long steps = steps0 + (accept ? 1 : 0);
+    long long rejects = rejects0 + (accept ? 0 : 1);
     int done = 0, converged = 0;
-    double fit[3] = {st->l1, st->T, st->lnz};
+    double fit[3] = {l1_0, T0, lnz0};
     if (accept && sv.check_every > 0 && sv.l1_tol > 0.0 && steps % sv.check_every == 0 &&
         tn >= sv.src[b].t_off) {
         const double fnew = in ? fb[i] : 0.0;
@@ -804,7 +815,7 @@ __global__ void __launch_bounds__(KX_FIN_THREADS)
     }
     int status = KX_OK;
     if (!done) {
-        if (tn >= st->t_end) done = 1;
+        if (tn >= t_end) done = 1;
         else if (steps + rejects >= max_attempts) {
             done = 1;
             status = KX_ENOCONV;

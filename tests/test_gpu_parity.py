@@ -203,6 +203,31 @@ def test_collision_edge_cases(ctx, kx, precision):
 
 
 @pytest.mark.parametrize("precision", [0, 1])
+def test_collision_steep_f_on_wide_grid(ctx, kx, precision):
+    """Cold, steep distributions on q in [1e-3, 1e2]: the log-linear reference of
+    the FP32 path leaves deviations of several hundred (in log2 units) at the
+    grid ends, so out-of-support elements see exponents beyond the float range;
+    C must stay finite and within tolerance.  Inputs: the first serving-stream
+    requests with N <= 120 and a cold Maxwell-Boltzmann (T = 0.05, underflowing
+    to zero at high q)."""
+    reqs = [r for r in ki.config5()[:40] if r["n"] <= 120][:4]
+    cases = [(r["q"], r["f0"], r["sigma"]) for r in reqs]
+    q = ki.log_grid(90, 1e-3, 1e2)
+    E = np.sqrt(q * q + 1.0)
+    cases.append((q, 0.7 * np.exp(-(E - 1.0) / 0.05) + 1e-3 * np.exp(-(E - 1.0) / 2.0), 3.0))
+    for q, f, sig in cases:
+        k = ctx.build_kernel(q, precision=precision)
+        W = oracle.kernel_tensor(q)
+        for project in (0, 1):
+            C, d = ctx.collision(k, dev(f[None]), sig, project=bool(project), diag=True)
+            C = C.cpu().numpy()[0]
+            assert d[0]["status"] == 0 and np.all(np.isfinite(C))
+            Co, _ = oracle_C(q, f, [sig], project, W)
+            assert relerr(C, Co[0]) <= TOL[precision], (q.size, project, relerr(C, Co[0]))
+        k.release()
+
+
+@pytest.mark.parametrize("precision", [0, 1])
 @pytest.mark.parametrize("N", [48, 200])
 def test_batch_is_bitwise_independent_of_co_scheduling(ctx, kx, precision, N):
     """Each instance's C is bit-identical alone and inside a batch."""
