@@ -110,7 +110,12 @@ __global__ void k_pack_fp32(int N, long long P, int V, const uint32_t *__restric
     int n = t & 0xffff, m0 = t >> 16;
     long long out = ((long long)i * V + v) * 4;
     long long base = (long long)i * P + kx_pair_base(n, N);
-    for (int c = 0; c < 4; ++c) {
+    // slot s of vector v holds element m0 + ((s + r) & 3), r = (v >> 2) & 3: the
+    // streaming kernel reads vector v in lane v mod 32, so at each slot the
+    // lanes of a warp touch grid points spread over all shared-memory banks
+    const int r = (v >> 2) & 3;
+    for (int sl = 0; sl < 4; ++sl) {
+        const int c = (sl + r) & 3;
         int m = m0 + c;
         float w = 0.f;
         uint32_t word = 0u;
@@ -130,8 +135,8 @@ __global__ void k_pack_fp32(int N, long long P, int V, const uint32_t *__restric
                 word = (j << 23) | (uint32_t)q;
             }
         }
-        W32[out + c] = w;
-        pk[out + c] = word;
+        W32[out + sl] = w;
+        pk[out + sl] = word;
     }
 }
 

@@ -95,29 +95,60 @@ static inline int kx_fin_threads(int n) { return ((n + 31) / 32) * 32; }
 //             f/f_max instance-minor (fT) and as TF32 hi/lo MMA operand tiles (bt)
 //             for the tensor-core gain; zeros in the k padding up to n rounded to 32.
 // Returns the non-finite flag (block-uniform).
+// Block sum of K floats (fixed shuffle tree, deterministic); all threads get
+// the result.  smem: K*32 floats.
+template <int K>
+__device__ __forceinline__ void kx_block_sumf(float (&v)[K], float *smem) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+    for (int k = 0; k < K; ++k)
+#pragma unroll
+        for (int off = 16; off; off >>= 1) v[k] += __shfl_xor_sync(0xffffffffu, v[k], off);
+    if (lane == 0)
+#pragma unroll
+        for (int k = 0; k < K; ++k) smem[k * 32 + warp] = v[k];
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        float x = lane < nw ? smem[k * 32 + lane] : 0.f;
+#pragma unroll
+        for (int off = 16; off; off >>= 1) x += __shfl_xor_sync(0xffffffffu, x, off);
+        v[k] = x;
+    }
+    __syncthreads();
+}
+
 __device__ int kx_prep_block(int n, int path, const double *__restrict__ fb,
                              const double *__restrict__ E, const double *__restrict__ h,
                              const kx_batch_views &v, int b, double *smem) {
+    __shared__ double s_scale[2];   // log2 f_max, 1 / f_max (computed once per block)
     const int i = threadIdx.x;
     double x = i < n ? fb[i] : 0.0;
     int bad = (i < n) && !isfinite(x);
     double fm = kx_block_max(fabs(x), smem);
-    bad = kx_block_or(bad, smem);
-    if (threadIdx.x == 0) v.fmax[b] = fm;
+    if (threadIdx.x == 0) {
+        v.fmax[b] = fm;
+        if (path != KX_FP64) {
+            s_scale[0] = fm > 0.0 ? log2(fm) : 0.0;
+            s_scale[1] = fm > 0.0 ? 1.0 / fm : 0.0;
+        }
+    }
+    bad = kx_block_or(bad, smem);   // (barrier: publishes s_scale)
     if (path == KX_FP64) {
         if (i < n) v.lf64[(long long)b * n + i] = log(x > KX_LOG_FLOOR ? x : KX_LOG_FLOOR);
         return bad;
     }
+    const double lfm = s_scale[0], rfm = s_scale[1];
+    double l2 = -2000.0;
+    if (i < n && fm > 0.0) l2 = log2(x > KX_LOG_FLOOR ? x : KX_LOG_FLOOR) - lfm;
     if (path == KX_SPLIT_TF32) {
         double *ll = smem + 64 + 32;
-        double l2 = -2000.0;
-        if (i < n && fm > 0.0) l2 = log2(x > KX_LOG_FLOOR ? x : KX_LOG_FLOOR) - log2(fm);
         if (i < n) ll[i] = l2;
         __syncthreads();
         if (i < n)
             v.td[(long long)b * n + i] =
                 make_float2((float)l2, i + 1 < n ? (float)(ll[i + 1] - l2) : 0.f);
-        const float fp = (i < n && fm > 0.0) ? (float)(x / fm) : 0.f;
+        const float fp = (i < n && fm > 0.0) ? (float)(x * rfm) : 0.f;
         if (i < n) v.fT[(size_t)i * v.Bpad + b] = fp;
         uint32_t hb;
         asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(hb) : "f"(fp));
@@ -133,23 +164,29 @@ __device__ int kx_prep_block(int n, int path, const double *__restrict__ fb,
     float2 *tl = v.tl + (long long)b * (n + 4);
     float2 *td = v.td + (long long)b * n;
     double *dl = smem + 64 + 32;           // deltas, n <= 512 doubles after the reduction scratch
+    float *fs = reinterpret_cast<float *>(smem);
     const double Ei = i < n ? E[i] : 0.0;
-    double l2 = -2000.0;
-    if (i < n && fm > 0.0) l2 = log2(x > KX_LOG_FLOOR ? x : KX_LOG_FLOOR) - log2(fm);
-    const double w = (i < n && fm > 0.0 && x > 0.0) ? h[i] * (x / fm) : 0.0;
-    double s[5] = {w, w * Ei, w * Ei * Ei, w * l2, w * Ei * l2};
-    kx_block_sum<5>(s, smem);
-    double det = s[0] * s[2] - s[1] * s[1];
-    double slope = 0.0, icpt = s[0] > 0.0 ? s[3] / s[0] : 0.0;
-    if (det > 1e-12 * s[0] * s[2]) {
-        slope = (s[0] * s[4] - s[1] * s[3]) / det;
-        icpt = (s[3] - slope * s[1]) / s[0];
+    // Reference line l2 ~ icpt + slope (E - E_0): weighted least squares (weights
+    // h f / f_max) in FP32, centred form (two passes).  Any line in E cancels
+    // exactly in the exponent differences; the fit only keeps the deviations small.
+    const float l2f = (float)l2, Ef = i < n ? (float)(Ei - E[0]) : 0.f;   // kinetic energy
+    const float w = (i < n && fm > 0.0 && x > 0.0) ? (float)h[i] * (float)(x * rfm) : 0.f;
+    float s1[3] = {w, w * Ef, w * l2f};
+    kx_block_sumf<3>(s1, fs);
+    float slope = 0.f, icpt = 0.f;
+    if (s1[0] > 0.f) {
+        const float Em = s1[1] / s1[0], lm = s1[2] / s1[0];
+        const float dE = Ef - Em;
+        float s2[2] = {w * dE * dE, w * dE * (l2f - lm)};
+        kx_block_sumf<2>(s2, fs);
+        if (s2[0] > 1e-6f * s1[0] * fmaxf(Em * Em, 1e-30f)) slope = s2[1] / s2[0];
+        icpt = lm - slope * Em;
     }
-    const double del = l2 - (icpt + slope * Ei);
+    const double del = l2 - ((double)icpt + (double)slope * (Ei - E[0]));
     if (i < n) dl[i] = del;
     __syncthreads();
     if (i < n) {
-        tl[i] = make_float2((float)l2, (float)del);
+        tl[i] = make_float2(l2f, (float)del);
         td[i] = make_float2((float)del, i + 1 < n ? (float)(dl[i + 1] - del) : 0.f);
     }
     if (i < 4) tl[n + i] = make_float2(-2000.f, 0.f);
@@ -268,17 +305,54 @@ __device__ __forceinline__ float kx_bracket_term(float a, float d) {
     return fabsf(d) < 0.25f ? nearv : farv;
 }
 
-// Persistent streaming contraction.  The work unit is one warp-sized slice of
-// a row: 32 x VPL consecutive 4-element vectors of row i.  Warps take units in
-// a fixed round-robin order, prefetch the next unit's tables into registers
-// while computing the current one, and reduce each unit inside the warp
-// (FP64 shuffles, no block barrier); the unit's sum is one partial of its row.
+// Error-free sum of two floats (Knuth's TwoSum): s + e == a + b exactly.
+__device__ __forceinline__ void kx_two_sum(float a, float b, float &s, float &e) {
+    s = a + b;
+    const float bv = s - a;
+    e = (a - (s - bv)) + (b - bv);
+}
+
+// (hi, lo) += x in double-float arithmetic (about 44 significant bits).
+__device__ __forceinline__ void kx_df_add(float &hi, float &lo, float x) {
+    float s, e;
+    kx_two_sum(hi, x, s, e);
+    hi = s;
+    lo += e;
+}
+
+// Vectors per lane of a streaming unit: short rows use smaller units so that
+// every SM gets work.
+static int kx_stream_vpl(int n) { return n <= 160 ? 2 : 4; }
+
+static int kx_stream_upr(const kx_kernel *k) {
+    const int unit = 32 * kx_stream_vpl(k->n);
+    return (k->V + unit - 1) / unit;
+}
+
+// Units per task: large grids group up to 8 consecutive units of a row into one
+// task so that the cross-lane reduction and the row partial are paid once per
+// task; small grids keep one unit per task to give every warp work.  Depends on
+// the grid size only, so an instance's arithmetic does not depend on the batch
+// it is launched with.
+static int kx_stream_group(const kx_kernel *k) {
+    const long long units = (long long)k->n * kx_stream_upr(k);
+    long long g = units / (2LL * 148 * 16);
+    return (int)(g < 1 ? 1 : (g > 8 ? 8 : g));
+}
+
+// Persistent streaming contraction.  A unit is one warp-sized slice of a row
+// (32 x VPL consecutive 4-element vectors of row i); a task is G consecutive
+// units of one row.  Warps take tasks in a fixed round-robin order and prefetch
+// the next unit's tables into registers while computing the current one.  Each
+// lane sums its unit's terms in FP32 and adds the unit sum into a double-float
+// accumulator; at the end of the task the warp reduces the double-float sums
+// (fixed shuffle tree) and lane 0 writes the task's (hi, lo) row partial.
 template <int BP, int VPL>
 __global__ void __launch_bounds__(KX_T32)
-    k_stream32(int n, int V, int upr, int B, const uint32_t *__restrict__ vt,
+    k_stream32(int n, int V, int upr, int G, int tpr, int B, const uint32_t *__restrict__ vt,
                const float4 *__restrict__ W, const uint4 *__restrict__ PK,
                const float2 *__restrict__ tl, const float2 *__restrict__ td,
-               double2 *__restrict__ partial, const kx_inst_state *__restrict__ st, int stage) {
+               float2 *__restrict__ partial, const kx_inst_state *__restrict__ st, int stage) {
     const int b0 = blockIdx.y * BP;
     __shared__ float2 s_l[BP][KX_MAX_N + 4];   // (l2_j, delta_j)
     __shared__ float2 s_d[BP][KX_MAX_N];       // (delta_j, delta_{j+1} - delta_j)
@@ -302,15 +376,19 @@ __global__ void __launch_bounds__(KX_T32)
     __syncthreads();
 
     const int lane = threadIdx.x & 31;
+    // element offset of each slot of this lane's vectors (slot rotation of the
+    // packed tables: vector v's slot s holds m0 + ((s + ((v >> 2) & 3)) & 3),
+    // and v mod 32 == lane)
+    const int rot = (lane >> 2) & 3;
+    const int so[4] = {rot, (1 + rot) & 3, (2 + rot) & 3, (3 + rot) & 3};
     const int wpb = blockDim.x >> 5;
-    const int total = n * upr;
+    const int ntask = n * tpr;
     const int stride = gridDim.x * wpb;
-    int u = blockIdx.x * wpb + (threadIdx.x >> 5);
+    int task = blockIdx.x * wpb + (threadIdx.x >> 5);
     float4 w[VPL];
     uint4 pk[VPL];
     uint32_t nv[VPL];
-    auto load_unit = [&](int uu) {
-        const int i = uu / upr, c = uu - i * upr;
+    auto load_unit = [&](int i, int c) {
         const float4 *Wr = W + (long long)i * V;
         const uint4 *Pr = PK + (long long)i * V;
 #pragma unroll
@@ -327,66 +405,98 @@ __global__ void __launch_bounds__(KX_T32)
             }
         }
     };
-    if (u < total) load_unit(u);
-    while (u < total) {
-        float4 wc[VPL];
-        uint4 pc[VPL];
-        uint32_t nc[VPL];
-#pragma unroll
-        for (int e = 0; e < VPL; ++e) {
-            wc[e] = w[e];
-            pc[e] = pk[e];
-            nc[e] = nv[e];
-        }
-        const int un = u + stride;
-        if (un < total) load_unit(un);
-        const int i = u / upr, c = u - i * upr;
-        float acc[BP], di[BP];
+    // the unit in the prefetch registers: row i, chunk c, of task `task`
+    int i = 0, c = 0, cend = 0;
+    if (task < ntask) {
+        i = task / tpr;
+        const int g = task - i * tpr;
+        c = g * G;
+        cend = min(c + G, upr);
+        load_unit(i, c);
+    }
+    while (task < ntask) {
+        float hi[BP], lo[BP], di[BP];
 #pragma unroll
         for (int bb = 0; bb < BP; ++bb) {
-            acc[bb] = 0.f;
+            hi[bb] = 0.f;
+            lo[bb] = 0.f;
             di[bb] = s_l[bb][i].y;
         }
+        const int ti = i, tg = task - i * tpr;
+        for (;;) {
+            float4 wc[VPL];
+            uint4 pc[VPL];
+            uint32_t nc[VPL];
 #pragma unroll
-        for (int e = 0; e < VPL; ++e) {
-            const int nn = nc[e] & 0xffff, m0 = nc[e] >> 16;
-            const float wk[4] = {wc[e].x, wc[e].y, wc[e].z, wc[e].w};
-            const uint32_t pw[4] = {pc[e].x, pc[e].y, pc[e].z, pc[e].w};
-#pragma unroll
-            for (int bb = 0; bb < BP; ++bb) {
-                const float2 ln = s_l[bb][nn];
-#pragma unroll
-                for (int q = 0; q < 4; ++q) {
-                    const float2 lm = s_l[bb][m0 + q];
-                    const float2 dj = s_d[bb][pw[q] >> 23];
-                    const float a = ln.x + lm.x;
-                    const float d =
-                        (di[bb] + fmaf(kx_unpack_omega(pw[q]), dj.y, dj.x)) - (ln.y + lm.y);
-                    acc[bb] = fmaf(wk[q], kx_bracket_term(a, d), acc[bb]);
+            for (int e = 0; e < VPL; ++e) {
+                wc[e] = w[e];
+                pc[e] = pk[e];
+                nc[e] = nv[e];
+            }
+            // advance to the next unit (this task's next chunk, or the next task)
+            bool more = c + 1 < cend;
+            if (more) {
+                ++c;
+                load_unit(i, c);
+            } else {
+                task += stride;
+                if (task < ntask) {
+                    i = task / tpr;
+                    const int g = task - i * tpr;
+                    c = g * G;
+                    cend = min(c + G, upr);
+                    load_unit(i, c);
                 }
             }
+            float acc[BP];
+#pragma unroll
+            for (int bb = 0; bb < BP; ++bb) acc[bb] = 0.f;
+#pragma unroll
+            for (int e = 0; e < VPL; ++e) {
+                const int nn = nc[e] & 0xffff, m0 = nc[e] >> 16;
+                const float wk[4] = {wc[e].x, wc[e].y, wc[e].z, wc[e].w};
+                const uint32_t pw[4] = {pc[e].x, pc[e].y, pc[e].z, pc[e].w};
+#pragma unroll
+                for (int bb = 0; bb < BP; ++bb) {
+                    const float2 ln = s_l[bb][nn];
+                    const float cn = di[bb] - ln.y;
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        const float2 lm = s_l[bb][m0 + so[q]];
+                        const float2 dj = s_d[bb][pw[q] >> 23];
+                        const float a = ln.x + lm.x;
+                        const float d = (cn + fmaf(kx_unpack_omega(pw[q]), dj.y, dj.x)) - lm.y;
+                        acc[bb] = fmaf(wk[q], kx_bracket_term(a, d), acc[bb]);
+                    }
+                }
+            }
+#pragma unroll
+            for (int bb = 0; bb < BP; ++bb) kx_df_add(hi[bb], lo[bb], acc[bb]);
+            if (!more) break;
         }
 #pragma unroll
         for (int bb = 0; bb < BP; ++bb) {
-            double x = acc[bb];
+            float h = hi[bb], l = lo[bb];
 #pragma unroll
-            for (int off = 16; off; off >>= 1) x += __shfl_xor_sync(0xffffffffu, x, off);
+            for (int off = 16; off; off >>= 1) {
+                const float h2 = __shfl_xor_sync(0xffffffffu, h, off);
+                const float l2 = __shfl_xor_sync(0xffffffffu, l, off);
+                float s, e;
+                kx_two_sum(h, h2, s, e);
+                h = s;
+                l = (l + l2) + e;
+            }
             if (lane == 0 && act[bb])
-                partial[((long long)(b0 + bb) * n + i) * upr + c] = make_double2(x, 0.0);
+                partial[((long long)(b0 + bb) * n + ti) * tpr + tg] = make_float2(h, l);
         }
-        u = un;
     }
 }
-
-// Vectors per lane of a streaming unit: short rows use smaller units so that
-// every SM gets work.
-static int kx_stream_vpl(int n) { return n <= 160 ? 2 : 4; }
 
 int kx_chunks_per_row(const kx_kernel *k) {
     if (k->precision == KX_SPLIT_TF32) return 1;
     if (k->precision == KX_FP64) return (int)((k->P + KX_CH64 - 1) / KX_CH64);
-    const int unit = 32 * kx_stream_vpl(k->n);
-    return (k->V + unit - 1) / unit;
+    const int upr = kx_stream_upr(k), G = kx_stream_group(k);
+    return (upr + G - 1) / G;
 }
 
 // SM count, queried once (kx_contract_prepare) before any stream capture.
@@ -422,8 +532,8 @@ static cudaError_t kx_launch_stream(const kx_kernel *k, int B, const kx_batch_vi
     if (e != cudaSuccess) return e;
     if (occ < 1) occ = 1;
     const int sms = g_sms > 0 ? g_sms : 148;
-    const int upr = v.chunks;
-    const int total = k->n * upr;
+    const int upr = kx_stream_upr(k), G = kx_stream_group(k), tpr = v.chunks;
+    const int total = k->n * tpr;
     const int wpb = KX_T32 / 32;
     const int groups = (B + BP - 1) / BP;
     int blocks = (total + wpb - 1) / wpb;
@@ -433,8 +543,9 @@ static cudaError_t kx_launch_stream(const kx_kernel *k, int B, const kx_batch_vi
     dim3 grid(blocks, groups);
     const float4 *W = reinterpret_cast<const float4 *>(k->d_W32);
     const uint4 *PK = reinterpret_cast<const uint4 *>(k->d_pk);
-    k_stream32<BP, VPL><<<grid, KX_T32, 0, s>>>(k->n, k->V, upr, B, k->d_vt, W, PK, v.tl, v.td,
-                                                v.partial, st, stage);
+    k_stream32<BP, VPL><<<grid, KX_T32, 0, s>>>(k->n, k->V, upr, G, tpr, B, k->d_vt, W, PK, v.tl,
+                                                v.td, reinterpret_cast<float2 *>(v.partial), st,
+                                                stage);
     return cudaGetLastError();
 }
 
@@ -474,7 +585,17 @@ __device__ kx_row_out kx_combine_project(int n, int chunks, int path, int b, dou
     const int i = threadIdx.x;
     const double fm = v.fmax[b];
     double G = 0.0, L = 0.0;
-    if (i < n) {
+    if (i < n && path == KX_FP32) {
+        // double-float task partials (hi, lo), summed in double-float
+        const float2 *pp = reinterpret_cast<const float2 *>(v.partial) + ((long long)b * n + i) * chunks;
+        float hi = 0.f, lo = 0.f;
+        for (int c = 0; c < chunks; ++c) {
+            const float2 x = pp[c];
+            kx_df_add(hi, lo, x.x);
+            lo += x.y;
+        }
+        G = (double)hi + (double)lo;
+    } else if (i < n) {
         const double2 *pp = v.partial + ((long long)b * n + i) * chunks;
         for (int c = 0; c < chunks; ++c) {
             double2 x = pp[c];
@@ -500,14 +621,44 @@ __device__ kx_row_out kx_combine_project(int n, int chunks, int path, int b, dou
         xi = q > KX_EPS_SUPP ? q : 0.0;
     }
     double s[5] = {hi * xi, hi * Ei * xi, hi * Ei * Ei * xi, hi * Craw, hi * Ei * Craw};
-    kx_block_sum<5>(s, smem);
-    double det = s[0] * s[2] - s[1] * s[1];
-    if (!(det > KX_DET_GUARD * s[0] * s[2])) {
-        r.singular = 1;
-    } else {
-        r.alpha = (s[3] * s[2] - s[4] * s[1]) / det;
-        r.beta = (s[4] * s[0] - s[3] * s[1]) / det;
+    // block sums of the five moments; one thread solves the 2x2 system and
+    // broadcasts (alpha, beta, singular)
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+    for (int k = 0; k < 5; ++k)
+#pragma unroll
+        for (int off = 16; off; off >>= 1) s[k] += __shfl_xor_sync(0xffffffffu, s[k], off);
+    if (lane == 0)
+#pragma unroll
+        for (int k = 0; k < 5; ++k) smem[k * 32 + warp] = s[k];
+    __syncthreads();
+    if (warp == 0) {
+#pragma unroll
+        for (int k = 0; k < 5; ++k) {
+            double x = lane < nw ? smem[k * 32 + lane] : 0.0;
+#pragma unroll
+            for (int off = 16; off; off >>= 1) x += __shfl_xor_sync(0xffffffffu, x, off);
+            s[k] = x;
+        }
+        if (lane == 0) {
+            const double det = s[0] * s[2] - s[1] * s[1];
+            double al = 0.0, be = 0.0, sg = 0.0;
+            if (!(det > KX_DET_GUARD * s[0] * s[2])) {
+                sg = 1.0;
+            } else {
+                al = (s[3] * s[2] - s[4] * s[1]) / det;
+                be = (s[4] * s[0] - s[3] * s[1]) / det;
+            }
+            smem[160] = al;
+            smem[161] = be;
+            smem[162] = sg;
+        }
     }
+    __syncthreads();
+    r.alpha = smem[160];
+    r.beta = smem[161];
+    r.singular = smem[162] != 0.0;
+    __syncthreads();
     r.Cproj = Craw - xi * (r.alpha + r.beta * Ei);
     return r;
 }
@@ -567,8 +718,8 @@ cudaError_t kx_launch_finalize(const kx_kernel *k, int B, const double *f, const
 // sum h f (safeguarded Newton in u = ln T inside [ln 1e-12, ln 1e12]; <E>(T) is
 // increasing with d<E>/du = Var(E)/T), z from the number moment,
 // L1 = sum h |f - f_MB| / sum h f.  Block-wide; returns (T, ln z, L1) to all threads.
-__device__ void kx_mb_fit_block(int n, double fi, double Ei, double hi, double E0, double *out,
-                                double *smem) {
+__device__ void kx_mb_fit_block(int n, double fi, double Ei, double hi, double E0, double T_guess,
+                                double *out, double *smem) {
     const bool in = threadIdx.x < n;
     double s0[2] = {in ? hi * fi : 0.0, in ? hi * Ei * fi : 0.0};
     kx_block_sum<2>(s0, smem);
@@ -581,7 +732,9 @@ __device__ void kx_mb_fit_block(int n, double fi, double Ei, double hi, double E
     }
     const double ebar = s0[1] / N0;
     double lo = log(1e-12), hi_u = log(1e12);
-    double T0 = (ebar - E0) / 1.5;
+    // start from the caller's guess (the previous fit of this instance) when it
+    // has one, else from the non-relativistic <E> - m = 3T/2
+    double T0 = T_guess > 0.0 ? T_guess : (ebar - E0) / 1.5;
     double u = T0 > 1e-12 ? log(T0) : lo;
     if (u > hi_u) u = hi_u;
     double T = exp(u);
@@ -622,7 +775,7 @@ __global__ void __launch_bounds__(KX_FIN_THREADS)
     double fi = i < n ? f[(long long)b * n + i] : 0.0;
     double Ei = i < n ? E[i] : 0.0, hi = i < n ? h[i] : 0.0;
     double o[3];
-    kx_mb_fit_block(n, fi, Ei, hi, E[0], o, smem);
+    kx_mb_fit_block(n, fi, Ei, hi, E[0], 0.0, o, smem);
     if (threadIdx.x == 0) {
         out3[3 * b] = o[0];
         out3[3 * b + 1] = o[1];
@@ -804,7 +957,7 @@ __global__ void __launch_bounds__(KX_FIN_THREADS)
         tn >= sv.src[b].t_off) {
         const double fnew = in ? fb[i] : 0.0;
         double o[3];
-        kx_mb_fit_block(n, fnew, Ei, hi, E[0], o, smem);
+        kx_mb_fit_block(n, fnew, Ei, hi, E[0], T0, o, smem);
         fit[0] = o[2];
         fit[1] = o[0];
         fit[2] = o[1];
