@@ -474,7 +474,7 @@ def main():
     achieved = alg_bytes / (ms_cold * 1e-3) / 1e9
     roof = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
             "frac": achieved / hbm, "traffic": NCU_TRAFFIC["stream_n128_b4"],
-            "kernel": "k_stream32<4,2> (N=128, 4 instances per pass)",
+            "kernel": "k_stream32<2,2> (N=128, 4 instances, 2 per pass)",
             "algorithmic_bytes_per_launch": alg_bytes, "avg_launch_ms_cold_l2": ms_cold,
             "avg_launch_ms_warm_l2": ms_warm, "peak_source": src_peak}
     # streaming single-instance roofline at N=384 (tables 227 MB > L2)

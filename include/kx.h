@@ -186,7 +186,7 @@ int kx_collision_host(kx_ctx *ctx, const kx_kernel *k, int batch, const double *
  * until the process exits); it calls no cudaMalloc/cudaFree and no allocating
  * library routine.  Limits: batch <= 64 and the call's scratch (per instance:
  * the partial row sums and prepared tables) <= 8 MiB, e.g. 64 instances at
- * n = 128 or 28 at n = 512 on the FP32 path; larger requests return KX_EINVAL
+ * n = 128 or 54 at n = 512 on the FP32 path; larger requests return KX_EINVAL
  * with a message in kx_last_error.  The first call on a device looks up the
  * array's device address (cudaGetSymbolAddress); make that first call outside
  * any stream capture.  All calls share the one array: calls whose work can
@@ -286,6 +286,16 @@ int kx_time_contraction(kx_ctx *ctx, const kx_kernel *k, int batch, const double
 /* Moment-matched discrete Maxwell-Boltzmann fit used by the stopping test:
  * out_host[batch][3] = (T, ln z, L1) with L1 = sum h |f - f_MB| / sum h f. */
 int kx_mb_fit(kx_ctx *ctx, const kx_kernel *k, int batch, const double *f_dev, double *out_host);
+
+/* ----------------------------------------------------------- diagnostics */
+/* Self-check of the library's own table-driven FP64 log2 and exp (the stage
+ * kernels use them for the per-point log of f, the source envelopes and the
+ * Maxwell-Boltzmann fit; they have no counterpart in the paper).  For n
+ * arguments x_dev (device, n doubles), writes out_dev[2i] = the library's
+ * value and out_dev[2i+1] = CUDA's log2 (which = 0) or exp (which = 1) of
+ * x_dev[i].  log2 takes x >= 1e-300.  Enqueues on the context's stream.
+ * KX_EINVAL for bad arguments, KX_ECUDA if the launch fails. */
+int kx_math_check(kx_ctx *ctx, int which, int n, const double *x_dev, double *out_dev);
 
 #ifdef __cplusplus
 }

@@ -27,7 +27,7 @@ EXPORTS = (
     "kx_kernel_grid", "kx_kernel_row", "kx_collision", "kx_collision_host", "kx_step",
     "kx_solve", "kx_solve_host", "kx_mb_fit", "kx_launch_count", "kx_time_contraction",
     "kx_collision_noalloc", "kx_server_start", "kx_submit", "kx_poll", "kx_server_get_stats",
-    "kx_server_stop",
+    "kx_server_stop", "kx_math_check",
 )
 
 
@@ -124,6 +124,7 @@ def load_library(path: str = LIB_PATH):
         "kx_solve": (i, [vp, vp, i, vp, vp, i, ctypes.POINTER(SolveParams), vp, vp]),
         "kx_solve_host": (i, [vp, vp, i, vp, vp, i, ctypes.POINTER(SolveParams), vp, vp]),
         "kx_mb_fit": (i, [vp, vp, i, vp, vp]),
+        "kx_math_check": (i, [vp, i, i, vp, vp]),
         "kx_launch_count": (ctypes.c_longlong, [vp]),
         "kx_time_contraction": (i, [vp, vp, i, vp, i, ctypes.c_longlong, vp]),
         "kx_collision_noalloc": (i, [vp, vp, i, vp, vp, vp, i]),
@@ -321,6 +322,17 @@ class Context:
         rc = self.lib.kx_mb_fit(self.h, kernel.h, f2.shape[0], _dptr(f2), _ptr(out))
         if rc:
             raise self.error(rc, "kx_mb_fit")
+        return out
+
+    def math_check(self, which, x):
+        """(library value, CUDA value) of log2 (which=0) or exp (which=1) of x
+        (a CUDA float64 tensor); returns a [n, 2] tensor."""
+        import torch
+        out = torch.empty((x.numel(), 2), dtype=torch.float64, device=x.device)
+        rc = self.lib.kx_math_check(self.h, int(which), x.numel(), _dptr(x), _dptr(out))
+        if rc:
+            raise self.error(rc, "kx_math_check")
+        torch.cuda.synchronize()
         return out
 
 

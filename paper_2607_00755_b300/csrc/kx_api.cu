@@ -57,7 +57,10 @@ extern "C" int kx_create(kx_ctx **out, int device, void *cuda_stream) {
     c->h_pinned = nullptr;
     c->pinned_bytes = 0;
     c->launches = 0;
-    kx_contract_prepare();
+    if (kx_contract_prepare() != cudaSuccess) {
+        delete c;
+        return KX_ECUDA;
+    }
     kx_batch_prepare();
     *out = c;
     return KX_OK;
@@ -111,6 +114,11 @@ static int kx_pinned_reserve(kx_ctx *ctx, size_t bytes) {
 static size_t kx_align(size_t x) { return (x + 255) & ~(size_t)255; }
 
 // Scratch views of one batched evaluation, carved from a base pointer.
+// Bytes of one row partial: (hi, lo) floats on the FP32 path, (G, L) doubles else.
+static size_t kx_partial_bytes(const kx_kernel *k) {
+    return k->precision == KX_FP32 ? sizeof(float2) : sizeof(double2);
+}
+
 size_t kx_views_bytes(const kx_kernel *k, int B) {
     const size_t n = k->n, chunks = kx_chunks_per_row(k);
     size_t s = 0;
@@ -118,7 +126,8 @@ size_t kx_views_bytes(const kx_kernel *k, int B) {
     s += kx_align(sizeof(double) * B * n);           // lf64
     s += kx_align(sizeof(float2) * B * (n + 4));     // tl
     s += kx_align(sizeof(float2) * B * n);           // td
-    s += kx_align(sizeof(double2) * B * n * chunks); // partial
+    s += kx_align(kx_partial_bytes(k) * B * n * chunks); // partial
+    s += kx_align(sizeof(double) * B);               // rfmax
     s += kx_align(sizeof(int) * B);                  // flags
     s += kx_align(sizeof(double) * B);               // M2
     s += kx_align(sizeof(kx_diag) * B);              // diag
@@ -140,12 +149,14 @@ void kx_carve_views(const kx_kernel *k, int B, void *base, kx_batch_views *v) {
     v->lf64 = (double *)p; p += kx_align(sizeof(double) * B * n);
     v->tl = (float2 *)p; p += kx_align(sizeof(float2) * B * (n + 4));
     v->td = (float2 *)p; p += kx_align(sizeof(float2) * B * n);
-    v->partial = (double2 *)p; p += kx_align(sizeof(double2) * B * n * chunks);
+    v->partial = (double2 *)p; p += kx_align(kx_partial_bytes(k) * B * n * chunks);
+    v->rfmax = (double *)p; p += kx_align(sizeof(double) * B);
     v->flags = (int *)p; p += kx_align(sizeof(int) * B);
     v->M2 = (double *)p; p += kx_align(sizeof(double) * B);
     v->diag = (kx_diag *)p; p += kx_align(sizeof(kx_diag) * B);
     v->err = (int *)p; p += kx_align(sizeof(int));
     v->chunks = chunks;
+    v->tasks = kx_tasks_per_row(k);
     v->bt = v->fT = v->T = nullptr;
     v->Bpad = ((B + 63) / 64) * 64;
     if (k->precision == KX_SPLIT_TF32) {
@@ -154,6 +165,10 @@ void kx_carve_views(const kx_kernel *k, int B, void *base, kx_batch_views *v) {
         v->fT = (float *)p; p += kx_align(sizeof(float) * Bpad * k->Kpad);
         v->T = (float *)p; p += kx_align(sizeof(float) * Bpad * k->Mpad);
     }
+}
+
+cudaError_t kx_views_clear(const kx_kernel *, int, const kx_batch_views &v, cudaStream_t s) {
+    return cudaMemsetAsync(v.err, 0, sizeof(int), s);
 }
 
 // ----------------------------------------------------------------- kernel
@@ -422,7 +437,7 @@ static int kx_collision_impl(kx_ctx *ctx, const kx_kernel *k, int B, const doubl
     std::vector<double> M2(B);
     for (int b = 0; b < B; ++b) M2[b] = kx_M2(k->mass, sigma[b]);
     KX_CUDA_TRY(ctx, cudaMemcpyAsync(v.M2, M2.data(), sizeof(double) * B, cudaMemcpyHostToDevice, s));
-    KX_CUDA_TRY(ctx, cudaMemsetAsync(v.err, 0, sizeof(int), s));
+    KX_CUDA_TRY(ctx, kx_views_clear(k, B, v, s));
     KX_CUDA_TRY(ctx, kx_launch_prep(k, B, f_dev, v, nullptr, s));
     KX_CUDA_TRY(ctx, kx_launch_contract(k, B, f_dev, v, nullptr, 1, s));
     KX_CUDA_TRY(ctx, kx_launch_finalize(k, B, f_dev, v, C_dev, project, diag != nullptr, s));
@@ -593,7 +608,7 @@ static int kx_setup_run(kx_ctx *ctx, const kx_kernel *k, int B, const double *si
     KX_CUDA_TRY(ctx, cudaMemcpyAsync((void *)sv.src, sd.data(), sizeof(kx_src_dev) * B, cudaMemcpyHostToDevice, s));
     KX_CUDA_TRY(ctx, cudaMemcpyAsync((void *)sv.shapes, shapes.data(), sizeof(double) * shapes.size(), cudaMemcpyHostToDevice, s));
     KX_CUDA_TRY(ctx, cudaMemcpyAsync(run->v.M2, M2.data(), sizeof(double) * B, cudaMemcpyHostToDevice, s));
-    KX_CUDA_TRY(ctx, cudaMemsetAsync(run->v.err, 0, sizeof(int), s));
+    KX_CUDA_TRY(ctx, kx_views_clear(k, B, run->v, s));
     return KX_OK;
 }
 
@@ -803,7 +818,8 @@ extern "C" int kx_time_contraction(kx_ctx *ctx, const kx_kernel *k, int B, const
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
-    cudaError_t e = kx_launch_prep(k, B, f_dev, v, nullptr, s);
+    cudaError_t e = kx_views_clear(k, B, v, s);
+    if (e == cudaSuccess) e = kx_launch_prep(k, B, f_dev, v, nullptr, s);
     ctx->launches += 1;
     double total = 0.0;
     for (int it = 0; it < iters && e == cudaSuccess; ++it) {

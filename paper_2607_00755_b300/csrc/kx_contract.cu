@@ -10,7 +10,61 @@
 // projection (Appendix B) and, in the integrator, the Heun stage (Sec. 4.2).
 #include <math.h>
 
+#include <mutex>
+
 #include "kx_internal.cuh"
+
+__device__ double4_32a g_kx_log2_tab[256];
+__device__ double2 g_kx_exp2_tab[64];
+
+#include "kx_math.cuh"
+
+// Tables of kx_math.cuh, computed in long double on the host and copied to the
+// current device once per device.
+static cudaError_t kx_math_tables_init(int dev) {
+    static std::mutex mu;
+    static bool ready[128];
+    std::lock_guard<std::mutex> lock(mu);
+    if (dev < 0 || dev >= 128) return cudaErrorInvalidDevice;
+    if (ready[dev]) return cudaSuccess;
+    double4_32a lt[256];
+    double2 et[64];
+    for (int k = 0; k < 256; ++k) {
+        const long double F = 1.0L + (long double)k / 256.0L;   // exact in double
+        const long double l = log2l(F);
+        const double hi = (double)l;
+        lt[k] = make_double4_32a((double)F, (double)(1.0L / F), hi, (double)(l - (long double)hi));
+    }
+    for (int j = 0; j < 64; ++j) {
+        const long double t = exp2l((long double)j / 64.0L);
+        const double hi = (double)t;
+        et[j] = make_double2(hi, (double)(t - (long double)hi));
+    }
+    cudaError_t e = cudaMemcpyToSymbol(g_kx_log2_tab, lt, sizeof(lt));
+    if (e == cudaSuccess) e = cudaMemcpyToSymbol(g_kx_exp2_tab, et, sizeof(et));
+    if (e == cudaSuccess) ready[dev] = true;
+    return e;
+}
+
+__global__ void k_math_check(int which, int n, const double *__restrict__ x, double *__restrict__ out) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= n) return;
+    const double v = x[t];
+    if (which == 0) {
+        out[2 * t] = kx_log2(v);
+        out[2 * t + 1] = log2(v);
+    } else {
+        out[2 * t] = kx_exp(v);
+        out[2 * t + 1] = exp(v);
+    }
+}
+
+extern "C" int kx_math_check(kx_ctx *ctx, int which, int n, const double *x_dev, double *out_dev) {
+    if (!ctx || (which != 0 && which != 1) || n < 1 || !x_dev || !out_dev) return KX_EINVAL;
+    if (cudaSetDevice(ctx->device) != cudaSuccess) return KX_ECUDA;
+    k_math_check<<<(n + 255) / 256, 256, 0, ctx->stream>>>(which, n, x_dev, out_dev);
+    return cudaGetLastError() == cudaSuccess ? KX_OK : KX_ECUDA;
+}
 
 // ----------------------------------------------------------------- helpers
 __device__ __forceinline__ float kx_ex2(float x) {
@@ -44,6 +98,37 @@ __device__ __forceinline__ void kx_block_sum(double (&v)[K], double *smem) {
     __syncthreads();
 #pragma unroll
     for (int k = 0; k < K; ++k) v[k] = smem[k * 32];
+    __syncthreads();
+}
+
+// Column sums of K doubles over the block: every thread stores its K values,
+// warp w adds columns k = w, w + nw, ... (lane-strided, then a shuffle tree;
+// fixed order) and lane 0 stores the total at sm[K*T + k] (T = blockDim.x).
+// A column costs nw + 5 FP64 adds on one warp, against 10 per value for a
+// per-warp butterfly (FP64 is a reduced-rate pipe here).  sm holds K*T + K
+// doubles; returns after the barrier that publishes the totals.
+template <int K>
+__device__ __forceinline__ void kx_block_cols(const double (&v)[K], double *sm) {
+    const int T = blockDim.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = T >> 5;
+#pragma unroll
+    for (int k = 0; k < K; ++k) sm[k * T + tid] = v[k];
+    __syncthreads();
+    for (int k = warp; k < K; k += nw) {
+        double x = sm[k * T + lane];
+        for (int j = lane + 32; j < T; j += 32) x += sm[k * T + j];
+#pragma unroll
+        for (int off = 16; off; off >>= 1) x += __shfl_xor_sync(0xffffffffu, x, off);
+        if (lane == 0) sm[K * T + k] = x;
+    }
+    __syncthreads();
+}
+
+// Block sums of K doubles via kx_block_cols; all threads receive them.
+template <int K>
+__device__ __forceinline__ void kx_block_sum_t(double (&v)[K], double *sm) {
+    kx_block_cols<K>(v, sm);
+#pragma unroll
+    for (int k = 0; k < K; ++k) v[k] = sm[K * blockDim.x + k];
     __syncthreads();
 }
 
@@ -95,10 +180,11 @@ static inline int kx_fin_threads(int n) { return ((n + 31) / 32) * 32; }
 //             f/f_max instance-minor (fT) and as TF32 hi/lo MMA operand tiles (bt)
 //             for the tensor-core gain; zeros in the k padding up to n rounded to 32.
 // Returns the non-finite flag (block-uniform).
-// Block sum of K floats (fixed shuffle tree, deterministic); all threads get
-// the result.  smem: K*32 floats.
+// Block sum of K floats (fixed shuffle tree and warp order, deterministic); all
+// threads get the result after one barrier.  fs (K*32 floats) must not be
+// written again by the block without another barrier in between.
 template <int K>
-__device__ __forceinline__ void kx_block_sumf(float (&v)[K], float *smem) {
+__device__ __forceinline__ void kx_block_sumf_once(float (&v)[K], float *fs) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
 #pragma unroll
     for (int k = 0; k < K; ++k)
@@ -106,50 +192,86 @@ __device__ __forceinline__ void kx_block_sumf(float (&v)[K], float *smem) {
         for (int off = 16; off; off >>= 1) v[k] += __shfl_xor_sync(0xffffffffu, v[k], off);
     if (lane == 0)
 #pragma unroll
-        for (int k = 0; k < K; ++k) smem[k * 32 + warp] = v[k];
+        for (int k = 0; k < K; ++k) fs[k * 32 + warp] = v[k];
     __syncthreads();
 #pragma unroll
     for (int k = 0; k < K; ++k) {
-        float x = lane < nw ? smem[k * 32 + lane] : 0.f;
-#pragma unroll
-        for (int off = 16; off; off >>= 1) x += __shfl_xor_sync(0xffffffffu, x, off);
+        float x = fs[k * 32];
+        for (int w = 1; w < nw; ++w) x += fs[k * 32 + w];
         v[k] = x;
     }
-    __syncthreads();
 }
 
-__device__ int kx_prep_block(int n, int path, const double *__restrict__ fb,
-                             const double *__restrict__ E, const double *__restrict__ h,
-                             const kx_batch_views &v, int b, double *smem) {
-    __shared__ double s_scale[2];   // log2 f_max, 1 / f_max (computed once per block)
-    const int i = threadIdx.x;
-    double x = i < n ? fb[i] : 0.0;
-    int bad = (i < n) && !isfinite(x);
-    double fm = kx_block_max(fabs(x), smem);
-    if (threadIdx.x == 0) {
-        v.fmax[b] = fm;
-        if (path != KX_FP64) {
-            s_scale[0] = fm > 0.0 ? log2(fm) : 0.0;
-            s_scale[1] = fm > 0.0 ? 1.0 / fm : 0.0;
-        }
+// Block maximum of 64-bit keys after one barrier; us (32 entries) must not be
+// written again by the block without another barrier in between.
+__device__ __forceinline__ unsigned long long kx_block_max_key(unsigned long long x,
+                                                               unsigned long long *us) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+    for (int off = 16; off; off >>= 1) {
+        const unsigned long long y = __shfl_xor_sync(0xffffffffu, x, off);
+        x = y > x ? y : x;
     }
-    bad = kx_block_or(bad, smem);   // (barrier: publishes s_scale)
+    if (lane == 0) us[warp] = x;
+    __syncthreads();
+    unsigned long long r = us[0];
+    for (int w = 1; w < nw; ++w) r = us[w] > r ? us[w] : r;
+    return r;
+}
+
+// Key of a non-finite value in kx_block_max_key: above the bits of every
+// non-negative double up to +inf.
+#define KX_KEY_NONFINITE 0x7ff0000000000001ull
+
+// x: this thread's f value (0 for threads past n).  Called at most once per
+// kernel launch (it uses block-scope shared arrays without a trailing barrier).
+// Ei, hi: this thread's grid energy and moment weight; E0 = E_0.
+__device__ int kx_prep_block(int n, int path, double x, double Ei, double hi, double E0,
+                             const kx_batch_views &v, int b, double *smem) {
+    __shared__ unsigned long long s_key[32];
+    __shared__ float s_fit[5 * 32];
+    __shared__ double s_scale[3];   // exponent and fraction of log2 f_max, 1 / f_max
+    const int i = threadIdx.x;
+    const bool in = i < n;
+    const bool nf = in && !isfinite(x);
+    // this point's log2 parts do not depend on f_max: compute them before the
+    // first barrier
+    int ex = 0;
+    double frx = 0.0;
+    if (path != KX_FP64 && in && !nf) kx_log2_parts(x > KX_LOG_FLOOR ? x : KX_LOG_FLOOR, ex, frx);
+    const unsigned long long key =
+        kx_block_max_key(nf ? KX_KEY_NONFINITE : (unsigned long long)__double_as_longlong(fabs(x)), s_key);
+    const int bad = key == KX_KEY_NONFINITE;
+    const double fm = bad ? INFINITY : __longlong_as_double((long long)key);
+    if (threadIdx.x == 0) {
+        const double rfm = (fm > 0.0 && !bad) ? 1.0 / fm : 0.0;
+        v.fmax[b] = fm;
+        v.rfmax[b] = rfm;
+        int e = 0;
+        double fr = 0.0;
+        if (path != KX_FP64 && fm > 0.0 && !bad) kx_log2_parts(fm > KX_LOG_FLOOR ? fm : KX_LOG_FLOOR, e, fr);
+        s_scale[0] = (double)e;
+        s_scale[1] = fr;
+        s_scale[2] = rfm;
+    }
     if (path == KX_FP64) {
-        if (i < n) v.lf64[(long long)b * n + i] = log(x > KX_LOG_FLOOR ? x : KX_LOG_FLOOR);
+        if (in) v.lf64[(long long)b * n + i] = log(x > KX_LOG_FLOOR ? x : KX_LOG_FLOOR);
         return bad;
     }
-    const double lfm = s_scale[0], rfm = s_scale[1];
+    __syncthreads();   // publishes s_scale
+    const double rfm = s_scale[2];
+    // l2 = log2(max(f, floor) / f_max) from the exponents and fractions (table log2)
     double l2 = -2000.0;
-    if (i < n && fm > 0.0) l2 = log2(x > KX_LOG_FLOOR ? x : KX_LOG_FLOOR) - lfm;
+    if (in && fm > 0.0 && !bad) l2 = ((double)ex - s_scale[0]) + (frx - s_scale[1]);
+    double *dl = smem + 64 + 32;           // n <= 512 doubles after the reduction scratch
     if (path == KX_SPLIT_TF32) {
-        double *ll = smem + 64 + 32;
-        if (i < n) ll[i] = l2;
+        if (in) dl[i] = l2;
         __syncthreads();
-        if (i < n)
+        if (in)
             v.td[(long long)b * n + i] =
-                make_float2((float)l2, i + 1 < n ? (float)(ll[i + 1] - l2) : 0.f);
-        const float fp = (i < n && fm > 0.0) ? (float)(x * rfm) : 0.f;
-        if (i < n) v.fT[(size_t)i * v.Bpad + b] = fp;
+                make_float2((float)l2, i + 1 < n ? (float)(dl[i + 1] - l2) : 0.f);
+        const float fp = (in && fm > 0.0) ? (float)(x * rfm) : 0.f;
+        if (in) v.fT[(size_t)i * v.Bpad + b] = fp;
         uint32_t hb;
         asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(hb) : "f"(fp));
         const float hi = __uint_as_float(hb);
@@ -158,39 +280,33 @@ __device__ int kx_prep_block(int n, int path, const double *__restrict__ fb,
         const int off = kx_tile_offset(b & 63, i & 31);
         v.bt[t * 2048 + off] = hi;
         v.bt[(t + 1) * 2048 + off] = fp - hi;
-        __syncthreads();
         return bad;
     }
     float2 *tl = v.tl + (long long)b * (n + 4);
     float2 *td = v.td + (long long)b * n;
-    double *dl = smem + 64 + 32;           // deltas, n <= 512 doubles after the reduction scratch
-    float *fs = reinterpret_cast<float *>(smem);
-    const double Ei = i < n ? E[i] : 0.0;
-    // Reference line l2 ~ icpt + slope (E - E_0): weighted least squares (weights
-    // h f / f_max) in FP32, centred form (two passes).  Any line in E cancels
-    // exactly in the exponent differences; the fit only keeps the deviations small.
-    const float l2f = (float)l2, Ef = i < n ? (float)(Ei - E[0]) : 0.f;   // kinetic energy
-    const float w = (i < n && fm > 0.0 && x > 0.0) ? (float)h[i] * (float)(x * rfm) : 0.f;
-    float s1[3] = {w, w * Ef, w * l2f};
-    kx_block_sumf<3>(s1, fs);
+    const double K = in ? Ei - E0 : 0.0;   // kinetic energy
+    // Reference line l2 ~ icpt + slope K: weighted least squares (weights h f /
+    // f_max) in FP32, one pass.  Any line in E cancels exactly in the exponent
+    // differences; the fit only keeps the deviations small, so a poorly
+    // conditioned fit (spread of K below 1% of its rms) falls back to slope 0.
+    const float l2f = (float)l2, Kf = (float)K;
+    const float w = (in && fm > 0.0 && x > 0.0) ? (float)hi * (float)(x * rfm) : 0.f;
+    float sf[5] = {w, w * Kf, w * Kf * Kf, w * l2f, w * Kf * l2f};
+    kx_block_sumf_once<5>(sf, s_fit);
     float slope = 0.f, icpt = 0.f;
-    if (s1[0] > 0.f) {
-        const float Em = s1[1] / s1[0], lm = s1[2] / s1[0];
-        const float dE = Ef - Em;
-        float s2[2] = {w * dE * dE, w * dE * (l2f - lm)};
-        kx_block_sumf<2>(s2, fs);
-        if (s2[0] > 1e-6f * s1[0] * fmaxf(Em * Em, 1e-30f)) slope = s2[1] / s2[0];
-        icpt = lm - slope * Em;
+    if (sf[0] > 0.f) {
+        const float det = sf[0] * sf[2] - sf[1] * sf[1];
+        if (det > 1e-4f * sf[0] * sf[2]) slope = (sf[0] * sf[4] - sf[1] * sf[3]) / det;
+        icpt = (sf[3] - slope * sf[1]) / sf[0];
     }
-    const double del = l2 - ((double)icpt + (double)slope * (Ei - E[0]));
-    if (i < n) dl[i] = del;
+    const double del = l2 - ((double)icpt + (double)slope * K);
+    if (in) dl[i] = del;
     __syncthreads();
-    if (i < n) {
+    if (in) {
         tl[i] = make_float2(l2f, (float)del);
         td[i] = make_float2((float)del, i + 1 < n ? (float)(dl[i + 1] - del) : 0.f);
     }
     if (i < 4) tl[n + i] = make_float2(-2000.f, 0.f);
-    __syncthreads();
     return bad;
 }
 
@@ -200,7 +316,10 @@ __global__ void __launch_bounds__(KX_FIN_THREADS)
     __shared__ double smem[64 + 32 + 2 * KX_MAX_N];
     const int b = blockIdx.x;
     if (st && st[b].done) return;
-    int bad = kx_prep_block(n, path, f + (long long)b * n, E, h, v, b, smem);
+    const bool in = threadIdx.x < n;
+    const double x = in ? f[(long long)b * n + threadIdx.x] : 0.0;
+    int bad = kx_prep_block(n, path, x, in ? E[threadIdx.x] : 0.0, in ? h[threadIdx.x] : 0.0, E[0],
+                            v, b, smem);
     if (threadIdx.x == 0) v.flags[b] = bad;
 }
 
@@ -352,7 +471,8 @@ __global__ void __launch_bounds__(KX_T32)
     k_stream32(int n, int V, int upr, int G, int tpr, int B, const uint32_t *__restrict__ vt,
                const float4 *__restrict__ W, const uint4 *__restrict__ PK,
                const float2 *__restrict__ tl, const float2 *__restrict__ td,
-               float2 *__restrict__ partial, const kx_inst_state *__restrict__ st, int stage) {
+               float2 *__restrict__ partial, int pstride, const kx_inst_state *__restrict__ st,
+               int stage) {
     const int b0 = blockIdx.y * BP;
     __shared__ float2 s_l[BP][KX_MAX_N + 4];   // (l2_j, delta_j)
     __shared__ float2 s_d[BP][KX_MAX_N];       // (delta_j, delta_{j+1} - delta_j)
@@ -487,7 +607,7 @@ __global__ void __launch_bounds__(KX_T32)
                 l = (l + l2) + e;
             }
             if (lane == 0 && act[bb])
-                partial[((long long)(b0 + bb) * n + ti) * tpr + tg] = make_float2(h, l);
+                partial[((long long)(b0 + bb) * n + ti) * pstride + tg] = make_float2(h, l);
         }
     }
 }
@@ -495,6 +615,16 @@ __global__ void __launch_bounds__(KX_T32)
 int kx_chunks_per_row(const kx_kernel *k) {
     if (k->precision == KX_SPLIT_TF32) return 1;
     if (k->precision == KX_FP64) return (int)((k->P + KX_CH64 - 1) / KX_CH64);
+    // task partials per row, rounded up to even so that the combine reads
+    // pairs of (hi, lo) partials as 16-byte vectors
+    const int upr = kx_stream_upr(k), G = kx_stream_group(k);
+    return ((upr + G - 1) / G + 1) & ~1;
+}
+
+// Partials per row actually written (FP32 path: tasks; the combine ignores the
+// padding slot).
+int kx_tasks_per_row(const kx_kernel *k) {
+    if (k->precision != KX_FP32) return kx_chunks_per_row(k);
     const int upr = kx_stream_upr(k), G = kx_stream_group(k);
     return (upr + G - 1) / G;
 }
@@ -508,19 +638,21 @@ static void kx_stream_attr() {
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_stream32<BP, VPL>, KX_T32, 0);
 }
 
-void kx_contract_prepare() {
-    if (g_sms) return;
+cudaError_t kx_contract_prepare() {
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
+    cudaError_t e = kx_math_tables_init(dev);
+    if (e != cudaSuccess) return e;
+    if (g_sms) return cudaSuccess;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     kx_stream_attr<1, 2>();
     kx_stream_attr<1, 4>();
     kx_stream_attr<2, 2>();
     kx_stream_attr<2, 4>();
-    kx_stream_attr<4, 2>();
     kx_stream_attr<4, 4>();
     cudaGetLastError();
     g_sms = sms > 0 ? sms : 1;
+    return cudaSuccess;
 }
 
 template <int BP, int VPL>
@@ -532,7 +664,7 @@ static cudaError_t kx_launch_stream(const kx_kernel *k, int B, const kx_batch_vi
     if (e != cudaSuccess) return e;
     if (occ < 1) occ = 1;
     const int sms = g_sms > 0 ? g_sms : 148;
-    const int upr = kx_stream_upr(k), G = kx_stream_group(k), tpr = v.chunks;
+    const int upr = kx_stream_upr(k), G = kx_stream_group(k), tpr = (upr + G - 1) / G;
     const int total = k->n * tpr;
     const int wpb = KX_T32 / 32;
     const int groups = (B + BP - 1) / BP;
@@ -544,8 +676,8 @@ static cudaError_t kx_launch_stream(const kx_kernel *k, int B, const kx_batch_vi
     const float4 *W = reinterpret_cast<const float4 *>(k->d_W32);
     const uint4 *PK = reinterpret_cast<const uint4 *>(k->d_pk);
     k_stream32<BP, VPL><<<grid, KX_T32, 0, s>>>(k->n, k->V, upr, G, tpr, B, k->d_vt, W, PK, v.tl,
-                                                v.td, reinterpret_cast<float2 *>(v.partial), st,
-                                                stage);
+                                                v.td, reinterpret_cast<float2 *>(v.partial),
+                                                v.chunks, st, stage);
     return cudaGetLastError();
 }
 
@@ -559,13 +691,15 @@ cudaError_t kx_launch_contract(const kx_kernel *k, int B, const double *f, const
                                              k->d_jl, f, v.lf64, v.partial, st, stage);
         return cudaGetLastError();
     }
+    // Instances per pass: four share each table load on long rows; short rows
+    // (few units per row, latency bound) do better with two per pass and twice
+    // the blocks (measured: N = 128, four instances, 9% per Heun attempt).
     const bool small = kx_stream_vpl(n) == 2;
-    if (B >= 4) return small ? kx_launch_stream<4, 2>(k, B, v, st, stage, s)
-                             : kx_launch_stream<4, 4>(k, B, v, st, stage, s);
-    if (B >= 2) return small ? kx_launch_stream<2, 2>(k, B, v, st, stage, s)
-                             : kx_launch_stream<2, 4>(k, B, v, st, stage, s);
-    return small ? kx_launch_stream<1, 2>(k, B, v, st, stage, s)
-                 : kx_launch_stream<1, 4>(k, B, v, st, stage, s);
+    if (small) return B >= 2 ? kx_launch_stream<2, 2>(k, B, v, st, stage, s)
+                             : kx_launch_stream<1, 2>(k, B, v, st, stage, s);
+    if (B >= 4) return kx_launch_stream<4, 4>(k, B, v, st, stage, s);
+    if (B >= 2) return kx_launch_stream<2, 4>(k, B, v, st, stage, s);
+    return kx_launch_stream<1, 4>(k, B, v, st, stage, s);
 }
 
 // ---------------------------------------------------- row combine + projection
@@ -579,22 +713,46 @@ struct kx_row_out {
     int singular;
 };
 
+// sm: at least 5 * blockDim.x + 8 doubles.
 __device__ kx_row_out kx_combine_project(int n, int chunks, int path, int b, double fi, double Ei,
                                          double hi, const kx_batch_views &v, int project,
-                                         double *smem) {
-    const int i = threadIdx.x;
-    const double fm = v.fmax[b];
+                                         double *sm) {
+    const int i = threadIdx.x, T = blockDim.x;
+    const double fm = v.fmax[b], rfm = v.rfmax[b], M2 = v.M2[b];
     double G = 0.0, L = 0.0;
     if (i < n && path == KX_FP32) {
-        // double-float task partials (hi, lo), summed in double-float
-        const float2 *pp = reinterpret_cast<const float2 *>(v.partial) + ((long long)b * n + i) * chunks;
-        float hi = 0.f, lo = 0.f;
-        for (int c = 0; c < chunks; ++c) {
-            const float2 x = pp[c];
-            kx_df_add(hi, lo, x.x);
-            lo += x.y;
+        // double-float task partials (hi, lo) in pairs per 16-byte load, four
+        // independent double-float sums combined in a fixed order
+        const float4 *pp = reinterpret_cast<const float4 *>(v.partial) + ((long long)b * n + i) * (chunks >> 1);
+        const int npair = chunks >> 1, ntask = v.tasks;
+        float h0 = 0.f, l0 = 0.f, h1 = 0.f, l1 = 0.f, h2 = 0.f, l2 = 0.f, h3 = 0.f, l3 = 0.f;
+        // batches of 8 pairs: the 8 loads of a batch are in flight together
+        for (int c0 = 0; c0 < npair; c0 += 8) {
+            float4 x[8];
+#pragma unroll
+            for (int j = 0; j < 8; ++j)
+                x[j] = c0 + j < npair ? pp[c0 + j] : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+            for (int j = 0; j < 8; j += 2) {
+                // slot 2 (c0 + j) + 1 is the padding slot when the task count is odd
+                const bool p1 = 2 * (c0 + j) + 1 >= ntask, p3 = 2 * (c0 + j) + 3 >= ntask;
+                kx_df_add(h0, l0, x[j].x);
+                l0 += x[j].y;
+                kx_df_add(h1, l1, p1 ? 0.f : x[j].z);
+                l1 += p1 ? 0.f : x[j].w;
+                kx_df_add(h2, l2, x[j + 1].x);
+                l2 += x[j + 1].y;
+                kx_df_add(h3, l3, p3 ? 0.f : x[j + 1].z);
+                l3 += p3 ? 0.f : x[j + 1].w;
+            }
         }
-        G = (double)hi + (double)lo;
+        kx_df_add(h0, l0, h1);
+        l0 += l1;
+        kx_df_add(h2, l2, h3);
+        l2 += l3;
+        kx_df_add(h0, l0, h2);
+        l0 += l2;
+        G = (double)h0 + (double)l0;
     } else if (i < n) {
         const double2 *pp = v.partial + ((long long)b * n + i) * chunks;
         for (int c = 0; c < chunks; ++c) {
@@ -606,8 +764,8 @@ __device__ kx_row_out kx_combine_project(int n, int chunks, int path, int b, dou
     double Craw;
     // FP32 path: G holds sum S (f_n f_m - f_i f_t) / f_max^2; the FP64 and batched
     // paths hold the gain G and the loss rate L
-    if (path == KX_FP32) Craw = v.M2[b] * (fm * fm * G);
-    else Craw = v.M2[b] * (G - fi * L);
+    if (path == KX_FP32) Craw = M2 * (fm * fm * G);
+    else Craw = M2 * (G - fi * L);
     if (i >= n) Craw = 0.0;
     kx_row_out r;
     r.Craw = Craw;
@@ -617,47 +775,32 @@ __device__ kx_row_out kx_combine_project(int n, int chunks, int path, int b, dou
     if (!project) return r;
     double xi = 0.0;
     if (i < n && fm > 0.0) {
-        double q = fabs(fi) / fm;
+        double q = fabs(fi) * rfm;
         xi = q > KX_EPS_SUPP ? q : 0.0;
     }
-    double s[5] = {hi * xi, hi * Ei * xi, hi * Ei * Ei * xi, hi * Craw, hi * Ei * Craw};
-    // block sums of the five moments; one thread solves the 2x2 system and
-    // broadcasts (alpha, beta, singular)
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-#pragma unroll
-    for (int k = 0; k < 5; ++k)
-#pragma unroll
-        for (int off = 16; off; off >>= 1) s[k] += __shfl_xor_sync(0xffffffffu, s[k], off);
-    if (lane == 0)
-#pragma unroll
-        for (int k = 0; k < 5; ++k) smem[k * 32 + warp] = s[k];
-    __syncthreads();
-    if (warp == 0) {
-#pragma unroll
-        for (int k = 0; k < 5; ++k) {
-            double x = lane < nw ? smem[k * 32 + lane] : 0.0;
-#pragma unroll
-            for (int off = 16; off; off >>= 1) x += __shfl_xor_sync(0xffffffffu, x, off);
-            s[k] = x;
+    const double hxi = hi * xi, hEx = hxi * Ei, hC = hi * Craw;
+    const double s[5] = {hxi, hEx, hEx * Ei, hC, hC * Ei};
+    // five block sums (column form); one thread solves the 2x2 system
+    kx_block_cols<5>(s, sm);
+    if (i == 0) {
+        const double *t = sm + 5 * T;
+        const double det = t[0] * t[2] - t[1] * t[1];
+        double al = 0.0, be = 0.0, sg = 0.0;
+        if (!(det > KX_DET_GUARD * t[0] * t[2])) {
+            sg = 1.0;
+        } else {
+            const double rd = 1.0 / det;
+            al = (t[3] * t[2] - t[4] * t[1]) * rd;
+            be = (t[4] * t[0] - t[3] * t[1]) * rd;
         }
-        if (lane == 0) {
-            const double det = s[0] * s[2] - s[1] * s[1];
-            double al = 0.0, be = 0.0, sg = 0.0;
-            if (!(det > KX_DET_GUARD * s[0] * s[2])) {
-                sg = 1.0;
-            } else {
-                al = (s[3] * s[2] - s[4] * s[1]) / det;
-                be = (s[4] * s[0] - s[3] * s[1]) / det;
-            }
-            smem[160] = al;
-            smem[161] = be;
-            smem[162] = sg;
-        }
+        sm[5 * T + 5] = al;
+        sm[5 * T + 6] = be;
+        sm[5 * T + 7] = sg;
     }
     __syncthreads();
-    r.alpha = smem[160];
-    r.beta = smem[161];
-    r.singular = smem[162] != 0.0;
+    r.alpha = sm[5 * T + 5];
+    r.beta = sm[5 * T + 6];
+    r.singular = sm[5 * T + 7] != 0.0;
     __syncthreads();
     r.Cproj = Craw - xi * (r.alpha + r.beta * Ei);
     return r;
@@ -692,7 +835,7 @@ __global__ void __launch_bounds__(KX_FIN_THREADS)
     k_finalize(int n, int chunks, int path, const double *__restrict__ f,
                const double *__restrict__ E, const double *__restrict__ h, kx_batch_views v,
                double *__restrict__ Cout, int project, int want_diag) {
-    __shared__ double smem[10 * 32];
+    __shared__ double smem[5 * KX_FIN_THREADS + 8];
     const int b = blockIdx.x, i = threadIdx.x;
     double fi = 0.0, Ei = 0.0, hi = 0.0;
     if (i < n) {
@@ -718,59 +861,81 @@ cudaError_t kx_launch_finalize(const kx_kernel *k, int B, const double *f, const
 // sum h f (safeguarded Newton in u = ln T inside [ln 1e-12, ln 1e12]; <E>(T) is
 // increasing with d<E>/du = Var(E)/T), z from the number moment,
 // L1 = sum h |f - f_MB| / sum h f.  Block-wide; returns (T, ln z, L1) to all threads.
+// sm: at least 4 * blockDim.x + 8 doubles.  The Newton bookkeeping (u, its
+// bracket, the convergence test) runs on thread 0, which broadcasts 1/T and
+// the stop flag; every thread evaluates its point's weight.
 __device__ void kx_mb_fit_block(int n, double fi, double Ei, double hi, double E0, double T_guess,
-                                double *out, double *smem) {
+                                double *out, double *sm) {
     const bool in = threadIdx.x < n;
-    double s0[2] = {in ? hi * fi : 0.0, in ? hi * Ei * fi : 0.0};
-    kx_block_sum<2>(s0, smem);
-    const double N0 = s0[0];
+    const int T = blockDim.x;
+    const bool lead = threadIdx.x == 0;
+    double *ctl = sm + 4 * T;   // [0] N0, [1] 1/T, [2] stop, [3] ebar
+    const double s0[2] = {in ? hi * fi : 0.0, in ? hi * Ei * fi : 0.0};
+    kx_block_cols<2>(s0, sm);
+    double u = 0.0, lo = log(1e-12), hi_u = log(1e12), ebar = 0.0, Tc = 0.0;
+    if (lead) {
+        const double N0 = sm[2 * T];
+        ebar = sm[2 * T + 1] / N0;
+        // start from the caller's guess (the previous fit of this instance) when
+        // it has one, else from the non-relativistic <E> - m = 3T/2
+        const double T0 = T_guess > 0.0 ? T_guess : (ebar - E0) / 1.5;
+        u = T0 > 1e-12 ? log(T0) : lo;
+        if (u > hi_u) u = hi_u;
+        Tc = kx_exp(u);
+        ctl[0] = N0;
+        ctl[1] = 1.0 / Tc;
+        ctl[2] = 0.0;
+    }
+    __syncthreads();
+    const double N0 = ctl[0];
     if (!(N0 > 0.0)) {
         out[0] = 0.0;
         out[1] = 0.0;
         out[2] = INFINITY;
+        __syncthreads();
         return;
     }
-    const double ebar = s0[1] / N0;
-    double lo = log(1e-12), hi_u = log(1e12);
-    // start from the caller's guess (the previous fit of this instance) when it
-    // has one, else from the non-relativistic <E> - m = 3T/2
-    double T0 = T_guess > 0.0 ? T_guess : (ebar - E0) / 1.5;
-    double u = T0 > 1e-12 ? log(T0) : lo;
-    if (u > hi_u) u = hi_u;
-    double T = exp(u);
     for (int it = 0; it < 200; ++it) {
-        T = exp(u);
-        double wgt = in ? hi * exp(-(Ei - E0) / T) : 0.0;
-        double s[3] = {wgt, wgt * Ei, wgt * Ei * Ei};
-        kx_block_sum<3>(s, smem);
-        double mean = s[1] / s[0];
-        double var = s[2] / s[0] - mean * mean;
-        double g = mean - ebar;
-        if (g < 0.0) lo = u; else hi_u = u;
-        double un = (var > 0.0) ? u - g * T / var : 0.5 * (lo + hi_u);
-        if (!(un > lo && un < hi_u)) un = 0.5 * (lo + hi_u);
-        if (fabs(un - u) < 1e-14 * fmax(1.0, fabs(u)) || hi_u - lo < 1e-15) {
+        const double beta = ctl[1];
+        const double wgt = in ? hi * kx_exp(-(Ei - E0) * beta) : 0.0;
+        const double s[3] = {wgt, wgt * Ei, wgt * Ei * Ei};
+        kx_block_cols<3>(s, sm);
+        if (lead) {
+            // g = <E> - ebar = gs / s0 and Var(E) = vs / s0^2, so the Newton step
+            // in u = ln T, -g T / Var(E), is -gs s0 T / vs (one division)
+            const double *t = sm + 3 * T;
+            const double gs = t[1] - ebar * t[0];
+            const double vs = t[2] * t[0] - t[1] * t[1];
+            if (gs < 0.0) lo = u; else hi_u = u;
+            double un = (vs > 0.0) ? u - gs * t[0] * Tc / vs : 0.5 * (lo + hi_u);
+            if (!(un > lo && un < hi_u)) un = 0.5 * (lo + hi_u);
+            const bool stop = fabs(un - u) < 1e-14 * fmax(1.0, fabs(u)) || hi_u - lo < 1e-15;
             u = un;
-            break;
+            Tc = kx_exp(u);
+            ctl[1] = 1.0 / Tc;
+            ctl[2] = stop ? 1.0 : 0.0;
         }
-        u = un;
+        __syncthreads();
+        const bool stop = ctl[2] != 0.0;
+        if (stop) break;
     }
-    T = exp(u);
-    double w = in ? exp(-(Ei - E0) / T) : 0.0;
+    // final weights at T = exp(u): f_MB = N0 w / sum h w, L1 = sum h |f - f_MB| / N0
+    const double beta = ctl[1];
+    const double w = in ? kx_exp(-(Ei - E0) * beta) : 0.0;
     double s1[1] = {in ? hi * w : 0.0};
-    kx_block_sum<1>(s1, smem);
-    double fmb = N0 * w / s1[0];
+    kx_block_sum_t<1>(s1, sm);
+    const double fmb = N0 * w / s1[0];
     double s2[1] = {in ? hi * fabs(fi - fmb) : 0.0};
-    kx_block_sum<1>(s2, smem);
-    out[0] = T;
-    out[1] = log(N0 / s1[0]) + E0 / T;
+    kx_block_sum_t<1>(s2, sm);
+    out[0] = 1.0 / beta;
+    out[1] = log(N0 / s1[0]) + E0 * beta;
     out[2] = s2[0] / N0;
 }
 
 __global__ void __launch_bounds__(KX_FIN_THREADS)
     k_mbfit(int n, const double *__restrict__ f, const double *__restrict__ E,
             const double *__restrict__ h, double *__restrict__ out3) {
-    __shared__ double smem[3 * 32];
+    __shared__ double smem[4 * KX_FIN_THREADS + 8];
     const int b = blockIdx.x, i = threadIdx.x;
     double fi = i < n ? f[(long long)b * n + i] : 0.0;
     double Ei = i < n ? E[i] : 0.0, hi = i < n ? h[i] : 0.0;
@@ -801,7 +966,9 @@ __global__ void __launch_bounds__(KX_FIN_THREADS)
     k_stage(int n, int chunks, int path, const double *__restrict__ E,
             const double *__restrict__ h, kx_batch_views v, kx_step_views sv, int stage,
             long long max_attempts) {
-    __shared__ double smem[64 + 32 + 2 * KX_MAX_N];
+    __shared__ double smem[5 * KX_FIN_THREADS + 8];
+    __shared__ unsigned long long s_key[32];
+    __shared__ double s_env[KX_MAX_SRC];
     const int b = blockIdx.x, i = threadIdx.x;
     kx_inst_state *st = sv.st + b;
     if (st->done) return;
@@ -813,16 +980,28 @@ __global__ void __launch_bounds__(KX_FIN_THREADS)
     // Every thread takes its copy of the instance state here, before the first
     // block barrier: thread 0 rewrites the state at the end of the stage, and a
     // warp that read it after that write could disagree with the others on
-    // block-uniform decisions (the MB check, which holds barriers).
+    // block-uniform decisions (the MB check, which holds barriers).  (Thread 0's
+    // early write of h_try and last in stage 1 is read only by stage 2.)
     const double t = st->t, t_end = st->t_end, h_state = st->h, h_try_state = st->h_try;
     const int last_state = st->last;
     const long long steps0 = st->steps, rejects0 = st->rejects;
     const double l1_0 = st->l1, T0 = st->T, lnz0 = st->lnz;
     const bool in = i < n;
-    const double Ei = in ? E[i] : 0.0, hi = in ? h[i] : 0.0;
     double *fb = sv.f + (long long)b * n;
     double *k1 = sv.k1 + (long long)b * n;
     double *fp = sv.fp + (long long)b * n;
+    // loads that do not depend on the reductions, issued up front
+    const double Ei = in ? E[i] : 0.0, hi = in ? h[i] : 0.0, E0 = E[0];
+    const double f0 = in ? fb[i] : 0.0;
+    const double fpv = (in && stage == 2) ? fp[i] : 0.0;
+    const double k1v = (in && stage == 2) ? k1[i] : 0.0;
+    const kx_src_dev &src = sv.src[b];
+    const int n_src = src.n_src;
+    double shp[KX_MAX_SRC];
+#pragma unroll
+    for (int k = 0; k < KX_MAX_SRC; ++k)
+        shp[k] = (in && k < n_src) ? sv.shapes[src.shape_off + (long long)k * n + i] : 0.0;
+    const int flag_in = v.flags[b];
     double htry;
     if (stage == 1) {
         htry = h_state;
@@ -835,7 +1014,6 @@ __global__ void __launch_bounds__(KX_FIN_THREADS)
             htry = t_end - t;
             last = 1;
         }
-        __syncthreads();
         if (threadIdx.x == 0) {
             st->h_try = htry;
             st->last = last;
@@ -843,31 +1021,31 @@ __global__ void __launch_bounds__(KX_FIN_THREADS)
     } else {
         htry = h_try_state;
     }
-    const double fcur = in ? (stage == 1 ? fb[i] : fp[i]) : 0.0;
+    // source envelopes, one exp per source on the last warp (off the critical
+    // path of warp 0, which solves the projection system)
+    const double tS = stage == 1 ? t : t + htry;
+    {
+        const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, lastw = (blockDim.x >> 5) - 1;
+        if (w == lastw && lane < n_src) {
+            const int k = lane;
+            s_env[k] = tS >= src.t_on[k] ? src.rate[k] * kx_exp(-(tS - src.t_on[k]) / src.tau[k]) : 0.0;
+        }
+    }
+    const double fcur = stage == 1 ? f0 : fpv;
     kx_row_out r = kx_combine_project(n, chunks, path, b, fcur, Ei, hi, v, sv.project, smem);
     const double C = sv.project ? r.Cproj : r.Craw;
-    const double tS = stage == 1 ? t : t + htry;
-    // source envelopes: one exp per source, shared by the block
-    __shared__ double s_env[KX_MAX_SRC];
-    const kx_src_dev &src = sv.src[b];
-    if (threadIdx.x < src.n_src) {
-        const int k = threadIdx.x;
-        s_env[k] = tS >= src.t_on[k] ? src.rate[k] * exp(-(tS - src.t_on[k]) / src.tau[k]) : 0.0;
-    }
-    __syncthreads();
+    __syncthreads();   // publishes s_env (also when the projection is off)
     double Si = 0.0;
-    if (in)
-        for (int k = 0; k < src.n_src; ++k) Si += s_env[k] * sv.shapes[src.shape_off + (long long)k * n + i];
+#pragma unroll
+    for (int k = 0; k < KX_MAX_SRC; ++k)
+        if (k < n_src) Si += s_env[k] * shp[k];
     const double kv = in ? C + Si : 0.0;
-    const double f0 = in ? fb[i] : 0.0;
-    __syncthreads();
     if (stage == 1) {
         const double fpi = f0 + htry * kv;
-        int bad = in && !isfinite(fpi);
-        int neg = in && fpi < 0.0;
-        bad = kx_block_or(bad | v.flags[b], smem);
-        neg = kx_block_or(neg, smem);
-        if (bad) {
+        // one reduction for both flags: 2 = non-finite, 1 = negative
+        const unsigned long long key = kx_block_max_key(
+            (in && !isfinite(fpi)) || flag_in ? 2ull : ((in && fpi < 0.0) ? 1ull : 0ull), s_key);
+        if (key == 2ull) {
             if (threadIdx.x == 0) {
                 st->status = KX_ENONFINITE;
                 st->done = 1;
@@ -875,7 +1053,7 @@ __global__ void __launch_bounds__(KX_FIN_THREADS)
             }
             return;
         }
-        if (neg) {
+        if (key == 1ull) {
             if (threadIdx.x == 0) {
                 st->evals += 1;
                 if (sv.fixed) {
@@ -898,21 +1076,21 @@ __global__ void __launch_bounds__(KX_FIN_THREADS)
             fp[i] = fpi;
         }
         if (threadIdx.x == 0) st->evals += 1;
-        __syncthreads();
-        int bad2 = kx_prep_block(n, path, fp, E, h, v, b, smem);
+        int bad2 = kx_prep_block(n, path, in ? fpi : 0.0, Ei, hi, E0, v, b, smem);
         if (threadIdx.x == 0) v.flags[b] = bad2;
         return;
     }
-    // stage 2
-    const double fpi = in ? fp[i] : 0.0;
-    const double fci = f0 + 0.5 * htry * ((in ? k1[i] : 0.0) + kv);
-    double e = in ? fabs(fci - fpi) / (sv.atol + sv.rtol * fabs(fci)) : 0.0;
-    int bad = in && !isfinite(fci);
-    int neg = in && fci < 0.0;
-    bad = kx_block_or(bad | v.flags[b], smem);
-    neg = kx_block_or(neg, smem);
-    double err = kx_block_max(e, smem);
-    if (bad) {
+    // stage 2: one reduction for the flags and the error norm (keys ordered
+    // non-finite > negative > the bits of err >= 0)
+    const double fci = f0 + 0.5 * htry * (k1v + kv);
+    const double e = in ? fabs(fci - fpv) / (sv.atol + sv.rtol * fabs(fci)) : 0.0;
+    const unsigned long long kneg = KX_KEY_NONFINITE - 1ull;   // bits of +inf
+    unsigned long long key;
+    if ((in && !isfinite(fci)) || flag_in) key = KX_KEY_NONFINITE;
+    else if (in && fci < 0.0) key = kneg;
+    else key = (unsigned long long)__double_as_longlong(e);
+    key = kx_block_max_key(key, s_key);
+    if (key == KX_KEY_NONFINITE) {
         if (threadIdx.x == 0) {
             st->status = KX_ENONFINITE;
             st->done = 1;
@@ -920,44 +1098,31 @@ __global__ void __launch_bounds__(KX_FIN_THREADS)
         }
         return;
     }
-    int accept;
-    double hnext;
-    if (sv.fixed) {
-        if (neg) {
-            if (threadIdx.x == 0) {
-                st->status = KX_ENEG;
-                st->done = 1;
-                st->evals += 1;
-            }
-            return;
+    const bool neg = key == kneg;
+    if (sv.fixed && neg) {
+        if (threadIdx.x == 0) {
+            st->status = KX_ENEG;
+            st->done = 1;
+            st->evals += 1;
         }
-        accept = 1;
-        hnext = htry;
-    } else if (neg) {
-        accept = 0;
-        hnext = 0.5 * htry;
-    } else {
-        double fac = err > 0.0 ? 0.9 / sqrt(err) : 5.0;
-        if (fac > 5.0) fac = 5.0;
-        if (fac < 0.2) fac = 0.2;
-        hnext = htry * fac;
-        accept = err <= 1.0;
+        return;
     }
+    const double err = neg ? INFINITY : __longlong_as_double((long long)key);
+    const int accept = sv.fixed ? 1 : (!neg && err <= 1.0);
     double tn = t;
     if (accept) {
         if (in) fb[i] = fci;
         tn = last_state ? t_end : t + htry;
     }
-    __syncthreads();
+    const double fnew = accept ? fci : f0;
     long long steps = steps0 + (accept ? 1 : 0);
     long long rejects = rejects0 + (accept ? 0 : 1);
     int done = 0, converged = 0;
     double fit[3] = {l1_0, T0, lnz0};
     if (accept && sv.check_every > 0 && sv.l1_tol > 0.0 && steps % sv.check_every == 0 &&
-        tn >= sv.src[b].t_off) {
-        const double fnew = in ? fb[i] : 0.0;
+        tn >= src.t_off) {
         double o[3];
-        kx_mb_fit_block(n, fnew, Ei, hi, E[0], T0, o, smem);
+        kx_mb_fit_block(n, in ? fnew : 0.0, Ei, hi, E0, T0, o, smem);
         fit[0] = o[2];
         fit[1] = o[0];
         fit[2] = o[1];
@@ -975,6 +1140,18 @@ __global__ void __launch_bounds__(KX_FIN_THREADS)
         }
     }
     if (threadIdx.x == 0) {
+        // step-size controller (one thread: only the state keeps h)
+        double hnext;
+        if (sv.fixed) {
+            hnext = htry;
+        } else if (neg) {
+            hnext = 0.5 * htry;
+        } else {
+            double fac = err > 0.0 ? 0.9 / sqrt(err) : 5.0;
+            if (fac > 5.0) fac = 5.0;
+            if (fac < 0.2) fac = 0.2;
+            hnext = htry * fac;
+        }
         st->t = tn;
         st->h = hnext;
         st->err = err;
@@ -991,7 +1168,7 @@ __global__ void __launch_bounds__(KX_FIN_THREADS)
         }
     }
     // prepare the next attempt's contraction input (f_new or the restored f)
-    int bad2 = kx_prep_block(n, path, fb, E, h, v, b, smem);
+    int bad2 = kx_prep_block(n, path, in ? fnew : 0.0, Ei, hi, E0, v, b, smem);
     if (threadIdx.x == 0) v.flags[b] = bad2;
 }
 

@@ -110,11 +110,13 @@ struct kx_batch_views {
     double *lf64;          // [B][n]       FP64 path: ln max(f, floor)
     float2 *tl;            // [B][n + 4]   FP32 path: (l2_j, delta_j), l2 = log2(max(f, floor)/f_max)
     float2 *td;            // [B][n]       FP32 path: (delta_j, delta_{j+1} - delta_j)
-    double2 *partial;      // [B][n][chunks]
+    double2 *partial;      // [B][n][chunks]  (FP32 path: float2 (hi, lo) task partials, [B][n][2 chunks])
+    double *rfmax;         // [B]          1 / f_max
     int *flags;            // [B] non-finite flags
     double *M2;            // [B] |M|^2 per instance
     kx_diag *diag;         // [B]
     int chunks;
+    int tasks;             // FP32 path: task partials per row (<= chunks)
     // batched (split TF32) path
     float *bt;             // [Bpad/64][Kpad/32][hi, lo][2048]: f/f_max as TF32 hi/lo MMA operand tiles
     float *fT;             // [Kpad][Bpad]: f/f_max, instance-minor
@@ -134,7 +136,10 @@ __host__ __device__ __forceinline__ int kx_tile_offset(int r, int k) {
 }
 
 int kx_chunks_per_row(const kx_kernel *k);
-void kx_contract_prepare();  // one-time launch-shape queries (call outside stream capture)
+int kx_tasks_per_row(const kx_kernel *k);
+// Zero the per-call flags of freshly carved views (before the first launch).
+cudaError_t kx_views_clear(const kx_kernel *k, int B, const kx_batch_views &v, cudaStream_t s);
+cudaError_t kx_contract_prepare();  // one-time launch-shape queries (call outside stream capture)
 size_t kx_views_bytes(const kx_kernel *k, int B);
 void kx_carve_views(const kx_kernel *k, int B, void *base, kx_batch_views *v);
 

@@ -380,3 +380,34 @@ def test_mb_fit_matches_oracle(ctx, kx):
         assert abs(out[b, 0] / r["T"] - 1) < 1e-12
         assert abs(out[b, 1] - r["ln_z"]) < 1e-10
         assert abs(out[b, 2] - r["l1"]) < 1e-10 * max(1.0, r["l1"])
+
+
+# ------------------------------------------------- table-driven log2 / exp ---
+def test_table_log2_exp_against_cuda_and_libm(ctx, kx):
+    """The stage kernels' own FP64 log2 and exp (Tang's table-driven methods)
+    against CUDA's log2/exp and the host libm: absolute error within 2 ulp of
+    the result's magnitude (log2), relative error within 2 ulp (exp, normal
+    range), exact special cases."""
+    import torch
+    rng = np.random.default_rng(11)
+    x = np.concatenate([10.0 ** rng.uniform(-300, 300, 20000), 1.0 + rng.uniform(-1e-3, 1e-3, 2000),
+                        2.0 ** np.arange(-996, 1000, 7.0), [1.0, 2.0, 0.5, 1e-300, 1.7e308]])
+    out = ctx.math_check(0, torch.as_tensor(x, device="cuda")).cpu().numpy()
+    ref = np.log2(x)
+    tol = 2 * np.spacing(np.maximum(np.abs(ref), 1.0))
+    assert np.all(np.abs(out[:, 0] - ref) <= tol)
+    assert np.all(np.abs(out[:, 0] - out[:, 1]) <= tol)
+    assert out[np.flatnonzero(x == 1.0)[0], 0] == 0.0
+    y = np.concatenate([rng.uniform(-745, 709.7, 20000), rng.uniform(-1, 1, 2000) * 1e-3,
+                        [0.0, -0.0, 1.0, -1.0, 709.78, -708.39, -745.1, -746.0, 710.0]])
+    out = ctx.math_check(1, torch.as_tensor(y, device="cuda")).cpu().numpy()
+    ref = np.exp(y)
+    normal = (ref > 2.3e-308) & np.isfinite(ref)
+    rel = np.abs(out[normal, 0] - ref[normal]) / ref[normal]
+    assert rel.max() <= 4.5e-16, rel.max()
+    sub = ref <= 2.3e-308
+    assert np.all(np.abs(out[sub, 0] - ref[sub]) <= 1e-322)
+    assert np.all(np.abs(out[normal, 0] - out[normal, 1]) / ref[normal] <= 4.5e-16)
+    assert out[-1, 0] == np.inf and out[-2, 0] == 0.0 and out[y.size - 9, 0] == 1.0
+    nan = ctx.math_check(1, torch.as_tensor(np.array([np.nan]), device="cuda")).cpu().numpy()
+    assert np.isnan(nan[0, 0])

@@ -68,9 +68,9 @@ def test_noalloc_rejects_requests_above_its_fixed_scratch(env):
     kx, ctx, torch = env
     q = ki.log_grid(512, 1e-3, 1e2)
     k = ctx.build_kernel(q, precision=kx.FP32)
-    f = torch.zeros((40, 512), dtype=torch.float64, device="cuda")
+    f = torch.zeros((62, 512), dtype=torch.float64, device="cuda")
     C = torch.empty_like(f)
-    rc = call_noalloc(kx, ctx, k, f, np.ones(40), C, 1)
+    rc = call_noalloc(kx, ctx, k, f, np.ones(62), C, 1)
     assert rc == kx.EINVAL
     assert b"8 MiB" in ctx.lib.kx_last_error(ctx.h)
     f = torch.zeros((65, 8), dtype=torch.float64, device="cuda")
