@@ -34,8 +34,8 @@ METRIC = "collision-term evals/s & solves/s vs plain FP64 path; p50/p99 solve la
 UNIT = "evals/s"
 L2_FLUSH_BYTES = 512 << 20     # > 126 MB L2
 # DRAM bytes (read + write) per launch from one ncu capture of the current kernels
-# (profiles/k_stream32_n128_batch4.md, profiles/k_stream32_n384_single.md); set to
-# None whenever those kernels change.
+# (profiles/k_stream32_n128_batch4.md, profiles/k_stream32_n384_single.md); None
+# whenever those kernels have changed since the capture.
 NCU_TRAFFIC = {"stream_n128_b4": None, "stream_n384": None}
 SOLVE = dict(t_end=1e5, h0=1e-3, rtol=1e-6, l1_tol=1e-3, check_every=10, max_attempts=2_000_000)
 
@@ -157,12 +157,9 @@ def run_contraction_only(args):
     k = ctx.build_kernel(q, precision=prec)
     f = torch.as_tensor(ki.batch_bimodal(np.random.default_rng(7), q, args.batch), device="cuda")
     ms = ctx.time_contraction(k, f, iters=args.iters, flush_bytes=L2_FLUSH_BYTES)
-    n = args.n
-    U = n * n * (n + 1) // 2
-    V = sum((n - a + 3) // 4 for a in range(n))
-    alg = (8 * U + 4 * V) if prec == kx.FP32 else 18 * U + 4 * U // n
+    alg = k.info()["stream_bytes"]
     hbm, src = peaks()
-    print(json.dumps({"kernel": "contraction", "n": n, "batch": args.batch,
+    print(json.dumps({"kernel": "contraction", "n": args.n, "batch": args.batch,
                       "precision": args.precision, "avg_ms": ms,
                       "algorithmic_bytes": alg, "achieved_gbs": alg / (ms * 1e-3) / 1e9,
                       "frac_of_" + src + "_hbm": alg / (ms * 1e-3) / 1e9 / hbm,
@@ -462,15 +459,14 @@ def main():
 
     # ---- roofline of the dominant kernel (FP32 contraction) --------------------
     hbm, src_peak = peaks()
-    n = q.size
-    U = n * n * (n + 1) // 2
-    V = sum((n - a + 3) // 4 for a in range(n))
     kk = ctx.build_kernel(q, precision=kx.FP32)
     fdev = torch.as_tensor(f0, device="cuda")
     ms_cold = ctx.time_contraction(kk, fdev, iters=30, flush_bytes=L2_FLUSH_BYTES)
     ms_warm = ctx.time_contraction(kk, fdev, iters=30, flush_bytes=0)
+    # algorithmic bytes: the compacted tables one launch streams (36 B per kept
+    # 4-element vector + task table), read once for all instances
+    alg_bytes = kk.info()["stream_bytes"]
     kk.release()
-    alg_bytes = 8 * U + 4 * V
     achieved = alg_bytes / (ms_cold * 1e-3) / 1e9
     roof = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
             "frac": achieved / hbm, "traffic": NCU_TRAFFIC["stream_n128_b4"],
@@ -482,10 +478,8 @@ def main():
     k384 = ctx.build_kernel(q384, precision=kx.FP32)
     f384 = torch.as_tensor(ki.batch_bimodal(np.random.default_rng(7), q384, 1), device="cuda")
     ms384 = ctx.time_contraction(k384, f384, iters=30, flush_bytes=L2_FLUSH_BYTES)
+    b384 = k384.info()["stream_bytes"]
     k384.release()
-    U384 = 384 * 384 * 385 // 2
-    V384 = sum((384 - a + 3) // 4 for a in range(384))
-    b384 = 8 * U384 + 4 * V384
     roof384 = {"bound": "hbm", "achieved": b384 / (ms384 * 1e-3) / 1e9, "peak": hbm,
                "unit": "GB/s", "frac": b384 / (ms384 * 1e-3) / 1e9 / hbm,
                "traffic": NCU_TRAFFIC["stream_n384"],

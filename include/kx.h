@@ -132,6 +132,11 @@ typedef struct {
     long long nonzero_elements;  /* elements inside the kinematic support */
     long long tensor_bytes;      /* device bytes of the kernel tables */
     double build_ms;             /* device time of the build */
+    long long stream_bytes;      /* table bytes one contraction launch reads: FP32 path = 36 B per
+                                    4-element vector inside the kinematic support (W, packed
+                                    (j_L, omega), (n, m0)) + the task table; FP64 path = 18 B per
+                                    (i, n <= m) element + 4 B per pair; split path = the TF32
+                                    operand tiles + the loss list */
 } kx_kernel_info;
 
 /* ------------------------------------------------------------- context */
@@ -186,7 +191,7 @@ int kx_collision_host(kx_ctx *ctx, const kx_kernel *k, int batch, const double *
  * until the process exits); it calls no cudaMalloc/cudaFree and no allocating
  * library routine.  Limits: batch <= 64 and the call's scratch (per instance:
  * the partial row sums and prepared tables) <= 8 MiB, e.g. 64 instances at
- * n = 128 or 54 at n = 512 on the FP32 path; larger requests return KX_EINVAL
+ * n = 512 on the FP32 path or 15 on the FP64 path; larger requests return KX_EINVAL
  * with a message in kx_last_error.  The first call on a device looks up the
  * array's device address (cudaGetSymbolAddress); make that first call outside
  * any stream capture.  All calls share the one array: calls whose work can

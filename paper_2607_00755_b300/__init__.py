@@ -74,7 +74,7 @@ class KernelInfo(ctypes.Structure):
     _fields_ = [("n", ctypes.c_int), ("n_mu", ctypes.c_int), ("measure", ctypes.c_int),
                 ("precision", ctypes.c_int), ("unique_elements", ctypes.c_longlong),
                 ("nonzero_elements", ctypes.c_longlong), ("tensor_bytes", ctypes.c_longlong),
-                ("build_ms", ctypes.c_double)]
+                ("build_ms", ctypes.c_double), ("stream_bytes", ctypes.c_longlong)]
 
 
 class ServerConfig(ctypes.Structure):

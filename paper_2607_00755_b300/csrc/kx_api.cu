@@ -119,6 +119,11 @@ static size_t kx_partial_bytes(const kx_kernel *k) {
     return k->precision == KX_FP32 ? sizeof(float2) : sizeof(double2);
 }
 
+// Partials per instance: the FP32 path's task slots, else rows x chunks.
+static size_t kx_partial_slots(const kx_kernel *k) {
+    return k->precision == KX_FP32 ? (size_t)k->tslots : (size_t)k->n * kx_chunks_per_row(k);
+}
+
 size_t kx_views_bytes(const kx_kernel *k, int B) {
     const size_t n = k->n, chunks = kx_chunks_per_row(k);
     size_t s = 0;
@@ -126,7 +131,7 @@ size_t kx_views_bytes(const kx_kernel *k, int B) {
     s += kx_align(sizeof(double) * B * n);           // lf64
     s += kx_align(sizeof(float2) * B * (n + 4));     // tl
     s += kx_align(sizeof(float2) * B * n);           // td
-    s += kx_align(kx_partial_bytes(k) * B * n * chunks); // partial
+    s += kx_align(kx_partial_bytes(k) * B * kx_partial_slots(k)); // partial
     s += kx_align(sizeof(double) * B);               // rfmax
     s += kx_align(sizeof(int) * B);                  // flags
     s += kx_align(sizeof(double) * B);               // M2
@@ -149,14 +154,14 @@ void kx_carve_views(const kx_kernel *k, int B, void *base, kx_batch_views *v) {
     v->lf64 = (double *)p; p += kx_align(sizeof(double) * B * n);
     v->tl = (float2 *)p; p += kx_align(sizeof(float2) * B * (n + 4));
     v->td = (float2 *)p; p += kx_align(sizeof(float2) * B * n);
-    v->partial = (double2 *)p; p += kx_align(kx_partial_bytes(k) * B * n * chunks);
+    v->partial = (double2 *)p; p += kx_align(kx_partial_bytes(k) * B * kx_partial_slots(k));
     v->rfmax = (double *)p; p += kx_align(sizeof(double) * B);
     v->flags = (int *)p; p += kx_align(sizeof(int) * B);
     v->M2 = (double *)p; p += kx_align(sizeof(double) * B);
     v->diag = (kx_diag *)p; p += kx_align(sizeof(kx_diag) * B);
     v->err = (int *)p; p += kx_align(sizeof(int));
     v->chunks = chunks;
-    v->tasks = kx_tasks_per_row(k);
+    v->rtask = k->d_rtask;
     v->bt = v->fT = v->T = nullptr;
     v->Bpad = ((B + 63) / 64) * 64;
     if (k->precision == KX_SPLIT_TF32) {
@@ -209,8 +214,8 @@ static void kx_free_kernel(kx_kernel *k) {
     if (!k) return;
     cudaSetDevice(k->device);
     void *ptrs[] = {k->d_p, k->d_E, k->d_dp, k->d_dE, k->d_h, k->d_pair, k->d_W64,
-                    k->d_om64, k->d_jl, k->d_vt, k->d_W32, k->d_pk, k->d_Atile, k->d_lel,
-                    k->d_lrow, k->d_lgrp};
+                    k->d_om64, k->d_jl, k->d_vt, k->d_W32, k->d_pk, k->d_roff, k->d_rtask,
+                    k->d_task, k->d_Atile, k->d_lel, k->d_lrow, k->d_lgrp};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     delete k;
@@ -296,16 +301,27 @@ extern "C" int kx_build_kernel(kx_ctx *ctx, const kx_grid_desc *d, kx_kernel **o
     KX_ALLOC(k->d_W64, (size_t)n * k->P);
     KX_ALLOC(k->d_om64, (size_t)n * k->P);
     KX_ALLOC(k->d_jl, (size_t)n * k->P);
+    uint32_t *d_vt_all = nullptr;   // FP32 build only: global vector list and row positions
+    int *d_pos = nullptr, *d_rcnt = nullptr;
     if (k->precision == KX_FP32) {
-        KX_ALLOC(k->d_vt, k->V);
-        KX_ALLOC(k->d_W32, (size_t)n * k->V * 4);
-        KX_ALLOC(k->d_pk, (size_t)n * k->V * 4);
+        long long tmp = 0;
+        if ((rc = kx_dev_alloc(ctx, &d_vt_all, k->V, &tmp)) != KX_OK ||
+            (rc = kx_dev_alloc(ctx, &d_pos, (size_t)n * k->V, &tmp)) != KX_OK ||
+            (rc = kx_dev_alloc(ctx, &d_rcnt, n, &tmp)) != KX_OK) {
+            cudaFree(d_vt_all);
+            cudaFree(d_pos);
+            kx_free_kernel(k);
+            return rc;
+        }
     }
 #undef KX_ALLOC
     unsigned long long *d_cnt = nullptr;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     auto fail = [&](const char *what, cudaError_t e) {
         if (d_cnt) cudaFree(d_cnt);
+        cudaFree(d_vt_all);
+        cudaFree(d_pos);
+        cudaFree(d_rcnt);
         if (e0) cudaEventDestroy(e0);
         if (e1) cudaEventDestroy(e1);
         kx_free_kernel(k);
@@ -320,8 +336,8 @@ extern "C" int kx_build_kernel(kx_ctx *ctx, const kx_grid_desc *d, kx_kernel **o
     KX_CHK("upload grid", cudaMemcpyAsync(k->d_dE, k->dE.data(), sizeof(double) * n, cudaMemcpyHostToDevice, s));
     KX_CHK("upload grid", cudaMemcpyAsync(k->d_h, k->h.data(), sizeof(double) * n, cudaMemcpyHostToDevice, s));
     KX_CHK("upload pairs", cudaMemcpyAsync(k->d_pair, pair.data(), sizeof(uint32_t) * k->P, cudaMemcpyHostToDevice, s));
-    if (k->d_vt)
-        KX_CHK("upload vectors", cudaMemcpyAsync(k->d_vt, vt.data(), sizeof(uint32_t) * k->V, cudaMemcpyHostToDevice, s));
+    if (d_vt_all)
+        KX_CHK("upload vectors", cudaMemcpyAsync(d_vt_all, vt.data(), sizeof(uint32_t) * k->V, cudaMemcpyHostToDevice, s));
     kx_gl_nodes gl;
     memset(&gl, 0, sizeof(gl));
     kx_gauss_legendre(k->n_mu, &gl);
@@ -331,7 +347,59 @@ extern "C" int kx_build_kernel(kx_ctx *ctx, const kx_grid_desc *d, kx_kernel **o
     KX_CHK("memset", cudaMemsetAsync(d_cnt, 0, sizeof(unsigned long long), s));
     KX_CHK("event", cudaEventRecord(e0, s));
     KX_CHK("build", kx_launch_build_fp64(k, gl, s));
-    if (k->precision == KX_FP32) KX_CHK("pack", kx_launch_pack_fp32(k, s));
+    if (k->precision == KX_FP32) {
+        // rows compacted to the vectors inside the kinematic support
+        KX_CHK("support", kx_launch_keep_scan(k, d_vt_all, k->V, d_pos, d_rcnt, s));
+        std::vector<int> rcnt(n);
+        KX_CHK("copy", cudaMemcpyAsync(rcnt.data(), d_rcnt, sizeof(int) * n, cudaMemcpyDeviceToHost, s));
+        KX_CHK("sync", cudaStreamSynchronize(s));
+        std::vector<int> roff(n + 1, 0);
+        for (int i = 0; i < n; ++i) roff[i + 1] = roff[i] + rcnt[i];
+        k->Vt = roff[n];
+        // streaming work: units of 32 x vpl vectors of a row, tasks of G units;
+        // G from the total units so that every SM gets work on small grids
+        k->vpl = n <= 160 ? 2 : 4;
+        const int unit = 32 * k->vpl;
+        long long units = 0;
+        for (int i = 0; i < n; ++i) units += (rcnt[i] + unit - 1) / unit;
+        long long g = units / (2LL * 148 * 16);
+        k->G = (int)(g < 1 ? 1 : (g > 8 ? 8 : g));
+        std::vector<int2> rtask(n);
+        std::vector<int4> task;
+        int slots = 0;
+        for (int i = 0; i < n; ++i) {
+            const int upr = (rcnt[i] + unit - 1) / unit;
+            const int tpr = (upr + k->G - 1) / k->G;
+            rtask[i] = make_int2(slots, tpr);
+            for (int t = 0; t < tpr; ++t)
+                task.push_back(make_int4(i, t * k->G, std::min(upr, (t + 1) * k->G), slots + t));
+            slots += (tpr + 1) & ~1;   // even, for paired 16-byte reads of the partials
+        }
+        k->ntask = (int)task.size();
+        k->tslots = slots > 0 ? slots : 2;
+        long long *by2 = &k->bytes;
+        if ((rc = kx_dev_alloc(ctx, &k->d_vt, k->Vt, by2)) != KX_OK ||
+            (rc = kx_dev_alloc(ctx, &k->d_W32, (size_t)k->Vt * 4, by2)) != KX_OK ||
+            (rc = kx_dev_alloc(ctx, &k->d_pk, (size_t)k->Vt * 4, by2)) != KX_OK ||
+            (rc = kx_dev_alloc(ctx, &k->d_roff, n + 1, by2)) != KX_OK ||
+            (rc = kx_dev_alloc(ctx, &k->d_rtask, n, by2)) != KX_OK ||
+            (rc = kx_dev_alloc(ctx, &k->d_task, task.size(), by2)) != KX_OK) {
+            cudaFree(d_cnt);
+            cudaFree(d_vt_all);
+            cudaFree(d_pos);
+            cudaFree(d_rcnt);
+            cudaEventDestroy(e0);
+            cudaEventDestroy(e1);
+            kx_free_kernel(k);
+            return rc;
+        }
+        KX_CHK("upload rows", cudaMemcpyAsync(k->d_roff, roff.data(), sizeof(int) * (n + 1), cudaMemcpyHostToDevice, s));
+        KX_CHK("upload rows", cudaMemcpyAsync(k->d_rtask, rtask.data(), sizeof(int2) * n, cudaMemcpyHostToDevice, s));
+        if (!task.empty())
+            KX_CHK("upload tasks", cudaMemcpyAsync(k->d_task, task.data(), sizeof(int4) * task.size(), cudaMemcpyHostToDevice, s));
+        KX_CHK("pack", kx_launch_pack_fp32(k, d_vt_all, k->V, d_pos, s));
+        ctx->launches += 1;
+    }
     KX_CHK("event", cudaEventRecord(e1, s));
     KX_CHK("count", kx_launch_count_nnz(k, d_cnt, s));
     ctx->launches += k->precision == KX_FP32 ? 3 : 2;
@@ -343,6 +411,9 @@ extern "C" int kx_build_kernel(kx_ctx *ctx, const kx_grid_desc *d, kx_kernel **o
     k->build_ms = ms;
     k->nnz = (long long)cnt;
     cudaFree(d_cnt);
+    cudaFree(d_vt_all);
+    cudaFree(d_pos);
+    cudaFree(d_rcnt);
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
 #undef KX_CHK
@@ -353,6 +424,12 @@ extern "C" int kx_build_kernel(kx_ctx *ctx, const kx_grid_desc *d, kx_kernel **o
             return rc2;
         }
     }
+    if (k->precision == KX_FP32)
+        k->stream_bytes = k->Vt * 36 + (long long)k->ntask * 16 + (long long)(n + 1) * 4;
+    else if (k->precision == KX_FP64)
+        k->stream_bytes = (long long)n * k->P * 18 + k->P * 4;
+    else
+        k->stream_bytes = (long long)k->Mpad * k->Kpad * 8 + k->nnz * 8;
     if (k->precision != KX_FP64) {
         // the FP32 and batched paths read only their own tables
         cudaFree(k->d_W64); k->d_W64 = nullptr;
@@ -383,6 +460,7 @@ extern "C" int kx_kernel_get_info(const kx_kernel *k, kx_kernel_info *info) {
     info->nonzero_elements = k->nnz;
     info->tensor_bytes = k->bytes;
     info->build_ms = k->build_ms;
+    info->stream_bytes = k->stream_bytes;
     return KX_OK;
 }
 

@@ -95,33 +95,92 @@ cudaError_t kx_launch_build_fp64(const kx_kernel *k, const kx_gl_nodes &gl, cuda
     return cudaGetLastError();
 }
 
-// FP32 streaming layout: row i holds V 4-element vectors; vector v covers
-// (n, m0..m0+3) of one n-segment (segments padded to a multiple of 4 with W = 0).
-// pk = j_L << 23 | round(omega 2^23) (omega quantised to 2^-23; omega that
-// rounds to 1 is stored as (j_L + 1, 0)).
-__global__ void k_pack_fp32(int N, long long P, int V, const uint32_t *__restrict__ vt,
+// Kinematic support per 4-element vector (n, m0..m0+3) of the global vector
+// list, one block per row i: pos[i][v] = index of vector v among row i's
+// vectors with an element inside the support (W != 0), or -1; cnt[i] = their
+// number.  Block-wide exclusive scan in tiles of blockDim vectors.
+__global__ void k_keep_scan(int N, long long P, int V, const uint32_t *__restrict__ vt,
+                            const double *__restrict__ W64, int *__restrict__ pos,
+                            int *__restrict__ cnt) {
+    __shared__ int s_warp[32];
+    __shared__ int s_base;
+    const int i = blockIdx.x, tid = threadIdx.x, lane = tid & 31, w = tid >> 5, nw = blockDim.x >> 5;
+    if (tid == 0) s_base = 0;
+    __syncthreads();
+    for (int v0 = 0; v0 < V; v0 += blockDim.x) {
+        const int v = v0 + tid;
+        int keep = 0;
+        if (v < V) {
+            const uint32_t t = vt[v];
+            const int n = t & 0xffff, m0 = t >> 16;
+            const long long base = (long long)i * P + kx_pair_base(n, N);
+            for (int c = 0; c < 4; ++c) {
+                const int m = m0 + c;
+                if (m < N && W64[base + (m - n)] != 0.0) keep = 1;
+            }
+        }
+        const unsigned bal = __ballot_sync(0xffffffffu, keep);
+        const int wpre = __popc(bal & ((1u << lane) - 1u));
+        if (lane == 0) s_warp[w] = __popc(bal);
+        __syncthreads();
+        if (w == 0) {
+            int x = lane < nw ? s_warp[lane] : 0;
+            for (int off = 1; off < 32; off <<= 1) {
+                const int y = __shfl_up_sync(0xffffffffu, x, off);
+                if (lane >= off) x += y;
+            }
+            if (lane < nw) s_warp[lane] = x;   // inclusive
+        }
+        __syncthreads();
+        const int wbase = w ? s_warp[w - 1] : 0;
+        if (v < V) pos[(long long)i * V + v] = keep ? s_base + wbase + wpre : -1;
+        __syncthreads();
+        if (tid == 0) s_base += s_warp[nw - 1];
+        __syncthreads();
+    }
+    if (tid == 0) cnt[i] = s_base;
+}
+
+cudaError_t kx_launch_keep_scan(const kx_kernel *k, const uint32_t *d_vt_all, int V, int *d_pos,
+                                int *d_cnt, cudaStream_t s) {
+    k_keep_scan<<<k->n, 1024, 0, s>>>(k->n, k->P, V, d_vt_all, k->d_W64, d_pos, d_cnt);
+    return cudaGetLastError();
+}
+
+// FP32 streaming tables, rows compacted to their kept vectors.  Kept vector v
+// of row i (index k = pos[i][v] in the row) goes to d_roff[i] + k with its
+// (n, m0) in d_vt and its four elements (W as float, pk = j_L << 23 |
+// round(omega 2^23)) in slots rotated by r = (k >> 2) & 3: slot s holds
+// element m0 + ((s + r) & 3).  The streaming kernel reads row vector k in lane
+// k mod 32, so at each slot the lanes of a warp touch grid points spread over
+// all shared-memory banks.  omega quantised to 2^-23; omega that rounds to 1 is
+// stored as (j_L + 1, 0).  Elements outside the support (and past the row end)
+// have W = 0 and pk = 0.
+__global__ void k_pack_fp32(int N, long long P, int V, const uint32_t *__restrict__ vt_all,
+                            const int *__restrict__ pos, const int *__restrict__ roff,
                             const double *__restrict__ W64, const double *__restrict__ om64,
-                            const uint16_t *__restrict__ jl, float *__restrict__ W32,
-                            uint32_t *__restrict__ pk) {
-    int v = blockIdx.x * blockDim.x + threadIdx.x;
-    int i = blockIdx.y;
+                            const uint16_t *__restrict__ jl, uint32_t *__restrict__ vt,
+                            float *__restrict__ W32, uint32_t *__restrict__ pk) {
+    const int v = blockIdx.x * blockDim.x + threadIdx.x;
+    const int i = blockIdx.y;
     if (v >= V) return;
-    uint32_t t = vt[v];
-    int n = t & 0xffff, m0 = t >> 16;
-    long long out = ((long long)i * V + v) * 4;
-    long long base = (long long)i * P + kx_pair_base(n, N);
-    // slot s of vector v holds element m0 + ((s + r) & 3), r = (v >> 2) & 3: the
-    // streaming kernel reads vector v in lane v mod 32, so at each slot the
-    // lanes of a warp touch grid points spread over all shared-memory banks
-    const int r = (v >> 2) & 3;
+    const int kk = pos[(long long)i * V + v];
+    if (kk < 0) return;
+    const uint32_t t = vt_all[v];
+    const int n = t & 0xffff, m0 = t >> 16;
+    const long long dst = (long long)roff[i] + kk;
+    vt[dst] = t;
+    const long long out = dst * 4;
+    const long long base = (long long)i * P + kx_pair_base(n, N);
+    const int r = (kk >> 2) & 3;
     for (int sl = 0; sl < 4; ++sl) {
         const int c = (sl + r) & 3;
-        int m = m0 + c;
+        const int m = m0 + c;
         float w = 0.f;
         uint32_t word = 0u;
         if (m < N) {
-            long long e = base + (m - n);
-            double wd = W64[e];
+            const long long e = base + (m - n);
+            const double wd = W64[e];
             if (wd != 0.0) {
                 w = (float)wd;
                 uint32_t j = jl[e];
@@ -140,11 +199,12 @@ __global__ void k_pack_fp32(int N, long long P, int V, const uint32_t *__restric
     }
 }
 
-cudaError_t kx_launch_pack_fp32(const kx_kernel *k, cudaStream_t s) {
+cudaError_t kx_launch_pack_fp32(const kx_kernel *k, const uint32_t *d_vt_all, int V,
+                                const int *d_pos, cudaStream_t s) {
     dim3 block(128);
-    dim3 grid((unsigned)((k->V + block.x - 1) / block.x), k->n);
-    k_pack_fp32<<<grid, block, 0, s>>>(k->n, k->P, k->V, k->d_vt, k->d_W64, k->d_om64, k->d_jl,
-                                       k->d_W32, k->d_pk);
+    dim3 grid((unsigned)((V + block.x - 1) / block.x), k->n);
+    k_pack_fp32<<<grid, block, 0, s>>>(k->n, k->P, V, d_vt_all, d_pos, k->d_roff, k->d_W64,
+                                       k->d_om64, k->d_jl, k->d_vt, k->d_W32, k->d_pk);
     return cudaGetLastError();
 }
 

@@ -439,40 +439,23 @@ __device__ __forceinline__ void kx_df_add(float &hi, float &lo, float x) {
     lo += e;
 }
 
-// Vectors per lane of a streaming unit: short rows use smaller units so that
-// every SM gets work.
-static int kx_stream_vpl(int n) { return n <= 160 ? 2 : 4; }
-
-static int kx_stream_upr(const kx_kernel *k) {
-    const int unit = 32 * kx_stream_vpl(k->n);
-    return (k->V + unit - 1) / unit;
-}
-
-// Units per task: large grids group up to 8 consecutive units of a row into one
-// task so that the cross-lane reduction and the row partial are paid once per
-// task; small grids keep one unit per task to give every warp work.  Depends on
-// the grid size only, so an instance's arithmetic does not depend on the batch
-// it is launched with.
-static int kx_stream_group(const kx_kernel *k) {
-    const long long units = (long long)k->n * kx_stream_upr(k);
-    long long g = units / (2LL * 148 * 16);
-    return (int)(g < 1 ? 1 : (g > 8 ? 8 : g));
-}
-
-// Persistent streaming contraction.  A unit is one warp-sized slice of a row
-// (32 x VPL consecutive 4-element vectors of row i); a task is G consecutive
-// units of one row.  Warps take tasks in a fixed round-robin order and prefetch
-// the next unit's tables into registers while computing the current one.  Each
-// lane sums its unit's terms in FP32 and adds the unit sum into a double-float
-// accumulator; at the end of the task the warp reduces the double-float sums
-// (fixed shuffle tree) and lane 0 writes the task's (hi, lo) row partial.
+// Persistent streaming contraction over the compacted FP32 tables.  A unit is
+// one warp-sized slice of a row (32 x VPL consecutive kept vectors of row i); a
+// task is up to G consecutive units of one row (the task table, built with the
+// kernel, fixes the work split: an instance's arithmetic does not depend on
+// the batch it is launched with).  Warps take tasks in a fixed round-robin
+// order and prefetch the next unit's tables into registers while computing the
+// current one.  Each lane sums its unit's terms in FP32 and adds the unit sum
+// into a double-float accumulator; at the end of the task the warp reduces the
+// double-float sums (fixed shuffle tree) and lane 0 writes the task's (hi, lo)
+// partial into the task's slot.
 template <int BP, int VPL>
 __global__ void __launch_bounds__(KX_T32)
-    k_stream32(int n, int V, int upr, int G, int tpr, int B, const uint32_t *__restrict__ vt,
-               const float4 *__restrict__ W, const uint4 *__restrict__ PK,
-               const float2 *__restrict__ tl, const float2 *__restrict__ td,
-               float2 *__restrict__ partial, int pstride, const kx_inst_state *__restrict__ st,
-               int stage) {
+    k_stream32(int n, int ntask, const int4 *__restrict__ task, const int *__restrict__ roff, int B,
+               const uint32_t *__restrict__ vt, const float4 *__restrict__ W,
+               const uint4 *__restrict__ PK, const float2 *__restrict__ tl,
+               const float2 *__restrict__ td, float2 *__restrict__ partial, int pstride,
+               const kx_inst_state *__restrict__ st, int stage) {
     const int b0 = blockIdx.y * BP;
     __shared__ float2 s_l[BP][KX_MAX_N + 4];   // (l2_j, delta_j)
     __shared__ float2 s_d[BP][KX_MAX_N];       // (delta_j, delta_{j+1} - delta_j)
@@ -497,27 +480,26 @@ __global__ void __launch_bounds__(KX_T32)
 
     const int lane = threadIdx.x & 31;
     // element offset of each slot of this lane's vectors (slot rotation of the
-    // packed tables: vector v's slot s holds m0 + ((s + ((v >> 2) & 3)) & 3),
-    // and v mod 32 == lane)
+    // packed tables: row vector k's slot s holds m0 + ((s + ((k >> 2) & 3)) & 3),
+    // and k mod 32 == lane)
     const int rot = (lane >> 2) & 3;
     const int so[4] = {rot, (1 + rot) & 3, (2 + rot) & 3, (3 + rot) & 3};
     const int wpb = blockDim.x >> 5;
-    const int ntask = n * tpr;
     const int stride = gridDim.x * wpb;
-    int task = blockIdx.x * wpb + (threadIdx.x >> 5);
+    int tk = blockIdx.x * wpb + (threadIdx.x >> 5);
     float4 w[VPL];
     uint4 pk[VPL];
     uint32_t nv[VPL];
-    auto load_unit = [&](int i, int c) {
-        const float4 *Wr = W + (long long)i * V;
-        const uint4 *Pr = PK + (long long)i * V;
+    // the unit in the prefetch registers: row i (kept vectors rb .. rb + rl), unit c
+    int i = 0, c = 0, cend = 0, slot = 0, rb = 0, rl = 0;
+    auto load_unit = [&]() {
 #pragma unroll
         for (int e = 0; e < VPL; ++e) {
             const int v = c * (32 * VPL) + e * 32 + lane;
-            if (v < V) {
-                w[e] = kx_ld_stream(Wr + v);
-                pk[e] = kx_ld_stream(Pr + v);
-                nv[e] = __ldg(vt + v);
+            if (v < rl) {
+                w[e] = kx_ld_stream(W + rb + v);
+                pk[e] = kx_ld_stream(PK + rb + v);
+                nv[e] = __ldg(vt + rb + v);
             } else {
                 w[e] = make_float4(0.f, 0.f, 0.f, 0.f);
                 pk[e] = make_uint4(0u, 0u, 0u, 0u);
@@ -525,16 +507,18 @@ __global__ void __launch_bounds__(KX_T32)
             }
         }
     };
-    // the unit in the prefetch registers: row i, chunk c, of task `task`
-    int i = 0, c = 0, cend = 0;
-    if (task < ntask) {
-        i = task / tpr;
-        const int g = task - i * tpr;
-        c = g * G;
-        cend = min(c + G, upr);
-        load_unit(i, c);
-    }
-    while (task < ntask) {
+    auto start_task = [&]() {
+        const int4 d = __ldg(task + tk);
+        i = d.x;
+        c = d.y;
+        cend = d.z;
+        slot = d.w;
+        rb = __ldg(roff + i);
+        rl = __ldg(roff + i + 1) - rb;
+        load_unit();
+    };
+    if (tk < ntask) start_task();
+    while (tk < ntask) {
         float hi[BP], lo[BP], di[BP];
 #pragma unroll
         for (int bb = 0; bb < BP; ++bb) {
@@ -542,7 +526,7 @@ __global__ void __launch_bounds__(KX_T32)
             lo[bb] = 0.f;
             di[bb] = s_l[bb][i].y;
         }
-        const int ti = i, tg = task - i * tpr;
+        const int tslot = slot;
         for (;;) {
             float4 wc[VPL];
             uint4 pc[VPL];
@@ -553,20 +537,14 @@ __global__ void __launch_bounds__(KX_T32)
                 pc[e] = pk[e];
                 nc[e] = nv[e];
             }
-            // advance to the next unit (this task's next chunk, or the next task)
-            bool more = c + 1 < cend;
+            // advance to the next unit (this task's next unit, or the next task)
+            const bool more = c + 1 < cend;
             if (more) {
                 ++c;
-                load_unit(i, c);
+                load_unit();
             } else {
-                task += stride;
-                if (task < ntask) {
-                    i = task / tpr;
-                    const int g = task - i * tpr;
-                    c = g * G;
-                    cend = min(c + G, upr);
-                    load_unit(i, c);
-                }
+                tk += stride;
+                if (tk < ntask) start_task();
             }
             float acc[BP];
 #pragma unroll
@@ -601,13 +579,12 @@ __global__ void __launch_bounds__(KX_T32)
             for (int off = 16; off; off >>= 1) {
                 const float h2 = __shfl_xor_sync(0xffffffffu, h, off);
                 const float l2 = __shfl_xor_sync(0xffffffffu, l, off);
-                float s, e;
-                kx_two_sum(h, h2, s, e);
-                h = s;
+                float sm, e;
+                kx_two_sum(h, h2, sm, e);
+                h = sm;
                 l = (l + l2) + e;
             }
-            if (lane == 0 && act[bb])
-                partial[((long long)(b0 + bb) * n + ti) * pstride + tg] = make_float2(h, l);
+            if (lane == 0 && act[bb]) partial[(long long)(b0 + bb) * pstride + tslot] = make_float2(h, l);
         }
     }
 }
@@ -615,18 +592,7 @@ __global__ void __launch_bounds__(KX_T32)
 int kx_chunks_per_row(const kx_kernel *k) {
     if (k->precision == KX_SPLIT_TF32) return 1;
     if (k->precision == KX_FP64) return (int)((k->P + KX_CH64 - 1) / KX_CH64);
-    // task partials per row, rounded up to even so that the combine reads
-    // pairs of (hi, lo) partials as 16-byte vectors
-    const int upr = kx_stream_upr(k), G = kx_stream_group(k);
-    return ((upr + G - 1) / G + 1) & ~1;
-}
-
-// Partials per row actually written (FP32 path: tasks; the combine ignores the
-// padding slot).
-int kx_tasks_per_row(const kx_kernel *k) {
-    if (k->precision != KX_FP32) return kx_chunks_per_row(k);
-    const int upr = kx_stream_upr(k), G = kx_stream_group(k);
-    return (upr + G - 1) / G;
+    return k->tslots;   // FP32 path: partial slots per instance
 }
 
 // SM count, queried once (kx_contract_prepare) before any stream capture.
@@ -664,8 +630,7 @@ static cudaError_t kx_launch_stream(const kx_kernel *k, int B, const kx_batch_vi
     if (e != cudaSuccess) return e;
     if (occ < 1) occ = 1;
     const int sms = g_sms > 0 ? g_sms : 148;
-    const int upr = kx_stream_upr(k), G = kx_stream_group(k), tpr = (upr + G - 1) / G;
-    const int total = k->n * tpr;
+    const int total = k->ntask;
     const int wpb = KX_T32 / 32;
     const int groups = (B + BP - 1) / BP;
     int blocks = (total + wpb - 1) / wpb;
@@ -675,9 +640,10 @@ static cudaError_t kx_launch_stream(const kx_kernel *k, int B, const kx_batch_vi
     dim3 grid(blocks, groups);
     const float4 *W = reinterpret_cast<const float4 *>(k->d_W32);
     const uint4 *PK = reinterpret_cast<const uint4 *>(k->d_pk);
-    k_stream32<BP, VPL><<<grid, KX_T32, 0, s>>>(k->n, k->V, upr, G, tpr, B, k->d_vt, W, PK, v.tl,
-                                                v.td, reinterpret_cast<float2 *>(v.partial),
-                                                v.chunks, st, stage);
+    k_stream32<BP, VPL><<<grid, KX_T32, 0, s>>>(k->n, k->ntask, k->d_task, k->d_roff, B, k->d_vt,
+                                                W, PK, v.tl, v.td,
+                                                reinterpret_cast<float2 *>(v.partial), v.chunks,
+                                                st, stage);
     return cudaGetLastError();
 }
 
@@ -694,7 +660,7 @@ cudaError_t kx_launch_contract(const kx_kernel *k, int B, const double *f, const
     // Instances per pass: four share each table load on long rows; short rows
     // (few units per row, latency bound) do better with two per pass and twice
     // the blocks (measured: N = 128, four instances, 9% per Heun attempt).
-    const bool small = kx_stream_vpl(n) == 2;
+    const bool small = k->vpl == 2;
     if (small) return B >= 2 ? kx_launch_stream<2, 2>(k, B, v, st, stage, s)
                              : kx_launch_stream<1, 2>(k, B, v, st, stage, s);
     if (B >= 4) return kx_launch_stream<4, 4>(k, B, v, st, stage, s);
@@ -723,8 +689,11 @@ __device__ kx_row_out kx_combine_project(int n, int chunks, int path, int b, dou
     if (i < n && path == KX_FP32) {
         // double-float task partials (hi, lo) in pairs per 16-byte load, four
         // independent double-float sums combined in a fixed order
-        const float4 *pp = reinterpret_cast<const float4 *>(v.partial) + ((long long)b * n + i) * (chunks >> 1);
-        const int npair = chunks >> 1, ntask = v.tasks;
+        // row i's task partials: slots rt.x .. rt.x + rt.y - 1 of instance b
+        // (rt.x even, so pairs of slots are 16-byte aligned)
+        const int2 rt = v.rtask[i];
+        const float4 *pp = reinterpret_cast<const float4 *>(v.partial) + (((long long)b * chunks + rt.x) >> 1);
+        const int ntask = rt.y, npair = (ntask + 1) >> 1;
         float h0 = 0.f, l0 = 0.f, h1 = 0.f, l1 = 0.f, h2 = 0.f, l2 = 0.f, h3 = 0.f, l3 = 0.f;
         // batches of 8 pairs: the 8 loads of a batch are in flight together
         for (int c0 = 0; c0 < npair; c0 += 8) {

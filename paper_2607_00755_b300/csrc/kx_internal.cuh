@@ -43,10 +43,18 @@ struct kx_kernel {
     double *d_W64;
     double *d_om64;
     uint16_t *d_jl;
-    // FP32 tables [n][4V]
-    uint32_t *d_vt;      // [V]: n | m0 << 16 (first m of the vector)
-    float *d_W32;
-    uint32_t *d_pk;      // j_L << 23 | round(omega 2^23)
+    // FP32 tables: per row i only the 4-element vectors with an element inside
+    // the kinematic support, rows concatenated (row i at d_roff[i] .. d_roff[i+1])
+    uint32_t *d_vt;      // [Vt]: n | m0 << 16 (first m of the vector)
+    float *d_W32;        // [Vt][4], slots rotated by (k >> 2) & 3, k = index in the row
+    uint32_t *d_pk;      // [Vt][4]: j_L << 23 | round(omega 2^23), same slots
+    int *d_roff;         // [n + 1] first kept vector of each row
+    int2 *d_rtask;       // [n]: (first partial slot, tasks) of each row
+    int4 *d_task;        // [ntask]: (row, first unit, end unit, partial slot)
+    long long Vt;        // kept vectors, all rows
+    int vpl, G;          // vectors per lane of a unit, units per task
+    int ntask;           // streaming tasks
+    int tslots;          // partial slots per instance (row task counts rounded up to even)
     // batched (split TF32) tables
     int Mpad;            // n^2 rows (i, n) padded to a multiple of 128
     int Kpad;            // n columns (m) padded to a multiple of 32
@@ -56,6 +64,7 @@ struct kx_kernel {
     int *d_lgrp;         // [n][n + 1] first element of each bracket group j_L in row i
     long long nnz;
     long long bytes;
+    long long stream_bytes;   // table bytes one contraction launch reads
     double build_ms;
 };
 
@@ -110,13 +119,13 @@ struct kx_batch_views {
     double *lf64;          // [B][n]       FP64 path: ln max(f, floor)
     float2 *tl;            // [B][n + 4]   FP32 path: (l2_j, delta_j), l2 = log2(max(f, floor)/f_max)
     float2 *td;            // [B][n]       FP32 path: (delta_j, delta_{j+1} - delta_j)
-    double2 *partial;      // [B][n][chunks]  (FP32 path: float2 (hi, lo) task partials, [B][n][2 chunks])
+    double2 *partial;      // [B][n][chunks]  (FP32 path: float2 (hi, lo) task partials, [B][chunks])
+    const int2 *rtask;     // FP32 path: [n] (first partial slot, tasks) per row
     double *rfmax;         // [B]          1 / f_max
     int *flags;            // [B] non-finite flags
     double *M2;            // [B] |M|^2 per instance
     kx_diag *diag;         // [B]
-    int chunks;
-    int tasks;             // FP32 path: task partials per row (<= chunks)
+    int chunks;            // partials per row (FP32 path: partial slots per instance)
     // batched (split TF32) path
     float *bt;             // [Bpad/64][Kpad/32][hi, lo][2048]: f/f_max as TF32 hi/lo MMA operand tiles
     float *fT;             // [Kpad][Bpad]: f/f_max, instance-minor
@@ -136,7 +145,6 @@ __host__ __device__ __forceinline__ int kx_tile_offset(int r, int k) {
 }
 
 int kx_chunks_per_row(const kx_kernel *k);
-int kx_tasks_per_row(const kx_kernel *k);
 // Zero the per-call flags of freshly carved views (before the first launch).
 cudaError_t kx_views_clear(const kx_kernel *k, int B, const kx_batch_views &v, cudaStream_t s);
 cudaError_t kx_contract_prepare();  // one-time launch-shape queries (call outside stream capture)
@@ -144,7 +152,10 @@ size_t kx_views_bytes(const kx_kernel *k, int B);
 void kx_carve_views(const kx_kernel *k, int B, void *base, kx_batch_views *v);
 
 cudaError_t kx_launch_build_fp64(const kx_kernel *k, const kx_gl_nodes &gl, cudaStream_t s);
-cudaError_t kx_launch_pack_fp32(const kx_kernel *k, cudaStream_t s);
+cudaError_t kx_launch_keep_scan(const kx_kernel *k, const uint32_t *d_vt_all, int V, int *d_pos,
+                                int *d_cnt, cudaStream_t s);
+cudaError_t kx_launch_pack_fp32(const kx_kernel *k, const uint32_t *d_vt_all, int V,
+                                const int *d_pos, cudaStream_t s);
 cudaError_t kx_launch_count_nnz(const kx_kernel *k, unsigned long long *d_count, cudaStream_t s);
 
 // prep: f -> (fmax, lf64 | sf, sld); mode selects path

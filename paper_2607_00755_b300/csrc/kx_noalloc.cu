@@ -23,8 +23,8 @@
 
 // Maximum scratch of one call: 8 MiB.  A call needs the same scratch as
 // kx_collision's arena (per instance: partial row sums plus the prepared
-// distribution tables); this covers, e.g., 64 instances at n = 128 on the FP32
-// path, or 54 instances at n = 512 on the FP32 path.
+// distribution tables); this covers, e.g., 64 instances at n = 512 on the FP32
+// path, or 15 instances at n = 512 on the FP64 path.
 #define KX_NOALLOC_SCRATCH_BYTES (8u << 20)
 #define KX_NOALLOC_MAX_BATCH 64
 #define KX_NOALLOC_MAX_DEVICES 64

@@ -67,10 +67,16 @@ def test_noalloc_matches_kx_collision_twice(env, precision):
 def test_noalloc_rejects_requests_above_its_fixed_scratch(env):
     kx, ctx, torch = env
     q = ki.log_grid(512, 1e-3, 1e2)
+    # the FP32 path fits 64 instances at the largest grid; the FP64 path's
+    # per-chunk partials (about 0.55 MB per instance at n = 512) do not
     k = ctx.build_kernel(q, precision=kx.FP32)
-    f = torch.zeros((62, 512), dtype=torch.float64, device="cuda")
+    f = torch.zeros((64, 512), dtype=torch.float64, device="cuda")
+    assert call_noalloc(kx, ctx, k, f, np.ones(64), torch.empty_like(f), 1) == kx.OK
+    k.release()
+    k = ctx.build_kernel(q, precision=kx.FP64)
+    f = torch.zeros((20, 512), dtype=torch.float64, device="cuda")
     C = torch.empty_like(f)
-    rc = call_noalloc(kx, ctx, k, f, np.ones(62), C, 1)
+    rc = call_noalloc(kx, ctx, k, f, np.ones(20), C, 1)
     assert rc == kx.EINVAL
     assert b"8 MiB" in ctx.lib.kx_last_error(ctx.h)
     f = torch.zeros((65, 8), dtype=torch.float64, device="cuda")
