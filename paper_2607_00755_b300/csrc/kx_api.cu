@@ -353,22 +353,24 @@ extern "C" int kx_build_kernel(kx_ctx *ctx, const kx_grid_desc *d, kx_kernel **o
         std::vector<int> rcnt(n);
         KX_CHK("copy", cudaMemcpyAsync(rcnt.data(), d_rcnt, sizeof(int) * n, cudaMemcpyDeviceToHost, s));
         KX_CHK("sync", cudaStreamSynchronize(s));
-        std::vector<int> roff(n + 1, 0);
-        for (int i = 0; i < n; ++i) roff[i + 1] = roff[i] + rcnt[i];
-        k->Vt = roff[n];
-        // streaming work: units of 32 x vpl vectors of a row, tasks of G units;
-        // G from the total units so that every SM gets work on small grids
+        // streaming work: units of 32 x vpl vectors of a row (64 on grids up to
+        // 160 points, 128 above), tasks of G units; rows padded to whole units
+        // (zero weights), so every unit is a full, 16-byte aligned block of each
+        // table; G from the total units so that every SM gets work on small grids
         k->vpl = n <= 160 ? 2 : 4;
         const int unit = 32 * k->vpl;
+        std::vector<int> roff(n + 1, 0);
+        for (int i = 0; i < n; ++i) roff[i + 1] = roff[i] + (rcnt[i] + unit - 1) / unit * unit;
+        k->Vt = roff[n];
         long long units = 0;
-        for (int i = 0; i < n; ++i) units += (rcnt[i] + unit - 1) / unit;
+        for (int i = 0; i < n; ++i) units += (roff[i + 1] - roff[i] + unit - 1) / unit;
         long long g = units / (2LL * 148 * 16);
-        k->G = (int)(g < 1 ? 1 : (g > 8 ? 8 : g));
+        k->G = (int)(g < 1 ? 1 : (g > 16 ? 16 : g));
         std::vector<int2> rtask(n);
         std::vector<int4> task;
         int slots = 0;
         for (int i = 0; i < n; ++i) {
-            const int upr = (rcnt[i] + unit - 1) / unit;
+            const int upr = (roff[i + 1] - roff[i] + unit - 1) / unit;
             const int tpr = (upr + k->G - 1) / k->G;
             rtask[i] = make_int2(slots, tpr);
             for (int t = 0; t < tpr; ++t)
@@ -393,6 +395,10 @@ extern "C" int kx_build_kernel(kx_ctx *ctx, const kx_grid_desc *d, kx_kernel **o
             kx_free_kernel(k);
             return rc;
         }
+        // padding vectors stay zero: (n, m0) = (0, 0), W = 0, pk = 0
+        KX_CHK("clear", cudaMemsetAsync(k->d_vt, 0, sizeof(uint32_t) * k->Vt, s));
+        KX_CHK("clear", cudaMemsetAsync(k->d_W32, 0, sizeof(float) * k->Vt * 4, s));
+        KX_CHK("clear", cudaMemsetAsync(k->d_pk, 0, sizeof(uint32_t) * k->Vt * 4, s));
         KX_CHK("upload rows", cudaMemcpyAsync(k->d_roff, roff.data(), sizeof(int) * (n + 1), cudaMemcpyHostToDevice, s));
         KX_CHK("upload rows", cudaMemcpyAsync(k->d_rtask, rtask.data(), sizeof(int2) * n, cudaMemcpyHostToDevice, s));
         if (!task.empty())

@@ -21,45 +21,10 @@
 #define KX_ATILE 4096              // floats per A tile: 128 rows x 32 k
 #define KX_BTILE 2048              // floats per B tile: 64 rows x 32 k
 #define KX_GEMM_SMEM (65536 + 32768 + 64)
-#define KX_WAIT_CYCLES (4ll << 30)  // bounded mbarrier wait, about 2 s
 #define KX_LOSS_WARPS 16           // warps per loss block (one shared instance table)
 
-// ------------------------------------------------------------ PTX helpers
-__device__ __forceinline__ uint32_t kx_smem_u32(const void *p) {
-    return (uint32_t)__cvta_generic_to_shared(p);
-}
-__device__ __forceinline__ void kx_mbar_init(uint32_t bar, uint32_t count) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
-}
-__device__ __forceinline__ void kx_mbar_expect_tx(uint32_t bar, uint32_t bytes) {
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
-                 : "memory");
-}
-__device__ __forceinline__ bool kx_mbar_try_wait(uint32_t bar, uint32_t parity) {
-    uint32_t ok;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-        "selp.u32 %0, 1, 0, p;\n\t}"
-        : "=r"(ok)
-        : "r"(bar), "r"(parity)
-        : "memory");
-    return ok != 0;
-}
-// Waits for the phase with the given parity; gives up after KX_WAIT_CYCLES.
-__device__ __forceinline__ bool kx_mbar_wait(uint32_t bar, uint32_t parity) {
-    const long long t0 = clock64();
-    while (!kx_mbar_try_wait(bar, parity))
-        if (clock64() - t0 > KX_WAIT_CYCLES) return false;
-    return true;
-}
-__device__ __forceinline__ void kx_bulk_g2s(uint32_t dst, const void *src, uint32_t bytes,
-                                            uint32_t bar) {
-    asm volatile(
-        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
-        "l"(src), "r"(bytes), "r"(bar)
-        : "memory");
-}
+#include "kx_ptx.cuh"
+
 // Shared-memory matrix descriptor: start >> 4 (bits 0-13), leading-dimension
 // byte offset >> 4 (16-29), stride-dimension byte offset >> 4 (32-45), the
 // fixed 0b001 at bits 46-48, base offset 0, no swizzle.

@@ -18,6 +18,7 @@ __device__ double4_32a g_kx_log2_tab[256];
 __device__ double2 g_kx_exp2_tab[64];
 
 #include "kx_math.cuh"
+#include "kx_ptx.cuh"
 
 // Tables of kx_math.cuh, computed in long double on the host and copied to the
 // current device once per device.
@@ -303,8 +304,9 @@ __device__ int kx_prep_block(int n, int path, double x, double Ei, double hi, do
     if (in) dl[i] = del;
     __syncthreads();
     if (in) {
+        const double D = i + 1 < n ? dl[i + 1] - del : 0.0;
         tl[i] = make_float2(l2f, (float)del);
-        td[i] = make_float2((float)del, i + 1 < n ? (float)(dl[i + 1] - del) : 0.f);
+        td[i] = make_float2((float)(del - D), (float)D);   // (delta_j - D_j, D_j)
     }
     if (i < 4) tl[n + i] = make_float2(-2000.f, 0.f);
     return bad;
@@ -391,17 +393,19 @@ __device__ __forceinline__ uint4 kx_ld_stream(const uint4 *p) {
     return r;
 }
 
-__device__ __forceinline__ float kx_unpack_omega(uint32_t w) {
-    return __uint_as_float(0x3f800000u | (w & 0x7fffffu)) - 1.0f;
+// 1 + omega from the packed word: omega's 23 bits as the significand of a float
+// in [1, 2).
+__device__ __forceinline__ float kx_one_plus_omega(uint32_t w) {
+    return __uint_as_float(0x3f800000u | (w & 0x7fffffu));
 }
 
-// 2^d - 1 for |d| < 1/4: Taylor series of expm1(x), x = d ln 2, through x^6
-// (truncation below 1e-9 relative); exactly 0 at d = 0.
+// 2^d - 1 for |d| < 1/4: Taylor series of expm1(x), x = d ln 2, through x^5
+// (truncation below 2.2e-7 relative at |d| = 1/4, the far form's own error
+// there is ~1.4e-6); exactly 0 at d = 0.
 __device__ __forceinline__ float kx_exp2m1_small(float d) {
     const float c1 = 0.69314718056f, c2 = 0.24022650695f, c3 = 0.05550410866f;
-    const float c4 = 0.00961812911f, c5 = 0.00133335581f, c6 = 0.00015403530f;
-    float p = fmaf(d, c6, c5);
-    p = fmaf(d, p, c4);
+    const float c4 = 0.00961812911f, c5 = 0.00133335581f;
+    float p = fmaf(d, c5, c4);
     p = fmaf(d, p, c3);
     p = fmaf(d, p, c2);
     p = fmaf(d, p, c1);
@@ -439,27 +443,73 @@ __device__ __forceinline__ void kx_df_add(float &hi, float &lo, float x) {
     lo += e;
 }
 
-// Persistent streaming contraction over the compacted FP32 tables.  A unit is
-// one warp-sized slice of a row (32 x VPL consecutive kept vectors of row i); a
-// task is up to G consecutive units of one row (the task table, built with the
-// kernel, fixes the work split: an instance's arithmetic does not depend on
-// the batch it is launched with).  Warps take tasks in a fixed round-robin
-// order and prefetch the next unit's tables into registers while computing the
-// current one.  Each lane sums its unit's terms in FP32 and adds the unit sum
-// into a double-float accumulator; at the end of the task the warp reduces the
-// double-float sums (fixed shuffle tree) and lane 0 writes the task's (hi, lo)
-// partial into the task's slot.
-template <int BP, int VPL>
-__global__ void __launch_bounds__(KX_T32)
-    k_stream32(int n, int ntask, const int4 *__restrict__ task, const int *__restrict__ roff, int B,
-               const uint32_t *__restrict__ vt, const float4 *__restrict__ W,
-               const uint4 *__restrict__ PK, const float2 *__restrict__ tl,
-               const float2 *__restrict__ td, float2 *__restrict__ partial, int pstride,
-               const kx_inst_state *__restrict__ st, int stage) {
-    const int b0 = blockIdx.y * BP;
-    __shared__ float2 s_l[BP][KX_MAX_N + 4];   // (l2_j, delta_j)
-    __shared__ float2 s_d[BP][KX_MAX_N];       // (delta_j, delta_{j+1} - delta_j)
-    bool act[BP];
+// The four elements of one packed vector (n, m0..m0+3) for BP instances:
+// acc[bb] += sum_q W_q [f_n f_m - f_i f_t] / f_max^2 in the bracket form.  The
+// same code serves both streaming kernels, so an instance's result does not
+// depend on which of them ran.
+template <int BP>
+__device__ __forceinline__ void kx_vector_terms(const float4 wv, const uint4 pv, const uint32_t nvw,
+                                                const float2 (*s_l)[KX_MAX_N + 4],
+                                                const float2 (*s_d)[KX_MAX_N], const float *di,
+                                                const int *so, float *acc) {
+    const int nn = nvw & 0xffff, m0 = nvw >> 16;
+    const float wk[4] = {wv.x, wv.y, wv.z, wv.w};
+    const uint32_t pw[4] = {pv.x, pv.y, pv.z, pv.w};
+#pragma unroll
+    for (int bb = 0; bb < BP; ++bb) {
+        const float2 ln = s_l[bb][nn];
+        const float cn = di[bb] - ln.y;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const float2 lm = s_l[bb][m0 + so[q]];
+            const float2 dj = s_d[bb][pw[q] >> 23];
+            const float a = ln.x + lm.x;
+            // delta_t = (delta_j - D_j) + (1 + omega) D_j
+            const float d = (cn + fmaf(kx_one_plus_omega(pw[q]), dj.y, dj.x)) - lm.y;
+            acc[bb] = fmaf(wk[q], kx_bracket_term(a, d), acc[bb]);
+        }
+    }
+}
+
+// Lane-level end of a task: fixed shuffle tree over the double-float sums and
+// the (hi, lo) partial into the task's slot.
+template <int BP>
+__device__ __forceinline__ void kx_task_partial(const float *hi, const float *lo, const bool *act,
+                                                int lane, int b0, int pstride, int tslot,
+                                                float2 *__restrict__ partial) {
+#pragma unroll
+    for (int bb = 0; bb < BP; ++bb) {
+        float h = hi[bb], l = lo[bb];
+#pragma unroll
+        for (int off = 16; off; off >>= 1) {
+            const float h2 = __shfl_xor_sync(0xffffffffu, h, off);
+            const float l2 = __shfl_xor_sync(0xffffffffu, l, off);
+            float sm, e;
+            kx_two_sum(h, h2, sm, e);
+            h = sm;
+            l = (l + l2) + e;
+        }
+        if (lane == 0 && act[bb]) partial[(long long)(b0 + bb) * pstride + tslot] = make_float2(h, l);
+    }
+}
+
+// A unit is 32 x VPL kept vectors of a row (VPL per lane): 64 on grids of up
+// to 160 points, 128 above (more bytes in flight per warp on long rows).
+#define KX_STAGE_BYTES(VPL) (32 * (VPL) * (16 + 16 + 4))   // W, pk, (n, m0) of one unit
+#define KX_STREAM_SMEM(VPL, wpb) (2 * KX_STAGE_BYTES(VPL) * (wpb))
+
+struct kx_unit {
+    int i, c, cend, slot, rb;
+};
+
+// Loads the instances' (l2, delta) and (delta - D, D) tables into shared
+// memory; returns false if no instance of the block is active.
+template <int BP>
+__device__ __forceinline__ bool kx_stream_tables(int n, int B, int b0, const float2 *__restrict__ tl,
+                                                 const float2 *__restrict__ td,
+                                                 const kx_inst_state *__restrict__ st, int stage,
+                                                 float2 (*s_l)[KX_MAX_N + 4],
+                                                 float2 (*s_d)[KX_MAX_N], bool *act) {
     bool any = false;
 #pragma unroll
     for (int bb = 0; bb < BP; ++bb) {
@@ -467,7 +517,7 @@ __global__ void __launch_bounds__(KX_T32)
         act[bb] = b < B && !(st && (st[b].done || (stage == 2 && st[b].skip2)));
         any |= act[bb];
     }
-    if (!any) return;
+    if (!any) return false;
 #pragma unroll
     for (int bb = 0; bb < BP; ++bb) {
         const int b = b0 + bb;
@@ -476,57 +526,68 @@ __global__ void __launch_bounds__(KX_T32)
         for (int t = threadIdx.x; t < n; t += blockDim.x)
             s_d[bb][t] = act[bb] ? td[(long long)b * n + t] : make_float2(0.f, 0.f);
     }
-    __syncthreads();
+    return true;
+}
 
+// Streaming contraction, register pipeline (one or two instances per pass).
+// Work split as in k_stream32 below (units of 32 x VPL kept vectors, tasks from
+// the task table); each warp holds the next unit's tables in registers while
+// it computes the current one.
+template <int BP, int VPL>
+__global__ void __launch_bounds__(KX_T32)
+    k_stream32r(int n, int ntask, const int4 *__restrict__ task, const int *__restrict__ roff, int B,
+                const uint32_t *__restrict__ vt, const float4 *__restrict__ W,
+                const uint4 *__restrict__ PK, const float2 *__restrict__ tl,
+                const float2 *__restrict__ td, float2 *__restrict__ partial, int pstride,
+                const kx_inst_state *__restrict__ st, int stage) {
+    __shared__ float2 s_l[BP][KX_MAX_N + 4];   // (l2_j, delta_j)
+    __shared__ float2 s_d[BP][KX_MAX_N];       // (delta_j - D_j, D_j), D_j = delta_{j+1} - delta_j
+    const int b0 = blockIdx.y * BP;
+    bool act[BP];
+    if (!kx_stream_tables<BP>(n, B, b0, tl, td, st, stage, s_l, s_d, act)) return;
+    __syncthreads();
     const int lane = threadIdx.x & 31;
-    // element offset of each slot of this lane's vectors (slot rotation of the
-    // packed tables: row vector k's slot s holds m0 + ((s + ((k >> 2) & 3)) & 3),
-    // and k mod 32 == lane)
     const int rot = (lane >> 2) & 3;
     const int so[4] = {rot, (1 + rot) & 3, (2 + rot) & 3, (3 + rot) & 3};
-    const int wpb = blockDim.x >> 5;
-    const int stride = gridDim.x * wpb;
-    int tk = blockIdx.x * wpb + (threadIdx.x >> 5);
     float4 w[VPL];
     uint4 pk[VPL];
     uint32_t nv[VPL];
-    // the unit in the prefetch registers: row i (kept vectors rb .. rb + rl), unit c
-    int i = 0, c = 0, cend = 0, slot = 0, rb = 0, rl = 0;
-    auto load_unit = [&]() {
+    auto first_unit = [&](int t) {
+        const int4 d = __ldg(task + t);
+        kx_unit u;
+        u.i = d.x;
+        u.c = d.y;
+        u.cend = d.z;
+        u.slot = d.w;
+        u.rb = __ldg(roff + d.x);
+        return u;
+    };
+    auto load_unit = [&](const kx_unit &u) {
+        const int v0 = u.rb + u.c * (32 * VPL) + lane;
 #pragma unroll
         for (int e = 0; e < VPL; ++e) {
-            const int v = c * (32 * VPL) + e * 32 + lane;
-            if (v < rl) {
-                w[e] = kx_ld_stream(W + rb + v);
-                pk[e] = kx_ld_stream(PK + rb + v);
-                nv[e] = __ldg(vt + rb + v);
-            } else {
-                w[e] = make_float4(0.f, 0.f, 0.f, 0.f);
-                pk[e] = make_uint4(0u, 0u, 0u, 0u);
-                nv[e] = 0u;
-            }
+            w[e] = kx_ld_stream(W + v0 + e * 32);
+            pk[e] = kx_ld_stream(PK + v0 + e * 32);
+            nv[e] = __ldg(vt + v0 + e * 32);
         }
     };
-    auto start_task = [&]() {
-        const int4 d = __ldg(task + tk);
-        i = d.x;
-        c = d.y;
-        cend = d.z;
-        slot = d.w;
-        rb = __ldg(roff + i);
-        rl = __ldg(roff + i + 1) - rb;
-        load_unit();
-    };
-    if (tk < ntask) start_task();
-    while (tk < ntask) {
+    const int stride = gridDim.x * (blockDim.x >> 5);
+    int tk = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    bool have = tk < ntask;
+    kx_unit u;
+    if (have) {
+        u = first_unit(tk);
+        load_unit(u);
+    }
+    while (have) {
         float hi[BP], lo[BP], di[BP];
 #pragma unroll
         for (int bb = 0; bb < BP; ++bb) {
             hi[bb] = 0.f;
             lo[bb] = 0.f;
-            di[bb] = s_l[bb][i].y;
+            di[bb] = s_l[bb][u.i].y;
         }
-        const int tslot = slot;
+        const int tslot = u.slot;
         for (;;) {
             float4 wc[VPL];
             uint4 pc[VPL];
@@ -537,55 +598,174 @@ __global__ void __launch_bounds__(KX_T32)
                 pc[e] = pk[e];
                 nc[e] = nv[e];
             }
-            // advance to the next unit (this task's next unit, or the next task)
-            const bool more = c + 1 < cend;
+            kx_unit nx = u;
+            bool nx_ok = true;
+            const bool more = u.c + 1 < u.cend;
             if (more) {
-                ++c;
-                load_unit();
+                nx.c = u.c + 1;
             } else {
                 tk += stride;
-                if (tk < ntask) start_task();
+                nx_ok = tk < ntask;
+                if (nx_ok) nx = first_unit(tk);
             }
+            if (nx_ok) load_unit(nx);
+            float acc[BP];
+#pragma unroll
+            for (int bb = 0; bb < BP; ++bb) acc[bb] = 0.f;
+#pragma unroll
+            for (int e = 0; e < VPL; ++e) kx_vector_terms<BP>(wc[e], pc[e], nc[e], s_l, s_d, di, so, acc);
+#pragma unroll
+            for (int bb = 0; bb < BP; ++bb) kx_df_add(hi[bb], lo[bb], acc[bb]);
+            u = nx;
+            if (!more) {
+                have = nx_ok;
+                break;
+            }
+        }
+        kx_task_partial<BP>(hi, lo, act, lane, b0, pstride, tslot, partial);
+    }
+}
+
+// Persistent streaming contraction over the compacted FP32 tables.  A unit is
+// 32 x VPL consecutive kept vectors of a row (VPL per lane); a task is up to G
+// consecutive units of one row (the task table, built with the kernel, fixes
+// the work split: an instance's arithmetic does not depend on the batch it is
+// launched with).  Each warp takes tasks in a fixed round-robin order and
+// streams its units through a two-stage shared-memory ring: lane 0 issues bulk
+// copies of the next unit's W, packed (j_L, omega) and (n, m0) words into one
+// stage while the warp computes the other, with an mbarrier transaction count
+// per stage (bounded waits; on expiry the kernel sets *err and stops).  Each
+// lane sums its unit's terms in FP32 and adds the unit sum into a double-float
+// accumulator; at the end of the task the warp reduces the double-float sums
+// (fixed shuffle tree) and lane 0 writes the task's (hi, lo) partial into the
+// task's slot.
+template <int BP, int VPL>
+__global__ void __launch_bounds__(KX_T32, VPL == 4 ? 2 : 3)
+    k_stream32(int n, int ntask, const int4 *__restrict__ task, const int *__restrict__ roff, int B,
+               const uint32_t *__restrict__ vt, const float4 *__restrict__ W,
+               const uint4 *__restrict__ PK, const float2 *__restrict__ tl,
+               const float2 *__restrict__ td, float2 *__restrict__ partial, int pstride,
+               const kx_inst_state *__restrict__ st, int stage, int *__restrict__ err) {
+    extern __shared__ __align__(128) unsigned char s_ring[];   // [warp][2 stages][KX_STAGE_BYTES]
+    __shared__ float2 s_l[BP][KX_MAX_N + 4];   // (l2_j, delta_j)
+    __shared__ float2 s_d[BP][KX_MAX_N];       // (delta_j - D_j, D_j), D_j = delta_{j+1} - delta_j
+    __shared__ __align__(8) unsigned long long s_bar[KX_T32 / 32][2];
+    const int b0 = blockIdx.y * BP;
+    bool act[BP];
+    if (!kx_stream_tables<BP>(n, B, b0, tl, td, st, stage, s_l, s_d, act)) return;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (lane == 0) {
+        kx_mbar_init(kx_smem_u32(&s_bar[warp][0]), 1);
+        kx_mbar_init(kx_smem_u32(&s_bar[warp][1]), 1);
+        kx_fence_mbar_init();
+    }
+    __syncthreads();
+
+    // element offset of each slot of this lane's vectors (slot rotation of the
+    // packed tables: row vector k's slot s holds m0 + ((s + ((k >> 2) & 3)) & 3),
+    // and k mod 32 == lane)
+    const int rot = (lane >> 2) & 3;
+    const int so[4] = {rot, (1 + rot) & 3, (2 + rot) & 3, (3 + rot) & 3};
+    constexpr int UNIT = 32 * VPL, SB = KX_STAGE_BYTES(VPL);
+    unsigned char *ring = s_ring + (size_t)warp * 2 * SB;
+    const uint32_t bar0 = kx_smem_u32(&s_bar[warp][0]), bar1 = kx_smem_u32(&s_bar[warp][1]);
+    uint32_t phase = 0u;     // bit sg: parity of stage sg's next completion
+    uint32_t pending = 0u;   // bit sg: a copy into stage sg is in flight
+
+    auto first_unit = [&](int t) {
+        const int4 d = __ldg(task + t);
+        kx_unit u;
+        u.i = d.x;
+        u.c = d.y;
+        u.cend = d.z;
+        u.slot = d.w;
+        u.rb = __ldg(roff + d.x);
+        return u;
+    };
+    // lane 0: copy unit u's tables into stage sg (rows are whole units of 64
+    // vectors, so every copy is full and 16-byte aligned)
+    auto issue = [&](const kx_unit &u, int sg) {
+        if (lane == 0) {
+            const int v0 = u.rb + u.c * UNIT;
+            unsigned char *dst = ring + sg * SB;
+            const uint32_t b = sg ? bar1 : bar0;
+            kx_fence_proxy_async();
+            kx_mbar_expect_tx(b, (uint32_t)SB);
+            kx_bulk_g2s(kx_smem_u32(dst), W + v0, UNIT * 16u, b);
+            kx_bulk_g2s(kx_smem_u32(dst + UNIT * 16), PK + v0, UNIT * 16u, b);
+            kx_bulk_g2s(kx_smem_u32(dst + UNIT * 32), vt + v0, UNIT * 4u, b);
+        }
+        pending |= 1u << sg;
+    };
+
+    const int stride = gridDim.x * (blockDim.x >> 5);
+    int tk = blockIdx.x * (blockDim.x >> 5) + warp;
+    bool have = tk < ntask;
+    kx_unit u;
+    if (have) {
+        u = first_unit(tk);
+        issue(u, 0);
+    }
+    int sg = 0;
+    bool aborted = false;
+    while (have) {
+        float hi[BP], lo[BP], di[BP];
+#pragma unroll
+        for (int bb = 0; bb < BP; ++bb) {
+            hi[bb] = 0.f;
+            lo[bb] = 0.f;
+            di[bb] = s_l[bb][u.i].y;
+        }
+        const int tslot = u.slot;
+        bool task_done = false;
+        while (!task_done) {
+            // the next unit: this task's next one, or the first of the next task
+            kx_unit nx = u;
+            bool nx_ok = true;
+            const bool more = u.c + 1 < u.cend;
+            if (more) {
+                nx.c = u.c + 1;
+            } else {
+                tk += stride;
+                nx_ok = tk < ntask;
+                if (nx_ok) nx = first_unit(tk);
+            }
+            if (nx_ok) issue(nx, sg ^ 1);
+            if (!kx_mbar_wait(sg ? bar1 : bar0, (phase >> sg) & 1u)) {
+                if (lane == 0) atomicExch(err, 1);
+                aborted = true;
+                break;
+            }
+            phase ^= 1u << sg;
+            pending &= ~(1u << sg);
+            const float4 *sW = reinterpret_cast<const float4 *>(ring + sg * SB);
+            const uint4 *sP = reinterpret_cast<const uint4 *>(ring + sg * SB + UNIT * 16);
+            const uint32_t *sV = reinterpret_cast<const uint32_t *>(ring + sg * SB + UNIT * 32);
             float acc[BP];
 #pragma unroll
             for (int bb = 0; bb < BP; ++bb) acc[bb] = 0.f;
 #pragma unroll
             for (int e = 0; e < VPL; ++e) {
-                const int nn = nc[e] & 0xffff, m0 = nc[e] >> 16;
-                const float wk[4] = {wc[e].x, wc[e].y, wc[e].z, wc[e].w};
-                const uint32_t pw[4] = {pc[e].x, pc[e].y, pc[e].z, pc[e].w};
-#pragma unroll
-                for (int bb = 0; bb < BP; ++bb) {
-                    const float2 ln = s_l[bb][nn];
-                    const float cn = di[bb] - ln.y;
-#pragma unroll
-                    for (int q = 0; q < 4; ++q) {
-                        const float2 lm = s_l[bb][m0 + so[q]];
-                        const float2 dj = s_d[bb][pw[q] >> 23];
-                        const float a = ln.x + lm.x;
-                        const float d = (cn + fmaf(kx_unpack_omega(pw[q]), dj.y, dj.x)) - lm.y;
-                        acc[bb] = fmaf(wk[q], kx_bracket_term(a, d), acc[bb]);
-                    }
-                }
+                const int vl = e * 32 + lane;
+                kx_vector_terms<BP>(sW[vl], sP[vl], sV[vl], s_l, s_d, di, so, acc);
             }
 #pragma unroll
             for (int bb = 0; bb < BP; ++bb) kx_df_add(hi[bb], lo[bb], acc[bb]);
-            if (!more) break;
-        }
-#pragma unroll
-        for (int bb = 0; bb < BP; ++bb) {
-            float h = hi[bb], l = lo[bb];
-#pragma unroll
-            for (int off = 16; off; off >>= 1) {
-                const float h2 = __shfl_xor_sync(0xffffffffu, h, off);
-                const float l2 = __shfl_xor_sync(0xffffffffu, l, off);
-                float sm, e;
-                kx_two_sum(h, h2, sm, e);
-                h = sm;
-                l = (l + l2) + e;
+            __syncwarp();   // every lane is done with stage sg before it is refilled
+            sg ^= 1;
+            u = nx;
+            if (!more) {
+                task_done = true;
+                have = nx_ok;
             }
-            if (lane == 0 && act[bb]) partial[(long long)(b0 + bb) * pstride + tslot] = make_float2(h, l);
         }
+        if (aborted) break;
+        kx_task_partial<BP>(hi, lo, act, lane, b0, pstride, tslot, partial);
+    }
+    if (aborted) {
+        // let copies still in flight land (bounded) before the block exits
+        for (int k = 0; k < 2; ++k)
+            if ((pending >> k) & 1u) kx_mbar_wait(k ? bar1 : bar0, (phase >> k) & 1u);
     }
 }
 
@@ -598,24 +778,22 @@ int kx_chunks_per_row(const kx_kernel *k) {
 // SM count, queried once (kx_contract_prepare) before any stream capture.
 static int g_sms;
 
+// The staging ring is dynamic shared memory; with the static tables it passes
+// the default 48 KB for two and four instances per pass.
 template <int BP, int VPL>
-static void kx_stream_attr() {
-    int occ = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_stream32<BP, VPL>, KX_T32, 0);
+static cudaError_t kx_stream_attr() {
+    return cudaFuncSetAttribute(k_stream32<BP, VPL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                KX_STREAM_SMEM(VPL, KX_T32 / 32));
 }
 
 cudaError_t kx_contract_prepare() {
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaError_t e = kx_math_tables_init(dev);
+    if (e == cudaSuccess) e = kx_stream_attr<4, 4>();
     if (e != cudaSuccess) return e;
     if (g_sms) return cudaSuccess;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    kx_stream_attr<1, 2>();
-    kx_stream_attr<1, 4>();
-    kx_stream_attr<2, 2>();
-    kx_stream_attr<2, 4>();
-    kx_stream_attr<4, 4>();
     cudaGetLastError();
     g_sms = sms > 0 ? sms : 1;
     return cudaSuccess;
@@ -624,9 +802,9 @@ cudaError_t kx_contract_prepare() {
 template <int BP, int VPL>
 static cudaError_t kx_launch_stream(const kx_kernel *k, int B, const kx_batch_views &v,
                                     const kx_inst_state *st, int stage, cudaStream_t s) {
+    const size_t smem = KX_STREAM_SMEM(VPL, KX_T32 / 32);
     int occ = 0;
-    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_stream32<BP, VPL>,
-                                                                  KX_T32, 0);
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_stream32<BP, VPL>, KX_T32, smem);
     if (e != cudaSuccess) return e;
     if (occ < 1) occ = 1;
     const int sms = g_sms > 0 ? g_sms : 148;
@@ -637,13 +815,37 @@ static cudaError_t kx_launch_stream(const kx_kernel *k, int B, const kx_batch_vi
     int cap = (occ * sms + groups - 1) / groups;
     if (cap < sms) cap = sms;
     if (blocks > cap) blocks = cap;
+    if (blocks < 1) blocks = 1;
     dim3 grid(blocks, groups);
     const float4 *W = reinterpret_cast<const float4 *>(k->d_W32);
     const uint4 *PK = reinterpret_cast<const uint4 *>(k->d_pk);
-    k_stream32<BP, VPL><<<grid, KX_T32, 0, s>>>(k->n, k->ntask, k->d_task, k->d_roff, B, k->d_vt,
-                                                W, PK, v.tl, v.td,
-                                                reinterpret_cast<float2 *>(v.partial), v.chunks,
-                                                st, stage);
+    k_stream32<BP, VPL><<<grid, KX_T32, smem, s>>>(k->n, k->ntask, k->d_task, k->d_roff, B, k->d_vt, W,
+                                              PK, v.tl, v.td, reinterpret_cast<float2 *>(v.partial),
+                                              v.chunks, st, stage, v.err);
+    return cudaGetLastError();
+}
+
+template <int BP, int VPL>
+static cudaError_t kx_launch_stream_r(const kx_kernel *k, int B, const kx_batch_views &v,
+                                      const kx_inst_state *st, int stage, cudaStream_t s) {
+    int occ = 0;
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_stream32r<BP, VPL>, KX_T32, 0);
+    if (e != cudaSuccess) return e;
+    if (occ < 1) occ = 1;
+    const int sms = g_sms > 0 ? g_sms : 148;
+    const int wpb = KX_T32 / 32;
+    const int groups = (B + BP - 1) / BP;
+    int blocks = (k->ntask + wpb - 1) / wpb;
+    int cap = (occ * sms + groups - 1) / groups;
+    if (cap < sms) cap = sms;
+    if (blocks > cap) blocks = cap;
+    if (blocks < 1) blocks = 1;
+    dim3 grid(blocks, groups);
+    k_stream32r<BP, VPL><<<grid, KX_T32, 0, s>>>(k->n, k->ntask, k->d_task, k->d_roff, B, k->d_vt,
+                                            reinterpret_cast<const float4 *>(k->d_W32),
+                                            reinterpret_cast<const uint4 *>(k->d_pk), v.tl, v.td,
+                                            reinterpret_cast<float2 *>(v.partial), v.chunks, st,
+                                            stage);
     return cudaGetLastError();
 }
 
@@ -660,12 +862,14 @@ cudaError_t kx_launch_contract(const kx_kernel *k, int B, const double *f, const
     // Instances per pass: four share each table load on long rows; short rows
     // (few units per row, latency bound) do better with two per pass and twice
     // the blocks (measured: N = 128, four instances, 9% per Heun attempt).
-    const bool small = k->vpl == 2;
-    if (small) return B >= 2 ? kx_launch_stream<2, 2>(k, B, v, st, stage, s)
-                             : kx_launch_stream<1, 2>(k, B, v, st, stage, s);
+    // four instances per pass (long rows, B >= 4): the staged kernel, whose
+    // register budget fits four accumulators at three blocks per SM; one or two
+    // per pass: the register pipeline (measured faster there)
+    if (k->vpl == 2) return B >= 2 ? kx_launch_stream_r<2, 2>(k, B, v, st, stage, s)
+                                   : kx_launch_stream_r<1, 2>(k, B, v, st, stage, s);
     if (B >= 4) return kx_launch_stream<4, 4>(k, B, v, st, stage, s);
-    if (B >= 2) return kx_launch_stream<2, 4>(k, B, v, st, stage, s);
-    return kx_launch_stream<1, 4>(k, B, v, st, stage, s);
+    if (B >= 2) return kx_launch_stream_r<2, 4>(k, B, v, st, stage, s);
+    return kx_launch_stream_r<1, 4>(k, B, v, st, stage, s);
 }
 
 // ---------------------------------------------------- row combine + projection

@@ -118,7 +118,8 @@ struct kx_batch_views {
     double *fmax;          // [B]
     double *lf64;          // [B][n]       FP64 path: ln max(f, floor)
     float2 *tl;            // [B][n + 4]   FP32 path: (l2_j, delta_j), l2 = log2(max(f, floor)/f_max)
-    float2 *td;            // [B][n]       FP32 path: (delta_j, delta_{j+1} - delta_j)
+    float2 *td;            // [B][n]       FP32 path: (delta_j - D_j, D_j), D_j = delta_{j+1} - delta_j;
+                           //              split path: (l2_j, l2_{j+1} - l2_j)
     double2 *partial;      // [B][n][chunks]  (FP32 path: float2 (hi, lo) task partials, [B][chunks])
     const int2 *rtask;     // FP32 path: [n] (first partial slot, tasks) per row
     double *rfmax;         // [B]          1 / f_max

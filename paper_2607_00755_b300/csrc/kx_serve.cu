@@ -110,12 +110,13 @@ static size_t kx_group_estimate(const kx_server_config &cfg, int n) {
     d.Mpad = ((n * n + 127) / 128) * 128;
     d.Kpad = ((n + 31) / 32) * 32;
     size_t tables;
-    // FP32: upper bounds (every vector kept, one unit per task)
-    const int unit = 32 * (n <= 160 ? 2 : 4);
-    const long long upr = (V + unit - 1) / unit;
+    // FP32: upper bounds (every vector kept, rows padded to whole units, one
+    // unit per task)
+    const long long unit = n <= 160 ? 64 : 128, upr = (V + unit - 1) / unit;
     d.tslots = (int)(n * ((upr + 2) & ~1LL));
     if (cfg.precision == KX_FP32)
-        tables = (size_t)n * V * (16 + 16 + 4) + (size_t)(n + 1) * 4 + (size_t)n * 8 + (size_t)n * upr * 16;
+        tables = (size_t)n * upr * unit * (16 + 16 + 4) + (size_t)(n + 1) * 4 + (size_t)n * 8 +
+                 (size_t)n * upr * 16;
     else if (cfg.precision == KX_FP64) tables = (size_t)n * d.P * 18 + 4 * d.P;
     else tables = (size_t)d.Mpad * d.Kpad * 8 + (size_t)n * d.P * 8 + (size_t)n * (n + 1) * 4;
     const int cap = cfg.slots_per_group;
