@@ -215,7 +215,7 @@ static void kx_free_kernel(kx_kernel *k) {
     cudaSetDevice(k->device);
     void *ptrs[] = {k->d_p, k->d_E, k->d_dp, k->d_dE, k->d_h, k->d_pair, k->d_W64,
                     k->d_om64, k->d_jl, k->d_vt, k->d_W32, k->d_pk, k->d_roff, k->d_rtask,
-                    k->d_task, k->d_Atile, k->d_lel, k->d_lrow, k->d_lgrp};
+                    k->d_task, k->d_bins, k->d_Atile, k->d_lel, k->d_lrow, k->d_lgrp};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     delete k;
@@ -354,29 +354,42 @@ extern "C" int kx_build_kernel(kx_ctx *ctx, const kx_grid_desc *d, kx_kernel **o
         KX_CHK("copy", cudaMemcpyAsync(rcnt.data(), d_rcnt, sizeof(int) * n, cudaMemcpyDeviceToHost, s));
         KX_CHK("sync", cudaStreamSynchronize(s));
         // streaming work: units of 32 x vpl vectors of a row (64 on grids up to
-        // 160 points, 128 above), tasks of G units; rows padded to whole units
-        // (zero weights), so every unit is a full, 16-byte aligned block of each
-        // table; G from the total units so that every SM gets work on small grids
+        // 160 points, 128 above); rows padded to whole units (zero weights), so
+        // every unit is a full, 16-byte aligned block of each table.  The units
+        // of all rows, in order, are cut into KX_BINS bins of equal size (fixed
+        // per kernel, so the split does not depend on the device or the batch);
+        // a bin's units within one row form one task with its own partial slot.
         k->vpl = n <= 160 ? 2 : 4;
         const int unit = 32 * k->vpl;
         std::vector<int> roff(n + 1, 0);
         for (int i = 0; i < n; ++i) roff[i + 1] = roff[i] + (rcnt[i] + unit - 1) / unit * unit;
         k->Vt = roff[n];
-        long long units = 0;
-        for (int i = 0; i < n; ++i) units += (roff[i + 1] - roff[i] + unit - 1) / unit;
-        long long g = units / (2LL * 148 * 16);
-        k->G = (int)(g < 1 ? 1 : (g > 16 ? 16 : g));
-        std::vector<int2> rtask(n);
+        std::vector<long long> uoff(n + 1, 0);   // first global unit of each row
+        for (int i = 0; i < n; ++i) uoff[i + 1] = uoff[i] + (roff[i + 1] - roff[i]) / unit;
+        const long long units = uoff[n];
+        std::vector<int> bins(KX_BINS + 1, 0);
         std::vector<int4> task;
+        std::vector<int> row_tasks(n, 0);
+        int row = 0;
+        for (int b = 0; b < KX_BINS; ++b) {
+            bins[b] = (int)task.size();
+            long long u0 = units * b / KX_BINS, u1 = units * (b + 1) / KX_BINS;
+            while (u0 < u1) {
+                while (uoff[row + 1] <= u0) ++row;
+                const long long e = std::min(u1, uoff[row + 1]);
+                task.push_back(make_int4(row, (int)(u0 - uoff[row]), (int)(e - uoff[row]), row_tasks[row]));
+                ++row_tasks[row];
+                u0 = e;
+            }
+        }
+        bins[KX_BINS] = (int)task.size();
+        std::vector<int2> rtask(n);
         int slots = 0;
         for (int i = 0; i < n; ++i) {
-            const int upr = (roff[i + 1] - roff[i] + unit - 1) / unit;
-            const int tpr = (upr + k->G - 1) / k->G;
-            rtask[i] = make_int2(slots, tpr);
-            for (int t = 0; t < tpr; ++t)
-                task.push_back(make_int4(i, t * k->G, std::min(upr, (t + 1) * k->G), slots + t));
-            slots += (tpr + 1) & ~1;   // even, for paired 16-byte reads of the partials
+            rtask[i] = make_int2(slots, row_tasks[i]);
+            slots += (row_tasks[i] + 1) & ~1;   // even, for paired 16-byte reads of the partials
         }
+        for (auto &t : task) t.w += rtask[t.x].x;   // slot = row's first slot + index in the row
         k->ntask = (int)task.size();
         k->tslots = slots > 0 ? slots : 2;
         long long *by2 = &k->bytes;
@@ -385,7 +398,8 @@ extern "C" int kx_build_kernel(kx_ctx *ctx, const kx_grid_desc *d, kx_kernel **o
             (rc = kx_dev_alloc(ctx, &k->d_pk, (size_t)k->Vt * 4, by2)) != KX_OK ||
             (rc = kx_dev_alloc(ctx, &k->d_roff, n + 1, by2)) != KX_OK ||
             (rc = kx_dev_alloc(ctx, &k->d_rtask, n, by2)) != KX_OK ||
-            (rc = kx_dev_alloc(ctx, &k->d_task, task.size(), by2)) != KX_OK) {
+            (rc = kx_dev_alloc(ctx, &k->d_task, task.size(), by2)) != KX_OK ||
+            (rc = kx_dev_alloc(ctx, &k->d_bins, KX_BINS + 1, by2)) != KX_OK) {
             cudaFree(d_cnt);
             cudaFree(d_vt_all);
             cudaFree(d_pos);
@@ -403,6 +417,7 @@ extern "C" int kx_build_kernel(kx_ctx *ctx, const kx_grid_desc *d, kx_kernel **o
         KX_CHK("upload rows", cudaMemcpyAsync(k->d_rtask, rtask.data(), sizeof(int2) * n, cudaMemcpyHostToDevice, s));
         if (!task.empty())
             KX_CHK("upload tasks", cudaMemcpyAsync(k->d_task, task.data(), sizeof(int4) * task.size(), cudaMemcpyHostToDevice, s));
+        KX_CHK("upload bins", cudaMemcpyAsync(k->d_bins, bins.data(), sizeof(int) * (KX_BINS + 1), cudaMemcpyHostToDevice, s));
         KX_CHK("pack", kx_launch_pack_fp32(k, d_vt_all, k->V, d_pos, s));
         ctx->launches += 1;
     }
@@ -431,7 +446,7 @@ extern "C" int kx_build_kernel(kx_ctx *ctx, const kx_grid_desc *d, kx_kernel **o
         }
     }
     if (k->precision == KX_FP32)
-        k->stream_bytes = k->Vt * 36 + (long long)k->ntask * 16 + (long long)(n + 1) * 4;
+        k->stream_bytes = k->Vt * 36 + (long long)k->ntask * 16 + (long long)(n + 1) * 4 + (KX_BINS + 1) * 4;
     else if (k->precision == KX_FP64)
         k->stream_bytes = (long long)n * k->P * 18 + k->P * 4;
     else

@@ -535,7 +535,8 @@ __device__ __forceinline__ bool kx_stream_tables(int n, int B, int b0, const flo
 // it computes the current one.
 template <int BP, int VPL>
 __global__ void __launch_bounds__(KX_T32)
-    k_stream32r(int n, int ntask, const int4 *__restrict__ task, const int *__restrict__ roff, int B,
+    k_stream32r(int n, const int *__restrict__ bins, const int4 *__restrict__ task,
+                const int *__restrict__ roff, int B,
                 const uint32_t *__restrict__ vt, const float4 *__restrict__ W,
                 const uint4 *__restrict__ PK, const float2 *__restrict__ tl,
                 const float2 *__restrict__ td, float2 *__restrict__ partial, int pstride,
@@ -571,9 +572,19 @@ __global__ void __launch_bounds__(KX_T32)
             nv[e] = __ldg(vt + v0 + e * 32);
         }
     };
+    // equal-work bins of tasks, taken by the warps in a fixed order
     const int stride = gridDim.x * (blockDim.x >> 5);
-    int tk = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-    bool have = tk < ntask;
+    int vb = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    int tk = 0, tend = 0;
+    auto seek = [&]() {   // first task of bin vb or of the next nonempty bin of this warp
+        for (; vb < KX_BINS; vb += stride) {
+            tk = __ldg(bins + vb);
+            tend = __ldg(bins + vb + 1);
+            if (tk < tend) return true;
+        }
+        return false;
+    };
+    bool have = seek();
     kx_unit u;
     if (have) {
         u = first_unit(tk);
@@ -604,8 +615,12 @@ __global__ void __launch_bounds__(KX_T32)
             if (more) {
                 nx.c = u.c + 1;
             } else {
-                tk += stride;
-                nx_ok = tk < ntask;
+                if (tk + 1 < tend) {
+                    ++tk;
+                } else {
+                    vb += stride;
+                    nx_ok = seek();
+                }
                 if (nx_ok) nx = first_unit(tk);
             }
             if (nx_ok) load_unit(nx);
@@ -641,7 +656,8 @@ __global__ void __launch_bounds__(KX_T32)
 // task's slot.
 template <int BP, int VPL>
 __global__ void __launch_bounds__(KX_T32, VPL == 4 ? 2 : 3)
-    k_stream32(int n, int ntask, const int4 *__restrict__ task, const int *__restrict__ roff, int B,
+    k_stream32(int n, const int *__restrict__ bins, const int4 *__restrict__ task,
+               const int *__restrict__ roff, int B,
                const uint32_t *__restrict__ vt, const float4 *__restrict__ W,
                const uint4 *__restrict__ PK, const float2 *__restrict__ tl,
                const float2 *__restrict__ td, float2 *__restrict__ partial, int pstride,
@@ -698,9 +714,19 @@ __global__ void __launch_bounds__(KX_T32, VPL == 4 ? 2 : 3)
         pending |= 1u << sg;
     };
 
+    // equal-work bins of tasks, taken by the warps in a fixed order
     const int stride = gridDim.x * (blockDim.x >> 5);
-    int tk = blockIdx.x * (blockDim.x >> 5) + warp;
-    bool have = tk < ntask;
+    int vb = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    int tk = 0, tend = 0;
+    auto seek = [&]() {   // first task of bin vb or of the next nonempty bin of this warp
+        for (; vb < KX_BINS; vb += stride) {
+            tk = __ldg(bins + vb);
+            tend = __ldg(bins + vb + 1);
+            if (tk < tend) return true;
+        }
+        return false;
+    };
+    bool have = seek();
     kx_unit u;
     if (have) {
         u = first_unit(tk);
@@ -726,8 +752,12 @@ __global__ void __launch_bounds__(KX_T32, VPL == 4 ? 2 : 3)
             if (more) {
                 nx.c = u.c + 1;
             } else {
-                tk += stride;
-                nx_ok = tk < ntask;
+                if (tk + 1 < tend) {
+                    ++tk;
+                } else {
+                    vb += stride;
+                    nx_ok = seek();
+                }
                 if (nx_ok) nx = first_unit(tk);
             }
             if (nx_ok) issue(nx, sg ^ 1);
@@ -799,6 +829,17 @@ cudaError_t kx_contract_prepare() {
     return cudaSuccess;
 }
 
+// Blocks per instance group: the KX_BINS bins (8 per block of KX_T32 threads)
+// split evenly over the resident blocks (a whole number of bins per warp, so
+// no warp gets a bin more than another), given `resident` blocks per launch.
+static int kx_bin_blocks(int resident, int groups) {
+    const int full = KX_BINS / (KX_T32 / 32);          // blocks with one bin per warp
+    int per = resident / (groups > 0 ? groups : 1);    // resident blocks per group
+    if (per < 1) per = 1;
+    const int rounds = (full + per - 1) / per;        // bins per warp
+    return (full + rounds - 1) / rounds;
+}
+
 template <int BP, int VPL>
 static cudaError_t kx_launch_stream(const kx_kernel *k, int B, const kx_batch_views &v,
                                     const kx_inst_state *st, int stage, cudaStream_t s) {
@@ -808,18 +849,12 @@ static cudaError_t kx_launch_stream(const kx_kernel *k, int B, const kx_batch_vi
     if (e != cudaSuccess) return e;
     if (occ < 1) occ = 1;
     const int sms = g_sms > 0 ? g_sms : 148;
-    const int total = k->ntask;
-    const int wpb = KX_T32 / 32;
     const int groups = (B + BP - 1) / BP;
-    int blocks = (total + wpb - 1) / wpb;
-    int cap = (occ * sms + groups - 1) / groups;
-    if (cap < sms) cap = sms;
-    if (blocks > cap) blocks = cap;
-    if (blocks < 1) blocks = 1;
+    const int blocks = kx_bin_blocks(occ * sms, groups);
     dim3 grid(blocks, groups);
     const float4 *W = reinterpret_cast<const float4 *>(k->d_W32);
     const uint4 *PK = reinterpret_cast<const uint4 *>(k->d_pk);
-    k_stream32<BP, VPL><<<grid, KX_T32, smem, s>>>(k->n, k->ntask, k->d_task, k->d_roff, B, k->d_vt, W,
+    k_stream32<BP, VPL><<<grid, KX_T32, smem, s>>>(k->n, k->d_bins, k->d_task, k->d_roff, B, k->d_vt, W,
                                               PK, v.tl, v.td, reinterpret_cast<float2 *>(v.partial),
                                               v.chunks, st, stage, v.err);
     return cudaGetLastError();
@@ -833,15 +868,10 @@ static cudaError_t kx_launch_stream_r(const kx_kernel *k, int B, const kx_batch_
     if (e != cudaSuccess) return e;
     if (occ < 1) occ = 1;
     const int sms = g_sms > 0 ? g_sms : 148;
-    const int wpb = KX_T32 / 32;
     const int groups = (B + BP - 1) / BP;
-    int blocks = (k->ntask + wpb - 1) / wpb;
-    int cap = (occ * sms + groups - 1) / groups;
-    if (cap < sms) cap = sms;
-    if (blocks > cap) blocks = cap;
-    if (blocks < 1) blocks = 1;
+    const int blocks = kx_bin_blocks(occ * sms, groups);
     dim3 grid(blocks, groups);
-    k_stream32r<BP, VPL><<<grid, KX_T32, 0, s>>>(k->n, k->ntask, k->d_task, k->d_roff, B, k->d_vt,
+    k_stream32r<BP, VPL><<<grid, KX_T32, 0, s>>>(k->n, k->d_bins, k->d_task, k->d_roff, B, k->d_vt,
                                             reinterpret_cast<const float4 *>(k->d_W32),
                                             reinterpret_cast<const uint4 *>(k->d_pk), v.tl, v.td,
                                             reinterpret_cast<float2 *>(v.partial), v.chunks, st,

@@ -21,6 +21,7 @@
 #define KX_EPT64 8            // pairs per thread
 #define KX_CH64 (KX_T64 * KX_EPT64)
 #define KX_T32 256            // threads per FP32 contraction block
+#define KX_BINS 2368          // equal-work bins of the FP32 contraction (148 SMs x 16 warps)
 #define KX_FIN_THREADS 512    // finalize / stage kernels: one block per instance, thread = grid point
 
 struct kx_gl_nodes {
@@ -51,8 +52,9 @@ struct kx_kernel {
     int *d_roff;         // [n + 1] first kept vector of each row
     int2 *d_rtask;       // [n]: (first partial slot, tasks) of each row
     int4 *d_task;        // [ntask]: (row, first unit, end unit, partial slot)
+    int *d_bins;         // [KX_BINS + 1]: first task of each equal-work bin
     long long Vt;        // kept vectors, all rows
-    int vpl, G;          // vectors per lane of a unit, units per task
+    int vpl;             // vectors per lane of a unit
     int ntask;           // streaming tasks
     int tslots;          // partial slots per instance (row task counts rounded up to even)
     // batched (split TF32) tables
