@@ -34,9 +34,9 @@ METRIC = "collision-term evals/s & solves/s vs plain FP64 path; p50/p99 solve la
 UNIT = "evals/s"
 L2_FLUSH_BYTES = 512 << 20     # > 126 MB L2
 # DRAM bytes (read + write) per launch from one ncu capture of the current kernels
-# (profiles/k_stream32_n128_batch4.md, profiles/k_stream32_n384_single.md); None
+# (profiles/k_stream32r_n128_batch4.md, profiles/k_stream32r_n384_single.md); None
 # whenever those kernels have changed since the capture.
-NCU_TRAFFIC = {"stream_n128_b4": None, "stream_n384": None}
+NCU_TRAFFIC = {"stream_n128_b4": 6.789376e6, "stream_n384": 172.478208e6 + 2.921728e6}
 SOLVE = dict(t_end=1e5, h0=1e-3, rtol=1e-6, l1_tol=1e-3, check_every=10, max_attempts=2_000_000)
 
 
@@ -470,7 +470,7 @@ def main():
     achieved = alg_bytes / (ms_cold * 1e-3) / 1e9
     roof = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
             "frac": achieved / hbm, "traffic": NCU_TRAFFIC["stream_n128_b4"],
-            "kernel": "k_stream32<2,2> (N=128, 4 instances, 2 per pass)",
+            "kernel": "k_stream32r<2,2> (N=128, 4 instances, 2 per pass)",
             "algorithmic_bytes_per_launch": alg_bytes, "avg_launch_ms_cold_l2": ms_cold,
             "avg_launch_ms_warm_l2": ms_warm, "peak_source": src_peak}
     # streaming single-instance roofline at N=384 (tables 227 MB > L2)
@@ -483,7 +483,7 @@ def main():
     roof384 = {"bound": "hbm", "achieved": b384 / (ms384 * 1e-3) / 1e9, "peak": hbm,
                "unit": "GB/s", "frac": b384 / (ms384 * 1e-3) / 1e9 / hbm,
                "traffic": NCU_TRAFFIC["stream_n384"],
-               "kernel": "k_stream32<1,4> (N=384, single instance, cold L2)",
+               "kernel": "k_stream32r<1,4> (N=384, single instance, cold L2)",
                "algorithmic_bytes_per_launch": b384, "avg_launch_ms": ms384,
                "evals_per_s": 1e3 / ms384}
 
