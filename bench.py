@@ -316,6 +316,20 @@ def measure_serving(ctx, kx, requests=100, fp64_requests=8):
     return out
 
 
+def aggregate_ranks(dist, total_ms, evals, solves, device):
+    """Whole-job figures of N independent replicas (one per rank, weak scaling):
+    the slowest rank's timed milliseconds and the work summed over ranks.  No
+    data-path collective: the ranks exchange only these three numbers."""
+    if dist is None:
+        return total_ms, evals, solves
+    import torch
+    t = torch.tensor([total_ms], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    cnt = torch.tensor([evals, solves], device=device, dtype=torch.float64)
+    dist.all_reduce(cnt)
+    return float(t.item()), int(cnt[0].item()), int(cnt[1].item())
+
+
 def config_desc(c, B):
     return {"workload": "single instance N=128 full integration: kernel build + adaptive Heun "
                         "solve with two freeze-in sources for sigma in {0.1,1,10,100} "
@@ -415,13 +429,7 @@ def main():
     launches = ctx.launch_count() - launches0
     clk = clocks.stop()
     t_local = total_ms
-    if dist is not None:
-        t = torch.tensor([total_ms], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
-        cnt = torch.tensor([evals, solves], device="cuda", dtype=torch.float64)
-        dist.all_reduce(cnt)
-        evals, solves = int(cnt[0].item()), int(cnt[1].item())
+    total_ms, evals, solves = aggregate_ranks(dist, total_ms, evals, solves, "cuda")
     value = evals / (total_ms / 1e3)
     solves_per_s = solves / (total_ms / 1e3)
     bad = [r for r in results if r["status"] != 0 or not r["converged"]]
