@@ -302,6 +302,16 @@ int kx_mb_fit(kx_ctx *ctx, const kx_kernel *k, int batch, const double *f_dev, d
  * KX_EINVAL for bad arguments, KX_ECUDA if the launch fails. */
 int kx_math_check(kx_ctx *ctx, int which, int n, const double *x_dev, double *out_dev);
 
+/* Pins the FP32 path's streaming variant for grids of n points and batches of
+ * `batch` instances on the context's device, in place of the autotuner's
+ * choice (which is otherwise timed once per (device, n, batch) before the
+ * first launch): 0 = one instance per pass, 1 = two per pass (batch >= 2),
+ * 2 = four per pass, bulk-copy staged (n > 160, batch >= 4); -1 forgets the
+ * pinned or tuned choice.  All variants give bit-identical results; this is
+ * for reproducible timing and for tests.  KX_EINVAL for a variant that does
+ * not apply. */
+int kx_set_stream_variant(kx_ctx *ctx, int n, int batch, int variant);
+
 #ifdef __cplusplus
 }
 #endif

@@ -27,7 +27,7 @@ EXPORTS = (
     "kx_kernel_grid", "kx_kernel_row", "kx_collision", "kx_collision_host", "kx_step",
     "kx_solve", "kx_solve_host", "kx_mb_fit", "kx_launch_count", "kx_time_contraction",
     "kx_collision_noalloc", "kx_server_start", "kx_submit", "kx_poll", "kx_server_get_stats",
-    "kx_server_stop", "kx_math_check",
+    "kx_server_stop", "kx_math_check", "kx_set_stream_variant",
 )
 
 
@@ -125,6 +125,7 @@ def load_library(path: str = LIB_PATH):
         "kx_solve_host": (i, [vp, vp, i, vp, vp, i, ctypes.POINTER(SolveParams), vp, vp]),
         "kx_mb_fit": (i, [vp, vp, i, vp, vp]),
         "kx_math_check": (i, [vp, i, i, vp, vp]),
+        "kx_set_stream_variant": (i, [vp, i, i, i]),
         "kx_launch_count": (ctypes.c_longlong, [vp]),
         "kx_time_contraction": (i, [vp, vp, i, vp, i, ctypes.c_longlong, vp]),
         "kx_collision_noalloc": (i, [vp, vp, i, vp, vp, vp, i]),
@@ -323,6 +324,12 @@ class Context:
         if rc:
             raise self.error(rc, "kx_mb_fit")
         return out
+
+    def set_stream_variant(self, n, batch, variant):
+        """Pin (0, 1, 2) or forget (-1) the streaming variant for (n, batch)."""
+        rc = self.lib.kx_set_stream_variant(self.h, int(n), int(batch), int(variant))
+        if rc:
+            raise self.error(rc, "kx_set_stream_variant")
 
     def math_check(self, which, x):
         """(library value, CUDA value) of log2 (which=0) or exp (which=1) of x

@@ -538,6 +538,8 @@ static int kx_collision_impl(kx_ctx *ctx, const kx_kernel *k, int B, const doubl
     KX_CUDA_TRY(ctx, cudaMemcpyAsync(v.M2, M2.data(), sizeof(double) * B, cudaMemcpyHostToDevice, s));
     KX_CUDA_TRY(ctx, kx_views_clear(k, B, v, s));
     KX_CUDA_TRY(ctx, kx_launch_prep(k, B, f_dev, v, nullptr, s));
+    if (kx_tune_contraction(k, B, v, nullptr, s, &ctx->launches))
+        return kx_set_error(ctx, KX_ECUDA, "contraction autotuning failed");
     KX_CUDA_TRY(ctx, kx_launch_contract(k, B, f_dev, v, nullptr, 1, s));
     KX_CUDA_TRY(ctx, kx_launch_finalize(k, B, f_dev, v, C_dev, project, diag != nullptr, s));
     ctx->launches += 3;
@@ -781,6 +783,8 @@ static int kx_solve_run(kx_ctx *ctx, const kx_kernel *k, int B, const kx_run &r,
     const auto t_start = std::chrono::steady_clock::now();
     KX_CUDA_TRY(ctx, kx_launch_prep(k, B, r.sv.f, r.v, r.sv.st, s));
     ctx->launches += 1;
+    if (kx_tune_contraction(k, B, r.v, r.sv.st, s, &ctx->launches))
+        return kx_set_error(ctx, KX_ECUDA, "contraction autotuning failed");
     const int G = 16;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
@@ -920,6 +924,7 @@ extern "C" int kx_time_contraction(kx_ctx *ctx, const kx_kernel *k, int B, const
     cudaError_t e = kx_views_clear(k, B, v, s);
     if (e == cudaSuccess) e = kx_launch_prep(k, B, f_dev, v, nullptr, s);
     ctx->launches += 1;
+    if (e == cudaSuccess && kx_tune_contraction(k, B, v, nullptr, s, &ctx->launches)) e = cudaErrorUnknown;
     double total = 0.0;
     for (int it = 0; it < iters && e == cudaSuccess; ++it) {
         if (flush) e = cudaMemsetAsync(flush, it & 0xff, (size_t)flush_bytes, s);

@@ -10,7 +10,9 @@
 // projection (Appendix B) and, in the integrator, the Heun stage (Sec. 4.2).
 #include <math.h>
 
+#include <map>
 #include <mutex>
+#include <tuple>
 
 #include "kx_internal.cuh"
 
@@ -879,6 +881,100 @@ static cudaError_t kx_launch_stream_r(const kx_kernel *k, int B, const kx_batch_
     return cudaGetLastError();
 }
 
+// ------------------------------------------------------------ autotuner
+// Streaming variants of the FP32 path: 0 = register pipeline, one instance per
+// pass; 1 = register pipeline, two per pass; 2 = bulk-copy staged, four per pass
+// (units of 128 vectors only).  All give bit-identical results (shared
+// arithmetic, the kernel's fixed bins), so the choice is purely a matter of
+// speed: it is timed once per (device, grid size, batch) on the caller's own
+// prepared inputs and kept for the process.
+static std::mutex g_tune_mu;
+static std::map<std::tuple<int, int, int>, int> g_tuned;
+
+static void kx_stream_candidates(const kx_kernel *k, int B, int *cand, int *nc) {
+    *nc = 0;
+    cand[(*nc)++] = 0;
+    if (B >= 2) cand[(*nc)++] = 1;
+    if (k->vpl == 4 && B >= 4) cand[(*nc)++] = 2;
+}
+
+// The rule used before a size is tuned (measured on this part): two per pass on
+// short rows, four per pass (staged) on long rows with B >= 4.
+static int kx_stream_default(const kx_kernel *k, int B) {
+    if (k->vpl == 2) return B >= 2 ? 1 : 0;
+    return B >= 4 ? 2 : (B >= 2 ? 1 : 0);
+}
+
+static int kx_stream_variant(const kx_kernel *k, int B) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    auto it = g_tuned.find(std::make_tuple(dev, k->n, B));
+    return it != g_tuned.end() ? it->second : kx_stream_default(k, B);
+}
+
+static cudaError_t kx_stream_launch(int variant, const kx_kernel *k, int B, const kx_batch_views &v,
+                                    const kx_inst_state *st, int stage, cudaStream_t s) {
+    if (k->vpl == 2) return variant == 1 ? kx_launch_stream_r<2, 2>(k, B, v, st, stage, s)
+                                         : kx_launch_stream_r<1, 2>(k, B, v, st, stage, s);
+    if (variant == 2) return kx_launch_stream<4, 4>(k, B, v, st, stage, s);
+    if (variant == 1) return kx_launch_stream_r<2, 4>(k, B, v, st, stage, s);
+    return kx_launch_stream_r<1, 4>(k, B, v, st, stage, s);
+}
+
+int kx_tune_contraction(const kx_kernel *k, int B, const kx_batch_views &v, const kx_inst_state *st,
+                        cudaStream_t s, long long *launches) {
+    if (k->precision != KX_FP32) return 0;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    const auto key = std::make_tuple(dev, k->n, B);
+    {
+        std::lock_guard<std::mutex> lock(g_tune_mu);
+        if (g_tuned.count(key)) return 0;
+    }
+    int cand[3], nc = 0;
+    kx_stream_candidates(k, B, cand, &nc);
+    int best = kx_stream_default(k, B);
+    if (nc > 1) {
+        cudaEvent_t e0 = nullptr, e1 = nullptr;
+        cudaError_t e = cudaEventCreate(&e0);
+        if (e == cudaSuccess) e = cudaEventCreate(&e1);
+        float best_ms = 0.f;
+        for (int c = 0; c < nc && e == cudaSuccess; ++c) {
+            e = kx_stream_launch(cand[c], k, B, v, st, 1, s);   // warm
+            if (e == cudaSuccess) e = cudaEventRecord(e0, s);
+            for (int r = 0; r < 3 && e == cudaSuccess; ++r) e = kx_stream_launch(cand[c], k, B, v, st, 1, s);
+            if (e == cudaSuccess) e = cudaEventRecord(e1, s);
+            if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+            float ms = 0.f;
+            if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+            if (launches) *launches += 4;
+            if (e == cudaSuccess && (c == 0 || ms < best_ms)) {
+                best_ms = ms;
+                best = cand[c];
+            }
+        }
+        if (e0) cudaEventDestroy(e0);
+        if (e1) cudaEventDestroy(e1);
+        if (e != cudaSuccess) return -1;
+    }
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    g_tuned[key] = best;
+    return 0;
+}
+
+extern "C" int kx_set_stream_variant(kx_ctx *ctx, int n, int batch, int variant) {
+    if (!ctx || n < 4 || n > KX_MAX_N || batch < 1 || variant < -1 || variant > 2) return KX_EINVAL;
+    const int vpl = n <= 160 ? 2 : 4;
+    if (variant == 1 && batch < 2) return KX_EINVAL;
+    if (variant == 2 && (vpl != 4 || batch < 4)) return KX_EINVAL;
+    const auto key = std::make_tuple(ctx->device, n, batch);
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    if (variant < 0) g_tuned.erase(key);
+    else g_tuned[key] = variant;
+    return KX_OK;
+}
+
 cudaError_t kx_launch_contract(const kx_kernel *k, int B, const double *f, const kx_batch_views &v,
                                const kx_inst_state *st, int stage, cudaStream_t s) {
     const int n = k->n, chunks = v.chunks;
@@ -889,17 +985,8 @@ cudaError_t kx_launch_contract(const kx_kernel *k, int B, const double *f, const
                                              k->d_jl, f, v.lf64, v.partial, st, stage);
         return cudaGetLastError();
     }
-    // Instances per pass: four share each table load on long rows; short rows
-    // (few units per row, latency bound) do better with two per pass and twice
-    // the blocks (measured: N = 128, four instances, 9% per Heun attempt).
-    // four instances per pass (long rows, B >= 4): the staged kernel, whose
-    // register budget fits four accumulators at three blocks per SM; one or two
-    // per pass: the register pipeline (measured faster there)
-    if (k->vpl == 2) return B >= 2 ? kx_launch_stream_r<2, 2>(k, B, v, st, stage, s)
-                                   : kx_launch_stream_r<1, 2>(k, B, v, st, stage, s);
-    if (B >= 4) return kx_launch_stream<4, 4>(k, B, v, st, stage, s);
-    if (B >= 2) return kx_launch_stream_r<2, 4>(k, B, v, st, stage, s);
-    return kx_launch_stream_r<1, 4>(k, B, v, st, stage, s);
+    // the variant tuned for this size and batch (or the default rule)
+    return kx_stream_launch(kx_stream_variant(k, B), k, B, v, st, stage, s);
 }
 
 // ---------------------------------------------------- row combine + projection

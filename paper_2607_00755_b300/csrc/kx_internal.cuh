@@ -164,6 +164,12 @@ cudaError_t kx_launch_count_nnz(const kx_kernel *k, unsigned long long *d_count,
 // prep: f -> (fmax, lf64 | sf, sld); mode selects path
 cudaError_t kx_launch_prep(const kx_kernel *k, int B, const double *f, const kx_batch_views &v,
                            const kx_inst_state *st, cudaStream_t s);
+// Times the FP32 path's streaming variants once per (device, grid size, batch)
+// on the caller's prepared views and keeps the fastest for later launches
+// (including graph captures).  Synchronises the stream; call outside capture.
+// Adds the launches it made to *launches.  0 on success, -1 on a CUDA error.
+int kx_tune_contraction(const kx_kernel *k, int B, const kx_batch_views &v, const kx_inst_state *st,
+                        cudaStream_t s, long long *launches);
 cudaError_t kx_launch_contract(const kx_kernel *k, int B, const double *f, const kx_batch_views &v,
                                const kx_inst_state *st, int stage, cudaStream_t s);
 // finalize for kx_collision: C_out = (proj) C_raw

@@ -223,6 +223,10 @@ static int kx_make_group(kx_server *srv, const Request &r, Group **out) {
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(g->src, sd.data(), sizeof(kx_src_dev) * cap, cudaMemcpyHostToDevice, g->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(g->stream);
+    // pick the streaming variant for this size and slot count before capture
+    // (timed on the group's zeroed tables: same work as real inputs)
+    if (e == cudaSuccess && kx_tune_contraction(k, cap, g->v, nullptr, g->stream, nullptr))
+        e = cudaErrorUnknown;
     // captured graph of attempts_per_tick Heun attempts over all slots
     cudaStream_t cap_s = nullptr;
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&cap_s, cudaStreamNonBlocking);

@@ -227,6 +227,27 @@ def test_collision_steep_f_on_wide_grid(ctx, kx, precision):
         k.release()
 
 
+@pytest.mark.parametrize("N", [48, 200])
+def test_streaming_variants_are_bitwise_identical(ctx, kx, N):
+    """Every streaming variant the autotuner may pick gives the same bits."""
+    q = ki.log_grid(N, 1e-3, 1e2)
+    f = ki.batch_bimodal(np.random.default_rng(19), q, 8)
+    sig = np.linspace(0.5, 4.0, 8)
+    k = ctx.build_kernel(q, precision=kx.FP32)
+    variants = [0, 1] + ([2] if N > 160 else [])
+    out = []
+    for var in variants:
+        ctx.set_stream_variant(N, 8, var)
+        C, _ = ctx.collision(k, dev(f), sig)
+        out.append(C.cpu().numpy())
+    ctx.set_stream_variant(N, 8, -1)
+    for o in out[1:]:
+        np.testing.assert_array_equal(o, out[0])
+    with pytest.raises(kx.KxError):
+        ctx.set_stream_variant(N, 1, 1)
+    k.release()
+
+
 @pytest.mark.parametrize("precision", [0, 1])
 @pytest.mark.parametrize("N", [48, 200])
 def test_batch_is_bitwise_independent_of_co_scheduling(ctx, kx, precision, N):
