@@ -71,13 +71,16 @@ typedef uint64_t kx_ticket;
 /* Momentum grid and kernel options (Appendix A).  q is the comoving momentum
  * grid (host, length n, strictly ascending, > 0); p_i = q_i / a, E_i = sqrt(p_i^2 + m^2);
  * widths Dq_i are the trapezoid widths in q (the paper leaves w_i unspecified).
- * n_mu = Gauss-Legendre nodes of the mu integral of eq. app_F_1d (the paper uses 18). */
+ * n_mu = Gauss-Legendre nodes of the mu integral of eq. app_F_1d (the paper uses 18);
+ * n_mu = 0 builds the exact N_mu -> infinity kernel instead: the mu integral in
+ * closed form, F = |M|^2 pi L / (4 (2 pi)^4 p_i) with L the overlap of
+ * [|p_i - p_n|, p_i + p_n] and [|p_t - p_m|, p_t + p_m] (no quadrature error). */
 typedef struct {
     int n;            /* 4 <= n <= 512 */
     const double *q;  /* host [n] */
     double a;         /* scale factor > 0 (1 for the static box) */
     double mass;      /* m_chi > 0 */
-    int n_mu;         /* 1 <= n_mu <= 64 */
+    int n_mu;         /* 1 <= n_mu <= 64, or 0 (exact angular kernel) */
     int measure;      /* KX_MEASURE_ENERGY | KX_MEASURE_LITERAL */
     int stats;        /* 0 = dilute f3 f4 - f1 f2 (eq. Lambda dilute); +-1 (quantum) -> KX_ENOTSUP */
     int precision;    /* KX_FP64 | KX_FP32 | KX_SPLIT_TF32 */

@@ -239,7 +239,8 @@ extern "C" int kx_build_kernel(kx_ctx *ctx, const kx_grid_desc *d, kx_kernel **o
     const int n = d->n;
     if (n < 4 || n > KX_MAX_N || !d->q) return kx_set_error(ctx, KX_EINVAL, "n must be in [4, 512]");
     if (!(d->a > 0) || !(d->mass > 0)) return kx_set_error(ctx, KX_EINVAL, "a and mass must be > 0");
-    if (d->n_mu < 1 || d->n_mu > KX_MAX_NMU) return kx_set_error(ctx, KX_EINVAL, "n_mu in [1, 64]");
+    if (d->n_mu < 0 || d->n_mu > KX_MAX_NMU)
+        return kx_set_error(ctx, KX_EINVAL, "n_mu in [1, 64], or 0 for the exact angular kernel");
     if (d->measure != KX_MEASURE_ENERGY && d->measure != KX_MEASURE_LITERAL)
         return kx_set_error(ctx, KX_EINVAL, "unknown measure");
     if (d->stats != 0) return kx_set_error(ctx, KX_ENOTSUP, "only dilute statistics are built");
@@ -340,7 +341,7 @@ extern "C" int kx_build_kernel(kx_ctx *ctx, const kx_grid_desc *d, kx_kernel **o
         KX_CHK("upload vectors", cudaMemcpyAsync(d_vt_all, vt.data(), sizeof(uint32_t) * k->V, cudaMemcpyHostToDevice, s));
     kx_gl_nodes gl;
     memset(&gl, 0, sizeof(gl));
-    kx_gauss_legendre(k->n_mu, &gl);
+    if (k->n_mu > 0) kx_gauss_legendre(k->n_mu, &gl);
     KX_CHK("event", cudaEventCreate(&e0));
     KX_CHK("event", cudaEventCreate(&e1));
     KX_CHK("malloc", cudaMalloc(&d_cnt, sizeof(unsigned long long)));

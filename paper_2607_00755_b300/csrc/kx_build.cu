@@ -44,6 +44,23 @@ __device__ double kx_F_unit(double m, double pi, double pn, double pm, double Ei
     return 1.0 * pn * pm / (4.0 * two_pi * two_pi * two_pi * two_pi) * acc;
 }
 
+// The N_mu -> infinity limit of kx_F_unit in closed form (|M|^2 = 1): with
+// k^2 = p_i^2 + p_n^2 - 2 p_i p_n mu, K^2 + A1^2 = p_m^2 k^2 and the Theta
+// condition is the triangle condition k in [|p_t - p_m|, p_t + p_m]; the mu
+// integral of pi / (p_m k) dmu = pi / (p_i p_n p_m) dk gives
+//   F = pi L / (4 (2 pi)^4 p_i),
+// L = max(0, min(p_i + p_n, p_t + p_m) - max(|p_i - p_n|, |p_t - p_m|)).
+__device__ double kx_F_exact_unit(double pi, double pn, double pm, double pt) {
+    double lo1 = fabs(pi - pn), hi1 = pi + pn;
+    double lo2 = fabs(pt - pm), hi2 = pt + pm;
+    double lo = lo1 > lo2 ? lo1 : lo2;
+    double hi = hi1 < hi2 ? hi1 : hi2;
+    double L = hi - lo;
+    if (L < 0.0) L = 0.0;
+    double two_pi = 2.0 * KX_PI;
+    return 1.0 * KX_PI * L / (4.0 * two_pi * two_pi * two_pi * two_pi * pi);
+}
+
 // One thread per (i, pair n <= m).  Writes the symmetrised weight
 // S_inm = W_inm + W_imn (n < m) or W_inn, the bracket j_L and omega_R of
 // eq. (app_interp_weights).  W_inm = mu_n mu_m F_inm / (2 E_i g), g = 1, with
@@ -73,11 +90,15 @@ __global__ void k_build_fp64(int N, long long P, int n_mu, int measure, double m
     double omega = (Et - E[j]) / (E[j + 1] - E[j]);
     double mun = measure == KX_MEASURE_LITERAL ? dp[n] : dE[n];
     double mum = measure == KX_MEASURE_LITERAL ? dp[mm] : dE[mm];
-    double F1 = kx_F_unit(m, p[i], p[n], p[mm], E[i], E[n], E[mm], gl, n_mu);
+    // n_mu = 0: the exact angular kernel (no quadrature)
+    const double pt = n_mu == 0 ? sqrt(Et * Et - m * m) : 0.0;
+    double F1 = n_mu == 0 ? kx_F_exact_unit(p[i], p[n], p[mm], pt)
+                          : kx_F_unit(m, p[i], p[n], p[mm], E[i], E[n], E[mm], gl, n_mu);
     double W1 = mun * mum * F1 / (2.0 * E[i] * 1.0);
     double S = W1;
     if (n != mm) {
-        double F2 = kx_F_unit(m, p[i], p[mm], p[n], E[i], E[mm], E[n], gl, n_mu);
+        double F2 = n_mu == 0 ? kx_F_exact_unit(p[i], p[mm], p[n], pt)
+                              : kx_F_unit(m, p[i], p[mm], p[n], E[i], E[mm], E[n], gl, n_mu);
         double W2 = mum * mun * F2 / (2.0 * E[i] * 1.0);
         S = W1 + W2;
     }

@@ -98,6 +98,32 @@ def test_kernel_tensor_matches_oracle(ctx, kx, N, measure, grid):
     assert info["nonzero_elements"] == int(np.count_nonzero(So))
 
 
+@pytest.mark.parametrize("N", [24, 70])
+def test_exact_angular_kernel_matches_oracle(ctx, kx, N):
+    """n_mu = 0: the closed-form N_mu -> infinity kernel (triangle overlap)
+    against the oracle's exact kernel, element by element; and C on both paths."""
+    q = ki.log_grid(N, 1e-3, 10.0)
+    k = ctx.build_kernel(q, n_mu=0, precision=kx.FP64)
+    Wo = oracle.kernel_tensor(q, angular=oracle.ANG_EXACT)
+    So = sym_pairs(Wo)
+    for i in range(N):
+        W, _, _ = k.row(i)
+        assert np.max(np.abs(W - So[i])) <= 1e-13 * np.max(np.abs(So))
+    f = ki.batch_bimodal(np.random.default_rng(31), q, 2)
+    Co, _ = oracle_C(q, f, [1.0, 2.0], 1, Wo)
+    for prec in (kx.FP64, kx.FP32):
+        kp = ctx.build_kernel(q, n_mu=0, precision=prec)
+        C, _ = ctx.collision(kp, dev(f), np.array([1.0, 2.0]))
+        C = C.cpu().numpy()
+        for b in range(2):
+            assert relerr(C[b], Co[b]) <= TOL[prec]
+        kp.release()
+    # the exact kernel is the limit of the GL kernels (algebraic convergence)
+    Wg = sym_pairs(oracle.kernel_tensor(q, n_mu=18))
+    assert np.max(np.abs(Wg - So)) < 0.05 * np.max(np.abs(So))
+    k.release()
+
+
 def test_build_rejects_bad_grids(ctx, kx):
     with pytest.raises(kx.KxError):
         ctx.build_kernel(np.array([1.0, 2.0, 3.0]))
@@ -432,3 +458,37 @@ def test_table_log2_exp_against_cuda_and_libm(ctx, kx):
     assert out[-1, 0] == np.inf and out[-2, 0] == 0.0 and out[y.size - 9, 0] == 1.0
     nan = ctx.math_check(1, torch.as_tensor(np.array([np.nan]), device="cuda")).cpu().numpy()
     assert np.isnan(nan[0, 0])
+
+
+# ----------------------------------------------- the bench workload itself ---
+def test_bench_workload_n128_four_sigmas_matches_oracle(ctx, kx):
+    """The timed configuration (N = 128, q in [1e-3, 10], the four sigmas
+    sharing one kernel, two sources) in the launch shape the bench uses (one
+    batch of four): C of f0 on both paths against the oracle, and a short
+    adaptive integration (t = 0.005, about 200 steps, sources on) against the
+    oracle's."""
+    c = ki.config2()
+    q, sig, src = c["q"], c["sigmas"], c["sources"]
+    f0 = np.tile(c["f0"], (4, 1))
+    W = oracle.kernel_tensor(q)
+    Co, _ = oracle_C(q, f0, sig, 1, W)
+    par = dict(t_end=0.005, h0=1e-3, rtol=1e-6, atol=1e-12 * f0.max(), l1_tol=1e-3, check_every=10)
+    fo = [oracle.solve(q, W, c["f0"], oracle.M2_from_sigma(1.0, s), sources=src, **par) for s in sig]
+    for prec in (kx.FP64, kx.FP32):
+        k = ctx.build_kernel(q, precision=prec)
+        C, _ = ctx.collision(k, dev(f0), sig)
+        C = C.cpu().numpy()
+        for b in range(4):
+            assert relerr(C[b], Co[b]) <= TOL[prec], (prec, b, relerr(C[b], Co[b]))
+        fd = dev(f0)
+        res = ctx.solve(k, fd, sig, sources=src, **par)
+        f = fd.cpu().numpy()
+        for b in range(4):
+            assert res[b]["status"] == 0 and abs(res[b]["t"] - 0.005) < 1e-12
+            err = relerr(f[b], fo[b][0])
+            if prec == kx.FP64:
+                assert res[b]["steps"] == fo[b][1]["steps"]
+                assert err <= 1e-10, (b, err)
+            else:
+                assert err <= 1e-6, (b, err)
+        k.release()
