@@ -52,7 +52,7 @@ extern "C" {
 #define KX_ENOCONV -7      /* integration hit max_attempts before finishing */
 #define KX_ETIMEOUT -8     /* a bounded device or host wait expired */
 #define KX_ECUDA -9        /* a CUDA runtime/driver call failed (see kx_last_error) */
-#define KX_ENOTSUP -10     /* option not supported by this build (e.g. quantum statistics) */
+#define KX_ENOTSUP -10     /* option not supported by this build (e.g. quantum statistics off the FP64 path) */
 
 /* -------------------------------------------------------------- options */
 #define KX_MEASURE_ENERGY 0   /* W = dE_n dE_m F / (2 E_i g): F of eq. app_F_2d is the kernel of dE_n dE_m (default) */
@@ -82,7 +82,9 @@ typedef struct {
     double mass;      /* m_chi > 0 */
     int n_mu;         /* 1 <= n_mu <= 64, or 0 (exact angular kernel) */
     int measure;      /* KX_MEASURE_ENERGY | KX_MEASURE_LITERAL */
-    int stats;        /* 0 = dilute f3 f4 - f1 f2 (eq. Lambda dilute); +-1 (quantum) -> KX_ENOTSUP */
+    int stats;        /* 0 = dilute f3 f4 - f1 f2 (eq. Lambda dilute); +1 Bose-Einstein, -1
+                         Fermi-Dirac: the factor of eq. Lambda_quantum per element, f_t from the
+                         log interpolation of f (FP64 path only; other paths -> KX_ENOTSUP) */
     int precision;    /* KX_FP64 | KX_FP32 | KX_SPLIT_TF32 */
 } kx_grid_desc;
 

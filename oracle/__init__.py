@@ -8,7 +8,8 @@ contraction); this module only compiles it (``gcc``) and marshals numpy arrays.
 
 Parity status per function (pins live in ``tests/test_oracle_pins.py``):
   grid, gauss_legendre, nu integrals, F, F_exact, kernel_tensor, bracket,
-  collision_tensor, collision_direct, project, source, mb_fit, solve: pinned.
+  collision_tensor, collision_tensor_stats, collision_direct, project, source,
+  mb_fit, solve: pinned.
 """
 from __future__ import annotations
 
@@ -60,6 +61,7 @@ def _load():
         "oracle_kernel_tensor": (i, [i, vp, d, d, d, i, i, i, vp]),
         "oracle_bracket_tensor": (i, [i, vp, d, d, vp, vp]),
         "oracle_collision_tensor": (i, [i, vp, d, d, vp, vp, vp, vp, vp]),
+        "oracle_collision_tensor_stats": (i, [i, vp, d, d, vp, vp, i, vp]),
         "oracle_collision_direct": (i, [i, vp, d, d, d, i, i, vp, vp]),
         "oracle_project": (i, [i, vp, vp, vp, vp, vp, vp]),
         "oracle_source": (None, [i, vp, d, i, vp, vp, vp, vp, vp]),
@@ -180,6 +182,18 @@ def collision_tensor(q, W, f, a=1.0, mass=1.0, parts=False):
     if rc:
         raise ValueError(rc)
     return (C, G, L) if parts else C
+
+
+def collision_tensor_stats(q, W, f, eta, a=1.0, mass=1.0):
+    """C_raw with the quantum statistical factor of eq. (Lambda_quantum):
+    eta = +1 Bose-Einstein, -1 Fermi-Dirac, 0 dilute."""
+    q, W, f = _f64(q), _f64(W), _f64(f)
+    n = q.size
+    C = np.empty(n)
+    rc = _load().oracle_collision_tensor_stats(n, _p(q), a, mass, _p(W), _p(f), int(eta), _p(C))
+    if rc:
+        raise ValueError(rc)
+    return C
 
 
 def collision_direct(q, f, a=1.0, mass=1.0, M2=1.0, n_mu=18, measure=MEASURE_ENERGY):

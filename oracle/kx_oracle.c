@@ -373,6 +373,48 @@ out:
     return rc;
 }
 
+/* Quantum statistics (eq. Lambda_quantum): the statistical factor of the
+ * collision integral with eta = +1 (Bose-Einstein) or -1 (Fermi-Dirac),
+ *   f_n f_m (1 + eta f_i)(1 + eta f_t) - f_i f_t (1 + eta f_n)(1 + eta f_m),
+ * in the discrete sum of eq. (discrete_collision_operator) with f_t from the
+ * log-energy interpolation of f itself (reading A14); eta = 0 is the dilute
+ * factor.  C[i] = sum_nm W_inm * factor (raw, no projection). */
+int oracle_collision_tensor_stats(int n, const double *q, double a, double mass,
+                                  const double *W, const double *f, int eta, double *C) {
+    double *p = malloc(sizeof(double) * n), *E = malloc(sizeof(double) * n);
+    double *dp = malloc(sizeof(double) * n), *dE = malloc(sizeof(double) * n);
+    double *h = malloc(sizeof(double) * n), *lf = malloc(sizeof(double) * n);
+    int rc = OR_OK;
+    if (eta < -1 || eta > 1) return OR_EINVAL;
+    if (!p || !E || !dp || !dE || !h || !lf) { rc = OR_ENOMEM; goto out; }
+    rc = oracle_grid(n, q, a, mass, p, E, dp, dE, h);
+    if (rc) goto out;
+    for (int j = 0; j < n; ++j) lf[j] = log_floor(f[j]);
+    const double et = (double)eta;
+#pragma omp parallel for schedule(dynamic)
+    for (int i = 0; i < n; ++i) {
+        double Ci = 0.0;
+        for (int nn = 0; nn < n; ++nn) {
+            for (int mm = 0; mm < n; ++mm) {
+                double Wv = W[((size_t)i * n + nn) * n + mm];
+                if (Wv == 0.0) continue;
+                double Et = (E[nn] + E[mm]) - E[i];
+                int j;
+                double om;
+                if (!oracle_bracket(n, E, Et, &j, &om)) continue;
+                double ft = exp((1.0 - om) * lf[j] + om * lf[j + 1]);
+                double gain = f[nn] * f[mm] * (1.0 + et * f[i]) * (1.0 + et * ft);
+                double loss = f[i] * ft * (1.0 + et * f[nn]) * (1.0 + et * f[mm]);
+                Ci += Wv * (gain - loss);
+            }
+        }
+        C[i] = Ci;
+    }
+out:
+    free(p); free(E); free(dp); free(dE); free(h); free(lf);
+    return rc;
+}
+
 /* Direct form: the same sum with F evaluated on the fly from the printed
  * arcsin form of eq. (app_I_mu) (no stored tensor). */
 int oracle_collision_direct(int n, const double *q, double a, double mass, double M2,

@@ -243,7 +243,9 @@ extern "C" int kx_build_kernel(kx_ctx *ctx, const kx_grid_desc *d, kx_kernel **o
         return kx_set_error(ctx, KX_EINVAL, "n_mu in [1, 64], or 0 for the exact angular kernel");
     if (d->measure != KX_MEASURE_ENERGY && d->measure != KX_MEASURE_LITERAL)
         return kx_set_error(ctx, KX_EINVAL, "unknown measure");
-    if (d->stats != 0) return kx_set_error(ctx, KX_ENOTSUP, "only dilute statistics are built");
+    if (d->stats < -1 || d->stats > 1) return kx_set_error(ctx, KX_EINVAL, "stats in {-1, 0, +1}");
+    if (d->stats != 0 && d->precision != KX_FP64)
+        return kx_set_error(ctx, KX_ENOTSUP, "quantum statistics are built on the FP64 path only");
     if (d->precision != KX_FP64 && d->precision != KX_FP32 && d->precision != KX_SPLIT_TF32)
         return kx_set_error(ctx, KX_ENOTSUP, "precision not available in this build");
     for (int i = 0; i < n; ++i) {
@@ -259,6 +261,7 @@ extern "C" int kx_build_kernel(kx_ctx *ctx, const kx_grid_desc *d, kx_kernel **o
     k->device = ctx->device;
     k->n = n;
     k->n_mu = d->n_mu;
+    k->stats = d->stats;
     k->measure = d->measure;
     k->precision = d->precision;
     k->a = d->a;

@@ -341,7 +341,7 @@ __global__ void __launch_bounds__(KX_T64)
                  const double *__restrict__ W, const double *__restrict__ om,
                  const uint16_t *__restrict__ jl, const double *__restrict__ f,
                  const double *__restrict__ lf, double2 *__restrict__ partial,
-                 const kx_inst_state *__restrict__ st, int stage) {
+                 const kx_inst_state *__restrict__ st, int stage, int eta) {
     const int c = blockIdx.x, i = blockIdx.y, b = blockIdx.z;
     if (st && (st[b].done || (stage == 2 && st[b].skip2))) return;
     __shared__ double s_f[KX_MAX_N], s_l[KX_MAX_N];
@@ -364,8 +364,17 @@ __global__ void __launch_bounds__(KX_T64)
                 int nn = pr & 0xffff, mm = pr >> 16;
                 int j = jl[base + pidx];
                 double o = om[base + pidx];
-                g += w * (s_f[nn] * s_f[mm]);
-                l += w * exp((1.0 - o) * s_l[j] + o * s_l[j + 1]);
+                const double ft = exp((1.0 - o) * s_l[j] + o * s_l[j + 1]);
+                if (eta == 0) {
+                    g += w * (s_f[nn] * s_f[mm]);
+                    l += w * ft;
+                } else {
+                    // quantum statistical factor (eq. Lambda_quantum), per element
+                    const double et = (double)eta, fi = s_f[i];
+                    const double gain = s_f[nn] * s_f[mm] * (1.0 + et * fi) * (1.0 + et * ft);
+                    const double loss = fi * ft * (1.0 + et * s_f[nn]) * (1.0 + et * s_f[mm]);
+                    g += w * (gain - loss);   // L stays 0: C = G
+                }
             }
         }
     }
@@ -982,7 +991,7 @@ cudaError_t kx_launch_contract(const kx_kernel *k, int B, const double *f, const
     if (k->precision == KX_FP64) {
         dim3 grid(chunks, n, B);
         k_contract64<<<grid, KX_T64, 0, s>>>(n, k->P, chunks, k->d_pair, k->d_W64, k->d_om64,
-                                             k->d_jl, f, v.lf64, v.partial, st, stage);
+                                             k->d_jl, f, v.lf64, v.partial, st, stage, k->stats);
         return cudaGetLastError();
     }
     // the variant tuned for this size and batch (or the default rule)

@@ -33,6 +33,7 @@ struct kx_kernel {
     int refcount;
     int device;
     int n, n_mu, measure, precision;
+    int stats;           // 0 dilute, +1 Bose-Einstein, -1 Fermi-Dirac (FP64 path)
     double a, mass;
     long long P;         // pairs n <= m: n(n+1)/2
     int V;               // 4-element vectors per row (FP32 layout, segments padded to 4)

@@ -133,8 +133,11 @@ def test_build_rejects_bad_grids(ctx, kx):
         ctx.build_kernel(ki.log_grid(513, 1e-3, 10.0))
     with pytest.raises(kx.KxError):
         ctx.build_kernel(ki.log_grid(16, 1e-3, 10.0), mass=0.0)
+    with pytest.raises(kx.KxError) as ei:
+        ctx.build_kernel(ki.log_grid(16, 1e-3, 10.0), stats=1, precision=kx.FP32)
+    assert ei.value.code == kx.ENOTSUP
     with pytest.raises(kx.KxError):
-        ctx.build_kernel(ki.log_grid(16, 1e-3, 10.0), stats=1)
+        ctx.build_kernel(ki.log_grid(16, 1e-3, 10.0), stats=2)
 
 
 # ------------------------------------------------------------ collision ----
@@ -492,3 +495,34 @@ def test_bench_workload_n128_four_sigmas_matches_oracle(ctx, kx):
             else:
                 assert err <= 1e-6, (b, err)
         k.release()
+
+
+# ------------------------------------------------------ quantum statistics ---
+@pytest.mark.parametrize("eta", [1, -1])
+def test_quantum_statistics_fp64_path_matches_oracle(ctx, kx, eta):
+    """Bose-Einstein / Fermi-Dirac factor (eq. Lambda_quantum) on the FP64 path:
+    C raw and projected against the oracle on a bimodal f scaled to occupations
+    of order one (where the factor matters), and the near-vanishing C on the
+    equilibrium distribution of that statistics."""
+    N = 40
+    q = ki.log_grid(N, 1e-2, 20.0)
+    g = oracle.grid(q)
+    W = oracle.kernel_tensor(q)
+    f = 0.8 * ki.batch_bimodal(np.random.default_rng(43 + eta), q, 2)
+    k = ctx.build_kernel(q, precision=kx.FP64, stats=eta)
+    for project in (0, 1):
+        C, _ = ctx.collision(k, dev(f), np.array([1.0, 3.0]), project=bool(project))
+        C = C.cpu().numpy()
+        for b, sgm in enumerate((1.0, 3.0)):
+            Co = oracle.collision_tensor_stats(q, W, f[b], eta) * oracle.M2_from_sigma(1.0, sgm)
+            if project:
+                Co, _ = oracle.project(g["E"], g["h"], f[b], Co)
+            assert relerr(C[b], Co) <= 1e-12, (project, b, relerr(C[b], Co))
+    feq = 1.0 / (np.exp((g["E"] - 0.6) / 0.7) - eta)
+    C, _ = ctx.collision(k, dev(feq[None]), 1.0, project=False)
+    Co = oracle.collision_tensor_stats(q, W, feq, eta) * oracle.M2_from_sigma(1.0, 1.0)
+    _, G, _ = oracle.collision_tensor(q, W, feq, parts=True)
+    scale = oracle.M2_from_sigma(1.0, 1.0) * np.max(G)
+    assert np.max(np.abs(C.cpu().numpy()[0] - Co)) <= 1e-13 * scale
+    assert np.max(np.abs(Co)) < 2e-2 * scale
+    k.release()

@@ -465,3 +465,38 @@ def test_fixed_step_negative_stage_is_an_error():
     M2 = oracle.M2_from_sigma(1.0, 1.0)
     f, res = oracle.solve(q, W, f0, M2, t_end=100.0, h0=50.0, fixed_step=1)
     assert res["status"] in (oracle.ENEG, oracle.ENONFINITE)
+
+
+# ------------------------------------------------ quantum statistics (f2) ---
+def test_quantum_statistics_dilute_limit_is_bitwise_the_dilute_operator():
+    """eta = 0 in the statistical factor of eq. (Lambda_quantum) is the dilute
+    factor f_n f_m - f_i f_t of the same sum."""
+    q = ki.log_grid(20, 1e-3, 10.0)
+    f = ki.bimodal(np.random.default_rng(41), q)
+    W = oracle.kernel_tensor(q)
+    np.testing.assert_array_equal(oracle.collision_tensor_stats(q, W, f, 0),
+                                  oracle.collision_tensor(q, W, f))
+
+
+@pytest.mark.parametrize("eta", [1, -1])
+def test_quantum_equilibrium_is_a_fixed_point_in_the_continuum_limit(eta):
+    """Bose-Einstein (eta = +1) and Fermi-Dirac (eta = -1) equilibria
+    f = 1/(exp((E - mu)/T) - eta) make the continuum factor vanish pointwise,
+    so the discrete C -> 0 as the grid is refined (second order: the log-energy
+    interpolation of a non-log-linear f is the only error); the dilute factor
+    on the same f, and the factor with the opposite eta, do not vanish."""
+    res, dil, wrong = [], [], []
+    for N in (24, 48, 96):
+        q = ki.log_grid(N, 1e-2, 20.0)
+        E = oracle.grid(q)["E"]
+        f = 1.0 / (np.exp((E - 0.6) / 0.7) - eta)
+        W = oracle.kernel_tensor(q)
+        _, G, _ = oracle.collision_tensor(q, W, f, parts=True)
+        sc = np.max(np.abs(G))
+        res.append(np.max(np.abs(oracle.collision_tensor_stats(q, W, f, eta))) / sc)
+        dil.append(np.max(np.abs(oracle.collision_tensor_stats(q, W, f, 0))) / sc)
+        wrong.append(np.max(np.abs(oracle.collision_tensor_stats(q, W, f, -eta))) / sc)
+    for a, b in zip(res[:-1], res[1:]):
+        assert 3.0 < a / b < 5.5, res
+    assert res[-1] < 2e-3
+    assert min(dil) > 0.05 and min(wrong) > 0.05
