@@ -21,7 +21,6 @@
 #define KX_ATILE 4096              // floats per A tile: 128 rows x 32 k
 #define KX_BTILE 2048              // floats per B tile: 64 rows x 32 k
 #define KX_GEMM_SMEM (65536 + 32768 + 64)
-#define KX_LOSS_WARPS 16           // warps per loss block (one shared instance table)
 
 #include "kx_ptx.cuh"
 
@@ -72,10 +71,6 @@ __device__ __forceinline__ float kx_ex2f(float x) {
     asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
     return y;
 }
-__device__ __forceinline__ float kx_omega(uint32_t w) {
-    return __uint_as_float(0x3f800000u | (w & 0x7fffffu)) - 1.0f;
-}
-
 // --------------------------------------------------------- gain GEMM (T)
 // One CTA (4 warps) per (128-row M tile, 64-instance N tile).  Thread 0 stages
 // the hi/lo operand tiles of each 32-wide k block with bulk copies into a
@@ -193,83 +188,167 @@ __global__ void __launch_bounds__(128)
 }
 
 // ------------------------------------------------------------- exact loss
-// One block per (row i, group of 32 instances); lane = instance.  The row's
-// nonzero elements, sorted by bracket j_L, are split into 16 contiguous ranges
-// (one per warp); each element's (S, j_L, omega) is warp-uniform.  A warp walks
-// its range group by group (all elements of a group share j_L, so the lane's
-// (l2_j, l2_{j+1} - l2_j) is read once per group) with a branch-free loop of
-// four independent accumulators.  Per element and instance: one FMA for the
-// interpolated exponent, one ex2, one FMA; group sums are added in FP64.  The
-// block also forms the gain G_ib = sum_n f'_nb T_(i n) b from the GEMM output.
-__global__ void __launch_bounds__(KX_LOSS_WARPS * 32)
-    k_batch_loss(int n, int B, int Bpad, const uint2 *__restrict__ lel,
-                 const int *__restrict__ lrow, const int *__restrict__ lgrp,
-                 const float2 *__restrict__ td,
+// A row's nonzero elements are sorted by bracket j_L and cut into segments of at
+// most 32 elements with one j_L each (host build); an element is (S_inm, omega)
+// as two floats.  One block per (group of 32 IPL instances, row); lane l holds
+// instances l, l + 32, ... of the group.  The block loads its instances'
+// (l2_j, D_j) tables once (IPL float2 per lane and j, read coalesced from the
+// instance-minor td); the row's segments go round-robin to the warps.  A warp
+// loads a segment's elements with one coalesced load (the next segment's are in
+// flight meanwhile) into its shared-memory slot, reads its (l2_j, D_j) once,
+// and then per element and instance spends one FMA (interpolated exponent), one
+// ex2 and one FMA (weight): the element's own decode is a broadcast read of two
+// floats shared by the IPL instances.  Each segment's FP32 sums go into a
+// double-float accumulator (exact TwoSum), FP64 across warps.  The block also
+// forms the gain G_ib = sum_n f'_nb T_(i n) b from the GEMM output.  Rows are
+// taken longest first (lorder) so that the short ones fill the tail.
+__device__ __forceinline__ void kx_two_sum_f(float a, float b, float &s, float &e) {
+    s = a + b;
+    const float bv = s - a;
+    e = (a - (s - bv)) + (b - bv);
+}
+
+template <int IPL, int WARPS>
+__global__ void __launch_bounds__(WARPS * 32, WARPS <= 16 ? 2 : 1)
+    k_batch_loss(int n, int B, int tds, int Bpad, const float2 *__restrict__ lel,
+                 const int2 *__restrict__ lseg, const int *__restrict__ lsrow,
+                 const int *__restrict__ lorder, const float2 *__restrict__ td,
                  const float *__restrict__ fT, const float *__restrict__ T,
                  const double *__restrict__ fmax, double2 *__restrict__ partial,
                  const kx_inst_state *__restrict__ st, int stage) {
-    extern __shared__ float2 kx_ltab[];   // [n][32]
-    __shared__ double red[2][KX_LOSS_WARPS][32];
-    const int i = blockIdx.y;
+    // [n][32][IPL] (l2_j, D_j) table; after the loss loop the same space holds
+    // the cross-warp reduction [2][WARPS][32 IPL] doubles
+    extern __shared__ __align__(16) float2 kx_ltab[];
+    __shared__ __align__(16) float2 s_el[WARPS][32];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int b = blockIdx.x * 32 + lane;
-    const bool act = b < B && !(st && (st[b].done || (stage == 2 && st[b].skip2)));
-    if (!__syncthreads_or(act)) return;
-    for (int j = warp; j < n; j += KX_LOSS_WARPS)
-        kx_ltab[j * 32 + lane] = act ? td[(long long)b * n + j] : make_float2(-2000.f, 0.f);
+    int b[IPL];
+    bool act[IPL];
+    bool any = false;
+#pragma unroll
+    for (int s = 0; s < IPL; ++s) {
+        b[s] = blockIdx.x * (32 * IPL) + s * 32 + lane;
+        act[s] = b[s] < B && !(st && (st[b[s]].done || (stage == 2 && st[b[s]].skip2)));
+        any |= act[s];
+    }
+    if (!__syncthreads_or(any)) return;
+    for (int j = warp; j < n; j += WARPS)
+#pragma unroll
+        for (int s = 0; s < IPL; ++s)
+            kx_ltab[(j * 32 + lane) * IPL + s] =
+                act[s] ? td[(size_t)j * tds + b[s]] : make_float2(-2000.f, 0.f);
     __syncthreads();
-    const int e0 = lrow[i], e1 = lrow[i + 1];
-    const int per = (e1 - e0 + KX_LOSS_WARPS - 1) / KX_LOSS_WARPS;
-    const int ea = e0 + warp * per, eb = min(e1, ea + per);
-    const int *gs = lgrp + (size_t)i * (n + 1);   // first element of each bracket group j
-    double accd = 0.0;
-    int e = ea;
-    while (e < eb) {
-        // one bracket group: (l2_j, l2_{j+1} - l2_j) of this lane's instance is fixed
-        const int j = __ldg(&lel[e].y) >> 23;
-        const int gend = min(eb, __ldg(gs + j + 1));
-        const float2 t = kx_ltab[j * 32 + lane];
-        float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
-        for (; e + 8 <= gend; e += 8) {
-            uint2 x[8];
+    const int i = lorder[blockIdx.y];
+    const int g0 = lsrow[i], g1 = lsrow[i + 1];
+    float hi[IPL], lo[IPL];
 #pragma unroll
-            for (int q = 0; q < 8; ++q) x[q] = __ldg(lel + e + q);
+    for (int s = 0; s < IPL; ++s) hi[s] = lo[s] = 0.f;
+    int g = g0 + warp;
+    int2 dsc = make_int2(0, 0);
+    float2 el = make_float2(0.f, 0.f);
+    if (g < g1) {
+        dsc = __ldg(lseg + g);
+        if (lane < (dsc.y & 63)) el = __ldg(lel + dsc.x + lane);
+    }
+    for (; g < g1; g += WARPS) {
+        int2 dn = dsc;
+        float2 en = make_float2(0.f, 0.f);
+        if (g + WARPS < g1) {
+            dn = __ldg(lseg + g + WARPS);
+            if (lane < (dn.y & 63)) en = __ldg(lel + dn.x + lane);
+        }
+        s_el[warp][lane] = el;   // lanes past the count hold (0, 0): weight 0
+        __syncwarp();
+        const int j = dsc.y >> 8, c4 = ((dsc.y & 63) + 3) & ~3;
+        float2 t[IPL];
+        if constexpr (IPL == 2) {
+            const float4 q = reinterpret_cast<const float4 *>(kx_ltab)[j * 32 + lane];
+            t[0] = make_float2(q.x, q.y);
+            t[1] = make_float2(q.z, q.w);
+        } else {
+            t[0] = kx_ltab[j * 32 + lane];
+        }
+        float a[IPL][4];
 #pragma unroll
-            for (int q = 0; q < 8; q += 4) {
-                a0 = fmaf(__uint_as_float(x[q].x), kx_ex2f(fmaf(kx_omega(x[q].y), t.y, t.x)), a0);
-                a1 = fmaf(__uint_as_float(x[q + 1].x), kx_ex2f(fmaf(kx_omega(x[q + 1].y), t.y, t.x)), a1);
-                a2 = fmaf(__uint_as_float(x[q + 2].x), kx_ex2f(fmaf(kx_omega(x[q + 2].y), t.y, t.x)), a2);
-                a3 = fmaf(__uint_as_float(x[q + 3].x), kx_ex2f(fmaf(kx_omega(x[q + 3].y), t.y, t.x)), a3);
+        for (int s = 0; s < IPL; ++s) a[s][0] = a[s][1] = a[s][2] = a[s][3] = 0.f;
+        const float4 *e4 = reinterpret_cast<const float4 *>(s_el[warp]);
+        for (int q = 0; q < c4; q += 4) {
+            const float4 x01 = e4[q >> 1], x23 = e4[(q >> 1) + 1];
+#pragma unroll
+            for (int s = 0; s < IPL; ++s) {
+                a[s][0] = fmaf(x01.x, kx_ex2f(fmaf(x01.y, t[s].y, t[s].x)), a[s][0]);
+                a[s][1] = fmaf(x01.z, kx_ex2f(fmaf(x01.w, t[s].y, t[s].x)), a[s][1]);
+                a[s][2] = fmaf(x23.x, kx_ex2f(fmaf(x23.y, t[s].y, t[s].x)), a[s][2]);
+                a[s][3] = fmaf(x23.z, kx_ex2f(fmaf(x23.w, t[s].y, t[s].x)), a[s][3]);
             }
         }
-        for (; e < gend; ++e) {
-            const uint2 x0 = __ldg(lel + e);
-            a0 = fmaf(__uint_as_float(x0.x), kx_ex2f(fmaf(kx_omega(x0.y), t.y, t.x)), a0);
-        }
-        accd += (double)((a0 + a1) + (a2 + a3));
-    }
-    float g = 0.f;
-    for (int nn = warp; nn < n; nn += KX_LOSS_WARPS)
-        g = fmaf(fT[(size_t)nn * Bpad + b], T[((size_t)i * n + nn) * Bpad + b], g);
-    red[0][warp][lane] = accd;
-    red[1][warp][lane] = g;
-    __syncthreads();
-    if (warp == 0 && act) {
-        double L = 0.0, G = 0.0;
 #pragma unroll
-        for (int w = 0; w < KX_LOSS_WARPS; ++w) {
-            L += red[0][w][lane];
-            G += red[1][w][lane];
+        for (int s = 0; s < IPL; ++s) {
+            float sm, er;
+            kx_two_sum_f(hi[s], (a[s][0] + a[s][1]) + (a[s][2] + a[s][3]), sm, er);
+            hi[s] = sm;
+            lo[s] += er;
         }
-        const double fm = fmax[b];
-        partial[(size_t)b * n + i] = make_double2(fm * fm * G, fm * L);
+        __syncwarp();   // the slot is refilled next segment
+        dsc = dn;
+        el = en;
     }
+    float gs[IPL];
+#pragma unroll
+    for (int s = 0; s < IPL; ++s) gs[s] = 0.f;
+    for (int nn = warp; nn < n; nn += WARPS) {
+        const float *fr = fT + (size_t)nn * Bpad;
+        const float *tr = T + ((size_t)i * n + nn) * Bpad;
+#pragma unroll
+        for (int s = 0; s < IPL; ++s) gs[s] = fmaf(fr[b[s]], tr[b[s]], gs[s]);
+    }
+    __syncthreads();   // every warp is done with the table
+    double *red = reinterpret_cast<double *>(kx_ltab);   // [2][WARPS][32 IPL]
+#pragma unroll
+    for (int s = 0; s < IPL; ++s) {
+        red[warp * 32 * IPL + s * 32 + lane] = (double)hi[s] + (double)lo[s];
+        red[(WARPS + warp) * 32 * IPL + s * 32 + lane] = gs[s];
+    }
+    __syncthreads();
+    if (warp < IPL) {
+        const int s = warp;   // warp s finishes instance slot s
+        const int bb = blockIdx.x * (32 * IPL) + s * 32 + lane;
+        if (bb < B && !(st && (st[bb].done || (stage == 2 && st[bb].skip2)))) {
+            double L = 0.0, G = 0.0;
+#pragma unroll
+            for (int w = 0; w < WARPS; ++w) {
+                L += red[w * 32 * IPL + s * 32 + lane];
+                G += red[(WARPS + w) * 32 * IPL + s * 32 + lane];
+            }
+            const double fm = fmax[bb];
+            partial[(size_t)bb * n + i] = make_double2(fm * fm * G, fm * L);
+        }
+    }
+}
+
+// Loss-kernel shape for an n-point grid: two instances per lane while the
+// table (n x 32 x 2 float2) leaves room for two 16-warp blocks per SM or, up to
+// n = 400, for one 32-warp block; one instance per lane (32 warps) above that.
+struct kx_loss_shape {
+    int ipl, warps;
+};
+static kx_loss_shape kx_loss_shape_for(int n) {
+    if (n <= 212) return {2, 16};
+    if (n <= 400) return {2, 32};
+    return {1, 32};
+}
+// dynamic shared memory: the table, or the reduction if that is larger
+static size_t kx_loss_smem(int n, kx_loss_shape sh) {
+    return std::max((size_t)n, (size_t)2 * sh.warps) * 32 * sh.ipl * sizeof(float2);
 }
 
 void kx_batch_prepare() {
     cudaFuncSetAttribute(k_gain_mma, cudaFuncAttributeMaxDynamicSharedMemorySize, KX_GEMM_SMEM);
-    cudaFuncSetAttribute(k_batch_loss, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         KX_MAX_N * 32 * (int)sizeof(float2));
+    cudaFuncSetAttribute(k_batch_loss<2, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)kx_loss_smem(212, {2, 16}));
+    cudaFuncSetAttribute(k_batch_loss<2, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)kx_loss_smem(400, {2, 32}));
+    cudaFuncSetAttribute(k_batch_loss<1, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)kx_loss_smem(KX_MAX_N, {1, 32}));
     cudaGetLastError();
 }
 
@@ -281,10 +360,19 @@ cudaError_t kx_launch_batch_contract(const kx_kernel *k, int B, const kx_batch_v
     k_gain_mma<<<g1, 128, KX_GEMM_SMEM, s>>>(k->d_Atile, v.bt, v.T, KB, v.Bpad, d_err);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    dim3 g2((B + 31) / 32, k->n);
-    k_batch_loss<<<g2, KX_LOSS_WARPS * 32, (size_t)k->n * 32 * sizeof(float2), s>>>(
-        k->n, B, v.Bpad, k->d_lel, k->d_lrow, k->d_lgrp, v.td, v.fT, v.T, v.fmax, v.partial, st,
-        stage);
+    const kx_loss_shape sh = kx_loss_shape_for(k->n);
+    const int per = 32 * sh.ipl;
+    dim3 g2((B + per - 1) / per, k->n);
+    const size_t smem = kx_loss_smem(k->n, sh);
+    if (sh.ipl == 2 && sh.warps == 16)
+        k_batch_loss<2, 16><<<g2, 512, smem, s>>>(k->n, B, v.B, v.Bpad, k->d_lel, k->d_lseg, k->d_lsrow,
+                                                  k->d_lorder, v.td, v.fT, v.T, v.fmax, v.partial, st, stage);
+    else if (sh.ipl == 2)
+        k_batch_loss<2, 32><<<g2, 1024, smem, s>>>(k->n, B, v.B, v.Bpad, k->d_lel, k->d_lseg, k->d_lsrow,
+                                                   k->d_lorder, v.td, v.fT, v.T, v.fmax, v.partial, st, stage);
+    else
+        k_batch_loss<1, 32><<<g2, 1024, smem, s>>>(k->n, B, v.B, v.Bpad, k->d_lel, k->d_lseg, k->d_lsrow,
+                                                   k->d_lorder, v.td, v.fT, v.T, v.fmax, v.partial, st, stage);
     return cudaGetLastError();
 }
 
@@ -292,8 +380,10 @@ cudaError_t kx_launch_batch_contract(const kx_kernel *k, int B, const kx_batch_v
 // From the device FP64 tables (symmetrised S over n <= m, j_L, omega):
 //  A tiles: W_full[(i n)][m] = S_inm / 2 (n != m), S_inn (n = m), TF32 hi/lo
 //           (hi rounded to nearest TF32, lo = W - hi), in MMA operand tiles;
-//  loss list: per row, the nonzero S with packed (j_L, omega) sorted by j_L
-//           (omega rounding to 1 stored as (j_L + 1, 0), as in the FP32 path).
+//  loss list: per row, the nonzero (S, omega) as floats sorted by j_L, cut into
+//           segments of at most 32 elements of one j_L: (first element,
+//           j_L << 8 | count) per segment, rows' segment offsets, and the rows
+//           ordered by element count, longest first.
 static float kx_tf32_round(float x) {
     uint32_t u;
     memcpy(&u, &x, 4);
@@ -318,12 +408,16 @@ int kx_batch_build_tables(kx_ctx *ctx, kx_kernel *k) {
     k->Kpad = ((n + 31) / 32) * 32;
     const int MT = k->Mpad / 128, KB = k->Kpad / 32;
     std::vector<float> At((size_t)MT * KB * 2 * KX_ATILE, 0.f);
-    std::vector<uint2> lel;
-    std::vector<int> lrow(n + 1, 0);
-    std::vector<int> lgrp((size_t)n * (n + 1), 0);
+    std::vector<float2> lel;
+    std::vector<int2> lseg;
+    std::vector<int> lsrow(n + 1, 0), rlen(n, 0);
     std::vector<long long> base(n);
     for (int a = 0; a < n; ++a) base[a] = (long long)a * n - (long long)a * (a - 1) / 2;
-    std::vector<std::pair<uint32_t, uint32_t>> row;
+    struct El {
+        int j;
+        float w, om;
+    };
+    std::vector<El> row;
     for (int i = 0; i < n; ++i) {
         row.clear();
         for (int a = 0; a < n; ++a) {
@@ -339,47 +433,42 @@ int kx_batch_build_tables(kx_ctx *ctx, kx_kernel *k) {
                 const size_t t = ((size_t)mt * KB + kb) * 2;
                 At[t * KX_ATILE + kx_tile_offset(rl, kk)] = wh;
                 At[(t + 1) * KX_ATILE + kx_tile_offset(rl, kk)] = wl;
-                if (a <= b && W[e] != 0.0) {
-                    uint32_t j = jl[e];
-                    double q = rint(om[e] * 8388608.0);
-                    if (q >= 8388608.0) {
-                        j += 1;
-                        q = 0.0;
-                    }
-                    const float ws = (float)W[e];
-                    uint32_t wb;
-                    memcpy(&wb, &ws, 4);
-                    row.push_back({wb, (j << 23) | (uint32_t)q});
-                }
+                if (a <= b && W[e] != 0.0) row.push_back({(int)jl[e], (float)W[e], (float)om[e]});
             }
         }
-        std::stable_sort(row.begin(), row.end(), [](const std::pair<uint32_t, uint32_t> &x,
-                                                    const std::pair<uint32_t, uint32_t> &y) {
-            return (x.second >> 23) < (y.second >> 23);
-        });
-        const int row0 = (int)lel.size();
-        size_t pos = 0;
-        for (int j = 0; j <= n; ++j) {
-            while (pos < row.size() && (int)(row[pos].second >> 23) < j) ++pos;
-            lgrp[(size_t)i * (n + 1) + j] = row0 + (int)pos;
+        std::stable_sort(row.begin(), row.end(), [](const El &x, const El &y) { return x.j < y.j; });
+        size_t p0 = 0;
+        while (p0 < row.size()) {
+            size_t p1 = p0;
+            while (p1 < row.size() && row[p1].j == row[p0].j && p1 - p0 < 32) ++p1;
+            lseg.push_back(make_int2((int)lel.size(), (row[p0].j << 8) | (int)(p1 - p0)));
+            for (size_t q = p0; q < p1; ++q) lel.push_back(make_float2(row[q].w, row[q].om));
+            p0 = p1;
         }
-        for (auto &p : row) lel.push_back(make_uint2(p.first, p.second));
-        lrow[i + 1] = (int)lel.size();
+        rlen[i] = (int)row.size();
+        lsrow[i + 1] = (int)lseg.size();
     }
-    if (lel.empty()) lel.push_back(make_uint2(0u, 0u));
+    std::vector<int> lorder(n);
+    std::iota(lorder.begin(), lorder.end(), 0);
+    std::stable_sort(lorder.begin(), lorder.end(), [&](int x, int y) { return rlen[x] > rlen[y]; });
+    if (lel.empty()) lel.push_back(make_float2(0.f, 0.f));
+    if (lseg.empty()) lseg.push_back(make_int2(0, 0));
     if (cudaMalloc(&k->d_Atile, sizeof(float) * At.size()) != cudaSuccess ||
-        cudaMalloc(&k->d_lel, sizeof(uint2) * lel.size()) != cudaSuccess ||
-        cudaMalloc(&k->d_lrow, sizeof(int) * lrow.size()) != cudaSuccess ||
-        cudaMalloc(&k->d_lgrp, sizeof(int) * lgrp.size()) != cudaSuccess) {
+        cudaMalloc(&k->d_lel, sizeof(float2) * lel.size()) != cudaSuccess ||
+        cudaMalloc(&k->d_lseg, sizeof(int2) * lseg.size()) != cudaSuccess ||
+        cudaMalloc(&k->d_lsrow, sizeof(int) * lsrow.size()) != cudaSuccess ||
+        cudaMalloc(&k->d_lorder, sizeof(int) * lorder.size()) != cudaSuccess) {
         cudaGetLastError();
         return kx_set_error(ctx, KX_ENOMEM, "batched build: allocation failed");
     }
-    k->bytes += (long long)(sizeof(float) * At.size() + sizeof(uint2) * lel.size() +
-                            sizeof(int) * (lrow.size() + lgrp.size()));
+    k->nseg = (long long)lsrow[n];
+    k->bytes += (long long)(sizeof(float) * At.size() + sizeof(float2) * lel.size() +
+                            sizeof(int2) * lseg.size() + sizeof(int) * (lsrow.size() + lorder.size()));
     if (cudaMemcpy(k->d_Atile, At.data(), sizeof(float) * At.size(), cudaMemcpyHostToDevice) != cudaSuccess ||
-        cudaMemcpy(k->d_lel, lel.data(), sizeof(uint2) * lel.size(), cudaMemcpyHostToDevice) != cudaSuccess ||
-        cudaMemcpy(k->d_lrow, lrow.data(), sizeof(int) * lrow.size(), cudaMemcpyHostToDevice) != cudaSuccess ||
-        cudaMemcpy(k->d_lgrp, lgrp.data(), sizeof(int) * lgrp.size(), cudaMemcpyHostToDevice) != cudaSuccess)
+        cudaMemcpy(k->d_lel, lel.data(), sizeof(float2) * lel.size(), cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(k->d_lseg, lseg.data(), sizeof(int2) * lseg.size(), cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(k->d_lsrow, lsrow.data(), sizeof(int) * lsrow.size(), cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(k->d_lorder, lorder.data(), sizeof(int) * lorder.size(), cudaMemcpyHostToDevice) != cudaSuccess)
         return kx_set_error(ctx, KX_ECUDA, "batched build: table upload failed");
     return KX_OK;
 }

@@ -270,9 +270,10 @@ __device__ int kx_prep_block(int n, int path, double x, double Ei, double hi, do
     if (path == KX_SPLIT_TF32) {
         if (in) dl[i] = l2;
         __syncthreads();
-        if (in)
-            v.td[(long long)b * n + i] =
-                make_float2((float)l2, i + 1 < n ? (float)(dl[i + 1] - l2) : 0.f);
+        if (in) {
+            const double D = i + 1 < n ? dl[i + 1] - l2 : 0.0;
+            v.td[(long long)i * v.B + b] = make_float2((float)l2, (float)D);   // (l2_j, D_j), instance-minor
+        }
         const float fp = (in && fm > 0.0) ? (float)(x * rfm) : 0.f;
         if (in) v.fT[(size_t)i * v.Bpad + b] = fp;
         uint32_t hb;

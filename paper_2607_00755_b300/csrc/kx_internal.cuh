@@ -62,9 +62,11 @@ struct kx_kernel {
     int Mpad;            // n^2 rows (i, n) padded to a multiple of 128
     int Kpad;            // n columns (m) padded to a multiple of 32
     float *d_Atile;      // [Mpad/128][Kpad/32][hi, lo][4096]: W_full as TF32 hi/lo in MMA operand tiles
-    uint2 *d_lel;        // per row i: nonzero (S_inm as float bits, j_L << 23 | omega) sorted by j_L
-    int *d_lrow;         // [n + 1] row offsets into d_lel
-    int *d_lgrp;         // [n][n + 1] first element of each bracket group j_L in row i
+    float2 *d_lel;       // per row i: nonzero (S_inm, omega) sorted by j_L
+    int2 *d_lseg;        // segments of <= 32 elements of one j_L: (first element, j_L << 8 | count)
+    int *d_lsrow;        // [n + 1] row offsets into d_lseg
+    int *d_lorder;       // [n] rows by element count, longest first
+    long long nseg;      // segments, all rows
     long long nnz;
     long long bytes;
     long long stream_bytes;   // table bytes one contraction launch reads
@@ -121,8 +123,8 @@ struct kx_batch_views {
     double *fmax;          // [B]
     double *lf64;          // [B][n]       FP64 path: ln max(f, floor)
     float2 *tl;            // [B][n + 4]   FP32 path: (l2_j, delta_j), l2 = log2(max(f, floor)/f_max)
-    float2 *td;            // [B][n]       FP32 path: (delta_j - D_j, D_j), D_j = delta_{j+1} - delta_j;
-                           //              split path: (l2_j, l2_{j+1} - l2_j)
+    float2 *td;            // FP32 path: [B][n] (delta_j - D_j, D_j), D_j = delta_{j+1} - delta_j;
+                           // split path: [n][B] (l2_j, D_j), D_j = l2_{j+1} - l2_j (instance-minor)
     double2 *partial;      // [B][n][chunks]  (FP32 path: float2 (hi, lo) task partials, [B][chunks])
     const int2 *rtask;     // FP32 path: [n] (first partial slot, tasks) per row
     double *rfmax;         // [B]          1 / f_max
@@ -135,6 +137,7 @@ struct kx_batch_views {
     float *fT;             // [Kpad][Bpad]: f/f_max, instance-minor
     float *T;              // [Mpad][Bpad]: T = W_full F (tensor-core product)
     int *err;              // tensor-core stage timeout flag (bounded waits)
+    int B;                 // instances the views were carved for (td's stride on the split path)
     int Bpad;
 };
 

@@ -118,7 +118,9 @@ static size_t kx_group_estimate(const kx_server_config &cfg, int n) {
         tables = (size_t)n * upr * unit * (16 + 16 + 4) + (size_t)(n + 1) * 4 + (size_t)n * 8 +
                  (size_t)n * upr * 16;
     else if (cfg.precision == KX_FP64) tables = (size_t)n * d.P * 18 + 4 * d.P;
-    else tables = (size_t)d.Mpad * d.Kpad * 8 + (size_t)n * d.P * 8 + (size_t)n * (n + 1) * 4;
+    else   // split: A tiles, loss elements, segments (at most P/32 + n per row), row tables
+        tables = (size_t)d.Mpad * d.Kpad * 8 + (size_t)n * d.P * 8 +
+                 (size_t)n * (d.P / 32 + n + 1) * 8 + (size_t)(2 * n + 1) * 4;
     const int cap = cfg.slots_per_group;
     size_t mem = kx_al(kx_views_bytes(&d, cap)) + 3 * kx_al(sizeof(double) * cap * n) +
                  kx_al(sizeof(kx_inst_state) * cap) + kx_al(sizeof(kx_src_dev) * cap) +
