@@ -216,7 +216,7 @@ static void kx_free_kernel(kx_kernel *k) {
     cudaSetDevice(k->device);
     void *ptrs[] = {k->d_p, k->d_E, k->d_dp, k->d_dE, k->d_h, k->d_pair, k->d_W64,
                     k->d_om64, k->d_jl, k->d_vt, k->d_W32, k->d_pk, k->d_roff, k->d_rtask,
-                    k->d_task, k->d_bins, k->d_Atile, k->d_lel, k->d_lseg, k->d_lsrow,
+                    k->d_task, k->d_bins, k->d_Atile, k->d_lel, k->d_lseg, k->d_lsw,
                     k->d_lorder};
     for (void *p : ptrs)
         if (p) cudaFree(p);
@@ -456,7 +456,7 @@ extern "C" int kx_build_kernel(kx_ctx *ctx, const kx_grid_desc *d, kx_kernel **o
     else if (k->precision == KX_FP64)
         k->stream_bytes = (long long)n * k->P * 18 + k->P * 4;
     else
-        k->stream_bytes = (long long)k->Mpad * k->Kpad * 8 + k->nnz * 8 + k->nseg * 8;
+        k->stream_bytes = (long long)k->Mpad * k->Kpad * 8 + k->nlel * 8 + k->nseg * 8;
     if (k->precision != KX_FP64) {
         // the FP32 and batched paths read only their own tables
         cudaFree(k->d_W64); k->d_W64 = nullptr;

@@ -21,6 +21,7 @@
 #define KX_ATILE 4096              // floats per A tile: 128 rows x 32 k
 #define KX_BTILE 2048              // floats per B tile: 64 rows x 32 k
 #define KX_GEMM_SMEM (65536 + 32768 + 64)
+#define KX_SEG 64                  // elements per loss segment at most (one j_L)
 
 #include "kx_ptx.cuh"
 
@@ -189,11 +190,12 @@ __global__ void __launch_bounds__(128)
 
 // ------------------------------------------------------------- exact loss
 // A row's nonzero elements are sorted by bracket j_L and cut into segments of at
-// most 32 elements with one j_L each (host build); an element is (S_inm, omega)
-// as two floats.  One block per (group of 32 IPL instances, row); lane l holds
+// most 64 elements with one j_L each, zero-padded to a multiple of 4 (host
+// build); an element is (S_inm, omega) as two floats.  One block per (group of 32 IPL instances, row); lane l holds
 // instances l, l + 32, ... of the group.  The block loads its instances'
 // (l2_j, D_j) tables once (IPL float2 per lane and j, read coalesced from the
-// instance-minor td); the row's segments go round-robin to the warps.  A warp
+// instance-minor td); the row's segments are dealt to the warps by the host,
+// balanced by element count.  A warp
 // loads a segment's elements with one coalesced load (the next segment's are in
 // flight meanwhile) into its shared-memory slot, reads its (l2_j, D_j) once,
 // and then per element and instance spends one FMA (interpolated exponent), one
@@ -209,9 +211,9 @@ __device__ __forceinline__ void kx_two_sum_f(float a, float b, float &s, float &
 }
 
 template <int IPL, int WARPS>
-__global__ void __launch_bounds__(WARPS * 32, WARPS <= 16 ? 2 : 1)
+__global__ void __launch_bounds__(WARPS * 32, (WARPS <= 16 && IPL <= 2) ? 2 : 1)
     k_batch_loss(int n, int B, int tds, int Bpad, const float2 *__restrict__ lel,
-                 const int2 *__restrict__ lseg, const int *__restrict__ lsrow,
+                 const int2 *__restrict__ lseg, const int *__restrict__ lsw,
                  const int *__restrict__ lorder, const float2 *__restrict__ td,
                  const float *__restrict__ fT, const float *__restrict__ T,
                  const double *__restrict__ fmax, double2 *__restrict__ partial,
@@ -219,7 +221,7 @@ __global__ void __launch_bounds__(WARPS * 32, WARPS <= 16 ? 2 : 1)
     // [n][32][IPL] (l2_j, D_j) table; after the loss loop the same space holds
     // the cross-warp reduction [2][WARPS][32 IPL] doubles
     extern __shared__ __align__(16) float2 kx_ltab[];
-    __shared__ __align__(16) float2 s_el[WARPS][32];
+    __shared__ __align__(16) float2 s_el[WARPS][KX_SEG];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     int b[IPL];
     bool act[IPL];
@@ -231,46 +233,79 @@ __global__ void __launch_bounds__(WARPS * 32, WARPS <= 16 ? 2 : 1)
         any |= act[s];
     }
     if (!__syncthreads_or(any)) return;
-    for (int j = warp; j < n; j += WARPS)
+    const int i = lorder[blockIdx.y];
+    // layout: IPL = 1: float2 at [j][lane]; else float4 (two instances) at
+    // [j][IPL / 2][lane], so that each table read is one conflict-free LDS.128
+    for (int j = warp; j < n; j += WARPS) {
+        float2 v[IPL];
+#pragma unroll
+        for (int s = 0; s < IPL; ++s) v[s] = act[s] ? td[(size_t)j * tds + b[s]] : make_float2(-2000.f, 0.f);
+        if constexpr (IPL == 1) {
+            kx_ltab[j * 32 + lane] = v[0];
+        } else {
+#pragma unroll
+            for (int h = 0; h < IPL / 2; ++h)
+                reinterpret_cast<float4 *>(kx_ltab)[(j * (IPL / 2) + h) * 32 + lane] =
+                    make_float4(v[2 * h].x, v[2 * h].y, v[2 * h + 1].x, v[2 * h + 1].y);
+        }
+    }
+    // the gain's loads go out together with the table's, before the barrier
+    float gs[IPL];
+#pragma unroll
+    for (int s = 0; s < IPL; ++s) gs[s] = 0.f;
+    for (int nn = warp; nn < n; nn += WARPS) {
+        const float *fr = fT + (size_t)nn * Bpad;
+        const float *tr = T + ((size_t)i * n + nn) * Bpad;
 #pragma unroll
         for (int s = 0; s < IPL; ++s)
-            kx_ltab[(j * 32 + lane) * IPL + s] =
-                act[s] ? td[(size_t)j * tds + b[s]] : make_float2(-2000.f, 0.f);
+            if (b[s] < B) gs[s] = fmaf(fr[b[s]], tr[b[s]], gs[s]);   // (Bpad rounds B to 64 only)
+    }
     __syncthreads();
-    const int i = lorder[blockIdx.y];
-    const int g0 = lsrow[i], g1 = lsrow[i + 1];
+    // this warp's segments of row i (balanced across the warps by the host)
+    const int gend = lsw[i * WARPS + warp + 1];
+    int g = lsw[i * WARPS + warp];
     float hi[IPL], lo[IPL];
 #pragma unroll
     for (int s = 0; s < IPL; ++s) hi[s] = lo[s] = 0.f;
-    int g = g0 + warp;
-    int2 dsc = make_int2(0, 0);
-    float2 el = make_float2(0.f, 0.f);
-    if (g < g1) {
+    // descriptors run two segments ahead of the compute, elements one
+    int2 dsc = make_int2(0, 0), dn = dsc;
+    float2 el0 = make_float2(0.f, 0.f), el1 = el0;
+    if (g < gend) {
         dsc = __ldg(lseg + g);
-        if (lane < (dsc.y & 63)) el = __ldg(lel + dsc.x + lane);
+        const int c = dsc.y & 255;
+        if (lane < c) el0 = __ldg(lel + dsc.x + lane);
+        if (lane + 32 < c) el1 = __ldg(lel + dsc.x + 32 + lane);
     }
-    for (; g < g1; g += WARPS) {
-        int2 dn = dsc;
-        float2 en = make_float2(0.f, 0.f);
-        if (g + WARPS < g1) {
-            dn = __ldg(lseg + g + WARPS);
-            if (lane < (dn.y & 63)) en = __ldg(lel + dn.x + lane);
+    if (g + 1 < gend) dn = __ldg(lseg + g + 1);
+    for (; g < gend; ++g) {
+        int2 dnn = dn;
+        if (g + 2 < gend) dnn = __ldg(lseg + g + 2);
+        float2 en0 = make_float2(0.f, 0.f), en1 = en0;
+        if (g + 1 < gend) {
+            const int c = dn.y & 255;
+            if (lane < c) en0 = __ldg(lel + dn.x + lane);
+            if (lane + 32 < c) en1 = __ldg(lel + dn.x + 32 + lane);
         }
-        s_el[warp][lane] = el;   // lanes past the count hold (0, 0): weight 0
+        s_el[warp][lane] = el0;
+        s_el[warp][32 + lane] = el1;
         __syncwarp();
-        const int j = dsc.y >> 8, c4 = ((dsc.y & 63) + 3) & ~3;
+        const int j = dsc.y >> 8, c4 = dsc.y & 255;   // count, a multiple of 4
         float2 t[IPL];
-        if constexpr (IPL == 2) {
-            const float4 q = reinterpret_cast<const float4 *>(kx_ltab)[j * 32 + lane];
-            t[0] = make_float2(q.x, q.y);
-            t[1] = make_float2(q.z, q.w);
-        } else {
+        if constexpr (IPL == 1) {
             t[0] = kx_ltab[j * 32 + lane];
+        } else {
+#pragma unroll
+            for (int h = 0; h < IPL / 2; ++h) {
+                const float4 q = reinterpret_cast<const float4 *>(kx_ltab)[(j * (IPL / 2) + h) * 32 + lane];
+                t[2 * h] = make_float2(q.x, q.y);
+                t[2 * h + 1] = make_float2(q.z, q.w);
+            }
         }
         float a[IPL][4];
 #pragma unroll
         for (int s = 0; s < IPL; ++s) a[s][0] = a[s][1] = a[s][2] = a[s][3] = 0.f;
         const float4 *e4 = reinterpret_cast<const float4 *>(s_el[warp]);
+#pragma unroll 2
         for (int q = 0; q < c4; q += 4) {
             const float4 x01 = e4[q >> 1], x23 = e4[(q >> 1) + 1];
 #pragma unroll
@@ -290,16 +325,9 @@ __global__ void __launch_bounds__(WARPS * 32, WARPS <= 16 ? 2 : 1)
         }
         __syncwarp();   // the slot is refilled next segment
         dsc = dn;
-        el = en;
-    }
-    float gs[IPL];
-#pragma unroll
-    for (int s = 0; s < IPL; ++s) gs[s] = 0.f;
-    for (int nn = warp; nn < n; nn += WARPS) {
-        const float *fr = fT + (size_t)nn * Bpad;
-        const float *tr = T + ((size_t)i * n + nn) * Bpad;
-#pragma unroll
-        for (int s = 0; s < IPL; ++s) gs[s] = fmaf(fr[b[s]], tr[b[s]], gs[s]);
+        dn = dnn;
+        el0 = en0;
+        el1 = en1;
     }
     __syncthreads();   // every warp is done with the table
     double *red = reinterpret_cast<double *>(kx_ltab);   // [2][WARPS][32 IPL]
@@ -328,11 +356,13 @@ __global__ void __launch_bounds__(WARPS * 32, WARPS <= 16 ? 2 : 1)
 // Loss-kernel shape for an n-point grid: two instances per lane while the
 // table (n x 32 x 2 float2) leaves room for two 16-warp blocks per SM or, up to
 // n = 400, for one 32-warp block; one instance per lane (32 warps) above that.
+// (Four instances per lane, one 16-warp block per SM, measured slower at
+// n = 192: the occupancy is worth more than the shared element reads.)
 struct kx_loss_shape {
     int ipl, warps;
 };
 static kx_loss_shape kx_loss_shape_for(int n) {
-    if (n <= 212) return {2, 16};
+    if (n <= 200) return {2, 16};
     if (n <= 400) return {2, 32};
     return {1, 32};
 }
@@ -344,7 +374,7 @@ static size_t kx_loss_smem(int n, kx_loss_shape sh) {
 void kx_batch_prepare() {
     cudaFuncSetAttribute(k_gain_mma, cudaFuncAttributeMaxDynamicSharedMemorySize, KX_GEMM_SMEM);
     cudaFuncSetAttribute(k_batch_loss<2, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)kx_loss_smem(212, {2, 16}));
+                         (int)kx_loss_smem(200, {2, 16}));
     cudaFuncSetAttribute(k_batch_loss<2, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)kx_loss_smem(400, {2, 32}));
     cudaFuncSetAttribute(k_batch_loss<1, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -365,13 +395,13 @@ cudaError_t kx_launch_batch_contract(const kx_kernel *k, int B, const kx_batch_v
     dim3 g2((B + per - 1) / per, k->n);
     const size_t smem = kx_loss_smem(k->n, sh);
     if (sh.ipl == 2 && sh.warps == 16)
-        k_batch_loss<2, 16><<<g2, 512, smem, s>>>(k->n, B, v.B, v.Bpad, k->d_lel, k->d_lseg, k->d_lsrow,
+        k_batch_loss<2, 16><<<g2, 512, smem, s>>>(k->n, B, v.B, v.Bpad, k->d_lel, k->d_lseg, k->d_lsw,
                                                   k->d_lorder, v.td, v.fT, v.T, v.fmax, v.partial, st, stage);
     else if (sh.ipl == 2)
-        k_batch_loss<2, 32><<<g2, 1024, smem, s>>>(k->n, B, v.B, v.Bpad, k->d_lel, k->d_lseg, k->d_lsrow,
+        k_batch_loss<2, 32><<<g2, 1024, smem, s>>>(k->n, B, v.B, v.Bpad, k->d_lel, k->d_lseg, k->d_lsw,
                                                    k->d_lorder, v.td, v.fT, v.T, v.fmax, v.partial, st, stage);
     else
-        k_batch_loss<1, 32><<<g2, 1024, smem, s>>>(k->n, B, v.B, v.Bpad, k->d_lel, k->d_lseg, k->d_lsrow,
+        k_batch_loss<1, 32><<<g2, 1024, smem, s>>>(k->n, B, v.B, v.Bpad, k->d_lel, k->d_lseg, k->d_lsw,
                                                    k->d_lorder, v.td, v.fT, v.T, v.fmax, v.partial, st, stage);
     return cudaGetLastError();
 }
@@ -381,9 +411,12 @@ cudaError_t kx_launch_batch_contract(const kx_kernel *k, int B, const kx_batch_v
 //  A tiles: W_full[(i n)][m] = S_inm / 2 (n != m), S_inn (n = m), TF32 hi/lo
 //           (hi rounded to nearest TF32, lo = W - hi), in MMA operand tiles;
 //  loss list: per row, the nonzero (S, omega) as floats sorted by j_L, cut into
-//           segments of at most 32 elements of one j_L: (first element,
-//           j_L << 8 | count) per segment, rows' segment offsets, and the rows
-//           ordered by element count, longest first.
+//           segments of at most KX_SEG elements of one j_L, each zero-padded to
+//           a multiple of 4: (first element, j_L << 8 | padded count) per
+//           segment; each row's segments are dealt to the loss kernel's warps
+//           (longest first, to the least loaded), stored warp by warp with the
+//           first segment of every (row, warp); the rows ordered by element
+//           count, longest first.
 static float kx_tf32_round(float x) {
     uint32_t u;
     memcpy(&u, &x, 4);
@@ -410,7 +443,8 @@ int kx_batch_build_tables(kx_ctx *ctx, kx_kernel *k) {
     std::vector<float> At((size_t)MT * KB * 2 * KX_ATILE, 0.f);
     std::vector<float2> lel;
     std::vector<int2> lseg;
-    std::vector<int> lsrow(n + 1, 0), rlen(n, 0);
+    const int WARPS = kx_loss_shape_for(n).warps;
+    std::vector<int> lsw((size_t)n * WARPS + 1, 0), rlen(n, 0);
     std::vector<long long> base(n);
     for (int a = 0; a < n; ++a) base[a] = (long long)a * n - (long long)a * (a - 1) / 2;
     struct El {
@@ -418,6 +452,10 @@ int kx_batch_build_tables(kx_ctx *ctx, kx_kernel *k) {
         float w, om;
     };
     std::vector<El> row;
+    std::vector<std::pair<size_t, size_t>> seg;
+    std::vector<size_t> ord;
+    std::vector<int> owner;
+    std::vector<long long> load;
     for (int i = 0; i < n; ++i) {
         row.clear();
         for (int a = 0; a < n; ++a) {
@@ -437,17 +475,40 @@ int kx_batch_build_tables(kx_ctx *ctx, kx_kernel *k) {
             }
         }
         std::stable_sort(row.begin(), row.end(), [](const El &x, const El &y) { return x.j < y.j; });
-        size_t p0 = 0;
-        while (p0 < row.size()) {
+        // segments (first element in row, end), then longest-first assignment to
+        // the least loaded warp (cost: padded count + a fixed per-segment share)
+        seg.clear();
+        for (size_t p0 = 0; p0 < row.size();) {
             size_t p1 = p0;
-            while (p1 < row.size() && row[p1].j == row[p0].j && p1 - p0 < 32) ++p1;
-            lseg.push_back(make_int2((int)lel.size(), (row[p0].j << 8) | (int)(p1 - p0)));
-            for (size_t q = p0; q < p1; ++q) lel.push_back(make_float2(row[q].w, row[q].om));
+            while (p1 < row.size() && row[p1].j == row[p0].j && p1 - p0 < KX_SEG) ++p1;
+            seg.push_back({p0, p1});
             p0 = p1;
         }
+        const auto cost = [&](size_t q) { return (long long)((seg[q].second - seg[q].first + 3) & ~(size_t)3) + 16; };
+        ord.resize(seg.size());
+        std::iota(ord.begin(), ord.end(), (size_t)0);
+        std::stable_sort(ord.begin(), ord.end(), [&](size_t x, size_t y) { return cost(x) > cost(y); });
+        owner.assign(seg.size(), 0);
+        load.assign(WARPS, 0);
+        for (size_t q : ord) {
+            const int w = (int)(std::min_element(load.begin(), load.end()) - load.begin());
+            owner[q] = w;
+            load[w] += cost(q);
+        }
+        for (int w = 0; w < WARPS; ++w) {
+            lsw[(size_t)i * WARPS + w] = (int)lseg.size();
+            for (size_t q = 0; q < seg.size(); ++q) {
+                if (owner[q] != w) continue;
+                const size_t p0 = seg[q].first, p1 = seg[q].second;
+                const int c4 = (int)((p1 - p0 + 3) & ~(size_t)3);
+                lseg.push_back(make_int2((int)lel.size(), (row[p0].j << 8) | c4));
+                for (size_t e = p0; e < p1; ++e) lel.push_back(make_float2(row[e].w, row[e].om));
+                for (size_t e = p1 - p0; e < (size_t)c4; ++e) lel.push_back(make_float2(0.f, 0.f));
+            }
+        }
         rlen[i] = (int)row.size();
-        lsrow[i + 1] = (int)lseg.size();
     }
+    lsw[(size_t)n * WARPS] = (int)lseg.size();
     std::vector<int> lorder(n);
     std::iota(lorder.begin(), lorder.end(), 0);
     std::stable_sort(lorder.begin(), lorder.end(), [&](int x, int y) { return rlen[x] > rlen[y]; });
@@ -456,18 +517,19 @@ int kx_batch_build_tables(kx_ctx *ctx, kx_kernel *k) {
     if (cudaMalloc(&k->d_Atile, sizeof(float) * At.size()) != cudaSuccess ||
         cudaMalloc(&k->d_lel, sizeof(float2) * lel.size()) != cudaSuccess ||
         cudaMalloc(&k->d_lseg, sizeof(int2) * lseg.size()) != cudaSuccess ||
-        cudaMalloc(&k->d_lsrow, sizeof(int) * lsrow.size()) != cudaSuccess ||
+        cudaMalloc(&k->d_lsw, sizeof(int) * lsw.size()) != cudaSuccess ||
         cudaMalloc(&k->d_lorder, sizeof(int) * lorder.size()) != cudaSuccess) {
         cudaGetLastError();
         return kx_set_error(ctx, KX_ENOMEM, "batched build: allocation failed");
     }
-    k->nseg = (long long)lsrow[n];
+    k->nseg = (long long)lsw[(size_t)n * WARPS];
+    k->nlel = (long long)lel.size();
     k->bytes += (long long)(sizeof(float) * At.size() + sizeof(float2) * lel.size() +
-                            sizeof(int2) * lseg.size() + sizeof(int) * (lsrow.size() + lorder.size()));
+                            sizeof(int2) * lseg.size() + sizeof(int) * (lsw.size() + lorder.size()));
     if (cudaMemcpy(k->d_Atile, At.data(), sizeof(float) * At.size(), cudaMemcpyHostToDevice) != cudaSuccess ||
         cudaMemcpy(k->d_lel, lel.data(), sizeof(float2) * lel.size(), cudaMemcpyHostToDevice) != cudaSuccess ||
         cudaMemcpy(k->d_lseg, lseg.data(), sizeof(int2) * lseg.size(), cudaMemcpyHostToDevice) != cudaSuccess ||
-        cudaMemcpy(k->d_lsrow, lsrow.data(), sizeof(int) * lsrow.size(), cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(k->d_lsw, lsw.data(), sizeof(int) * lsw.size(), cudaMemcpyHostToDevice) != cudaSuccess ||
         cudaMemcpy(k->d_lorder, lorder.data(), sizeof(int) * lorder.size(), cudaMemcpyHostToDevice) != cudaSuccess)
         return kx_set_error(ctx, KX_ECUDA, "batched build: table upload failed");
     return KX_OK;

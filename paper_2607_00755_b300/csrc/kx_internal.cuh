@@ -64,9 +64,10 @@ struct kx_kernel {
     float *d_Atile;      // [Mpad/128][Kpad/32][hi, lo][4096]: W_full as TF32 hi/lo in MMA operand tiles
     float2 *d_lel;       // per row i: nonzero (S_inm, omega) sorted by j_L
     int2 *d_lseg;        // segments of <= 32 elements of one j_L: (first element, j_L << 8 | count)
-    int *d_lsrow;        // [n + 1] row offsets into d_lseg
+    int *d_lsw;          // [n * warps + 1] first segment of each (row, loss-kernel warp)
     int *d_lorder;       // [n] rows by element count, longest first
     long long nseg;      // segments, all rows
+    long long nlel;      // loss elements with the segments' zero padding
     long long nnz;
     long long bytes;
     long long stream_bytes;   // table bytes one contraction launch reads

@@ -118,9 +118,11 @@ static size_t kx_group_estimate(const kx_server_config &cfg, int n) {
         tables = (size_t)n * upr * unit * (16 + 16 + 4) + (size_t)(n + 1) * 4 + (size_t)n * 8 +
                  (size_t)n * upr * 16;
     else if (cfg.precision == KX_FP64) tables = (size_t)n * d.P * 18 + 4 * d.P;
-    else   // split: A tiles, loss elements, segments (at most P/32 + n per row), row tables
-        tables = (size_t)d.Mpad * d.Kpad * 8 + (size_t)n * d.P * 8 +
-                 (size_t)n * (d.P / 32 + n + 1) * 8 + (size_t)(2 * n + 1) * 4;
+    else {   // split: A tiles, loss elements (with padding), segments, row tables
+        const size_t segs = (size_t)n * (d.P / 64 + n + 1);   // at most P/64 + n per row
+        tables = (size_t)d.Mpad * d.Kpad * 8 + ((size_t)n * d.P + 3 * segs) * 8 + segs * 8 +
+                 (size_t)(34 * n + 1) * 4;
+    }
     const int cap = cfg.slots_per_group;
     size_t mem = kx_al(kx_views_bytes(&d, cap)) + 3 * kx_al(sizeof(double) * cap * n) +
                  kx_al(sizeof(kx_inst_state) * cap) + kx_al(sizeof(kx_src_dev) * cap) +
