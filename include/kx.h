@@ -311,7 +311,8 @@ int kx_math_check(kx_ctx *ctx, int which, int n, const double *x_dev, double *ou
  * `batch` instances on the context's device, in place of the autotuner's
  * choice (which is otherwise timed once per (device, n, batch) before the
  * first launch): 0 = one instance per pass, 1 = two per pass (batch >= 2),
- * 2 = four per pass, bulk-copy staged (n > 160, batch >= 4); -1 forgets the
+ * 2 = four per pass, bulk-copy staged (n > 160, batch >= 4), 3 = four per
+ * pass, register pipeline (batch >= 4); -1 forgets the
  * pinned or tuned choice.  All variants give bit-identical results; this is
  * for reproducible timing and for tests.  KX_EINVAL for a variant that does
  * not apply. */

@@ -389,15 +389,15 @@ extern "C" int kx_build_kernel(kx_ctx *ctx, const kx_grid_desc *d, kx_kernel **o
             }
         }
         bins[KX_BINS] = (int)task.size();
+        // partial slots: MT per row (the largest task count, rounded up to even
+        // for paired 16-byte reads), so that a row's slots sit at a fixed stride
+        int MT = 2;
+        for (int i = 0; i < n; ++i) MT = std::max(MT, (row_tasks[i] + 1) & ~1);
         std::vector<int2> rtask(n);
-        int slots = 0;
-        for (int i = 0; i < n; ++i) {
-            rtask[i] = make_int2(slots, row_tasks[i]);
-            slots += (row_tasks[i] + 1) & ~1;   // even, for paired 16-byte reads of the partials
-        }
+        for (int i = 0; i < n; ++i) rtask[i] = make_int2(i * MT, row_tasks[i]);
         for (auto &t : task) t.w += rtask[t.x].x;   // slot = row's first slot + index in the row
         k->ntask = (int)task.size();
-        k->tslots = slots > 0 ? slots : 2;
+        k->tslots = n * MT;
         long long *by2 = &k->bytes;
         if ((rc = kx_dev_alloc(ctx, &k->d_vt, k->Vt, by2)) != KX_OK ||
             (rc = kx_dev_alloc(ctx, &k->d_W32, (size_t)k->Vt * 4, by2)) != KX_OK ||

@@ -116,12 +116,24 @@ __device__ __forceinline__ void kx_block_cols(const double (&v)[K], double *sm) 
 #pragma unroll
     for (int k = 0; k < K; ++k) sm[k * T + tid] = v[k];
     __syncthreads();
-    for (int k = warp; k < K; k += nw) {
-        double x = sm[k * T + lane];
-        for (int j = lane + 32; j < T; j += 32) x += sm[k * T + j];
+    // a warp's columns k and k + nw are summed together (two independent chains)
+    for (int k = warp; k < K; k += 2 * nw) {
+        const int k2 = k + nw;
+        const bool two = k2 < K;
+        double x = sm[k * T + lane], y = two ? sm[k2 * T + lane] : 0.0;
+        for (int j = lane + 32; j < T; j += 32) {
+            x += sm[k * T + j];
+            if (two) y += sm[k2 * T + j];
+        }
 #pragma unroll
-        for (int off = 16; off; off >>= 1) x += __shfl_xor_sync(0xffffffffu, x, off);
-        if (lane == 0) sm[K * T + k] = x;
+        for (int off = 16; off; off >>= 1) {
+            x += __shfl_xor_sync(0xffffffffu, x, off);
+            if (two) y += __shfl_xor_sync(0xffffffffu, y, off);
+        }
+        if (lane == 0) {
+            sm[K * T + k] = x;
+            if (two) sm[K * T + k2] = y;
+        }
     }
     __syncthreads();
 }
@@ -229,7 +241,7 @@ __device__ __forceinline__ unsigned long long kx_block_max_key(unsigned long lon
 // x: this thread's f value (0 for threads past n).  Called at most once per
 // kernel launch (it uses block-scope shared arrays without a trailing barrier).
 // Ei, hi: this thread's grid energy and moment weight; E0 = E_0.
-__device__ int kx_prep_block(int n, int path, double x, double Ei, double hi, double E0,
+__device__ __forceinline__ int kx_prep_block(int n, int path, double x, double Ei, double hi, double E0,
                              const kx_batch_views &v, int b, double *smem) {
     __shared__ unsigned long long s_key[32];
     __shared__ float s_fit[5 * 32];
@@ -246,16 +258,21 @@ __device__ int kx_prep_block(int n, int path, double x, double Ei, double hi, do
         kx_block_max_key(nf ? KX_KEY_NONFINITE : (unsigned long long)__double_as_longlong(fabs(x)), s_key);
     const int bad = key == KX_KEY_NONFINITE;
     const double fm = bad ? INFINITY : __longlong_as_double((long long)key);
+    // 1 / f_max on thread 0 and log2 f_max on the first thread of the second
+    // warp (another sub-partition's FP64 unit), so the two chains overlap
+    const int tlog = blockDim.x > 32 ? 32 : 0;
     if (threadIdx.x == 0) {
         const double rfm = (fm > 0.0 && !bad) ? 1.0 / fm : 0.0;
         v.fmax[b] = fm;
         v.rfmax[b] = rfm;
+        s_scale[2] = rfm;
+    }
+    if (threadIdx.x == tlog) {
         int e = 0;
         double fr = 0.0;
         if (path != KX_FP64 && fm > 0.0 && !bad) kx_log2_parts(fm > KX_LOG_FLOOR ? fm : KX_LOG_FLOOR, e, fr);
         s_scale[0] = (double)e;
         s_scale[1] = fr;
-        s_scale[2] = rfm;
     }
     if (path == KX_FP64) {
         if (in) v.lf64[(long long)b * n + i] = log(x > KX_LOG_FLOOR ? x : KX_LOG_FLOOR);
@@ -894,7 +911,7 @@ static cudaError_t kx_launch_stream_r(const kx_kernel *k, int B, const kx_batch_
 // ------------------------------------------------------------ autotuner
 // Streaming variants of the FP32 path: 0 = register pipeline, one instance per
 // pass; 1 = register pipeline, two per pass; 2 = bulk-copy staged, four per pass
-// (units of 128 vectors only).  All give bit-identical results (shared
+// (units of 128 vectors only); 3 = register pipeline, four per pass.  All give bit-identical results (shared
 // arithmetic, the kernel's fixed bins), so the choice is purely a matter of
 // speed: it is timed once per (device, grid size, batch) on the caller's own
 // prepared inputs and kept for the process.
@@ -906,6 +923,7 @@ static void kx_stream_candidates(const kx_kernel *k, int B, int *cand, int *nc) 
     cand[(*nc)++] = 0;
     if (B >= 2) cand[(*nc)++] = 1;
     if (k->vpl == 4 && B >= 4) cand[(*nc)++] = 2;
+    if (B >= 4) cand[(*nc)++] = 3;
 }
 
 // The rule used before a size is tuned (measured on this part): two per pass on
@@ -925,8 +943,12 @@ static int kx_stream_variant(const kx_kernel *k, int B) {
 
 static cudaError_t kx_stream_launch(int variant, const kx_kernel *k, int B, const kx_batch_views &v,
                                     const kx_inst_state *st, int stage, cudaStream_t s) {
-    if (k->vpl == 2) return variant == 1 ? kx_launch_stream_r<2, 2>(k, B, v, st, stage, s)
-                                         : kx_launch_stream_r<1, 2>(k, B, v, st, stage, s);
+    if (k->vpl == 2) {
+        if (variant == 3) return kx_launch_stream_r<4, 2>(k, B, v, st, stage, s);
+        return variant == 1 ? kx_launch_stream_r<2, 2>(k, B, v, st, stage, s)
+                            : kx_launch_stream_r<1, 2>(k, B, v, st, stage, s);
+    }
+    if (variant == 3) return kx_launch_stream_r<4, 4>(k, B, v, st, stage, s);
     if (variant == 2) return kx_launch_stream<4, 4>(k, B, v, st, stage, s);
     if (variant == 1) return kx_launch_stream_r<2, 4>(k, B, v, st, stage, s);
     return kx_launch_stream_r<1, 4>(k, B, v, st, stage, s);
@@ -974,10 +996,11 @@ int kx_tune_contraction(const kx_kernel *k, int B, const kx_batch_views &v, cons
 }
 
 extern "C" int kx_set_stream_variant(kx_ctx *ctx, int n, int batch, int variant) {
-    if (!ctx || n < 4 || n > KX_MAX_N || batch < 1 || variant < -1 || variant > 2) return KX_EINVAL;
+    if (!ctx || n < 4 || n > KX_MAX_N || batch < 1 || variant < -1 || variant > 3) return KX_EINVAL;
     const int vpl = n <= 160 ? 2 : 4;
     if (variant == 1 && batch < 2) return KX_EINVAL;
     if (variant == 2 && (vpl != 4 || batch < 4)) return KX_EINVAL;
+    if (variant == 3 && batch < 4) return KX_EINVAL;
     const auto key = std::make_tuple(ctx->device, n, batch);
     std::lock_guard<std::mutex> lock(g_tune_mu);
     if (variant < 0) g_tuned.erase(key);
@@ -1011,7 +1034,7 @@ struct kx_row_out {
 };
 
 // sm: at least 5 * blockDim.x + 8 doubles.
-__device__ kx_row_out kx_combine_project(int n, int chunks, int path, int b, double fi, double Ei,
+__device__ __forceinline__ kx_row_out kx_combine_project(int n, int chunks, int path, int b, double fi, double Ei,
                                          double hi, const kx_batch_views &v, int project,
                                          double *sm) {
     const int i = threadIdx.x, T = blockDim.x;
@@ -1019,29 +1042,31 @@ __device__ kx_row_out kx_combine_project(int n, int chunks, int path, int b, dou
     double G = 0.0, L = 0.0;
     if (i < n && path == KX_FP32) {
         // double-float task partials (hi, lo) in pairs per 16-byte load, four
-        // independent double-float sums combined in a fixed order
-        // row i's task partials: slots rt.x .. rt.x + rt.y - 1 of instance b
-        // (rt.x even, so pairs of slots are 16-byte aligned)
-        const int2 rt = v.rtask[i];
-        const float4 *pp = reinterpret_cast<const float4 *>(v.partial) + (((long long)b * chunks + rt.x) >> 1);
-        const int ntask = rt.y, npair = (ntask + 1) >> 1;
+        // independent double-float sums combined in a fixed order.  Row i's
+        // slots are i MT .. i MT + MT - 1 of instance b (MT = chunks / n, even),
+        // the first rt.y of them written by its tasks: the addresses do not
+        // wait for the task count, which only masks the sums.
+        const int MT = chunks / n;
+        const float4 *pp = reinterpret_cast<const float4 *>(v.partial) +
+                           (((long long)b * chunks + (long long)i * MT) >> 1);
+        const int ntask = v.rtask[i].y, npair = MT >> 1;
         float h0 = 0.f, l0 = 0.f, h1 = 0.f, l1 = 0.f, h2 = 0.f, l2 = 0.f, h3 = 0.f, l3 = 0.f;
-        // batches of 8 pairs: the 8 loads of a batch are in flight together
-        for (int c0 = 0; c0 < npair; c0 += 8) {
-            float4 x[8];
+        // batches of 12 pairs: the loads of a batch are in flight together
+        for (int c0 = 0; c0 < npair; c0 += 12) {
+            float4 x[12];
 #pragma unroll
-            for (int j = 0; j < 8; ++j)
+            for (int j = 0; j < 12; ++j)
                 x[j] = c0 + j < npair ? pp[c0 + j] : make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll
-            for (int j = 0; j < 8; j += 2) {
-                // slot 2 (c0 + j) + 1 is the padding slot when the task count is odd
-                const bool p1 = 2 * (c0 + j) + 1 >= ntask, p3 = 2 * (c0 + j) + 3 >= ntask;
-                kx_df_add(h0, l0, x[j].x);
-                l0 += x[j].y;
+            for (int j = 0; j < 12; j += 2) {
+                const int s0 = 2 * (c0 + j);   // slots s0 .. s0 + 3; those >= ntask hold no task
+                const bool p0 = s0 >= ntask, p1 = s0 + 1 >= ntask, p2 = s0 + 2 >= ntask, p3 = s0 + 3 >= ntask;
+                kx_df_add(h0, l0, p0 ? 0.f : x[j].x);
+                l0 += p0 ? 0.f : x[j].y;
                 kx_df_add(h1, l1, p1 ? 0.f : x[j].z);
                 l1 += p1 ? 0.f : x[j].w;
-                kx_df_add(h2, l2, x[j + 1].x);
-                l2 += x[j + 1].y;
+                kx_df_add(h2, l2, p2 ? 0.f : x[j + 1].x);
+                l2 += p2 ? 0.f : x[j + 1].y;
                 kx_df_add(h3, l3, p3 ? 0.f : x[j + 1].z);
                 l3 += p3 ? 0.f : x[j + 1].w;
             }
@@ -1164,7 +1189,7 @@ cudaError_t kx_launch_finalize(const kx_kernel *k, int B, const double *f, const
 // sm: at least 4 * blockDim.x + 8 doubles.  The Newton bookkeeping (u, its
 // bracket, the convergence test) runs on thread 0, which broadcasts 1/T and
 // the stop flag; every thread evaluates its point's weight.
-__device__ void kx_mb_fit_block(int n, double fi, double Ei, double hi, double E0, double T_guess,
+__device__ __forceinline__ void kx_mb_fit_block(int n, double fi, double Ei, double hi, double E0, double T_guess,
                                 double *out, double *sm) {
     const bool in = threadIdx.x < n;
     const int T = blockDim.x;
@@ -1262,14 +1287,15 @@ cudaError_t kx_launch_mbfit(const kx_kernel *k, int B, const double *f, double *
 // stage 2: k2 = C_proj[f_p] + S(t + h); f_c = f + h/2 (k1 + k2) (trapezoid
 //          corrector), err = max |f_c - f_p| / (atol + rtol |f_c|), accept or
 //          reject, next h, MB stopping test, prep(next f).
-__global__ void __launch_bounds__(KX_FIN_THREADS)
-    k_stage(int n, int chunks, int path, const double *__restrict__ E,
-            const double *__restrict__ h, kx_batch_views v, kx_step_views sv, int stage,
-            long long max_attempts) {
-    __shared__ double smem[5 * KX_FIN_THREADS + 8];
+// One instance's stage in one block (thread = grid point; smem: 5 blockDim.x +
+// 8 doubles).  Every exit is block-uniform.
+__device__ __forceinline__ void kx_stage_body(int b, int n, int chunks, int path, const double *__restrict__ E,
+                              const double *__restrict__ h, kx_batch_views v,
+                              kx_step_views sv, int stage, long long max_attempts,
+                              double *smem) {
     __shared__ unsigned long long s_key[32];
     __shared__ double s_env[KX_MAX_SRC];
-    const int b = blockIdx.x, i = threadIdx.x;
+    const int i = threadIdx.x;
     kx_inst_state *st = sv.st + b;
     if (st->done) return;
     if (stage == 2 && st->skip2) {
@@ -1470,6 +1496,14 @@ __global__ void __launch_bounds__(KX_FIN_THREADS)
     // prepare the next attempt's contraction input (f_new or the restored f)
     int bad2 = kx_prep_block(n, path, in ? fnew : 0.0, Ei, hi, E0, v, b, smem);
     if (threadIdx.x == 0) v.flags[b] = bad2;
+}
+
+__global__ void __launch_bounds__(KX_FIN_THREADS)
+    k_stage(int n, int chunks, int path, const double *__restrict__ E,
+            const double *__restrict__ h, kx_batch_views v, kx_step_views sv, int stage,
+            long long max_attempts) {
+    __shared__ double smem[5 * KX_FIN_THREADS + 8];
+    kx_stage_body(blockIdx.x, n, chunks, path, E, h, v, sv, stage, max_attempts, smem);
 }
 
 cudaError_t kx_launch_stage(const kx_kernel *k, int B, const kx_batch_views &v,

@@ -51,13 +51,13 @@ struct kx_kernel {
     float *d_W32;        // [Vt][4], slots rotated by (k >> 2) & 3, k = index in the row
     uint32_t *d_pk;      // [Vt][4]: j_L << 23 | round(omega 2^23), same slots
     int *d_roff;         // [n + 1] first kept vector of each row
-    int2 *d_rtask;       // [n]: (first partial slot, tasks) of each row
+    int2 *d_rtask;       // [n]: (first partial slot = i MT, tasks) of each row
     int4 *d_task;        // [ntask]: (row, first unit, end unit, partial slot)
     int *d_bins;         // [KX_BINS + 1]: first task of each equal-work bin
     long long Vt;        // kept vectors, all rows
     int vpl;             // vectors per lane of a unit
     int ntask;           // streaming tasks
-    int tslots;          // partial slots per instance (row task counts rounded up to even)
+    int tslots;          // partial slots per instance: n x MT, MT = largest row task count rounded up to even
     // batched (split TF32) tables
     int Mpad;            // n^2 rows (i, n) padded to a multiple of 128
     int Kpad;            // n columns (m) padded to a multiple of 32

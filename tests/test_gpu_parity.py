@@ -263,7 +263,7 @@ def test_streaming_variants_are_bitwise_identical(ctx, kx, N):
     f = ki.batch_bimodal(np.random.default_rng(19), q, 8)
     sig = np.linspace(0.5, 4.0, 8)
     k = ctx.build_kernel(q, precision=kx.FP32)
-    variants = [0, 1] + ([2] if N > 160 else [])
+    variants = [0, 1, 3] + ([2] if N > 160 else [])
     out = []
     for var in variants:
         ctx.set_stream_variant(N, 8, var)
@@ -274,6 +274,8 @@ def test_streaming_variants_are_bitwise_identical(ctx, kx, N):
         np.testing.assert_array_equal(o, out[0])
     with pytest.raises(kx.KxError):
         ctx.set_stream_variant(N, 1, 1)
+    with pytest.raises(kx.KxError):
+        ctx.set_stream_variant(N, 3, 3)
     k.release()
 
 
