@@ -544,7 +544,7 @@ static int kx_collision_impl(kx_ctx *ctx, const kx_kernel *k, int B, const doubl
     KX_CUDA_TRY(ctx, cudaMemcpyAsync(v.M2, M2.data(), sizeof(double) * B, cudaMemcpyHostToDevice, s));
     KX_CUDA_TRY(ctx, kx_views_clear(k, B, v, s));
     KX_CUDA_TRY(ctx, kx_launch_prep(k, B, f_dev, v, nullptr, s));
-    if (kx_tune_contraction(k, B, v, nullptr, s, &ctx->launches))
+    if (kx_tune_contraction(k, B, f_dev, v, nullptr, s, &ctx->launches))
         return kx_set_error(ctx, KX_ECUDA, "contraction autotuning failed");
     KX_CUDA_TRY(ctx, kx_launch_contract(k, B, f_dev, v, nullptr, 1, s));
     KX_CUDA_TRY(ctx, kx_launch_finalize(k, B, f_dev, v, C_dev, project, diag != nullptr, s));
@@ -719,12 +719,17 @@ static int kx_setup_run(kx_ctx *ctx, const kx_kernel *k, int B, const double *si
     return KX_OK;
 }
 
-static cudaError_t kx_enqueue_attempt(const kx_kernel *k, int B, const kx_run &r, cudaStream_t s) {
+// One Heun attempt: contraction, stage 1, contraction, stage 2.  Inside a
+// sequence (first = false for all but its first attempt) every launch may start
+// early (programmatic dependent launch): each kernel waits for its predecessor
+// before it reads the predecessor's outputs.
+static cudaError_t kx_enqueue_attempt(const kx_kernel *k, int B, const kx_run &r, cudaStream_t s,
+                                      bool first = true) {
     cudaError_t e;
-    if ((e = kx_launch_contract(k, B, r.sv.f, r.v, r.sv.st, 1, s)) != cudaSuccess) return e;
-    if ((e = kx_launch_stage(k, B, r.v, r.sv, 1, s)) != cudaSuccess) return e;
-    if ((e = kx_launch_contract(k, B, r.sv.fp, r.v, r.sv.st, 2, s)) != cudaSuccess) return e;
-    return kx_launch_stage(k, B, r.v, r.sv, 2, s);
+    if ((e = kx_launch_contract(k, B, r.sv.f, r.v, r.sv.st, 1, s, !first)) != cudaSuccess) return e;
+    if ((e = kx_launch_stage(k, B, r.v, r.sv, 1, s, true)) != cudaSuccess) return e;
+    if ((e = kx_launch_contract(k, B, r.sv.fp, r.v, r.sv.st, 2, s, true)) != cudaSuccess) return e;
+    return kx_launch_stage(k, B, r.v, r.sv, 2, s, true);
 }
 
 static int kx_collect(kx_ctx *ctx, const kx_kernel *k, int B, const kx_run &r, kx_result *res,
@@ -789,7 +794,7 @@ static int kx_solve_run(kx_ctx *ctx, const kx_kernel *k, int B, const kx_run &r,
     const auto t_start = std::chrono::steady_clock::now();
     KX_CUDA_TRY(ctx, kx_launch_prep(k, B, r.sv.f, r.v, r.sv.st, s));
     ctx->launches += 1;
-    if (kx_tune_contraction(k, B, r.v, r.sv.st, s, &ctx->launches))
+    if (kx_tune_contraction(k, B, r.sv.f, r.v, r.sv.st, s, &ctx->launches))
         return kx_set_error(ctx, KX_ECUDA, "contraction autotuning failed");
     const int G = 16;
     cudaGraph_t graph = nullptr;
@@ -801,7 +806,7 @@ static int kx_solve_run(kx_ctx *ctx, const kx_kernel *k, int B, const kx_run &r,
     cudaError_t e = cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
     if (e == cudaSuccess) {
-        for (int a = 0; a < G && e == cudaSuccess; ++a) e = kx_enqueue_attempt(k, B, r, cap);
+        for (int a = 0; a < G && e == cudaSuccess; ++a) e = kx_enqueue_attempt(k, B, r, cap, a == 0);
         cudaError_t e2 = cudaStreamEndCapture(cap, &graph);
         if (e == cudaSuccess) e = e2;
     }
@@ -930,7 +935,7 @@ extern "C" int kx_time_contraction(kx_ctx *ctx, const kx_kernel *k, int B, const
     cudaError_t e = kx_views_clear(k, B, v, s);
     if (e == cudaSuccess) e = kx_launch_prep(k, B, f_dev, v, nullptr, s);
     ctx->launches += 1;
-    if (e == cudaSuccess && kx_tune_contraction(k, B, v, nullptr, s, &ctx->launches)) e = cudaErrorUnknown;
+    if (e == cudaSuccess && kx_tune_contraction(k, B, f_dev, v, nullptr, s, &ctx->launches)) e = cudaErrorUnknown;
     double total = 0.0;
     for (int it = 0; it < iters && e == cudaSuccess; ++it) {
         if (flush) e = cudaMemsetAsync(flush, it & 0xff, (size_t)flush_bytes, s);

@@ -179,6 +179,25 @@ __device__ __forceinline__ int kx_block_or(int v, double *) { return __syncthrea
 // Threads per instance block: the grid points rounded up to whole warps.
 static inline int kx_fin_threads(int n) { return ((n + 31) / 32) * 32; }
 
+// Launch with (pdl = true) or without programmatic stream serialization.
+template <typename... KArgs, typename... Args>
+static cudaError_t kx_launch_ex(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem,
+                                cudaStream_t s, bool pdl, Args... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    if (pdl) {
+        at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+        at[0].val.programmaticStreamSerializationAllowed = 1;
+        cfg.attrs = at;
+        cfg.numAttrs = 1;
+    }
+    return cudaLaunchKernelEx(&cfg, kern, args...);
+}
+
 // ------------------------------------------------------------------- prep
 // Per instance (block b, thread = grid point): f_max = max |f|, and either
 //  FP64 path: lf = ln max(f, 1e-300)
@@ -336,6 +355,8 @@ __global__ void __launch_bounds__(KX_FIN_THREADS)
     k_prep(int n, int path, const double *__restrict__ f, const double *__restrict__ E,
            const double *__restrict__ h, kx_batch_views v, const kx_inst_state *__restrict__ st) {
     __shared__ double smem[64 + 32 + 2 * KX_MAX_N];
+    kx_pdl_trigger();
+    kx_pdl_wait();
     const int b = blockIdx.x;
     if (st && st[b].done) return;
     const bool in = threadIdx.x < n;
@@ -346,10 +367,10 @@ __global__ void __launch_bounds__(KX_FIN_THREADS)
 }
 
 cudaError_t kx_launch_prep(const kx_kernel *k, int B, const double *f, const kx_batch_views &v,
-                           const kx_inst_state *st, cudaStream_t s) {
+                           const kx_inst_state *st, cudaStream_t s, bool pdl) {
     int path = k->precision;
-    k_prep<<<B, kx_fin_threads(k->n), 0, s>>>(k->n, path, f, k->d_E, k->d_h, v, st);
-    return cudaGetLastError();
+    return kx_launch_ex(k_prep, dim3(B), dim3(kx_fin_threads(k->n)), 0, s, pdl, k->n, path, f,
+                        (const double *)k->d_E, (const double *)k->d_h, v, st);
 }
 
 // ------------------------------------------------------- FP64 contraction
@@ -572,10 +593,8 @@ __global__ void __launch_bounds__(KX_T32)
                 const kx_inst_state *__restrict__ st, int stage) {
     __shared__ float2 s_l[BP][KX_MAX_N + 4];   // (l2_j, delta_j)
     __shared__ float2 s_d[BP][KX_MAX_N];       // (delta_j - D_j, D_j), D_j = delta_{j+1} - delta_j
+    kx_pdl_trigger();
     const int b0 = blockIdx.y * BP;
-    bool act[BP];
-    if (!kx_stream_tables<BP>(n, B, b0, tl, td, st, stage, s_l, s_d, act)) return;
-    __syncthreads();
     const int lane = threadIdx.x & 31;
     const int rot = (lane >> 2) & 3;
     const int so[4] = {rot, (1 + rot) & 3, (2 + rot) & 3, (3 + rot) & 3};
@@ -613,12 +632,18 @@ __global__ void __launch_bounds__(KX_T32)
         }
         return false;
     };
+    // the first unit's tables are constant: they are in flight before the wait
+    // for the predecessor (which writes the per-instance tables and states)
     bool have = seek();
     kx_unit u;
     if (have) {
         u = first_unit(tk);
         load_unit(u);
     }
+    kx_pdl_wait();
+    bool act[BP];
+    if (!kx_stream_tables<BP>(n, B, b0, tl, td, st, stage, s_l, s_d, act)) return;
+    __syncthreads();
     while (have) {
         float hi[BP], lo[BP], di[BP];
 #pragma unroll
@@ -695,6 +720,8 @@ __global__ void __launch_bounds__(KX_T32, VPL == 4 ? 2 : 3)
     __shared__ float2 s_l[BP][KX_MAX_N + 4];   // (l2_j, delta_j)
     __shared__ float2 s_d[BP][KX_MAX_N];       // (delta_j - D_j, D_j), D_j = delta_{j+1} - delta_j
     __shared__ __align__(8) unsigned long long s_bar[KX_T32 / 32][2];
+    kx_pdl_trigger();
+    kx_pdl_wait();
     const int b0 = blockIdx.y * BP;
     bool act[BP];
     if (!kx_stream_tables<BP>(n, B, b0, tl, td, st, stage, s_l, s_d, act)) return;
@@ -871,7 +898,8 @@ static int kx_bin_blocks(int resident, int groups) {
 
 template <int BP, int VPL>
 static cudaError_t kx_launch_stream(const kx_kernel *k, int B, const kx_batch_views &v,
-                                    const kx_inst_state *st, int stage, cudaStream_t s) {
+                                    const kx_inst_state *st, int stage, cudaStream_t s,
+                                    bool pdl = false) {
     const size_t smem = KX_STREAM_SMEM(VPL, KX_T32 / 32);
     int occ = 0;
     cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_stream32<BP, VPL>, KX_T32, smem);
@@ -883,15 +911,16 @@ static cudaError_t kx_launch_stream(const kx_kernel *k, int B, const kx_batch_vi
     dim3 grid(blocks, groups);
     const float4 *W = reinterpret_cast<const float4 *>(k->d_W32);
     const uint4 *PK = reinterpret_cast<const uint4 *>(k->d_pk);
-    k_stream32<BP, VPL><<<grid, KX_T32, smem, s>>>(k->n, k->d_bins, k->d_task, k->d_roff, B, k->d_vt, W,
-                                              PK, v.tl, v.td, reinterpret_cast<float2 *>(v.partial),
-                                              v.chunks, st, stage, v.err);
-    return cudaGetLastError();
+    return kx_launch_ex(k_stream32<BP, VPL>, grid, dim3(KX_T32), smem, s, pdl, k->n,
+                        (const int *)k->d_bins, (const int4 *)k->d_task, (const int *)k->d_roff, B,
+                        (const uint32_t *)k->d_vt, W, PK, (const float2 *)v.tl, (const float2 *)v.td,
+                        reinterpret_cast<float2 *>(v.partial), v.chunks, st, stage, v.err);
 }
 
 template <int BP, int VPL>
 static cudaError_t kx_launch_stream_r(const kx_kernel *k, int B, const kx_batch_views &v,
-                                      const kx_inst_state *st, int stage, cudaStream_t s) {
+                                      const kx_inst_state *st, int stage, cudaStream_t s,
+                                      bool pdl = false) {
     int occ = 0;
     cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_stream32r<BP, VPL>, KX_T32, 0);
     if (e != cudaSuccess) return e;
@@ -900,12 +929,11 @@ static cudaError_t kx_launch_stream_r(const kx_kernel *k, int B, const kx_batch_
     const int groups = (B + BP - 1) / BP;
     const int blocks = kx_bin_blocks(occ * sms, groups);
     dim3 grid(blocks, groups);
-    k_stream32r<BP, VPL><<<grid, KX_T32, 0, s>>>(k->n, k->d_bins, k->d_task, k->d_roff, B, k->d_vt,
-                                            reinterpret_cast<const float4 *>(k->d_W32),
-                                            reinterpret_cast<const uint4 *>(k->d_pk), v.tl, v.td,
-                                            reinterpret_cast<float2 *>(v.partial), v.chunks, st,
-                                            stage);
-    return cudaGetLastError();
+    return kx_launch_ex(k_stream32r<BP, VPL>, grid, dim3(KX_T32), 0, s, pdl, k->n,
+                        (const int *)k->d_bins, (const int4 *)k->d_task, (const int *)k->d_roff, B,
+                        (const uint32_t *)k->d_vt, reinterpret_cast<const float4 *>(k->d_W32),
+                        reinterpret_cast<const uint4 *>(k->d_pk), (const float2 *)v.tl,
+                        (const float2 *)v.td, reinterpret_cast<float2 *>(v.partial), v.chunks, st, stage);
 }
 
 // ------------------------------------------------------------ autotuner
@@ -942,20 +970,42 @@ static int kx_stream_variant(const kx_kernel *k, int B) {
 }
 
 static cudaError_t kx_stream_launch(int variant, const kx_kernel *k, int B, const kx_batch_views &v,
-                                    const kx_inst_state *st, int stage, cudaStream_t s) {
+                                    const kx_inst_state *st, int stage, cudaStream_t s,
+                                    bool pdl = false) {
     if (k->vpl == 2) {
-        if (variant == 3) return kx_launch_stream_r<4, 2>(k, B, v, st, stage, s);
-        return variant == 1 ? kx_launch_stream_r<2, 2>(k, B, v, st, stage, s)
-                            : kx_launch_stream_r<1, 2>(k, B, v, st, stage, s);
+        if (variant == 3) return kx_launch_stream_r<4, 2>(k, B, v, st, stage, s, pdl);
+        return variant == 1 ? kx_launch_stream_r<2, 2>(k, B, v, st, stage, s, pdl)
+                            : kx_launch_stream_r<1, 2>(k, B, v, st, stage, s, pdl);
     }
-    if (variant == 3) return kx_launch_stream_r<4, 4>(k, B, v, st, stage, s);
-    if (variant == 2) return kx_launch_stream<4, 4>(k, B, v, st, stage, s);
-    if (variant == 1) return kx_launch_stream_r<2, 4>(k, B, v, st, stage, s);
-    return kx_launch_stream_r<1, 4>(k, B, v, st, stage, s);
+    if (variant == 3) return kx_launch_stream_r<4, 4>(k, B, v, st, stage, s, pdl);
+    if (variant == 2) return kx_launch_stream<4, 4>(k, B, v, st, stage, s, pdl);
+    if (variant == 1) return kx_launch_stream_r<2, 4>(k, B, v, st, stage, s, pdl);
+    return kx_launch_stream_r<1, 4>(k, B, v, st, stage, s, pdl);
 }
 
-int kx_tune_contraction(const kx_kernel *k, int B, const kx_batch_views &v, const kx_inst_state *st,
-                        cudaStream_t s, long long *launches) {
+// Stand-in predecessor for the autotuner: lets its successor launch at once
+// and keeps one thread busy for about ns nanoseconds (at most 2^16 polls of
+// the global timer), as a Heun stage occupies the GPU before a contraction.
+__global__ void k_hold(unsigned long long ns) {
+    kx_pdl_trigger();
+    if (threadIdx.x != 0) return;
+    unsigned long long t0;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t0));
+    for (int it = 0; it < (1 << 16); ++it) {
+        unsigned long long t;
+        asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+        if (t - t0 >= ns) break;
+        __nanosleep(64);
+    }
+}
+
+// The candidates are timed the way the solve runs them: a captured graph of
+// six (hold, contraction) pairs, each contraction launched as a programmatic
+// dependent of a 10 us hold, so that a variant's early start (its first table
+// loads in flight while the predecessor still runs) counts as it does between
+// Heun stages.
+int kx_tune_contraction(const kx_kernel *k, int B, const double *f, const kx_batch_views &v,
+                        const kx_inst_state *st, cudaStream_t s, long long *launches) {
     if (k->precision != KX_FP32) return 0;
     int dev = 0;
     cudaGetDevice(&dev);
@@ -964,23 +1014,42 @@ int kx_tune_contraction(const kx_kernel *k, int B, const kx_batch_views &v, cons
         std::lock_guard<std::mutex> lock(g_tune_mu);
         if (g_tuned.count(key)) return 0;
     }
-    int cand[3], nc = 0;
+    int cand[4], nc = 0;
     kx_stream_candidates(k, B, cand, &nc);
     int best = kx_stream_default(k, B);
     if (nc > 1) {
+        const int R = 6;
         cudaEvent_t e0 = nullptr, e1 = nullptr;
         cudaError_t e = cudaEventCreate(&e0);
         if (e == cudaSuccess) e = cudaEventCreate(&e1);
         float best_ms = 0.f;
         for (int c = 0; c < nc && e == cudaSuccess; ++c) {
-            e = kx_stream_launch(cand[c], k, B, v, st, 1, s);   // warm
+            cudaStream_t cap = nullptr;
+            cudaGraph_t graph = nullptr;
+            cudaGraphExec_t exec = nullptr;
+            e = cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking);
+            if (e == cudaSuccess) e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+            if (e == cudaSuccess) {
+                for (int r = 0; r < R && e == cudaSuccess; ++r) {
+                    k_hold<<<1, 32, 0, cap>>>(10000ull);
+                    e = cudaGetLastError();
+                    if (e == cudaSuccess) e = kx_stream_launch(cand[c], k, B, v, st, 1, cap, true);
+                }
+                cudaError_t e2 = cudaStreamEndCapture(cap, &graph);
+                if (e == cudaSuccess) e = e2;
+            }
+            if (e == cudaSuccess) e = cudaGraphInstantiate(&exec, graph, 0);
+            if (e == cudaSuccess) e = cudaGraphLaunch(exec, s);   // warm
             if (e == cudaSuccess) e = cudaEventRecord(e0, s);
-            for (int r = 0; r < 3 && e == cudaSuccess; ++r) e = kx_stream_launch(cand[c], k, B, v, st, 1, s);
+            for (int r = 0; r < 2 && e == cudaSuccess; ++r) e = cudaGraphLaunch(exec, s);
             if (e == cudaSuccess) e = cudaEventRecord(e1, s);
             if (e == cudaSuccess) e = cudaEventSynchronize(e1);
             float ms = 0.f;
             if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
-            if (launches) *launches += 4;
+            if (exec) cudaGraphExecDestroy(exec);
+            if (graph) cudaGraphDestroy(graph);
+            if (cap) cudaStreamDestroy(cap);
+            if (launches) *launches += 3 * 2 * R;
             if (e == cudaSuccess && (c == 0 || ms < best_ms)) {
                 best_ms = ms;
                 best = cand[c];
@@ -1009,7 +1078,7 @@ extern "C" int kx_set_stream_variant(kx_ctx *ctx, int n, int batch, int variant)
 }
 
 cudaError_t kx_launch_contract(const kx_kernel *k, int B, const double *f, const kx_batch_views &v,
-                               const kx_inst_state *st, int stage, cudaStream_t s) {
+                               const kx_inst_state *st, int stage, cudaStream_t s, bool pdl) {
     const int n = k->n, chunks = v.chunks;
     if (k->precision == KX_SPLIT_TF32) return kx_launch_batch_contract(k, B, v, st, stage, v.err, s);
     if (k->precision == KX_FP64) {
@@ -1019,7 +1088,9 @@ cudaError_t kx_launch_contract(const kx_kernel *k, int B, const double *f, const
         return cudaGetLastError();
     }
     // the variant tuned for this size and batch (or the default rule)
-    return kx_stream_launch(kx_stream_variant(k, B), k, B, v, st, stage, s);
+    // (only the streaming kernels wait for their predecessor: the other paths'
+    // contractions always launch in full stream order)
+    return kx_stream_launch(kx_stream_variant(k, B), k, B, v, st, stage, s, pdl);
 }
 
 // ---------------------------------------------------- row combine + projection
@@ -1503,13 +1574,14 @@ __global__ void __launch_bounds__(KX_FIN_THREADS)
             const double *__restrict__ h, kx_batch_views v, kx_step_views sv, int stage,
             long long max_attempts) {
     __shared__ double smem[5 * KX_FIN_THREADS + 8];
+    kx_pdl_trigger();
+    kx_pdl_wait();
     kx_stage_body(blockIdx.x, n, chunks, path, E, h, v, sv, stage, max_attempts, smem);
 }
 
 cudaError_t kx_launch_stage(const kx_kernel *k, int B, const kx_batch_views &v,
-                            const kx_step_views &sv, int stage, cudaStream_t s) {
+                            const kx_step_views &sv, int stage, cudaStream_t s, bool pdl) {
     int path = k->precision;
-    k_stage<<<B, kx_fin_threads(k->n), 0, s>>>(k->n, v.chunks, path, k->d_E, k->d_h, v, sv, stage,
-                                         sv.max_attempts);
-    return cudaGetLastError();
+    return kx_launch_ex(k_stage, dim3(B), dim3(kx_fin_threads(k->n)), 0, s, pdl, k->n, v.chunks, path,
+                        (const double *)k->d_E, (const double *)k->d_h, v, sv, stage, sv.max_attempts);
 }

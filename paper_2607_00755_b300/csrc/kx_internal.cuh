@@ -168,15 +168,18 @@ cudaError_t kx_launch_count_nnz(const kx_kernel *k, unsigned long long *d_count,
 
 // prep: f -> (fmax, lf64 | sf, sld); mode selects path
 cudaError_t kx_launch_prep(const kx_kernel *k, int B, const double *f, const kx_batch_views &v,
-                           const kx_inst_state *st, cudaStream_t s);
+                           const kx_inst_state *st, cudaStream_t s, bool pdl = false);
 // Times the FP32 path's streaming variants once per (device, grid size, batch)
 // on the caller's prepared views and keeps the fastest for later launches
 // (including graph captures).  Synchronises the stream; call outside capture.
 // Adds the launches it made to *launches.  0 on success, -1 on a CUDA error.
-int kx_tune_contraction(const kx_kernel *k, int B, const kx_batch_views &v, const kx_inst_state *st,
-                        cudaStream_t s, long long *launches);
+int kx_tune_contraction(const kx_kernel *k, int B, const double *f, const kx_batch_views &v,
+                        const kx_inst_state *st, cudaStream_t s, long long *launches);
+// pdl: launch with programmatic stream serialization where the kernel supports
+// it (the FP32 streaming contraction and the stage kernel wait for their
+// predecessor inside; other kernels launch in full stream order).
 cudaError_t kx_launch_contract(const kx_kernel *k, int B, const double *f, const kx_batch_views &v,
-                               const kx_inst_state *st, int stage, cudaStream_t s);
+                               const kx_inst_state *st, int stage, cudaStream_t s, bool pdl = false);
 // finalize for kx_collision: C_out = (proj) C_raw
 cudaError_t kx_launch_finalize(const kx_kernel *k, int B, const double *f, const kx_batch_views &v,
                                double *C_out, int project, int want_diag, cudaStream_t s);
@@ -194,7 +197,7 @@ struct kx_step_views {
     int fixed, check_every, project;
 };
 cudaError_t kx_launch_stage(const kx_kernel *k, int B, const kx_batch_views &v,
-                            const kx_step_views &sv, int stage, cudaStream_t s);
+                            const kx_step_views &sv, int stage, cudaStream_t s, bool pdl = false);
 cudaError_t kx_launch_mbfit(const kx_kernel *k, int B, const double *f, double *out3,
                             cudaStream_t s);
 

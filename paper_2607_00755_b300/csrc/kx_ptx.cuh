@@ -6,6 +6,15 @@
 
 #define KX_WAIT_CYCLES (4ll << 30)  // bounded mbarrier wait, about 2 s
 
+// Programmatic dependent launch.  A kernel launched with programmatic stream
+// serialization may start while its predecessor in the stream still runs:
+// kx_pdl_wait blocks until the predecessor grid has completed and its memory
+// operations are visible (it returns at once for an ordinary launch), and
+// kx_pdl_trigger allows the successor's blocks to be scheduled.  Work before
+// the wait may read only data that no earlier kernel of the sequence writes.
+__device__ __forceinline__ void kx_pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void kx_pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
 __device__ __forceinline__ uint32_t kx_smem_u32(const void *p) {
     return (uint32_t)__cvta_generic_to_shared(p);
 }

@@ -142,12 +142,15 @@ static void kx_free_group(Group *g) {
     if (g->k) kx_kernel_release(g->k);
 }
 
-static cudaError_t kx_group_attempt(Group *g, cudaStream_t s) {
+// One Heun attempt over all slots; after the first attempt of a captured tick
+// every launch may start early (programmatic dependent launch, each kernel
+// waits for its predecessor before reading its outputs).
+static cudaError_t kx_group_attempt(Group *g, cudaStream_t s, bool first) {
     cudaError_t e;
-    if ((e = kx_launch_contract(g->k, g->cap, g->sv.f, g->v, g->sv.st, 1, s)) != cudaSuccess) return e;
-    if ((e = kx_launch_stage(g->k, g->cap, g->v, g->sv, 1, s)) != cudaSuccess) return e;
-    if ((e = kx_launch_contract(g->k, g->cap, g->sv.fp, g->v, g->sv.st, 2, s)) != cudaSuccess) return e;
-    return kx_launch_stage(g->k, g->cap, g->v, g->sv, 2, s);
+    if ((e = kx_launch_contract(g->k, g->cap, g->sv.f, g->v, g->sv.st, 1, s, !first)) != cudaSuccess) return e;
+    if ((e = kx_launch_stage(g->k, g->cap, g->v, g->sv, 1, s, true)) != cudaSuccess) return e;
+    if ((e = kx_launch_contract(g->k, g->cap, g->sv.fp, g->v, g->sv.st, 2, s, true)) != cudaSuccess) return e;
+    return kx_launch_stage(g->k, g->cap, g->v, g->sv, 2, s, true);
 }
 
 // Build (or fail) the group of request r.  Called on the worker thread.
@@ -229,7 +232,7 @@ static int kx_make_group(kx_server *srv, const Request &r, Group **out) {
     if (e == cudaSuccess) e = cudaStreamSynchronize(g->stream);
     // pick the streaming variant for this size and slot count before capture
     // (timed on the group's zeroed tables: same work as real inputs)
-    if (e == cudaSuccess && kx_tune_contraction(k, cap, g->v, nullptr, g->stream, nullptr))
+    if (e == cudaSuccess && kx_tune_contraction(k, cap, g->sv.f, g->v, nullptr, g->stream, nullptr))
         e = cudaErrorUnknown;
     // captured graph of attempts_per_tick Heun attempts over all slots
     cudaStream_t cap_s = nullptr;
@@ -237,7 +240,7 @@ static int kx_make_group(kx_server *srv, const Request &r, Group **out) {
     if (e == cudaSuccess) e = cudaStreamBeginCapture(cap_s, cudaStreamCaptureModeThreadLocal);
     if (e == cudaSuccess) {
         for (int a = 0; a < srv->cfg.attempts_per_tick && e == cudaSuccess; ++a)
-            e = kx_group_attempt(g.get(), cap_s);
+            e = kx_group_attempt(g.get(), cap_s, a == 0);
         cudaError_t e2 = cudaStreamEndCapture(cap_s, &g->graph);
         if (e == cudaSuccess) e = e2;
     }
