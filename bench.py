@@ -36,7 +36,16 @@ L2_FLUSH_BYTES = 512 << 20     # > 126 MB L2
 # DRAM bytes (read + write) per launch from one ncu capture of the current kernels
 # (profiles/k_stream32r_n128_batch4.md, profiles/k_stream32r_n384_single.md); None
 # whenever those kernels have changed since the capture.
-NCU_TRAFFIC = {"stream_n128_b4": 6.789376e6, "stream_n384": 172.478208e6 + 2.921728e6}
+NCU_TRAFFIC = {"stream_n128_b4": 6.783488e6, "stream_n384": 172.482048e6 + 2.700800e6}
+
+
+def stream_kernel_name(ctx, n, batch):
+    """Name of the FP32 streaming kernel the contraction of (n, batch) uses."""
+    var, tuned = ctx.stream_variant(n, batch)
+    vpl = 2 if n <= 160 else 4
+    per = {0: 1, 1: 2, 2: 4, 3: 4}[var]
+    name = f"k_stream32<4,4> (bulk-copy staged)" if var == 2 else f"k_stream32r<{per},{vpl}>"
+    return f"{name} ({per} instance{'s' if per > 1 else ''} per pass, {'tuned' if tuned else 'default rule'})"
 SOLVE = dict(t_end=1e5, h0=1e-3, rtol=1e-6, l1_tol=1e-3, check_every=10, max_attempts=2_000_000)
 
 
@@ -156,10 +165,13 @@ def run_contraction_only(args):
     prec = {"fp32": kx.FP32, "fp64": kx.FP64, "split": kx.SPLIT_TF32}[args.precision]
     k = ctx.build_kernel(q, precision=prec)
     f = torch.as_tensor(ki.batch_bimodal(np.random.default_rng(7), q, args.batch), device="cuda")
+    if args.variant >= 0 and prec == kx.FP32:
+        ctx.set_stream_variant(args.n, args.batch, args.variant)
     ms = ctx.time_contraction(k, f, iters=args.iters, flush_bytes=L2_FLUSH_BYTES)
     alg = k.info()["stream_bytes"]
     hbm, src = peaks()
-    print(json.dumps({"kernel": "contraction", "n": args.n, "batch": args.batch,
+    name = stream_kernel_name(ctx, args.n, args.batch) if prec == kx.FP32 else args.precision
+    print(json.dumps({"kernel": "contraction", "variant": name, "n": args.n, "batch": args.batch,
                       "precision": args.precision, "avg_ms": ms,
                       "algorithmic_bytes": alg, "achieved_gbs": alg / (ms * 1e-3) / 1e9,
                       "frac_of_" + src + "_hbm": alg / (ms * 1e-3) / 1e9 / hbm,
@@ -354,6 +366,8 @@ def main():
     ap.add_argument("--batch", type=int, default=1)
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64", "split"])
     ap.add_argument("--iters", type=int, default=20)
+    ap.add_argument("--variant", type=int, default=-1,
+                    help="FP32: pin the streaming variant (0..3) instead of tuning it")
     ap.add_argument("--requests", type=int, default=100)
     ap.add_argument("--no-serving", action="store_true",
                     help="skip the uneven-batch and serving measurements")
@@ -401,6 +415,8 @@ def main():
             dist.barrier()
         torch.cuda.synchronize()
 
+    if args.variant >= 0:   # (profiling: a serialising profiler would tune differently)
+        ctx.set_stream_variant(len(q), B, args.variant)
     for _ in range(args.warmup):
         one_step(kx.FP32)
     if args.only == "step":
@@ -478,7 +494,7 @@ def main():
     achieved = alg_bytes / (ms_cold * 1e-3) / 1e9
     roof = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
             "frac": achieved / hbm, "traffic": NCU_TRAFFIC["stream_n128_b4"],
-            "kernel": "k_stream32r<2,2> (N=128, 4 instances, 2 per pass)",
+            "kernel": f"N=128, 4 instances: {stream_kernel_name(ctx, 128, B)}",
             "algorithmic_bytes_per_launch": alg_bytes, "avg_launch_ms_cold_l2": ms_cold,
             "avg_launch_ms_warm_l2": ms_warm, "peak_source": src_peak}
     # streaming single-instance roofline at N=384 (tables 227 MB > L2)
@@ -491,7 +507,7 @@ def main():
     roof384 = {"bound": "hbm", "achieved": b384 / (ms384 * 1e-3) / 1e9, "peak": hbm,
                "unit": "GB/s", "frac": b384 / (ms384 * 1e-3) / 1e9 / hbm,
                "traffic": NCU_TRAFFIC["stream_n384"],
-               "kernel": "k_stream32r<1,4> (N=384, single instance, cold L2)",
+               "kernel": f"N=384, single instance, cold L2: {stream_kernel_name(ctx, 384, 1)}",
                "algorithmic_bytes_per_launch": b384, "avg_launch_ms": ms384,
                "evals_per_s": 1e3 / ms384}
 

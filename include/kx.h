@@ -318,6 +318,12 @@ int kx_math_check(kx_ctx *ctx, int which, int n, const double *x_dev, double *ou
  * not apply. */
 int kx_set_stream_variant(kx_ctx *ctx, int n, int batch, int variant);
 
+/* The FP32 streaming variant (numbering as for kx_set_stream_variant) that
+ * contractions of n-point grids with `batch` instances use on the context's
+ * device: the pinned or tuned one (*tuned = 1; tuned = NULL allowed), else the
+ * rule used before tuning (*tuned = 0).  KX_EINVAL for bad arguments. */
+int kx_get_stream_variant(kx_ctx *ctx, int n, int batch, int *variant, int *tuned);
+
 #ifdef __cplusplus
 }
 #endif

@@ -27,7 +27,7 @@ EXPORTS = (
     "kx_kernel_grid", "kx_kernel_row", "kx_collision", "kx_collision_host", "kx_step",
     "kx_solve", "kx_solve_host", "kx_mb_fit", "kx_launch_count", "kx_time_contraction",
     "kx_collision_noalloc", "kx_server_start", "kx_submit", "kx_poll", "kx_server_get_stats",
-    "kx_server_stop", "kx_math_check", "kx_set_stream_variant",
+    "kx_server_stop", "kx_math_check", "kx_set_stream_variant", "kx_get_stream_variant",
 )
 
 
@@ -126,6 +126,7 @@ def load_library(path: str = LIB_PATH):
         "kx_mb_fit": (i, [vp, vp, i, vp, vp]),
         "kx_math_check": (i, [vp, i, i, vp, vp]),
         "kx_set_stream_variant": (i, [vp, i, i, i]),
+        "kx_get_stream_variant": (i, [vp, i, i, vp, vp]),
         "kx_launch_count": (ctypes.c_longlong, [vp]),
         "kx_time_contraction": (i, [vp, vp, i, vp, i, ctypes.c_longlong, vp]),
         "kx_collision_noalloc": (i, [vp, vp, i, vp, vp, vp, i]),
@@ -330,6 +331,15 @@ class Context:
         rc = self.lib.kx_set_stream_variant(self.h, int(n), int(batch), int(variant))
         if rc:
             raise self.error(rc, "kx_set_stream_variant")
+
+    def stream_variant(self, n, batch):
+        """(variant, tuned) of the FP32 streaming contraction for (n, batch)."""
+        var, tun = ctypes.c_int(-1), ctypes.c_int(0)
+        rc = self.lib.kx_get_stream_variant(self.h, int(n), int(batch), ctypes.byref(var),
+                                            ctypes.byref(tun))
+        if rc:
+            raise self.error(rc, "kx_get_stream_variant")
+        return var.value, bool(tun.value)
 
     def math_check(self, which, x):
         """(library value, CUDA value) of log2 (which=0) or exp (which=1) of x

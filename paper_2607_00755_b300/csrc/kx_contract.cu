@@ -256,12 +256,54 @@ __device__ __forceinline__ unsigned long long kx_block_max_key(unsigned long lon
 // Key of a non-finite value in kx_block_max_key: above the bits of every
 // non-negative double up to +inf.
 #define KX_KEY_NONFINITE 0x7ff0000000000001ull
+// "No key": kx_prep_block reduces max |f| itself.
+#define KX_KEY_NONE 0xffffffffffffffffull
+
+// Block maxima of K 64-bit keys together, after one barrier; us (32 K entries)
+// must not be written again by the block without another barrier in between.
+template <int K>
+__device__ __forceinline__ void kx_block_max_keys(unsigned long long (&x)[K], unsigned long long *us) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+    for (int off = 16; off; off >>= 1)
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            const unsigned long long y = __shfl_xor_sync(0xffffffffu, x[k], off);
+            x[k] = y > x[k] ? y : x[k];
+        }
+    if (lane == 0)
+#pragma unroll
+        for (int k = 0; k < K; ++k) us[k * 32 + warp] = x[k];
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        unsigned long long r = us[k * 32];
+        for (int w = 1; w < nw; ++w) r = us[k * 32 + w] > r ? us[k * 32 + w] : r;
+        x[k] = r;
+    }
+}
 
 // x: this thread's f value (0 for threads past n).  Called at most once per
 // kernel launch (it uses block-scope shared arrays without a trailing barrier).
 // Ei, hi: this thread's grid energy and moment weight; E0 = E_0.
+// key_in: the block maximum of the keys of x (bits of |x|, KX_KEY_NONFINITE for
+// a non-finite x) when the caller has it from its own reduction, else
+// KX_KEY_NONE.
+// FP32 path reference line (any line cancels exactly in the exponent
+// differences; it only keeps the deviations small).  v.fit[b] holds the line
+// the instance's current tables use and the fit of the f they were made from.
+//   mode KX_LINE_FIT: fit this f and use that line (a new instance);
+//   mode KX_LINE_NEXT: use the stored fit of the previous prep's f (as good as
+//     a new fit after one Heun stage) and store this f's fit, so that the fit's
+//     reduction is off the critical path (the stages);
+//   mode KX_LINE_SAME: use the line the current tables use (rebuilding the
+//     tables of the same f gives the same bits: a re-prep is idempotent).
+#define KX_LINE_FIT 0
+#define KX_LINE_NEXT 1
+#define KX_LINE_SAME 2
 __device__ __forceinline__ int kx_prep_block(int n, int path, double x, double Ei, double hi, double E0,
-                             const kx_batch_views &v, int b, double *smem) {
+                             const kx_batch_views &v, int b, double *smem,
+                             unsigned long long key_in = KX_KEY_NONE, int line_mode = KX_LINE_FIT) {
     __shared__ unsigned long long s_key[32];
     __shared__ float s_fit[5 * 32];
     __shared__ double s_scale[3];   // exponent and fraction of log2 f_max, 1 / f_max
@@ -273,8 +315,11 @@ __device__ __forceinline__ int kx_prep_block(int n, int path, double x, double E
     int ex = 0;
     double frx = 0.0;
     if (path != KX_FP64 && in && !nf) kx_log2_parts(x > KX_LOG_FLOOR ? x : KX_LOG_FLOOR, ex, frx);
+    const float4 lines = (line_mode != KX_LINE_FIT && path == KX_FP32) ? v.fit[b] : make_float4(0.f, 0.f, 0.f, 0.f);
     const unsigned long long key =
-        kx_block_max_key(nf ? KX_KEY_NONFINITE : (unsigned long long)__double_as_longlong(fabs(x)), s_key);
+        key_in != KX_KEY_NONE
+            ? key_in
+            : kx_block_max_key(nf ? KX_KEY_NONFINITE : (unsigned long long)__double_as_longlong(fabs(x)), s_key);
     const int bad = key == KX_KEY_NONFINITE;
     const double fm = bad ? INFINITY : __longlong_as_double((long long)key);
     // 1 / f_max on thread 0 and log2 f_max on the first thread of the second
@@ -332,16 +377,46 @@ __device__ __forceinline__ int kx_prep_block(int n, int path, double x, double E
     const float l2f = (float)l2, Kf = (float)K;
     const float w = (in && fm > 0.0 && x > 0.0) ? (float)hi * (float)(x * rfm) : 0.f;
     float sf[5] = {w, w * Kf, w * Kf * Kf, w * l2f, w * Kf * l2f};
-    kx_block_sumf_once<5>(sf, s_fit);
-    float slope = 0.f, icpt = 0.f;
-    if (sf[0] > 0.f) {
-        const float det = sf[0] * sf[2] - sf[1] * sf[1];
-        if (det > 1e-4f * sf[0] * sf[2]) slope = (sf[0] * sf[4] - sf[1] * sf[3]) / det;
-        icpt = (sf[3] - slope * sf[1]) / sf[0];
+    auto solve_line = [](const float *t) {
+        float slope = 0.f, icpt = 0.f;
+        if (t[0] > 0.f) {
+            const float det = t[0] * t[2] - t[1] * t[1];
+            if (det > 1e-4f * t[0] * t[2]) slope = (t[0] * t[4] - t[1] * t[3]) / det;
+            icpt = (t[3] - slope * t[1]) / t[0];
+        }
+        return make_float2(icpt, slope);
+    };
+    float2 line;
+    if (line_mode != KX_LINE_FIT) {
+        // this f's fit sums: warp partials now, the block total after the
+        // barrier below (which the D_j exchange needs anyway)
+        const int lane = i & 31, warp = i >> 5;
+#pragma unroll
+        for (int k = 0; k < 5; ++k)
+#pragma unroll
+            for (int off = 16; off; off >>= 1) sf[k] += __shfl_xor_sync(0xffffffffu, sf[k], off);
+        if (lane == 0)
+#pragma unroll
+            for (int k = 0; k < 5; ++k) s_fit[k * 32 + warp] = sf[k];
+        line = line_mode == KX_LINE_NEXT ? make_float2(lines.z, lines.w) : make_float2(lines.x, lines.y);
+    } else {
+        kx_block_sumf_once<5>(sf, s_fit);
+        line = solve_line(sf);
+        if (i == 0) v.fit[b] = make_float4(line.x, line.y, line.x, line.y);
     }
-    const double del = l2 - ((double)icpt + (double)slope * K);
+    const double del = l2 - ((double)line.x + (double)line.y * K);
     if (in) dl[i] = del;
     __syncthreads();
+    if (line_mode != KX_LINE_FIT && i == 0) {
+        float t[5];
+        for (int k = 0; k < 5; ++k) {
+            float x2 = s_fit[k * 32];
+            for (int w2 = 1; w2 < (int)(blockDim.x >> 5); ++w2) x2 += s_fit[k * 32 + w2];
+            t[k] = x2;
+        }
+        const float2 nx = solve_line(t);
+        v.fit[b] = make_float4(line.x, line.y, nx.x, nx.y);
+    }
     if (in) {
         const double D = i + 1 < n ? dl[i + 1] - del : 0.0;
         tl[i] = make_float2(l2f, (float)del);
@@ -361,8 +436,10 @@ __global__ void __launch_bounds__(KX_FIN_THREADS)
     if (st && st[b].done) return;
     const bool in = threadIdx.x < n;
     const double x = in ? f[(long long)b * n + threadIdx.x] : 0.0;
+    // an instance that has been evaluated already keeps the line of its tables
+    const int mode = (st && st[b].evals > 0) ? KX_LINE_SAME : KX_LINE_FIT;
     int bad = kx_prep_block(n, path, x, in ? E[threadIdx.x] : 0.0, in ? h[threadIdx.x] : 0.0, E[0],
-                            v, b, smem);
+                            v, b, smem, KX_KEY_NONE, mode);
     if (threadIdx.x == 0) v.flags[b] = bad;
 }
 
@@ -1064,6 +1141,18 @@ int kx_tune_contraction(const kx_kernel *k, int B, const double *f, const kx_bat
     return 0;
 }
 
+extern "C" int kx_get_stream_variant(kx_ctx *ctx, int n, int batch, int *variant, int *tuned) {
+    if (!ctx || !variant || n < 4 || n > KX_MAX_N || batch < 1) return KX_EINVAL;
+    kx_kernel probe;
+    probe.vpl = n <= 160 ? 2 : 4;
+    const auto key = std::make_tuple(ctx->device, n, batch);
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    auto it = g_tuned.find(key);
+    *variant = it != g_tuned.end() ? it->second : kx_stream_default(&probe, batch);
+    if (tuned) *tuned = it != g_tuned.end();
+    return KX_OK;
+}
+
 extern "C" int kx_set_stream_variant(kx_ctx *ctx, int n, int batch, int variant) {
     if (!ctx || n < 4 || n > KX_MAX_N || batch < 1 || variant < -1 || variant > 3) return KX_EINVAL;
     const int vpl = n <= 160 ? 2 : 4;
@@ -1104,7 +1193,9 @@ struct kx_row_out {
     int singular;
 };
 
-// sm: at least 5 * blockDim.x + 8 doubles.
+// sm: at least 5 * blockDim.x + 8 doubles; the caller passes a block barrier
+// before it writes sm[5 blockDim.x .. + 4] again (the projection sums, read by
+// every thread).
 __device__ __forceinline__ kx_row_out kx_combine_project(int n, int chunks, int path, int b, double fi, double Ei,
                                          double hi, const kx_batch_views &v, int project,
                                          double *sm) {
@@ -1178,26 +1269,26 @@ __device__ __forceinline__ kx_row_out kx_combine_project(int n, int chunks, int 
     const double s[5] = {hxi, hEx, hEx * Ei, hC, hC * Ei};
     // five block sums (column form); one thread solves the 2x2 system
     kx_block_cols<5>(s, sm);
-    if (i == 0) {
+    {
+        // every thread solves the 2x2 system from the five sums (the same
+        // arithmetic everywhere; no broadcast barrier).  sm[5T .. 5T + 4] is not
+        // written again before the block's next barrier.
         const double *t = sm + 5 * T;
-        const double det = t[0] * t[2] - t[1] * t[1];
-        double al = 0.0, be = 0.0, sg = 0.0;
-        if (!(det > KX_DET_GUARD * t[0] * t[2])) {
-            sg = 1.0;
+        const double t0 = t[0], t1 = t[1], t2 = t[2], t3 = t[3], t4 = t[4];
+        const double det = t0 * t2 - t1 * t1;
+        double al = 0.0, be = 0.0;
+        int sg = 0;
+        if (!(det > KX_DET_GUARD * t0 * t2)) {
+            sg = 1;
         } else {
             const double rd = 1.0 / det;
-            al = (t[3] * t[2] - t[4] * t[1]) * rd;
-            be = (t[4] * t[0] - t[3] * t[1]) * rd;
+            al = (t3 * t2 - t4 * t1) * rd;
+            be = (t4 * t0 - t3 * t1) * rd;
         }
-        sm[5 * T + 5] = al;
-        sm[5 * T + 6] = be;
-        sm[5 * T + 7] = sg;
+        r.alpha = al;
+        r.beta = be;
+        r.singular = sg;
     }
-    __syncthreads();
-    r.alpha = sm[5 * T + 5];
-    r.beta = sm[5 * T + 6];
-    r.singular = sm[5 * T + 7] != 0.0;
-    __syncthreads();
     r.Cproj = Craw - xi * (r.alpha + r.beta * Ei);
     return r;
 }
@@ -1241,6 +1332,7 @@ __global__ void __launch_bounds__(KX_FIN_THREADS)
     }
     kx_row_out r = kx_combine_project(n, chunks, path, b, fi, Ei, hi, v, project, smem);
     if (i < n) Cout[(long long)b * n + i] = project ? r.Cproj : r.Craw;
+    __syncthreads();   // every thread has read the projection sums (sm[5T ..])
     if (want_diag) kx_write_diag(n, Ei, hi, r, v.diag + b, v.fmax[b], v.flags[b], smem);
 }
 
@@ -1364,7 +1456,7 @@ __device__ __forceinline__ void kx_stage_body(int b, int n, int chunks, int path
                               const double *__restrict__ h, kx_batch_views v,
                               kx_step_views sv, int stage, long long max_attempts,
                               double *smem) {
-    __shared__ unsigned long long s_key[32];
+    __shared__ unsigned long long s_keys[3 * 32];
     __shared__ double s_env[KX_MAX_SRC];
     const int i = threadIdx.x;
     kx_inst_state *st = sv.st + b;
@@ -1439,9 +1531,13 @@ __device__ __forceinline__ void kx_stage_body(int b, int n, int chunks, int path
     const double kv = in ? C + Si : 0.0;
     if (stage == 1) {
         const double fpi = f0 + htry * kv;
-        // one reduction for both flags: 2 = non-finite, 1 = negative
-        const unsigned long long key = kx_block_max_key(
-            (in && !isfinite(fpi)) || flag_in ? 2ull : ((in && fpi < 0.0) ? 1ull : 0ull), s_key);
+        // one reduction for both flags (2 = non-finite, 1 = negative) and for
+        // max |f_p| of the next prep
+        unsigned long long keys[2] = {
+            (in && !isfinite(fpi)) || flag_in ? 2ull : ((in && fpi < 0.0) ? 1ull : 0ull),
+            (in && isfinite(fpi)) ? (unsigned long long)__double_as_longlong(fabs(fpi)) : 0ull};
+        kx_block_max_keys<2>(keys, s_keys);
+        const unsigned long long key = keys[0];
         if (key == 2ull) {
             if (threadIdx.x == 0) {
                 st->status = KX_ENONFINITE;
@@ -1473,12 +1569,13 @@ __device__ __forceinline__ void kx_stage_body(int b, int n, int chunks, int path
             fp[i] = fpi;
         }
         if (threadIdx.x == 0) st->evals += 1;
-        int bad2 = kx_prep_block(n, path, in ? fpi : 0.0, Ei, hi, E0, v, b, smem);
+        int bad2 = kx_prep_block(n, path, in ? fpi : 0.0, Ei, hi, E0, v, b, smem, keys[1], KX_LINE_NEXT);
         if (threadIdx.x == 0) v.flags[b] = bad2;
         return;
     }
     // stage 2: one reduction for the flags and the error norm (keys ordered
-    // non-finite > negative > the bits of err >= 0)
+    // non-finite > negative > the bits of err >= 0), and for max |f_c| and
+    // max |f| (the next prep takes the one the step decision keeps)
     const double fci = f0 + 0.5 * htry * (k1v + kv);
     const double e = in ? fabs(fci - fpv) / (sv.atol + sv.rtol * fabs(fci)) : 0.0;
     const unsigned long long kneg = KX_KEY_NONFINITE - 1ull;   // bits of +inf
@@ -1486,7 +1583,11 @@ __device__ __forceinline__ void kx_stage_body(int b, int n, int chunks, int path
     if ((in && !isfinite(fci)) || flag_in) key = KX_KEY_NONFINITE;
     else if (in && fci < 0.0) key = kneg;
     else key = (unsigned long long)__double_as_longlong(e);
-    key = kx_block_max_key(key, s_key);
+    unsigned long long keys[3] = {
+        key, (in && isfinite(fci)) ? (unsigned long long)__double_as_longlong(fabs(fci)) : 0ull,
+        in ? (unsigned long long)__double_as_longlong(fabs(f0)) : 0ull};
+    kx_block_max_keys<3>(keys, s_keys);
+    key = keys[0];
     if (key == KX_KEY_NONFINITE) {
         if (threadIdx.x == 0) {
             st->status = KX_ENONFINITE;
@@ -1565,7 +1666,8 @@ __device__ __forceinline__ void kx_stage_body(int b, int n, int chunks, int path
         }
     }
     // prepare the next attempt's contraction input (f_new or the restored f)
-    int bad2 = kx_prep_block(n, path, in ? fnew : 0.0, Ei, hi, E0, v, b, smem);
+    int bad2 = kx_prep_block(n, path, in ? fnew : 0.0, Ei, hi, E0, v, b, smem, accept ? keys[1] : keys[2],
+                             KX_LINE_NEXT);
     if (threadIdx.x == 0) v.flags[b] = bad2;
 }
 

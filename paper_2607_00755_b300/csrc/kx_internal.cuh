@@ -129,6 +129,8 @@ struct kx_batch_views {
     double2 *partial;      // [B][n][chunks]  (FP32 path: float2 (hi, lo) task partials, [B][chunks])
     const int2 *rtask;     // FP32 path: [n] (first partial slot, tasks) per row
     double *rfmax;         // [B]          1 / f_max
+    float4 *fit;           // [B]          FP32 path: reference lines (icpt, slope) of the current
+                           //              tables and of the fit of their f
     int *flags;            // [B] non-finite flags
     double *M2;            // [B] |M|^2 per instance
     kx_diag *diag;         // [B]
