@@ -142,7 +142,7 @@ size_t kx_views_bytes(const kx_kernel *k, int B) {
         const size_t Bpad = ((B + 63) / 64) * 64;
         s += kx_align(sizeof(float) * Bpad * k->Kpad * 2);   // bt (hi, lo)
         s += kx_align(sizeof(float) * Bpad * k->Kpad);       // fT
-        s += kx_align(sizeof(float) * Bpad * k->Mpad);       // T
+        s += kx_align(sizeof(float) * Bpad * (k->Mpad / 128) * (128 / k->n + 2));   // Gp
     }
     return s;
 }
@@ -164,14 +164,14 @@ void kx_carve_views(const kx_kernel *k, int B, void *base, kx_batch_views *v) {
     v->err = (int *)p; p += kx_align(sizeof(int));
     v->chunks = chunks;
     v->rtask = k->d_rtask;
-    v->bt = v->fT = v->T = nullptr;
+    v->bt = v->fT = v->Gp = nullptr;
     v->B = B;
     v->Bpad = ((B + 63) / 64) * 64;
     if (k->precision == KX_SPLIT_TF32) {
         const size_t Bpad = v->Bpad;
         v->bt = (float *)p; p += kx_align(sizeof(float) * Bpad * k->Kpad * 2);
         v->fT = (float *)p; p += kx_align(sizeof(float) * Bpad * k->Kpad);
-        v->T = (float *)p; p += kx_align(sizeof(float) * Bpad * k->Mpad);
+        v->Gp = (float *)p; p += kx_align(sizeof(float) * Bpad * (k->Mpad / 128) * (128 / k->n + 2));
     }
 }
 

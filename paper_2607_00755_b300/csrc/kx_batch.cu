@@ -17,10 +17,8 @@
 
 #include "kx_internal.cuh"
 
-#define KX_MMA_NT 64               // instances per MMA tile (the MMA's N)
 #define KX_ATILE 4096              // floats per A tile: 128 rows x 32 k
 #define KX_BTILE 2048              // floats per B tile: 64 rows x 32 k
-#define KX_GEMM_SMEM (65536 + 32768 + 64)
 #define KX_SEG 64                  // elements per loss segment at most (one j_L)
 
 #include "kx_ptx.cuh"
@@ -72,26 +70,41 @@ __device__ __forceinline__ float kx_ex2f(float x) {
     asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
     return y;
 }
-// --------------------------------------------------------- gain GEMM (T)
-// One CTA (4 warps) per (128-row M tile, 64-instance N tile).  Thread 0 stages
-// the hi/lo operand tiles of each 32-wide k block with bulk copies into a
-// two-stage ring (mbarrier transaction counts), issues the 3 x 4 MMAs of the
-// block (M = 128, N = 64, K = 8 each) and commits them to the stage's
-// completion barrier.  The accumulator (128 lanes x 64 FP32 columns of tensor
-// memory) is read back by all four warps (warp w owns lanes 32w..32w+31).
-__global__ void __launch_bounds__(128)
-    k_gain_mma(const float *__restrict__ A, const float *__restrict__ Bt, float *__restrict__ T,
-               int KB, int ldT, int *err) {
+// --------------------------------------------------------- gain GEMM (fused)
+// One CTA (4 warps) per (128-row M tile of W_full, N tile of up to 256
+// instances).  Thread 0 stages the hi/lo operand tiles of each 32-wide k block
+// with bulk copies into a two-stage ring (mbarrier transaction counts: the A
+// tile and up to four 64-instance B tiles, which form one 256-row K-major
+// operand), issues the 3 x 4 MMAs of the block (M = 128, N = NTc, K = 8 each)
+// and commits them to the stage's completion barrier.  The accumulator
+// (128 lanes x NTc FP32 columns of tensor memory) holds T = W_full F for the
+// tile's rows (i, a); the epilogue forms the gain directly: each thread
+// multiplies its row's T by f'_a (instance-minor f/f_max) into a shared-memory
+// product matrix, and each column (instance) is summed over the rows of every
+// grid point i the tile touches, giving one FP32 partial per (tile, i, instance):
+//   Gp[(mt * segmax + i - i_first(mt)) * Bpad + b] = sum_{a in tile} f'_ab T_(i a) b,
+// i_first(mt) = floor(128 mt / n).  T itself never reaches global memory.
+#define KX_GN 256
+#define KX_GSTAGE (2 * KX_ATILE * 4 + 2 * 4 * KX_BTILE * 4)   // A hi/lo 32 KB + B hi/lo 64 KB
+#define KX_GAIN_SMEM (2 * KX_GSTAGE + 64)
+#define KX_GP_LD 129                                          // product matrix: [col][128 rows + 1]
+static_assert(KX_GN * KX_GP_LD * 4 <= 2 * KX_GSTAGE, "product matrix must fit in the stage buffers");
+
+__host__ __device__ __forceinline__ int kx_gain_segmax(int n) { return 128 / n + 2; }
+
+__global__ void __launch_bounds__(128, 1)
+    k_gain_fused(const float *__restrict__ A, const float *__restrict__ Bt,
+                 const float *__restrict__ fT, float *__restrict__ Gp, int KB, int n, int Bpad,
+                 int *err) {
     extern __shared__ __align__(1024) unsigned char kx_gsm[];
-    float *sA = reinterpret_cast<float *>(kx_gsm);                  // [2 stages][hi, lo][4096]
-    float *sB = reinterpret_cast<float *>(kx_gsm + 65536);          // [2 stages][hi, lo][2048]
-    uint64_t *bars = reinterpret_cast<uint64_t *>(kx_gsm + 98304);  // full[2], done[2]
-    uint32_t *slot = reinterpret_cast<uint32_t *>(kx_gsm + 98304 + 32);
-    int *okf = reinterpret_cast<int *>(kx_gsm + 98304 + 40);
+    uint64_t *bars = reinterpret_cast<uint64_t *>(kx_gsm + 2 * KX_GSTAGE);   // full[2], done[2]
+    uint32_t *slot = reinterpret_cast<uint32_t *>(kx_gsm + 2 * KX_GSTAGE + 32);
+    int *okf = reinterpret_cast<int *>(kx_gsm + 2 * KX_GSTAGE + 40);
     const int nt = blockIdx.x, mt = blockIdx.y;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int NTc = min(KX_GN, Bpad - nt * KX_GN);   // 64, 128, 192 or 256
+    const int nsub = NTc >> 6;
     const float *Ab = A + (size_t)mt * KB * 2 * KX_ATILE;
-    const float *Bb = Bt + (size_t)nt * KB * 2 * KX_BTILE;
     const uint32_t full0 = kx_smem_u32(&bars[0]), done0 = kx_smem_u32(&bars[2]);
     if (tid == 0) {
         for (int k = 0; k < 4; ++k) kx_mbar_init(kx_smem_u32(&bars[k]), 1);
@@ -99,7 +112,7 @@ __global__ void __launch_bounds__(128)
         *okf = 1;
     }
     if (warp == 0) {
-        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 64;" ::"r"(
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 256;" ::"r"(
                          kx_smem_u32(slot))
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
@@ -109,20 +122,23 @@ __global__ void __launch_bounds__(128)
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const uint32_t tmem = *slot;
     if (tid == 0) {
-        constexpr uint32_t idesc = kx_idesc_tf32(128, KX_MMA_NT);
+        const uint32_t idesc = kx_idesc_tf32(128, NTc);
         int ok = 1;
         int issued = 0;   // k blocks whose copies were issued
+        auto stage_a = [&](int s) { return kx_gsm + (size_t)s * KX_GSTAGE; };
+        auto stage_b = [&](int s) { return kx_gsm + (size_t)s * KX_GSTAGE + 2 * KX_ATILE * 4; };
         auto load = [&](int kb, int s) {
             const uint32_t bar = full0 + 8 * s;
-            kx_mbar_expect_tx(bar, 2 * KX_ATILE * 4 + 2 * KX_BTILE * 4);
-            kx_bulk_g2s(kx_smem_u32(sA + (2 * s) * KX_ATILE), Ab + (size_t)(2 * kb) * KX_ATILE,
-                        KX_ATILE * 4, bar);
-            kx_bulk_g2s(kx_smem_u32(sA + (2 * s + 1) * KX_ATILE),
-                        Ab + (size_t)(2 * kb + 1) * KX_ATILE, KX_ATILE * 4, bar);
-            kx_bulk_g2s(kx_smem_u32(sB + (2 * s) * KX_BTILE), Bb + (size_t)(2 * kb) * KX_BTILE,
-                        KX_BTILE * 4, bar);
-            kx_bulk_g2s(kx_smem_u32(sB + (2 * s + 1) * KX_BTILE),
-                        Bb + (size_t)(2 * kb + 1) * KX_BTILE, KX_BTILE * 4, bar);
+            kx_mbar_expect_tx(bar, 2 * KX_ATILE * 4 + 2 * nsub * KX_BTILE * 4);
+            unsigned char *a = stage_a(s), *bsm = stage_b(s);
+            kx_bulk_g2s(kx_smem_u32(a), Ab + (size_t)(2 * kb) * KX_ATILE, KX_ATILE * 4, bar);
+            kx_bulk_g2s(kx_smem_u32(a + KX_ATILE * 4), Ab + (size_t)(2 * kb + 1) * KX_ATILE, KX_ATILE * 4, bar);
+            for (int j = 0; j < nsub; ++j) {
+                const float *src = Bt + ((size_t)(nt * 4 + j) * KB + kb) * 2 * KX_BTILE;
+                kx_bulk_g2s(kx_smem_u32(bsm + j * KX_BTILE * 4), src, KX_BTILE * 4, bar);
+                kx_bulk_g2s(kx_smem_u32(bsm + 4 * KX_BTILE * 4 + j * KX_BTILE * 4), src + KX_BTILE,
+                            KX_BTILE * 4, bar);
+            }
             issued = kb + 1;
         };
         load(0, 0);
@@ -142,10 +158,8 @@ __global__ void __launch_bounds__(128)
                 break;
             }
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            const uint32_t aH = kx_smem_u32(sA + (2 * s) * KX_ATILE);
-            const uint32_t aL = kx_smem_u32(sA + (2 * s + 1) * KX_ATILE);
-            const uint32_t bH = kx_smem_u32(sB + (2 * s) * KX_BTILE);
-            const uint32_t bL = kx_smem_u32(sB + (2 * s + 1) * KX_BTILE);
+            const uint32_t aH = kx_smem_u32(stage_a(s)), aL = aH + KX_ATILE * 4;
+            const uint32_t bH = kx_smem_u32(stage_b(s)), bL = bH + 4 * KX_BTILE * 4;
 #pragma unroll
             for (int step = 0; step < 4; ++step) {
                 const uint32_t o = 256u * step;   // 8 TF32 = two 16-byte core-matrix columns
@@ -170,22 +184,57 @@ __global__ void __launch_bounds__(128)
     }
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    if (*okf) {
-        const int row = mt * 128 + warp * 32 + lane;
-        float *Tr = T + (size_t)row * ldT + (size_t)nt * KX_MMA_NT;
+    const bool ok = *okf != 0;
+    const int nrows = n * n;
+    if (ok) {
+        // products f'_ab T_(i a) b into sP[col][row] (the stage buffers are free:
+        // every copy landed and every MMA completed)
+        float *sP = reinterpret_cast<float *>(kx_gsm);
+        const int rl = warp * 32 + lane, r = mt * 128 + rl;
+        const bool rin = r < nrows;
+        const float *frow = fT + (size_t)(rin ? r % n : 0) * Bpad + (size_t)nt * KX_GN;
+        for (int c = 0; c < NTc; c += 16) {
+            float t[16];
+            kx_tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c, t);
 #pragma unroll
-        for (int c = 0; c < KX_MMA_NT; c += 16) {
-            float r[16];
-            kx_tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c, r);
-#pragma unroll
-            for (int q = 0; q < 16; q += 4)
-                *reinterpret_cast<float4 *>(Tr + c + q) = make_float4(r[q], r[q + 1], r[q + 2], r[q + 3]);
+            for (int q = 0; q < 16; q += 4) {
+                const float4 f4 = rin ? __ldg(reinterpret_cast<const float4 *>(frow + c + q))
+                                      : make_float4(0.f, 0.f, 0.f, 0.f);
+                sP[(c + q) * KX_GP_LD + rl] = t[q] * f4.x;
+                sP[(c + q + 1) * KX_GP_LD + rl] = t[q + 1] * f4.y;
+                sP[(c + q + 2) * KX_GP_LD + rl] = t[q + 2] * f4.z;
+                sP[(c + q + 3) * KX_GP_LD + rl] = t[q + 3] * f4.w;
+            }
         }
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     if (warp == 0)
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 64;" ::"r"(tmem) : "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 256;" ::"r"(tmem) : "memory");
+    if (!ok) return;
+    // column sums over the rows of each grid point i in the tile (four
+    // interleaved FP32 partial sums, combined pairwise)
+    const float *sP = reinterpret_cast<const float *>(kx_gsm);
+    const int segmax = kx_gain_segmax(n), i_first = (mt * 128) / n;
+    for (int col = tid; col < NTc; col += 128) {
+        const float *pc = sP + col * KX_GP_LD;
+        for (int sg = 0; sg < segmax; ++sg) {
+            const int i = i_first + sg;
+            if (i >= n) break;
+            const int r0 = max(mt * 128, i * n) - mt * 128, r1 = min(mt * 128 + 128, (i + 1) * n) - mt * 128;
+            if (r0 >= r1) break;
+            float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
+            int rr = r0;
+            for (; rr + 4 <= r1; rr += 4) {
+                a0 += pc[rr];
+                a1 += pc[rr + 1];
+                a2 += pc[rr + 2];
+                a3 += pc[rr + 3];
+            }
+            for (; rr < r1; ++rr) a0 += pc[rr];
+            Gp[(size_t)(mt * segmax + sg) * Bpad + (size_t)nt * KX_GN + col] = (a0 + a1) + (a2 + a3);
+        }
+    }
 }
 
 // ------------------------------------------------------------- exact loss
@@ -202,7 +251,7 @@ __global__ void __launch_bounds__(128)
 // ex2 and one FMA (weight): the element's own decode is a broadcast read of two
 // floats shared by the IPL instances.  Each segment's FP32 sums go into a
 // double-float accumulator (exact TwoSum), FP64 across warps.  The block also
-// forms the gain G_ib = sum_n f'_nb T_(i n) b from the GEMM output.  Rows are
+// adds up the gain G_ib from the fused GEMM's per-tile partials.  Rows are
 // taken longest first (lorder) so that the short ones fill the tail.
 __device__ __forceinline__ void kx_two_sum_f(float a, float b, float &s, float &e) {
     s = a + b;
@@ -215,8 +264,8 @@ __global__ void __launch_bounds__(WARPS * 32, (WARPS <= 16 && IPL <= 2) ? 2 : 1)
     k_batch_loss(int n, int B, int tds, int Bpad, const float2 *__restrict__ lel,
                  const int2 *__restrict__ lseg, const int *__restrict__ lsw,
                  const int *__restrict__ lorder, const float2 *__restrict__ td,
-                 const float *__restrict__ fT, const float *__restrict__ T,
-                 const double *__restrict__ fmax, double2 *__restrict__ partial,
+                 const float *__restrict__ Gp, const double *__restrict__ fmax,
+                 double2 *__restrict__ partial,
                  const kx_inst_state *__restrict__ st, int stage) {
     // [n][32][IPL] (l2_j, D_j) table; after the loss loop the same space holds
     // the cross-warp reduction [2][WARPS][32 IPL] doubles
@@ -248,17 +297,6 @@ __global__ void __launch_bounds__(WARPS * 32, (WARPS <= 16 && IPL <= 2) ? 2 : 1)
                 reinterpret_cast<float4 *>(kx_ltab)[(j * (IPL / 2) + h) * 32 + lane] =
                     make_float4(v[2 * h].x, v[2 * h].y, v[2 * h + 1].x, v[2 * h + 1].y);
         }
-    }
-    // the gain's loads go out together with the table's, before the barrier
-    float gs[IPL];
-#pragma unroll
-    for (int s = 0; s < IPL; ++s) gs[s] = 0.f;
-    for (int nn = warp; nn < n; nn += WARPS) {
-        const float *fr = fT + (size_t)nn * Bpad;
-        const float *tr = T + ((size_t)i * n + nn) * Bpad;
-#pragma unroll
-        for (int s = 0; s < IPL; ++s)
-            if (b[s] < B) gs[s] = fmaf(fr[b[s]], tr[b[s]], gs[s]);   // (Bpad rounds B to 64 only)
     }
     __syncthreads();
     // this warp's segments of row i (balanced across the warps by the host)
@@ -330,12 +368,9 @@ __global__ void __launch_bounds__(WARPS * 32, (WARPS <= 16 && IPL <= 2) ? 2 : 1)
         el1 = en1;
     }
     __syncthreads();   // every warp is done with the table
-    double *red = reinterpret_cast<double *>(kx_ltab);   // [2][WARPS][32 IPL]
+    double *red = reinterpret_cast<double *>(kx_ltab);   // [WARPS][32 IPL]
 #pragma unroll
-    for (int s = 0; s < IPL; ++s) {
-        red[warp * 32 * IPL + s * 32 + lane] = (double)hi[s] + (double)lo[s];
-        red[(WARPS + warp) * 32 * IPL + s * 32 + lane] = gs[s];
-    }
+    for (int s = 0; s < IPL; ++s) red[warp * 32 * IPL + s * 32 + lane] = (double)hi[s] + (double)lo[s];
     __syncthreads();
     if (warp < IPL) {
         const int s = warp;   // warp s finishes instance slot s
@@ -343,10 +378,11 @@ __global__ void __launch_bounds__(WARPS * 32, (WARPS <= 16 && IPL <= 2) ? 2 : 1)
         if (bb < B && !(st && (st[bb].done || (stage == 2 && st[bb].skip2)))) {
             double L = 0.0, G = 0.0;
 #pragma unroll
-            for (int w = 0; w < WARPS; ++w) {
-                L += red[w * 32 * IPL + s * 32 + lane];
-                G += red[(WARPS + w) * 32 * IPL + s * 32 + lane];
-            }
+            for (int w = 0; w < WARPS; ++w) L += red[w * 32 * IPL + s * 32 + lane];
+            // the gain of row i: the GEMM tiles' partials over the rows (i, a)
+            const int segmax = 128 / n + 2;
+            for (int mt = (i * n) / 128; mt <= (i * n + n - 1) / 128; ++mt)
+                G += (double)Gp[(size_t)(mt * segmax + i - (mt * 128) / n) * Bpad + bb];
             const double fm = fmax[bb];
             partial[(size_t)bb * n + i] = make_double2(fm * fm * G, fm * L);
         }
@@ -368,11 +404,11 @@ static kx_loss_shape kx_loss_shape_for(int n) {
 }
 // dynamic shared memory: the table, or the reduction if that is larger
 static size_t kx_loss_smem(int n, kx_loss_shape sh) {
-    return std::max((size_t)n, (size_t)2 * sh.warps) * 32 * sh.ipl * sizeof(float2);
+    return std::max((size_t)n, (size_t)sh.warps) * 32 * sh.ipl * sizeof(float2);
 }
 
 void kx_batch_prepare() {
-    cudaFuncSetAttribute(k_gain_mma, cudaFuncAttributeMaxDynamicSharedMemorySize, KX_GEMM_SMEM);
+    cudaFuncSetAttribute(k_gain_fused, cudaFuncAttributeMaxDynamicSharedMemorySize, KX_GAIN_SMEM);
     cudaFuncSetAttribute(k_batch_loss<2, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)kx_loss_smem(200, {2, 16}));
     cudaFuncSetAttribute(k_batch_loss<2, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -385,9 +421,9 @@ void kx_batch_prepare() {
 cudaError_t kx_launch_batch_contract(const kx_kernel *k, int B, const kx_batch_views &v,
                                      const kx_inst_state *st, int stage, int *d_err,
                                      cudaStream_t s) {
-    const int KB = k->Kpad / 32, MT = k->Mpad / 128, NT = v.Bpad / KX_MMA_NT;
+    const int KB = k->Kpad / 32, MT = k->Mpad / 128, NT = (v.Bpad + KX_GN - 1) / KX_GN;
     dim3 g1(NT, MT);
-    k_gain_mma<<<g1, 128, KX_GEMM_SMEM, s>>>(k->d_Atile, v.bt, v.T, KB, v.Bpad, d_err);
+    k_gain_fused<<<g1, 128, KX_GAIN_SMEM, s>>>(k->d_Atile, v.bt, v.fT, v.Gp, KB, k->n, v.Bpad, d_err);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     const kx_loss_shape sh = kx_loss_shape_for(k->n);
@@ -396,13 +432,13 @@ cudaError_t kx_launch_batch_contract(const kx_kernel *k, int B, const kx_batch_v
     const size_t smem = kx_loss_smem(k->n, sh);
     if (sh.ipl == 2 && sh.warps == 16)
         k_batch_loss<2, 16><<<g2, 512, smem, s>>>(k->n, B, v.B, v.Bpad, k->d_lel, k->d_lseg, k->d_lsw,
-                                                  k->d_lorder, v.td, v.fT, v.T, v.fmax, v.partial, st, stage);
+                                                  k->d_lorder, v.td, v.Gp, v.fmax, v.partial, st, stage);
     else if (sh.ipl == 2)
         k_batch_loss<2, 32><<<g2, 1024, smem, s>>>(k->n, B, v.B, v.Bpad, k->d_lel, k->d_lseg, k->d_lsw,
-                                                   k->d_lorder, v.td, v.fT, v.T, v.fmax, v.partial, st, stage);
+                                                   k->d_lorder, v.td, v.Gp, v.fmax, v.partial, st, stage);
     else
         k_batch_loss<1, 32><<<g2, 1024, smem, s>>>(k->n, B, v.B, v.Bpad, k->d_lel, k->d_lseg, k->d_lsw,
-                                                   k->d_lorder, v.td, v.fT, v.T, v.fmax, v.partial, st, stage);
+                                                   k->d_lorder, v.td, v.Gp, v.fmax, v.partial, st, stage);
     return cudaGetLastError();
 }
 

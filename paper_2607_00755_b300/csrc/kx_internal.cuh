@@ -138,7 +138,8 @@ struct kx_batch_views {
     // batched (split TF32) path
     float *bt;             // [Bpad/64][Kpad/32][hi, lo][2048]: f/f_max as TF32 hi/lo MMA operand tiles
     float *fT;             // [Kpad][Bpad]: f/f_max, instance-minor
-    float *T;              // [Mpad][Bpad]: T = W_full F (tensor-core product)
+    float *Gp;             // [Mpad/128][128/n + 2][Bpad]: gain partials per (GEMM row tile, grid
+                           //   point i in the tile, instance)
     int *err;              // tensor-core stage timeout flag (bounded waits)
     int B;                 // instances the views were carved for (td's stride on the split path)
     int Bpad;

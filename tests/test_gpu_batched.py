@@ -35,7 +35,9 @@ def oracle_rows(q, f, sigma, project):
     return np.array(out)
 
 
-@pytest.mark.parametrize("N,B", [(20, 1), (48, 3), (64, 70), (100, 5)])
+# B covers every gain-GEMM tile width: 64 (B <= 64), 128, 192, 256 and two
+# column tiles (256 + 64)
+@pytest.mark.parametrize("N,B", [(20, 1), (48, 3), (64, 70), (100, 5), (32, 190), (24, 256), (40, 300)])
 def test_batched_collision_matches_oracle(env, N, B):
     kx, ctx, torch = env
     rng = np.random.default_rng(300 + N)
@@ -55,16 +57,17 @@ def test_batched_collision_matches_oracle(env, N, B):
     k.release()
 
 
-def test_batched_alone_equals_in_batch(env):
+@pytest.mark.parametrize("B,picks", [(67, (0, 5, 63, 64, 66)), (300, (0, 255, 256, 299))])
+def test_batched_alone_equals_in_batch(env, B, picks):
     kx, ctx, torch = env
     N = 40
     q = ki.log_grid(N, 1e-3, 1e2)
-    f = ki.batch_bimodal(np.random.default_rng(31), q, 67)
-    sig = np.linspace(0.5, 2.0, 67)
+    f = ki.batch_bimodal(np.random.default_rng(31), q, B)
+    sig = np.linspace(0.5, 2.0, B)
     k = ctx.build_kernel(q, precision=kx.SPLIT_TF32)
     Cb, _ = ctx.collision(k, torch.as_tensor(f, device="cuda"), sig)
     Cb = Cb.cpu().numpy()
-    for b in (0, 5, 63, 64, 66):
+    for b in picks:
         Ca, _ = ctx.collision(k, torch.as_tensor(f[b:b + 1], device="cuda"), sig[b:b + 1])
         np.testing.assert_array_equal(Ca.cpu().numpy()[0], Cb[b])
     k.release()
