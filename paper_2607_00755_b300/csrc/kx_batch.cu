@@ -17,8 +17,8 @@
 
 #include "kx_internal.cuh"
 
-#define KX_ATILE 4096              // floats per A tile: 128 rows x 32 k
-#define KX_BTILE 2048              // floats per B tile: 64 rows x 32 k
+#define KX_ATILE (128 * KX_TILE_K)   // floats per A tile: 128 rows x 16 k
+#define KX_BTILE (64 * KX_TILE_K)    // floats per B tile: 64 rows x 16 k
 #define KX_SEG 64                  // elements per loss segment at most (one j_L)
 
 #include "kx_ptx.cuh"
@@ -72,42 +72,48 @@ __device__ __forceinline__ float kx_ex2f(float x) {
 }
 // --------------------------------------------------------- gain GEMM (fused)
 // One CTA (4 warps) per (128-row M tile of W_full, N tile of up to 256
-// instances).  Thread 0 stages the hi/lo operand tiles of each 32-wide k block
-// with bulk copies into a two-stage ring (mbarrier transaction counts: the A
-// tile and up to four 64-instance B tiles, which form one 256-row K-major
-// operand), issues the 3 x 4 MMAs of the block (M = 128, N = NTc, K = 8 each)
-// and commits them to the stage's completion barrier.  The accumulator
+// instances), two CTAs per SM.  Thread 0 stages the hi/lo operand tiles of each
+// 16-wide k block with bulk copies into a two-stage ring (mbarrier transaction
+// counts: the A tile and up to four 64-instance B tiles, which form one 256-row
+// K-major operand), issues the 3 x 2 MMAs of the block (M = 128, N = NTc,
+// K = 8 each) and commits them to the stage's completion barrier.  The accumulator
 // (128 lanes x NTc FP32 columns of tensor memory) holds T = W_full F for the
 // tile's rows (i, a); the epilogue forms the gain directly: each thread
 // multiplies its row's T by f'_a (instance-minor f/f_max) into a shared-memory
-// product matrix, and each column (instance) is summed over the rows of every
-// grid point i the tile touches, giving one FP32 partial per (tile, i, instance):
+// product matrix (128 instance columns at a time), and each column is summed
+// over the rows of every grid point i the tile touches, giving one FP32 partial
+// per (tile, i, instance):
 //   Gp[(mt * segmax + i - i_first(mt)) * Bpad + b] = sum_{a in tile} f'_ab T_(i a) b,
 // i_first(mt) = floor(128 mt / n).  T itself never reaches global memory.
 #define KX_GN 256
-#define KX_GSTAGE (2 * KX_ATILE * 4 + 2 * 4 * KX_BTILE * 4)   // A hi/lo 32 KB + B hi/lo 64 KB
-#define KX_GAIN_SMEM (2 * KX_GSTAGE + 64)
-#define KX_GP_LD 129                                          // product matrix: [col][128 rows + 1]
-static_assert(KX_GN * KX_GP_LD * 4 <= 2 * KX_GSTAGE, "product matrix must fit in the stage buffers");
+#define KX_GSTAGE (2 * KX_ATILE * 4 + 2 * 4 * KX_BTILE * 4)   // A hi/lo 16 KB + B hi/lo 32 KB
+#define KX_GAIN_SMEM(S) ((S) * KX_GSTAGE + 128)
+#define KX_GP_LD 129                                          // product matrix: [128 cols][128 rows + 1]
+static_assert(128 * KX_GP_LD * 4 <= 2 * KX_GSTAGE, "product matrix must fit in the stage buffers");
 
 __host__ __device__ __forceinline__ int kx_gain_segmax(int n) { return 128 / n + 2; }
 
-__global__ void __launch_bounds__(128, 1)
+// S: stages of the copy ring.  Two stages and two CTAs per SM (one CTA's
+// epilogue and copy waits overlap the other's MMAs) measured faster than four
+// stages and one CTA per SM (0.273 vs 0.300 ms for the N = 192, B = 512
+// contraction).
+template <int S>
+__global__ void __launch_bounds__(128, S == 2 ? 2 : 1)
     k_gain_fused(const float *__restrict__ A, const float *__restrict__ Bt,
                  const float *__restrict__ fT, float *__restrict__ Gp, int KB, int n, int Bpad,
                  int *err) {
     extern __shared__ __align__(1024) unsigned char kx_gsm[];
-    uint64_t *bars = reinterpret_cast<uint64_t *>(kx_gsm + 2 * KX_GSTAGE);   // full[2], done[2]
-    uint32_t *slot = reinterpret_cast<uint32_t *>(kx_gsm + 2 * KX_GSTAGE + 32);
-    int *okf = reinterpret_cast<int *>(kx_gsm + 2 * KX_GSTAGE + 40);
+    uint64_t *bars = reinterpret_cast<uint64_t *>(kx_gsm + S * KX_GSTAGE);   // full[S], done[S]
+    uint32_t *slot = reinterpret_cast<uint32_t *>(kx_gsm + S * KX_GSTAGE + 16 * S);
+    int *okf = reinterpret_cast<int *>(kx_gsm + S * KX_GSTAGE + 16 * S + 8);
     const int nt = blockIdx.x, mt = blockIdx.y;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int NTc = min(KX_GN, Bpad - nt * KX_GN);   // 64, 128, 192 or 256
     const int nsub = NTc >> 6;
     const float *Ab = A + (size_t)mt * KB * 2 * KX_ATILE;
-    const uint32_t full0 = kx_smem_u32(&bars[0]), done0 = kx_smem_u32(&bars[2]);
+    const uint32_t full0 = kx_smem_u32(&bars[0]), done0 = kx_smem_u32(&bars[S]);
     if (tid == 0) {
-        for (int k = 0; k < 4; ++k) kx_mbar_init(kx_smem_u32(&bars[k]), 1);
+        for (int k = 0; k < 2 * S; ++k) kx_mbar_init(kx_smem_u32(&bars[k]), 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         *okf = 1;
     }
@@ -141,19 +147,22 @@ __global__ void __launch_bounds__(128, 1)
             }
             issued = kb + 1;
         };
-        load(0, 0);
+        // blocks 0 .. S - 2 in flight before the first MMA; iteration kb refills
+        // the stage of block kb - 1 with block kb + S - 1
+        for (int kb = 0; kb < S - 1 && kb < KB; ++kb) load(kb, kb);
         int committed = 0;  // k blocks whose MMAs were committed
         for (int kb = 0; kb < KB; ++kb) {
-            const int s = kb & 1;
-            if (kb + 1 < KB) {
+            const int s = kb % S;
+            if (kb + S - 1 < KB) {
+                const int sr = (kb + S - 1) % S;
                 // the stage about to be refilled was read by the MMAs of block kb - 1
-                if (kb >= 1 && !kx_mbar_wait(done0 + 8 * (s ^ 1), ((kb - 1) >> 1) & 1)) {
+                if (kb >= 1 && !kx_mbar_wait(done0 + 8 * sr, ((kb - 1) / S) & 1)) {
                     ok = 0;
                     break;
                 }
-                load(kb + 1, s ^ 1);
+                load(kb + S - 1, sr);
             }
-            if (!kx_mbar_wait(full0 + 8 * s, (kb >> 1) & 1)) {
+            if (!kx_mbar_wait(full0 + 8 * s, (kb / S) & 1)) {
                 ok = 0;
                 break;
             }
@@ -161,23 +170,23 @@ __global__ void __launch_bounds__(128, 1)
             const uint32_t aH = kx_smem_u32(stage_a(s)), aL = aH + KX_ATILE * 4;
             const uint32_t bH = kx_smem_u32(stage_b(s)), bL = bH + 4 * KX_BTILE * 4;
 #pragma unroll
-            for (int step = 0; step < 4; ++step) {
+            for (int step = 0; step < KX_TILE_K / 8; ++step) {
                 const uint32_t o = 256u * step;   // 8 TF32 = two 16-byte core-matrix columns
-                kx_mma_tf32(tmem, kx_desc(aH + o, 128, 1024), kx_desc(bH + o, 128, 1024), idesc,
+                kx_mma_tf32(tmem, kx_desc(aH + o, 128, 512), kx_desc(bH + o, 128, 512), idesc,
                             (kb | step) ? 1u : 0u);
-                kx_mma_tf32(tmem, kx_desc(aH + o, 128, 1024), kx_desc(bL + o, 128, 1024), idesc, 1u);
-                kx_mma_tf32(tmem, kx_desc(aL + o, 128, 1024), kx_desc(bH + o, 128, 1024), idesc, 1u);
+                kx_mma_tf32(tmem, kx_desc(aH + o, 128, 512), kx_desc(bL + o, 128, 512), idesc, 1u);
+                kx_mma_tf32(tmem, kx_desc(aL + o, 128, 512), kx_desc(bH + o, 128, 512), idesc, 1u);
             }
             kx_mma_commit(done0 + 8 * s);
             committed = kb + 1;
         }
-        if (ok && !kx_mbar_wait(done0 + 8 * ((KB - 1) & 1), ((KB - 1) >> 1) & 1)) ok = 0;
+        if (ok && !kx_mbar_wait(done0 + 8 * ((KB - 1) % S), ((KB - 1) / S) & 1)) ok = 0;
         if (!ok) {
             // give outstanding copies and MMAs a bounded chance to land before the
             // shared memory and tensor memory are released
-            for (int kb = committed; kb < issued; ++kb) kx_mbar_wait(full0 + 8 * (kb & 1), (kb >> 1) & 1);
+            for (int kb = committed; kb < issued; ++kb) kx_mbar_wait(full0 + 8 * (kb % S), (kb / S) & 1);
             if (committed > 0)
-                kx_mbar_wait(done0 + 8 * ((committed - 1) & 1), ((committed - 1) >> 1) & 1);
+                kx_mbar_wait(done0 + 8 * ((committed - 1) % S), ((committed - 1) / S) & 1);
             *okf = 0;
             atomicExch(err, 1);
         }
@@ -186,55 +195,57 @@ __global__ void __launch_bounds__(128, 1)
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const bool ok = *okf != 0;
     const int nrows = n * n;
-    if (ok) {
-        // products f'_ab T_(i a) b into sP[col][row] (the stage buffers are free:
-        // every copy landed and every MMA completed)
-        float *sP = reinterpret_cast<float *>(kx_gsm);
-        const int rl = warp * 32 + lane, r = mt * 128 + rl;
-        const bool rin = r < nrows;
-        const float *frow = fT + (size_t)(rin ? r % n : 0) * Bpad + (size_t)nt * KX_GN;
-        for (int c = 0; c < NTc; c += 16) {
-            float t[16];
-            kx_tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c, t);
+    const int rl = warp * 32 + lane, r = mt * 128 + rl;
+    const bool rin = r < nrows;
+    const float *frow = fT + (size_t)(rin ? r % n : 0) * Bpad + (size_t)nt * KX_GN;
+    float *sP = reinterpret_cast<float *>(kx_gsm);   // free: every copy landed, every MMA completed
+    const int segmax = kx_gain_segmax(n), i_first = (mt * 128) / n;
+    for (int h0 = 0; h0 < NTc; h0 += 128) {
+        const int hw = min(128, NTc - h0);
+        if (ok) {
+            // products f'_ab T_(i a) b of columns h0 .. h0 + hw - 1 into sP[col][row]
+            for (int c = 0; c < hw; c += 16) {
+                float t[16];
+                kx_tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(h0 + c), t);
 #pragma unroll
-            for (int q = 0; q < 16; q += 4) {
-                const float4 f4 = rin ? __ldg(reinterpret_cast<const float4 *>(frow + c + q))
-                                      : make_float4(0.f, 0.f, 0.f, 0.f);
-                sP[(c + q) * KX_GP_LD + rl] = t[q] * f4.x;
-                sP[(c + q + 1) * KX_GP_LD + rl] = t[q + 1] * f4.y;
-                sP[(c + q + 2) * KX_GP_LD + rl] = t[q + 2] * f4.z;
-                sP[(c + q + 3) * KX_GP_LD + rl] = t[q + 3] * f4.w;
+                for (int q = 0; q < 16; q += 4) {
+                    const float4 f4 = rin ? __ldg(reinterpret_cast<const float4 *>(frow + h0 + c + q))
+                                          : make_float4(0.f, 0.f, 0.f, 0.f);
+                    sP[(c + q) * KX_GP_LD + rl] = t[q] * f4.x;
+                    sP[(c + q + 1) * KX_GP_LD + rl] = t[q + 1] * f4.y;
+                    sP[(c + q + 2) * KX_GP_LD + rl] = t[q + 2] * f4.z;
+                    sP[(c + q + 3) * KX_GP_LD + rl] = t[q + 3] * f4.w;
+                }
             }
         }
+        __syncthreads();
+        // column sums over the rows of each grid point i in the tile (four
+        // interleaved FP32 partial sums, combined pairwise)
+        if (ok && tid < hw) {
+            const float *pc = sP + tid * KX_GP_LD;
+            for (int sg = 0; sg < segmax; ++sg) {
+                const int i = i_first + sg;
+                if (i >= n) break;
+                const int r0 = max(mt * 128, i * n) - mt * 128, r1 = min(mt * 128 + 128, (i + 1) * n) - mt * 128;
+                if (r0 >= r1) break;
+                float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
+                int rr = r0;
+                for (; rr + 4 <= r1; rr += 4) {
+                    a0 += pc[rr];
+                    a1 += pc[rr + 1];
+                    a2 += pc[rr + 2];
+                    a3 += pc[rr + 3];
+                }
+                for (; rr < r1; ++rr) a0 += pc[rr];
+                Gp[(size_t)(mt * segmax + sg) * Bpad + (size_t)nt * KX_GN + h0 + tid] = (a0 + a1) + (a2 + a3);
+            }
+        }
+        __syncthreads();   // sP is refilled by the next half
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     if (warp == 0)
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 256;" ::"r"(tmem) : "memory");
-    if (!ok) return;
-    // column sums over the rows of each grid point i in the tile (four
-    // interleaved FP32 partial sums, combined pairwise)
-    const float *sP = reinterpret_cast<const float *>(kx_gsm);
-    const int segmax = kx_gain_segmax(n), i_first = (mt * 128) / n;
-    for (int col = tid; col < NTc; col += 128) {
-        const float *pc = sP + col * KX_GP_LD;
-        for (int sg = 0; sg < segmax; ++sg) {
-            const int i = i_first + sg;
-            if (i >= n) break;
-            const int r0 = max(mt * 128, i * n) - mt * 128, r1 = min(mt * 128 + 128, (i + 1) * n) - mt * 128;
-            if (r0 >= r1) break;
-            float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
-            int rr = r0;
-            for (; rr + 4 <= r1; rr += 4) {
-                a0 += pc[rr];
-                a1 += pc[rr + 1];
-                a2 += pc[rr + 2];
-                a3 += pc[rr + 3];
-            }
-            for (; rr < r1; ++rr) a0 += pc[rr];
-            Gp[(size_t)(mt * segmax + sg) * Bpad + (size_t)nt * KX_GN + col] = (a0 + a1) + (a2 + a3);
-        }
-    }
 }
 
 // ------------------------------------------------------------- exact loss
@@ -408,7 +419,7 @@ static size_t kx_loss_smem(int n, kx_loss_shape sh) {
 }
 
 void kx_batch_prepare() {
-    cudaFuncSetAttribute(k_gain_fused, cudaFuncAttributeMaxDynamicSharedMemorySize, KX_GAIN_SMEM);
+    cudaFuncSetAttribute(k_gain_fused<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, KX_GAIN_SMEM(2));
     cudaFuncSetAttribute(k_batch_loss<2, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)kx_loss_smem(200, {2, 16}));
     cudaFuncSetAttribute(k_batch_loss<2, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -421,9 +432,9 @@ void kx_batch_prepare() {
 cudaError_t kx_launch_batch_contract(const kx_kernel *k, int B, const kx_batch_views &v,
                                      const kx_inst_state *st, int stage, int *d_err,
                                      cudaStream_t s) {
-    const int KB = k->Kpad / 32, MT = k->Mpad / 128, NT = (v.Bpad + KX_GN - 1) / KX_GN;
+    const int KB = k->Kpad / KX_TILE_K, MT = k->Mpad / 128, NT = (v.Bpad + KX_GN - 1) / KX_GN;
     dim3 g1(NT, MT);
-    k_gain_fused<<<g1, 128, KX_GAIN_SMEM, s>>>(k->d_Atile, v.bt, v.fT, v.Gp, KB, k->n, v.Bpad, d_err);
+    k_gain_fused<2><<<g1, 128, KX_GAIN_SMEM(2), s>>>(k->d_Atile, v.bt, v.fT, v.Gp, KB, k->n, v.Bpad, d_err);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     const kx_loss_shape sh = kx_loss_shape_for(k->n);
@@ -475,7 +486,7 @@ int kx_batch_build_tables(kx_ctx *ctx, kx_kernel *k) {
         return kx_set_error(ctx, KX_ECUDA, "batched build: table download failed");
     k->Mpad = ((n * n + 127) / 128) * 128;
     k->Kpad = ((n + 31) / 32) * 32;
-    const int MT = k->Mpad / 128, KB = k->Kpad / 32;
+    const int MT = k->Mpad / 128, KB = k->Kpad / KX_TILE_K;
     std::vector<float> At((size_t)MT * KB * 2 * KX_ATILE, 0.f);
     std::vector<float2> lel;
     std::vector<int2> lseg;
@@ -503,7 +514,7 @@ int kx_batch_build_tables(kx_ctx *ctx, kx_kernel *k) {
                 const float wh = kx_tf32_round(w);
                 const float wl = w - wh;
                 const int r = i * n + a;
-                const int mt = r / 128, rl = r % 128, kb = b / 32, kk = b % 32;
+                const int mt = r / 128, rl = r % 128, kb = b / KX_TILE_K, kk = b % KX_TILE_K;
                 const size_t t = ((size_t)mt * KB + kb) * 2;
                 At[t * KX_ATILE + kx_tile_offset(rl, kk)] = wh;
                 At[(t + 1) * KX_ATILE + kx_tile_offset(rl, kk)] = wl;

@@ -360,11 +360,11 @@ __device__ __forceinline__ int kx_prep_block(int n, int path, double x, double E
         uint32_t hb;
         asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(hb) : "f"(fp));
         const float hi = __uint_as_float(hb);
-        const int KB = blockDim.x >> 5;   // blockDim = n rounded up to 32 = padded k extent
-        const size_t t = ((size_t)(b >> 6) * KB + (i >> 5)) * 2;
-        const int off = kx_tile_offset(b & 63, i & 31);
-        v.bt[t * 2048 + off] = hi;
-        v.bt[(t + 1) * 2048 + off] = fp - hi;
+        const int KB = blockDim.x / KX_TILE_K;   // blockDim = n rounded up to 32 = padded k extent
+        const size_t t = ((size_t)(b >> 6) * KB + i / KX_TILE_K) * 2;
+        const int off = kx_tile_offset(b & 63, i % KX_TILE_K);
+        v.bt[t * (64 * KX_TILE_K) + off] = hi;
+        v.bt[(t + 1) * (64 * KX_TILE_K) + off] = fp - hi;
         return bad;
     }
     float2 *tl = v.tl + (long long)b * (n + 4);

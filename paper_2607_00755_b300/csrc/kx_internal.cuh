@@ -61,7 +61,7 @@ struct kx_kernel {
     // batched (split TF32) tables
     int Mpad;            // n^2 rows (i, n) padded to a multiple of 128
     int Kpad;            // n columns (m) padded to a multiple of 32
-    float *d_Atile;      // [Mpad/128][Kpad/32][hi, lo][4096]: W_full as TF32 hi/lo in MMA operand tiles
+    float *d_Atile;      // [Mpad/128][Kpad/16][hi, lo][2048]: W_full as TF32 hi/lo in MMA operand tiles
     float2 *d_lel;       // per row i: nonzero (S_inm, omega) sorted by j_L
     int2 *d_lseg;        // segments of <= 32 elements of one j_L: (first element, j_L << 8 | count)
     int *d_lsw;          // [n * warps + 1] first segment of each (row, loss-kernel warp)
@@ -136,7 +136,7 @@ struct kx_batch_views {
     kx_diag *diag;         // [B]
     int chunks;            // partials per row (FP32 path: partial slots per instance)
     // batched (split TF32) path
-    float *bt;             // [Bpad/64][Kpad/32][hi, lo][2048]: f/f_max as TF32 hi/lo MMA operand tiles
+    float *bt;             // [Bpad/64][Kpad/16][hi, lo][1024]: f/f_max as TF32 hi/lo MMA operand tiles
     float *fT;             // [Kpad][Bpad]: f/f_max, instance-minor
     float *Gp;             // [Mpad/128][128/n + 2][Bpad]: gain partials per (GEMM row tile, grid
                            //   point i in the tile, instance)
@@ -146,13 +146,14 @@ struct kx_batch_views {
 };
 
 // The MMA operand tile layout (K-major, no swizzle, 8-row x 16-byte core
-// matrices): element (row r, k) of a 128-row (A) or 64-row (B) tile with 32
+// matrices): element (row r, k) of a 128-row (A) or 64-row (B) tile with 16
 // TF32 values of k per row sits at float offset
-//   (r / 8) * 256 + (k / 4) * 32 + (r % 8) * 4 + (k % 4),
+//   (r / 8) * 128 + (k / 4) * 32 + (r % 8) * 4 + (k % 4),
 // i.e. leading-dimension (k) stride 128 B between core matrices and
-// stride-dimension (row) stride 1024 B between 8-row groups.
+// stride-dimension (row) stride 512 B between 8-row groups.
+#define KX_TILE_K 16
 __host__ __device__ __forceinline__ int kx_tile_offset(int r, int k) {
-    return (r >> 3) * 256 + (k >> 2) * 32 + (r & 7) * 4 + (k & 3);
+    return (r >> 3) * 128 + (k >> 2) * 32 + (r & 7) * 4 + (k & 3);
 }
 
 int kx_chunks_per_row(const kx_kernel *k);
