@@ -260,8 +260,9 @@ __global__ void __launch_bounds__(128, S == 2 ? 2 : 1)
 // flight meanwhile) into its shared-memory slot, reads its (l2_j, D_j) once,
 // and then per element and instance spends one FMA (interpolated exponent), one
 // ex2 and one FMA (weight): the element's own decode is a broadcast read of two
-// floats shared by the IPL instances.  Each segment's FP32 sums go into a
-// double-float accumulator (exact TwoSum), FP64 across warps.  The block also
+// floats shared by the IPL instances.  The FP32 sums (four per instance) go
+// into a double-float accumulator (exact TwoSum) after every 64 or more
+// elements, FP64 across warps.  The block also
 // adds up the gain G_ib from the fused GEMM's per-tile partials.  Rows are
 // taken longest first (lorder) so that the short ones fill the tail.
 __device__ __forceinline__ void kx_two_sum_f(float a, float b, float &s, float &e) {
@@ -313,9 +314,10 @@ __global__ void __launch_bounds__(WARPS * 32, (WARPS <= 16 && IPL <= 2) ? 2 : 1)
     // this warp's segments of row i (balanced across the warps by the host)
     const int gend = lsw[i * WARPS + warp + 1];
     int g = lsw[i * WARPS + warp];
-    float hi[IPL], lo[IPL];
+    float hi[IPL], lo[IPL], a[IPL][4];
 #pragma unroll
-    for (int s = 0; s < IPL; ++s) hi[s] = lo[s] = 0.f;
+    for (int s = 0; s < IPL; ++s) hi[s] = lo[s] = a[s][0] = a[s][1] = a[s][2] = a[s][3] = 0.f;
+    int na = 0;   // elements in the FP32 sums since the last flush
     // descriptors run two segments ahead of the compute, elements one
     int2 dsc = make_int2(0, 0), dn = dsc;
     float2 el0 = make_float2(0.f, 0.f), el1 = el0;
@@ -350,13 +352,13 @@ __global__ void __launch_bounds__(WARPS * 32, (WARPS <= 16 && IPL <= 2) ? 2 : 1)
                 t[2 * h + 1] = make_float2(q.z, q.w);
             }
         }
-        float a[IPL][4];
-#pragma unroll
-        for (int s = 0; s < IPL; ++s) a[s][0] = a[s][1] = a[s][2] = a[s][3] = 0.f;
-        const float4 *e4 = reinterpret_cast<const float4 *>(s_el[warp]);
+        // two elements (S, omega) per float4; a running pointer keeps the loop's
+        // address arithmetic to one add per four elements
+        const float4 *pe = reinterpret_cast<const float4 *>(s_el[warp]);
+        const float4 *const pend = pe + (c4 >> 1);
 #pragma unroll 2
-        for (int q = 0; q < c4; q += 4) {
-            const float4 x01 = e4[q >> 1], x23 = e4[(q >> 1) + 1];
+        for (; pe < pend; pe += 2) {
+            const float4 x01 = pe[0], x23 = pe[1];
 #pragma unroll
             for (int s = 0; s < IPL; ++s) {
                 a[s][0] = fmaf(x01.x, kx_ex2f(fmaf(x01.y, t[s].y, t[s].x)), a[s][0]);
@@ -365,18 +367,32 @@ __global__ void __launch_bounds__(WARPS * 32, (WARPS <= 16 && IPL <= 2) ? 2 : 1)
                 a[s][3] = fmaf(x23.z, kx_ex2f(fmaf(x23.w, t[s].y, t[s].x)), a[s][3]);
             }
         }
+        // the FP32 sums go into the double-float accumulator once they hold at
+        // least 64 elements (short segments share a flush), and at the end
+        na += c4;
+        if (na >= KX_SEG) {
 #pragma unroll
-        for (int s = 0; s < IPL; ++s) {
-            float sm, er;
-            kx_two_sum_f(hi[s], (a[s][0] + a[s][1]) + (a[s][2] + a[s][3]), sm, er);
-            hi[s] = sm;
-            lo[s] += er;
+            for (int s = 0; s < IPL; ++s) {
+                float sm, er;
+                kx_two_sum_f(hi[s], (a[s][0] + a[s][1]) + (a[s][2] + a[s][3]), sm, er);
+                hi[s] = sm;
+                lo[s] += er;
+                a[s][0] = a[s][1] = a[s][2] = a[s][3] = 0.f;
+            }
+            na = 0;
         }
         __syncwarp();   // the slot is refilled next segment
         dsc = dn;
         dn = dnn;
         el0 = en0;
         el1 = en1;
+    }
+#pragma unroll
+    for (int s = 0; s < IPL; ++s) {
+        float sm, er;
+        kx_two_sum_f(hi[s], (a[s][0] + a[s][1]) + (a[s][2] + a[s][3]), sm, er);
+        hi[s] = sm;
+        lo[s] += er;
     }
     __syncthreads();   // every warp is done with the table
     double *red = reinterpret_cast<double *>(kx_ltab);   // [WARPS][32 IPL]
