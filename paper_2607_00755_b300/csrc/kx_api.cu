@@ -739,7 +739,7 @@ static int kx_collect(kx_ctx *ctx, const kx_kernel *k, int B, const kx_run &r, k
     cudaStream_t s = ctx->stream;
     std::vector<kx_inst_state> st(B);
     std::vector<double> mb(3 * B);
-    KX_CUDA_TRY(ctx, kx_launch_mbfit(k, B, r.sv.f, r.mb, s));
+    KX_CUDA_TRY(ctx, kx_launch_mbfit(k, B, r.sv.f, r.mb, s, r.sv.st, nullptr));
     ctx->launches += 1;
     KX_CUDA_TRY(ctx, cudaMemcpyAsync(st.data(), r.sv.st, sizeof(kx_inst_state) * B, cudaMemcpyDeviceToHost, s));
     KX_CUDA_TRY(ctx, cudaMemcpyAsync(mb.data(), r.mb, sizeof(double) * 3 * B, cudaMemcpyDeviceToHost, s));

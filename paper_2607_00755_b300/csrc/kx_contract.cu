@@ -1420,15 +1420,19 @@ __device__ __forceinline__ void kx_mb_fit_block(int n, double fi, double Ei, dou
     out[2] = s2[0] / N0;
 }
 
+// Block b fits instance idx[b] (b when idx is null).  With a state, the last
+// in-solve fit's temperature starts the Newton iteration.
 __global__ void __launch_bounds__(KX_FIN_THREADS)
     k_mbfit(int n, const double *__restrict__ f, const double *__restrict__ E,
-            const double *__restrict__ h, double *__restrict__ out3) {
+            const double *__restrict__ h, double *__restrict__ out3,
+            const kx_inst_state *__restrict__ st, const int *__restrict__ idx) {
     __shared__ double smem[4 * KX_FIN_THREADS + 8];
-    const int b = blockIdx.x, i = threadIdx.x;
+    const int b = idx ? idx[blockIdx.x] : blockIdx.x, i = threadIdx.x;
     double fi = i < n ? f[(long long)b * n + i] : 0.0;
     double Ei = i < n ? E[i] : 0.0, hi = i < n ? h[i] : 0.0;
+    const double Tg = st ? st[b].T : 0.0;
     double o[3];
-    kx_mb_fit_block(n, fi, Ei, hi, E[0], 0.0, o, smem);
+    kx_mb_fit_block(n, fi, Ei, hi, E[0], (Tg > 0.0 && Tg < INFINITY) ? Tg : 0.0, o, smem);
     if (threadIdx.x == 0) {
         out3[3 * b] = o[0];
         out3[3 * b + 1] = o[1];
@@ -1436,9 +1440,10 @@ __global__ void __launch_bounds__(KX_FIN_THREADS)
     }
 }
 
-cudaError_t kx_launch_mbfit(const kx_kernel *k, int B, const double *f, double *out3,
-                            cudaStream_t s) {
-    k_mbfit<<<B, kx_fin_threads(k->n), 0, s>>>(k->n, f, k->d_E, k->d_h, out3);
+cudaError_t kx_launch_mbfit(const kx_kernel *k, int nb, const double *f, double *out3,
+                            cudaStream_t s, const kx_inst_state *st, const int *idx) {
+    if (nb < 1) return cudaSuccess;
+    k_mbfit<<<nb, kx_fin_threads(k->n), 0, s>>>(k->n, f, k->d_E, k->d_h, out3, st, idx);
     return cudaGetLastError();
 }
 

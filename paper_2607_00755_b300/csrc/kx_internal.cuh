@@ -202,8 +202,10 @@ struct kx_step_views {
 };
 cudaError_t kx_launch_stage(const kx_kernel *k, int B, const kx_batch_views &v,
                             const kx_step_views &sv, int stage, cudaStream_t s, bool pdl = false);
-cudaError_t kx_launch_mbfit(const kx_kernel *k, int B, const double *f, double *out3,
-                            cudaStream_t s);
+// MB fit of nb instances: block b fits instance idx[b] (b when idx is null);
+// st (nullable) gives each instance's last in-solve temperature as the start.
+cudaError_t kx_launch_mbfit(const kx_kernel *k, int nb, const double *f, double *out3,
+                            cudaStream_t s, const kx_inst_state *st = nullptr, const int *idx = nullptr);
 
 // batched split-TF32 path (kx_batch.cu)
 int kx_batch_build_tables(kx_ctx *ctx, kx_kernel *k);   // after the FP64 build

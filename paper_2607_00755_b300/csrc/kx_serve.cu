@@ -55,6 +55,7 @@ struct Group {
     kx_batch_views v;
     kx_step_views sv;
     double *mb = nullptr;
+    int *fin = nullptr;      // [cap] slots to fit on completion
     double *shapes = nullptr;
     kx_src_dev *src = nullptr;
     std::vector<std::shared_ptr<Request>> slot;
@@ -126,7 +127,8 @@ static size_t kx_group_estimate(const kx_server_config &cfg, int n) {
     const int cap = cfg.slots_per_group;
     size_t mem = kx_al(kx_views_bytes(&d, cap)) + 3 * kx_al(sizeof(double) * cap * n) +
                  kx_al(sizeof(kx_inst_state) * cap) + kx_al(sizeof(kx_src_dev) * cap) +
-                 kx_al(sizeof(double) * cap * KX_MAX_SRC * n) + kx_al(sizeof(double) * 3 * cap);
+                 kx_al(sizeof(double) * cap * KX_MAX_SRC * n) + kx_al(sizeof(double) * 3 * cap) +
+                 kx_al(sizeof(int) * cap);
     return tables + mem + 5 * n * 8;
 }
 
@@ -183,6 +185,7 @@ static int kx_make_group(kx_server *srv, const Request &r, Group **out) {
     const size_t o_src = o; o += kx_al(sizeof(kx_src_dev) * cap);
     const size_t o_sh = o; o += kx_al(sizeof(double) * cap * KX_MAX_SRC * n);
     const size_t o_mb = o; o += kx_al(sizeof(double) * 3 * cap);
+    const size_t o_fin = o; o += kx_al(sizeof(int) * cap);
     g->mem_bytes = o;
     if (cudaMalloc(&g->mem, o) != cudaSuccess) {
         cudaGetLastError();
@@ -201,6 +204,7 @@ static int kx_make_group(kx_server *srv, const Request &r, Group **out) {
     sv.src = g->src;
     sv.shapes = g->shapes;
     g->mb = (double *)(base + o_mb);
+    g->fin = (int *)(base + o_fin);
     const kx_solve_params &p = srv->cfg.par;
     sv.rtol = p.rtol;
     sv.atol = p.atol;
@@ -308,7 +312,11 @@ static void kx_complete(kx_server *srv, Group *g) {
     if (fin.empty()) return;
     const int n = g->n;
     std::vector<double> f((size_t)g->cap * n), mb((size_t)3 * g->cap);
-    cudaError_t e = kx_launch_mbfit(g->k, g->cap, g->sv.f, g->mb, g->stream);
+    // fit only the finished slots (from their last in-solve fit's temperature)
+    cudaError_t e = cudaMemcpyAsync(g->fin, fin.data(), sizeof(int) * fin.size(), cudaMemcpyHostToDevice,
+                                    g->stream);
+    if (e == cudaSuccess)
+        e = kx_launch_mbfit(g->k, (int)fin.size(), g->sv.f, g->mb, g->stream, g->sv.st, g->fin);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(f.data(), g->sv.f, sizeof(double) * f.size(), cudaMemcpyDeviceToHost, g->stream);
     if (e == cudaSuccess)
