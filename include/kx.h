@@ -297,6 +297,32 @@ int kx_time_contraction(kx_ctx *ctx, const kx_kernel *k, int batch, const double
  * out_host[batch][3] = (T, ln z, L1) with L1 = sum h |f - f_MB| / sum h f. */
 int kx_mb_fit(kx_ctx *ctx, const kx_kernel *k, int batch, const double *f_dev, double *out_host);
 
+/* ------------------------------------------------ the paper's sources */
+/* The two freeze-in source terms of Sec. 2 as rows for kx_source (host
+ * functions, no device work).  q: host [n] comoving grid (ascending, > 0) and
+ * a the scale factor, as in kx_grid_desc (p_i = q_i / a); mass = m_chi.
+ * shape: host [n] out; rate: out, the row's number injection rate
+ * (sum_i h_i S_i with h_i = p_i^2 dp_i, the grid's weights), so that
+ * {shape, rate, tau, t_on} in kx_source reproduce the formula times the
+ * envelope.  KX_EINVAL for a bad grid or parameters.
+ *
+ * Higgs decay into dark matter (eq. C_higgs_decay):
+ *   S(p) = coupling^2 / (8 pi g_chi) * T / (E p) * (exp(-E_h^-(p)/T) - exp(-E_h^+(p)/T)),
+ *   E_h^(+/-) = (m_h^2 E +/- m_h p sqrt(m_h^2 - 4 m_chi^2)) / (2 m_chi^2),
+ * coupling = lambda_Hchi v, T the bath temperature (m_h > 2 m_chi, T > 0);
+ * shape = S(p_i), rate = sum_i h_i S(p_i). */
+int kx_source_higgs_decay(int n, const double *q, double a, double mass, double m_h, double T,
+                          double coupling, double g_chi, double *shape, double *rate);
+
+/* Decay of a cold condensate (eq. C_condensate_decay):
+ *   S(p) = (2 pi^2 / g_chi) gamma_n delta(p - p0) / p0^2,  p0 = sqrt(m_phi^2 - 4 m_chi^2) / 2,
+ * gamma_n = 2 Gamma_Phi n_Phi.  The delta function is binned into the one grid
+ * cell (trapezoid widths in q) containing a p0: shape = 1 there, 0 elsewhere,
+ * rate = (2 pi^2 / g_chi) gamma_n, the formula's number injection exactly.
+ * KX_EINVAL also when p0 lies outside the grid. */
+int kx_source_condensate(int n, const double *q, double a, double mass, double m_phi, double g_chi,
+                         double gamma_n, double *shape, double *rate);
+
 /* ----------------------------------------------------------- diagnostics */
 /* Self-check of the library's own table-driven FP64 log2 and exp (the stage
  * kernels use them for the per-point log of f, the source envelopes and the

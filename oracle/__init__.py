@@ -242,6 +242,30 @@ def source(h, t, shape, rate, tau, t_on):
     return S
 
 
+def higgs_decay_source(q, mass, m_h, T, coupling, g_chi=1.0, a=1.0):
+    """Higgs decay into dark matter, eq. C_higgs_decay (Sec. 2), at p = q / a:
+    coupling^2/(8 pi g) T/(E p) (exp(-E_h^-/T) - exp(-E_h^+/T)) with
+    E_h^(+/-) = (m_h^2 E +/- m_h p sqrt(m_h^2 - 4 m^2)) / (2 m^2)."""
+    p = _f64(q) / a
+    E = np.sqrt(p * p + mass * mass)
+    k = np.sqrt(m_h * m_h - 4.0 * mass * mass)
+    e_minus = (m_h * m_h * E - m_h * p * k) / (2.0 * mass * mass)
+    e_plus = (m_h * m_h * E + m_h * p * k) / (2.0 * mass * mass)
+    return coupling ** 2 / (8.0 * np.pi * g_chi) * T / (E * p) * (np.exp(-e_minus / T) - np.exp(-e_plus / T))
+
+
+def condensate_source_cell(q, mass, m_phi, a=1.0):
+    """Grid cell of the condensate's delta function, eq. C_condensate_decay:
+    p0 = sqrt(m_phi^2 - 4 m^2) / 2, cells = the trapezoid widths in q (edges at
+    the midpoints, the ends at q_0 and q_{n-1}); None outside the grid."""
+    q = _f64(q)
+    x = 0.5 * np.sqrt(m_phi * m_phi - 4.0 * mass * mass) * a
+    edges = np.concatenate(([q[0]], 0.5 * (q[1:] + q[:-1]), [q[-1]]))
+    if x < edges[0] or x > edges[-1]:
+        return None
+    return int(min(np.searchsorted(edges, x, side="right") - 1, q.size - 1))
+
+
 def mb_fit(E, h, f):
     E, h, f = _f64(E), _f64(h), _f64(f)
     out = np.empty(3)

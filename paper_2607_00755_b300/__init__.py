@@ -28,6 +28,7 @@ EXPORTS = (
     "kx_solve", "kx_solve_host", "kx_mb_fit", "kx_launch_count", "kx_time_contraction",
     "kx_collision_noalloc", "kx_server_start", "kx_submit", "kx_poll", "kx_server_get_stats",
     "kx_server_stop", "kx_math_check", "kx_set_stream_variant", "kx_get_stream_variant",
+    "kx_source_higgs_decay", "kx_source_condensate",
 )
 
 
@@ -127,6 +128,8 @@ def load_library(path: str = LIB_PATH):
         "kx_math_check": (i, [vp, i, i, vp, vp]),
         "kx_set_stream_variant": (i, [vp, i, i, i]),
         "kx_get_stream_variant": (i, [vp, i, i, vp, vp]),
+        "kx_source_higgs_decay": (i, [i, vp, d, d, d, d, d, d, vp, vp]),
+        "kx_source_condensate": (i, [i, vp, d, d, d, d, d, vp, vp]),
         "kx_launch_count": (ctypes.c_longlong, [vp]),
         "kx_time_contraction": (i, [vp, vp, i, vp, i, ctypes.c_longlong, vp]),
         "kx_collision_noalloc": (i, [vp, vp, i, vp, vp, vp, i]),
@@ -351,6 +354,32 @@ class Context:
             raise self.error(rc, "kx_math_check")
         torch.cuda.synchronize()
         return out
+
+
+def source_higgs_decay(q, mass, m_h, T, coupling, g_chi=1.0, a=1.0):
+    """Higgs-decay source row (eq. C_higgs_decay): (shape [n], rate)."""
+    lib = load_library()
+    q = _np(q)
+    shape = np.empty(q.size)
+    rate = ctypes.c_double()
+    rc = lib.kx_source_higgs_decay(q.size, _ptr(q), float(a), float(mass), float(m_h), float(T),
+                                   float(coupling), float(g_chi), _ptr(shape), ctypes.byref(rate))
+    if rc:
+        raise KxError(rc, "kx_source_higgs_decay")
+    return shape, rate.value
+
+
+def source_condensate(q, mass, m_phi, gamma_n, g_chi=1.0, a=1.0):
+    """Condensate-decay source row (eq. C_condensate_decay): (shape [n], rate)."""
+    lib = load_library()
+    q = _np(q)
+    shape = np.empty(q.size)
+    rate = ctypes.c_double()
+    rc = lib.kx_source_condensate(q.size, _ptr(q), float(a), float(mass), float(m_phi), float(g_chi),
+                                  float(gamma_n), _ptr(shape), ctypes.byref(rate))
+    if rc:
+        raise KxError(rc, "kx_source_condensate")
+    return shape, rate.value
 
 
 class Server:

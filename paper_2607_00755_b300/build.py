@@ -20,7 +20,8 @@ COMMON = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler",
 # The kernel-tensor build is compiled without FMA contraction so that its
 # support and Theta decisions are the IEEE results of the written expressions.
 PER_FILE = {"kx_build.cu": ["-fmad=false"]}
-SOURCES = ["kx_build.cu", "kx_contract.cu", "kx_batch.cu", "kx_api.cu", "kx_serve.cu", "kx_noalloc.cu"]
+SOURCES = ["kx_build.cu", "kx_contract.cu", "kx_batch.cu", "kx_api.cu", "kx_serve.cu", "kx_noalloc.cu",
+           "kx_sources.cu"]
 HEADERS = ["kx_internal.cuh", "kx_math.cuh", "kx_ptx.cuh", os.path.join(INCLUDE, "kx.h")]
 
 

@@ -528,3 +528,53 @@ def test_quantum_statistics_fp64_path_matches_oracle(ctx, kx, eta):
     assert np.max(np.abs(C.cpu().numpy()[0] - Co)) <= 1e-13 * scale
     assert np.max(np.abs(Co)) < 2e-2 * scale
     k.release()
+
+
+# ------------------------------------------------- the paper's physical sources ---
+def test_solve_with_paper_sources_matches_oracle_and_cbe(ctx, kx):
+    """A static box with the paper's two freeze-in terms (Sec. 2: Higgs decay at
+    a bath temperature cooling with an e-folding time, and a decaying cold
+    condensate binned to one cell): the FP64 solve follows the oracle's step for
+    step, the number and energy it ends with are the initial ones plus the
+    injected integrals (the fluid, cBE-like bookkeeping: sum_k rate_k tau_k
+    (1 - exp(-(t - t_on)/tau_k)) times 1 and the row's mean energy), and the
+    final Maxwell-Boltzmann temperature is the one those two moments fix."""
+    N = 48
+    q = ki.log_grid(N, 1e-3, 10.0)
+    g = oracle.grid(q)
+    f0 = ki.bimodal(np.random.default_rng(27), q)
+    n0, e0 = np.sum(g["h"] * f0), np.sum(g["h"] * g["E"] * f0)
+    sh, rh = kx.source_higgs_decay(q, 1.0, 5.0, 0.8, 1.0, 1.0)
+    sc, rc = kx.source_condensate(q, 1.0, 3.0, 1.0, 1.0)
+    tau, t_on = np.array([2.0, 1.0]), np.array([0.0, 0.5])
+    # rates scaled (coupling^2 and 2 Gamma n_Phi are free) to inject 30 % and 15 % of n0
+    rate = np.array([0.30 * n0 / tau[0], 0.15 * n0 / tau[1]])
+    src = {"shape": np.stack([sh, sc]), "rate": rate, "tau": tau, "t_on": t_on}
+    W = oracle.kernel_tensor(q)
+    par = dict(t_end=1e4, h0=1e-3, rtol=1e-6, atol=1e-12 * f0.max(), l1_tol=1e-3, check_every=5)
+    fo, ro = oracle.solve(q, W, f0, oracle.M2_from_sigma(1.0, 2.0), sources=src, **par)
+    assert ro["converged"] == 1
+    k = ctx.build_kernel(q, precision=kx.FP64)
+    fd = dev(f0[None])
+    res = ctx.solve(k, fd, 2.0, sources=src, **par)[0]
+    f = fd.cpu().numpy()[0]
+    assert res["converged"] == 1 and res["status"] == 0
+    assert res["steps"] == ro["steps"] and res["rejects"] == ro["rejects"]
+    assert relerr(f, fo) <= 1e-10
+    # injected number and energy (trapezoid-integrated by the stepper: ~1e-7)
+    inj = rate * tau * -np.expm1(-(res["t"] - t_on) / tau)
+    ebar = [np.sum(g["h"] * g["E"] * s) / np.sum(g["h"] * s) for s in (sh, sc)]
+    assert abs(np.sum(g["h"] * f) / (n0 + inj.sum()) - 1) < 1e-6
+    assert abs(np.sum(g["h"] * g["E"] * f) / (e0 + np.dot(inj, ebar)) - 1) < 1e-6
+    # the temperature the two injected moments fix: <E>_MB(T) = rho / n on the grid
+    target = (e0 + np.dot(inj, ebar)) / (n0 + inj.sum())
+    lo, hi = 1e-3, 1e3
+    for _ in range(200):
+        T = np.sqrt(lo * hi)
+        w = g["h"] * np.exp(-(g["E"] - g["E"][0]) / T)
+        if np.sum(w * g["E"]) / np.sum(w) < target:
+            lo = T
+        else:
+            hi = T
+    assert abs(res["T_mb"] / T - 1) < 1e-5, (res["T_mb"], T)
+    k.release()
