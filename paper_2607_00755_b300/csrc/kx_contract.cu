@@ -360,9 +360,10 @@ __device__ __forceinline__ int kx_prep_block(int n, int path, double x, double E
         uint32_t hb;
         asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(hb) : "f"(fp));
         const float hi = __uint_as_float(hb);
-        const int KB = blockDim.x / KX_TILE_K;   // blockDim = n rounded up to 32 = padded k extent
-        const size_t t = ((size_t)(b >> 6) * KB + i / KX_TILE_K) * 2;
-        const int off = kx_tile_offset(b & 63, i % KX_TILE_K);
+        static_assert(KX_TILE_K == 16, "tile indexing below uses k blocks of 16");
+        const int KB = blockDim.x >> 4;   // blockDim = n rounded up to 32 = padded k extent
+        const size_t t = ((size_t)(b >> 6) * KB + (i >> 4)) * 2;
+        const int off = kx_tile_offset(b & 63, i & 15);
         v.bt[t * (64 * KX_TILE_K) + off] = hi;
         v.bt[(t + 1) * (64 * KX_TILE_K) + off] = fp - hi;
         return bad;
@@ -1676,19 +1677,23 @@ __device__ __forceinline__ void kx_stage_body(int b, int n, int chunks, int path
     if (threadIdx.x == 0) v.flags[b] = bad2;
 }
 
+// PATH >= 0: an instantiation for that path alone (the FP32 path's, which holds
+// only its own prep: a smaller kernel, and a register allocation that the
+// other paths' code does not move); PATH = -1: the path is the argument.
+template <int PATH>
 __global__ void __launch_bounds__(KX_FIN_THREADS)
-    k_stage(int n, int chunks, int path, const double *__restrict__ E,
-            const double *__restrict__ h, kx_batch_views v, kx_step_views sv, int stage,
-            long long max_attempts) {
+    k_stage(int n, int chunks, int path, const double *__restrict__ E, const double *__restrict__ h,
+            kx_batch_views v, kx_step_views sv, int stage, long long max_attempts) {
     __shared__ double smem[5 * KX_FIN_THREADS + 8];
     kx_pdl_trigger();
     kx_pdl_wait();
-    kx_stage_body(blockIdx.x, n, chunks, path, E, h, v, sv, stage, max_attempts, smem);
+    kx_stage_body(blockIdx.x, n, chunks, PATH >= 0 ? PATH : path, E, h, v, sv, stage, max_attempts, smem);
 }
 
 cudaError_t kx_launch_stage(const kx_kernel *k, int B, const kx_batch_views &v,
                             const kx_step_views &sv, int stage, cudaStream_t s, bool pdl) {
-    int path = k->precision;
-    return kx_launch_ex(k_stage, dim3(B), dim3(kx_fin_threads(k->n)), 0, s, pdl, k->n, v.chunks, path,
-                        (const double *)k->d_E, (const double *)k->d_h, v, sv, stage, sv.max_attempts);
+    auto *fn = k->precision == KX_FP32 ? k_stage<KX_FP32> : k_stage<-1>;
+    return kx_launch_ex(fn, dim3(B), dim3(kx_fin_threads(k->n)), 0, s, pdl, k->n, v.chunks,
+                        (int)k->precision, (const double *)k->d_E, (const double *)k->d_h, v, sv,
+                        stage, sv.max_attempts);
 }
