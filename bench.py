@@ -496,7 +496,12 @@ def main():
             "frac": achieved / hbm, "traffic": NCU_TRAFFIC["stream_n128_b4"],
             "kernel": f"N=128, 4 instances: {stream_kernel_name(ctx, 128, B)}",
             "algorithmic_bytes_per_launch": alg_bytes, "avg_launch_ms_cold_l2": ms_cold,
-            "avg_launch_ms_warm_l2": ms_warm, "peak_source": src_peak}
+            "avg_launch_ms_warm_l2": ms_warm, "peak_source": src_peak,
+            "note": "the collision contraction of the step; by device time the per-instance "
+                    "stage kernel (k_stage<1>: FP64 chains and block reductions on one block per "
+                    "instance, 4 SMs) is the larger share (~58 %, profiles/launch_list_config2_"
+                    "n128_step.md, profiles/k_stage_config2_n128.md); both are latency bound at "
+                    "N = 128 with 4 instances (tables 6.8 MB, L2-resident in the solve)"}
     # streaming single-instance roofline at N=384 (tables 227 MB > L2)
     q384 = ki.log_grid(384, 1e-3, 1e2)
     k384 = ctx.build_kernel(q384, precision=kx.FP32)
