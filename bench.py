@@ -34,9 +34,10 @@ METRIC = "collision-term evals/s & solves/s vs plain FP64 path; p50/p99 solve la
 UNIT = "evals/s"
 L2_FLUSH_BYTES = 512 << 20     # > 126 MB L2
 # DRAM bytes (read + write) per launch from one ncu capture of the current kernels
-# (profiles/k_stream32r_n128_batch4.md, profiles/k_stream32r_n384_single.md); None
+# (profiles/k_stream32r_n128_batch4.md, profiles/k_stream32r_single_n384_n512.md); None
 # whenever those kernels have changed since the capture.
-NCU_TRAFFIC = {"stream_n128_b4": 6.783488e6, "stream_n384": 172.482048e6 + 2.700800e6}
+NCU_TRAFFIC = {"stream_n128_b4": 6.783488e6, "stream_n384": 172.423424e6,
+               "stream_n512": 406.064896e6 + 0.035584e6}
 
 
 def stream_kernel_name(ctx, n, batch):
@@ -157,26 +158,33 @@ def run_reference(args, rank):
 
 def run_contraction_only(args):
     """Contraction kernel alone on an n-point grid (q in [1e-3, 1e2]) for
-    `batch` seeded bimodal distributions; cold L2 before every launch."""
+    `batch` seeded bimodal distributions: cold L2 before every launch, or with
+    --rotate R, R kernels of the grid whose contractions run back to back in
+    rotation (each launch reads its tables from HBM when R x tables > L2)."""
     import torch
     import paper_2607_00755_b300 as kx
     ctx = kx.Context(0)
     q = ki.log_grid(args.n, 1e-3, 1e2)
     prec = {"fp32": kx.FP32, "fp64": kx.FP64, "split": kx.SPLIT_TF32}[args.precision]
-    k = ctx.build_kernel(q, precision=prec)
+    ks = [ctx.build_kernel(q, precision=prec) for _ in range(max(1, args.rotate))]
+    k = ks[0]
     f = torch.as_tensor(ki.batch_bimodal(np.random.default_rng(7), q, args.batch), device="cuda")
     if args.variant >= 0 and prec == kx.FP32:
         ctx.set_stream_variant(args.n, args.batch, args.variant)
-    ms = ctx.time_contraction(k, f, iters=args.iters, flush_bytes=L2_FLUSH_BYTES)
+    if args.rotate > 0:
+        ms = ctx.time_contractions(ks, f, iters=args.iters)
+    else:
+        ms = ctx.time_contraction(k, f, iters=args.iters, flush_bytes=L2_FLUSH_BYTES)
     alg = k.info()["stream_bytes"]
     hbm, src = peaks()
     name = stream_kernel_name(ctx, args.n, args.batch) if prec == kx.FP32 else args.precision
     print(json.dumps({"kernel": "contraction", "variant": name, "n": args.n, "batch": args.batch,
-                      "precision": args.precision, "avg_ms": ms,
+                      "precision": args.precision, "rotate": args.rotate, "avg_ms": ms,
                       "algorithmic_bytes": alg, "achieved_gbs": alg / (ms * 1e-3) / 1e9,
                       "frac_of_" + src + "_hbm": alg / (ms * 1e-3) / 1e9 / hbm,
                       "info": k.info()}), flush=True)
-    k.release()
+    for kk in ks:
+        kk.release()
     ctx.close()
     return 0
 
@@ -221,6 +229,39 @@ def measure_batched(ctx, kx, torch, flush, iters=5, oracle_sample=4):
             "split_tf32": out["split_tf32"], "fp64_path": out["fp64"],
             "speedup_vs_fp64": out["split_tf32"]["evals_per_s"] / out["fp64"]["evals_per_s"],
             "max_rel_err_vs_oracle": err, "oracle_sample": f"{oracle_sample} instances"}
+
+
+def measure_config1(ctx, kx, torch, reps=5):
+    """Single instance, N = 32 (q in [1e-3, 10]), sigma = 1: 100 fixed Heun
+    steps of h = 0.02 per solve (2 evaluations a step), on the plain FP64 and
+    the FP32 path; steps/s from CUDA events around `reps` solves, and the
+    contraction alone (warm L2, the kernel is 0.3 MB)."""
+    c = ki.config1()
+    q, f0 = c["q"], c["f0"]
+    out = {"workload": "N=32, q in [1e-3,10], sigma=1, 100 fixed Heun steps (h=0.02) from the "
+                       "seeded bimodal f"}
+    for name, prec in (("fp64", kx.FP64), ("fp32", kx.FP32)):
+        k = ctx.build_kernel(q, precision=prec)
+        fd = torch.as_tensor(np.tile(f0, (1, 1)), device="cuda")
+        kw = dict(t_end=c["n_steps"] * c["h"], h0=c["h"], fixed_step=1)
+        ctx.solve(k, fd.clone(), c["sigma"], **kw)              # warm (graph capture, tuning)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record()
+        steps = 0
+        for _ in range(reps):
+            f = fd.clone()
+            res = ctx.solve(k, f, c["sigma"], **kw)
+            steps += res[0]["steps"]
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        us_c = 1e3 * ctx.time_contraction(k, fd, iters=50, flush_bytes=0)
+        k.release()
+        out[name] = {"steps_per_s": steps / (ms * 1e-3), "us_per_step": 1e3 * ms / steps,
+                     "us_per_eval": 1e3 * ms / (2 * steps), "contraction_us": us_c}
+    out["speedup_fp32_vs_fp64_steps"] = out["fp32"]["steps_per_s"] / out["fp64"]["steps_per_s"]
+    return out
 
 
 def measure_uneven(ctx, kx, t_end=5.0, fp64_per_size=4):
@@ -366,6 +407,8 @@ def main():
     ap.add_argument("--batch", type=int, default=1)
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64", "split"])
     ap.add_argument("--iters", type=int, default=20)
+    ap.add_argument("--rotate", type=int, default=0,
+                    help="--only contraction: time R kernels of the grid back to back in rotation")
     ap.add_argument("--variant", type=int, default=-1,
                     help="FP32: pin the streaming variant (0..3) instead of tuning it")
     ap.add_argument("--requests", type=int, default=100)
@@ -502,20 +545,35 @@ def main():
                     "instance, 4 SMs) is the larger share (~58 %, profiles/launch_list_config2_"
                     "n128_step.md, profiles/k_stage_config2_n128.md); both are latency bound at "
                     "N = 128 with 4 instances (tables 6.8 MB, L2-resident in the solve)"}
-    # streaming single-instance roofline at N=384 (tables 227 MB > L2)
-    q384 = ki.log_grid(384, 1e-3, 1e2)
-    k384 = ctx.build_kernel(q384, precision=kx.FP32)
-    f384 = torch.as_tensor(ki.batch_bimodal(np.random.default_rng(7), q384, 1), device="cuda")
-    ms384 = ctx.time_contraction(k384, f384, iters=30, flush_bytes=L2_FLUSH_BYTES)
-    b384 = k384.info()["stream_bytes"]
-    k384.release()
-    roof384 = {"bound": "hbm", "achieved": b384 / (ms384 * 1e-3) / 1e9, "peak": hbm,
-               "unit": "GB/s", "frac": b384 / (ms384 * 1e-3) / 1e9 / hbm,
-               "traffic": NCU_TRAFFIC["stream_n384"],
-               "kernel": f"N=384, single instance, cold L2: {stream_kernel_name(ctx, 384, 1)}",
-               "algorithmic_bytes_per_launch": b384, "avg_launch_ms": ms384,
-               "evals_per_s": 1e3 / ms384}
+    # streaming single-instance rooflines at N=384 and N=512 (tables 172 MB
+    # and 406 MB, both > L2): several kernels of the same grid whose
+    # contractions run back to back in rotation, so that each launch streams
+    # its tables from HBM (about 1 GB read between two launches of one
+    # kernel); the isolated launch after an L2 flush beside it
+    def streaming_roofline(n, rotate):
+        qn = ki.log_grid(n, 1e-3, 1e2)
+        ks = [ctx.build_kernel(qn, precision=kx.FP32) for _ in range(rotate)]
+        fn = torch.as_tensor(ki.batch_bimodal(np.random.default_rng(7), qn, 1), device="cuda")
+        ms_rot = ctx.time_contractions(ks, fn, iters=10)
+        ms_iso = ctx.time_contraction(ks[0], fn, iters=20, flush_bytes=L2_FLUSH_BYTES)
+        nb = ks[0].info()["stream_bytes"]
+        for kr in ks:
+            kr.release()
+        gbs = nb / (ms_rot * 1e-3) / 1e9
+        return {"bound": "hbm", "achieved": gbs, "peak": hbm, "unit": "GB/s", "frac": gbs / hbm,
+                "traffic": NCU_TRAFFIC.get(f"stream_n{n}"),
+                "kernel": f"N={n}, single instance: {stream_kernel_name(ctx, n, 1)}",
+                "algorithmic_bytes_per_launch": nb, "avg_launch_ms": ms_rot,
+                "timing": f"{rotate} kernels of the grid ({rotate} x {nb / 1e6:.0f} MB tables) in "
+                          f"rotation, {10 * rotate} launches back to back between CUDA events",
+                "avg_launch_ms_isolated_cold_l2": ms_iso,
+                "frac_isolated_cold_l2": nb / (ms_iso * 1e-3) / 1e9 / hbm,
+                "evals_per_s": 1e3 / ms_rot}
 
+    roof384 = streaming_roofline(384, 6)
+    roof512 = streaming_roofline(512, 3)
+
+    config1 = measure_config1(ctx, kx, torch) if rank == 0 else None
     batched = measure_batched(ctx, kx, torch, flush) if rank == 0 else None
     uneven = measure_uneven(ctx, kx) if rank == 0 and not args.no_serving else None
     serving = (measure_serving(ctx, kx, requests=args.requests)
@@ -538,6 +596,8 @@ def main():
                 "speedup_vs_fp64": (value / fp64["value"]) if fp64 else None,
                 "failed_solves": len(bad),
                 "roofline": roof, "roofline_streaming_n384": roof384,
+                "roofline_streaming_n512": roof512,
+                "fixed_steps_n32": config1,
                 "batched_n192_b512": batched,
                 "uneven_batch": uneven,
                 "serving": serving,

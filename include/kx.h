@@ -293,6 +293,18 @@ long long kx_launch_count(const kx_ctx *ctx);
 int kx_time_contraction(kx_ctx *ctx, const kx_kernel *k, int batch, const double *f_dev,
                         int iters, long long flush_bytes, double *avg_ms);
 
+/* Time contractions of several kernels of one grid size issued back to back:
+ * prepares f_dev [batch][n] (device) for each of the nk kernels ks[0..nk-1]
+ * (library-owned, all with the same n), then launches the contraction of
+ * ks[0], ks[1], ..., ks[nk-1], `iters` times over, on the context's stream
+ * between two CUDA events; *avg_ms = device time / (iters * nk).  With
+ * kernels whose tables together exceed the L2 cache, every launch streams its
+ * tables from HBM (rotating buffers) while the launches still follow each
+ * other as in a solve.  KX_EINVAL for nk < 1, a null kernel, mixed sizes or
+ * bad arguments; KX_ECUDA on a CUDA error.  Synchronises the stream. */
+int kx_time_contractions(kx_ctx *ctx, int nk, const kx_kernel *const *ks, int batch,
+                         const double *f_dev, int iters, double *avg_ms);
+
 /* Moment-matched discrete Maxwell-Boltzmann fit used by the stopping test:
  * out_host[batch][3] = (T, ln z, L1) with L1 = sum h |f - f_MB| / sum h f. */
 int kx_mb_fit(kx_ctx *ctx, const kx_kernel *k, int batch, const double *f_dev, double *out_host);

@@ -26,6 +26,7 @@ EXPORTS = (
     "kx_build_kernel", "kx_kernel_retain", "kx_kernel_release", "kx_kernel_get_info",
     "kx_kernel_grid", "kx_kernel_row", "kx_collision", "kx_collision_host", "kx_step",
     "kx_solve", "kx_solve_host", "kx_mb_fit", "kx_launch_count", "kx_time_contraction",
+    "kx_time_contractions",
     "kx_collision_noalloc", "kx_server_start", "kx_submit", "kx_poll", "kx_server_get_stats",
     "kx_server_stop", "kx_math_check", "kx_set_stream_variant", "kx_get_stream_variant",
     "kx_source_higgs_decay", "kx_source_condensate",
@@ -132,6 +133,7 @@ def load_library(path: str = LIB_PATH):
         "kx_source_condensate": (i, [i, vp, d, d, d, d, d, vp, vp]),
         "kx_launch_count": (ctypes.c_longlong, [vp]),
         "kx_time_contraction": (i, [vp, vp, i, vp, i, ctypes.c_longlong, vp]),
+        "kx_time_contractions": (i, [vp, i, vp, i, vp, i, vp]),
         "kx_collision_noalloc": (i, [vp, vp, i, vp, vp, vp, i]),
         "kx_server_start": (i, [vp, ctypes.POINTER(ServerConfig), vp]),
         "kx_submit": (i, [vp, ctypes.POINTER(GridDesc), d, vp, d, d, d, vp, vp]),
@@ -319,6 +321,18 @@ class Context:
                                           int(flush_bytes), ctypes.byref(ms))
         if rc:
             raise self.error(rc, "kx_time_contraction")
+        return ms.value
+
+    def time_contractions(self, kernels, f, iters=10):
+        """Mean device time (ms) per launch of the kernels' contractions issued
+        back to back (rotating tables), for f [B, n]."""
+        f2 = f if f.dim() == 2 else f.view(1, -1)
+        arr = (ctypes.c_void_p * len(kernels))(*[k.h for k in kernels])
+        ms = ctypes.c_double()
+        rc = self.lib.kx_time_contractions(self.h, len(kernels), arr, f2.shape[0], _dptr(f2),
+                                           int(iters), ctypes.byref(ms))
+        if rc:
+            raise self.error(rc, "kx_time_contractions")
         return ms.value
 
     def mb_fit(self, kernel, f):

@@ -957,3 +957,46 @@ extern "C" int kx_time_contraction(kx_ctx *ctx, const kx_kernel *k, int B, const
     *avg_ms = total / iters;
     return KX_OK;
 }
+
+extern "C" int kx_time_contractions(kx_ctx *ctx, int nk, const kx_kernel *const *ks, int B,
+                                    const double *f_dev, int iters, double *avg_ms) {
+    if (!ctx || nk < 1 || !ks || B < 1 || !f_dev || iters < 1 || !avg_ms) return KX_EINVAL;
+    for (int i = 0; i < nk; ++i)
+        if (!ks[i] || ks[i]->n != ks[0]->n) return KX_EINVAL;
+    KX_CUDA_TRY(ctx, cudaSetDevice(ctx->device));
+    std::vector<size_t> off(nk + 1, 0);
+    for (int i = 0; i < nk; ++i) off[i + 1] = off[i] + kx_align(kx_views_bytes(ks[i], B));
+    int rc = kx_arena_reserve(ctx, off[nk]);
+    if (rc) return rc;
+    cudaStream_t s = ctx->stream;
+    std::vector<kx_batch_views> v(nk);
+    cudaError_t e = cudaSuccess;
+    for (int i = 0; i < nk && e == cudaSuccess; ++i) {
+        kx_carve_views(ks[i], B, (char *)ctx->d_arena + off[i], &v[i]);
+        e = kx_views_clear(ks[i], B, v[i], s);
+        if (e == cudaSuccess) e = kx_launch_prep(ks[i], B, f_dev, v[i], nullptr, s);
+        ctx->launches += 1;
+        if (e == cudaSuccess && kx_tune_contraction(ks[i], B, f_dev, v[i], nullptr, s, &ctx->launches))
+            e = cudaErrorUnknown;
+    }
+    // one untimed pass, then iters passes over the kernels back to back
+    for (int i = 0; i < nk && e == cudaSuccess; ++i, ++ctx->launches)
+        e = kx_launch_contract(ks[i], B, f_dev, v[i], nullptr, 1, s);
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (e == cudaSuccess) e = cudaEventCreate(&e0);
+    if (e == cudaSuccess) e = cudaEventCreate(&e1);
+    if (e == cudaSuccess) e = cudaEventRecord(e0, s);
+    for (int it = 0; it < iters && e == cudaSuccess; ++it)
+        for (int i = 0; i < nk && e == cudaSuccess; ++i, ++ctx->launches)
+            e = kx_launch_contract(ks[i], B, f_dev, v[i], nullptr, 1, s);
+    if (e == cudaSuccess) e = cudaEventRecord(e1, s);
+    if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+    float ms = 0.f;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    if (e != cudaSuccess)
+        return kx_set_error(ctx, KX_ECUDA, std::string("time contractions: ") + cudaGetErrorString(e));
+    *avg_ms = (double)ms / ((double)iters * nk);
+    return KX_OK;
+}

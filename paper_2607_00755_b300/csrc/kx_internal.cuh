@@ -63,7 +63,7 @@ struct kx_kernel {
     int Kpad;            // n columns (m) padded to a multiple of 32
     float *d_Atile;      // [Mpad/128][Kpad/16][hi, lo][2048]: W_full as TF32 hi/lo in MMA operand tiles
     float2 *d_lel;       // per row i: nonzero (S_inm, omega) sorted by j_L
-    int2 *d_lseg;        // segments of <= 32 elements of one j_L: (first element, j_L << 8 | count)
+    int2 *d_lseg;        // segments of <= 64 elements of one j_L: (first element, j_L << 8 | count)
     int *d_lsw;          // [n * warps + 1] first segment of each (row, loss-kernel warp)
     int *d_lorder;       // [n] rows by element count, longest first
     long long nseg;      // segments, all rows

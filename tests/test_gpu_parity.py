@@ -453,7 +453,8 @@ def test_table_log2_exp_against_cuda_and_libm(ctx, kx):
     y = np.concatenate([rng.uniform(-745, 709.7, 20000), rng.uniform(-1, 1, 2000) * 1e-3,
                         [0.0, -0.0, 1.0, -1.0, 709.78, -708.39, -745.1, -746.0, 710.0]])
     out = ctx.math_check(1, torch.as_tensor(y, device="cuda")).cpu().numpy()
-    ref = np.exp(y)
+    with np.errstate(over="ignore"):   # exp(710) = inf is one of the checked cases
+        ref = np.exp(y)
     normal = (ref > 2.3e-308) & np.isfinite(ref)
     rel = np.abs(out[normal, 0] - ref[normal]) / ref[normal]
     assert rel.max() <= 4.5e-16, rel.max()
