@@ -189,11 +189,12 @@ def run_contraction_only(args):
     return 0
 
 
-def measure_batched(ctx, kx, torch, flush, iters=5, oracle_sample=4):
+def measure_batched(ctx, kx, torch, flush, iters=5, check_sample=4):
     """Batched configuration: B = 512 seeded bimodal distributions sharing one
     N = 192 kernel (q in [1e-3, 1e2]); projected C per instance through
     kx_collision, split-TF32 tensor-core path vs the plain FP64 path on the same
-    inputs; max relative error of a sample of instances vs the FP64 oracle."""
+    inputs.  Returns the line and the first `check_sample` instances' outputs
+    (compared with the FP64 oracle in the CPU-baseline leg)."""
     c = ki.config3()
     q, f, B = c["q"], c["f"], c["f"].shape[0]
     stream = torch.cuda.current_stream()
@@ -212,23 +213,74 @@ def measure_batched(ctx, kx, torch, flush, iters=5, oracle_sample=4):
             e1.record(stream)
             e1.synchronize()
             tot += e0.elapsed_time(e1)
-        Cs[name] = C.cpu().numpy()
+        Cs[name] = C[:check_sample].cpu().numpy()
         out[name] = {"evals_per_s": B * reps / (tot / 1e3), "ms_per_batch": tot / reps}
         k.release()
-    import oracle
-    W = oracle.kernel_tensor(q)
-    g = oracle.grid(q)
-    err = {"split_tf32": 0.0, "fp64": 0.0}
-    for b in range(oracle_sample):
-        Co = oracle.collision_tensor(q, W, f[b]) * oracle.M2_from_sigma(1.0, c["sigma"][b])
-        Co, _ = oracle.project(g["E"], g["h"], f[b], Co)
-        for name in err:
-            err[name] = max(err[name], float(np.max(np.abs(Cs[name][b] - Co)) / np.max(np.abs(Co))))
-    return {"workload": "B=512 distributions sharing one N=192 kernel, q in [1e-3,1e2], "
+    line = {"workload": "B=512 distributions sharing one N=192 kernel, q in [1e-3,1e2], "
                         "projected C (kx_collision)",
             "split_tf32": out["split_tf32"], "fp64_path": out["fp64"],
             "speedup_vs_fp64": out["split_tf32"]["evals_per_s"] / out["fp64"]["evals_per_s"],
-            "max_rel_err_vs_oracle": err, "oracle_sample": f"{oracle_sample} instances"}
+            "max_rel_err_vs_oracle": None, "oracle_sample": f"{check_sample} instances"}
+    check = {"q": q, "f": f[:check_sample], "sigma": c["sigma"][:check_sample], "C": Cs}
+    return line, check
+
+
+def measure_paper_runtime(ctx, kx, torch, sizes=(32, 64, 96, 128, 192, 256, 384, 512),
+                          check_max_n=256, iters=20):
+    """The paper's runtime benchmark (Sec. 5, Fig. run_time): one full-grid
+    evaluation of the elastic self-collision operator for the two-bump f of
+    eq. (benchmark_two_bump) with m = 1, a = 1, q in [1e-3, 1e2], N_mu = 18,
+    Bose-Einstein factors and no projection, as a function of N; device time
+    of the whole evaluation (prepare f, contraction, row combine) replayed as a
+    CUDA graph, warm caches, on the plain FP64 and the FP32 path.  Returns the
+    line and the outputs at N <= check_max_n (compared with the FP64 oracle in
+    the CPU-baseline leg)."""
+    rows, check = [], []
+    for n in sizes:
+        q = ki.log_grid(n, 1e-3, 1e2)
+        f = ki.paper_two_bump(q)
+        fd = torch.as_tensor(f[None], device="cuda")
+        row = {"n": n}
+        outs = {}
+        for name, prec in (("fp64", kx.FP64), ("fp32", kx.FP32)):
+            k = ctx.build_kernel(q, precision=prec, stats=1)
+            ms, C = ctx.time_collision(k, fd, 1.0, project=False, iters=iters)
+            row[name + "_us_per_eval"] = 1e3 * ms
+            outs[name] = C.cpu().numpy()[0]
+            k.release()
+        row["speedup_fp32_vs_fp64"] = row["fp64_us_per_eval"] / row["fp32_us_per_eval"]
+        rows.append(row)
+        if n <= check_max_n:
+            check.append({"n": n, "q": q, "f": f, "C": outs, "row": row})
+    line = {"workload": "Fig. run_time of the paper: eq. (benchmark_two_bump), m=1, a=1, "
+                        "q in [1e-3,1e2], N_mu=18, Bose-Einstein factors, no projection; one "
+                        "full-grid evaluation (graph replay, warm caches)",
+            "rows": rows}
+    return line, check
+
+
+def oracle_errors(batched_check, runtime_check):
+    """CPU-baseline leg: the FP64 oracle on the samples the GPU lines kept;
+    max relative error (max-norm over the grid) of each path against it."""
+    import oracle
+    out = {}
+    if batched_check is not None:
+        q, f, sig = batched_check["q"], batched_check["f"], batched_check["sigma"]
+        W = oracle.kernel_tensor(q)
+        g = oracle.grid(q)
+        err = {name: 0.0 for name in batched_check["C"]}
+        for b in range(f.shape[0]):
+            Co = oracle.collision_tensor(q, W, f[b]) * oracle.M2_from_sigma(1.0, sig[b])
+            Co, _ = oracle.project(g["E"], g["h"], f[b], Co)
+            for name, C in batched_check["C"].items():
+                err[name] = max(err[name], float(np.max(np.abs(C[b] - Co)) / np.max(np.abs(Co))))
+        out["batched"] = err
+    for item in runtime_check or []:
+        q, f = item["q"], item["f"]
+        Co = oracle.collision_tensor_stats(q, oracle.kernel_tensor(q), f, 1) * oracle.M2_from_sigma(1.0, 1.0)
+        for name, C in item["C"].items():
+            item["row"][name + "_max_rel_err_vs_oracle"] = float(np.max(np.abs(C - Co)) / np.max(np.abs(Co)))
+    return out
 
 
 def measure_config1(ctx, kx, torch, reps=5):
@@ -574,7 +626,8 @@ def main():
     roof512 = streaming_roofline(512, 3)
 
     config1 = measure_config1(ctx, kx, torch) if rank == 0 else None
-    batched = measure_batched(ctx, kx, torch, flush) if rank == 0 else None
+    batched, batched_check = measure_batched(ctx, kx, torch, flush) if rank == 0 else (None, None)
+    runtime, runtime_check = measure_paper_runtime(ctx, kx, torch) if rank == 0 else (None, None)
     uneven = measure_uneven(ctx, kx) if rank == 0 and not args.no_serving else None
     serving = (measure_serving(ctx, kx, requests=args.requests)
                if rank == 0 and not args.no_serving else None)
@@ -585,6 +638,9 @@ def main():
         cpu = {"value": e / t, "unit": UNIT, "cores": cores, "kind": "oracle",
                "sample": f"{e} RHS evaluations (tensor-form C + projection + sources) of the "
                          f"N=128 workload's first Heun attempts in {t:.1f} s"}
+        errs = oracle_errors(batched_check, runtime_check)
+        if batched is not None:
+            batched["max_rel_err_vs_oracle"] = errs.get("batched")
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
                 "steps": args.steps, "warmup": args.warmup,
@@ -599,6 +655,7 @@ def main():
                 "roofline_streaming_n512": roof512,
                 "fixed_steps_n32": config1,
                 "batched_n192_b512": batched,
+                "paper_runtime_bose_einstein": runtime,
                 "uneven_batch": uneven,
                 "serving": serving,
                 "cpu_baseline": cpu,

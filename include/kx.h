@@ -84,7 +84,8 @@ typedef struct {
     int measure;      /* KX_MEASURE_ENERGY | KX_MEASURE_LITERAL */
     int stats;        /* 0 = dilute f3 f4 - f1 f2 (eq. Lambda dilute); +1 Bose-Einstein, -1
                          Fermi-Dirac: the factor of eq. Lambda_quantum per element, f_t from the
-                         log interpolation of f (FP64 path only; other paths -> KX_ENOTSUP) */
+                         log interpolation of f (FP64 and FP32 paths; KX_SPLIT_TF32 ->
+                         KX_ENOTSUP) */
     int precision;    /* KX_FP64 | KX_FP32 | KX_SPLIT_TF32 */
 } kx_grid_desc;
 
@@ -292,6 +293,16 @@ long long kx_launch_count(const kx_ctx *ctx);
  * cold L2.  Synchronises the stream. */
 int kx_time_contraction(kx_ctx *ctx, const kx_kernel *k, int batch, const double *f_dev,
                         int iters, long long flush_bytes, double *avg_ms);
+
+/* Time one full evaluation of C[f] for `batch` instances: the work of
+ * kx_collision without diagnostics (prepare f, contraction, row combine and
+ * the projection if `project`), captured once as a CUDA graph and launched
+ * `iters` times back to back between two CUDA events on the context's stream;
+ * *avg_ms = device time per evaluation.  Arguments as in kx_collision; C_dev
+ * [batch][n] (device) receives C[f].  Errors as kx_collision, KX_EINVAL for
+ * iters < 1 or a null avg_ms.  Synchronises the stream. */
+int kx_time_collision(kx_ctx *ctx, const kx_kernel *k, int batch, const double *sigma_host,
+                      const double *f_dev, double *C_dev, int project, int iters, double *avg_ms);
 
 /* Time contractions of several kernels of one grid size issued back to back:
  * prepares f_dev [batch][n] (device) for each of the nk kernels ks[0..nk-1]

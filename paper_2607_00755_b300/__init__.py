@@ -26,7 +26,7 @@ EXPORTS = (
     "kx_build_kernel", "kx_kernel_retain", "kx_kernel_release", "kx_kernel_get_info",
     "kx_kernel_grid", "kx_kernel_row", "kx_collision", "kx_collision_host", "kx_step",
     "kx_solve", "kx_solve_host", "kx_mb_fit", "kx_launch_count", "kx_time_contraction",
-    "kx_time_contractions",
+    "kx_time_contractions", "kx_time_collision",
     "kx_collision_noalloc", "kx_server_start", "kx_submit", "kx_poll", "kx_server_get_stats",
     "kx_server_stop", "kx_math_check", "kx_set_stream_variant", "kx_get_stream_variant",
     "kx_source_higgs_decay", "kx_source_condensate",
@@ -134,6 +134,7 @@ def load_library(path: str = LIB_PATH):
         "kx_launch_count": (ctypes.c_longlong, [vp]),
         "kx_time_contraction": (i, [vp, vp, i, vp, i, ctypes.c_longlong, vp]),
         "kx_time_contractions": (i, [vp, i, vp, i, vp, i, vp]),
+        "kx_time_collision": (i, [vp, vp, i, vp, vp, vp, i, i, vp]),
         "kx_collision_noalloc": (i, [vp, vp, i, vp, vp, vp, i]),
         "kx_server_start": (i, [vp, ctypes.POINTER(ServerConfig), vp]),
         "kx_submit": (i, [vp, ctypes.POINTER(GridDesc), d, vp, d, d, d, vp, vp]),
@@ -322,6 +323,21 @@ class Context:
         if rc:
             raise self.error(rc, "kx_time_contraction")
         return ms.value
+
+    def time_collision(self, kernel, f, sigma=1.0, project=True, iters=20):
+        """Device time (ms) of one full evaluation of C[f] for f [B, n] (graph
+        replay); returns (ms, C)."""
+        import torch
+        f2 = f if f.dim() == 2 else f.view(1, -1)
+        B = f2.shape[0]
+        sig = _np(np.broadcast_to(np.asarray(sigma, dtype=np.float64), (B,)))
+        C = torch.empty_like(f2)
+        ms = ctypes.c_double()
+        rc = self.lib.kx_time_collision(self.h, kernel.h, B, _ptr(sig), _dptr(f2), _dptr(C),
+                                        int(project), int(iters), ctypes.byref(ms))
+        if rc:
+            raise self.error(rc, "kx_time_collision")
+        return ms.value, C.view_as(f)
 
     def time_contractions(self, kernels, f, iters=10):
         """Mean device time (ms) per launch of the kernels' contractions issued

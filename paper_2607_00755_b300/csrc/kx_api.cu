@@ -138,6 +138,10 @@ size_t kx_views_bytes(const kx_kernel *k, int B) {
     s += kx_align(sizeof(double) * B);               // M2
     s += kx_align(sizeof(kx_diag) * B);              // diag
     s += kx_align(sizeof(int));                      // err
+    if (k->precision == KX_FP32 && k->stats) {
+        s += kx_align(sizeof(float4) * B * n);       // tq
+        s += kx_align(sizeof(float) * B * n);        // tlam
+    }
     if (k->precision == KX_SPLIT_TF32) {
         const size_t Bpad = ((B + 63) / 64) * 64;
         s += kx_align(sizeof(float) * Bpad * k->Kpad * 2);   // bt (hi, lo)
@@ -165,6 +169,13 @@ void kx_carve_views(const kx_kernel *k, int B, void *base, kx_batch_views *v) {
     v->chunks = chunks;
     v->rtask = k->d_rtask;
     v->bt = v->fT = v->Gp = nullptr;
+    v->tq = nullptr;
+    v->tlam = nullptr;
+    v->eta = k->stats;
+    if (k->precision == KX_FP32 && k->stats) {
+        v->tq = (float4 *)p; p += kx_align(sizeof(float4) * B * n);
+        v->tlam = (float *)p; p += kx_align(sizeof(float) * B * n);
+    }
     v->B = B;
     v->Bpad = ((B + 63) / 64) * 64;
     if (k->precision == KX_SPLIT_TF32) {
@@ -248,8 +259,8 @@ extern "C" int kx_build_kernel(kx_ctx *ctx, const kx_grid_desc *d, kx_kernel **o
     if (d->measure != KX_MEASURE_ENERGY && d->measure != KX_MEASURE_LITERAL)
         return kx_set_error(ctx, KX_EINVAL, "unknown measure");
     if (d->stats < -1 || d->stats > 1) return kx_set_error(ctx, KX_EINVAL, "stats in {-1, 0, +1}");
-    if (d->stats != 0 && d->precision != KX_FP64)
-        return kx_set_error(ctx, KX_ENOTSUP, "quantum statistics are built on the FP64 path only");
+    if (d->stats != 0 && d->precision == KX_SPLIT_TF32)
+        return kx_set_error(ctx, KX_ENOTSUP, "quantum statistics: FP64 and FP32 paths only");
     if (d->precision != KX_FP64 && d->precision != KX_FP32 && d->precision != KX_SPLIT_TF32)
         return kx_set_error(ctx, KX_ENOTSUP, "precision not available in this build");
     for (int i = 0; i < n; ++i) {
@@ -955,6 +966,56 @@ extern "C" int kx_time_contraction(kx_ctx *ctx, const kx_kernel *k, int B, const
     if (flush) cudaFree(flush);
     if (e != cudaSuccess) return kx_set_error(ctx, KX_ECUDA, std::string("time contraction: ") + cudaGetErrorString(e));
     *avg_ms = total / iters;
+    return KX_OK;
+}
+
+extern "C" int kx_time_collision(kx_ctx *ctx, const kx_kernel *k, int B, const double *sigma,
+                                 const double *f_dev, double *C_dev, int project, int iters,
+                                 double *avg_ms) {
+    int rc = kx_check_batch(ctx, k, B, sigma);
+    if (rc) return rc;
+    if (!f_dev || !C_dev || iters < 1 || !avg_ms) return kx_set_error(ctx, KX_EINVAL, "bad arguments");
+    KX_CUDA_TRY(ctx, cudaSetDevice(ctx->device));
+    if ((rc = kx_arena_reserve(ctx, kx_views_bytes(k, B))) != KX_OK) return rc;
+    // one plain evaluation (uploads |M|^2, tunes the contraction), then the
+    // same three launches captured once and replayed
+    if ((rc = kx_collision_impl(ctx, k, B, sigma, f_dev, C_dev, project, nullptr, 0)) != KX_OK) return rc;
+    cudaStream_t s = ctx->stream;
+    KX_CUDA_TRY(ctx, cudaStreamSynchronize(s));
+    kx_batch_views v;
+    kx_carve_views(k, B, ctx->d_arena, &v);
+    cudaStream_t cap = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaError_t e = cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+        e = kx_launch_prep(k, B, f_dev, v, nullptr, cap);
+        if (e == cudaSuccess) e = kx_launch_contract(k, B, f_dev, v, nullptr, 1, cap);
+        if (e == cudaSuccess) e = kx_launch_finalize(k, B, f_dev, v, C_dev, project, 0, cap);
+        cudaError_t e2 = cudaStreamEndCapture(cap, &graph);
+        if (e == cudaSuccess) e = e2;
+    }
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&exec, graph, 0);
+    if (e == cudaSuccess) e = cudaGraphLaunch(exec, s);   // warm
+    if (e == cudaSuccess) e = cudaEventCreate(&e0);
+    if (e == cudaSuccess) e = cudaEventCreate(&e1);
+    if (e == cudaSuccess) e = cudaEventRecord(e0, s);
+    for (int it = 0; it < iters && e == cudaSuccess; ++it) e = cudaGraphLaunch(exec, s);
+    if (e == cudaSuccess) e = cudaEventRecord(e1, s);
+    if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+    float ms = 0.f;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+    ctx->launches += 3LL * (iters + 1);
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    if (exec) cudaGraphExecDestroy(exec);
+    if (graph) cudaGraphDestroy(graph);
+    if (cap) cudaStreamDestroy(cap);
+    if (e != cudaSuccess)
+        return kx_set_error(ctx, KX_ECUDA, std::string("time collision: ") + cudaGetErrorString(e));
+    *avg_ms = (double)ms / iters;
     return KX_OK;
 }
 

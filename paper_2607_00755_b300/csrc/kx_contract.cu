@@ -75,6 +75,11 @@ __device__ __forceinline__ float kx_ex2(float x) {
     asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
     return y;
 }
+__device__ __forceinline__ float kx_lg2(float x) {
+    float y;
+    asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
 
 // Deterministic block reduction of K doubles (sum).  All threads receive the
 // result.  smem holds K*32 doubles.
@@ -301,6 +306,11 @@ __device__ __forceinline__ void kx_block_max_keys(unsigned long long (&x)[K], un
 #define KX_LINE_FIT 0
 #define KX_LINE_NEXT 1
 #define KX_LINE_SAME 2
+// Q: quantum statistics on the FP32 path (v.eta = +1 BE, -1 FD): the line is
+// fitted to g = l2 - lambda, lambda = log2(1 + eta f) (g is linear in E on the
+// equilibrium of that statistics), tl holds (l2_j, g_j - line), tq the
+// interpolation tables of eps = l2 - line and of l2, tlam lambda_j.
+template <bool Q = false>
 __device__ __forceinline__ int kx_prep_block(int n, int path, double x, double Ei, double hi, double E0,
                              const kx_batch_views &v, int b, double *smem,
                              unsigned long long key_in = KX_KEY_NONE, int line_mode = KX_LINE_FIT) {
@@ -315,6 +325,17 @@ __device__ __forceinline__ int kx_prep_block(int n, int path, double x, double E
     int ex = 0;
     double frx = 0.0;
     if (path != KX_FP64 && in && !nf) kx_log2_parts(x > KX_LOG_FLOOR ? x : KX_LOG_FLOOR, ex, frx);
+    double lam = 0.0;   // log2(1 + eta f), quantum statistics only
+    if constexpr (Q) {
+        if (in && !nf) {
+            double y = 1.0 + (double)v.eta * x;
+            if (!(y > 1e-30)) y = 1e-30;   // Fermi-Dirac at f >= 1 (outside its range): finite floor
+            int e2 = 0;
+            double fr2 = 0.0;
+            kx_log2_parts(y, e2, fr2);
+            lam = (double)e2 + fr2;
+        }
+    }
     const float4 lines = (line_mode != KX_LINE_FIT && path == KX_FP32) ? v.fit[b] : make_float4(0.f, 0.f, 0.f, 0.f);
     const unsigned long long key =
         key_in != KX_KEY_NONE
@@ -376,8 +397,10 @@ __device__ __forceinline__ int kx_prep_block(int n, int path, double x, double E
     // differences; the fit only keeps the deviations small, so a poorly
     // conditioned fit (spread of K below 1% of its rms) falls back to slope 0.
     const float l2f = (float)l2, Kf = (float)K;
+    const double gq = Q ? l2 - lam : l2;   // the fitted quantity
+    const float gf = Q ? (float)gq : l2f;
     const float w = (in && fm > 0.0 && x > 0.0) ? (float)hi * (float)(x * rfm) : 0.f;
-    float sf[5] = {w, w * Kf, w * Kf * Kf, w * l2f, w * Kf * l2f};
+    float sf[5] = {w, w * Kf, w * Kf * Kf, w * gf, w * Kf * gf};
     auto solve_line = [](const float *t) {
         float slope = 0.f, icpt = 0.f;
         if (t[0] > 0.f) {
@@ -405,8 +428,16 @@ __device__ __forceinline__ int kx_prep_block(int n, int path, double x, double E
         line = solve_line(sf);
         if (i == 0) v.fit[b] = make_float4(line.x, line.y, line.x, line.y);
     }
-    const double del = l2 - ((double)line.x + (double)line.y * K);
-    if (in) dl[i] = del;
+    const double del = gq - ((double)line.x + (double)line.y * K);
+    double *dl2 = dl + n;   // quantum statistics: l2 for its forward differences
+    if constexpr (Q) {
+        if (in) {
+            dl[i] = del + lam;   // eps = l2 - line
+            dl2[i] = l2;
+        }
+    } else {
+        if (in) dl[i] = del;
+    }
     __syncthreads();
     if (line_mode != KX_LINE_FIT && i == 0) {
         float t[5];
@@ -418,10 +449,21 @@ __device__ __forceinline__ int kx_prep_block(int n, int path, double x, double E
         const float2 nx = solve_line(t);
         v.fit[b] = make_float4(line.x, line.y, nx.x, nx.y);
     }
-    if (in) {
-        const double D = i + 1 < n ? dl[i + 1] - del : 0.0;
-        tl[i] = make_float2(l2f, (float)del);
-        td[i] = make_float2((float)(del - D), (float)D);   // (delta_j - D_j, D_j)
+    if constexpr (Q) {
+        if (in) {
+            const double eps = del + lam;
+            const double De = i + 1 < n ? dl[i + 1] - eps : 0.0;
+            const double Dl = i + 1 < n ? dl2[i + 1] - l2 : 0.0;
+            tl[i] = make_float2(l2f, (float)del);
+            v.tq[(long long)b * n + i] = make_float4((float)(eps - De), (float)De, (float)(l2 - Dl), (float)Dl);
+            v.tlam[(long long)b * n + i] = (float)lam;
+        }
+    } else {
+        if (in) {
+            const double D = i + 1 < n ? dl[i + 1] - del : 0.0;
+            tl[i] = make_float2(l2f, (float)del);
+            td[i] = make_float2((float)(del - D), (float)D);   // (delta_j - D_j, D_j)
+        }
     }
     if (i < 4) tl[n + i] = make_float2(-2000.f, 0.f);
     return bad;
@@ -439,8 +481,10 @@ __global__ void __launch_bounds__(KX_FIN_THREADS)
     const double x = in ? f[(long long)b * n + threadIdx.x] : 0.0;
     // an instance that has been evaluated already keeps the line of its tables
     const int mode = (st && st[b].evals > 0) ? KX_LINE_SAME : KX_LINE_FIT;
-    int bad = kx_prep_block(n, path, x, in ? E[threadIdx.x] : 0.0, in ? h[threadIdx.x] : 0.0, E[0],
-                            v, b, smem, KX_KEY_NONE, mode);
+    const double Ei = in ? E[threadIdx.x] : 0.0, hi = in ? h[threadIdx.x] : 0.0;
+    int bad = (path == KX_FP32 && v.eta)
+                  ? kx_prep_block<true>(n, path, x, Ei, hi, E[0], v, b, smem, KX_KEY_NONE, mode)
+                  : kx_prep_block<false>(n, path, x, Ei, hi, E[0], v, b, smem, KX_KEY_NONE, mode);
     if (threadIdx.x == 0) v.flags[b] = bad;
 }
 
@@ -599,6 +643,64 @@ __device__ __forceinline__ void kx_vector_terms(const float4 wv, const uint4 pv,
     }
 }
 
+// The same four elements with the quantum statistical factor (eq.
+// Lambda_quantum): f_n f_m (1 + eta f_i)(1 + eta f_t) - f_i f_t (1 + eta f_n)(1 + eta f_m)
+// = 2^a (1 - 2^d) with, in units of f_max^2 (lambda = log2(1 + eta f)),
+//   a = l2_n + l2_m + lambda_i + lambda_t,
+//   d = (g_i + eps_t - lambda_t) - g_n - g_m  (g: deviation of l2 - lambda from
+//   the reference line, eps_t the interpolated deviation of l2 from it), and
+//   f_t from the log interpolation of f (l2_t), lambda_t = log2(1 + eta f_max 2^l2_t).
+// lamn = l2 tables' row constant lambda_i, efm = eta f_max (FP32).
+template <int BP>
+__device__ __forceinline__ void kx_vector_terms_q(const float4 wv, const uint4 pv, const uint32_t nvw,
+                                                  const float2 (*s_l)[KX_MAX_N + 4],
+                                                  const float4 (*s_q)[KX_MAX_N], const float *di,
+                                                  const float *lami, const float *efm,
+                                                  const int *so, float *acc) {
+    const int nn = nvw & 0xffff, m0 = nvw >> 16;
+    const float wk[4] = {wv.x, wv.y, wv.z, wv.w};
+    const uint32_t pw[4] = {pv.x, pv.y, pv.z, pv.w};
+#pragma unroll
+    for (int bb = 0; bb < BP; ++bb) {
+        const float2 ln = s_l[bb][nn];
+        const float cn = di[bb] - ln.y;
+        const float an = ln.x + lami[bb];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const float2 lm = s_l[bb][m0 + so[q]];
+            const float4 dj = s_q[bb][pw[q] >> 23];
+            const float opo = kx_one_plus_omega(pw[q]);
+            const float et = fmaf(opo, dj.y, dj.x);   // eps_t
+            const float lt = fmaf(opo, dj.w, dj.z);   // l2_t
+            // lambda_t; a non-positive 1 + eta f_t (Fermi-Dirac at f_t >= 1) takes the floor
+            const float lamt = fmaxf(kx_lg2(fmaf(efm[bb], kx_ex2(lt), 1.f)), -100.f);
+            const float a = (an + lm.x) + lamt;
+            const float d = ((cn + et) - lamt) - lm.y;
+            acc[bb] = fmaf(wk[q], kx_bracket_term(a, d), acc[bb]);
+        }
+    }
+}
+
+// Quantum statistics: the per-instance interpolation tables, lambda_i and
+// eta f_max (FP32 path with v.eta != 0).
+template <int BP>
+__device__ __forceinline__ void kx_stream_tables_q(int n, int b0, const bool *act,
+                                                   const float4 *__restrict__ tq,
+                                                   const float *__restrict__ tlam,
+                                                   const double *__restrict__ fmax, int eta,
+                                                   float4 (*s_q)[KX_MAX_N], float (*s_lam)[KX_MAX_N],
+                                                   float *efm) {
+#pragma unroll
+    for (int bb = 0; bb < BP; ++bb) {
+        const int b = b0 + bb;
+        for (int t = threadIdx.x; t < n; t += blockDim.x) {
+            s_q[bb][t] = act[bb] ? tq[(long long)b * n + t] : make_float4(0.f, 0.f, -2000.f, 0.f);
+            s_lam[bb][t] = act[bb] ? tlam[(long long)b * n + t] : 0.f;
+        }
+        efm[bb] = act[bb] ? (float)((double)eta * fmax[b]) : 0.f;
+    }
+}
+
 // Lane-level end of a task: fixed shuffle tree over the double-float sums and
 // the (hi, lo) partial into the task's slot.
 template <int BP>
@@ -632,7 +734,7 @@ struct kx_unit {
 
 // Loads the instances' (l2, delta) and (delta - D, D) tables into shared
 // memory; returns false if no instance of the block is active.
-template <int BP>
+template <int BP, bool WITH_D = true>
 __device__ __forceinline__ bool kx_stream_tables(int n, int B, int b0, const float2 *__restrict__ tl,
                                                  const float2 *__restrict__ td,
                                                  const kx_inst_state *__restrict__ st, int stage,
@@ -651,8 +753,9 @@ __device__ __forceinline__ bool kx_stream_tables(int n, int B, int b0, const flo
         const int b = b0 + bb;
         for (int t = threadIdx.x; t < n + 4; t += blockDim.x)
             s_l[bb][t] = act[bb] ? tl[(long long)b * (n + 4) + t] : make_float2(-2000.f, 0.f);
-        for (int t = threadIdx.x; t < n; t += blockDim.x)
-            s_d[bb][t] = act[bb] ? td[(long long)b * n + t] : make_float2(0.f, 0.f);
+        if constexpr (WITH_D)
+            for (int t = threadIdx.x; t < n; t += blockDim.x)
+                s_d[bb][t] = act[bb] ? td[(long long)b * n + t] : make_float2(0.f, 0.f);
     }
     return true;
 }
@@ -661,16 +764,22 @@ __device__ __forceinline__ bool kx_stream_tables(int n, int B, int b0, const flo
 // Work split as in k_stream32 below (units of 32 x VPL kept vectors, tasks from
 // the task table); each warp holds the next unit's tables in registers while
 // it computes the current one.
-template <int BP, int VPL>
+// Q: quantum statistics (tq, tlam, fmax, eta used; td unused).
+template <int BP, int VPL, bool Q = false>
 __global__ void __launch_bounds__(KX_T32)
     k_stream32r(int n, const int *__restrict__ bins, const int4 *__restrict__ task,
                 const int *__restrict__ roff, int B,
                 const uint32_t *__restrict__ vt, const float4 *__restrict__ W,
                 const uint4 *__restrict__ PK, const float2 *__restrict__ tl,
                 const float2 *__restrict__ td, float2 *__restrict__ partial, int pstride,
-                const kx_inst_state *__restrict__ st, int stage) {
+                const kx_inst_state *__restrict__ st, int stage,
+                const float4 *__restrict__ tq, const float *__restrict__ tlam,
+                const double *__restrict__ fmax, int eta) {
     __shared__ float2 s_l[BP][KX_MAX_N + 4];   // (l2_j, delta_j)
-    __shared__ float2 s_d[BP][KX_MAX_N];       // (delta_j - D_j, D_j), D_j = delta_{j+1} - delta_j
+    __shared__ float2 s_d[Q ? 1 : BP][Q ? 1 : KX_MAX_N];   // (delta_j - D_j, D_j), D_j = delta_{j+1} - delta_j
+    __shared__ float4 s_q[Q ? BP : 1][Q ? KX_MAX_N : 1];   // quantum: (eps_j - De_j, De_j, l2_j - Dl_j, Dl_j)
+    __shared__ float s_lam[Q ? BP : 1][Q ? KX_MAX_N : 1];  // quantum: lambda_j
+    __shared__ float s_efm[BP];                            // quantum: eta f_max
     kx_pdl_trigger();
     const int b0 = blockIdx.y * BP;
     const int lane = threadIdx.x & 31;
@@ -720,15 +829,25 @@ __global__ void __launch_bounds__(KX_T32)
     }
     kx_pdl_wait();
     bool act[BP];
-    if (!kx_stream_tables<BP>(n, B, b0, tl, td, st, stage, s_l, s_d, act)) return;
+    if constexpr (Q) {
+        // s_d is not used: the quantum tables replace it
+        if (!kx_stream_tables<BP, false>(n, B, b0, tl, nullptr, st, stage, s_l, nullptr, act)) return;
+        kx_stream_tables_q<BP>(n, b0, act, tq, tlam, fmax, eta, s_q, s_lam, s_efm);
+    } else {
+        if (!kx_stream_tables<BP>(n, B, b0, tl, td, st, stage, s_l, s_d, act)) return;
+    }
     __syncthreads();
+    float efm[BP];
+#pragma unroll
+    for (int bb = 0; bb < BP; ++bb) efm[bb] = Q ? s_efm[bb] : 0.f;
     while (have) {
-        float hi[BP], lo[BP], di[BP];
+        float hi[BP], lo[BP], di[BP], lami[BP];
 #pragma unroll
         for (int bb = 0; bb < BP; ++bb) {
             hi[bb] = 0.f;
             lo[bb] = 0.f;
             di[bb] = s_l[bb][u.i].y;
+            lami[bb] = Q ? s_lam[bb][u.i] : 0.f;
         }
         const int tslot = u.slot;
         for (;;) {
@@ -759,8 +878,14 @@ __global__ void __launch_bounds__(KX_T32)
             float acc[BP];
 #pragma unroll
             for (int bb = 0; bb < BP; ++bb) acc[bb] = 0.f;
+            if constexpr (Q) {
 #pragma unroll
-            for (int e = 0; e < VPL; ++e) kx_vector_terms<BP>(wc[e], pc[e], nc[e], s_l, s_d, di, so, acc);
+                for (int e = 0; e < VPL; ++e)
+                    kx_vector_terms_q<BP>(wc[e], pc[e], nc[e], s_l, s_q, di, lami, efm, so, acc);
+            } else {
+#pragma unroll
+                for (int e = 0; e < VPL; ++e) kx_vector_terms<BP>(wc[e], pc[e], nc[e], s_l, s_d, di, so, acc);
+            }
 #pragma unroll
             for (int bb = 0; bb < BP; ++bb) kx_df_add(hi[bb], lo[bb], acc[bb]);
             u = nx;
@@ -995,23 +1120,24 @@ static cudaError_t kx_launch_stream(const kx_kernel *k, int B, const kx_batch_vi
                         reinterpret_cast<float2 *>(v.partial), v.chunks, st, stage, v.err);
 }
 
-template <int BP, int VPL>
+template <int BP, int VPL, bool Q = false>
 static cudaError_t kx_launch_stream_r(const kx_kernel *k, int B, const kx_batch_views &v,
                                       const kx_inst_state *st, int stage, cudaStream_t s,
                                       bool pdl = false) {
     int occ = 0;
-    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_stream32r<BP, VPL>, KX_T32, 0);
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_stream32r<BP, VPL, Q>, KX_T32, 0);
     if (e != cudaSuccess) return e;
     if (occ < 1) occ = 1;
     const int sms = g_sms > 0 ? g_sms : 148;
     const int groups = (B + BP - 1) / BP;
     const int blocks = kx_bin_blocks(occ * sms, groups);
     dim3 grid(blocks, groups);
-    return kx_launch_ex(k_stream32r<BP, VPL>, grid, dim3(KX_T32), 0, s, pdl, k->n,
+    return kx_launch_ex(k_stream32r<BP, VPL, Q>, grid, dim3(KX_T32), 0, s, pdl, k->n,
                         (const int *)k->d_bins, (const int4 *)k->d_task, (const int *)k->d_roff, B,
                         (const uint32_t *)k->d_vt, reinterpret_cast<const float4 *>(k->d_W32),
                         reinterpret_cast<const uint4 *>(k->d_pk), (const float2 *)v.tl,
-                        (const float2 *)v.td, reinterpret_cast<float2 *>(v.partial), v.chunks, st, stage);
+                        (const float2 *)v.td, reinterpret_cast<float2 *>(v.partial), v.chunks, st, stage,
+                        (const float4 *)v.tq, (const float *)v.tlam, (const double *)v.fmax, v.eta);
 }
 
 // ------------------------------------------------------------ autotuner
@@ -1050,6 +1176,10 @@ static int kx_stream_variant(const kx_kernel *k, int B) {
 static cudaError_t kx_stream_launch(int variant, const kx_kernel *k, int B, const kx_batch_views &v,
                                     const kx_inst_state *st, int stage, cudaStream_t s,
                                     bool pdl = false) {
+    // quantum statistics: one instance per pass (the only instantiation)
+    if (k->stats)
+        return k->vpl == 2 ? kx_launch_stream_r<1, 2, true>(k, B, v, st, stage, s, pdl)
+                           : kx_launch_stream_r<1, 4, true>(k, B, v, st, stage, s, pdl);
     if (k->vpl == 2) {
         if (variant == 3) return kx_launch_stream_r<4, 2>(k, B, v, st, stage, s, pdl);
         return variant == 1 ? kx_launch_stream_r<2, 2>(k, B, v, st, stage, s, pdl)
@@ -1084,7 +1214,7 @@ __global__ void k_hold(unsigned long long ns) {
 // Heun stages.
 int kx_tune_contraction(const kx_kernel *k, int B, const double *f, const kx_batch_views &v,
                         const kx_inst_state *st, cudaStream_t s, long long *launches) {
-    if (k->precision != KX_FP32) return 0;
+    if (k->precision != KX_FP32 || k->stats) return 0;   // quantum statistics: one variant
     int dev = 0;
     cudaGetDevice(&dev);
     const auto key = std::make_tuple(dev, k->n, B);
@@ -1458,6 +1588,7 @@ cudaError_t kx_launch_mbfit(const kx_kernel *k, int nb, const double *f, double 
 //          reject, next h, MB stopping test, prep(next f).
 // One instance's stage in one block (thread = grid point; smem: 5 blockDim.x +
 // 8 doubles).  Every exit is block-uniform.
+template <bool Q>
 __device__ __forceinline__ void kx_stage_body(int b, int n, int chunks, int path, const double *__restrict__ E,
                               const double *__restrict__ h, kx_batch_views v,
                               kx_step_views sv, int stage, long long max_attempts,
@@ -1575,7 +1706,7 @@ __device__ __forceinline__ void kx_stage_body(int b, int n, int chunks, int path
             fp[i] = fpi;
         }
         if (threadIdx.x == 0) st->evals += 1;
-        int bad2 = kx_prep_block(n, path, in ? fpi : 0.0, Ei, hi, E0, v, b, smem, keys[1], KX_LINE_NEXT);
+        int bad2 = kx_prep_block<Q>(n, path, in ? fpi : 0.0, Ei, hi, E0, v, b, smem, keys[1], KX_LINE_NEXT);
         if (threadIdx.x == 0) v.flags[b] = bad2;
         return;
     }
@@ -1672,27 +1803,29 @@ __device__ __forceinline__ void kx_stage_body(int b, int n, int chunks, int path
         }
     }
     // prepare the next attempt's contraction input (f_new or the restored f)
-    int bad2 = kx_prep_block(n, path, in ? fnew : 0.0, Ei, hi, E0, v, b, smem, accept ? keys[1] : keys[2],
-                             KX_LINE_NEXT);
+    int bad2 = kx_prep_block<Q>(n, path, in ? fnew : 0.0, Ei, hi, E0, v, b, smem, accept ? keys[1] : keys[2],
+                                KX_LINE_NEXT);
     if (threadIdx.x == 0) v.flags[b] = bad2;
 }
 
 // PATH >= 0: an instantiation for that path alone (the FP32 path's, which holds
 // only its own prep: a smaller kernel, and a register allocation that the
 // other paths' code does not move); PATH = -1: the path is the argument.
-template <int PATH>
+// Q: the FP32 path with quantum statistics.
+template <int PATH, bool Q = false>
 __global__ void __launch_bounds__(KX_FIN_THREADS)
     k_stage(int n, int chunks, int path, const double *__restrict__ E, const double *__restrict__ h,
             kx_batch_views v, kx_step_views sv, int stage, long long max_attempts) {
     __shared__ double smem[5 * KX_FIN_THREADS + 8];
     kx_pdl_trigger();
     kx_pdl_wait();
-    kx_stage_body(blockIdx.x, n, chunks, PATH >= 0 ? PATH : path, E, h, v, sv, stage, max_attempts, smem);
+    kx_stage_body<Q>(blockIdx.x, n, chunks, PATH >= 0 ? PATH : path, E, h, v, sv, stage, max_attempts, smem);
 }
 
 cudaError_t kx_launch_stage(const kx_kernel *k, int B, const kx_batch_views &v,
                             const kx_step_views &sv, int stage, cudaStream_t s, bool pdl) {
-    auto *fn = k->precision == KX_FP32 ? k_stage<KX_FP32> : k_stage<-1>;
+    auto *fn = k->precision != KX_FP32 ? k_stage<-1>
+                                       : (k->stats ? k_stage<KX_FP32, true> : k_stage<KX_FP32>);
     return kx_launch_ex(fn, dim3(B), dim3(kx_fin_threads(k->n)), 0, s, pdl, k->n, v.chunks,
                         (int)k->precision, (const double *)k->d_E, (const double *)k->d_h, v, sv,
                         stage, sv.max_attempts);

@@ -33,7 +33,7 @@ struct kx_kernel {
     int refcount;
     int device;
     int n, n_mu, measure, precision;
-    int stats;           // 0 dilute, +1 Bose-Einstein, -1 Fermi-Dirac (FP64 path)
+    int stats;           // 0 dilute, +1 Bose-Einstein, -1 Fermi-Dirac (FP64 and FP32 paths)
     double a, mass;
     long long P;         // pairs n <= m: n(n+1)/2
     int V;               // 4-element vectors per row (FP32 layout, segments padded to 4)
@@ -126,6 +126,10 @@ struct kx_batch_views {
     float2 *tl;            // [B][n + 4]   FP32 path: (l2_j, delta_j), l2 = log2(max(f, floor)/f_max)
     float2 *td;            // FP32 path: [B][n] (delta_j - D_j, D_j), D_j = delta_{j+1} - delta_j;
                            // split path: [n][B] (l2_j, D_j), D_j = l2_{j+1} - l2_j (instance-minor)
+    float4 *tq;            // FP32 path with quantum statistics: [B][n] (eps_j - De_j, De_j,
+                           //   l2_j - Dl_j, Dl_j), eps = l2 - line, De/Dl forward differences
+    float *tlam;           // FP32 path with quantum statistics: [B][n] lambda_j = log2(1 + eta f_j)
+    int eta;               // quantum statistics of the kernel: 0 dilute, +1 BE, -1 FD
     double2 *partial;      // [B][n][chunks]  (FP32 path: float2 (hi, lo) task partials, [B][chunks])
     const int2 *rtask;     // FP32 path: [n] (first partial slot, tasks) per row
     double *rfmax;         // [B]          1 / f_max

@@ -134,7 +134,7 @@ def test_build_rejects_bad_grids(ctx, kx):
     with pytest.raises(kx.KxError):
         ctx.build_kernel(ki.log_grid(16, 1e-3, 10.0), mass=0.0)
     with pytest.raises(kx.KxError) as ei:
-        ctx.build_kernel(ki.log_grid(16, 1e-3, 10.0), stats=1, precision=kx.FP32)
+        ctx.build_kernel(ki.log_grid(16, 1e-3, 10.0), stats=1, precision=kx.SPLIT_TF32)
     assert ei.value.code == kx.ENOTSUP
     with pytest.raises(kx.KxError):
         ctx.build_kernel(ki.log_grid(16, 1e-3, 10.0), stats=2)
@@ -528,6 +528,85 @@ def test_quantum_statistics_fp64_path_matches_oracle(ctx, kx, eta):
     scale = oracle.M2_from_sigma(1.0, 1.0) * np.max(G)
     assert np.max(np.abs(C.cpu().numpy()[0] - Co)) <= 1e-13 * scale
     assert np.max(np.abs(Co)) < 2e-2 * scale
+    k.release()
+
+
+@pytest.mark.parametrize("eta", [1, -1])
+def test_quantum_statistics_fp32_path_matches_oracle(ctx, kx, eta):
+    """The FP32 streaming path with the Bose-Einstein / Fermi-Dirac factor
+    (eq. Lambda_quantum; per element 2^a (1 - 2^d) with the line fitted to
+    log2 f/(1 + eta f)): C raw and projected within the mixed-precision
+    tolerance of the oracle, instances bit-identical alone and in the batch,
+    and the equilibrium of that statistics near its fixed point."""
+    N = 40
+    q = ki.log_grid(N, 1e-2, 20.0)
+    g = oracle.grid(q)
+    W = oracle.kernel_tensor(q)
+    f = 0.8 * ki.batch_bimodal(np.random.default_rng(53 + eta), q, 3)
+    sig = np.array([1.0, 3.0, 0.5])
+    k = ctx.build_kernel(q, precision=kx.FP32, stats=eta)
+    for project in (0, 1):
+        C, _ = ctx.collision(k, dev(f), sig, project=bool(project))
+        C = C.cpu().numpy()
+        for b in range(3):
+            Co = oracle.collision_tensor_stats(q, W, f[b], eta) * oracle.M2_from_sigma(1.0, sig[b])
+            if project:
+                Co, _ = oracle.project(g["E"], g["h"], f[b], Co)
+            assert relerr(C[b], Co) <= TOL[1], (project, b, relerr(C[b], Co))
+        if project:
+            C1, _ = ctx.collision(k, dev(f[1:2]), sig[1:2], project=True)
+            np.testing.assert_array_equal(C1.cpu().numpy()[0], C[1])
+    feq = 1.0 / (np.exp((g["E"] - 0.6) / 0.7) - eta)
+    C, _ = ctx.collision(k, dev(feq[None]), 1.0, project=False)
+    Co = oracle.collision_tensor_stats(q, W, feq, eta) * oracle.M2_from_sigma(1.0, 1.0)
+    _, G, _ = oracle.collision_tensor(q, W, feq, parts=True)
+    scale = oracle.M2_from_sigma(1.0, 1.0) * np.max(G)
+    assert np.max(np.abs(C.cpu().numpy()[0] - Co)) <= 1e-6 * scale
+    k.release()
+
+
+def test_quantum_statistics_fp32_paper_benchmark_distribution(ctx, kx):
+    """The paper's runtime workload (eq. benchmark_two_bump: m = 1, a = 1,
+    q in [1e-3, 1e2], N = 96, Bose-Einstein factors, no projection) on the FP32
+    path against the oracle."""
+    q = ki.log_grid(96, 1e-3, 1e2)
+    f = ki.paper_two_bump(q)
+    W = oracle.kernel_tensor(q)
+    Co = oracle.collision_tensor_stats(q, W, f, 1) * oracle.M2_from_sigma(1.0, 1.0)
+    for prec, tol in ((kx.FP32, TOL[1]), (kx.FP64, TOL[0])):
+        k = ctx.build_kernel(q, precision=prec, stats=1)
+        C, _ = ctx.collision(k, dev(f[None]), 1.0, project=False)
+        assert relerr(C.cpu().numpy()[0], Co) <= tol, (prec, relerr(C.cpu().numpy()[0], Co))
+        k.release()
+
+
+def test_quantum_statistics_fp32_fixed_step_solve(ctx, kx):
+    """Twenty fixed Heun steps with Bose-Einstein factors on the FP32 path
+    against the same steps taken with the oracle's operator and projection;
+    number and energy conserved to the mixed-precision bound."""
+    c = ki.config1()
+    q, f0 = c["q"], c["f0"]
+    g = oracle.grid(q)
+    W = oracle.kernel_tensor(q)
+    M2 = oracle.M2_from_sigma(1.0, c["sigma"])
+    h, steps = c["h"], 20
+
+    def rhs(f):
+        return oracle.project(g["E"], g["h"], f, oracle.collision_tensor_stats(q, W, f, 1) * M2)[0]
+
+    fo = f0.copy()
+    for _ in range(steps):
+        k1 = rhs(fo)
+        fp = fo + h * k1
+        fo = fo + 0.5 * h * (k1 + rhs(fp))
+    k = ctx.build_kernel(q, precision=kx.FP32, stats=1)
+    fd = dev(f0[None])
+    res = ctx.solve(k, fd, c["sigma"], t_end=steps * h, h0=h, fixed_step=1)
+    f = fd.cpu().numpy()[0]
+    assert res[0]["status"] == 0 and res[0]["steps"] == steps
+    assert relerr(f, fo) <= TOL[1], relerr(f, fo)
+    for w in (g["h"], g["h"] * g["E"]):
+        assert abs(np.sum(w * f) / np.sum(w * f0) - 1) < 1e-7
     k.release()
 
 

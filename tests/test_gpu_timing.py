@@ -51,3 +51,20 @@ def test_rotating_timing_rejects_mixed_sizes(env):
         ctx.time_contractions([], f)
     k1.release()
     k2.release()
+
+
+@pytest.mark.parametrize("precision,stats", [("FP32", 0), ("FP64", 0), ("SPLIT_TF32", 0), ("FP32", 1)])
+def test_time_collision_output_is_the_collision(env, precision, stats):
+    """kx_time_collision replays the evaluation kx_collision makes: the C it
+    leaves is bit-identical to kx_collision's, with and without projection."""
+    kx, ctx, torch = env
+    q = ki.log_grid(36, 1e-3, 1e2)
+    f = torch.as_tensor(0.8 * ki.batch_bimodal(np.random.default_rng(6), q, 2), device="cuda")
+    sig = np.array([1.0, 2.5])
+    k = ctx.build_kernel(q, precision=getattr(kx, precision), stats=stats)
+    for project in (False, True):
+        ms, C = ctx.time_collision(k, f, sig, project=project, iters=3)
+        ref, _ = ctx.collision(k, f, sig, project=project)
+        assert 0.0 < ms < 1e3
+        np.testing.assert_array_equal(C.cpu().numpy(), ref.cpu().numpy())
+    k.release()
