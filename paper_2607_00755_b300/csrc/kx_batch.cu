@@ -70,6 +70,24 @@ __device__ __forceinline__ float kx_ex2f(float x) {
     asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
     return y;
 }
+// Packed pairs of FP32 values (.f32x2): the per-lane arithmetic is that of the
+// scalar fma (round to nearest, no flush), two values per instruction.
+__device__ __forceinline__ unsigned long long kx_pk2(float lo, float hi) {
+    unsigned long long r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+    return r;
+}
+__device__ __forceinline__ float2 kx_upk2(unsigned long long v) {
+    float2 r;
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(r.x), "=f"(r.y) : "l"(v));
+    return r;
+}
+__device__ __forceinline__ unsigned long long kx_fma2(unsigned long long a, unsigned long long b,
+                                                      unsigned long long c) {
+    unsigned long long d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
+}
 // --------------------------------------------------------- gain GEMM (fused)
 // One CTA (4 warps) per (128-row M tile of W_full, N tile of up to 256
 // instances), two CTAs per SM.  Thread 0 stages the hi/lo operand tiles of each
@@ -314,9 +332,13 @@ __global__ void __launch_bounds__(WARPS * 32, (WARPS <= 16 && IPL <= 2) ? 2 : 1)
     // this warp's segments of row i (balanced across the warps by the host)
     const int gend = lsw[i * WARPS + warp + 1];
     int g = lsw[i * WARPS + warp];
-    float hi[IPL], lo[IPL], a[IPL][4];
+    float hi[IPL], lo[IPL];
 #pragma unroll
-    for (int s = 0; s < IPL; ++s) hi[s] = lo[s] = a[s][0] = a[s][1] = a[s][2] = a[s][3] = 0.f;
+    for (int s = 0; s < IPL; ++s) hi[s] = lo[s] = 0.f;
+    // a[s][0..3] live as two packed pairs (elements 0, 1 and 2, 3 of each four)
+    unsigned long long a2[IPL][2];
+#pragma unroll
+    for (int s = 0; s < IPL; ++s) a2[s][0] = a2[s][1] = kx_pk2(0.f, 0.f);
     int na = 0;   // elements in the FP32 sums since the last flush
     // descriptors run two segments ahead of the compute, elements one
     int2 dsc = make_int2(0, 0), dn = dsc;
@@ -352,19 +374,29 @@ __global__ void __launch_bounds__(WARPS * 32, (WARPS <= 16 && IPL <= 2) ? 2 : 1)
                 t[2 * h + 1] = make_float2(q.z, q.w);
             }
         }
-        // two elements (S, omega) per float4; a running pointer keeps the loop's
-        // address arithmetic to one add per four elements
+        // a pair of elements per float4, stored (S_0, S_1, omega_0, omega_1); per
+        // pair and instance one packed FMA for the two exponents, two ex2 and one
+        // packed FMA for the weights.  A running pointer keeps the loop's address
+        // arithmetic to one add per four elements.
+        unsigned long long tD[IPL], tL[IPL];
+#pragma unroll
+        for (int s = 0; s < IPL; ++s) {
+            tD[s] = kx_pk2(t[s].y, t[s].y);
+            tL[s] = kx_pk2(t[s].x, t[s].x);
+        }
         const float4 *pe = reinterpret_cast<const float4 *>(s_el[warp]);
         const float4 *const pend = pe + (c4 >> 1);
 #pragma unroll 2
         for (; pe < pend; pe += 2) {
             const float4 x01 = pe[0], x23 = pe[1];
+            const unsigned long long s01 = kx_pk2(x01.x, x01.y), w01 = kx_pk2(x01.z, x01.w);
+            const unsigned long long s23 = kx_pk2(x23.x, x23.y), w23 = kx_pk2(x23.z, x23.w);
 #pragma unroll
             for (int s = 0; s < IPL; ++s) {
-                a[s][0] = fmaf(x01.x, kx_ex2f(fmaf(x01.y, t[s].y, t[s].x)), a[s][0]);
-                a[s][1] = fmaf(x01.z, kx_ex2f(fmaf(x01.w, t[s].y, t[s].x)), a[s][1]);
-                a[s][2] = fmaf(x23.x, kx_ex2f(fmaf(x23.y, t[s].y, t[s].x)), a[s][2]);
-                a[s][3] = fmaf(x23.z, kx_ex2f(fmaf(x23.w, t[s].y, t[s].x)), a[s][3]);
+                const float2 e01 = kx_upk2(kx_fma2(w01, tD[s], tL[s]));
+                const float2 e23 = kx_upk2(kx_fma2(w23, tD[s], tL[s]));
+                a2[s][0] = kx_fma2(s01, kx_pk2(kx_ex2f(e01.x), kx_ex2f(e01.y)), a2[s][0]);
+                a2[s][1] = kx_fma2(s23, kx_pk2(kx_ex2f(e23.x), kx_ex2f(e23.y)), a2[s][1]);
             }
         }
         // the FP32 sums go into the double-float accumulator once they hold at
@@ -373,11 +405,12 @@ __global__ void __launch_bounds__(WARPS * 32, (WARPS <= 16 && IPL <= 2) ? 2 : 1)
         if (na >= KX_SEG) {
 #pragma unroll
             for (int s = 0; s < IPL; ++s) {
+                const float2 p = kx_upk2(a2[s][0]), q = kx_upk2(a2[s][1]);
                 float sm, er;
-                kx_two_sum_f(hi[s], (a[s][0] + a[s][1]) + (a[s][2] + a[s][3]), sm, er);
+                kx_two_sum_f(hi[s], (p.x + p.y) + (q.x + q.y), sm, er);
                 hi[s] = sm;
                 lo[s] += er;
-                a[s][0] = a[s][1] = a[s][2] = a[s][3] = 0.f;
+                a2[s][0] = a2[s][1] = kx_pk2(0.f, 0.f);
             }
             na = 0;
         }
@@ -389,8 +422,9 @@ __global__ void __launch_bounds__(WARPS * 32, (WARPS <= 16 && IPL <= 2) ? 2 : 1)
     }
 #pragma unroll
     for (int s = 0; s < IPL; ++s) {
+        const float2 p = kx_upk2(a2[s][0]), q = kx_upk2(a2[s][1]);
         float sm, er;
-        kx_two_sum_f(hi[s], (a[s][0] + a[s][1]) + (a[s][2] + a[s][3]), sm, er);
+        kx_two_sum_f(hi[s], (p.x + p.y) + (q.x + q.y), sm, er);
         hi[s] = sm;
         lo[s] += er;
     }
@@ -565,8 +599,12 @@ int kx_batch_build_tables(kx_ctx *ctx, kx_kernel *k) {
                 const size_t p0 = seg[q].first, p1 = seg[q].second;
                 const int c4 = (int)((p1 - p0 + 3) & ~(size_t)3);
                 lseg.push_back(make_int2((int)lel.size(), (row[p0].j << 8) | c4));
-                for (size_t e = p0; e < p1; ++e) lel.push_back(make_float2(row[e].w, row[e].om));
-                for (size_t e = p1 - p0; e < (size_t)c4; ++e) lel.push_back(make_float2(0.f, 0.f));
+                // element pairs as (S_0, S_1), (omega_0, omega_1); zero padding
+                for (size_t e = 0; e < (size_t)c4; e += 2) {
+                    const bool v0 = p0 + e < p1, v1 = p0 + e + 1 < p1;
+                    lel.push_back(make_float2(v0 ? row[p0 + e].w : 0.f, v1 ? row[p0 + e + 1].w : 0.f));
+                    lel.push_back(make_float2(v0 ? row[p0 + e].om : 0.f, v1 ? row[p0 + e + 1].om : 0.f));
+                }
             }
         }
         rlen[i] = (int)row.size();

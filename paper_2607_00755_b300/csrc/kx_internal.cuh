@@ -62,7 +62,8 @@ struct kx_kernel {
     int Mpad;            // n^2 rows (i, n) padded to a multiple of 128
     int Kpad;            // n columns (m) padded to a multiple of 32
     float *d_Atile;      // [Mpad/128][Kpad/16][hi, lo][2048]: W_full as TF32 hi/lo in MMA operand tiles
-    float2 *d_lel;       // per row i: nonzero (S_inm, omega) sorted by j_L
+    float2 *d_lel;       // per row i: nonzero (S_inm, omega) sorted by j_L, element pairs as
+                         // (S_0, S_1), (omega_0, omega_1)
     int2 *d_lseg;        // segments of <= 64 elements of one j_L: (first element, j_L << 8 | count)
     int *d_lsw;          // [n * warps + 1] first segment of each (row, loss-kernel warp)
     int *d_lorder;       // [n] rows by element count, longest first
