@@ -402,13 +402,15 @@ extern "C" int kx_build_kernel(kx_ctx *ctx, const kx_grid_desc *d, kx_kernel **o
             }
         }
         bins[KX_BINS] = (int)task.size();
-        // partial slots: MT per row (the largest task count, rounded up to even
-        // for paired 16-byte reads), so that a row's slots sit at a fixed stride
+        // partial slots: MT per row (the largest task count, rounded up to
+        // even), slot k of row i at k n + i: a row's slots sit at a fixed
+        // stride and the rows of one slot index are adjacent (coalesced reads
+        // in the row combine)
         int MT = 2;
         for (int i = 0; i < n; ++i) MT = std::max(MT, (row_tasks[i] + 1) & ~1);
         std::vector<int2> rtask(n);
-        for (int i = 0; i < n; ++i) rtask[i] = make_int2(i * MT, row_tasks[i]);
-        for (auto &t : task) t.w += rtask[t.x].x;   // slot = row's first slot + index in the row
+        for (int i = 0; i < n; ++i) rtask[i] = make_int2(i, row_tasks[i]);
+        for (auto &t : task) t.w = t.w * n + t.x;   // slot = index in the row x n + row
         k->ntask = (int)task.size();
         k->tslots = n * MT;
         long long *by2 = &k->bytes;

@@ -1334,34 +1334,34 @@ __device__ __forceinline__ kx_row_out kx_combine_project(int n, int chunks, int 
     const double fm = v.fmax[b], rfm = v.rfmax[b], M2 = v.M2[b];
     double G = 0.0, L = 0.0;
     if (i < n && path == KX_FP32) {
-        // double-float task partials (hi, lo) in pairs per 16-byte load, four
-        // independent double-float sums combined in a fixed order.  Row i's
-        // slots are i MT .. i MT + MT - 1 of instance b (MT = chunks / n, even),
-        // the first rt.y of them written by its tasks: the addresses do not
-        // wait for the task count, which only masks the sums.
+        // double-float task partials (hi, lo), four independent double-float
+        // sums (slot k mod 4) combined in a fixed order.  Row i's slots are
+        // i + k n, k = 0 .. MT - 1, of instance b (MT = chunks / n): consecutive
+        // rows are adjacent, so each load is coalesced across the warp; the
+        // first rt.y of them are written by the row's tasks (the addresses do
+        // not wait for the task count, which only masks the sums).
         const int MT = chunks / n;
-        const float4 *pp = reinterpret_cast<const float4 *>(v.partial) +
-                           (((long long)b * chunks + (long long)i * MT) >> 1);
-        const int ntask = v.rtask[i].y, npair = MT >> 1;
+        const float2 *pp = reinterpret_cast<const float2 *>(v.partial) + (long long)b * chunks + i;
+        const int ntask = v.rtask[i].y;
         float h0 = 0.f, l0 = 0.f, h1 = 0.f, l1 = 0.f, h2 = 0.f, l2 = 0.f, h3 = 0.f, l3 = 0.f;
-        // batches of 12 pairs: the loads of a batch are in flight together
-        for (int c0 = 0; c0 < npair; c0 += 12) {
-            float4 x[12];
+        // batches of 24 slots: the loads of a batch are in flight together
+        for (int c0 = 0; c0 < MT; c0 += 24) {
+            float2 x[24];
+            const float2 *q = pp + (long long)c0 * n;
 #pragma unroll
-            for (int j = 0; j < 12; ++j)
-                x[j] = c0 + j < npair ? pp[c0 + j] : make_float4(0.f, 0.f, 0.f, 0.f);
+            for (int j = 0; j < 24; ++j, q += n) x[j] = c0 + j < MT ? *q : make_float2(0.f, 0.f);
 #pragma unroll
-            for (int j = 0; j < 12; j += 2) {
-                const int s0 = 2 * (c0 + j);   // slots s0 .. s0 + 3; those >= ntask hold no task
+            for (int j = 0; j < 24; j += 4) {
+                const int s0 = c0 + j;   // slots s0 .. s0 + 3; those >= ntask hold no task
                 const bool p0 = s0 >= ntask, p1 = s0 + 1 >= ntask, p2 = s0 + 2 >= ntask, p3 = s0 + 3 >= ntask;
                 kx_df_add(h0, l0, p0 ? 0.f : x[j].x);
                 l0 += p0 ? 0.f : x[j].y;
-                kx_df_add(h1, l1, p1 ? 0.f : x[j].z);
-                l1 += p1 ? 0.f : x[j].w;
-                kx_df_add(h2, l2, p2 ? 0.f : x[j + 1].x);
-                l2 += p2 ? 0.f : x[j + 1].y;
-                kx_df_add(h3, l3, p3 ? 0.f : x[j + 1].z);
-                l3 += p3 ? 0.f : x[j + 1].w;
+                kx_df_add(h1, l1, p1 ? 0.f : x[j + 1].x);
+                l1 += p1 ? 0.f : x[j + 1].y;
+                kx_df_add(h2, l2, p2 ? 0.f : x[j + 2].x);
+                l2 += p2 ? 0.f : x[j + 2].y;
+                kx_df_add(h3, l3, p3 ? 0.f : x[j + 3].x);
+                l3 += p3 ? 0.f : x[j + 3].y;
             }
         }
         kx_df_add(h0, l0, h1);

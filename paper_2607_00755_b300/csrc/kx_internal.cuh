@@ -51,7 +51,7 @@ struct kx_kernel {
     float *d_W32;        // [Vt][4], slots rotated by (k >> 2) & 3, k = index in the row
     uint32_t *d_pk;      // [Vt][4]: j_L << 23 | round(omega 2^23), same slots
     int *d_roff;         // [n + 1] first kept vector of each row
-    int2 *d_rtask;       // [n]: (first partial slot = i MT, tasks) of each row
+    int2 *d_rtask;       // [n]: (first partial slot = i, tasks) of each row; slot k at k n + i
     int4 *d_task;        // [ntask]: (row, first unit, end unit, partial slot)
     int *d_bins;         // [KX_BINS + 1]: first task of each equal-work bin
     long long Vt;        // kept vectors, all rows
@@ -132,7 +132,7 @@ struct kx_batch_views {
     float *tlam;           // FP32 path with quantum statistics: [B][n] lambda_j = log2(1 + eta f_j)
     int eta;               // quantum statistics of the kernel: 0 dilute, +1 BE, -1 FD
     double2 *partial;      // [B][n][chunks]  (FP32 path: float2 (hi, lo) task partials, [B][chunks])
-    const int2 *rtask;     // FP32 path: [n] (first partial slot, tasks) per row
+    const int2 *rtask;     // FP32 path: [n] (first partial slot i, tasks) per row; slot k at k n + i
     double *rfmax;         // [B]          1 / f_max
     float4 *fit;           // [B]          FP32 path: reference lines (icpt, slope) of the current
                            //              tables and of the fit of their f
