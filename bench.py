@@ -651,6 +651,11 @@ def main():
                 "fp64_path": fp64,
                 "speedup_vs_fp64": (value / fp64["value"]) if fp64 else None,
                 "failed_solves": len(bad),
+                "per_instance": [{"sigma": float(sig[b]), "steps": int(results[b]["steps"]),
+                                  "rejects": int(results[b]["rejects"]),
+                                  "evals": int(results[b]["evals"]), "t": results[b]["t"],
+                                  "l1_to_mb": results[b]["l1_to_mb"]}
+                                 for b in range(min(B, len(results)))],
                 "roofline": roof, "roofline_streaming_n384": roof384,
                 "roofline_streaming_n512": roof512,
                 "fixed_steps_n32": config1,
