@@ -279,6 +279,20 @@ int kx_server_get_stats(kx_server *srv, kx_server_stats *out);
 /* Finish the requests in flight, stop the worker and free the server. */
 void kx_server_stop(kx_server *srv);
 
+/* ------------------------------------------------------ fault injection */
+/* For tests of the failure paths, the environment variable KX_FAULT (read at
+ * each check; a comma-separated list) makes the host side of the library fail
+ * on purpose.  No injected failure touches the GPU: kernels never fault, trap
+ * or wait on anything that is not set.
+ *   alloc    every device allocation the library makes (context arena, kernel
+ *            tables) fails: KX_ENOMEM, with the message in kx_last_error;
+ *   admit    kx_submit refuses every request: KX_EADMIT;
+ *   nan      kx_collision_host and kx_solve_host stage f[0][0] = NaN after the
+ *            host->device copy: KX_ENONFINITE (in the diagnostics / the first
+ *            instance's result);
+ *   timeout  kx_solve and kx_solve_host stop polling at once: the graphs
+ *            already launched run to their end, then KX_ETIMEOUT. */
+
 /* ------------------------------------------------------------ profiling */
 /* Number of this library's kernels enqueued through `ctx` so far (a captured
  * graph counts each of its kernel nodes at every launch). */

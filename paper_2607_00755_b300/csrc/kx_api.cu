@@ -1,6 +1,7 @@
 // kx_api.cu -- host side of the C ABI declared in include/kx.h.
 #include <math.h>
 #include <string.h>
+#include <stdlib.h>
 
 #include <algorithm>
 #include <chrono>
@@ -16,6 +17,19 @@
 int kx_set_error(kx_ctx *ctx, int code, const std::string &msg) {
     if (ctx) ctx->last_error = msg;
     return code;
+}
+
+bool kx_fault(const char *what) {
+    const char *e = getenv("KX_FAULT");
+    if (!e || !*e) return false;
+    const size_t L = strlen(what);
+    for (const char *p = e;;) {
+        const char *q = strchr(p, ',');
+        const size_t len = q ? (size_t)(q - p) : strlen(p);
+        if (len == L && strncmp(p, what, L) == 0) return true;
+        if (!q) return false;
+        p = q + 1;
+    }
 }
 
 extern "C" const char *kx_strerror(int code) {
@@ -83,6 +97,7 @@ extern "C" int kx_set_stream(kx_ctx *ctx, void *cuda_stream) {
 
 static int kx_arena_reserve(kx_ctx *ctx, size_t bytes) {
     if (bytes <= ctx->arena_bytes) return KX_OK;
+    if (kx_fault("alloc")) return kx_set_error(ctx, KX_ENOMEM, "arena allocation failed (KX_FAULT=alloc)");
     KX_CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
     if (ctx->d_arena) cudaFree(ctx->d_arena);
     ctx->d_arena = nullptr;
@@ -240,6 +255,7 @@ template <typename T>
 static int kx_dev_alloc(kx_ctx *ctx, T **p, size_t count, long long *bytes) {
     *p = nullptr;
     if (count == 0) count = 1;
+    if (kx_fault("alloc")) return kx_set_error(ctx, KX_ENOMEM, "kernel table allocation failed (KX_FAULT=alloc)");
     if (cudaMalloc((void **)p, sizeof(T) * count) != cudaSuccess) {
         cudaGetLastError();
         return kx_set_error(ctx, KX_ENOMEM, "kernel table allocation failed");
@@ -595,6 +611,7 @@ extern "C" int kx_collision_host(kx_ctx *ctx, const kx_kernel *k, int B, const d
     double *d_C = (double *)((char *)ctx->d_arena + fb);
     cudaStream_t s = ctx->stream;
     KX_CUDA_TRY(ctx, cudaMemcpyAsync(d_f, f_host, sizeof(double) * B * k->n, cudaMemcpyHostToDevice, s));
+    if (kx_fault("nan")) KX_CUDA_TRY(ctx, cudaMemsetAsync(d_f, 0xff, sizeof(double), s));   // f[0][0] = NaN
     rc = kx_collision_impl(ctx, k, B, sigma, d_f, d_C, project, diag, 2 * fb);
     if (rc && rc != KX_ENONFINITE) return rc;
     KX_CUDA_TRY(ctx, cudaMemcpyAsync(C_host, d_C, sizeof(double) * B * k->n, cudaMemcpyDeviceToHost, s));
@@ -837,6 +854,7 @@ static int kx_solve_run(kx_ctx *ctx, const kx_kernel *k, int B, const kx_run &r,
     cudaEventCreateWithFlags(&ev[1], cudaEventDisableTiming);
     const long long max_launch = (long long)par->max_attempts / G + 2;
     const double wall_limit = 600.0;
+    const bool fault_timeout = kx_fault("timeout");
     long long launched = 0;
     auto launch_one = [&](int slot) -> cudaError_t {
         cudaError_t x = cudaGraphLaunch(exec, s);
@@ -853,6 +871,7 @@ static int kx_solve_run(kx_ctx *ctx, const kx_kernel *k, int B, const kx_run &r,
     for (long long g = 0; e == cudaSuccess; ++g) {
         const int slot = (int)(g & 1);
         for (;;) {  // bounded wait on the status copy of graph g
+            if (fault_timeout) { rc = KX_ETIMEOUT; break; }
             cudaError_t q = cudaEventQuery(ev[slot]);
             if (q == cudaSuccess) break;
             if (q != cudaErrorNotReady) { e = q; break; }
@@ -907,6 +926,7 @@ extern "C" int kx_solve_host(kx_ctx *ctx, const kx_kernel *k, int B, const doubl
         return rc;
     cudaStream_t s = ctx->stream;
     KX_CUDA_TRY(ctx, cudaMemcpyAsync(f, f_host, sizeof(double) * B * k->n, cudaMemcpyHostToDevice, s));
+    if (kx_fault("nan")) KX_CUDA_TRY(ctx, cudaMemsetAsync(f, 0xff, sizeof(double), s));   // f[0][0] = NaN
     int rc2 = kx_solve_run(ctx, k, B, r, par, res);
     if (rc2 == KX_ECUDA || rc2 == KX_ETIMEOUT) return rc2;
     KX_CUDA_TRY(ctx, cudaMemcpyAsync(f_host, f, sizeof(double) * B * k->n, cudaMemcpyDeviceToHost, s));

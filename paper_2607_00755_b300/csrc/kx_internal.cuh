@@ -111,6 +111,9 @@ struct kx_ctx {
 
 // error helpers ---------------------------------------------------------------
 int kx_set_error(kx_ctx *ctx, int code, const std::string &msg);
+// Host-side fault injection (KX_FAULT, a comma-separated list read at each
+// check): true if `what` is listed.  Nothing it does touches the GPU's state.
+bool kx_fault(const char *what);
 #define KX_CUDA_TRY(ctx, expr)                                                         \
     do {                                                                               \
         cudaError_t _e = (expr);                                                       \

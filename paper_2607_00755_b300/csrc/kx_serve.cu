@@ -572,7 +572,8 @@ extern "C" int kx_submit(kx_server *srv, const kx_grid_desc *grid, double sigma,
         }
     }
     r->key = kx_key(*r);
-    if (kx_group_estimate(srv->cfg, n) > (size_t)srv->cfg.hbm_budget_bytes) return KX_EADMIT;
+    if (kx_fault("admit") || kx_group_estimate(srv->cfg, n) > (size_t)srv->cfg.hbm_budget_bytes)
+        return KX_EADMIT;
     r->t_submit = kx_now();
     {
         std::lock_guard<std::mutex> lock(srv->mu);

@@ -500,6 +500,38 @@ def test_bench_workload_n128_four_sigmas_matches_oracle(ctx, kx):
         k.release()
 
 
+# ------------------------------------------------------- checkpoint / resume ---
+@pytest.mark.parametrize("precision", [0, 1])
+def test_solve_resumes_from_the_returned_state(ctx, kx, precision):
+    """A solve stopped by max_attempts returns (t, h) and leaves f on the
+    device; a second solve entered with t0 = t, h0 = h continues the same
+    trajectory (sources included): the plain FP64 path bit for bit, the FP32
+    path within its tolerance (its tables' reference line is refitted on
+    entry)."""
+    N = 40
+    q = ki.log_grid(N, 1e-3, 10.0)
+    f0 = ki.bimodal(np.random.default_rng(61), q)
+    src = ki.two_sources(q, t_scale=2.0)
+    k = ctx.build_kernel(q, precision=precision)
+    kw = dict(t_end=30.0, rtol=1e-6, atol=1e-12, l1_tol=0.0)
+    fa = dev(f0[None])
+    ra = ctx.solve(k, fa, 1.0, sources=src, h0=1e-3, **kw)[0]
+    assert ra["status"] == 0 and ra["steps"] > 40
+    K = (ra["steps"] + ra["rejects"]) // 2
+    fb = dev(f0[None])
+    r1 = ctx.solve(k, fb, 1.0, sources=src, h0=1e-3, max_attempts=K, **kw)[0]
+    assert r1["status"] == kx.ENOCONV and r1["steps"] + r1["rejects"] == K and r1["t"] < kw["t_end"]
+    r2 = ctx.solve(k, fb, 1.0, sources=src, t0=r1["t"], h0=r1["h"], **kw)[0]
+    assert r2["status"] == 0 and r2["t"] == kw["t_end"]
+    if precision == 0:
+        assert r1["steps"] + r2["steps"] == ra["steps"] and r1["rejects"] + r2["rejects"] == ra["rejects"]
+        np.testing.assert_array_equal(fb.cpu().numpy(), fa.cpu().numpy())
+    else:
+        assert abs(r1["steps"] + r2["steps"] - ra["steps"]) <= 2
+        assert relerr(fb.cpu().numpy()[0], fa.cpu().numpy()[0]) <= TOL[1]
+    k.release()
+
+
 # ------------------------------------------------------ quantum statistics ---
 @pytest.mark.parametrize("eta", [1, -1])
 def test_quantum_statistics_fp64_path_matches_oracle(ctx, kx, eta):
