@@ -265,6 +265,7 @@ static int kx_dev_alloc(kx_ctx *ctx, T **p, size_t count, long long *bytes) {
 }
 
 extern "C" int kx_build_kernel(kx_ctx *ctx, const kx_grid_desc *d, kx_kernel **out) {
+    kx_nvtx range_("kx_build_kernel");
     if (!ctx || !d || !out) return KX_EINVAL;
     *out = nullptr;
     const int n = d->n;
@@ -591,6 +592,7 @@ static int kx_collision_impl(kx_ctx *ctx, const kx_kernel *k, int B, const doubl
 
 extern "C" int kx_collision(kx_ctx *ctx, const kx_kernel *k, int B, const double *sigma,
                             const double *f_dev, double *C_dev, int project, kx_diag *diag) {
+    kx_nvtx range_("kx_collision");
     int rc = kx_check_batch(ctx, k, B, sigma);
     if (rc) return rc;
     if (!f_dev || !C_dev) return kx_set_error(ctx, KX_EINVAL, "null device pointer");
@@ -601,6 +603,7 @@ extern "C" int kx_collision(kx_ctx *ctx, const kx_kernel *k, int B, const double
 
 extern "C" int kx_collision_host(kx_ctx *ctx, const kx_kernel *k, int B, const double *sigma,
                                  const double *f_host, double *C_host, int project, kx_diag *diag) {
+    kx_nvtx range_("kx_collision_host");
     int rc = kx_check_batch(ctx, k, B, sigma);
     if (rc) return rc;
     if (!f_host || !C_host) return kx_set_error(ctx, KX_EINVAL, "null host pointer");
@@ -800,6 +803,7 @@ static int kx_collect(kx_ctx *ctx, const kx_kernel *k, int B, const kx_run &r, k
 extern "C" int kx_step(kx_ctx *ctx, const kx_kernel *k, int B, const double *sigma,
                        const kx_source *src, int nsets, const kx_solve_params *par, double *t_host,
                        double *h_host, double *f_dev, kx_result *res) {
+    kx_nvtx range_("kx_step");
     int rc = kx_check_batch(ctx, k, B, sigma);
     if (rc) return rc;
     if ((rc = kx_check_params(ctx, par)) != KX_OK) return rc;
@@ -900,6 +904,7 @@ static int kx_solve_run(kx_ctx *ctx, const kx_kernel *k, int B, const kx_run &r,
 extern "C" int kx_solve(kx_ctx *ctx, const kx_kernel *k, int B, const double *sigma,
                         const kx_source *src, int nsets, const kx_solve_params *par, double *f_dev,
                         kx_result *res) {
+    kx_nvtx range_("kx_solve");
     int rc = kx_check_batch(ctx, k, B, sigma);
     if (rc) return rc;
     if ((rc = kx_check_params(ctx, par)) != KX_OK) return rc;
@@ -915,6 +920,7 @@ extern "C" int kx_solve(kx_ctx *ctx, const kx_kernel *k, int B, const double *si
 extern "C" int kx_solve_host(kx_ctx *ctx, const kx_kernel *k, int B, const double *sigma,
                              const kx_source *src, int nsets, const kx_solve_params *par,
                              double *f_host, kx_result *res) {
+    kx_nvtx range_("kx_solve_host");
     int rc = kx_check_batch(ctx, k, B, sigma);
     if (rc) return rc;
     if ((rc = kx_check_params(ctx, par)) != KX_OK) return rc;

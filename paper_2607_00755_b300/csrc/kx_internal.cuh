@@ -111,6 +111,12 @@ struct kx_ctx {
 
 // error helpers ---------------------------------------------------------------
 int kx_set_error(kx_ctx *ctx, int code, const std::string &msg);
+// NVTX range over a host call (visible to profilers that record NVTX).
+#include <nvtx3/nvToolsExt.h>
+struct kx_nvtx {
+    explicit kx_nvtx(const char *name) { nvtxRangePushA(name); }
+    ~kx_nvtx() { nvtxRangePop(); }
+};
 // Host-side fault injection (KX_FAULT, a comma-separated list read at each
 // check): true if `what` is listed.  Nothing it does touches the GPU's state.
 bool kx_fault(const char *what);

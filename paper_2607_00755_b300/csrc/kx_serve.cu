@@ -384,6 +384,7 @@ static void kx_fail(kx_server *srv, const std::shared_ptr<Request> &r, int code)
 }
 
 static void kx_worker(kx_server *srv) {
+    kx_nvtx range_("kx_server_worker");
     cudaSetDevice(srv->ctx->device);
     const double wall_limit = 3600.0;
     double t_stop = 0.0;
