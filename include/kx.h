@@ -325,10 +325,13 @@ int kx_time_collision(kx_ctx *ctx, const kx_kernel *k, int batch, const double *
  * between two CUDA events; *avg_ms = device time / (iters * nk).  With
  * kernels whose tables together exceed the L2 cache, every launch streams its
  * tables from HBM (rotating buffers) while the launches still follow each
- * other as in a solve.  KX_EINVAL for nk < 1, a null kernel, mixed sizes or
+ * other as in a solve.  pdl != 0: the FP32 streaming contractions launch with
+ * programmatic stream serialization, as inside the solve's graphs (a launch
+ * issues its first table loads while its predecessor finishes; the other
+ * paths ignore the flag).  KX_EINVAL for nk < 1, a null kernel, mixed sizes or
  * bad arguments; KX_ECUDA on a CUDA error.  Synchronises the stream. */
 int kx_time_contractions(kx_ctx *ctx, int nk, const kx_kernel *const *ks, int batch,
-                         const double *f_dev, int iters, double *avg_ms);
+                         const double *f_dev, int iters, int pdl, double *avg_ms);
 
 /* Moment-matched discrete Maxwell-Boltzmann fit used by the stopping test:
  * out_host[batch][3] = (T, ln z, L1) with L1 = sum h |f - f_MB| / sum h f. */

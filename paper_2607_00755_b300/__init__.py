@@ -133,7 +133,7 @@ def load_library(path: str = LIB_PATH):
         "kx_source_condensate": (i, [i, vp, d, d, d, d, d, vp, vp]),
         "kx_launch_count": (ctypes.c_longlong, [vp]),
         "kx_time_contraction": (i, [vp, vp, i, vp, i, ctypes.c_longlong, vp]),
-        "kx_time_contractions": (i, [vp, i, vp, i, vp, i, vp]),
+        "kx_time_contractions": (i, [vp, i, vp, i, vp, i, i, vp]),
         "kx_time_collision": (i, [vp, vp, i, vp, vp, vp, i, i, vp]),
         "kx_collision_noalloc": (i, [vp, vp, i, vp, vp, vp, i]),
         "kx_server_start": (i, [vp, ctypes.POINTER(ServerConfig), vp]),
@@ -339,14 +339,15 @@ class Context:
             raise self.error(rc, "kx_time_collision")
         return ms.value, C.view_as(f)
 
-    def time_contractions(self, kernels, f, iters=10):
+    def time_contractions(self, kernels, f, iters=10, pdl=False):
         """Mean device time (ms) per launch of the kernels' contractions issued
-        back to back (rotating tables), for f [B, n]."""
+        back to back (rotating tables), for f [B, n]; pdl: programmatic
+        dependent launch, as inside the solve's graphs."""
         f2 = f if f.dim() == 2 else f.view(1, -1)
         arr = (ctypes.c_void_p * len(kernels))(*[k.h for k in kernels])
         ms = ctypes.c_double()
         rc = self.lib.kx_time_contractions(self.h, len(kernels), arr, f2.shape[0], _dptr(f2),
-                                           int(iters), ctypes.byref(ms))
+                                           int(iters), int(bool(pdl)), ctypes.byref(ms))
         if rc:
             raise self.error(rc, "kx_time_contractions")
         return ms.value

@@ -1048,7 +1048,7 @@ extern "C" int kx_time_collision(kx_ctx *ctx, const kx_kernel *k, int B, const d
 }
 
 extern "C" int kx_time_contractions(kx_ctx *ctx, int nk, const kx_kernel *const *ks, int B,
-                                    const double *f_dev, int iters, double *avg_ms) {
+                                    const double *f_dev, int iters, int pdl, double *avg_ms) {
     if (!ctx || nk < 1 || !ks || B < 1 || !f_dev || iters < 1 || !avg_ms) return KX_EINVAL;
     for (int i = 0; i < nk; ++i)
         if (!ks[i] || ks[i]->n != ks[0]->n) return KX_EINVAL;
@@ -1077,7 +1077,7 @@ extern "C" int kx_time_contractions(kx_ctx *ctx, int nk, const kx_kernel *const 
     if (e == cudaSuccess) e = cudaEventRecord(e0, s);
     for (int it = 0; it < iters && e == cudaSuccess; ++it)
         for (int i = 0; i < nk && e == cudaSuccess; ++i, ++ctx->launches)
-            e = kx_launch_contract(ks[i], B, f_dev, v[i], nullptr, 1, s);
+            e = kx_launch_contract(ks[i], B, f_dev, v[i], nullptr, 1, s, pdl != 0);
     if (e == cudaSuccess) e = cudaEventRecord(e1, s);
     if (e == cudaSuccess) e = cudaEventSynchronize(e1);
     float ms = 0.f;

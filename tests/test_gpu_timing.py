@@ -31,8 +31,9 @@ def test_rotating_timing_runs_and_leaves_results(env, precision):
     sig = np.ones(3)
     before, _ = ctx.collision(ks[0], f, sig)
     ms = ctx.time_contractions(ks, f, iters=4)
+    ms_pdl = ctx.time_contractions(ks, f, iters=4, pdl=True)
     one = ctx.time_contraction(ks[1], f, iters=3, flush_bytes=1 << 20)
-    assert 0.0 < ms < 1e3 and 0.0 < one < 1e3
+    assert 0.0 < ms < 1e3 and 0.0 < ms_pdl < 1e3 and 0.0 < one < 1e3
     after, _ = ctx.collision(ks[2], f, sig)
     np.testing.assert_array_equal(before.cpu().numpy(), after.cpu().numpy())
     for k in ks:
