@@ -1596,7 +1596,28 @@ __device__ __forceinline__ void kx_stage_body(int b, int n, int chunks, int path
     __shared__ unsigned long long s_keys[3 * 32];
     __shared__ double s_env[KX_MAX_SRC];
     const int i = threadIdx.x;
+    const bool in = i < n;
+    // The grid and the source rows do not change while a graph of attempts
+    // runs: their loads are issued before the wait for the predecessor kernel
+    // (programmatic dependent launch), so that they overlap its tail.
+    const double Ei = in ? E[i] : 0.0, hi = in ? h[i] : 0.0, E0 = E[0];
+    const kx_src_dev &src = sv.src[b];
+    const int n_src = src.n_src;
+    double shp[KX_MAX_SRC];
+#pragma unroll
+    for (int k = 0; k < KX_MAX_SRC; ++k)
+        shp[k] = (in && k < n_src) ? sv.shapes[src.shape_off + (long long)k * n + i] : 0.0;
+    kx_pdl_wait();
     kx_inst_state *st = sv.st + b;
+    double *fb = sv.f + (long long)b * n;
+    double *k1 = sv.k1 + (long long)b * n;
+    double *fp = sv.fp + (long long)b * n;
+    // the instance's inputs, issued together with the state loads (a finished
+    // instance loads them in vain)
+    const double f0 = in ? fb[i] : 0.0;
+    const double fpv = (in && stage == 2) ? fp[i] : 0.0;
+    const double k1v = (in && stage == 2) ? k1[i] : 0.0;
+    const int flag_in = v.flags[b];
     if (st->done) return;
     if (stage == 2 && st->skip2) {
         __syncthreads();
@@ -1612,22 +1633,6 @@ __device__ __forceinline__ void kx_stage_body(int b, int n, int chunks, int path
     const int last_state = st->last;
     const long long steps0 = st->steps, rejects0 = st->rejects;
     const double l1_0 = st->l1, T0 = st->T, lnz0 = st->lnz;
-    const bool in = i < n;
-    double *fb = sv.f + (long long)b * n;
-    double *k1 = sv.k1 + (long long)b * n;
-    double *fp = sv.fp + (long long)b * n;
-    // loads that do not depend on the reductions, issued up front
-    const double Ei = in ? E[i] : 0.0, hi = in ? h[i] : 0.0, E0 = E[0];
-    const double f0 = in ? fb[i] : 0.0;
-    const double fpv = (in && stage == 2) ? fp[i] : 0.0;
-    const double k1v = (in && stage == 2) ? k1[i] : 0.0;
-    const kx_src_dev &src = sv.src[b];
-    const int n_src = src.n_src;
-    double shp[KX_MAX_SRC];
-#pragma unroll
-    for (int k = 0; k < KX_MAX_SRC; ++k)
-        shp[k] = (in && k < n_src) ? sv.shapes[src.shape_off + (long long)k * n + i] : 0.0;
-    const int flag_in = v.flags[b];
     double htry;
     if (stage == 1) {
         htry = h_state;
@@ -1817,8 +1822,7 @@ __global__ void __launch_bounds__(KX_FIN_THREADS)
     k_stage(int n, int chunks, int path, const double *__restrict__ E, const double *__restrict__ h,
             kx_batch_views v, kx_step_views sv, int stage, long long max_attempts) {
     __shared__ double smem[5 * KX_FIN_THREADS + 8];
-    kx_pdl_trigger();
-    kx_pdl_wait();
+    kx_pdl_trigger();   // (the body waits for the predecessor after its constant loads)
     kx_stage_body<Q>(blockIdx.x, n, chunks, PATH >= 0 ? PATH : path, E, h, v, sv, stage, max_attempts, smem);
 }
 
