@@ -310,10 +310,16 @@ __device__ __forceinline__ void kx_block_max_keys(unsigned long long (&x)[K], un
 // fitted to g = l2 - lambda, lambda = log2(1 + eta f) (g is linear in E on the
 // equilibrium of that statistics), tl holds (l2_j, g_j - line), tq the
 // interpolation tables of eps = l2 - line and of l2, tlam lambda_j.
-template <bool Q = false>
+struct kx_noop {
+    __device__ void operator()() const {}
+};
+// idle: run by every thread just before the barrier that publishes 1/f_max and
+// log2 f_max, while threads 0 and 32 compute them (the other warps wait there)
+template <bool Q = false, typename Idle = kx_noop>
 __device__ __forceinline__ int kx_prep_block(int n, int path, double x, double Ei, double hi, double E0,
                              const kx_batch_views &v, int b, double *smem,
-                             unsigned long long key_in = KX_KEY_NONE, int line_mode = KX_LINE_FIT) {
+                             unsigned long long key_in = KX_KEY_NONE, int line_mode = KX_LINE_FIT,
+                             Idle idle = Idle()) {
     __shared__ unsigned long long s_key[32];
     __shared__ float s_fit[5 * 32];
     __shared__ double s_scale[3];   // exponent and fraction of log2 f_max, 1 / f_max
@@ -363,6 +369,7 @@ __device__ __forceinline__ int kx_prep_block(int n, int path, double x, double E
         if (in) v.lf64[(long long)b * n + i] = log(x > KX_LOG_FLOOR ? x : KX_LOG_FLOOR);
         return bad;
     }
+    idle();
     __syncthreads();   // publishes s_scale
     const double rfm = s_scale[2];
     // l2 = log2(max(f, floor) / f_max) from the exponents and fractions (table log2)
@@ -1618,21 +1625,30 @@ __device__ __forceinline__ void kx_stage_body(int b, int n, int chunks, int path
     const double fpv = (in && stage == 2) ? fp[i] : 0.0;
     const double k1v = (in && stage == 2) ? k1[i] : 0.0;
     const int flag_in = v.flags[b];
-    if (st->done) return;
-    if (stage == 2 && st->skip2) {
-        __syncthreads();
-        if (threadIdx.x == 0) st->skip2 = 0;
-        return;
-    }
     // Every thread takes its copy of the instance state here, before the first
     // block barrier: thread 0 rewrites the state at the end of the stage, and a
     // warp that read it after that write could disagree with the others on
     // block-uniform decisions (the MB check, which holds barriers).  (Thread 0's
     // early write of h_try and last in stage 1 is read only by stage 2.)
+    const int done0 = st->done, skip2_0 = st->skip2;
     const double t = st->t, t_end = st->t_end, h_state = st->h, h_try_state = st->h_try;
     const int last_state = st->last;
     const long long steps0 = st->steps, rejects0 = st->rejects;
     const double l1_0 = st->l1, T0 = st->T, lnz0 = st->lnz;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, lastw = (blockDim.x >> 5) - 1;
+    const bool envw = wid == lastw && lane < n_src;   // the lanes that own the envelopes
+    const int env_ok = st->env_ok;
+    const double env_t = st->env_t, env_mine = envw ? st->env[lane] : 0.0;
+    // the row combine and the projection first: their loads do not wait for
+    // the state (a finished instance computes them in vain and writes nothing)
+    const double fcur = stage == 1 ? f0 : fpv;
+    kx_row_out r = kx_combine_project(n, chunks, path, b, fcur, Ei, hi, v, sv.project, smem);
+    if (done0) return;
+    if (stage == 2 && skip2_0) {
+        __syncthreads();
+        if (threadIdx.x == 0) st->skip2 = 0;
+        return;
+    }
     double htry;
     if (stage == 1) {
         htry = h_state;
@@ -1652,20 +1668,16 @@ __device__ __forceinline__ void kx_stage_body(int b, int n, int chunks, int path
     } else {
         htry = h_try_state;
     }
-    // source envelopes, one exp per source on the last warp (off the critical
-    // path of warp 0, which solves the projection system)
+    // source envelopes at this stage's time, one per source on the last warp:
+    // the previous stage kernel made them for this time (during an idle wait of
+    // its prep), else (a new state) they are made here
+    auto envelope = [&](double tt) {
+        return tt >= src.t_on[lane] ? src.rate[lane] * kx_exp(-(tt - src.t_on[lane]) / src.tau[lane]) : 0.0;
+    };
     const double tS = stage == 1 ? t : t + htry;
-    {
-        const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, lastw = (blockDim.x >> 5) - 1;
-        if (w == lastw && lane < n_src) {
-            const int k = lane;
-            s_env[k] = tS >= src.t_on[k] ? src.rate[k] * kx_exp(-(tS - src.t_on[k]) / src.tau[k]) : 0.0;
-        }
-    }
-    const double fcur = stage == 1 ? f0 : fpv;
-    kx_row_out r = kx_combine_project(n, chunks, path, b, fcur, Ei, hi, v, sv.project, smem);
+    if (envw) s_env[lane] = (env_ok && env_t == tS) ? env_mine : envelope(tS);
     const double C = sv.project ? r.Cproj : r.Craw;
-    __syncthreads();   // publishes s_env (also when the projection is off)
+    __syncthreads();   // publishes s_env
     double Si = 0.0;
 #pragma unroll
     for (int k = 0; k < KX_MAX_SRC; ++k)
@@ -1711,7 +1723,17 @@ __device__ __forceinline__ void kx_stage_body(int b, int n, int chunks, int path
             fp[i] = fpi;
         }
         if (threadIdx.x == 0) st->evals += 1;
-        int bad2 = kx_prep_block<Q>(n, path, in ? fpi : 0.0, Ei, hi, E0, v, b, smem, keys[1], KX_LINE_NEXT);
+        // the envelopes of stage 2 (at t + h_try), made while the prep waits
+        auto idle = [&]() {
+            if (envw) {
+                st->env[lane] = envelope(t + htry);
+                if (lane == 0) {
+                    st->env_t = t + htry;
+                    st->env_ok = 1;
+                }
+            }
+        };
+        int bad2 = kx_prep_block<Q>(n, path, in ? fpi : 0.0, Ei, hi, E0, v, b, smem, keys[1], KX_LINE_NEXT, idle);
         if (threadIdx.x == 0) v.flags[b] = bad2;
         return;
     }
@@ -1808,8 +1830,18 @@ __device__ __forceinline__ void kx_stage_body(int b, int n, int chunks, int path
         }
     }
     // prepare the next attempt's contraction input (f_new or the restored f)
+    // the envelopes of the next stage 1 (at the new t), made while the prep waits
+    auto idle = [&]() {
+        if (envw) {
+            st->env[lane] = envelope(tn);
+            if (lane == 0) {
+                st->env_t = tn;
+                st->env_ok = 1;
+            }
+        }
+    };
     int bad2 = kx_prep_block<Q>(n, path, in ? fnew : 0.0, Ei, hi, E0, v, b, smem, accept ? keys[1] : keys[2],
-                                KX_LINE_NEXT);
+                                KX_LINE_NEXT, idle);
     if (threadIdx.x == 0) v.flags[b] = bad2;
 }
 

@@ -79,13 +79,16 @@ struct kx_kernel {
 struct kx_inst_state {
     double t, h, h_try, t_end, err;
     double l1, T, lnz;
+    double env_t;               // time of the stored source envelopes
+    double env[KX_MAX_SRC];     // envelopes rate_k exp(-(env_t - t_on_k) / tau_k), made by the
+                                // previous stage kernel for the next stage's time
     long long steps, rejects, evals;
     int status;      // KX_OK or error
     int done;        // 1: finished (converged, t_end, error)
     int converged;
     int skip2;       // stage 1 rejected: skip stage 2 of this attempt
     int last;        // this attempt ends exactly at t_end
-    int pad;
+    int env_ok;      // env holds the envelopes at env_t (0 in a new state)
 };
 
 struct kx_src_dev {
