@@ -596,7 +596,7 @@ def main():
             "avg_launch_ms_warm_l2": ms_warm, "peak_source": src_peak,
             "note": "the collision contraction of the step; by device time the per-instance "
                     "stage kernel (k_stage<1>: FP64 chains and block reductions on one block per "
-                    "instance, 4 SMs) is the larger share (~58 %, profiles/launch_list_config2_"
+                    "instance, 4 SMs) is the larger share (~57 %, profiles/launch_list_config2_"
                     "n128_step.md, profiles/k_stage_config2_n128.md); both are latency bound at "
                     "N = 128 with 4 instances (tables 6.8 MB, L2-resident in the solve)"}
     # streaming single-instance rooflines at N=384 and N=512 (tables 172 MB
