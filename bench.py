@@ -36,8 +36,8 @@ L2_FLUSH_BYTES = 512 << 20     # > 126 MB L2
 # DRAM bytes (read + write) per launch from one ncu capture of the current kernels
 # (profiles/k_stream32r_n128_batch4.md, profiles/k_stream32r_single_n384_n512.md); None
 # whenever those kernels have changed since the capture.
-NCU_TRAFFIC = {"stream_n128_b4": 6.783488e6, "stream_n384": 172.423424e6,
-               "stream_n512": 406.064896e6 + 0.035584e6}
+NCU_TRAFFIC = {"stream_n128_b4": 6.783232e6, "stream_n384": 172.422656e6,
+               "stream_n512": 406.062848e6 + 0.040448e6}
 
 
 def stream_kernel_name(ctx, n, batch):
