@@ -313,13 +313,22 @@ __device__ __forceinline__ void kx_block_max_keys(unsigned long long (&x)[K], un
 struct kx_noop {
     __device__ void operator()() const {}
 };
+// Per-point values of the prep that do not depend on f, and the instance's
+// stored reference lines, when the caller has them already (the stage kernel
+// loads them early); have = false: the prep makes them itself.
+struct kx_prep_pre {
+    double K;       // E_i - E_0
+    float Kf, hf;   // K and h_i as floats
+    float4 lines;   // v.fit[b]
+    bool have;
+};
 // idle: run by every thread just before the barrier that publishes 1/f_max and
 // log2 f_max, while threads 0 and 32 compute them (the other warps wait there)
 template <bool Q = false, typename Idle = kx_noop>
 __device__ __forceinline__ int kx_prep_block(int n, int path, double x, double Ei, double hi, double E0,
                              const kx_batch_views &v, int b, double *smem,
                              unsigned long long key_in = KX_KEY_NONE, int line_mode = KX_LINE_FIT,
-                             Idle idle = Idle()) {
+                             Idle idle = Idle(), kx_prep_pre pre = kx_prep_pre{0.0, 0.f, 0.f, {}, false}) {
     __shared__ unsigned long long s_key[32];
     __shared__ float s_fit[5 * 32];
     __shared__ double s_scale[3];   // exponent and fraction of log2 f_max, 1 / f_max
@@ -342,7 +351,8 @@ __device__ __forceinline__ int kx_prep_block(int n, int path, double x, double E
             lam = (double)e2 + fr2;
         }
     }
-    const float4 lines = (line_mode != KX_LINE_FIT && path == KX_FP32) ? v.fit[b] : make_float4(0.f, 0.f, 0.f, 0.f);
+    const float4 lines = pre.have ? pre.lines
+                         : ((line_mode != KX_LINE_FIT && path == KX_FP32) ? v.fit[b] : make_float4(0.f, 0.f, 0.f, 0.f));
     const unsigned long long key =
         key_in != KX_KEY_NONE
             ? key_in
@@ -398,15 +408,15 @@ __device__ __forceinline__ int kx_prep_block(int n, int path, double x, double E
     }
     float2 *tl = v.tl + (long long)b * (n + 4);
     float2 *td = v.td + (long long)b * n;
-    const double K = in ? Ei - E0 : 0.0;   // kinetic energy
+    const double K = pre.have ? pre.K : (in ? Ei - E0 : 0.0);   // kinetic energy
     // Reference line l2 ~ icpt + slope K: weighted least squares (weights h f /
     // f_max) in FP32, one pass.  Any line in E cancels exactly in the exponent
     // differences; the fit only keeps the deviations small, so a poorly
     // conditioned fit (spread of K below 1% of its rms) falls back to slope 0.
-    const float l2f = (float)l2, Kf = (float)K;
+    const float l2f = (float)l2, Kf = pre.have ? pre.Kf : (float)K;
     const double gq = Q ? l2 - lam : l2;   // the fitted quantity
     const float gf = Q ? (float)gq : l2f;
-    const float w = (in && fm > 0.0 && x > 0.0) ? (float)hi * (float)(x * rfm) : 0.f;
+    const float w = (in && fm > 0.0 && x > 0.0) ? (pre.have ? pre.hf : (float)hi) * (float)(x * rfm) : 0.f;
     float sf[5] = {w, w * Kf, w * Kf * Kf, w * gf, w * Kf * gf};
     auto solve_line = [](const float *t) {
         float slope = 0.f, icpt = 0.f;
@@ -1608,6 +1618,11 @@ __device__ __forceinline__ void kx_stage_body(int b, int n, int chunks, int path
     // runs: their loads are issued before the wait for the predecessor kernel
     // (programmatic dependent launch), so that they overlap its tail.
     const double Ei = in ? E[i] : 0.0, hi = in ? h[i] : 0.0, E0 = E[0];
+    kx_prep_pre pre;
+    pre.K = in ? Ei - E0 : 0.0;
+    pre.Kf = (float)pre.K;
+    pre.hf = (float)hi;
+    pre.have = path == KX_FP32;
     const kx_src_dev &src = sv.src[b];
     const int n_src = src.n_src;
     double shp[KX_MAX_SRC];
@@ -1625,6 +1640,7 @@ __device__ __forceinline__ void kx_stage_body(int b, int n, int chunks, int path
     const double fpv = (in && stage == 2) ? fp[i] : 0.0;
     const double k1v = (in && stage == 2) ? k1[i] : 0.0;
     const int flag_in = v.flags[b];
+    pre.lines = path == KX_FP32 ? v.fit[b] : make_float4(0.f, 0.f, 0.f, 0.f);
     // Every thread takes its copy of the instance state here, before the first
     // block barrier: thread 0 rewrites the state at the end of the stage, and a
     // warp that read it after that write could disagree with the others on
@@ -1733,7 +1749,7 @@ __device__ __forceinline__ void kx_stage_body(int b, int n, int chunks, int path
                 }
             }
         };
-        int bad2 = kx_prep_block<Q>(n, path, in ? fpi : 0.0, Ei, hi, E0, v, b, smem, keys[1], KX_LINE_NEXT, idle);
+        int bad2 = kx_prep_block<Q>(n, path, in ? fpi : 0.0, Ei, hi, E0, v, b, smem, keys[1], KX_LINE_NEXT, idle, pre);
         if (threadIdx.x == 0) v.flags[b] = bad2;
         return;
     }
@@ -1841,7 +1857,7 @@ __device__ __forceinline__ void kx_stage_body(int b, int n, int chunks, int path
         }
     };
     int bad2 = kx_prep_block<Q>(n, path, in ? fnew : 0.0, Ei, hi, E0, v, b, smem, accept ? keys[1] : keys[2],
-                                KX_LINE_NEXT, idle);
+                                KX_LINE_NEXT, idle, pre);
     if (threadIdx.x == 0) v.flags[b] = bad2;
 }
 
