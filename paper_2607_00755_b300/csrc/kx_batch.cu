@@ -335,10 +335,9 @@ __global__ void __launch_bounds__(WARPS * 32, (WARPS <= 16 && IPL <= 2) ? 2 : 1)
     float hi[IPL], lo[IPL];
 #pragma unroll
     for (int s = 0; s < IPL; ++s) hi[s] = lo[s] = 0.f;
-    // a[s][0..3] live as two packed pairs (elements 0, 1 and 2, 3 of each four)
-    unsigned long long a2[IPL][2];
+    float a[IPL][4];   // FP32 sums of elements 0..3 of each four
 #pragma unroll
-    for (int s = 0; s < IPL; ++s) a2[s][0] = a2[s][1] = kx_pk2(0.f, 0.f);
+    for (int s = 0; s < IPL; ++s) a[s][0] = a[s][1] = a[s][2] = a[s][3] = 0.f;
     int na = 0;   // elements in the FP32 sums since the last flush
     // descriptors run two segments ahead of the compute, elements one
     int2 dsc = make_int2(0, 0), dn = dsc;
@@ -375,9 +374,10 @@ __global__ void __launch_bounds__(WARPS * 32, (WARPS <= 16 && IPL <= 2) ? 2 : 1)
             }
         }
         // a pair of elements per float4, stored (S_0, S_1, omega_0, omega_1); per
-        // pair and instance one packed FMA for the two exponents, two ex2 and one
-        // packed FMA for the weights.  A running pointer keeps the loop's address
-        // arithmetic to one add per four elements.
+        // pair and instance one packed FMA for the two exponents, two ex2 and two
+        // FMAs for the weights (scalar: the ex2 results need no repacking).  A
+        // running pointer keeps the loop's address arithmetic to one add per four
+        // elements.
         unsigned long long tD[IPL], tL[IPL];
 #pragma unroll
         for (int s = 0; s < IPL; ++s) {
@@ -389,14 +389,15 @@ __global__ void __launch_bounds__(WARPS * 32, (WARPS <= 16 && IPL <= 2) ? 2 : 1)
 #pragma unroll 2
         for (; pe < pend; pe += 2) {
             const float4 x01 = pe[0], x23 = pe[1];
-            const unsigned long long s01 = kx_pk2(x01.x, x01.y), w01 = kx_pk2(x01.z, x01.w);
-            const unsigned long long s23 = kx_pk2(x23.x, x23.y), w23 = kx_pk2(x23.z, x23.w);
+            const unsigned long long w01 = kx_pk2(x01.z, x01.w), w23 = kx_pk2(x23.z, x23.w);
 #pragma unroll
             for (int s = 0; s < IPL; ++s) {
                 const float2 e01 = kx_upk2(kx_fma2(w01, tD[s], tL[s]));
                 const float2 e23 = kx_upk2(kx_fma2(w23, tD[s], tL[s]));
-                a2[s][0] = kx_fma2(s01, kx_pk2(kx_ex2f(e01.x), kx_ex2f(e01.y)), a2[s][0]);
-                a2[s][1] = kx_fma2(s23, kx_pk2(kx_ex2f(e23.x), kx_ex2f(e23.y)), a2[s][1]);
+                a[s][0] = fmaf(x01.x, kx_ex2f(e01.x), a[s][0]);
+                a[s][1] = fmaf(x01.y, kx_ex2f(e01.y), a[s][1]);
+                a[s][2] = fmaf(x23.x, kx_ex2f(e23.x), a[s][2]);
+                a[s][3] = fmaf(x23.y, kx_ex2f(e23.y), a[s][3]);
             }
         }
         // the FP32 sums go into the double-float accumulator once they hold at
@@ -405,12 +406,11 @@ __global__ void __launch_bounds__(WARPS * 32, (WARPS <= 16 && IPL <= 2) ? 2 : 1)
         if (na >= KX_SEG) {
 #pragma unroll
             for (int s = 0; s < IPL; ++s) {
-                const float2 p = kx_upk2(a2[s][0]), q = kx_upk2(a2[s][1]);
                 float sm, er;
-                kx_two_sum_f(hi[s], (p.x + p.y) + (q.x + q.y), sm, er);
+                kx_two_sum_f(hi[s], (a[s][0] + a[s][1]) + (a[s][2] + a[s][3]), sm, er);
                 hi[s] = sm;
                 lo[s] += er;
-                a2[s][0] = a2[s][1] = kx_pk2(0.f, 0.f);
+                a[s][0] = a[s][1] = a[s][2] = a[s][3] = 0.f;
             }
             na = 0;
         }
@@ -422,9 +422,8 @@ __global__ void __launch_bounds__(WARPS * 32, (WARPS <= 16 && IPL <= 2) ? 2 : 1)
     }
 #pragma unroll
     for (int s = 0; s < IPL; ++s) {
-        const float2 p = kx_upk2(a2[s][0]), q = kx_upk2(a2[s][1]);
         float sm, er;
-        kx_two_sum_f(hi[s], (p.x + p.y) + (q.x + q.y), sm, er);
+        kx_two_sum_f(hi[s], (a[s][0] + a[s][1]) + (a[s][2] + a[s][3]), sm, er);
         hi[s] = sm;
         lo[s] += er;
     }
