@@ -52,7 +52,7 @@ extern "C" {
 #define KX_ENOCONV -7      /* integration hit max_attempts before finishing */
 #define KX_ETIMEOUT -8     /* a bounded device or host wait expired */
 #define KX_ECUDA -9        /* a CUDA runtime/driver call failed (see kx_last_error) */
-#define KX_ENOTSUP -10     /* option not supported by this build (e.g. quantum statistics off the FP64 path) */
+#define KX_ENOTSUP -10     /* option not supported by the library (e.g. quantum statistics on the split-TF32 path) */
 
 /* -------------------------------------------------------------- options */
 #define KX_MEASURE_ENERGY 0   /* W = dE_n dE_m F / (2 E_i g): F of eq. app_F_2d is the kernel of dE_n dE_m (default) */

@@ -279,7 +279,7 @@ extern "C" int kx_build_kernel(kx_ctx *ctx, const kx_grid_desc *d, kx_kernel **o
     if (d->stats != 0 && d->precision == KX_SPLIT_TF32)
         return kx_set_error(ctx, KX_ENOTSUP, "quantum statistics: FP64 and FP32 paths only");
     if (d->precision != KX_FP64 && d->precision != KX_FP32 && d->precision != KX_SPLIT_TF32)
-        return kx_set_error(ctx, KX_ENOTSUP, "precision not available in this build");
+        return kx_set_error(ctx, KX_ENOTSUP, "precision not available in this library");
     for (int i = 0; i < n; ++i) {
         if (!(d->q[i] > 0) || !isfinite(d->q[i]))
             return kx_set_error(ctx, KX_EINVAL, "q must be finite and > 0");
