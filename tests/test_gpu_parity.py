@@ -612,26 +612,28 @@ def test_quantum_statistics_fp32_paper_benchmark_distribution(ctx, kx):
         k.release()
 
 
-def test_quantum_statistics_fp32_fixed_step_solve(ctx, kx):
-    """Twenty fixed Heun steps with Bose-Einstein factors on the FP32 path
-    against the same steps taken with the oracle's operator and projection;
-    number and energy conserved to the mixed-precision bound."""
+@pytest.mark.parametrize("eta", [1, -1])
+def test_quantum_statistics_fp32_fixed_step_solve(ctx, kx, eta):
+    """Twenty fixed Heun steps with Bose-Einstein (Fermi-Dirac: f scaled below
+    one) factors on the FP32 path against the same steps taken with the
+    oracle's operator and projection; number and energy conserved to the
+    mixed-precision bound."""
     c = ki.config1()
-    q, f0 = c["q"], c["f0"]
+    q, f0 = c["q"], c["f0"] * (1.0 if eta == 1 else 0.5)
     g = oracle.grid(q)
     W = oracle.kernel_tensor(q)
     M2 = oracle.M2_from_sigma(1.0, c["sigma"])
     h, steps = c["h"], 20
 
     def rhs(f):
-        return oracle.project(g["E"], g["h"], f, oracle.collision_tensor_stats(q, W, f, 1) * M2)[0]
+        return oracle.project(g["E"], g["h"], f, oracle.collision_tensor_stats(q, W, f, eta) * M2)[0]
 
     fo = f0.copy()
     for _ in range(steps):
         k1 = rhs(fo)
         fp = fo + h * k1
         fo = fo + 0.5 * h * (k1 + rhs(fp))
-    k = ctx.build_kernel(q, precision=kx.FP32, stats=1)
+    k = ctx.build_kernel(q, precision=kx.FP32, stats=eta)
     fd = dev(f0[None])
     res = ctx.solve(k, fd, c["sigma"], t_end=steps * h, h0=h, fixed_step=1)
     f = fd.cpu().numpy()[0]
