@@ -1757,7 +1757,15 @@ __device__ __forceinline__ void kx_stage_body(int b, int n, int chunks, int path
     // non-finite > negative > the bits of err >= 0), and for max |f_c| and
     // max |f| (the next prep takes the one the step decision keeps)
     const double fci = f0 + 0.5 * htry * (k1v + kv);
-    const double e = in ? fabs(fci - fpv) / (sv.atol + sv.rtol * fabs(fci)) : 0.0;
+    // The error ratio only decides acceptance and scales h.  On the FP32 path,
+    // whose C carries FP32 rounding (~1e-7 relative) anyway, it is divided in
+    // FP32 from the FP64 difference and scale (an FP64 division is a long chain
+    // of FP64 operations on this part); the plain FP64 path divides in FP64.
+    double e = 0.0;
+    if (in) {
+        const double num = fabs(fci - fpv), den = sv.atol + sv.rtol * fabs(fci);
+        e = path == KX_FP32 ? (double)((float)num / (float)den) : num / den;
+    }
     const unsigned long long kneg = KX_KEY_NONFINITE - 1ull;   // bits of +inf
     unsigned long long key;
     if ((in && !isfinite(fci)) || flag_in) key = KX_KEY_NONFINITE;
@@ -1824,6 +1832,13 @@ __device__ __forceinline__ void kx_stage_body(int b, int n, int chunks, int path
             hnext = htry;
         } else if (neg) {
             hnext = 0.5 * htry;
+        } else if (path == KX_FP32) {
+            // the same factor in FP32 (err came from an FP32 ratio)
+            const float ef = (float)err;
+            float fac = ef > 0.f ? 0.9f * rsqrtf(ef) : 5.f;
+            if (fac > 5.f) fac = 5.f;
+            if (fac < 0.2f) fac = 0.2f;
+            hnext = htry * (double)fac;
         } else {
             double fac = err > 0.0 ? 0.9 / sqrt(err) : 5.0;
             if (fac > 5.0) fac = 5.0;
