@@ -38,14 +38,15 @@ def call_noalloc(kx, ctx, kernel, f, sigma, C, project):
                                         ctypes.c_void_p(C.data_ptr()), int(project))
 
 
-@pytest.mark.parametrize("precision", [0, 1])
-def test_noalloc_matches_kx_collision_twice(env, precision):
+@pytest.mark.parametrize("precision,stats", [(0, 0), (1, 0), (1, 1)])
+def test_noalloc_matches_kx_collision_twice(env, precision, stats):
     """Two calls in a row (different inputs, so stale scratch from the first
-    would show) agree with kx_collision within the parity tolerance."""
+    would show) agree with kx_collision within the parity tolerance (also with
+    the Bose-Einstein factor on the FP32 path)."""
     kx, ctx, torch = env
     n = 96
     q = ki.log_grid(n, 1e-3, 10.0)
-    k = ctx.build_kernel(q, precision=precision)
+    k = ctx.build_kernel(q, precision=precision, stats=stats)
     rng = np.random.default_rng(41)
     for call in range(2):
         B = 3 + call
