@@ -386,7 +386,7 @@ __global__ void __launch_bounds__(WARPS * 32, (WARPS <= 16 && IPL <= 2) ? 2 : 1)
         }
         const float4 *pe = reinterpret_cast<const float4 *>(s_el[warp]);
         const float4 *const pend = pe + (c4 >> 1);
-#pragma unroll 2
+#pragma unroll 4
         for (; pe < pend; pe += 2) {
             const float4 x01 = pe[0], x23 = pe[1];
             const unsigned long long w01 = kx_pk2(x01.z, x01.w), w23 = kx_pk2(x23.z, x23.w);
