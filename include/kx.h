@@ -251,6 +251,11 @@ typedef struct {
     int n_mu, measure;           /* kernel options of every request */
     kx_solve_params par;         /* integration controls of every request (t0, t_end, h0
                                     are per request; see kx_submit) */
+    int grid_div;                /* while more than 8 groups have work, the FP32 streaming
+                                    contraction of each group launches with 1/grid_div of
+                                    the GPU's resident blocks, so that several groups'
+                                    contractions run side by side; with fewer, with all of
+                                    them (results do not depend on it); 1..16, 0 = 2 */
 } kx_server_config;
 
 typedef struct {

@@ -82,7 +82,8 @@ class KernelInfo(ctypes.Structure):
 class ServerConfig(ctypes.Structure):
     _fields_ = [("hbm_budget_bytes", ctypes.c_longlong), ("slots_per_group", ctypes.c_int),
                 ("attempts_per_tick", ctypes.c_int), ("precision", ctypes.c_int),
-                ("n_mu", ctypes.c_int), ("measure", ctypes.c_int), ("par", SolveParams)]
+                ("n_mu", ctypes.c_int), ("measure", ctypes.c_int), ("par", SolveParams),
+                ("grid_div", ctypes.c_int)]
 
 
 class ServerStats(ctypes.Structure):
@@ -417,10 +418,12 @@ class Server:
     """Continuous-batching solve server (kx_server): submit solves, poll results."""
 
     def __init__(self, ctx: Context, budget_bytes=8 << 30, slots_per_group=16,
-                 attempts_per_tick=8, precision=FP32, n_mu=18, measure=MEASURE_ENERGY, **params):
+                 attempts_per_tick=8, precision=FP32, n_mu=18, measure=MEASURE_ENERGY,
+                 grid_div=0, **params):
         self.ctx, self.lib = ctx, ctx.lib
         cfg = ServerConfig(int(budget_bytes), int(slots_per_group), int(attempts_per_tick),
-                           int(precision), int(n_mu), int(measure), Context.params(**params))
+                           int(precision), int(n_mu), int(measure), Context.params(**params),
+                           int(grid_div))
         h = ctypes.c_void_p()
         rc = self.lib.kx_server_start(ctx.h, ctypes.byref(cfg), ctypes.byref(h))
         if rc:

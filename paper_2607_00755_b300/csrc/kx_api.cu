@@ -187,6 +187,7 @@ void kx_carve_views(const kx_kernel *k, int B, void *base, kx_batch_views *v) {
     v->tq = nullptr;
     v->tlam = nullptr;
     v->eta = k->stats;
+    v->grid_div = 1;
     if (k->precision == KX_FP32 && k->stats) {
         v->tq = (float4 *)p; p += kx_align(sizeof(float4) * B * n);
         v->tlam = (float *)p; p += kx_align(sizeof(float) * B * n);

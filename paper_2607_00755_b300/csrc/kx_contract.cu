@@ -1127,7 +1127,7 @@ static cudaError_t kx_launch_stream(const kx_kernel *k, int B, const kx_batch_vi
     if (occ < 1) occ = 1;
     const int sms = g_sms > 0 ? g_sms : 148;
     const int groups = (B + BP - 1) / BP;
-    const int blocks = kx_bin_blocks(occ * sms, groups);
+    const int blocks = kx_bin_blocks(occ * sms / (v.grid_div > 1 ? v.grid_div : 1), groups);
     dim3 grid(blocks, groups);
     const float4 *W = reinterpret_cast<const float4 *>(k->d_W32);
     const uint4 *PK = reinterpret_cast<const uint4 *>(k->d_pk);
@@ -1147,7 +1147,7 @@ static cudaError_t kx_launch_stream_r(const kx_kernel *k, int B, const kx_batch_
     if (occ < 1) occ = 1;
     const int sms = g_sms > 0 ? g_sms : 148;
     const int groups = (B + BP - 1) / BP;
-    const int blocks = kx_bin_blocks(occ * sms, groups);
+    const int blocks = kx_bin_blocks(occ * sms / (v.grid_div > 1 ? v.grid_div : 1), groups);
     dim3 grid(blocks, groups);
     return kx_launch_ex(k_stream32r<BP, VPL, Q>, grid, dim3(KX_T32), 0, s, pdl, k->n,
                         (const int *)k->d_bins, (const int4 *)k->d_task, (const int *)k->d_roff, B,

@@ -143,6 +143,8 @@ struct kx_batch_views {
                            //   l2_j - Dl_j, Dl_j), eps = l2 - line, De/Dl forward differences
     float *tlam;           // FP32 path with quantum statistics: [B][n] lambda_j = log2(1 + eta f_j)
     int eta;               // quantum statistics of the kernel: 0 dilute, +1 BE, -1 FD
+    int grid_div;          // FP32 streaming launches use 1/grid_div of the resident blocks
+                           // (1: the whole GPU; the server shares it among its groups)
     double2 *partial;      // [B][n][chunks]  (FP32 path: float2 (hi, lo) task partials, [B][chunks])
     const int2 *rtask;     // FP32 path: [n] (first partial slot i, tasks) per row; slot k at k n + i
     double *rfmax;         // [B]          1 / f_max
