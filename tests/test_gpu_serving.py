@@ -98,3 +98,33 @@ def test_admission_budget(env):
     rc, f, res = srv.poll(t, 24, timeout=60.0)
     srv.stop()
     assert rc == kx.OK
+
+
+def test_served_results_with_shared_contraction_grids_equal_solving_alone(env):
+    """Twelve requests on twelve different grids, submitted at once: more than
+    eight groups have work, so their FP32 contractions run with the shared
+    (half) grid; each result is still bit-identical to kx_solve alone (whole
+    GPU per launch).  A bad grid share is refused."""
+    kx, ctx, torch = env
+    with pytest.raises(kx.KxError):
+        kx.Server(ctx, precision=kx.FP32, grid_div=17, **PAR)
+    rng = np.random.default_rng(77)
+    reqs = []
+    for n in range(24, 48, 2):
+        q = ki.log_grid(n, 1e-3, 10.0)
+        reqs.append(dict(q=q, f0=ki.batch_bimodal(rng, q, 1)[0], sigma=float(rng.uniform(0.5, 2.0))))
+    srv = kx.Server(ctx, slots_per_group=2, attempts_per_tick=4, precision=kx.FP32, **PAR)
+    tickets = [srv.submit(r["q"], r["f0"], r["sigma"], t_end=20.0, h0=1e-3) for r in reqs]
+    served = []
+    for t, r in zip(tickets, reqs):
+        rc, f, res = srv.poll(t, r["q"].size, timeout=300.0)
+        assert rc == kx.OK, (rc, res)
+        served.append((f, res))
+    srv.stop()
+    for (f, res), r in zip(served, reqs):
+        k = ctx.build_kernel(r["q"], precision=kx.FP32)
+        fd = torch.as_tensor(r["f0"][None], device="cuda")
+        ra = ctx.solve(k, fd, r["sigma"], t_end=20.0, h0=1e-3, **PAR)[0]
+        np.testing.assert_array_equal(f, fd.cpu().numpy()[0])
+        assert res["steps"] == ra["steps"] and res["rejects"] == ra["rejects"]
+        k.release()
