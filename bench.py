@@ -361,7 +361,7 @@ def measure_uneven(ctx, kx, t_end=5.0, fp64_per_size=4):
             "speedup_vs_fp64_evals": out["split_tf32"]["evals_per_s"] / out["fp64"]["evals_per_s"]}
 
 
-def serve_stream(kx, ctx, reqs, precision, budget=96 << 30, slots=8, phases=("run",)):
+def serve_stream(kx, ctx, reqs, precision, budget=96 << 30, slots=2, phases=("run",)):
     """Submit `reqs` at their arrival times to one server; one result dict per phase
     (the same stream again in each phase, kernels cached after the first)."""
     par = dict(rtol=1e-6, atol=1e-12, l1_tol=1e-3, check_every=10, max_attempts=2_000_000)
@@ -416,7 +416,7 @@ def measure_serving(ctx, kx, requests=100, fp64_requests=8):
                                            if b["solves_per_s"] > 0 else None)
     out["workload"] = (f"{requests} requests of a Poisson stream (200 req/s), N ~ U{{64..384}}, "
                        "sigma logU[1e-2,10], two random source bumps each, full solves to "
-                       "L1<=1e-3 after the sources are off; FP32 path, 8 slots per kernel; "
+                       "L1<=1e-3 after the sources are off; FP32 path, 2 slots per kernel group; "
                        f"FP32 vs FP64 path on the first {fp64_requests} requests")
     return out
 
