@@ -200,7 +200,11 @@ int kx_collision_host(kx_ctx *ctx, const kx_kernel *k, int batch, const double *
  * n = 512 on the FP32 path or 15 on the FP64 path; larger requests return KX_EINVAL
  * with a message in kx_last_error.  The first call on a device looks up the
  * array's device address (cudaGetSymbolAddress); make that first call outside
- * any stream capture.  All calls share the one array: calls whose work can
+ * any stream capture.  That address is kept for the life of the process and
+ * is not looked up again: a caller that resets the device (cudaDeviceReset, or
+ * anything else that tears down its primary context) must not call this entry
+ * point afterwards.  If a bounded device wait of the contraction expires, C
+ * holds NaN.  All calls share the one array: calls whose work can
  * overlap on the GPU (other streams, other contexts on the same device) race
  * and must be serialised by the caller.  Only enqueues work on the stream. */
 int kx_collision_noalloc(kx_ctx *ctx, const kx_kernel *k, int batch, const double *sigma_host,
@@ -264,6 +268,11 @@ typedef struct {
     double p50_latency_s, p99_latency_s, mean_latency_s;   /* submit -> result available */
     double p50_wait_s;                                     /* submit -> admitted */
     long long evals;                                       /* collision evaluations done */
+    long long converged;          /* completed solves that met the L1 stopping test */
+    long long ticks_shared;       /* group graph launches on a share (1/grid_div) of the GPU */
+    long long ticks_whole;        /* group graph launches on the whole GPU */
+    double p99_wait_s;            /* submit -> admitted */
+    double p50_service_s, p99_service_s;   /* admitted -> result available */
 } kx_server_stats;
 
 /* Start a server on the context's device (the context's stream is not used).
@@ -378,20 +387,32 @@ int kx_source_condensate(int n, const double *q, double a, double mass, double m
  * KX_EINVAL for bad arguments, KX_ECUDA if the launch fails. */
 int kx_math_check(kx_ctx *ctx, int which, int n, const double *x_dev, double *out_dev);
 
+/* Self-check of the bounded device waits (no counterpart in the paper): every
+ * mbarrier wait of the library's kernels gives up after a cycle limit, sets an
+ * error flag and lets the kernel return, so that a lost copy cannot hang the
+ * GPU (the contraction then reports KX_ETIMEOUT: NaN in C, the diag status and
+ * the return value of kx_collision with diag, the instance status of a solve).
+ * This call launches one thread that waits, with a limit of `cycles` SM clock
+ * cycles (1 .. 2^32), on an mbarrier that nothing arrives on; *expired_host = 1
+ * when the wait gave up, as it must.  Synchronises the context's stream. */
+int kx_wait_check(kx_ctx *ctx, long long cycles, int *expired_host);
+
 /* Pins the FP32 path's streaming variant for grids of n points and batches of
  * `batch` instances on the context's device, in place of the autotuner's
  * choice (which is otherwise timed once per (device, n, batch) before the
  * first launch): 0 = one instance per pass, 1 = two per pass (batch >= 2),
  * 2 = four per pass, bulk-copy staged (n > 160, batch >= 4), 3 = four per
  * pass, register pipeline (batch >= 4); -1 forgets the
- * pinned or tuned choice.  All variants give bit-identical results; this is
+ * pinned or tuned choice.  The pin applies to whole-GPU launches and to the
+ * serving groups' launches on a share of the GPU alike (the autotuner keys its
+ * choice by that share as well).  All variants give bit-identical results; this is
  * for reproducible timing and for tests.  KX_EINVAL for a variant that does
  * not apply. */
 int kx_set_stream_variant(kx_ctx *ctx, int n, int batch, int variant);
 
 /* The FP32 streaming variant (numbering as for kx_set_stream_variant) that
- * contractions of n-point grids with `batch` instances use on the context's
- * device: the pinned or tuned one (*tuned = 1; tuned = NULL allowed), else the
+ * whole-GPU contractions of n-point grids with `batch` instances use on the
+ * context's device: the pinned or tuned one (*tuned = 1; tuned = NULL allowed), else the
  * rule used before tuning (*tuned = 0).  KX_EINVAL for bad arguments. */
 int kx_get_stream_variant(kx_ctx *ctx, int n, int batch, int *variant, int *tuned);
 

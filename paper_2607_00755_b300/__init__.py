@@ -28,7 +28,7 @@ EXPORTS = (
     "kx_solve", "kx_solve_host", "kx_mb_fit", "kx_launch_count", "kx_time_contraction",
     "kx_time_contractions", "kx_time_collision",
     "kx_collision_noalloc", "kx_server_start", "kx_submit", "kx_poll", "kx_server_get_stats",
-    "kx_server_stop", "kx_math_check", "kx_set_stream_variant", "kx_get_stream_variant",
+    "kx_server_stop", "kx_math_check", "kx_wait_check", "kx_set_stream_variant", "kx_get_stream_variant",
     "kx_source_higgs_decay", "kx_source_condensate",
 )
 
@@ -91,7 +91,9 @@ class ServerStats(ctypes.Structure):
                                                  "active", "kernels_built", "kernel_cache_hits",
                                                  "evictions")] + \
                [(k, ctypes.c_double) for k in ("p50_latency_s", "p99_latency_s", "mean_latency_s",
-                                               "p50_wait_s")] + [("evals", ctypes.c_longlong)]
+                                               "p50_wait_s")] + \
+               [(k, ctypes.c_longlong) for k in ("evals", "converged", "ticks_shared", "ticks_whole")] + \
+               [(k, ctypes.c_double) for k in ("p99_wait_s", "p50_service_s", "p99_service_s")]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -128,6 +130,7 @@ def load_library(path: str = LIB_PATH):
         "kx_solve_host": (i, [vp, vp, i, vp, vp, i, ctypes.POINTER(SolveParams), vp, vp]),
         "kx_mb_fit": (i, [vp, vp, i, vp, vp]),
         "kx_math_check": (i, [vp, i, i, vp, vp]),
+        "kx_wait_check": (i, [vp, ctypes.c_longlong, vp]),
         "kx_set_stream_variant": (i, [vp, i, i, i]),
         "kx_get_stream_variant": (i, [vp, i, i, vp, vp]),
         "kx_source_higgs_decay": (i, [i, vp, d, d, d, d, d, d, vp, vp]),
@@ -386,6 +389,15 @@ class Context:
             raise self.error(rc, "kx_math_check")
         torch.cuda.synchronize()
         return out
+
+    def wait_check(self, cycles):
+        """1 if a bounded device wait of `cycles` SM cycles on an mbarrier that
+        nothing arrives on gave up (kx_wait_check)."""
+        out = ctypes.c_int(-1)
+        rc = self.lib.kx_wait_check(self.h, int(cycles), ctypes.byref(out))
+        if rc:
+            raise self.error(rc, "kx_wait_check")
+        return out.value
 
 
 def source_higgs_decay(q, mass, m_h, T, coupling, g_chi=1.0, a=1.0):

@@ -580,11 +580,16 @@ static int kx_collision_impl(kx_ctx *ctx, const kx_kernel *k, int B, const doubl
     if (kx_tune_contraction(k, B, f_dev, v, nullptr, s, &ctx->launches))
         return kx_set_error(ctx, KX_ECUDA, "contraction autotuning failed");
     KX_CUDA_TRY(ctx, kx_launch_contract(k, B, f_dev, v, nullptr, 1, s));
+    // KX_FAULT=deverr: the flag a contraction sets when one of its bounded device
+    // waits expires is set from the host instead (no wait is made to expire)
+    if (kx_fault("deverr")) KX_CUDA_TRY(ctx, cudaMemsetAsync(v.err, 0x01, 1, s));
     KX_CUDA_TRY(ctx, kx_launch_finalize(k, B, f_dev, v, C_dev, project, diag != nullptr, s));
     ctx->launches += 3;
     if (diag) {
         KX_CUDA_TRY(ctx, cudaMemcpyAsync(diag, v.diag, sizeof(kx_diag) * B, cudaMemcpyDeviceToHost, s));
         KX_CUDA_TRY(ctx, cudaStreamSynchronize(s));
+        for (int b = 0; b < B; ++b)
+            if (diag[b].status == KX_ETIMEOUT) return kx_set_error(ctx, KX_ETIMEOUT, "a bounded device wait of the contraction expired");
         for (int b = 0; b < B; ++b)
             if (diag[b].status != KX_OK) return KX_ENONFINITE;
     }
@@ -833,6 +838,7 @@ static int kx_solve_run(kx_ctx *ctx, const kx_kernel *k, int B, const kx_run &r,
     ctx->launches += 1;
     if (kx_tune_contraction(k, B, r.sv.f, r.v, r.sv.st, s, &ctx->launches))
         return kx_set_error(ctx, KX_ECUDA, "contraction autotuning failed");
+    if (kx_fault("deverr")) KX_CUDA_TRY(ctx, cudaMemsetAsync(r.v.err, 0x01, 1, s));   // as in kx_collision
     const int G = 16;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
@@ -950,6 +956,20 @@ extern "C" int kx_mb_fit(kx_ctx *ctx, const kx_kernel *k, int B, const double *f
     KX_CUDA_TRY(ctx, kx_launch_mbfit(k, B, f_dev, d, ctx->stream));
     ctx->launches += 1;
     KX_CUDA_TRY(ctx, cudaMemcpyAsync(out, d, sizeof(double) * 3 * B, cudaMemcpyDeviceToHost, ctx->stream));
+    KX_CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
+    return KX_OK;
+}
+
+extern "C" int kx_wait_check(kx_ctx *ctx, long long cycles, int *expired_host) {
+    if (!ctx || !expired_host || cycles < 1 || cycles > KX_WAIT_CYCLES_MAX)
+        return kx_set_error(ctx, KX_EINVAL, "cycles must be in [1, 2^32]");
+    KX_CUDA_TRY(ctx, cudaSetDevice(ctx->device));
+    int rc = kx_arena_reserve(ctx, kx_align(sizeof(int)));
+    if (rc) return rc;
+    int *d = (int *)ctx->d_arena;
+    KX_CUDA_TRY(ctx, kx_launch_wait_check(cycles, d, ctx->stream));
+    ctx->launches += 1;
+    KX_CUDA_TRY(ctx, cudaMemcpyAsync(expired_host, d, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
     KX_CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
     return KX_OK;
 }

@@ -69,6 +69,24 @@ extern "C" int kx_math_check(kx_ctx *ctx, int which, int n, const double *x_dev,
     return cudaGetLastError() == cudaSuccess ? KX_OK : KX_ECUDA;
 }
 
+// Bounded-wait self-check: one thread initialises an mbarrier that expects one
+// arrival, never arrives on it, and waits for its phase with the given cycle
+// limit; *out = 1 if the wait gave up (the expected result), 0 if it completed.
+// No copy is in flight, so returning after the expiry is safe.
+__global__ void k_wait_check(long long limit, int *out) {
+    __shared__ __align__(8) unsigned long long bar;
+    if (threadIdx.x != 0) return;
+    const uint32_t a = kx_smem_u32(&bar);
+    kx_mbar_init(a, 1);
+    kx_fence_mbar_init();
+    *out = kx_mbar_wait(a, 0, limit) ? 0 : 1;
+}
+
+cudaError_t kx_launch_wait_check(long long cycles, int *out, cudaStream_t s) {
+    k_wait_check<<<1, 32, 0, s>>>(cycles, out);
+    return cudaGetLastError();
+}
+
 // ----------------------------------------------------------------- helpers
 __device__ __forceinline__ float kx_ex2(float x) {
     float y;
@@ -1165,7 +1183,11 @@ static cudaError_t kx_launch_stream_r(const kx_kernel *k, int B, const kx_batch_
 // speed: it is timed once per (device, grid size, batch) on the caller's own
 // prepared inputs and kept for the process.
 static std::mutex g_tune_mu;
-static std::map<std::tuple<int, int, int>, int> g_tuned;
+// tuned variant per (device, n, batch, grid share 1/grid_div): the same size
+// launched on a fraction of the GPU (the server's shared graphs) can rank the
+// variants differently from a whole-GPU launch
+static std::map<std::tuple<int, int, int, int>, int> g_tuned;
+static int kx_gd(int grid_div) { return grid_div > 1 ? grid_div : 1; }
 
 static void kx_stream_candidates(const kx_kernel *k, int B, int *cand, int *nc) {
     *nc = 0;
@@ -1182,11 +1204,11 @@ static int kx_stream_default(const kx_kernel *k, int B) {
     return B >= 4 ? 2 : (B >= 2 ? 1 : 0);
 }
 
-static int kx_stream_variant(const kx_kernel *k, int B) {
+static int kx_stream_variant(const kx_kernel *k, int B, int grid_div) {
     int dev = 0;
     cudaGetDevice(&dev);
     std::lock_guard<std::mutex> lock(g_tune_mu);
-    auto it = g_tuned.find(std::make_tuple(dev, k->n, B));
+    auto it = g_tuned.find(std::make_tuple(dev, k->n, B, kx_gd(grid_div)));
     return it != g_tuned.end() ? it->second : kx_stream_default(k, B);
 }
 
@@ -1234,7 +1256,7 @@ int kx_tune_contraction(const kx_kernel *k, int B, const double *f, const kx_bat
     if (k->precision != KX_FP32 || k->stats) return 0;   // quantum statistics: one variant
     int dev = 0;
     cudaGetDevice(&dev);
-    const auto key = std::make_tuple(dev, k->n, B);
+    const auto key = std::make_tuple(dev, k->n, B, kx_gd(v.grid_div));
     {
         std::lock_guard<std::mutex> lock(g_tune_mu);
         if (g_tuned.count(key)) return 0;
@@ -1293,7 +1315,7 @@ extern "C" int kx_get_stream_variant(kx_ctx *ctx, int n, int batch, int *variant
     if (!ctx || !variant || n < 4 || n > KX_MAX_N || batch < 1) return KX_EINVAL;
     kx_kernel probe;
     probe.vpl = n <= 160 ? 2 : 4;
-    const auto key = std::make_tuple(ctx->device, n, batch);
+    const auto key = std::make_tuple(ctx->device, n, batch, 1);
     std::lock_guard<std::mutex> lock(g_tune_mu);
     auto it = g_tuned.find(key);
     *variant = it != g_tuned.end() ? it->second : kx_stream_default(&probe, batch);
@@ -1307,10 +1329,13 @@ extern "C" int kx_set_stream_variant(kx_ctx *ctx, int n, int batch, int variant)
     if (variant == 1 && batch < 2) return KX_EINVAL;
     if (variant == 2 && (vpl != 4 || batch < 4)) return KX_EINVAL;
     if (variant == 3 && batch < 4) return KX_EINVAL;
-    const auto key = std::make_tuple(ctx->device, n, batch);
+    // pinned (or forgotten) for every grid share
     std::lock_guard<std::mutex> lock(g_tune_mu);
-    if (variant < 0) g_tuned.erase(key);
-    else g_tuned[key] = variant;
+    for (int gd = 1; gd <= 16; ++gd) {
+        const auto key = std::make_tuple(ctx->device, n, batch, gd);
+        if (variant < 0) g_tuned.erase(key);
+        else g_tuned[key] = variant;
+    }
     return KX_OK;
 }
 
@@ -1327,7 +1352,7 @@ cudaError_t kx_launch_contract(const kx_kernel *k, int B, const double *f, const
     // the variant tuned for this size and batch (or the default rule)
     // (only the streaming kernels wait for their predecessor: the other paths'
     // contractions always launch in full stream order)
-    return kx_stream_launch(kx_stream_variant(k, B), k, B, v, st, stage, s, pdl);
+    return kx_stream_launch(kx_stream_variant(k, B, v.grid_div), k, B, v, st, stage, s, pdl);
 }
 
 // ---------------------------------------------------- row combine + projection
@@ -1478,10 +1503,17 @@ __global__ void __launch_bounds__(KX_FIN_THREADS)
         Ei = E[i];
         hi = h[i];
     }
+    // a contraction whose bounded device wait expired left partials unfilled:
+    // its C is NaN and the diagnostics say KX_ETIMEOUT
+    const int timed_out = *v.err;
     kx_row_out r = kx_combine_project(n, chunks, path, b, fi, Ei, hi, v, project, smem);
-    if (i < n) Cout[(long long)b * n + i] = project ? r.Cproj : r.Craw;
+    if (i < n) Cout[(long long)b * n + i] = timed_out ? __longlong_as_double(0x7ff8000000000000ll)
+                                                      : (project ? r.Cproj : r.Craw);
     __syncthreads();   // every thread has read the projection sums (sm[5T ..])
-    if (want_diag) kx_write_diag(n, Ei, hi, r, v.diag + b, v.fmax[b], v.flags[b], smem);
+    if (want_diag) {
+        kx_write_diag(n, Ei, hi, r, v.diag + b, v.fmax[b], v.flags[b], smem);
+        if (timed_out && threadIdx.x == 0) v.diag[b].status = KX_ETIMEOUT;
+    }
 }
 
 cudaError_t kx_launch_finalize(const kx_kernel *k, int B, const double *f, const kx_batch_views &v,
@@ -1640,6 +1672,7 @@ __device__ __forceinline__ void kx_stage_body(int b, int n, int chunks, int path
     const double fpv = (in && stage == 2) ? fp[i] : 0.0;
     const double k1v = (in && stage == 2) ? k1[i] : 0.0;
     const int flag_in = v.flags[b];
+    const int timed_out = *v.err;   // a contraction's bounded device wait expired
     pre.lines = path == KX_FP32 ? v.fit[b] : make_float4(0.f, 0.f, 0.f, 0.f);
     // Every thread takes its copy of the instance state here, before the first
     // block barrier: thread 0 rewrites the state at the end of the stage, and a
@@ -1660,6 +1693,14 @@ __device__ __forceinline__ void kx_stage_body(int b, int n, int chunks, int path
     const double fcur = stage == 1 ? f0 : fpv;
     kx_row_out r = kx_combine_project(n, chunks, path, b, fcur, Ei, hi, v, sv.project, smem);
     if (done0) return;
+    if (timed_out) {   // its partials are incomplete: stop the instance, report it
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            st->status = KX_ETIMEOUT;
+            st->done = 1;
+        }
+        return;
+    }
     if (stage == 2 && skip2_0) {
         __syncthreads();
         if (threadIdx.x == 0) st->skip2 = 0;

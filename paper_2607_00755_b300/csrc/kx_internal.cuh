@@ -23,6 +23,7 @@
 #define KX_T32 256            // threads per FP32 contraction block
 #define KX_BINS 2368          // equal-work bins of the FP32 contraction (148 SMs x 16 warps)
 #define KX_FIN_THREADS 512    // finalize / stage kernels: one block per instance, thread = grid point
+#define KX_WAIT_CYCLES_MAX (4ll << 30)   // longest bounded device wait (the kernels' own limit, ~2 s)
 
 struct kx_gl_nodes {
     double x[KX_MAX_NMU];
@@ -225,6 +226,10 @@ cudaError_t kx_launch_stage(const kx_kernel *k, int B, const kx_batch_views &v,
 // st (nullable) gives each instance's last in-solve temperature as the start.
 cudaError_t kx_launch_mbfit(const kx_kernel *k, int nb, const double *f, double *out3,
                             cudaStream_t s, const kx_inst_state *st = nullptr, const int *idx = nullptr);
+
+// bounded-wait self-check: *out = 1 if a wait on an mbarrier nothing arrives
+// on gave up after `cycles` SM clock cycles
+cudaError_t kx_launch_wait_check(long long cycles, int *out, cudaStream_t s);
 
 // batched split-TF32 path (kx_batch.cu)
 int kx_batch_build_tables(kx_ctx *ctx, kx_kernel *k);   // after the FP64 build

@@ -85,9 +85,12 @@ extern "C" int kx_collision_noalloc(kx_ctx *ctx, const kx_kernel *k, int B,
     if (rc) return rc;
     // Every scratch word a call reads is written earlier in the same call (the
     // prepared tables by the prep kernel, every partial by the contraction,
-    // M2 below), so nothing needs clearing between calls.
+    // M2 below), except the flag a contraction sets when one of its bounded
+    // device waits expires: that one is cleared here (a memset allocates
+    // nothing), so that an expiry in one call is not reported by the next.
     kx_batch_views v;
     kx_carve_views(k, B, base, &v);
+    KX_CUDA_TRY(ctx, cudaMemsetAsync(v.err, 0, sizeof(int), ctx->stream));
     kx_noalloc_m2 m2;
     for (int b = 0; b < KX_NOALLOC_MAX_BATCH; ++b)
         m2.m2[b] = b < B ? 64.0 * 3.14159265358979323846 * k->mass * k->mass * sigma_host[b] : 0.0;

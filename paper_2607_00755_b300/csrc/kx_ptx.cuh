@@ -36,11 +36,13 @@ __device__ __forceinline__ bool kx_mbar_try_wait(uint32_t bar, uint32_t parity) 
         : "memory");
     return ok != 0;
 }
-// Waits for the phase with the given parity; gives up after KX_WAIT_CYCLES.
-__device__ __forceinline__ bool kx_mbar_wait(uint32_t bar, uint32_t parity) {
+// Waits for the phase with the given parity; gives up after `limit` SM clock
+// cycles (KX_WAIT_CYCLES unless a caller asks for less) and returns false.
+__device__ __forceinline__ bool kx_mbar_wait(uint32_t bar, uint32_t parity,
+                                             long long limit = KX_WAIT_CYCLES) {
     const long long t0 = clock64();
     while (!kx_mbar_try_wait(bar, parity))
-        if (clock64() - t0 > KX_WAIT_CYCLES) return false;
+        if (clock64() - t0 > limit) return false;
     return true;
 }
 __device__ __forceinline__ void kx_bulk_g2s(uint32_t dst, const void *src, uint32_t bytes,

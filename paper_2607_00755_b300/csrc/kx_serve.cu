@@ -93,7 +93,7 @@ struct kx_server {
     size_t used = 0;
     kx_ticket next_id = 1;
     kx_server_stats stats;
-    std::vector<double> lat, wait;
+    std::vector<double> lat, wait, service;   // submit->done, submit->admit, admit->done
 };
 
 // ------------------------------------------------------------------ helpers
@@ -244,9 +244,11 @@ static int kx_make_group(kx_server *srv, const Request &r, Group **out) {
     if (e == cudaSuccess) e = cudaStreamSynchronize(g->stream);
     // pick the streaming variant for this size and slot count before capture
     // (timed on the group's zeroed tables: same work as real inputs)
-    g->v.grid_div = srv->cfg.grid_div;   // tuned as the shared graph launches it
-    if (e == cudaSuccess && kx_tune_contraction(k, cap, g->sv.f, g->v, nullptr, g->stream, nullptr))
-        e = cudaErrorUnknown;
+    // (tuned for each grid share the group's graphs launch with)
+    for (int pass = 0; pass < (srv->cfg.grid_div > 1 ? 2 : 1) && e == cudaSuccess; ++pass) {
+        g->v.grid_div = pass == 0 ? srv->cfg.grid_div : 1;
+        if (kx_tune_contraction(k, cap, g->sv.f, g->v, nullptr, g->stream, nullptr)) e = cudaErrorUnknown;
+    }
     // captured graph of attempts_per_tick Heun attempts over all slots: one with
     // the shared contraction grid and, if that is a fraction, one with the
     // whole GPU (the worker picks by the number of groups with work)
@@ -359,7 +361,9 @@ static void kx_complete(kx_server *srv, Group *g) {
         o.latency_s = r->t_done - r->t_submit;
         r->status = o.status;
         srv->stats.completed += o.status == KX_OK;
+        srv->stats.converged += o.status == KX_OK && o.converged;
         srv->stats.failed += o.status != KX_OK;
+        srv->service.push_back(r->t_done - r->t_admit);
         srv->stats.active--;
         srv->stats.evals += st.evals;
         srv->lat.push_back(o.latency_s);
@@ -496,7 +500,13 @@ static void kx_worker(kx_server *srv) {
                 e = kx_launch_prep(g->k, g->cap, g->sv.f, g->v, g->sv.st, g->stream);
                 g->need_prep = false;
             }
-            if (e == cudaSuccess) e = cudaGraphLaunch(shared || !g->exec1 ? g->exec : g->exec1, g->stream);
+            const bool on_share = shared || !g->exec1;
+            if (e == cudaSuccess) e = cudaGraphLaunch(on_share ? g->exec : g->exec1, g->stream);
+            if (e == cudaSuccess) {
+                std::lock_guard<std::mutex> lock(srv->mu);
+                if (on_share && srv->cfg.grid_div > 1) srv->stats.ticks_shared++;
+                else srv->stats.ticks_whole++;
+            }
             if (e == cudaSuccess)
                 e = cudaMemcpyAsync(g->h_st, g->sv.st, sizeof(kx_inst_state) * g->cap,
                                     cudaMemcpyDeviceToHost, g->stream);
@@ -657,6 +667,9 @@ extern "C" int kx_server_get_stats(kx_server *srv, kx_server_stats *out) {
     for (double x : srv->lat) m += x;
     out->mean_latency_s = srv->lat.empty() ? 0.0 : m / srv->lat.size();
     out->p50_wait_s = kx_quantile(srv->wait, 0.5);
+    out->p99_wait_s = kx_quantile(srv->wait, 0.99);
+    out->p50_service_s = kx_quantile(srv->service, 0.5);
+    out->p99_service_s = kx_quantile(srv->service, 0.99);
     return KX_OK;
 }
 

@@ -1,8 +1,9 @@
 """Failure paths through host-side fault injection (KX_FAULT): allocation
 failures, admission refusal, a non-finite staged input and an expired host
 wait each return their error code, and the context keeps working afterwards.
-No injected failure touches the GPU (no kernel faults, traps or waits on a
-flag that nothing sets)."""
+No injected failure touches the GPU (no kernel faults or traps); the one
+device wait made to expire is a self-check kernel's wait on an mbarrier that
+nothing arrives on, with a limit of about 1 ms and no copy in flight."""
 import time
 
 import numpy as np
@@ -108,3 +109,47 @@ def test_injected_admission_refusal(env, monkeypatch):
             break
     assert rc == kx.OK and res["status"] == 0 and np.all(np.isfinite(fo))
     srv.stop()
+
+
+@pytest.mark.parametrize("precision", ["FP64", "FP32", "SPLIT_TF32"])
+def test_expired_device_wait_is_reported(env, monkeypatch, precision):
+    """The flag a contraction sets when one of its bounded device waits expires
+    (KX_FAULT=deverr sets it from the host; no wait is made to expire here):
+    kx_collision with diagnostics returns KX_ETIMEOUT and C is NaN, a solve
+    stops every instance with KX_ETIMEOUT, and the next calls are clean."""
+    kx, ctx, torch = env
+    q, f = grid_and_f()
+    k = ctx.build_kernel(q, precision=getattr(kx, precision))
+    fd = torch.as_tensor(f, device="cuda")
+    ref, _ = ctx.collision(k, fd, 1.0)
+    monkeypatch.setenv("KX_FAULT", "deverr")
+    with pytest.raises(kx.KxError) as ei:
+        ctx.collision(k, fd, 1.0, diag=True)
+    assert ei.value.code == kx.ETIMEOUT
+    C, _ = ctx.collision(k, fd, 1.0)
+    assert np.all(np.isnan(C.cpu().numpy()))
+    with pytest.raises(kx.KxError) as ei:
+        ctx.solve(k, torch.as_tensor(f, device="cuda"), 1.0, t_end=0.5, h0=1e-3)
+    assert ei.value.code == kx.ETIMEOUT
+    monkeypatch.delenv("KX_FAULT")
+    C2, d2 = ctx.collision(k, fd, 1.0, diag=True)
+    assert all(x["status"] == 0 for x in d2)
+    np.testing.assert_array_equal(C2.cpu().numpy(), ref.cpu().numpy())
+    res = ctx.solve(k, torch.as_tensor(f, device="cuda"), 1.0, t_end=0.5, h0=1e-3)
+    assert all(r["status"] == 0 for r in res)
+    k.release()
+
+
+def test_bounded_device_wait_gives_up(env):
+    """A device wait on an mbarrier that nothing arrives on gives up after its
+    cycle limit (about 1 ms here) and the kernel returns: the context stays
+    usable (a collision afterwards is exact)."""
+    kx, ctx, torch = env
+    t0 = time.time()
+    assert ctx.wait_check(2_000_000) == 1
+    assert time.time() - t0 < 30.0
+    q, f = grid_and_f()
+    k = ctx.build_kernel(q, precision=kx.FP32)
+    C, d = ctx.collision(k, torch.as_tensor(f, device="cuda"), 1.0, diag=True)
+    assert all(x["status"] == 0 for x in d) and np.all(np.isfinite(C.cpu().numpy()))
+    k.release()

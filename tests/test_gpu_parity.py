@@ -180,8 +180,10 @@ def test_collision_matches_oracle(ctx, kx, precision, N):
 
 @pytest.mark.parametrize("precision", [0, 1])
 def test_collision_full_size_sampled_rows(ctx, kx, precision):
-    """N = 384 and 512 (the maximum): every row on the GPU, sampled rows by the
-    oracle's direct per-row form."""
+    """N = 384 and 512 (the maximum): every row on the GPU; every 8th row, both
+    ends and a few random rows by the oracle's direct per-row form.  The
+    tolerance scale is the largest |C| among the oracle's rows, never the GPU's
+    own output (a kernel that inflated a row cannot loosen its own bound)."""
     for N in (384, 512):
         rng = np.random.default_rng(N)
         q = ki.log_grid(N, 1e-3, 1e2)
@@ -189,10 +191,17 @@ def test_collision_full_size_sampled_rows(ctx, kx, precision):
         k = ctx.build_kernel(q, precision=precision)
         C, _ = ctx.collision(k, dev(f[None]), 1.0, project=False)
         C = C.cpu().numpy()[0]
-        rows = np.unique(np.concatenate([[0, 1, N // 2, N - 2, N - 1], rng.integers(0, N, 5)]))
+        assert np.all(np.isfinite(C))
+        rows = np.unique(np.concatenate([np.arange(0, N, 8), [1, N // 2 + 3, N - 2, N - 1],
+                                         rng.integers(0, N, 6)]))
         Co, G, L = oracle.collision_rows(q, f, rows, M2=oracle.M2_from_sigma(1.0, 1.0))
-        scale = np.max(np.abs(C))
-        assert np.max(np.abs(C[rows] - Co)) <= TOL[precision] * scale
+        scale = np.max(np.abs(Co))
+        err = np.max(np.abs(C[rows] - Co)) / scale
+        assert err <= TOL[precision], (N, err)
+        # the unsampled rows cannot exceed the sampled maximum by much: the
+        # operator is smooth in i (a row larger than twice the sampled maximum
+        # would be a kernel fault, not physics)
+        assert np.max(np.abs(C)) <= 2.0 * scale
         k.release()
 
 

@@ -120,7 +120,10 @@ def test_served_results_with_shared_contraction_grids_equal_solving_alone(env):
         rc, f, res = srv.poll(t, r["q"].size, timeout=300.0)
         assert rc == kx.OK, (rc, res)
         served.append((f, res))
+    st = srv.stats()
     srv.stop()
+    # the shared-grid graphs did run (more than eight groups had work at once)
+    assert st["ticks_shared"] > 0, st
     for (f, res), r in zip(served, reqs):
         k = ctx.build_kernel(r["q"], precision=kx.FP32)
         fd = torch.as_tensor(r["f0"][None], device="cuda")

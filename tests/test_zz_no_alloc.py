@@ -15,7 +15,7 @@ import kx_inputs as ki
 
 pytestmark = pytest.mark.gpu
 
-TOL = {0: 1e-12, 1: 1e-5}
+TOL = {0: 1e-12, 1: 1e-5, 2: 1e-5}
 
 
 @pytest.fixture(scope="module")
@@ -38,11 +38,13 @@ def call_noalloc(kx, ctx, kernel, f, sigma, C, project):
                                         ctypes.c_void_p(C.data_ptr()), int(project))
 
 
-@pytest.mark.parametrize("precision,stats", [(0, 0), (1, 0), (1, 1)])
+@pytest.mark.parametrize("precision,stats", [(0, 0), (1, 0), (1, 1), (2, 0)])
 def test_noalloc_matches_kx_collision_twice(env, precision, stats):
     """Two calls in a row (different inputs, so stale scratch from the first
-    would show) agree with kx_collision within the parity tolerance (also with
-    the Bose-Einstein factor on the FP32 path)."""
+    would show) give kx_collision's results bit for bit: the two entry points
+    run the same kernels on the same inputs, only the scratch differs.  Paths:
+    plain FP64, FP32 streaming (also with the Bose-Einstein factor) and the
+    split-TF32 tensor-core path."""
     kx, ctx, torch = env
     n = 96
     q = ki.log_grid(n, 1e-3, 10.0)
@@ -54,14 +56,35 @@ def test_noalloc_matches_kx_collision_twice(env, precision, stats):
         sig = rng.uniform(0.5, 5.0, size=B)
         for project in (0, 1):
             ref, _ = ctx.collision(k, f, sig, project=bool(project))
-            C = torch.empty_like(f)
+            C = torch.full_like(f, float("nan"))
             rc = call_noalloc(kx, ctx, k, f, sig, C, project)
             assert rc == 0, ctx.lib.kx_last_error(ctx.h)
             torch.cuda.synchronize()
-            r, c = ref.cpu().numpy(), C.cpu().numpy()
-            for b in range(B):
-                err = np.max(np.abs(c[b] - r[b])) / np.max(np.abs(r[b]))
-                assert err <= TOL[precision], (call, project, b, err)
+            np.testing.assert_array_equal(C.cpu().numpy(), ref.cpu().numpy())
+    k.release()
+
+
+@pytest.mark.parametrize("precision", [0, 1, 2])
+def test_noalloc_matches_oracle(env, precision):
+    """The allocation-free call against the FP64 oracle (projected C of a
+    bimodal batch) at the parity tolerance of each path."""
+    import oracle
+    kx, ctx, torch = env
+    n = 40
+    q = ki.log_grid(n, 1e-3, 10.0)
+    f = ki.batch_bimodal(np.random.default_rng(43), q, 3)
+    sig = np.array([0.7, 1.0, 3.0])
+    k = ctx.build_kernel(q, precision=precision)
+    C = torch.empty((3, n), dtype=torch.float64, device="cuda")
+    assert call_noalloc(kx, ctx, k, torch.as_tensor(f, device="cuda"), sig, C, 1) == 0
+    torch.cuda.synchronize()
+    C = C.cpu().numpy()
+    g = oracle.grid(q)
+    W = oracle.kernel_tensor(q)
+    for b in range(3):
+        Co = oracle.collision_tensor(q, W, f[b]) * oracle.M2_from_sigma(1.0, sig[b])
+        Co, _ = oracle.project(g["E"], g["h"], f[b], Co)
+        assert np.max(np.abs(C[b] - Co)) / np.max(np.abs(Co)) <= TOL[precision], b
     k.release()
 
 
