@@ -87,6 +87,16 @@ typedef struct {
                          log interpolation of f (FP64 and FP32 paths; KX_SPLIT_TF32 ->
                          KX_ENOTSUP) */
     int precision;    /* KX_FP64 | KX_FP32 | KX_SPLIT_TF32 */
+    int loss_terms;   /* KX_SPLIT_TF32 only (else must be 0): 0 = exact loss (one exp2 per element
+                         and instance); 8, 16 or 32 = the loss rate as a second tensor-core GEMM
+                         L = M Y with the interpolated f_t of eq. app_log_interp expanded in that
+                         many Chebyshev polynomials of t = 2 omega - 1:
+                           f_t = f_j e^{d/2} sum_k eps_k I_k(d/2) T_k(t), d = ln f_{j+1} - ln f_j,
+                           M_k[i][j] = sum_{(n,m): j_L = j} S_inm T_k(2 omega_inm - 1) (kernel table),
+                           Y_k[j][b] = f_jb e^{d/2} eps_k I_k(d/2) (per call, from f).
+                         Truncation error of a bracket <= max(f_j, f_{j+1}) 2 sum_{k>=K} e^{-|d|/2}
+                         I_k(|d|/2); an instance with a bracket whose bound exceeds 2^-30 f_max
+                         has its loss evaluated exactly instead (same result as loss_terms = 0). */
 } kx_grid_desc;
 
 /* Synthetic freeze-in sources: S_i(t) = sum_k rate_k env_k(t) shape_k,i / sum_j h_j shape_k,j,
@@ -260,6 +270,7 @@ typedef struct {
                                     the GPU's resident blocks, so that several groups'
                                     contractions run side by side; with fewer, with all of
                                     them (results do not depend on it); 1..16, 0 = 2 */
+    int loss_terms;              /* kx_grid_desc.loss_terms of every kernel (KX_SPLIT_TF32) */
 } kx_server_config;
 
 typedef struct {

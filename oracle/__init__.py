@@ -9,7 +9,7 @@ contraction); this module only compiles it (``gcc``) and marshals numpy arrays.
 Parity status per function (pins live in ``tests/test_oracle_pins.py``):
   grid, gauss_legendre, nu integrals, F, F_exact, kernel_tensor, bracket,
   collision_tensor, collision_tensor_stats, collision_direct, project, source,
-  mb_fit, solve: pinned.
+  mb_fit, solve, bessel_ive, collision_chebyshev: pinned.
 """
 from __future__ import annotations
 
@@ -69,6 +69,8 @@ def _load():
         "oracle_solve": (i, [i, vp, d, d, vp, d, i, vp, vp, vp, vp, vp, vp, vp]),
         "oracle_M2_from_sigma": (d, [d, d]),
         "oracle_collision_rows": (i, [i, vp, d, d, d, i, i, vp, i, vp, vp, vp, vp]),
+        "oracle_bessel_ive": (i, [i, d, vp]),
+        "oracle_loss_chebyshev": (i, [i, vp, d, d, vp, vp, i, vp, vp, vp, vp]),
         "oracle_num_threads": (i, []),
         "oracle_set_threads": (None, [i]),
     }
@@ -194,6 +196,29 @@ def collision_tensor_stats(q, W, f, eta, a=1.0, mass=1.0):
     if rc:
         raise ValueError(rc)
     return C
+
+
+def bessel_ive(K, x):
+    """e^{-x} I_k(x) for k = 0 .. K-1 (power series; x >= 0)."""
+    out = np.empty(int(K))
+    rc = _load().oracle_bessel_ive(int(K), float(x), _p(out))
+    if rc:
+        raise ValueError(rc)
+    return out
+
+
+def collision_chebyshev(q, W, f, K, a=1.0, mass=1.0):
+    """C_raw with the loss rate's interpolated f_t expanded in K Chebyshev terms
+    of t = 2 omega - 1 (coefficients e^{d/2} eps_k I_k(d/2)); returns
+    (C, G, L, bound) with |L - exact L| <= bound row by row."""
+    q, W, f = _f64(q), _f64(W), _f64(f)
+    n = q.size
+    C, G, L, B = (np.empty(n) for _ in range(4))
+    rc = _load().oracle_loss_chebyshev(n, _p(q), a, mass, _p(W), _p(f), int(K), _p(C), _p(G),
+                                       _p(L), _p(B))
+    if rc:
+        raise ValueError(rc)
+    return C, G, L, B
 
 
 def collision_direct(q, f, a=1.0, mass=1.0, M2=1.0, n_mu=18, measure=MEASURE_ENERGY):

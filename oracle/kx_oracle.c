@@ -798,3 +798,110 @@ out:
     free(p); free(E); free(dp); free(dE); free(h); free(lf); free(x); free(w);
     return rc;
 }
+
+/* ------------------------------------------- Chebyshev loss expansion --- */
+/* Exponentially scaled modified Bessel functions of the first kind,
+ *   ive[k] = e^{-x} I_k(x),  k = 0 .. K-1,  x >= 0,
+ * from the power series I_k(x) = sum_{m>=0} (x/2)^{2m+k} / (m! (m+k)!)
+ * (Abramowitz & Stegun 9.6.10), each term formed as exp of its logarithm
+ * (lgamma) so that large x does not overflow; summed until past the largest
+ * term and below 1e-20 of the sum. */
+int oracle_bessel_ive(int K, double x, double *ive) {
+    if (K < 1 || !(x >= 0.0)) return OR_EINVAL;
+    for (int k = 0; k < K; ++k) {
+        if (x == 0.0) { ive[k] = k == 0 ? 1.0 : 0.0; continue; }
+        double lx = log(0.5 * x), s = 0.0;
+        for (int m = 0; m < 100000; ++m) {
+            double lt = (2.0 * m + k) * lx - lgamma(m + 1.0) - lgamma(m + k + 1.0) - x;
+            double t = exp(lt);
+            s += t;
+            if (m > 0.5 * x + 2 && t < 1e-20 * s) break;
+        }
+        ive[k] = s;
+    }
+    return OR_OK;
+}
+
+/* Loss rate of eq. (discrete_collision_operator) with the interpolated f_t of
+ * eq. (app_log_interp) expanded in Chebyshev polynomials of t = 2 omega - 1.
+ * With d = ln f_{jL+1} - ln f_jL (logs of max(f, 1e-300), reading A5),
+ *   f_t = f_jL e^{omega d} = f_jL e^{d/2} e^{t d/2}
+ *       = f_jL e^{d/2} sum_k eps_k I_k(d/2) T_k(t),   eps_0 = 1, eps_k = 2
+ * (the generating function of I_k: e^{x cos theta} = sum eps_k I_k(x) cos k theta),
+ * truncated after K terms:
+ *   M_k[i][j] = sum_{n,m: jL(i,n,m) = j} W_inm T_k(2 omega_inm - 1),
+ *   Y_k[j]    = f_j e^{d_j/2} eps_k I_k(d_j/2),      I_k(-x) = (-1)^k I_k(x),
+ *   L_i       = sum_j sum_{k<K} M_k[i][j] Y_k[j].
+ * Since f_j e^{d/2} I_k(d/2) = max(f_j, f_{j+1}) (+-1)^k e^{-|d|/2} I_k(|d|/2) and
+ * |T_k| <= 1, the truncation error of row i is at most
+ *   bound[i] = sum_{n,m} W_inm max(f_j, f_{j+1}) 2 sum_{k>=K} e^{-|d_j|/2} I_k(|d_j|/2).
+ * C[i] = sum W f_n f_m - f_i L_i (dilute), G[i] the gain.  W as from
+ * oracle_kernel_tensor ([i][n][m]).  T_k from the three-term recurrence. */
+int oracle_loss_chebyshev(int n, const double *q, double a, double mass, const double *W,
+                          const double *f, int K, double *C, double *G, double *L, double *bound) {
+    if (n < 2 || K < 1) return OR_EINVAL;
+    const int KT = K + 80;   /* terms of the tail sum (enough for |d|/2 up to ~40) */
+    double *p = malloc(sizeof(double) * n), *E = malloc(sizeof(double) * n);
+    double *dp = malloc(sizeof(double) * n), *dE = malloc(sizeof(double) * n);
+    double *h = malloc(sizeof(double) * n), *lf = malloc(sizeof(double) * n);
+    double *M = calloc((size_t)n * n * K, sizeof(double));     /* M[i][j][k] */
+    double *Y = malloc(sizeof(double) * (size_t)n * K);        /* Y[j][k] */
+    double *tail = malloc(sizeof(double) * n);                 /* per bracket j */
+    double *iv = malloc(sizeof(double) * KT);
+    int rc = OR_OK;
+    if (!p || !E || !dp || !dE || !h || !lf || !M || !Y || !tail || !iv) { rc = OR_ENOMEM; goto out; }
+    rc = oracle_grid(n, q, a, mass, p, E, dp, dE, h);
+    if (rc) goto out;
+    for (int j = 0; j < n; ++j) lf[j] = log_floor(f[j]);
+    /* Y_k[j] and the truncation tail of bracket j */
+    for (int j = 0; j + 1 < n; ++j) {
+        double d = lf[j + 1] - lf[j], x = 0.5 * fabs(d);
+        double fmx = exp(lf[j] > lf[j + 1] ? lf[j] : lf[j + 1]);
+        rc = oracle_bessel_ive(KT, x, iv);
+        if (rc) goto out;
+        for (int k = 0; k < K; ++k) {
+            double sg = (d < 0.0 && (k & 1)) ? -1.0 : 1.0;
+            Y[(size_t)j * K + k] = fmx * (k == 0 ? 1.0 : 2.0) * sg * iv[k];
+        }
+        double tl = 0.0;
+        for (int k = KT - 1; k >= K; --k) tl += iv[k];
+        tail[j] = fmx * 2.0 * tl;
+    }
+    /* M_k[i][j] */
+    for (int i = 0; i < n; ++i) {
+        double bi = 0.0;
+        for (int nn = 0; nn < n; ++nn) {
+            for (int mm = 0; mm < n; ++mm) {
+                double Wv = W[((size_t)i * n + nn) * n + mm];
+                if (Wv == 0.0) continue;
+                double Et = (E[nn] + E[mm]) - E[i];
+                int j;
+                double om;
+                if (!oracle_bracket(n, E, Et, &j, &om)) continue;
+                double t = 2.0 * om - 1.0, T0 = 1.0, T1 = t;
+                double *Mij = M + ((size_t)i * n + j) * K;
+                for (int k = 0; k < K; ++k) {
+                    double Tk = k == 0 ? 1.0 : (k == 1 ? t : 2.0 * t * T1 - T0);
+                    if (k >= 2) { T0 = T1; T1 = Tk; }
+                    Mij[k] += Wv * Tk;
+                }
+                bi += Wv * tail[j];
+            }
+        }
+        bound[i] = bi;
+    }
+    /* L_i = sum_j sum_k M_k[i][j] Y_k[j];  C_i = G_i - f_i L_i */
+    for (int i = 0; i < n; ++i) {
+        double Li = 0.0, Gi = 0.0;
+        for (int j = 0; j + 1 < n; ++j)
+            for (int k = 0; k < K; ++k) Li += M[((size_t)i * n + j) * K + k] * Y[(size_t)j * K + k];
+        for (int nn = 0; nn < n; ++nn)
+            for (int mm = 0; mm < n; ++mm) Gi += W[((size_t)i * n + nn) * n + mm] * (f[nn] * f[mm]);
+        L[i] = Li;
+        G[i] = Gi;
+        C[i] = Gi - f[i] * Li;
+    }
+out:
+    free(p); free(E); free(dp); free(dE); free(h); free(lf); free(M); free(Y); free(tail); free(iv);
+    return rc;
+}

@@ -36,7 +36,7 @@ EXPORTS = (
 class GridDesc(ctypes.Structure):
     _fields_ = [("n", ctypes.c_int), ("q", ctypes.c_void_p), ("a", ctypes.c_double),
                 ("mass", ctypes.c_double), ("n_mu", ctypes.c_int), ("measure", ctypes.c_int),
-                ("stats", ctypes.c_int), ("precision", ctypes.c_int)]
+                ("stats", ctypes.c_int), ("precision", ctypes.c_int), ("loss_terms", ctypes.c_int)]
 
 
 class Source(ctypes.Structure):
@@ -83,7 +83,7 @@ class ServerConfig(ctypes.Structure):
     _fields_ = [("hbm_budget_bytes", ctypes.c_longlong), ("slots_per_group", ctypes.c_int),
                 ("attempts_per_tick", ctypes.c_int), ("precision", ctypes.c_int),
                 ("n_mu", ctypes.c_int), ("measure", ctypes.c_int), ("par", SolveParams),
-                ("grid_div", ctypes.c_int)]
+                ("grid_div", ctypes.c_int), ("loss_terms", ctypes.c_int)]
 
 
 class ServerStats(ctypes.Structure):
@@ -210,9 +210,9 @@ class Context:
 
     # -------------------------------------------------------------- kernels
     def build_kernel(self, q, mass=1.0, a=1.0, n_mu=18, measure=MEASURE_ENERGY,
-                     precision=FP64, stats=0):
+                     precision=FP64, stats=0, loss_terms=0):
         q = _np(q)
-        desc = GridDesc(q.size, q.ctypes.data, a, mass, n_mu, measure, stats, precision)
+        desc = GridDesc(q.size, q.ctypes.data, a, mass, n_mu, measure, stats, precision, loss_terms)
         h = ctypes.c_void_p()
         rc = self.lib.kx_build_kernel(self.h, ctypes.byref(desc), ctypes.byref(h))
         if rc:
@@ -431,11 +431,11 @@ class Server:
 
     def __init__(self, ctx: Context, budget_bytes=8 << 30, slots_per_group=16,
                  attempts_per_tick=8, precision=FP32, n_mu=18, measure=MEASURE_ENERGY,
-                 grid_div=0, **params):
+                 grid_div=0, loss_terms=0, **params):
         self.ctx, self.lib = ctx, ctx.lib
         cfg = ServerConfig(int(budget_bytes), int(slots_per_group), int(attempts_per_tick),
                            int(precision), int(n_mu), int(measure), Context.params(**params),
-                           int(grid_div))
+                           int(grid_div), int(loss_terms))
         h = ctypes.c_void_p()
         rc = self.lib.kx_server_start(ctx.h, ctypes.byref(cfg), ctypes.byref(h))
         if rc:
@@ -445,7 +445,7 @@ class Server:
     def submit(self, q, f0, sigma, sources=None, t0=0.0, t_end=1.0, h0=1e-3, mass=1.0, a=1.0):
         """Queue one solve; returns a ticket (int).  Raises KxError (e.g. KX_EADMIT)."""
         q, f0 = _np(q), _np(f0)
-        desc = GridDesc(q.size, q.ctypes.data, a, mass, 0, 0, 0, 0)
+        desc = GridDesc(q.size, q.ctypes.data, a, mass, 0, 0, 0, 0, 0)
         src, ns, keep = Context._sources(sources, 1, q.size)
         t = ctypes.c_uint64()
         rc = self.lib.kx_submit(self.h, ctypes.byref(desc), float(sigma), src, float(t0),

@@ -162,6 +162,11 @@ size_t kx_views_bytes(const kx_kernel *k, int B) {
         s += kx_align(sizeof(float) * Bpad * k->Kpad * 2);   // bt (hi, lo)
         s += kx_align(sizeof(float) * Bpad * k->Kpad);       // fT
         s += kx_align(sizeof(float) * Bpad * (k->Mpad / 128) * (128 / k->n + 2));   // Gp
+        if (k->cheb_K) {
+            s += kx_align(sizeof(float) * Bpad * (size_t)k->KBL * 16 * 2);           // yt
+            s += kx_align(sizeof(float) * Bpad * (size_t)k->lsk * k->MTL * 128);     // Lp
+            s += kx_align(sizeof(int) * B);                                           // cflag
+        }
     }
     return s;
 }
@@ -184,6 +189,10 @@ void kx_carve_views(const kx_kernel *k, int B, void *base, kx_batch_views *v) {
     v->chunks = chunks;
     v->rtask = k->d_rtask;
     v->bt = v->fT = v->Gp = nullptr;
+    v->yt = v->Lp = nullptr;
+    v->cflag = nullptr;
+    v->cheb_K = k->cheb_K;
+    v->KBL = k->KBL;
     v->tq = nullptr;
     v->tlam = nullptr;
     v->eta = k->stats;
@@ -199,6 +208,11 @@ void kx_carve_views(const kx_kernel *k, int B, void *base, kx_batch_views *v) {
         v->bt = (float *)p; p += kx_align(sizeof(float) * Bpad * k->Kpad * 2);
         v->fT = (float *)p; p += kx_align(sizeof(float) * Bpad * k->Kpad);
         v->Gp = (float *)p; p += kx_align(sizeof(float) * Bpad * (k->Mpad / 128) * (128 / k->n + 2));
+        if (k->cheb_K) {
+            v->yt = (float *)p; p += kx_align(sizeof(float) * Bpad * (size_t)k->KBL * 16 * 2);
+            v->Lp = (float *)p; p += kx_align(sizeof(float) * Bpad * (size_t)k->lsk * k->MTL * 128);
+            v->cflag = (int *)p; p += kx_align(sizeof(int) * B);
+        }
     }
 }
 
@@ -246,7 +260,7 @@ static void kx_free_kernel(kx_kernel *k) {
     void *ptrs[] = {k->d_p, k->d_E, k->d_dp, k->d_dE, k->d_h, k->d_pair, k->d_W64,
                     k->d_om64, k->d_jl, k->d_vt, k->d_W32, k->d_pk, k->d_roff, k->d_rtask,
                     k->d_task, k->d_bins, k->d_Atile, k->d_lel, k->d_lseg, k->d_lsw,
-                    k->d_lorder};
+                    k->d_lorder, k->d_Mtile};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     delete k;
@@ -279,6 +293,10 @@ extern "C" int kx_build_kernel(kx_ctx *ctx, const kx_grid_desc *d, kx_kernel **o
     if (d->stats < -1 || d->stats > 1) return kx_set_error(ctx, KX_EINVAL, "stats in {-1, 0, +1}");
     if (d->stats != 0 && d->precision == KX_SPLIT_TF32)
         return kx_set_error(ctx, KX_ENOTSUP, "quantum statistics: FP64 and FP32 paths only");
+    if (d->loss_terms != 0 && d->precision != KX_SPLIT_TF32)
+        return kx_set_error(ctx, KX_ENOTSUP, "the Chebyshev loss GEMM: KX_SPLIT_TF32 path only");
+    if (d->loss_terms != 0 && d->loss_terms != 8 && d->loss_terms != 16 && d->loss_terms != 32)
+        return kx_set_error(ctx, KX_EINVAL, "loss_terms must be 0, 8, 16 or 32");
     if (d->precision != KX_FP64 && d->precision != KX_FP32 && d->precision != KX_SPLIT_TF32)
         return kx_set_error(ctx, KX_ENOTSUP, "precision not available in this library");
     for (int i = 0; i < n; ++i) {
@@ -297,6 +315,7 @@ extern "C" int kx_build_kernel(kx_ctx *ctx, const kx_grid_desc *d, kx_kernel **o
     k->stats = d->stats;
     k->measure = d->measure;
     k->precision = d->precision;
+    k->cheb_K = d->precision == KX_SPLIT_TF32 ? d->loss_terms : 0;
     k->a = d->a;
     k->mass = d->mass;
     k->P = (long long)n * (n + 1) / 2;
@@ -489,7 +508,8 @@ extern "C" int kx_build_kernel(kx_ctx *ctx, const kx_grid_desc *d, kx_kernel **o
     else if (k->precision == KX_FP64)
         k->stream_bytes = (long long)n * k->P * 18 + k->P * 4;
     else
-        k->stream_bytes = (long long)k->Mpad * k->Kpad * 8 + k->nlel * 8 + k->nseg * 8;
+        k->stream_bytes = (long long)k->Mpad * k->Kpad * 8 +
+                          (k->cheb_K ? (long long)k->MTL * k->KBL * 2048 * 8 : k->nlel * 8 + k->nseg * 8);
     if (k->precision != KX_FP64) {
         // the FP32 and batched paths read only their own tables
         cudaFree(k->d_W64); k->d_W64 = nullptr;

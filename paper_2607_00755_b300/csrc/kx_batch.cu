@@ -266,6 +266,196 @@ __global__ void __launch_bounds__(128, S == 2 ? 2 : 1)
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 256;" ::"r"(tmem) : "memory");
 }
 
+// ------------------------------------------------- Chebyshev loss GEMM
+// L'_ib = sum_c Lp[c][i][b],  Lp[c][i][b] = sum_{(j,k) in chunk c} M_k[i][j] Y'_k[j][b]
+// (Y' = Y / f_max): the loss rate of the Chebyshev expansion of f_t as one
+// split-TF32 GEMM, A = M (rows i, 128-row tiles), B = Y' (rows b, 64-row
+// tiles), K = the flattened (j, k) index in 16-wide blocks, cut into lsk
+// chunks of KC blocks (fixed by the kernel, so an instance's sums do not
+// depend on the batch).  A work item is (row tile, instance tile of up to 256,
+// chunk); the CTAs take work items round robin (persistent, one CTA per SM).
+// Warp-specialised: warp 0 (one lane) stages the hi/lo tiles of each k block
+// with bulk copies into an S-stage ring (full/empty mbarriers), warp 1 (one
+// lane) issues the 3 x 2 MMAs of each block (hi*hi + hi*lo + lo*hi, K = 8 per
+// MMA) into one of two tensor-memory accumulators and commits the block to the
+// stage's empty barrier and the item to the accumulator's full barrier; warps
+// 2-5 read the accumulator of the previous item (lane quarter = warp % 4) and
+// store it as FP32 partials while the next item's MMAs run.  Every wait is
+// bounded: on expiry the CTA sets *err, every role stops, copies and MMAs in
+// flight get a bounded wait, and tensor memory is freed.
+#define KX_LG_STAGES 4
+#define KX_LG_SMEM (KX_LG_STAGES * KX_GSTAGE + 256)
+
+// A bounded mbarrier wait that also gives up when another role of the CTA has
+// given up (abort != 0); on its own expiry it raises abort and *err.
+__device__ __forceinline__ bool kx_wait_role(uint32_t bar, uint32_t parity, volatile int *abort, int *err) {
+    const long long t0 = clock64();
+    for (;;) {
+        if (kx_mbar_try_wait(bar, parity)) return true;
+        if (*abort) return false;
+        if (clock64() - t0 > KX_WAIT_CYCLES) {
+            *abort = 1;
+            atomicExch(err, 1);
+            return false;
+        }
+    }
+}
+
+__device__ __forceinline__ void kx_mbar_arrive(uint32_t bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+
+__global__ void __launch_bounds__(192, 1)
+    k_loss_gemm(const float *__restrict__ A, const float *__restrict__ Bt, float *__restrict__ Lp,
+                int KB, int KC, int lsk, int MT, int NT, int Bpad, int n, int ncols, int *err) {
+    constexpr int S = KX_LG_STAGES;
+    extern __shared__ __align__(1024) unsigned char kx_lsm[];
+    uint64_t *bars = reinterpret_cast<uint64_t *>(kx_lsm + S * KX_GSTAGE);   // full[S] empty[S] accf[2] acce[2]
+    uint32_t *tslot = reinterpret_cast<uint32_t *>(bars + 2 * S + 4);
+    volatile int *abort = reinterpret_cast<volatile int *>(tslot + 1);
+    int *issued = reinterpret_cast<int *>(tslot + 2);          // [S] last round issued per stage (+1)
+    int *seen = issued + S;                                     // [S] last round consumed per stage (+1)
+    int *lastc = seen + S;                                      // rounds committed by the MMA thread
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const uint32_t full0 = kx_smem_u32(&bars[0]), empty0 = kx_smem_u32(&bars[S]);
+    const uint32_t accf0 = kx_smem_u32(&bars[2 * S]), acce0 = kx_smem_u32(&bars[2 * S + 2]);
+    if (tid == 0) {
+        for (int q = 0; q < S; ++q) {
+            kx_mbar_init(full0 + 8 * q, 1);
+            kx_mbar_init(empty0 + 8 * q, 1);
+            issued[q] = 0;
+            seen[q] = 0;
+        }
+        for (int q = 0; q < 2; ++q) {
+            kx_mbar_init(accf0 + 8 * q, 1);
+            kx_mbar_init(acce0 + 8 * q, 4);   // one arrival per epilogue warp
+        }
+        *lastc = 0;
+        *abort = 0;
+        kx_fence_mbar_init();
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(kx_smem_u32(tslot)),
+                     "r"(ncols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = *tslot;
+    const int items = MT * NT * lsk;
+    const int half = ncols >> 1;   // columns of one accumulator
+    if (warp == 0) {
+        if (lane == 0) {
+            int it = 0;
+            for (int w = blockIdx.x; w < items && !*abort; w += gridDim.x) {
+                const int c = w % lsk, nt = (w / lsk) % NT, mt = w / (lsk * NT);
+                const int kb0 = c * KC, kb1 = min(KB, kb0 + KC);
+                const int nsub = min(KX_GN, Bpad - nt * KX_GN) >> 6;
+                for (int kb = kb0; kb < kb1; ++kb, ++it) {
+                    const int q = it % S, round = it / S;
+                    if (round > 0 && !kx_wait_role(empty0 + 8 * q, (round - 1) & 1, abort, err)) break;
+                    const uint32_t bar = full0 + 8 * q;
+                    kx_mbar_expect_tx(bar, 2 * KX_ATILE * 4 + 2 * nsub * KX_BTILE * 4);
+                    unsigned char *sa = kx_lsm + (size_t)q * KX_GSTAGE, *sb = sa + 2 * KX_ATILE * 4;
+                    const float *a = A + ((size_t)mt * KB + kb) * 2 * KX_ATILE;
+                    kx_bulk_g2s(kx_smem_u32(sa), a, KX_ATILE * 4, bar);
+                    kx_bulk_g2s(kx_smem_u32(sa + KX_ATILE * 4), a + KX_ATILE, KX_ATILE * 4, bar);
+                    for (int j = 0; j < nsub; ++j) {
+                        const float *src = Bt + ((size_t)(nt * 4 + j) * KB + kb) * 2 * KX_BTILE;
+                        kx_bulk_g2s(kx_smem_u32(sb + j * KX_BTILE * 4), src, KX_BTILE * 4, bar);
+                        kx_bulk_g2s(kx_smem_u32(sb + 4 * KX_BTILE * 4 + j * KX_BTILE * 4), src + KX_BTILE,
+                                    KX_BTILE * 4, bar);
+                    }
+                    issued[q] = round + 1;
+                }
+            }
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {
+            int it = 0, li = 0;
+            for (int w = blockIdx.x; w < items && !*abort; w += gridDim.x, ++li) {
+                const int c = w % lsk, nt = (w / lsk) % NT;
+                const int kb0 = c * KC, kb1 = min(KB, kb0 + KC);
+                const int NTc = min(KX_GN, Bpad - nt * KX_GN);
+                const int buf = li & 1, use = li >> 1;
+                if (use > 0 && !kx_wait_role(acce0 + 8 * buf, (use - 1) & 1, abort, err)) break;
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                const uint32_t d = tmem + (uint32_t)(buf * half);
+                const uint32_t idesc = kx_idesc_tf32(128, NTc);
+                bool ok = true;
+                for (int kb = kb0; kb < kb1; ++kb, ++it) {
+                    const int q = it % S, round = it / S;
+                    if (!kx_wait_role(full0 + 8 * q, round & 1, abort, err)) {
+                        ok = false;
+                        break;
+                    }
+                    seen[q] = round + 1;
+                    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                    const uint32_t aH = kx_smem_u32(kx_lsm + (size_t)q * KX_GSTAGE), aL = aH + KX_ATILE * 4;
+                    const uint32_t bH = aH + 2 * KX_ATILE * 4, bL = bH + 4 * KX_BTILE * 4;
+#pragma unroll
+                    for (int step = 0; step < KX_TILE_K / 8; ++step) {
+                        const uint32_t o = 256u * step;
+                        kx_mma_tf32(d, kx_desc(aH + o, 128, 512), kx_desc(bH + o, 128, 512), idesc,
+                                    (kb > kb0 || step) ? 1u : 0u);
+                        kx_mma_tf32(d, kx_desc(aH + o, 128, 512), kx_desc(bL + o, 128, 512), idesc, 1u);
+                        kx_mma_tf32(d, kx_desc(aL + o, 128, 512), kx_desc(bH + o, 128, 512), idesc, 1u);
+                    }
+                    kx_mma_commit(empty0 + 8 * q);
+                    *lastc = it + 1;
+                }
+                if (!ok) break;
+                kx_mma_commit(accf0 + 8 * buf);
+            }
+        }
+    } else {
+        const int qtr = warp & 3;   // tensor-memory lane quarter this warp may read
+        int li = 0;
+        for (int w = blockIdx.x; w < items; w += gridDim.x, ++li) {
+            const int c = w % lsk, nt = (w / lsk) % NT, mt = w / (lsk * NT);
+            const int NTc = min(KX_GN, Bpad - nt * KX_GN);
+            const int buf = li & 1, use = li >> 1;
+            bool ok = true;
+            if (lane == 0) ok = kx_wait_role(accf0 + 8 * buf, use & 1, abort, err);
+            ok = __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
+            if (!ok) break;
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const int row = mt * 128 + qtr * 32 + lane;
+            float *dst = Lp + ((size_t)c * MT * 128 + row) * Bpad + (size_t)nt * KX_GN;
+            for (int c0 = 0; c0 < NTc; c0 += 16) {
+                float t[16];
+                kx_tmem_ld16(tmem + ((uint32_t)(qtr * 32) << 16) + (uint32_t)(buf * half + c0), t);
+                if (row < n) {
+#pragma unroll
+                    for (int q = 0; q < 16; q += 4)
+                        *reinterpret_cast<float4 *>(dst + c0 + q) = make_float4(t[q], t[q + 1], t[q + 2], t[q + 3]);
+                }
+            }
+            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+            __syncwarp();
+            if (lane == 0) kx_mbar_arrive(acce0 + 8 * buf);
+        }
+    }
+    __syncthreads();
+    if (*abort && tid == 0) {
+        // bounded waits for the copies and MMAs still in flight before the shared
+        // and tensor memory are released
+        for (int q = 0; q < S; ++q)
+            if (issued[q] > seen[q]) kx_mbar_wait(full0 + 8 * q, (issued[q] - 1) & 1, 1ll << 24);
+        if (*lastc > 0) {
+            const int it = *lastc - 1;
+            kx_mbar_wait(empty0 + 8 * (it % S), (it / S) & 1, 1ll << 24);
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    if (warp == 1)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(ncols) : "memory");
+}
+
 // ------------------------------------------------------------- exact loss
 // A row's nonzero elements are sorted by bracket j_L and cut into segments of at
 // most 64 elements with one j_L each, zero-padded to a multiple of 4 (host
@@ -296,7 +486,8 @@ __global__ void __launch_bounds__(WARPS * 32, (WARPS <= 16 && IPL <= 2) ? 2 : 1)
                  const int *__restrict__ lorder, const float2 *__restrict__ td,
                  const float *__restrict__ Gp, const double *__restrict__ fmax,
                  double2 *__restrict__ partial,
-                 const kx_inst_state *__restrict__ st, int stage) {
+                 const kx_inst_state *__restrict__ st, int stage,
+                 const float *__restrict__ Lp, const int *__restrict__ cflag, int lsk, int MTL) {
     // [n][32][IPL] (l2_j, D_j) table; after the loss loop the same space holds
     // the cross-warp reduction [2][WARPS][32 IPL] doubles
     extern __shared__ __align__(16) float2 kx_ltab[];
@@ -313,120 +504,132 @@ __global__ void __launch_bounds__(WARPS * 32, (WARPS <= 16 && IPL <= 2) ? 2 : 1)
     }
     if (!__syncthreads_or(any)) return;
     const int i = lorder[blockIdx.y];
-    // layout: IPL = 1: float2 at [j][lane]; else float4 (two instances) at
-    // [j][IPL / 2][lane], so that each table read is one conflict-free LDS.128
-    for (int j = warp; j < n; j += WARPS) {
-        float2 v[IPL];
+    // Chebyshev loss (Lp non-null): the loss comes from the GEMM partials; the
+    // exact loop runs only for a block holding an instance whose truncation
+    // bound was exceeded (cflag), and only that instance takes its result
+    bool exact = true;
+    if (Lp) {
+        bool fl = false;
 #pragma unroll
-        for (int s = 0; s < IPL; ++s) v[s] = act[s] ? td[(size_t)j * tds + b[s]] : make_float2(-2000.f, 0.f);
-        if constexpr (IPL == 1) {
-            kx_ltab[j * 32 + lane] = v[0];
-        } else {
-#pragma unroll
-            for (int h = 0; h < IPL / 2; ++h)
-                reinterpret_cast<float4 *>(kx_ltab)[(j * (IPL / 2) + h) * 32 + lane] =
-                    make_float4(v[2 * h].x, v[2 * h].y, v[2 * h + 1].x, v[2 * h + 1].y);
-        }
+        for (int s = 0; s < IPL; ++s) fl |= act[s] && cflag[b[s]] != 0;
+        exact = __syncthreads_or(fl) != 0;
     }
-    __syncthreads();
-    // this warp's segments of row i (balanced across the warps by the host)
-    const int gend = lsw[i * WARPS + warp + 1];
-    int g = lsw[i * WARPS + warp];
     float hi[IPL], lo[IPL];
 #pragma unroll
     for (int s = 0; s < IPL; ++s) hi[s] = lo[s] = 0.f;
-    float a[IPL][4];   // FP32 sums of elements 0..3 of each four
+    if (exact) {
+        // layout: IPL = 1: float2 at [j][lane]; else float4 (two instances) at
+        // [j][IPL / 2][lane], so that each table read is one conflict-free LDS.128
+        for (int j = warp; j < n; j += WARPS) {
+            float2 v[IPL];
 #pragma unroll
-    for (int s = 0; s < IPL; ++s) a[s][0] = a[s][1] = a[s][2] = a[s][3] = 0.f;
-    int na = 0;   // elements in the FP32 sums since the last flush
-    // descriptors run two segments ahead of the compute, elements one
-    int2 dsc = make_int2(0, 0), dn = dsc;
-    float2 el0 = make_float2(0.f, 0.f), el1 = el0;
-    if (g < gend) {
-        dsc = __ldg(lseg + g);
-        const int c = dsc.y & 255;
-        if (lane < c) el0 = __ldg(lel + dsc.x + lane);
-        if (lane + 32 < c) el1 = __ldg(lel + dsc.x + 32 + lane);
-    }
-    if (g + 1 < gend) dn = __ldg(lseg + g + 1);
-    for (; g < gend; ++g) {
-        int2 dnn = dn;
-        if (g + 2 < gend) dnn = __ldg(lseg + g + 2);
-        float2 en0 = make_float2(0.f, 0.f), en1 = en0;
-        if (g + 1 < gend) {
-            const int c = dn.y & 255;
-            if (lane < c) en0 = __ldg(lel + dn.x + lane);
-            if (lane + 32 < c) en1 = __ldg(lel + dn.x + 32 + lane);
-        }
-        s_el[warp][lane] = el0;
-        s_el[warp][32 + lane] = el1;
-        __syncwarp();
-        const int j = dsc.y >> 8, c4 = dsc.y & 255;   // count, a multiple of 4
-        float2 t[IPL];
-        if constexpr (IPL == 1) {
-            t[0] = kx_ltab[j * 32 + lane];
-        } else {
+            for (int s = 0; s < IPL; ++s) v[s] = act[s] ? td[(size_t)j * tds + b[s]] : make_float2(-2000.f, 0.f);
+            if constexpr (IPL == 1) {
+                kx_ltab[j * 32 + lane] = v[0];
+            } else {
 #pragma unroll
-            for (int h = 0; h < IPL / 2; ++h) {
-                const float4 q = reinterpret_cast<const float4 *>(kx_ltab)[(j * (IPL / 2) + h) * 32 + lane];
-                t[2 * h] = make_float2(q.x, q.y);
-                t[2 * h + 1] = make_float2(q.z, q.w);
+                for (int h = 0; h < IPL / 2; ++h)
+                    reinterpret_cast<float4 *>(kx_ltab)[(j * (IPL / 2) + h) * 32 + lane] =
+                        make_float4(v[2 * h].x, v[2 * h].y, v[2 * h + 1].x, v[2 * h + 1].y);
             }
         }
-        // a pair of elements per float4, stored (S_0, S_1, omega_0, omega_1); per
-        // pair and instance one packed FMA for the two exponents, two ex2 and two
-        // FMAs for the weights (scalar: the ex2 results need no repacking).  A
-        // running pointer keeps the loop's address arithmetic to one add per four
-        // elements.
-        unsigned long long tD[IPL], tL[IPL];
+        __syncthreads();
+        // this warp's segments of row i (balanced across the warps by the host)
+        const int gend = lsw[i * WARPS + warp + 1];
+        int g = lsw[i * WARPS + warp];
+        float a[IPL][4];   // FP32 sums of elements 0..3 of each four
+#pragma unroll
+        for (int s = 0; s < IPL; ++s) a[s][0] = a[s][1] = a[s][2] = a[s][3] = 0.f;
+        int na = 0;   // elements in the FP32 sums since the last flush
+        // descriptors run two segments ahead of the compute, elements one
+        int2 dsc = make_int2(0, 0), dn = dsc;
+        float2 el0 = make_float2(0.f, 0.f), el1 = el0;
+        if (g < gend) {
+            dsc = __ldg(lseg + g);
+            const int c = dsc.y & 255;
+            if (lane < c) el0 = __ldg(lel + dsc.x + lane);
+            if (lane + 32 < c) el1 = __ldg(lel + dsc.x + 32 + lane);
+        }
+        if (g + 1 < gend) dn = __ldg(lseg + g + 1);
+        for (; g < gend; ++g) {
+            int2 dnn = dn;
+            if (g + 2 < gend) dnn = __ldg(lseg + g + 2);
+            float2 en0 = make_float2(0.f, 0.f), en1 = en0;
+            if (g + 1 < gend) {
+                const int c = dn.y & 255;
+                if (lane < c) en0 = __ldg(lel + dn.x + lane);
+                if (lane + 32 < c) en1 = __ldg(lel + dn.x + 32 + lane);
+            }
+            s_el[warp][lane] = el0;
+            s_el[warp][32 + lane] = el1;
+            __syncwarp();
+            const int j = dsc.y >> 8, c4 = dsc.y & 255;   // count, a multiple of 4
+            float2 t[IPL];
+            if constexpr (IPL == 1) {
+                t[0] = kx_ltab[j * 32 + lane];
+            } else {
+#pragma unroll
+                for (int h = 0; h < IPL / 2; ++h) {
+                    const float4 q = reinterpret_cast<const float4 *>(kx_ltab)[(j * (IPL / 2) + h) * 32 + lane];
+                    t[2 * h] = make_float2(q.x, q.y);
+                    t[2 * h + 1] = make_float2(q.z, q.w);
+                }
+            }
+            // a pair of elements per float4, stored (S_0, S_1, omega_0, omega_1); per
+            // pair and instance one packed FMA for the two exponents, two ex2 and two
+            // FMAs for the weights (scalar: the ex2 results need no repacking).  A
+            // running pointer keeps the loop's address arithmetic to one add per four
+            // elements.
+            unsigned long long tD[IPL], tL[IPL];
+#pragma unroll
+            for (int s = 0; s < IPL; ++s) {
+                tD[s] = kx_pk2(t[s].y, t[s].y);
+                tL[s] = kx_pk2(t[s].x, t[s].x);
+            }
+            const float4 *pe = reinterpret_cast<const float4 *>(s_el[warp]);
+            const float4 *const pend = pe + (c4 >> 1);
+#pragma unroll 4
+            for (; pe < pend; pe += 2) {
+                const float4 x01 = pe[0], x23 = pe[1];
+                const unsigned long long w01 = kx_pk2(x01.z, x01.w), w23 = kx_pk2(x23.z, x23.w);
+#pragma unroll
+                for (int s = 0; s < IPL; ++s) {
+                    const float2 e01 = kx_upk2(kx_fma2(w01, tD[s], tL[s]));
+                    const float2 e23 = kx_upk2(kx_fma2(w23, tD[s], tL[s]));
+                    a[s][0] = fmaf(x01.x, kx_ex2f(e01.x), a[s][0]);
+                    a[s][1] = fmaf(x01.y, kx_ex2f(e01.y), a[s][1]);
+                    a[s][2] = fmaf(x23.x, kx_ex2f(e23.x), a[s][2]);
+                    a[s][3] = fmaf(x23.y, kx_ex2f(e23.y), a[s][3]);
+                }
+            }
+            // the FP32 sums go into the double-float accumulator once they hold at
+            // least 64 elements (short segments share a flush), and at the end
+            na += c4;
+            if (na >= KX_SEG) {
+#pragma unroll
+                for (int s = 0; s < IPL; ++s) {
+                    float sm, er;
+                    kx_two_sum_f(hi[s], (a[s][0] + a[s][1]) + (a[s][2] + a[s][3]), sm, er);
+                    hi[s] = sm;
+                    lo[s] += er;
+                    a[s][0] = a[s][1] = a[s][2] = a[s][3] = 0.f;
+                }
+                na = 0;
+            }
+            __syncwarp();   // the slot is refilled next segment
+            dsc = dn;
+            dn = dnn;
+            el0 = en0;
+            el1 = en1;
+        }
 #pragma unroll
         for (int s = 0; s < IPL; ++s) {
-            tD[s] = kx_pk2(t[s].y, t[s].y);
-            tL[s] = kx_pk2(t[s].x, t[s].x);
+            float sm, er;
+            kx_two_sum_f(hi[s], (a[s][0] + a[s][1]) + (a[s][2] + a[s][3]), sm, er);
+            hi[s] = sm;
+            lo[s] += er;
         }
-        const float4 *pe = reinterpret_cast<const float4 *>(s_el[warp]);
-        const float4 *const pend = pe + (c4 >> 1);
-#pragma unroll 4
-        for (; pe < pend; pe += 2) {
-            const float4 x01 = pe[0], x23 = pe[1];
-            const unsigned long long w01 = kx_pk2(x01.z, x01.w), w23 = kx_pk2(x23.z, x23.w);
-#pragma unroll
-            for (int s = 0; s < IPL; ++s) {
-                const float2 e01 = kx_upk2(kx_fma2(w01, tD[s], tL[s]));
-                const float2 e23 = kx_upk2(kx_fma2(w23, tD[s], tL[s]));
-                a[s][0] = fmaf(x01.x, kx_ex2f(e01.x), a[s][0]);
-                a[s][1] = fmaf(x01.y, kx_ex2f(e01.y), a[s][1]);
-                a[s][2] = fmaf(x23.x, kx_ex2f(e23.x), a[s][2]);
-                a[s][3] = fmaf(x23.y, kx_ex2f(e23.y), a[s][3]);
-            }
-        }
-        // the FP32 sums go into the double-float accumulator once they hold at
-        // least 64 elements (short segments share a flush), and at the end
-        na += c4;
-        if (na >= KX_SEG) {
-#pragma unroll
-            for (int s = 0; s < IPL; ++s) {
-                float sm, er;
-                kx_two_sum_f(hi[s], (a[s][0] + a[s][1]) + (a[s][2] + a[s][3]), sm, er);
-                hi[s] = sm;
-                lo[s] += er;
-                a[s][0] = a[s][1] = a[s][2] = a[s][3] = 0.f;
-            }
-            na = 0;
-        }
-        __syncwarp();   // the slot is refilled next segment
-        dsc = dn;
-        dn = dnn;
-        el0 = en0;
-        el1 = en1;
-    }
-#pragma unroll
-    for (int s = 0; s < IPL; ++s) {
-        float sm, er;
-        kx_two_sum_f(hi[s], (a[s][0] + a[s][1]) + (a[s][2] + a[s][3]), sm, er);
-        hi[s] = sm;
-        lo[s] += er;
-    }
+    }   // exact
     __syncthreads();   // every warp is done with the table
     double *red = reinterpret_cast<double *>(kx_ltab);   // [WARPS][32 IPL]
 #pragma unroll
@@ -437,8 +640,13 @@ __global__ void __launch_bounds__(WARPS * 32, (WARPS <= 16 && IPL <= 2) ? 2 : 1)
         const int bb = blockIdx.x * (32 * IPL) + s * 32 + lane;
         if (bb < B && !(st && (st[bb].done || (stage == 2 && st[bb].skip2)))) {
             double L = 0.0, G = 0.0;
+            if (Lp && cflag[bb] == 0) {
+                // the GEMM's k chunks in order
+                for (int c = 0; c < lsk; ++c) L += (double)Lp[((size_t)c * MTL * 128 + i) * Bpad + bb];
+            } else {
 #pragma unroll
-            for (int w = 0; w < WARPS; ++w) L += red[w * 32 * IPL + s * 32 + lane];
+                for (int w = 0; w < WARPS; ++w) L += red[w * 32 * IPL + s * 32 + lane];
+            }
             // the gain of row i: the GEMM tiles' partials over the rows (i, a)
             const int segmax = 128 / n + 2;
             for (int mt = (i * n) / 128; mt <= (i * n + n - 1) / 128; ++mt)
@@ -469,6 +677,7 @@ static size_t kx_loss_smem(int n, kx_loss_shape sh) {
 
 void kx_batch_prepare() {
     cudaFuncSetAttribute(k_gain_fused<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, KX_GAIN_SMEM(2));
+    cudaFuncSetAttribute(k_loss_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, KX_LG_SMEM);
     cudaFuncSetAttribute(k_batch_loss<2, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)kx_loss_smem(200, {2, 16}));
     cudaFuncSetAttribute(k_batch_loss<2, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -486,19 +695,38 @@ cudaError_t kx_launch_batch_contract(const kx_kernel *k, int B, const kx_batch_v
     k_gain_fused<2><<<g1, 128, KX_GAIN_SMEM(2), s>>>(k->d_Atile, v.bt, v.fT, v.Gp, KB, k->n, v.Bpad, d_err);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
+    const float *Lp = nullptr;
+    if (k->cheb_K) {
+        // the Chebyshev loss GEMM: one CTA per SM over the work items
+        const int MT = k->MTL, NTl = (v.Bpad + KX_GN - 1) / KX_GN;
+        const int items = MT * NTl * k->lsk;
+        int dev = 0, sms = 148;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        const int maxc = std::min(KX_GN, v.Bpad);
+        int ncols = 32;
+        while (ncols < 2 * maxc) ncols <<= 1;
+        k_loss_gemm<<<std::min(items, sms), 192, KX_LG_SMEM, s>>>(k->d_Mtile, v.yt, v.Lp, k->KBL, 8, k->lsk,
+                                                                  MT, NTl, v.Bpad, k->n, ncols, d_err);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        Lp = v.Lp;
+    }
     const kx_loss_shape sh = kx_loss_shape_for(k->n);
     const int per = 32 * sh.ipl;
     dim3 g2((B + per - 1) / per, k->n);
     const size_t smem = kx_loss_smem(k->n, sh);
     if (sh.ipl == 2 && sh.warps == 16)
         k_batch_loss<2, 16><<<g2, 512, smem, s>>>(k->n, B, v.B, v.Bpad, k->d_lel, k->d_lseg, k->d_lsw,
-                                                  k->d_lorder, v.td, v.Gp, v.fmax, v.partial, st, stage);
+                                                  k->d_lorder, v.td, v.Gp, v.fmax, v.partial, st, stage,
+                                                  Lp, v.cflag, k->lsk, k->MTL);
     else if (sh.ipl == 2)
         k_batch_loss<2, 32><<<g2, 1024, smem, s>>>(k->n, B, v.B, v.Bpad, k->d_lel, k->d_lseg, k->d_lsw,
-                                                   k->d_lorder, v.td, v.Gp, v.fmax, v.partial, st, stage);
+                                                   k->d_lorder, v.td, v.Gp, v.fmax, v.partial, st, stage,
+                                                   Lp, v.cflag, k->lsk, k->MTL);
     else
         k_batch_loss<1, 32><<<g2, 1024, smem, s>>>(k->n, B, v.B, v.Bpad, k->d_lel, k->d_lseg, k->d_lsw,
-                                                   k->d_lorder, v.td, v.Gp, v.fmax, v.partial, st, stage);
+                                                   k->d_lorder, v.td, v.Gp, v.fmax, v.partial, st, stage,
+                                                   Lp, v.cflag, k->lsk, k->MTL);
     return cudaGetLastError();
 }
 
@@ -609,6 +837,52 @@ int kx_batch_build_tables(kx_ctx *ctx, kx_kernel *k) {
         rlen[i] = (int)row.size();
     }
     lsw[(size_t)n * WARPS] = (int)lseg.size();
+    // Chebyshev loss (loss_terms = K): M_k[i][j] = sum_{n<=m: j_L = j} S_inm T_k(2 omega - 1)
+    // in FP64 (T_k by the three-term recurrence), as TF32 hi/lo tiles of 128 rows i
+    // x 16 columns of the flattened (j, k) index j K + k
+    std::vector<float> Mt;
+    if (k->cheb_K) {
+        const int K = k->cheb_K;
+        k->MTL = (n + 127) / 128;
+        k->KBL = ((n - 1) * K + 15) / 16;
+        k->lsk = (k->KBL + 7) / 8;   // GEMM work items of about eight k blocks
+        std::vector<double> M((size_t)n * (n - 1) * K, 0.0);
+        for (int i = 0; i < n; ++i) {
+            for (long long e = 0; e < P; ++e) {
+                const size_t x = (size_t)i * P + e;
+                if (W[x] == 0.0) continue;
+                const double t = 2.0 * om[x] - 1.0;
+                double *Mi = &M[((size_t)i * (n - 1) + jl[x]) * K];
+                double T0 = 1.0, T1 = t;
+                Mi[0] += W[x];
+                if (K > 1) Mi[1] += W[x] * t;
+                for (int kk = 2; kk < K; ++kk) {
+                    const double T2 = 2.0 * t * T1 - T0;
+                    Mi[kk] += W[x] * T2;
+                    T0 = T1;
+                    T1 = T2;
+                }
+            }
+        }
+        Mt.assign((size_t)k->MTL * k->KBL * 2 * KX_ATILE, 0.f);
+        for (int i = 0; i < n; ++i)
+            for (int j = 0; j + 1 < n; ++j)
+                for (int kk = 0; kk < K; ++kk) {
+                    const float w = (float)M[((size_t)i * (n - 1) + j) * K + kk];
+                    const float wh = kx_tf32_round(w), wl = w - wh;
+                    const int c = j * K + kk, mt = i / 128, r = i % 128, kb = c / KX_TILE_K;
+                    const size_t t = ((size_t)mt * k->KBL + kb) * 2;
+                    Mt[t * KX_ATILE + kx_tile_offset(r, c % KX_TILE_K)] = wh;
+                    Mt[(t + 1) * KX_ATILE + kx_tile_offset(r, c % KX_TILE_K)] = wl;
+                }
+        if (cudaMalloc(&k->d_Mtile, sizeof(float) * Mt.size()) != cudaSuccess) {
+            cudaGetLastError();
+            return kx_set_error(ctx, KX_ENOMEM, "batched build: allocation failed");
+        }
+        k->bytes += (long long)(sizeof(float) * Mt.size());
+        if (cudaMemcpy(k->d_Mtile, Mt.data(), sizeof(float) * Mt.size(), cudaMemcpyHostToDevice) != cudaSuccess)
+            return kx_set_error(ctx, KX_ECUDA, "batched build: table upload failed");
+    }
     std::vector<int> lorder(n);
     std::iota(lorder.begin(), lorder.end(), 0);
     std::stable_sort(lorder.begin(), lorder.end(), [&](int x, int y) { return rlen[x] > rlen[y]; });

@@ -237,6 +237,85 @@ static cudaError_t kx_launch_ex(void (*kern)(KArgs...), dim3 grid, dim3 block, s
 //             f/f_max instance-minor (fT) and as TF32 hi/lo MMA operand tiles (bt)
 //             for the tensor-core gain; zeros in the k padding up to n rounded to 32.
 // Returns the non-finite flag (block-uniform).
+
+// Chebyshev coefficients of one bracket for the loss GEMM (split path,
+// loss_terms = K).  With D = l2_{j+1} - l2_j (log2 of f / f_max), d = D ln 2,
+// x = |d| / 2 and s = sign(d), the interpolated f_t / f_max of the bracket is
+//   2^{max(l2_j, l2_{j+1})} sum_k eps_k s^k e^{-x} I_k(x) T_k(2 omega - 1)
+// (eps_0 = 1, eps_k = 2): y_k = 2^{l2max} eps_k s^k e^{-x} I_k(x).  The ratios
+// r_k = I_{k+1}(x) / I_k(x) come from the backward recurrence
+// r_{k-1} = x / (2k + x r_k), started at r = 0 well above K (Miller's backward
+// recurrence in ratio form, stable for every x >= 0); v_0 = 1, v_k = v_{k-1}
+// r_{k-1}, and the normalisation sum_k eps_k e^{-x} I_k(x) = 1 (the generating
+// function at t = 1) turns them into e^{-x} I_k(x) = v_k / sum_k eps_k v_k; the
+// tail v_K (1 + r_K + r_K r_{K+1} + ...) gives the truncation bound
+// 2 sum_{k >= K} e^{-x} I_k(x).  Beyond x = 24 the coefficients are dropped and
+// the bound is 2^{l2max}.  Writes the K coefficients (TF32 hi/lo) of instance b,
+// flattened column j K + k, into the operand tiles yt; returns the bound (in
+// units of f_max).
+#define KX_CHEB_EPS 9.313225746e-10f   // 2^-30: larger bounds send the instance to the exact loss
+template <int K>
+__device__ __noinline__ float kx_cheb_tile(float D, float l2m, bool real, float *yt, int KBL, int b, int j) {
+    float y[K];
+    float bound = 0.f;
+#pragma unroll
+    for (int k = 0; k < K; ++k) y[k] = 0.f;
+    if (real) {
+        const float x = fabsf(D) * 0.3465735902799727f;   // |D| ln2 / 2
+        const float scale = exp2f(l2m);
+        if (x > 24.f) {
+            bound = scale;
+        } else {
+            const int k0 = K + 16 + (int)(2.f * x);
+            float rk = 0.f, t = 1.f;
+            for (int k = k0; k > K; --k) {
+                t = fmaf(rk, t, 1.f);
+                rk = x / (2.f * (float)k + x * rk);
+            }
+            const float tK = fmaf(rk, t, 1.f);
+            float r[K];
+#pragma unroll
+            for (int k = K; k >= 1; --k) {
+                rk = x / (2.f * (float)k + x * rk);
+                r[k - 1] = rk;
+            }
+            float vk = 1.f, ssum = 0.f;
+            y[0] = 1.f;
+#pragma unroll
+            for (int k = 1; k < K; ++k) {
+                vk *= r[k - 1];
+                y[k] = vk;
+                ssum += vk;
+            }
+            const float vK = vk * r[K - 1];
+            const float S = fmaf(2.f, fmaf(vK, tK, ssum), 1.f);
+            const float sc = scale / S;
+            const bool neg = D < 0.f;
+#pragma unroll
+            for (int k = 0; k < K; ++k) y[k] *= (k == 0 ? sc : ((neg && (k & 1)) ? -2.f * sc : 2.f * sc));
+            bound = 2.f * vK * tK * sc;
+        }
+    }
+    // operand tiles [b / 64][k block][hi, lo][64 x 16]
+#pragma unroll
+    for (int k4 = 0; k4 < K; k4 += 4) {
+        const int c = j * K + k4, kb = c >> 4;
+        const size_t tb = ((size_t)(b >> 6) * KBL + kb) * 2;
+        const int off = kx_tile_offset(b & 63, c & 15);
+        float h[4], l[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            uint32_t hb;
+            asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(hb) : "f"(y[k4 + q]));
+            h[q] = __uint_as_float(hb);
+            l[q] = y[k4 + q] - h[q];
+        }
+        *reinterpret_cast<float4 *>(yt + tb * (64 * KX_TILE_K) + off) = make_float4(h[0], h[1], h[2], h[3]);
+        *reinterpret_cast<float4 *>(yt + (tb + 1) * (64 * KX_TILE_K) + off) = make_float4(l[0], l[1], l[2], l[3]);
+    }
+    return bound;
+}
+
 // Block sum of K floats (fixed shuffle tree and warp order, deterministic); all
 // threads get the result after one barrier.  fs (K*32 floats) must not be
 // written again by the block without another barrier in between.
@@ -422,6 +501,23 @@ __device__ __forceinline__ int kx_prep_block(int n, int path, double x, double E
         const int off = kx_tile_offset(b & 63, i & 15);
         v.bt[t * (64 * KX_TILE_K) + off] = hi;
         v.bt[(t + 1) * (64 * KX_TILE_K) + off] = fp - hi;
+        if (v.yt) {
+            // Chebyshev loss: the coefficients of bracket (i, i + 1) of this
+            // instance (zeros in the k padding), and whether any bracket's
+            // truncation bound exceeds KX_CHEB_EPS f_max
+            const int nslot = v.KBL * KX_TILE_K / v.cheb_K;
+            float bound = 0.f;
+            if (i < nslot) {
+                const bool real = in && i + 1 < n && fm > 0.0 && !bad;
+                const double D = real ? dl[i + 1] - l2 : 0.0;
+                const float l2m = (float)(D > 0.0 ? l2 + D : l2);
+                if (v.cheb_K == 8) bound = kx_cheb_tile<8>((float)D, l2m, real, v.yt, v.KBL, b, i);
+                else if (v.cheb_K == 16) bound = kx_cheb_tile<16>((float)D, l2m, real, v.yt, v.KBL, b, i);
+                else bound = kx_cheb_tile<32>((float)D, l2m, real, v.yt, v.KBL, b, i);
+            }
+            const int fl = __syncthreads_or(bound > KX_CHEB_EPS);
+            if (i == 0) v.cflag[b] = fl;
+        }
         return bad;
     }
     float2 *tl = v.tl + (long long)b * (n + 4);
@@ -1671,8 +1767,9 @@ __device__ __forceinline__ void kx_stage_body(int b, int n, int chunks, int path
     const double f0 = in ? fb[i] : 0.0;
     const double fpv = (in && stage == 2) ? fp[i] : 0.0;
     const double k1v = (in && stage == 2) ? k1[i] : 0.0;
-    const int flag_in = v.flags[b];
-    const int timed_out = *v.err;   // a contraction's bounded device wait expired
+    // bit 2: a contraction's bounded device wait expired (checked, and the
+    // instance stopped, before flag_in is used as the non-finite flag)
+    const int flag_in = v.flags[b] | (*v.err ? 4 : 0);
     pre.lines = path == KX_FP32 ? v.fit[b] : make_float4(0.f, 0.f, 0.f, 0.f);
     // Every thread takes its copy of the instance state here, before the first
     // block barrier: thread 0 rewrites the state at the end of the stage, and a
@@ -1693,7 +1790,7 @@ __device__ __forceinline__ void kx_stage_body(int b, int n, int chunks, int path
     const double fcur = stage == 1 ? f0 : fpv;
     kx_row_out r = kx_combine_project(n, chunks, path, b, fcur, Ei, hi, v, sv.project, smem);
     if (done0) return;
-    if (timed_out) {   // its partials are incomplete: stop the instance, report it
+    if (flag_in & 4) {   // its partials are incomplete: stop the instance, report it
         __syncthreads();
         if (threadIdx.x == 0) {
             st->status = KX_ETIMEOUT;

@@ -68,6 +68,12 @@ struct kx_kernel {
     int2 *d_lseg;        // segments of <= 64 elements of one j_L: (first element, j_L << 8 | count)
     int *d_lsw;          // [n * warps + 1] first segment of each (row, loss-kernel warp)
     int *d_lorder;       // [n] rows by element count, longest first
+    // Chebyshev loss GEMM (loss_terms > 0): M_k[i][j] as TF32 hi/lo operand tiles
+    int cheb_K;          // terms (0: exact loss only)
+    int KBL;             // 16-wide k blocks of the flattened (j, k) dimension: ceil((n - 1) K / 16)
+    int MTL;             // 128-row tiles of the rows i: ceil(n / 128)
+    int lsk;             // k chunks of the loss GEMM (each CTA work item sums one chunk)
+    float *d_Mtile;      // [MTL][KBL][hi, lo][2048]
     long long nseg;      // segments, all rows
     long long nlel;      // loss elements with the segments' zero padding
     long long nnz;
@@ -160,6 +166,10 @@ struct kx_batch_views {
     float *fT;             // [Kpad][Bpad]: f/f_max, instance-minor
     float *Gp;             // [Mpad/128][128/n + 2][Bpad]: gain partials per (GEMM row tile, grid
                            //   point i in the tile, instance)
+    float *yt;             // Chebyshev loss: [Bpad/64][KBL][hi, lo][1024] coefficient operand tiles
+    float *Lp;             // Chebyshev loss: [lsk][MTL 128][Bpad] FP32 loss partials per k chunk
+    int *cflag;            // Chebyshev loss: [B] 1 = an instance bracket beyond the truncation bound
+    int cheb_K, KBL;       // Chebyshev loss: terms (0: exact loss), k blocks of the coefficient tiles
     int *err;              // tensor-core stage timeout flag (bounded waits)
     int B;                 // instances the views were carved for (td's stride on the split path)
     int Bpad;

@@ -175,6 +175,7 @@ static int kx_make_group(kx_server *srv, const Request &r, Group **out) {
     d.measure = srv->cfg.measure;
     d.stats = 0;
     d.precision = srv->cfg.precision;
+    d.loss_terms = srv->cfg.loss_terms;
     kx_kernel *k = nullptr;
     int rc = kx_build_kernel(srv->wctx, &d, &k);
     if (rc) return rc;
@@ -552,7 +553,9 @@ extern "C" int kx_server_start(kx_ctx *ctx, const kx_server_config *cfg, kx_serv
         cfg->n_mu > KX_MAX_NMU ||
         (cfg->precision != KX_FP32 && cfg->precision != KX_FP64 && cfg->precision != KX_SPLIT_TF32) ||
         !(cfg->par.rtol >= 0) || !(cfg->par.atol >= 0) || cfg->par.max_attempts < 1 ||
-        cfg->grid_div < 0 || cfg->grid_div > 16)
+        cfg->grid_div < 0 || cfg->grid_div > 16 ||
+        (cfg->loss_terms != 0 && (cfg->precision != KX_SPLIT_TF32 ||
+                                  (cfg->loss_terms != 8 && cfg->loss_terms != 16 && cfg->loss_terms != 32))))
         return kx_set_error(ctx, KX_EINVAL, "bad server configuration");
     kx_server *srv = new (std::nothrow) kx_server();
     if (!srv) return KX_ENOMEM;

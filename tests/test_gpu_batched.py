@@ -145,3 +145,129 @@ def test_batched_fixed_step_solve_matches_oracle(env):
         for w in (g["h"], g["h"] * g["E"]):
             assert abs(np.sum(w * f[b]) / np.sum(w * f0[b]) - 1) < 1e-7
     k.release()
+
+
+# ------------------------------------------- loss rate as a Chebyshev GEMM ---
+def oracle_cheb_rows(q, f, sigma, project, K):
+    """Oracle C with the loss rate's f_t in K Chebyshev terms (same truncation
+    as the GPU option), and the exact oracle C beside it."""
+    g = oracle.grid(q)
+    W = oracle.kernel_tensor(q)
+    out, exact = [], []
+    for b in range(f.shape[0]):
+        M2 = oracle.M2_from_sigma(1.0, sigma[b])
+        Cc = oracle.collision_chebyshev(q, W, f[b], K)[0] * M2
+        Ce = oracle.collision_tensor(q, W, f[b]) * M2
+        if project:
+            Cc, _ = oracle.project(g["E"], g["h"], f[b], Cc)
+            Ce, _ = oracle.project(g["E"], g["h"], f[b], Ce)
+        out.append(Cc)
+        exact.append(Ce)
+    return np.array(out), np.array(exact)
+
+
+# sizes cover one and two 128-row tiles of M, every instance tile width (64 ..
+# 256, and 256 + 64), and K = 8 with an odd bracket count (a padded k block)
+@pytest.mark.parametrize("N,B,K", [(20, 1, 16), (48, 70, 8), (65, 3, 8), (64, 130, 32),
+                                   (150, 5, 16), (40, 300, 16), (33, 190, 32)])
+def test_chebyshev_loss_matches_oracle(env, N, B, K):
+    """loss_terms = K: the loss rate as the GEMM M (N x (N-1)K) Y against the
+    oracle's Chebyshev expansion with the same K, and against the exact oracle
+    (the truncation bound of these inputs is far below the tolerance)."""
+    kx, ctx, torch = env
+    rng = np.random.default_rng(500 + N + K)
+    q = ki.log_grid(N, 1e-3, 1e2)
+    f = ki.batch_bimodal(rng, q, B)
+    sig = rng.uniform(0.3, 3.0, size=B)
+    k = ctx.build_kernel(q, precision=kx.SPLIT_TF32, loss_terms=K)
+    fd = torch.as_tensor(f, device="cuda")
+    picks = sorted(set([0, B - 1, B // 2] + list(rng.integers(0, B, 3))))
+    for project in (0, 1):
+        C, d = ctx.collision(k, fd, sig, project=bool(project), diag=True)
+        C = C.cpu().numpy()
+        Cc, Ce = oracle_cheb_rows(q, f[picks], sig[picks], project, K)
+        for r, b in enumerate(picks):
+            scale = np.max(np.abs(Cc[r]))
+            assert np.max(np.abs(C[b] - Cc[r])) / scale <= TOL, (b, project)
+            assert np.max(np.abs(C[b] - Ce[r])) / np.max(np.abs(Ce[r])) <= TOL, (b, project)
+            assert d[b]["status"] == 0
+    k.release()
+
+
+def test_chebyshev_loss_falls_back_to_the_exact_loss(env):
+    """An instance with a bracket beyond the truncation bound (zeros inside the
+    support: the log floor makes |d| ~ 690) takes the exact loss: its C is
+    bit-identical to the exact path's; the other instances of the batch keep
+    the GEMM loss and are bit-identical alone and in the batch."""
+    kx, ctx, torch = env
+    N = 40
+    q = ki.log_grid(N, 1e-3, 10.0)
+    f = ki.batch_bimodal(np.random.default_rng(61), q, 5)
+    f[2, 10:14] = 0.0
+    sig = np.linspace(0.5, 2.0, 5)
+    kc = ctx.build_kernel(q, precision=kx.SPLIT_TF32, loss_terms=16)
+    ke = ctx.build_kernel(q, precision=kx.SPLIT_TF32)
+    fd = torch.as_tensor(f, device="cuda")
+    Cc, _ = ctx.collision(kc, fd, sig)
+    Ce, _ = ctx.collision(ke, fd, sig)
+    Cc, Ce = Cc.cpu().numpy(), Ce.cpu().numpy()
+    np.testing.assert_array_equal(Cc[2], Ce[2])
+    assert not np.array_equal(Cc[0], Ce[0])   # the others did take the GEMM loss
+    for b in (0, 2, 4):
+        Ca, _ = ctx.collision(kc, torch.as_tensor(f[b:b + 1], device="cuda"), sig[b:b + 1])
+        np.testing.assert_array_equal(Ca.cpu().numpy()[0], Cc[b])
+    Co = oracle_rows(q, f[2:3], sig[2:3], 1)
+    assert np.max(np.abs(Cc[2] - Co[0])) / np.max(np.abs(Co[0])) <= TOL
+    kc.release()
+    ke.release()
+
+
+def test_chebyshev_loss_full_size_configuration_sampled(env):
+    """The batched configuration at full size (B = 512 on one N = 192 kernel)
+    with loss_terms = 16: sampled instances against the oracle."""
+    kx, ctx, torch = env
+    c = ki.config3()
+    q, f, sig = c["q"], c["f"], c["sigma"]
+    picks = (0, 1, 255, 256, 511)
+    k = ctx.build_kernel(q, precision=kx.SPLIT_TF32, loss_terms=16)
+    C, d = ctx.collision(k, torch.as_tensor(f, device="cuda"), sig, project=True, diag=True)
+    C = C.cpu().numpy()
+    Co = oracle_rows(q, f[list(picks)], np.asarray(sig)[list(picks)], True)
+    for r, b in enumerate(picks):
+        assert np.max(np.abs(C[b] - Co[r])) / np.max(np.abs(Co[r])) <= TOL, b
+        assert d[b]["status"] == 0
+    k.release()
+
+
+def test_chebyshev_loss_fixed_step_solve(env):
+    """Fixed-step integration with the Chebyshev loss (K = 16) against the
+    oracle's solve: element-wise at the mixed bound, moments to 1e-7."""
+    kx, ctx, torch = env
+    c = ki.config1()
+    q = c["q"]
+    g = oracle.grid(q)
+    W = oracle.kernel_tensor(q)
+    f0 = ki.batch_bimodal(np.random.default_rng(34), q, 3)
+    sig = np.array([0.7, 1.0, 1.3]) * c["sigma"]
+    t_end = c["n_steps"] * c["h"]
+    k = ctx.build_kernel(q, precision=kx.SPLIT_TF32, loss_terms=16)
+    fd = torch.as_tensor(f0, device="cuda")
+    res = ctx.solve(k, fd, sig, t_end=t_end, h0=c["h"], fixed_step=1)
+    f = fd.cpu().numpy()
+    for b in range(3):
+        fo, ro = oracle.solve(q, W, f0[b], oracle.M2_from_sigma(1.0, sig[b]), t_end=t_end,
+                              h0=c["h"], fixed_step=1)
+        assert res[b]["status"] == 0 and res[b]["steps"] == c["n_steps"]
+        assert np.max(np.abs(f[b] - fo)) / np.max(np.abs(fo)) <= TOL, b
+        for w in (g["h"], g["h"] * g["E"]):
+            assert abs(np.sum(w * f[b]) / np.sum(w * f0[b]) - 1) < 1e-7
+    k.release()
+
+
+def test_chebyshev_option_is_validated(env):
+    kx, ctx, torch = env
+    q = ki.log_grid(16, 1e-3, 10.0)
+    for prec, K, code in ((kx.FP32, 16, kx.ENOTSUP), (kx.FP64, 8, kx.ENOTSUP), (kx.SPLIT_TF32, 12, kx.EINVAL)):
+        with pytest.raises(kx.KxError) as ei:
+            ctx.build_kernel(q, precision=prec, loss_terms=K)
+        assert ei.value.code == code
