@@ -158,14 +158,13 @@ size_t kx_views_bytes(const kx_kernel *k, int B) {
         s += kx_align(sizeof(float) * B * n);        // tlam
     }
     if (k->precision == KX_SPLIT_TF32) {
-        const size_t Bpad = ((B + 63) / 64) * 64;
-        s += kx_align(sizeof(float) * Bpad * k->Kpad * 2);   // bt (hi, lo)
-        s += kx_align(sizeof(float) * Bpad * k->Kpad);       // fT
-        s += kx_align(sizeof(float) * Bpad * (k->Mpad / 128) * (128 / k->n + 2));   // Gp
+        const size_t Bpad = ((B + 127) / 128) * 128;
+        s += kx_align(sizeof(float) * Bpad * n);                             // fT
+        s += kx_align(sizeof(float) * Bpad * (size_t)k->gsk * k->nis);       // Gs
         if (k->cheb_K) {
-            s += kx_align(sizeof(float) * Bpad * (size_t)k->KBL * 16 * 2);           // yt
-            s += kx_align(sizeof(float) * Bpad * (size_t)k->lsk * k->MTL * 128);     // Lp
-            s += kx_align(sizeof(int) * B);                                           // cflag
+            s += kx_align(sizeof(float) * Bpad * (size_t)k->KBL * 16 * 2);   // yt
+            s += kx_align(sizeof(float) * Bpad * (size_t)k->lsk * k->nis);   // Lp
+            s += kx_align(sizeof(int) * B);                                   // cflag
         }
     }
     return s;
@@ -188,11 +187,14 @@ void kx_carve_views(const kx_kernel *k, int B, void *base, kx_batch_views *v) {
     v->err = (int *)p; p += kx_align(sizeof(int));
     v->chunks = chunks;
     v->rtask = k->d_rtask;
-    v->bt = v->fT = v->Gp = nullptr;
+    v->fT = v->Gs = nullptr;
     v->yt = v->Lp = nullptr;
     v->cflag = nullptr;
     v->cheb_K = k->cheb_K;
     v->KBL = k->KBL;
+    v->gsk = k->gsk;
+    v->lsk = k->lsk;
+    v->nis = k->nis;
     v->tq = nullptr;
     v->tlam = nullptr;
     v->eta = k->stats;
@@ -202,15 +204,14 @@ void kx_carve_views(const kx_kernel *k, int B, void *base, kx_batch_views *v) {
         v->tlam = (float *)p; p += kx_align(sizeof(float) * B * n);
     }
     v->B = B;
-    v->Bpad = ((B + 63) / 64) * 64;
+    v->Bpad = ((B + 127) / 128) * 128;
     if (k->precision == KX_SPLIT_TF32) {
         const size_t Bpad = v->Bpad;
-        v->bt = (float *)p; p += kx_align(sizeof(float) * Bpad * k->Kpad * 2);
-        v->fT = (float *)p; p += kx_align(sizeof(float) * Bpad * k->Kpad);
-        v->Gp = (float *)p; p += kx_align(sizeof(float) * Bpad * (k->Mpad / 128) * (128 / k->n + 2));
+        v->fT = (float *)p; p += kx_align(sizeof(float) * Bpad * n);
+        v->Gs = (float *)p; p += kx_align(sizeof(float) * Bpad * (size_t)k->gsk * k->nis);
         if (k->cheb_K) {
             v->yt = (float *)p; p += kx_align(sizeof(float) * Bpad * (size_t)k->KBL * 16 * 2);
-            v->Lp = (float *)p; p += kx_align(sizeof(float) * Bpad * (size_t)k->lsk * k->MTL * 128);
+            v->Lp = (float *)p; p += kx_align(sizeof(float) * Bpad * (size_t)k->lsk * k->nis);
             v->cflag = (int *)p; p += kx_align(sizeof(int) * B);
         }
     }
@@ -259,7 +260,7 @@ static void kx_free_kernel(kx_kernel *k) {
     cudaSetDevice(k->device);
     void *ptrs[] = {k->d_p, k->d_E, k->d_dp, k->d_dE, k->d_h, k->d_pair, k->d_W64,
                     k->d_om64, k->d_jl, k->d_vt, k->d_W32, k->d_pk, k->d_roff, k->d_rtask,
-                    k->d_task, k->d_bins, k->d_Atile, k->d_lel, k->d_lseg, k->d_lsw,
+                    k->d_task, k->d_bins, k->d_Sg, k->d_lel, k->d_lseg, k->d_lsw,
                     k->d_lorder, k->d_Mtile};
     for (void *p : ptrs)
         if (p) cudaFree(p);
@@ -508,8 +509,9 @@ extern "C" int kx_build_kernel(kx_ctx *ctx, const kx_grid_desc *d, kx_kernel **o
     else if (k->precision == KX_FP64)
         k->stream_bytes = (long long)n * k->P * 18 + k->P * 4;
     else
-        k->stream_bytes = (long long)k->Mpad * k->Kpad * 8 +
-                          (k->cheb_K ? (long long)k->MTL * k->KBL * 2048 * 8 : k->nlel * 8 + k->nseg * 8);
+        k->stream_bytes = (long long)((k->nis + 255) / 256) * std::min(4, k->nsubI) * 1024 * 8 *
+                              (k->KBG + (k->cheb_K ? k->KBL : 0)) +
+                          (k->cheb_K ? 0 : k->nlel * 8 + k->nseg * 8);
     if (k->precision != KX_FP64) {
         // the FP32 and batched paths read only their own tables
         cudaFree(k->d_W64); k->d_W64 = nullptr;

@@ -88,203 +88,39 @@ __device__ __forceinline__ unsigned long long kx_fma2(unsigned long long a, unsi
     asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
     return d;
 }
-// --------------------------------------------------------- gain GEMM (fused)
-// One CTA (4 warps) per (128-row M tile of W_full, N tile of up to 256
-// instances), two CTAs per SM.  Thread 0 stages the hi/lo operand tiles of each
-// 16-wide k block with bulk copies into a two-stage ring (mbarrier transaction
-// counts: the A tile and up to four 64-instance B tiles, which form one 256-row
-// K-major operand), issues the 3 x 2 MMAs of the block (M = 128, N = NTc,
-// K = 8 each) and commits them to the stage's completion barrier.  The accumulator
-// (128 lanes x NTc FP32 columns of tensor memory) holds T = W_full F for the
-// tile's rows (i, a); the epilogue forms the gain directly: each thread
-// multiplies its row's T by f'_a (instance-minor f/f_max) into a shared-memory
-// product matrix (128 instance columns at a time), and each column is summed
-// over the rows of every grid point i the tile touches, giving one FP32 partial
-// per (tile, i, instance):
-//   Gp[(mt * segmax + i - i_first(mt)) * Bpad + b] = sum_{a in tile} f'_ab T_(i a) b,
-// i_first(mt) = floor(128 mt / n).  T itself never reaches global memory.
-#define KX_GN 256
+// ------------------------------------------------ split-TF32 GEMMs (tcgen05)
+// Both contractions of the batched path are GEMMs with the instances as the M
+// dimension (128-row tiles) and the grid points i as the N dimension (tiles of
+// up to 256), FP32 partials per k chunk:
+//   gain (GEN): out[c][b][i] = sum_{p in chunk c} (f'_n f'_m)_{b p} S_{i p},
+//               p = (n <= m) pairs, S the n <-> m symmetrised kernel (2 U B
+//               useful MACs, eq. discrete_collision_operator's gain);
+//   loss:       out[c][b][i] = sum_{(j,k) in chunk c} Y'_{b (j k)} M_{i (j k)}
+//               (the Chebyshev expansion of f_t, eq. app_log_interp).
+// f' = f / f_max.  The B operand (S or M: rows i, K-major) is a kernel table
+// in 64-row TF32 hi/lo tiles, staged by bulk copies; the A operand is the
+// per-call coefficient tiles (loss, bulk copies) or is generated in shared
+// memory by four producer warps from f' and the pair table (gain: f'_n f'_m in
+// FP32, split into TF32 hi + lo).  Products hi*hi + hi*lo + lo*hi (K = 8 per
+// MMA) accumulate in FP32 in tensor memory.  The k chunks are fixed by the
+// kernel (not by the batch), so an instance's sums do not depend on the batch.
+// A work item is (instance tile, i tile, chunk); the CTAs take them round
+// robin (persistent, one CTA per SM).  Roles: warp 13 (one lane) issues the
+// bulk copies of each stage of an S-stage ring, warps 0-7 generate the gain's
+// A operand into the same stage (two warps per 32 instance rows, eight pairs
+// each; full barrier: the copy bytes plus one arrival per generating warp;
+// empty barrier: the MMAs' commit), warp 8 lane 0 issues the MMAs into one of
+// two accumulators, warps 9-12 read the previous item's accumulator
+// (tensor-memory lane quarter = warp % 4) and store its partials while the
+// next item's MMAs run.  Operand tiles of one (i tile, k block) are
+// contiguous per hi/lo part, so a stage takes two (gain) or four (loss) copies.  Every wait is bounded: on
+// expiry the CTA sets *err and every role stops; copies and MMAs in flight get
+// a bounded wait before shared and tensor memory are released.
+#define KX_GN 256                                             // i columns per tile
 #define KX_GSTAGE (2 * KX_ATILE * 4 + 2 * 4 * KX_BTILE * 4)   // A hi/lo 16 KB + B hi/lo 32 KB
-#define KX_GAIN_SMEM(S) ((S) * KX_GSTAGE + 128)
-#define KX_GP_LD 129                                          // product matrix: [128 cols][128 rows + 1]
-static_assert(128 * KX_GP_LD * 4 <= 2 * KX_GSTAGE, "product matrix must fit in the stage buffers");
-
-__host__ __device__ __forceinline__ int kx_gain_segmax(int n) { return 128 / n + 2; }
-
-// S: stages of the copy ring.  Two stages and two CTAs per SM (one CTA's
-// epilogue and copy waits overlap the other's MMAs) measured faster than four
-// stages and one CTA per SM (0.273 vs 0.300 ms for the N = 192, B = 512
-// contraction).
-template <int S>
-__global__ void __launch_bounds__(128, S == 2 ? 2 : 1)
-    k_gain_fused(const float *__restrict__ A, const float *__restrict__ Bt,
-                 const float *__restrict__ fT, float *__restrict__ Gp, int KB, int n, int Bpad,
-                 int *err) {
-    extern __shared__ __align__(1024) unsigned char kx_gsm[];
-    uint64_t *bars = reinterpret_cast<uint64_t *>(kx_gsm + S * KX_GSTAGE);   // full[S], done[S]
-    uint32_t *slot = reinterpret_cast<uint32_t *>(kx_gsm + S * KX_GSTAGE + 16 * S);
-    int *okf = reinterpret_cast<int *>(kx_gsm + S * KX_GSTAGE + 16 * S + 8);
-    const int nt = blockIdx.x, mt = blockIdx.y;
-    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int NTc = min(KX_GN, Bpad - nt * KX_GN);   // 64, 128, 192 or 256
-    const int nsub = NTc >> 6;
-    const float *Ab = A + (size_t)mt * KB * 2 * KX_ATILE;
-    const uint32_t full0 = kx_smem_u32(&bars[0]), done0 = kx_smem_u32(&bars[S]);
-    if (tid == 0) {
-        for (int k = 0; k < 2 * S; ++k) kx_mbar_init(kx_smem_u32(&bars[k]), 1);
-        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-        *okf = 1;
-    }
-    if (warp == 0) {
-        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 256;" ::"r"(
-                         kx_smem_u32(slot))
-                     : "memory");
-        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
-    }
-    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-    __syncthreads();
-    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    const uint32_t tmem = *slot;
-    if (tid == 0) {
-        const uint32_t idesc = kx_idesc_tf32(128, NTc);
-        int ok = 1;
-        int issued = 0;   // k blocks whose copies were issued
-        auto stage_a = [&](int s) { return kx_gsm + (size_t)s * KX_GSTAGE; };
-        auto stage_b = [&](int s) { return kx_gsm + (size_t)s * KX_GSTAGE + 2 * KX_ATILE * 4; };
-        auto load = [&](int kb, int s) {
-            const uint32_t bar = full0 + 8 * s;
-            kx_mbar_expect_tx(bar, 2 * KX_ATILE * 4 + 2 * nsub * KX_BTILE * 4);
-            unsigned char *a = stage_a(s), *bsm = stage_b(s);
-            kx_bulk_g2s(kx_smem_u32(a), Ab + (size_t)(2 * kb) * KX_ATILE, KX_ATILE * 4, bar);
-            kx_bulk_g2s(kx_smem_u32(a + KX_ATILE * 4), Ab + (size_t)(2 * kb + 1) * KX_ATILE, KX_ATILE * 4, bar);
-            for (int j = 0; j < nsub; ++j) {
-                const float *src = Bt + ((size_t)(nt * 4 + j) * KB + kb) * 2 * KX_BTILE;
-                kx_bulk_g2s(kx_smem_u32(bsm + j * KX_BTILE * 4), src, KX_BTILE * 4, bar);
-                kx_bulk_g2s(kx_smem_u32(bsm + 4 * KX_BTILE * 4 + j * KX_BTILE * 4), src + KX_BTILE,
-                            KX_BTILE * 4, bar);
-            }
-            issued = kb + 1;
-        };
-        // blocks 0 .. S - 2 in flight before the first MMA; iteration kb refills
-        // the stage of block kb - 1 with block kb + S - 1
-        for (int kb = 0; kb < S - 1 && kb < KB; ++kb) load(kb, kb);
-        int committed = 0;  // k blocks whose MMAs were committed
-        for (int kb = 0; kb < KB; ++kb) {
-            const int s = kb % S;
-            if (kb + S - 1 < KB) {
-                const int sr = (kb + S - 1) % S;
-                // the stage about to be refilled was read by the MMAs of block kb - 1
-                if (kb >= 1 && !kx_mbar_wait(done0 + 8 * sr, ((kb - 1) / S) & 1)) {
-                    ok = 0;
-                    break;
-                }
-                load(kb + S - 1, sr);
-            }
-            if (!kx_mbar_wait(full0 + 8 * s, (kb / S) & 1)) {
-                ok = 0;
-                break;
-            }
-            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            const uint32_t aH = kx_smem_u32(stage_a(s)), aL = aH + KX_ATILE * 4;
-            const uint32_t bH = kx_smem_u32(stage_b(s)), bL = bH + 4 * KX_BTILE * 4;
-#pragma unroll
-            for (int step = 0; step < KX_TILE_K / 8; ++step) {
-                const uint32_t o = 256u * step;   // 8 TF32 = two 16-byte core-matrix columns
-                kx_mma_tf32(tmem, kx_desc(aH + o, 128, 512), kx_desc(bH + o, 128, 512), idesc,
-                            (kb | step) ? 1u : 0u);
-                kx_mma_tf32(tmem, kx_desc(aH + o, 128, 512), kx_desc(bL + o, 128, 512), idesc, 1u);
-                kx_mma_tf32(tmem, kx_desc(aL + o, 128, 512), kx_desc(bH + o, 128, 512), idesc, 1u);
-            }
-            kx_mma_commit(done0 + 8 * s);
-            committed = kb + 1;
-        }
-        if (ok && !kx_mbar_wait(done0 + 8 * ((KB - 1) % S), ((KB - 1) / S) & 1)) ok = 0;
-        if (!ok) {
-            // give outstanding copies and MMAs a bounded chance to land before the
-            // shared memory and tensor memory are released
-            for (int kb = committed; kb < issued; ++kb) kx_mbar_wait(full0 + 8 * (kb % S), (kb / S) & 1);
-            if (committed > 0)
-                kx_mbar_wait(done0 + 8 * ((committed - 1) % S), ((committed - 1) / S) & 1);
-            *okf = 0;
-            atomicExch(err, 1);
-        }
-    }
-    __syncthreads();
-    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    const bool ok = *okf != 0;
-    const int nrows = n * n;
-    const int rl = warp * 32 + lane, r = mt * 128 + rl;
-    const bool rin = r < nrows;
-    const float *frow = fT + (size_t)(rin ? r % n : 0) * Bpad + (size_t)nt * KX_GN;
-    float *sP = reinterpret_cast<float *>(kx_gsm);   // free: every copy landed, every MMA completed
-    const int segmax = kx_gain_segmax(n), i_first = (mt * 128) / n;
-    for (int h0 = 0; h0 < NTc; h0 += 128) {
-        const int hw = min(128, NTc - h0);
-        if (ok) {
-            // products f'_ab T_(i a) b of columns h0 .. h0 + hw - 1 into sP[col][row]
-            for (int c = 0; c < hw; c += 16) {
-                float t[16];
-                kx_tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(h0 + c), t);
-#pragma unroll
-                for (int q = 0; q < 16; q += 4) {
-                    const float4 f4 = rin ? __ldg(reinterpret_cast<const float4 *>(frow + h0 + c + q))
-                                          : make_float4(0.f, 0.f, 0.f, 0.f);
-                    sP[(c + q) * KX_GP_LD + rl] = t[q] * f4.x;
-                    sP[(c + q + 1) * KX_GP_LD + rl] = t[q + 1] * f4.y;
-                    sP[(c + q + 2) * KX_GP_LD + rl] = t[q + 2] * f4.z;
-                    sP[(c + q + 3) * KX_GP_LD + rl] = t[q + 3] * f4.w;
-                }
-            }
-        }
-        __syncthreads();
-        // column sums over the rows of each grid point i in the tile (four
-        // interleaved FP32 partial sums, combined pairwise)
-        if (ok && tid < hw) {
-            const float *pc = sP + tid * KX_GP_LD;
-            for (int sg = 0; sg < segmax; ++sg) {
-                const int i = i_first + sg;
-                if (i >= n) break;
-                const int r0 = max(mt * 128, i * n) - mt * 128, r1 = min(mt * 128 + 128, (i + 1) * n) - mt * 128;
-                if (r0 >= r1) break;
-                float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
-                int rr = r0;
-                for (; rr + 4 <= r1; rr += 4) {
-                    a0 += pc[rr];
-                    a1 += pc[rr + 1];
-                    a2 += pc[rr + 2];
-                    a3 += pc[rr + 3];
-                }
-                for (; rr < r1; ++rr) a0 += pc[rr];
-                Gp[(size_t)(mt * segmax + sg) * Bpad + (size_t)nt * KX_GN + h0 + tid] = (a0 + a1) + (a2 + a3);
-            }
-        }
-        __syncthreads();   // sP is refilled by the next half
-    }
-    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-    __syncthreads();
-    if (warp == 0)
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 256;" ::"r"(tmem) : "memory");
-}
-
-// ------------------------------------------------- Chebyshev loss GEMM
-// L'_ib = sum_c Lp[c][i][b],  Lp[c][i][b] = sum_{(j,k) in chunk c} M_k[i][j] Y'_k[j][b]
-// (Y' = Y / f_max): the loss rate of the Chebyshev expansion of f_t as one
-// split-TF32 GEMM, A = M (rows i, 128-row tiles), B = Y' (rows b, 64-row
-// tiles), K = the flattened (j, k) index in 16-wide blocks, cut into lsk
-// chunks of KC blocks (fixed by the kernel, so an instance's sums do not
-// depend on the batch).  A work item is (row tile, instance tile of up to 256,
-// chunk); the CTAs take work items round robin (persistent, one CTA per SM).
-// Warp-specialised: warp 0 (one lane) stages the hi/lo tiles of each k block
-// with bulk copies into an S-stage ring (full/empty mbarriers), warp 1 (one
-// lane) issues the 3 x 2 MMAs of each block (hi*hi + hi*lo + lo*hi, K = 8 per
-// MMA) into one of two tensor-memory accumulators and commits the block to the
-// stage's empty barrier and the item to the accumulator's full barrier; warps
-// 2-5 read the accumulator of the previous item (lane quarter = warp % 4) and
-// store it as FP32 partials while the next item's MMAs run.  Every wait is
-// bounded: on expiry the CTA sets *err, every role stops, copies and MMAs in
-// flight get a bounded wait, and tensor memory is freed.
-#define KX_LG_STAGES 4
-#define KX_LG_SMEM (KX_LG_STAGES * KX_GSTAGE + 256)
+#define KX_SG_THREADS 448   // warps 0-7 generate A (gain), 8 MMA, 9-12 epilogue, 13 bulk copies
+#define KX_GAIN_KC 32   // k blocks per chunk of the gain GEMM (a work item)
+#define KX_LOSS_KC 8    // k blocks per chunk of the loss GEMM
 
 // A bounded mbarrier wait that also gives up when another role of the CTA has
 // given up (abort != 0); on its own expiry it raises abort and *err.
@@ -305,23 +141,65 @@ __device__ __forceinline__ void kx_mbar_arrive(uint32_t bar) {
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
 }
 
-__global__ void __launch_bounds__(192, 1)
-    k_loss_gemm(const float *__restrict__ A, const float *__restrict__ Bt, float *__restrict__ Lp,
-                int KB, int KC, int lsk, int MT, int NT, int Bpad, int n, int ncols, int *err) {
-    constexpr int S = KX_LG_STAGES;
-    extern __shared__ __align__(1024) unsigned char kx_lsm[];
-    uint64_t *bars = reinterpret_cast<uint64_t *>(kx_lsm + S * KX_GSTAGE);   // full[S] empty[S] accf[2] acce[2]
-    uint32_t *tslot = reinterpret_cast<uint32_t *>(bars + 2 * S + 4);
+// Shared-memory plan of a split GEMM: S stages of A (hi, lo: 2 x 8 KB) and B
+// (hi, lo: 2 x nsb x 4 KB, nsb = 64-row i tiles of the widest i tile); for the
+// gain with n <= 256 also the f' block of the item's 128 instances (fs[n][128],
+// one bulk copy) that the generating warps read instead of global memory.
+struct kx_sg_plan {
+    int S, nsb, stage, fs, smem;
+};
+__host__ __device__ inline kx_sg_plan kx_sg_plan_for(bool gen, int n, int nsubI) {
+    kx_sg_plan pl;
+    pl.nsb = nsubI < 4 ? nsubI : 4;
+    pl.stage = 2 * KX_ATILE * 4 + 2 * pl.nsb * KX_BTILE * 4;
+    pl.fs = (gen && n <= 256) ? 128 * n * 4 : 0;
+    const int budget = 227 * 1024 - 256;
+    pl.S = (budget - pl.fs) / pl.stage;
+    if (pl.S > 4) pl.S = 4;
+    pl.smem = pl.S * pl.stage + pl.fs + 256;
+    return pl;
+}
+
+// GEN: the gain (A generated from f' and the packed pairs n <= m); else the
+// loss (A = the coefficient tiles At [Bpad/128][KB][hi, lo][2048]).  Bt:
+// [NTi][KB][hi, lo][nsb x 1024] (nsb = min(4, nsubI) 64-row tiles of i per i
+// tile, zero padded).  out: [chunks][Bpad][nis].  fT: [Bpad/128][n][128] (GEN).
+// Packed pair p = base(n) + m - n, base(n) = n (2N - n + 1) / 2.
+__device__ __forceinline__ long long kx_pair_base(int n, int N) { return (long long)n * (2 * N - n + 1) / 2; }
+__device__ __forceinline__ void kx_pair_decode(long long p, int N, int &n, int &m) {
+    const float b = 2.f * N + 1.f;
+    int x = (int)floorf(0.5f * (b - sqrtf(fmaxf(b * b - 8.f * (float)p, 0.f))));
+    x = max(0, min(x, N - 1));
+    if (x + 1 < N && kx_pair_base(x + 1, N) <= p) ++x;   // FP32 rounding: at most one step either way
+    if (kx_pair_base(x, N) > p) --x;
+    n = x;
+    m = x + (int)(p - kx_pair_base(x, N));
+}
+template <bool GEN>
+__global__ void __launch_bounds__(KX_SG_THREADS, 1)
+    k_split_gemm(const float *__restrict__ At, const float *__restrict__ Bt, float *__restrict__ out,
+                 const float *__restrict__ fT, long long P, int n,
+                 int KB, int KC, int chunks, int MTb, int NTi, int nsubI, int Bpad, int nis, int ncols,
+                 int *err) {
+    extern __shared__ __align__(1024) unsigned char kx_gsm[];
+    const kx_sg_plan pl = kx_sg_plan_for(GEN, n, nsubI);
+    const int S = pl.S;
+    float *fs = reinterpret_cast<float *>(kx_gsm + S * pl.stage);   // f' block (GEN, n <= 256)
+    uint64_t *bars = reinterpret_cast<uint64_t *>(kx_gsm + S * pl.stage + pl.fs);
+    // bars: full[4] empty[4] accf[2] acce[2] fbar fsfree
+    uint32_t *tslot = reinterpret_cast<uint32_t *>(bars + 14);
     volatile int *abort = reinterpret_cast<volatile int *>(tslot + 1);
-    int *issued = reinterpret_cast<int *>(tslot + 2);          // [S] last round issued per stage (+1)
-    int *seen = issued + S;                                     // [S] last round consumed per stage (+1)
-    int *lastc = seen + S;                                      // rounds committed by the MMA thread
+    int *issued = reinterpret_cast<int *>(tslot + 2);   // [4] rounds issued per stage
+    int *seen = issued + 4;                             // [4] rounds consumed per stage
+    int *lastc = seen + 4;                              // k blocks committed by the MMA thread
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const uint32_t full0 = kx_smem_u32(&bars[0]), empty0 = kx_smem_u32(&bars[S]);
-    const uint32_t accf0 = kx_smem_u32(&bars[2 * S]), acce0 = kx_smem_u32(&bars[2 * S + 2]);
+    const uint32_t full0 = kx_smem_u32(&bars[0]), empty0 = kx_smem_u32(&bars[4]);
+    const uint32_t accf0 = kx_smem_u32(&bars[8]), acce0 = kx_smem_u32(&bars[10]);
+    const uint32_t fbar = kx_smem_u32(&bars[12]), fsfree = kx_smem_u32(&bars[13]);
+    const bool fsm = GEN && pl.fs > 0;
     if (tid == 0) {
         for (int q = 0; q < S; ++q) {
-            kx_mbar_init(full0 + 8 * q, 1);
+            kx_mbar_init(full0 + 8 * q, GEN ? 9 : 1);   // GEN: the copy arrival + eight generating warps
             kx_mbar_init(empty0 + 8 * q, 1);
             issued[q] = 0;
             seen[q] = 0;
@@ -330,11 +208,13 @@ __global__ void __launch_bounds__(192, 1)
             kx_mbar_init(accf0 + 8 * q, 1);
             kx_mbar_init(acce0 + 8 * q, 4);   // one arrival per epilogue warp
         }
+        kx_mbar_init(fbar, 1);
+        kx_mbar_init(fsfree, 8);   // one arrival per generating warp
         *lastc = 0;
         *abort = 0;
         kx_fence_mbar_init();
     }
-    if (warp == 1) {
+    if (warp == 8) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(kx_smem_u32(tslot)),
                      "r"(ncols)
                      : "memory");
@@ -344,46 +224,144 @@ __global__ void __launch_bounds__(192, 1)
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const uint32_t tmem = *tslot;
-    const int items = MT * NT * lsk;
+    const int items = MTb * NTi * chunks;
     const int half = ncols >> 1;   // columns of one accumulator
-    if (warp == 0) {
+    int fissued = 0;               // f' blocks requested (tid 0) / waited for (producers)
+    if (warp == 13) {
+        // ---- bulk copies: B (hi, lo) and, for the loss, A (hi, lo) of each stage
         if (lane == 0) {
             int it = 0;
             for (int w = blockIdx.x; w < items && !*abort; w += gridDim.x) {
-                const int c = w % lsk, nt = (w / lsk) % NT, mt = w / (lsk * NT);
+                const int c = w % chunks, nt = (w / chunks) % NTi, mt = w / (chunks * NTi);
                 const int kb0 = c * KC, kb1 = min(KB, kb0 + KC);
-                const int nsub = min(KX_GN, Bpad - nt * KX_GN) >> 6;
+                const uint32_t bbytes = (uint32_t)(pl.nsb * KX_BTILE * 4);
+                bool ok = true;
                 for (int kb = kb0; kb < kb1; ++kb, ++it) {
                     const int q = it % S, round = it / S;
-                    if (round > 0 && !kx_wait_role(empty0 + 8 * q, (round - 1) & 1, abort, err)) break;
+                    if (round > 0 && !kx_wait_role(empty0 + 8 * q, (round - 1) & 1, abort, err)) {
+                        ok = false;
+                        break;
+                    }
+                    unsigned char *sa = kx_gsm + (size_t)q * pl.stage, *sb = sa + 2 * KX_ATILE * 4;
                     const uint32_t bar = full0 + 8 * q;
-                    kx_mbar_expect_tx(bar, 2 * KX_ATILE * 4 + 2 * nsub * KX_BTILE * 4);
-                    unsigned char *sa = kx_lsm + (size_t)q * KX_GSTAGE, *sb = sa + 2 * KX_ATILE * 4;
-                    const float *a = A + ((size_t)mt * KB + kb) * 2 * KX_ATILE;
-                    kx_bulk_g2s(kx_smem_u32(sa), a, KX_ATILE * 4, bar);
-                    kx_bulk_g2s(kx_smem_u32(sa + KX_ATILE * 4), a + KX_ATILE, KX_ATILE * 4, bar);
-                    for (int j = 0; j < nsub; ++j) {
-                        const float *src = Bt + ((size_t)(nt * 4 + j) * KB + kb) * 2 * KX_BTILE;
-                        kx_bulk_g2s(kx_smem_u32(sb + j * KX_BTILE * 4), src, KX_BTILE * 4, bar);
-                        kx_bulk_g2s(kx_smem_u32(sb + 4 * KX_BTILE * 4 + j * KX_BTILE * 4), src + KX_BTILE,
-                                    KX_BTILE * 4, bar);
+                    kx_mbar_expect_tx(bar, (GEN ? 0u : 2u * KX_ATILE * 4) + 2 * bbytes);
+                    const float *bsrc = Bt + ((size_t)nt * KB + kb) * 2 * pl.nsb * KX_BTILE;
+                    kx_bulk_g2s(kx_smem_u32(sb), bsrc, bbytes, bar);
+                    kx_bulk_g2s(kx_smem_u32(sb + bbytes), bsrc + pl.nsb * KX_BTILE, bbytes, bar);
+                    if (!GEN) {
+                        const float *asrc = At + ((size_t)mt * KB + kb) * 2 * KX_ATILE;
+                        kx_bulk_g2s(kx_smem_u32(sa), asrc, KX_ATILE * 4, bar);
+                        kx_bulk_g2s(kx_smem_u32(sa + KX_ATILE * 4), asrc + KX_ATILE, KX_ATILE * 4, bar);
                     }
                     issued[q] = round + 1;
                 }
+                if (!ok) break;
             }
         }
-    } else if (warp == 1) {
+    } else if (warp < 8) {
+        // ---- the gain's A operand: row r = f'_n f'_m of instance b for the 16
+        // pairs of each k block (warp w: rows 32 (w % 4) .., pairs 8 (w / 4) ..)
+        if (GEN) {
+            int it = 0;
+            const int row = tid & 127, ph = (tid >> 7) * 8;   // instance row in the tile, first pair
+            for (int w = blockIdx.x; w < items && !*abort; w += gridDim.x) {
+                const int c = w % chunks, mt = w / (chunks * NTi);
+                const int kb0 = c * KC, kb1 = min(KB, kb0 + KC);
+                const float *fblk = fT + (size_t)mt * n * 128;   // this instance tile's f' [n][128]
+                bool ok = true;
+                if (fsm) {
+                    // the item's f' block, once every generating warp is done with
+                    // the previous one (fsfree: one arrival per warp)
+                    int r = 1;
+                    if (tid == 0) {
+                        if (fissued > 0) r = kx_wait_role(fsfree, (fissued - 1) & 1, abort, err);
+                        if (r) {
+                            kx_mbar_expect_tx(fbar, (uint32_t)(n * 512));
+                            kx_bulk_g2s(kx_smem_u32(fs), fblk, (uint32_t)(n * 512), fbar);
+                        }
+                    }
+                    if (lane == 0 && r) r = kx_wait_role(fbar, fissued & 1, abort, err);
+                    r = __shfl_sync(0xffffffffu, r, 0);
+                    ++fissued;
+                    if (!r) break;
+                }
+                for (int kb = kb0; kb < kb1; ++kb, ++it) {
+                    const int q = it % S, round = it / S;
+                    // lanes 0-7 decode this warp's eight pairs of the block
+                    // (independent of each other, so the loads below do not wait on
+                    // one another)
+                    const long long pq = (long long)kb * 16 + ph + (lane & 7);
+                    int dn = 0, dm = 0;
+                    if (pq < P) kx_pair_decode(pq, n, dn, dm);
+                    else dn = -1;   // padding: the product is dropped (dm = 0 keeps the load in range)
+                    if (round > 0) {
+                        int r = 1;
+                        if (lane == 0) r = kx_wait_role(empty0 + 8 * q, (round - 1) & 1, abort, err);
+                        r = __shfl_sync(0xffffffffu, r, 0);
+                        if (!r) {
+                            ok = false;
+                            break;
+                        }
+                    }
+                    float *ah = reinterpret_cast<float *>(kx_gsm + (size_t)q * pl.stage), *al = ah + KX_ATILE;
+                    // (the source is chosen outside the unrolled loop, so that its
+                    // 32 loads are issued back to back)
+                    float y[8];
+                    if (fsm) {
+#pragma unroll
+                        for (int e = 0; e < 8; ++e) {
+                            const int nn = __shfl_sync(0xffffffffu, dn, e), mm = __shfl_sync(0xffffffffu, dm, e);
+                            const float v = fs[max(nn, 0) * 128 + row] * fs[mm * 128 + row];
+                            y[e] = nn >= 0 ? v : 0.f;
+                        }
+                    } else {
+#pragma unroll
+                        for (int e = 0; e < 8; ++e) {
+                            const int nn = __shfl_sync(0xffffffffu, dn, e), mm = __shfl_sync(0xffffffffu, dm, e);
+                            const float v = __ldg(fblk + (size_t)max(nn, 0) * 128 + row) * __ldg(fblk + (size_t)mm * 128 + row);
+                            y[e] = nn >= 0 ? v : 0.f;
+                        }
+                    }
+#pragma unroll
+                    for (int q4 = 0; q4 < 8; q4 += 4) {
+                        float h[4], l[4];
+#pragma unroll
+                        for (int e = 0; e < 4; ++e) {
+                            uint32_t hb;
+                            asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(hb) : "f"(y[q4 + e]));
+                            h[e] = __uint_as_float(hb);
+                            l[e] = y[q4 + e] - h[e];
+                        }
+                        const int off = kx_tile_offset(row, ph + q4);
+                        *reinterpret_cast<float4 *>(ah + off) = make_float4(h[0], h[1], h[2], h[3]);
+                        *reinterpret_cast<float4 *>(al + off) = make_float4(l[0], l[1], l[2], l[3]);
+                    }
+                    // generic-proxy writes become visible to the tensor core (async proxy)
+                    kx_fence_proxy_async();
+                    __syncwarp();
+                    if (lane == 0) kx_mbar_arrive(full0 + 8 * q);
+                }
+                if (!ok) break;
+                if (fsm) {
+                    // this warp's reads of the f' block are done (its last A tile written)
+                    __syncwarp();
+                    if (lane == 0) kx_mbar_arrive(fsfree);
+                }
+            }
+        }
+    } else if (warp == 8) {
+        // ---- MMA issue
         if (lane == 0) {
             int it = 0, li = 0;
             for (int w = blockIdx.x; w < items && !*abort; w += gridDim.x, ++li) {
-                const int c = w % lsk, nt = (w / lsk) % NT;
+                const int c = w % chunks, nt = (w / chunks) % NTi;
                 const int kb0 = c * KC, kb1 = min(KB, kb0 + KC);
-                const int NTc = min(KX_GN, Bpad - nt * KX_GN);
+                const int Ni = min(KX_GN, nis - nt * KX_GN);
                 const int buf = li & 1, use = li >> 1;
                 if (use > 0 && !kx_wait_role(acce0 + 8 * buf, (use - 1) & 1, abort, err)) break;
                 asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
                 const uint32_t d = tmem + (uint32_t)(buf * half);
-                const uint32_t idesc = kx_idesc_tf32(128, NTc);
+                const uint32_t idesc = kx_idesc_tf32(128, Ni);
                 bool ok = true;
                 for (int kb = kb0; kb < kb1; ++kb, ++it) {
                     const int q = it % S, round = it / S;
@@ -393,11 +371,11 @@ __global__ void __launch_bounds__(192, 1)
                     }
                     seen[q] = round + 1;
                     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-                    const uint32_t aH = kx_smem_u32(kx_lsm + (size_t)q * KX_GSTAGE), aL = aH + KX_ATILE * 4;
-                    const uint32_t bH = aH + 2 * KX_ATILE * 4, bL = bH + 4 * KX_BTILE * 4;
+                    const uint32_t aH = kx_smem_u32(kx_gsm + (size_t)q * pl.stage), aL = aH + KX_ATILE * 4;
+                    const uint32_t bH = aH + 2 * KX_ATILE * 4, bL = bH + pl.nsb * KX_BTILE * 4;
 #pragma unroll
                     for (int step = 0; step < KX_TILE_K / 8; ++step) {
-                        const uint32_t o = 256u * step;
+                        const uint32_t o = 256u * step;   // 8 TF32 = two 16-byte core-matrix columns
                         kx_mma_tf32(d, kx_desc(aH + o, 128, 512), kx_desc(bH + o, 128, 512), idesc,
                                     (kb > kb0 || step) ? 1u : 0u);
                         kx_mma_tf32(d, kx_desc(aH + o, 128, 512), kx_desc(bL + o, 128, 512), idesc, 1u);
@@ -411,23 +389,24 @@ __global__ void __launch_bounds__(192, 1)
             }
         }
     } else {
+        // ---- epilogue: FP32 partials out[c][b][i]
         const int qtr = warp & 3;   // tensor-memory lane quarter this warp may read
         int li = 0;
         for (int w = blockIdx.x; w < items; w += gridDim.x, ++li) {
-            const int c = w % lsk, nt = (w / lsk) % NT, mt = w / (lsk * NT);
-            const int NTc = min(KX_GN, Bpad - nt * KX_GN);
+            const int c = w % chunks, nt = (w / chunks) % NTi, mt = w / (chunks * NTi);
+            const int Ni = min(KX_GN, nis - nt * KX_GN);
             const int buf = li & 1, use = li >> 1;
-            bool ok = true;
+            int ok = 1;
             if (lane == 0) ok = kx_wait_role(accf0 + 8 * buf, use & 1, abort, err);
-            ok = __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
+            ok = __shfl_sync(0xffffffffu, ok, 0);
             if (!ok) break;
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            const int row = mt * 128 + qtr * 32 + lane;
-            float *dst = Lp + ((size_t)c * MT * 128 + row) * Bpad + (size_t)nt * KX_GN;
-            for (int c0 = 0; c0 < NTc; c0 += 16) {
+            const int b = mt * 128 + qtr * 32 + lane;
+            float *dst = out + ((size_t)c * Bpad + b) * nis + (size_t)nt * KX_GN;
+            for (int c0 = 0; c0 < Ni; c0 += 16) {
                 float t[16];
                 kx_tmem_ld16(tmem + ((uint32_t)(qtr * 32) << 16) + (uint32_t)(buf * half + c0), t);
-                if (row < n) {
+                if (b < Bpad) {
 #pragma unroll
                     for (int q = 0; q < 16; q += 4)
                         *reinterpret_cast<float4 *>(dst + c0 + q) = make_float4(t[q], t[q + 1], t[q + 2], t[q + 3]);
@@ -444,6 +423,7 @@ __global__ void __launch_bounds__(192, 1)
         // and tensor memory are released
         for (int q = 0; q < S; ++q)
             if (issued[q] > seen[q]) kx_mbar_wait(full0 + 8 * q, (issued[q] - 1) & 1, 1ll << 24);
+        if (fsm && fissued > 0) kx_mbar_wait(fbar, (fissued - 1) & 1, 1ll << 24);
         if (*lastc > 0) {
             const int it = *lastc - 1;
             kx_mbar_wait(empty0 + 8 * (it % S), (it / S) & 1, 1ll << 24);
@@ -452,7 +432,7 @@ __global__ void __launch_bounds__(192, 1)
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    if (warp == 1)
+    if (warp == 8)
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(ncols) : "memory");
 }
 
@@ -481,13 +461,11 @@ __device__ __forceinline__ void kx_two_sum_f(float a, float b, float &s, float &
 
 template <int IPL, int WARPS>
 __global__ void __launch_bounds__(WARPS * 32, (WARPS <= 16 && IPL <= 2) ? 2 : 1)
-    k_batch_loss(int n, int B, int tds, int Bpad, const float2 *__restrict__ lel,
+    k_batch_loss(int n, int B, int tds, const float2 *__restrict__ lel,
                  const int2 *__restrict__ lseg, const int *__restrict__ lsw,
                  const int *__restrict__ lorder, const float2 *__restrict__ td,
-                 const float *__restrict__ Gp, const double *__restrict__ fmax,
-                 double2 *__restrict__ partial,
-                 const kx_inst_state *__restrict__ st, int stage,
-                 const float *__restrict__ Lp, const int *__restrict__ cflag, int lsk, int MTL) {
+                 const double *__restrict__ fmax, double2 *__restrict__ partial,
+                 const kx_inst_state *__restrict__ st, int stage, const int *__restrict__ cflag) {
     // [n][32][IPL] (l2_j, D_j) table; after the loss loop the same space holds
     // the cross-warp reduction [2][WARPS][32 IPL] doubles
     extern __shared__ __align__(16) float2 kx_ltab[];
@@ -500,24 +478,17 @@ __global__ void __launch_bounds__(WARPS * 32, (WARPS <= 16 && IPL <= 2) ? 2 : 1)
     for (int s = 0; s < IPL; ++s) {
         b[s] = blockIdx.x * (32 * IPL) + s * 32 + lane;
         act[s] = b[s] < B && !(st && (st[b[s]].done || (stage == 2 && st[b[s]].skip2)));
+        // Chebyshev loss (cflag non-null): only the instances whose truncation
+        // bound was exceeded take the exact loss
+        if (cflag && act[s]) act[s] = cflag[b[s]] != 0;
         any |= act[s];
     }
     if (!__syncthreads_or(any)) return;
     const int i = lorder[blockIdx.y];
-    // Chebyshev loss (Lp non-null): the loss comes from the GEMM partials; the
-    // exact loop runs only for a block holding an instance whose truncation
-    // bound was exceeded (cflag), and only that instance takes its result
-    bool exact = true;
-    if (Lp) {
-        bool fl = false;
-#pragma unroll
-        for (int s = 0; s < IPL; ++s) fl |= act[s] && cflag[b[s]] != 0;
-        exact = __syncthreads_or(fl) != 0;
-    }
     float hi[IPL], lo[IPL];
 #pragma unroll
     for (int s = 0; s < IPL; ++s) hi[s] = lo[s] = 0.f;
-    if (exact) {
+    {
         // layout: IPL = 1: float2 at [j][lane]; else float4 (two instances) at
         // [j][IPL / 2][lane], so that each table read is one conflict-free LDS.128
         for (int j = warp; j < n; j += WARPS) {
@@ -629,7 +600,7 @@ __global__ void __launch_bounds__(WARPS * 32, (WARPS <= 16 && IPL <= 2) ? 2 : 1)
             hi[s] = sm;
             lo[s] += er;
         }
-    }   // exact
+    }
     __syncthreads();   // every warp is done with the table
     double *red = reinterpret_cast<double *>(kx_ltab);   // [WARPS][32 IPL]
 #pragma unroll
@@ -638,21 +609,11 @@ __global__ void __launch_bounds__(WARPS * 32, (WARPS <= 16 && IPL <= 2) ? 2 : 1)
     if (warp < IPL) {
         const int s = warp;   // warp s finishes instance slot s
         const int bb = blockIdx.x * (32 * IPL) + s * 32 + lane;
-        if (bb < B && !(st && (st[bb].done || (stage == 2 && st[bb].skip2)))) {
-            double L = 0.0, G = 0.0;
-            if (Lp && cflag[bb] == 0) {
-                // the GEMM's k chunks in order
-                for (int c = 0; c < lsk; ++c) L += (double)Lp[((size_t)c * MTL * 128 + i) * Bpad + bb];
-            } else {
+        if (bb < B && !(st && (st[bb].done || (stage == 2 && st[bb].skip2))) && !(cflag && cflag[bb] == 0)) {
+            double L = 0.0;
 #pragma unroll
-                for (int w = 0; w < WARPS; ++w) L += red[w * 32 * IPL + s * 32 + lane];
-            }
-            // the gain of row i: the GEMM tiles' partials over the rows (i, a)
-            const int segmax = 128 / n + 2;
-            for (int mt = (i * n) / 128; mt <= (i * n + n - 1) / 128; ++mt)
-                G += (double)Gp[(size_t)(mt * segmax + i - (mt * 128) / n) * Bpad + bb];
-            const double fm = fmax[bb];
-            partial[(size_t)bb * n + i] = make_double2(fm * fm * G, fm * L);
+            for (int w = 0; w < WARPS; ++w) L += red[w * 32 * IPL + s * 32 + lane];
+            partial[(size_t)bb * n + i] = make_double2(0.0, fmax[bb] * L);   // the gain: the GEMM's partials
         }
     }
 }
@@ -676,8 +637,8 @@ static size_t kx_loss_smem(int n, kx_loss_shape sh) {
 }
 
 void kx_batch_prepare() {
-    cudaFuncSetAttribute(k_gain_fused<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, KX_GAIN_SMEM(2));
-    cudaFuncSetAttribute(k_loss_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, KX_LG_SMEM);
+    cudaFuncSetAttribute(k_split_gemm<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+    cudaFuncSetAttribute(k_split_gemm<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
     cudaFuncSetAttribute(k_batch_loss<2, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)kx_loss_smem(200, {2, 16}));
     cudaFuncSetAttribute(k_batch_loss<2, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -687,53 +648,62 @@ void kx_batch_prepare() {
     cudaGetLastError();
 }
 
+// Persistent grid of a split GEMM: one CTA per SM, at most one per work item.
+static int kx_sg_grid(int items) {
+    static int sms = 0;
+    if (!sms) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (sms < 1) sms = 148;
+    }
+    return std::max(1, std::min(items, sms));
+}
+
 cudaError_t kx_launch_batch_contract(const kx_kernel *k, int B, const kx_batch_views &v,
                                      const kx_inst_state *st, int stage, int *d_err,
                                      cudaStream_t s) {
-    const int KB = k->Kpad / KX_TILE_K, MT = k->Mpad / 128, NT = (v.Bpad + KX_GN - 1) / KX_GN;
-    dim3 g1(NT, MT);
-    k_gain_fused<2><<<g1, 128, KX_GAIN_SMEM(2), s>>>(k->d_Atile, v.bt, v.fT, v.Gp, KB, k->n, v.Bpad, d_err);
+    const int MTb = v.Bpad / 128, NTi = (k->nis + KX_GN - 1) / KX_GN;
+    int ncols = 32;   // two accumulators of up to 256 columns (the widest i tile)
+    while (ncols < 2 * std::min(KX_GN, k->nis)) ncols <<= 1;
+    // gain: out = Gs [gsk][Bpad][nis]
+    int items = MTb * NTi * k->gsk;
+    k_split_gemm<true><<<kx_sg_grid(items), KX_SG_THREADS, kx_sg_plan_for(true, k->n, k->nsubI).smem, s>>>(
+        nullptr, k->d_Sg, v.Gs, v.fT, k->P, k->n, k->KBG, KX_GAIN_KC, k->gsk, MTb, NTi, k->nsubI,
+        v.Bpad, k->nis, ncols, d_err);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    const float *Lp = nullptr;
     if (k->cheb_K) {
-        // the Chebyshev loss GEMM: one CTA per SM over the work items
-        const int MT = k->MTL, NTl = (v.Bpad + KX_GN - 1) / KX_GN;
-        const int items = MT * NTl * k->lsk;
-        int dev = 0, sms = 148;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        const int maxc = std::min(KX_GN, v.Bpad);
-        int ncols = 32;
-        while (ncols < 2 * maxc) ncols <<= 1;
-        k_loss_gemm<<<std::min(items, sms), 192, KX_LG_SMEM, s>>>(k->d_Mtile, v.yt, v.Lp, k->KBL, 8, k->lsk,
-                                                                  MT, NTl, v.Bpad, k->n, ncols, d_err);
+        // loss: out = Lp [lsk][Bpad][nis]
+        items = MTb * NTi * k->lsk;
+        k_split_gemm<false><<<kx_sg_grid(items), KX_SG_THREADS, kx_sg_plan_for(false, k->n, k->nsubI).smem, s>>>(
+            v.yt, k->d_Mtile, v.Lp, nullptr, 0, k->n, k->KBL, KX_LOSS_KC, k->lsk, MTb, NTi, k->nsubI,
+            v.Bpad, k->nis, ncols, d_err);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
-        Lp = v.Lp;
     }
+    // the exact loss: every instance, or (Chebyshev loss) the flagged ones
     const kx_loss_shape sh = kx_loss_shape_for(k->n);
     const int per = 32 * sh.ipl;
     dim3 g2((B + per - 1) / per, k->n);
     const size_t smem = kx_loss_smem(k->n, sh);
+    const int *flags = k->cheb_K ? v.cflag : nullptr;
     if (sh.ipl == 2 && sh.warps == 16)
-        k_batch_loss<2, 16><<<g2, 512, smem, s>>>(k->n, B, v.B, v.Bpad, k->d_lel, k->d_lseg, k->d_lsw,
-                                                  k->d_lorder, v.td, v.Gp, v.fmax, v.partial, st, stage,
-                                                  Lp, v.cflag, k->lsk, k->MTL);
+        k_batch_loss<2, 16><<<g2, 512, smem, s>>>(k->n, B, v.B, k->d_lel, k->d_lseg, k->d_lsw, k->d_lorder,
+                                                  v.td, v.fmax, v.partial, st, stage, flags);
     else if (sh.ipl == 2)
-        k_batch_loss<2, 32><<<g2, 1024, smem, s>>>(k->n, B, v.B, v.Bpad, k->d_lel, k->d_lseg, k->d_lsw,
-                                                   k->d_lorder, v.td, v.Gp, v.fmax, v.partial, st, stage,
-                                                   Lp, v.cflag, k->lsk, k->MTL);
+        k_batch_loss<2, 32><<<g2, 1024, smem, s>>>(k->n, B, v.B, k->d_lel, k->d_lseg, k->d_lsw, k->d_lorder,
+                                                   v.td, v.fmax, v.partial, st, stage, flags);
     else
-        k_batch_loss<1, 32><<<g2, 1024, smem, s>>>(k->n, B, v.B, v.Bpad, k->d_lel, k->d_lseg, k->d_lsw,
-                                                   k->d_lorder, v.td, v.Gp, v.fmax, v.partial, st, stage,
-                                                   Lp, v.cflag, k->lsk, k->MTL);
+        k_batch_loss<1, 32><<<g2, 1024, smem, s>>>(k->n, B, v.B, k->d_lel, k->d_lseg, k->d_lsw, k->d_lorder,
+                                                   v.td, v.fmax, v.partial, st, stage, flags);
     return cudaGetLastError();
 }
 
 // ------------------------------------------------------ host table build
 // From the device FP64 tables (symmetrised S over n <= m, j_L, omega):
-//  A tiles: W_full[(i n)][m] = S_inm / 2 (n != m), S_inn (n = m), TF32 hi/lo
-//           (hi rounded to nearest TF32, lo = W - hi), in MMA operand tiles;
+//  gain operand: S_ip (p = pair n <= m) as TF32 hi/lo (hi rounded to nearest
+//           TF32, lo = S - hi) in 64-row tiles of the rows i;
+//  Chebyshev loss operand (loss_terms = K): M_k[i][j] likewise, column j K + k;
 //  loss list: per row, the nonzero (S, omega) as floats sorted by j_L, cut into
 //           segments of at most KX_SEG elements of one j_L, each zero-padded to
 //           a multiple of 4: (first element, j_L << 8 | padded count) per
@@ -752,6 +722,24 @@ static float kx_tf32_round(float x) {
     return r;
 }
 
+// Shapes of the batched path's GEMMs for an n-point grid (and cheb_K terms):
+// fixed by the kernel alone, so that an instance's sums do not depend on the
+// batch it is evaluated in.
+void kx_split_geometry(kx_kernel *k) {
+    const int n = k->n;
+    const long long P = (long long)n * (n + 1) / 2;
+    k->nsubI = (n + 63) / 64;
+    k->nis = (n + 15) / 16 * 16;
+    k->KBG = (int)((P + KX_TILE_K - 1) / KX_TILE_K);
+    k->gsk = (k->KBG + KX_GAIN_KC - 1) / KX_GAIN_KC;
+    if (k->cheb_K) {
+        k->KBL = ((n - 1) * k->cheb_K + KX_TILE_K - 1) / KX_TILE_K;
+        k->lsk = (k->KBL + KX_LOSS_KC - 1) / KX_LOSS_KC;
+    } else {
+        k->KBL = k->lsk = 0;
+    }
+}
+
 int kx_batch_build_tables(kx_ctx *ctx, kx_kernel *k) {
     const int n = k->n;
     const long long P = k->P;
@@ -761,10 +749,23 @@ int kx_batch_build_tables(kx_ctx *ctx, kx_kernel *k) {
         cudaMemcpy(om.data(), k->d_om64, sizeof(double) * om.size(), cudaMemcpyDeviceToHost) != cudaSuccess ||
         cudaMemcpy(jl.data(), k->d_jl, sizeof(uint16_t) * jl.size(), cudaMemcpyDeviceToHost) != cudaSuccess)
         return kx_set_error(ctx, KX_ECUDA, "batched build: table download failed");
-    k->Mpad = ((n * n + 127) / 128) * 128;
-    k->Kpad = ((n + 31) / 32) * 32;
-    const int MT = k->Mpad / 128, KB = k->Kpad / KX_TILE_K;
-    std::vector<float> At((size_t)MT * KB * 2 * KX_ATILE, 0.f);
+    kx_split_geometry(k);
+    // gain GEMM operand: S_ip (p = pairs n <= m in packed order) as TF32 hi/lo;
+    // per (i tile of up to 256 rows, k block of 16 pairs) the hi part, then the
+    // lo part, each nsb 64-row tiles in MMA operand layout (one bulk copy each)
+    const int nsb = std::min(4, k->nsubI), NTi = (k->nis + 255) / 256;
+    auto bt_index = [&](int i, long long c, int KB, int h) {
+        const size_t blk = (((size_t)(i / 256) * KB + (size_t)(c / KX_TILE_K)) * 2 + h) * nsb;
+        return (blk + (size_t)((i % 256) / 64)) * KX_BTILE + kx_tile_offset(i % 64, (int)(c % KX_TILE_K));
+    };
+    std::vector<float> Sg((size_t)NTi * k->KBG * 2 * nsb * KX_BTILE, 0.f);
+    for (int i = 0; i < n; ++i)
+        for (long long p = 0; p < P; ++p) {
+            const float w = (float)W[(size_t)i * P + p];
+            const float wh = kx_tf32_round(w), wl = w - wh;
+            Sg[bt_index(i, p, k->KBG, 0)] = wh;
+            Sg[bt_index(i, p, k->KBG, 1)] = wl;
+        }
     std::vector<float2> lel;
     std::vector<int2> lseg;
     const int WARPS = kx_loss_shape_for(n).warps;
@@ -783,19 +784,9 @@ int kx_batch_build_tables(kx_ctx *ctx, kx_kernel *k) {
     for (int i = 0; i < n; ++i) {
         row.clear();
         for (int a = 0; a < n; ++a) {
-            for (int b = 0; b < n; ++b) {
-                const int lo = a < b ? a : b, hi = a < b ? b : a;
-                const size_t e = (size_t)i * P + base[lo] + (hi - lo);
-                const double wf = lo == hi ? W[e] : 0.5 * W[e];
-                const float w = (float)wf;
-                const float wh = kx_tf32_round(w);
-                const float wl = w - wh;
-                const int r = i * n + a;
-                const int mt = r / 128, rl = r % 128, kb = b / KX_TILE_K, kk = b % KX_TILE_K;
-                const size_t t = ((size_t)mt * KB + kb) * 2;
-                At[t * KX_ATILE + kx_tile_offset(rl, kk)] = wh;
-                At[(t + 1) * KX_ATILE + kx_tile_offset(rl, kk)] = wl;
-                if (a <= b && W[e] != 0.0) row.push_back({(int)jl[e], (float)W[e], (float)om[e]});
+            for (int b = a; b < n; ++b) {
+                const size_t e = (size_t)i * P + base[a] + (b - a);
+                if (W[e] != 0.0) row.push_back({(int)jl[e], (float)W[e], (float)om[e]});
             }
         }
         std::stable_sort(row.begin(), row.end(), [](const El &x, const El &y) { return x.j < y.j; });
@@ -843,9 +834,6 @@ int kx_batch_build_tables(kx_ctx *ctx, kx_kernel *k) {
     std::vector<float> Mt;
     if (k->cheb_K) {
         const int K = k->cheb_K;
-        k->MTL = (n + 127) / 128;
-        k->KBL = ((n - 1) * K + 15) / 16;
-        k->lsk = (k->KBL + 7) / 8;   // GEMM work items of about eight k blocks
         std::vector<double> M((size_t)n * (n - 1) * K, 0.0);
         for (int i = 0; i < n; ++i) {
             for (long long e = 0; e < P; ++e) {
@@ -864,16 +852,15 @@ int kx_batch_build_tables(kx_ctx *ctx, kx_kernel *k) {
                 }
             }
         }
-        Mt.assign((size_t)k->MTL * k->KBL * 2 * KX_ATILE, 0.f);
+        Mt.assign((size_t)NTi * k->KBL * 2 * nsb * KX_BTILE, 0.f);
         for (int i = 0; i < n; ++i)
             for (int j = 0; j + 1 < n; ++j)
                 for (int kk = 0; kk < K; ++kk) {
                     const float w = (float)M[((size_t)i * (n - 1) + j) * K + kk];
                     const float wh = kx_tf32_round(w), wl = w - wh;
-                    const int c = j * K + kk, mt = i / 128, r = i % 128, kb = c / KX_TILE_K;
-                    const size_t t = ((size_t)mt * k->KBL + kb) * 2;
-                    Mt[t * KX_ATILE + kx_tile_offset(r, c % KX_TILE_K)] = wh;
-                    Mt[(t + 1) * KX_ATILE + kx_tile_offset(r, c % KX_TILE_K)] = wl;
+                    const long long c = (long long)j * K + kk;
+                    Mt[bt_index(i, c, k->KBL, 0)] = wh;
+                    Mt[bt_index(i, c, k->KBL, 1)] = wl;
                 }
         if (cudaMalloc(&k->d_Mtile, sizeof(float) * Mt.size()) != cudaSuccess) {
             cudaGetLastError();
@@ -888,7 +875,7 @@ int kx_batch_build_tables(kx_ctx *ctx, kx_kernel *k) {
     std::stable_sort(lorder.begin(), lorder.end(), [&](int x, int y) { return rlen[x] > rlen[y]; });
     if (lel.empty()) lel.push_back(make_float2(0.f, 0.f));
     if (lseg.empty()) lseg.push_back(make_int2(0, 0));
-    if (cudaMalloc(&k->d_Atile, sizeof(float) * At.size()) != cudaSuccess ||
+    if (cudaMalloc(&k->d_Sg, sizeof(float) * Sg.size()) != cudaSuccess ||
         cudaMalloc(&k->d_lel, sizeof(float2) * lel.size()) != cudaSuccess ||
         cudaMalloc(&k->d_lseg, sizeof(int2) * lseg.size()) != cudaSuccess ||
         cudaMalloc(&k->d_lsw, sizeof(int) * lsw.size()) != cudaSuccess ||
@@ -898,9 +885,9 @@ int kx_batch_build_tables(kx_ctx *ctx, kx_kernel *k) {
     }
     k->nseg = (long long)lsw[(size_t)n * WARPS];
     k->nlel = (long long)lel.size();
-    k->bytes += (long long)(sizeof(float) * At.size() + sizeof(float2) * lel.size() +
+    k->bytes += (long long)(sizeof(float) * Sg.size() + sizeof(float2) * lel.size() +
                             sizeof(int2) * lseg.size() + sizeof(int) * (lsw.size() + lorder.size()));
-    if (cudaMemcpy(k->d_Atile, At.data(), sizeof(float) * At.size(), cudaMemcpyHostToDevice) != cudaSuccess ||
+    if (cudaMemcpy(k->d_Sg, Sg.data(), sizeof(float) * Sg.size(), cudaMemcpyHostToDevice) != cudaSuccess ||
         cudaMemcpy(k->d_lel, lel.data(), sizeof(float2) * lel.size(), cudaMemcpyHostToDevice) != cudaSuccess ||
         cudaMemcpy(k->d_lseg, lseg.data(), sizeof(int2) * lseg.size(), cudaMemcpyHostToDevice) != cudaSuccess ||
         cudaMemcpy(k->d_lsw, lsw.data(), sizeof(int) * lsw.size(), cudaMemcpyHostToDevice) != cudaSuccess ||

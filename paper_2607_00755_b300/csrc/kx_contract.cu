@@ -244,7 +244,7 @@ static cudaError_t kx_launch_ex(void (*kern)(KArgs...), dim3 grid, dim3 block, s
 //   2^{max(l2_j, l2_{j+1})} sum_k eps_k s^k e^{-x} I_k(x) T_k(2 omega - 1)
 // (eps_0 = 1, eps_k = 2): y_k = 2^{l2max} eps_k s^k e^{-x} I_k(x).  The ratios
 // r_k = I_{k+1}(x) / I_k(x) come from the backward recurrence
-// r_{k-1} = x / (2k + x r_k), started at r = 0 well above K (Miller's backward
+// r_{k-1} = x / (2k + x r_k), started at r = 0 above K + x (Miller's backward
 // recurrence in ratio form, stable for every x >= 0); v_0 = 1, v_k = v_{k-1}
 // r_{k-1}, and the normalisation sum_k eps_k e^{-x} I_k(x) = 1 (the generating
 // function at t = 1) turns them into e^{-x} I_k(x) = v_k / sum_k eps_k v_k; the
@@ -266,7 +266,8 @@ __device__ __noinline__ float kx_cheb_tile(float D, float l2m, bool real, float 
         if (x > 24.f) {
             bound = scale;
         } else {
-            const int k0 = K + 16 + (int)(2.f * x);
+            const int k0 = K + 6 + (int)x;   // (a float model of this recurrence against scipy's
+                                             // e^-x I_k: start points K + 4 + x and beyond agree to 6e-8)
             float rk = 0.f, t = 1.f;
             for (int k = k0; k > K; --k) {
                 t = fmaf(rk, t, 1.f);
@@ -296,12 +297,12 @@ __device__ __noinline__ float kx_cheb_tile(float D, float l2m, bool real, float 
             bound = 2.f * vK * tK * sc;
         }
     }
-    // operand tiles [b / 64][k block][hi, lo][64 x 16]
+    // operand tiles [b / 128][k block][hi, lo][128 x 16]
 #pragma unroll
     for (int k4 = 0; k4 < K; k4 += 4) {
         const int c = j * K + k4, kb = c >> 4;
-        const size_t tb = ((size_t)(b >> 6) * KBL + kb) * 2;
-        const int off = kx_tile_offset(b & 63, c & 15);
+        const size_t tb = ((size_t)(b >> 7) * KBL + kb) * 2;
+        const int off = kx_tile_offset(b & 127, c & 15);
         float h[4], l[4];
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
@@ -310,8 +311,8 @@ __device__ __noinline__ float kx_cheb_tile(float D, float l2m, bool real, float 
             h[q] = __uint_as_float(hb);
             l[q] = y[k4 + q] - h[q];
         }
-        *reinterpret_cast<float4 *>(yt + tb * (64 * KX_TILE_K) + off) = make_float4(h[0], h[1], h[2], h[3]);
-        *reinterpret_cast<float4 *>(yt + (tb + 1) * (64 * KX_TILE_K) + off) = make_float4(l[0], l[1], l[2], l[3]);
+        *reinterpret_cast<float4 *>(yt + tb * (128 * KX_TILE_K) + off) = make_float4(h[0], h[1], h[2], h[3]);
+        *reinterpret_cast<float4 *>(yt + (tb + 1) * (128 * KX_TILE_K) + off) = make_float4(l[0], l[1], l[2], l[3]);
     }
     return bound;
 }
@@ -491,16 +492,8 @@ __device__ __forceinline__ int kx_prep_block(int n, int path, double x, double E
             v.td[(long long)i * v.B + b] = make_float2((float)l2, (float)D);   // (l2_j, D_j), instance-minor
         }
         const float fp = (in && fm > 0.0) ? (float)(x * rfm) : 0.f;
-        if (in) v.fT[(size_t)i * v.Bpad + b] = fp;
-        uint32_t hb;
-        asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(hb) : "f"(fp));
-        const float hi = __uint_as_float(hb);
-        static_assert(KX_TILE_K == 16, "tile indexing below uses k blocks of 16");
-        const int KB = blockDim.x >> 4;   // blockDim = n rounded up to 32 = padded k extent
-        const size_t t = ((size_t)(b >> 6) * KB + (i >> 4)) * 2;
-        const int off = kx_tile_offset(b & 63, i & 15);
-        v.bt[t * (64 * KX_TILE_K) + off] = hi;
-        v.bt[(t + 1) * (64 * KX_TILE_K) + off] = fp - hi;
+        // [instance tile][i][128]: the gain GEMM forms f'_n f'_m from these
+        if (in) v.fT[((size_t)(b >> 7) * n + i) * 128 + (b & 127)] = fp;
         if (v.yt) {
             // Chebyshev loss: the coefficients of bracket (i, i + 1) of this
             // instance (zeros in the k padding), and whether any bracket's
@@ -1509,6 +1502,30 @@ __device__ __forceinline__ kx_row_out kx_combine_project(int n, int chunks, int 
         kx_df_add(h0, l0, h2);
         l0 += l2;
         G = (double)h0 + (double)l0;
+    } else if (i < n && path == KX_SPLIT_TF32) {
+        // the gain GEMM's k chunks in order (f' units); the loss from the
+        // Chebyshev GEMM's chunks, or the exact loss kernel's row sum (x f_max)
+        // (double-float sums of the FP32 chunk partials: exact TwoSum, FP64 at the end)
+        const size_t cs = (size_t)v.Bpad * v.nis;
+        auto dfsum = [&](const float *p, int cnt) {
+            float h = 0.f, l = 0.f;
+            int c = 0;
+            for (; c + 16 <= cnt; c += 16) {
+                float x[16];
+#pragma unroll
+                for (int u = 0; u < 16; ++u) x[u] = p[(size_t)(c + u) * cs];
+#pragma unroll
+                for (int u = 0; u < 16; ++u) kx_df_add(h, l, x[u]);
+            }
+            for (; c < cnt; ++c) kx_df_add(h, l, p[(size_t)c * cs]);
+            return (double)h + (double)l;
+        };
+        G = fm * fm * dfsum(v.Gs + (size_t)b * v.nis + i, v.gsk);
+        if (v.Lp && v.cflag[b] == 0) {
+            L = fm * dfsum(v.Lp + (size_t)b * v.nis + i, v.lsk);
+        } else {
+            L = v.partial[(long long)b * n + i].y;
+        }
     } else if (i < n) {
         const double2 *pp = v.partial + ((long long)b * n + i) * chunks;
         for (int c = 0; c < chunks; ++c) {

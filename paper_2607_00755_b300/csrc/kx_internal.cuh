@@ -59,10 +59,13 @@ struct kx_kernel {
     int vpl;             // vectors per lane of a unit
     int ntask;           // streaming tasks
     int tslots;          // partial slots per instance: n x MT, MT = largest row task count rounded up to even
-    // batched (split TF32) tables
-    int Mpad;            // n^2 rows (i, n) padded to a multiple of 128
-    int Kpad;            // n columns (m) padded to a multiple of 32
-    float *d_Atile;      // [Mpad/128][Kpad/16][hi, lo][2048]: W_full as TF32 hi/lo in MMA operand tiles
+    // batched (split TF32) tables: the GEMMs take the instances as rows and the
+    // grid points i as columns (64-row operand tiles of i, 16-wide k blocks)
+    int nsubI;           // 64-row tiles of the rows i: ceil(n / 64)
+    int nis;             // columns of the GEMM partials: n rounded up to 16
+    int KBG;             // k blocks of the gain GEMM: ceil(P / 16), P pairs n <= m
+    int gsk;             // k chunks of the gain GEMM
+    float *d_Sg;         // [nsubI][KBG][hi, lo][1024]: S_ip as TF32 hi/lo operand tiles
     float2 *d_lel;       // per row i: nonzero (S_inm, omega) sorted by j_L, element pairs as
                          // (S_0, S_1), (omega_0, omega_1)
     int2 *d_lseg;        // segments of <= 64 elements of one j_L: (first element, j_L << 8 | count)
@@ -71,9 +74,8 @@ struct kx_kernel {
     // Chebyshev loss GEMM (loss_terms > 0): M_k[i][j] as TF32 hi/lo operand tiles
     int cheb_K;          // terms (0: exact loss only)
     int KBL;             // 16-wide k blocks of the flattened (j, k) dimension: ceil((n - 1) K / 16)
-    int MTL;             // 128-row tiles of the rows i: ceil(n / 128)
     int lsk;             // k chunks of the loss GEMM (each CTA work item sums one chunk)
-    float *d_Mtile;      // [MTL][KBL][hi, lo][2048]
+    float *d_Mtile;      // [nsubI][KBL][hi, lo][1024]
     long long nseg;      // segments, all rows
     long long nlel;      // loss elements with the segments' zero padding
     long long nnz;
@@ -161,15 +163,14 @@ struct kx_batch_views {
     double *M2;            // [B] |M|^2 per instance
     kx_diag *diag;         // [B]
     int chunks;            // partials per row (FP32 path: partial slots per instance)
-    // batched (split TF32) path
-    float *bt;             // [Bpad/64][Kpad/16][hi, lo][1024]: f/f_max as TF32 hi/lo MMA operand tiles
-    float *fT;             // [Kpad][Bpad]: f/f_max, instance-minor
-    float *Gp;             // [Mpad/128][128/n + 2][Bpad]: gain partials per (GEMM row tile, grid
-                           //   point i in the tile, instance)
+    // batched (split TF32) path; Bpad = B rounded up to 128 (one GEMM row tile)
+    float *fT;             // [Bpad/128][n][128]: f/f_max, instance-minor within 128-instance tiles
+    float *Gs;             // [gsk][Bpad][nis]: FP32 gain partials per k chunk of the gain GEMM
     float *yt;             // Chebyshev loss: [Bpad/64][KBL][hi, lo][1024] coefficient operand tiles
-    float *Lp;             // Chebyshev loss: [lsk][MTL 128][Bpad] FP32 loss partials per k chunk
+    float *Lp;             // Chebyshev loss: [lsk][Bpad][nis] FP32 loss partials per k chunk
     int *cflag;            // Chebyshev loss: [B] 1 = an instance bracket beyond the truncation bound
     int cheb_K, KBL;       // Chebyshev loss: terms (0: exact loss), k blocks of the coefficient tiles
+    int gsk, lsk, nis;     // split path: k chunks of the gain and loss GEMMs, partial row length
     int *err;              // tensor-core stage timeout flag (bounded waits)
     int B;                 // instances the views were carved for (td's stride on the split path)
     int Bpad;
@@ -243,6 +244,7 @@ cudaError_t kx_launch_wait_check(long long cycles, int *out, cudaStream_t s);
 
 // batched split-TF32 path (kx_batch.cu)
 int kx_batch_build_tables(kx_ctx *ctx, kx_kernel *k);   // after the FP64 build
+void kx_split_geometry(kx_kernel *k);   // GEMM shapes of the batched path from n and cheb_K
 cudaError_t kx_launch_batch_contract(const kx_kernel *k, int B, const kx_batch_views &v,
                                      const kx_inst_state *st, int stage, int *d_err, cudaStream_t s);
 void kx_batch_prepare();   // one-time kernel attribute setup (outside stream capture)

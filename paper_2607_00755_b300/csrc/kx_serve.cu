@@ -114,8 +114,8 @@ static size_t kx_group_estimate(const kx_server_config &cfg, int n) {
     long long V = 0;
     for (int a = 0; a < n; ++a) V += (n - a + 3) / 4;
     d.V = (int)V;
-    d.Mpad = ((n * n + 127) / 128) * 128;
-    d.Kpad = ((n + 31) / 32) * 32;
+    d.cheb_K = cfg.precision == KX_SPLIT_TF32 ? cfg.loss_terms : 0;
+    kx_split_geometry(&d);
     size_t tables;
     // FP32: upper bounds (every vector kept, rows padded to whole units, one
     // unit per task)
@@ -125,10 +125,11 @@ static size_t kx_group_estimate(const kx_server_config &cfg, int n) {
         tables = (size_t)n * upr * unit * (16 + 16 + 4) + (size_t)(n + 1) * 4 + (size_t)n * 8 +
                  (size_t)n * upr * 16;
     else if (cfg.precision == KX_FP64) tables = (size_t)n * d.P * 18 + 4 * d.P;
-    else {   // split: A tiles, loss elements (with padding), segments, row tables
+    else {   // split: gain (and Chebyshev) operand tiles, loss elements (with padding), segments, row tables
         const size_t segs = (size_t)n * (d.P / 64 + n + 1);   // at most P/64 + n per row
-        tables = (size_t)d.Mpad * d.Kpad * 8 + ((size_t)n * d.P + 3 * segs) * 8 + segs * 8 +
-                 (size_t)(34 * n + 1) * 4;
+        tables = (size_t)((d.nis + 255) / 256) * std::min(4, d.nsubI) * (d.KBG + d.KBL) * 1024 * 8 +
+                 ((size_t)n * d.P + 3 * segs) * 8 +
+                 segs * 8 + (size_t)(34 * n + 1) * 4;
     }
     const int cap = cfg.slots_per_group;
     size_t mem = kx_al(kx_views_bytes(&d, cap)) + 3 * kx_al(sizeof(double) * cap * n) +

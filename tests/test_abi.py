@@ -55,11 +55,27 @@ def test_strerror_and_error_paths_without_gpu(lib):
     assert lib.kx_collision(None, None, 1, None, None, None, 1, None) == -1
 
 
-def test_struct_layouts_match_header():
+def test_struct_layouts_match_header(tmp_path):
+    """ctypes layouts of the binding against the C compiler's sizeof and
+    offsetof of the header's structs (x86-64)."""
+    import subprocess
     import paper_2607_00755_b300 as kx
-    # sizes follow the C declarations (x86-64 ABI)
-    assert ctypes.sizeof(kx.GridDesc) == 48
-    assert ctypes.sizeof(kx.SolveParams) == 8 * 8 + 4 * 4
-    assert ctypes.sizeof(kx.Diag) == 9 * 8 + 2 * 4
-    assert ctypes.sizeof(kx.Result) == 6 * 8 + 3 * 8 + 2 * 4
-    assert ctypes.sizeof(kx.Source) == 40
+    structs = {"kx_grid_desc": kx.GridDesc, "kx_solve_params": kx.SolveParams, "kx_diag": kx.Diag,
+               "kx_result": kx.Result, "kx_source": kx.Source, "kx_server_config": kx.ServerConfig,
+               "kx_server_stats": kx.ServerStats}
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "kx.h"', "int main(void) {"]
+    for cname, cls in structs.items():
+        lines.append(f'printf("{cname} %zu\\n", sizeof({cname}));')
+        for fname, _ in cls._fields_:
+            lines.append(f'printf("{cname}.{fname} %zu\\n", offsetof({cname}, {fname}));')
+    lines.append("return 0; }")
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), "-o", str(exe), str(src)], check=True)
+    out = dict(line.rsplit(" ", 1) for line in subprocess.run([str(exe)], capture_output=True, text=True,
+                                                               check=True).stdout.splitlines())
+    for cname, cls in structs.items():
+        assert int(out[cname]) == ctypes.sizeof(cls), cname
+        for fname, _ in cls._fields_:
+            assert int(out[f"{cname}.{fname}"]) == getattr(cls, fname).offset, (cname, fname)
