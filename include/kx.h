@@ -243,6 +243,54 @@ int kx_solve_host(kx_ctx *ctx, const kx_kernel *k, int batch, const double *sigm
                   const kx_source *src, int n_src_sets, const kx_solve_params *par,
                   double *f_host, kx_result *res_host);
 
+/* ------------------------------------------------------ expanding universe */
+/* Hubble rate and the two regimes of the integration in u = ln a (Sec. 4,
+ * eq. numerical_evolution_loga; Sec. 4.2).  The paper's H(a) comes from
+ * Standard-Model thermodynamics that it does not list, so it is an input:
+ * H(u) = exp of the piecewise-linear interpolation of ln H through the table
+ * (linear extrapolation beyond it; n_h = 1: constant H; radiation domination
+ * is a two-point table of slope -2). */
+typedef struct {
+    int n_h;               /* points of the table, >= 1 */
+    const double *u;       /* host [n_h], strictly ascending (may be NULL when n_h = 1) */
+    const double *ln_H;    /* host [n_h] */
+    double u0, u_end;      /* integration range in u = ln a */
+    double du_rk4;         /* fixed interval of the source-only RK4 regime, > 0 */
+    int check_every;       /* RK4 steps between checks of Gamma_2->2 / H, >= 1 */
+    double eps_switch;     /* the collisions start once Gamma_2->2 / H > eps_switch (the paper: 1e-2) */
+} kx_expansion;
+
+typedef struct {
+    kx_result r;           /* u reached (r.t), Heun steps, rejects, evaluations, status */
+    double u_switch;       /* u where the collisions started (NaN: never) */
+    double gamma_over_H;   /* Gamma_2->2 / H at the switch, or at the last check */
+    long long rk4_steps;   /* RK4 steps of the source-only regime */
+    long long checks;      /* Gamma_2->2 / H evaluations */
+} kx_expansion_result;
+
+/* One distribution in an expanding universe (Sec. 4): the comoving grid q of
+ * grid (grid->a is ignored; a = e^u), physical momenta p = q/a, and
+ *   df/du = [C_el[f; a] + S(u)] / H(u)             (eq. numerical_evolution_loga)
+ * with the kernel tensor rebuilt at the scale factor of every evaluation (it
+ * depends on a through p = q/a).  Regime 1: the collisions are off and f
+ * advances by classical RK4 on fixed intervals du_rk4 (the right-hand side
+ * S/H does not depend on f); Gamma_2->2 = n <sigma v> -- read as the
+ * number-weighted loss rate of the operator, |M|^2 sum h f nu / sum h f,
+ * nu_i = sum W_inm f_t -- is compared with H at u0 and every check_every RK4
+ * steps.  Regime 2, from the first check with Gamma_2->2 / H > eps_switch:
+ * adaptive Heun in u (the controller of kx_solve_params: h0, rtol, atol,
+ * h_min, h_max, max_attempts; t0, t_end, fixed_step, l1_tol, check_every are
+ * not used) on the projected operator until u_end.  Sources: u is their clock
+ * (t_on in u), shapes normalised with the comoving weights q_i^2 Dq_i, so rate_k
+ * is the comoving number injected per unit time.  One instance per call (every
+ * evaluation needs the kernel at its own a); f_dev is the caller's device
+ * array [n], updated in place.  Precision KX_FP64 or KX_FP32 (dilute
+ * statistics, exact loss); else KX_ENOTSUP.  Synchronises the stream once per
+ * Heun attempt and per check. */
+int kx_solve_expanding(kx_ctx *ctx, const kx_grid_desc *grid, double sigma, const kx_source *src,
+                       const kx_expansion *ex, const kx_solve_params *par, double *f_dev,
+                       kx_expansion_result *res);
+
 /* -------------------------------------------------------------- serving */
 /* A solve server for parameter scans (continuous batching; no counterpart in
  * the paper, which integrates one distribution at a time): requests (grid,

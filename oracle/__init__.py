@@ -9,7 +9,7 @@ contraction); this module only compiles it (``gcc``) and marshals numpy arrays.
 Parity status per function (pins live in ``tests/test_oracle_pins.py``):
   grid, gauss_legendre, nu integrals, F, F_exact, kernel_tensor, bracket,
   collision_tensor, collision_tensor_stats, collision_direct, project, source,
-  mb_fit, solve, bessel_ive, collision_chebyshev: pinned.
+  mb_fit, solve, bessel_ive, collision_chebyshev, solve_expanding: pinned.
 """
 from __future__ import annotations
 
@@ -71,6 +71,7 @@ def _load():
         "oracle_collision_rows": (i, [i, vp, d, d, d, i, i, vp, i, vp, vp, vp, vp]),
         "oracle_bessel_ive": (i, [i, d, vp]),
         "oracle_loss_chebyshev": (i, [i, vp, d, d, vp, vp, i, vp, vp, vp, vp]),
+        "oracle_solve_expanding": (i, [i, vp, d, i, i, i, vp, vp, vp, vp, i, vp, vp, vp, vp, vp]),
         "oracle_num_threads": (i, []),
         "oracle_set_threads": (None, [i]),
     }
@@ -219,6 +220,35 @@ def collision_chebyshev(q, W, f, K, a=1.0, mass=1.0):
     if rc:
         raise ValueError(rc)
     return C, G, L, B
+
+
+def solve_expanding(q, f0, M2, hu, hlnH, u0, u_end, du_rk4=0.05, check_every=1, eps_switch=1e-2,
+                    h0=1e-3, rtol=1e-6, atol=1e-12, h_min=0.0, h_max=np.inf, max_attempts=1_000_000,
+                    sources=None, mass=1.0, n_mu=18, measure=MEASURE_ENERGY):
+    """Expanding universe in u = log a (Sec. 4, eq. numerical_evolution_loga):
+    RK4 on the sources while Gamma/H <= eps_switch, then adaptive Heun with the
+    collisions.  H(u) = exp(piecewise-linear ln H through (hu, hlnH)).  Returns
+    (f, result dict)."""
+    q, f = _f64(q), _f64(f0).copy()
+    n = q.size
+    hu, hl = _f64(np.atleast_1d(hu)), _f64(np.atleast_1d(hlnH))
+    if sources is None:
+        shape = np.zeros((1, n)); rate = tau = u_on = np.zeros(1); ns = 0
+    else:
+        shape = _f64(np.atleast_2d(sources["shape"]))
+        rate, tau, u_on = _f64(sources["rate"]), _f64(sources["tau"]), _f64(sources["t_on"])
+        ns = shape.shape[0]
+    p = _f64([u0, u_end, du_rk4, check_every, eps_switch, h0, rtol, atol, h_min,
+              h_max if np.isfinite(h_max) else 1e300, max_attempts, M2])
+    res = np.empty(10)
+    rc = _load().oracle_solve_expanding(n, _p(q), mass, n_mu, measure, ns, _p(shape), _p(rate),
+                                        _p(tau), _p(u_on), hu.size, _p(hu), _p(hl), _p(p), _p(f),
+                                        _p(res))
+    keys = ("u", "u_switch", "rk4_steps", "steps", "rejects", "evals", "status", "h",
+            "gamma_over_H", "checks")
+    out = dict(zip(keys, res))
+    out["rc"] = rc
+    return f, out
 
 
 def collision_direct(q, f, a=1.0, mass=1.0, M2=1.0, n_mu=18, measure=MEASURE_ENERGY):

@@ -905,3 +905,192 @@ out:
     free(p); free(E); free(dp); free(dE); free(h); free(lf); free(M); free(Y); free(tail); free(iv);
     return rc;
 }
+
+/* --------------------------------------------- expanding universe, u = log a */
+/* Sec. 4 with the scale factor as clock: q is the comoving grid (fixed), the
+ * physical momenta are p_i = q_i / a, a = e^u, and eq. (numerical_evolution_loga)
+ *   df_i/du = [C_el,i[f; a] + C_FI,i(u)] / H(u).
+ * The kernel W depends on a through p = q/a and is rebuilt (eq. discrete_weight
+ * at that a) for every evaluation.  H(u): exp of the piecewise-linear
+ * interpolation of ln H through (hu_k, hlnH_k) (n_h >= 1 points, linear
+ * extrapolation beyond them; n_h = 1: constant H) -- the paper's H(a) comes
+ * from Standard-Model thermodynamics it does not list, so it is an input
+ * (reading).  C_FI (reading): the synthetic sources of the static box with u as
+ * their clock, shapes normalised with the comoving weights q_i^2 Dq_i, so that
+ * rate_k is the comoving number injected per unit time.
+ * Two regimes (Sec. 4.2): while Gamma_2->2 / H <= eps_switch the collisions are
+ * off and f advances by classical RK4 on fixed intervals du (the right-hand
+ * side S(u)/H(u) does not depend on f); Gamma_2->2 = n <sigma v> is read here
+ * as the number-weighted loss rate of the discrete operator,
+ *   Gamma = |M|^2 sum_i h_i f_i nu_i / sum_i h_i f_i,  nu_i = sum_nm W_inm f_t,
+ * checked at u0 and after every check_every RK4 steps.  Once it exceeds
+ * eps_switch H, adaptive Heun in u (the controller of oracle_solve, projected
+ * operator) runs to u_end.
+ * p[12]: u0 u_end du_rk4 check_every eps_switch h0 rtol atol h_min h_max
+ *        max_attempts M2
+ * res[10]: [0] u [1] u_switch (NaN: never) [2] rk4 steps [3] heun steps
+ *          [4] rejects [5] evaluations [6] status [7] h [8] Gamma/H at the switch
+ *          (or at the last check) [9] checks */
+static double oracle_H(int n_h, const double *hu, const double *hl, double u) {
+    if (n_h == 1) return exp(hl[0]);
+    int k = 0;
+    while (k + 2 < n_h && u > hu[k + 1]) ++k;
+    double s = (hl[k + 1] - hl[k]) / (hu[k + 1] - hu[k]);
+    return exp(hl[k] + s * (u - hu[k]));
+}
+
+typedef struct {
+    int n; const double *q; double mass, M2; int n_mu, measure;
+    int n_src; const double *shape, *rate, *tau, *u_on, *hc;
+    int n_h; const double *hu, *hl;
+    double *W, *p, *E, *dp, *dE, *h;
+} exp_ctx;
+
+/* grid and kernel at a = e^u */
+static int exp_at(const exp_ctx *c, double u) {
+    double a = exp(u);
+    int rc = oracle_grid(c->n, c->q, a, c->mass, c->p, c->E, c->dp, c->dE, c->h);
+    if (rc) return rc;
+    return oracle_kernel_tensor(c->n, c->q, a, c->mass, 1.0, c->n_mu, c->measure, 0, c->W);
+}
+
+/* S(u) with comoving-weight normalisation */
+static void exp_source(const exp_ctx *c, double u, double *S) {
+    oracle_source(c->n, c->hc, u, c->n_src, c->shape, c->rate, c->tau, c->u_on, S);
+}
+
+/* RHS(f, u) = (C_proj[f; a(u)] + S(u)) / H(u) */
+static int exp_rhs(const exp_ctx *c, const double *f, double u, double *out, double *work) {
+    int n = c->n;
+    int rc = exp_at(c, u);
+    if (rc) return rc;
+    rc = oracle_collision_tensor(n, c->q, exp(u), c->mass, c->W, f, work, NULL, NULL);
+    if (rc) return rc;
+    for (int i = 0; i < n; ++i) work[i] *= c->M2;
+    rc = oracle_project(n, c->E, c->h, f, work, out, NULL);
+    if (rc == OR_ESINGULAR) rc = OR_OK;
+    if (rc) return rc;
+    double *S = work + n;
+    exp_source(c, u, S);
+    double inv = 1.0 / oracle_H(c->n_h, c->hu, c->hl, u);
+    for (int i = 0; i < n; ++i) out[i] = (out[i] + S[i]) * inv;
+    return OR_OK;
+}
+
+/* Gamma_2->2 / H at u */
+static int exp_gamma_over_H(const exp_ctx *c, const double *f, double u, double *g, double *work) {
+    int n = c->n;
+    int rc = exp_at(c, u);
+    if (rc) return rc;
+    double *L = work;
+    rc = oracle_collision_tensor(n, c->q, exp(u), c->mass, c->W, f, work + n, work + 2 * n, L);
+    if (rc) return rc;
+    double num = 0.0, den = 0.0;
+    for (int i = 0; i < n; ++i) {
+        num += c->h[i] * f[i] * L[i];
+        den += c->h[i] * f[i];
+    }
+    *g = den > 0.0 ? c->M2 * num / den / oracle_H(c->n_h, c->hu, c->hl, u) : 0.0;
+    return OR_OK;
+}
+
+int oracle_solve_expanding(int n, const double *q, double mass, int n_mu, int measure,
+                           int n_src, const double *shape, const double *rate, const double *tau,
+                           const double *u_on, int n_h, const double *hu, const double *hlnH,
+                           const double *p, double *f, double *res) {
+    if (n < 4 || n_h < 1) return OR_EINVAL;
+    double *buf = malloc(sizeof(double) * ((size_t)n * n * n + 16 * (size_t)n));
+    if (!buf) return OR_ENOMEM;
+    double *W = buf, *v = buf + (size_t)n * n * n;
+    double *pp = v, *E = v + n, *dp = v + 2 * n, *dE = v + 3 * n, *h = v + 4 * n, *hc = v + 5 * n;
+    double *k1 = v + 6 * n, *k2 = v + 7 * n, *fp = v + 8 * n, *fc = v + 9 * n, *work = v + 10 * n;
+    double *k3 = v + 13 * n, *k4 = v + 14 * n;
+    int rc = oracle_grid(n, q, 1.0, mass, pp, E, dp, dE, hc);   /* comoving weights q^2 Dq */
+    if (rc) { free(buf); return rc; }
+    exp_ctx c = { n, q, mass, p[11], n_mu, measure, n_src, shape, rate, tau, u_on, hc, n_h, hu, hlnH,
+                  W, pp, E, dp, dE, h };
+    double u = p[0], u_end = p[1], du = p[2], eps = p[4];
+    int check_every = (int)p[3];
+    double hs = p[5], rtol = p[6], atol = p[7], h_min = p[8], h_max = p[9];
+    long max_att = (long)p[10];
+    long rk4 = 0, steps = 0, rejects = 0, evals = 0, checks = 0;
+    double u_switch = NAN, gh = 0.0;
+    int status = OR_OK, switched = 0;
+    /* regime 1: sources only, RK4 on fixed intervals, Gamma/H checks */
+    rc = exp_gamma_over_H(&c, f, u, &gh, work);
+    if (rc) { free(buf); return rc; }
+    checks++;
+    if (gh > eps) { switched = 1; u_switch = u; }
+    while (!switched && u < u_end) {
+        /* step k spans [u0 + k du, u0 + (k+1) du], the last one clipped at u_end */
+        double d = du;
+        u = p[0] + (double)rk4 * du;
+        if (u + d >= u_end) d = u_end - u;
+        double u1 = u + 0.5 * d, u2 = u + d;
+        double i0 = 1.0 / oracle_H(n_h, hu, hlnH, u), i1 = 1.0 / oracle_H(n_h, hu, hlnH, u1);
+        double i2 = 1.0 / oracle_H(n_h, hu, hlnH, u2);
+        exp_source(&c, u, k1);
+        exp_source(&c, u1, k2);
+        exp_source(&c, u1, k3);
+        exp_source(&c, u2, k4);
+        for (int i = 0; i < n; ++i)
+            f[i] = f[i] + d / 6.0 * (((k1[i] * i0 + 2.0 * (k2[i] * i1)) + 2.0 * (k3[i] * i1)) + k4[i] * i2);
+        u = (u + d >= u_end) ? u_end : u + d;
+        rk4++;
+        if (check_every > 0 && rk4 % check_every == 0) {
+            rc = exp_gamma_over_H(&c, f, u, &gh, work);
+            if (rc) { free(buf); return rc; }
+            checks++;
+            if (gh > eps) { switched = 1; u_switch = u; }
+        }
+    }
+    /* regime 2: adaptive Heun in u with collisions (controller of oracle_solve) */
+    while (switched && u < u_end) {
+        if (steps + rejects >= max_att) { status = OR_ENOCONV; break; }
+        double htry = hs;
+        if (htry > h_max) htry = h_max;
+        if (htry < h_min) htry = h_min;
+        int last = 0;
+        if (u + htry >= u_end) { htry = u_end - u; last = 1; }
+        rc = exp_rhs(&c, f, u, k1, work);
+        if (rc) { status = rc; break; }
+        evals++;
+        int neg = 0;
+        for (int i = 0; i < n; ++i) {
+            fp[i] = f[i] + htry * k1[i];
+            if (!isfinite(fp[i])) { status = OR_ENONFINITE; break; }
+            if (fp[i] < 0.0) neg = 1;
+        }
+        if (status) break;
+        if (neg) { hs = 0.5 * htry; rejects++; continue; }
+        rc = exp_rhs(&c, fp, u + htry, k2, work);
+        if (rc) { status = rc; break; }
+        evals++;
+        double err = 0.0;
+        for (int i = 0; i < n; ++i) {
+            fc[i] = f[i] + 0.5 * htry * (k1[i] + k2[i]);
+            if (!isfinite(fc[i])) { status = OR_ENONFINITE; break; }
+            if (fc[i] < 0.0) neg = 1;
+            double e = fabs(fc[i] - fp[i]) / (atol + rtol * fabs(fc[i]));
+            if (e > err) err = e;
+        }
+        if (status) break;
+        if (neg) { hs = 0.5 * htry; rejects++; continue; }
+        double fac = err > 0.0 ? 0.9 / sqrt(err) : 5.0;
+        if (fac > 5.0) fac = 5.0;
+        if (fac < 0.2) fac = 0.2;
+        if (err <= 1.0) {
+            for (int i = 0; i < n; ++i) f[i] = fc[i];
+            u = last ? u_end : u + htry;
+            steps++;
+        } else {
+            rejects++;
+        }
+        hs = htry * fac;
+    }
+    res[0] = u; res[1] = u_switch; res[2] = (double)rk4; res[3] = (double)steps;
+    res[4] = (double)rejects; res[5] = (double)evals; res[6] = status; res[7] = hs; res[8] = gh;
+    res[9] = (double)checks;
+    free(buf);
+    return status;
+}

@@ -29,7 +29,7 @@ EXPORTS = (
     "kx_time_contractions", "kx_time_collision",
     "kx_collision_noalloc", "kx_server_start", "kx_submit", "kx_poll", "kx_server_get_stats",
     "kx_server_stop", "kx_math_check", "kx_wait_check", "kx_set_stream_variant", "kx_get_stream_variant",
-    "kx_source_higgs_decay", "kx_source_condensate",
+    "kx_source_higgs_decay", "kx_source_condensate", "kx_solve_expanding",
 )
 
 
@@ -72,11 +72,28 @@ class Result(ctypes.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
+class ExpansionResult(ctypes.Structure):
+    _fields_ = [("r", Result), ("u_switch", ctypes.c_double), ("gamma_over_H", ctypes.c_double),
+                ("rk4_steps", ctypes.c_longlong), ("checks", ctypes.c_longlong)]
+
+    def as_dict(self):
+        d = self.r.as_dict()
+        d.update(u=self.r.t, u_switch=self.u_switch, gamma_over_H=self.gamma_over_H,
+                 rk4_steps=self.rk4_steps, checks=self.checks)
+        return d
+
+
 class KernelInfo(ctypes.Structure):
     _fields_ = [("n", ctypes.c_int), ("n_mu", ctypes.c_int), ("measure", ctypes.c_int),
                 ("precision", ctypes.c_int), ("unique_elements", ctypes.c_longlong),
                 ("nonzero_elements", ctypes.c_longlong), ("tensor_bytes", ctypes.c_longlong),
                 ("build_ms", ctypes.c_double), ("stream_bytes", ctypes.c_longlong)]
+
+
+class Expansion(ctypes.Structure):
+    _fields_ = [("n_h", ctypes.c_int), ("u", ctypes.c_void_p), ("ln_H", ctypes.c_void_p),
+                ("u0", ctypes.c_double), ("u_end", ctypes.c_double), ("du_rk4", ctypes.c_double),
+                ("check_every", ctypes.c_int), ("eps_switch", ctypes.c_double)]
 
 
 class ServerConfig(ctypes.Structure):
@@ -135,6 +152,8 @@ def load_library(path: str = LIB_PATH):
         "kx_get_stream_variant": (i, [vp, i, i, vp, vp]),
         "kx_source_higgs_decay": (i, [i, vp, d, d, d, d, d, d, vp, vp]),
         "kx_source_condensate": (i, [i, vp, d, d, d, d, d, vp, vp]),
+        "kx_solve_expanding": (i, [vp, ctypes.POINTER(GridDesc), d, vp, ctypes.POINTER(Expansion),
+                                   ctypes.POINTER(SolveParams), vp, ctypes.POINTER(ExpansionResult)]),
         "kx_launch_count": (ctypes.c_longlong, [vp]),
         "kx_time_contraction": (i, [vp, vp, i, vp, i, ctypes.c_longlong, vp]),
         "kx_time_contractions": (i, [vp, i, vp, i, vp, i, i, vp]),
@@ -314,6 +333,26 @@ class Context:
         if rc in (EINVAL, ENOMEM, ECUDA, ETIMEOUT, ENOTSUP):
             raise self.error(rc, "kx_step")
         return [r.as_dict() for r in res]
+
+    def solve_expanding(self, q, f, sigma, hu, ln_H, u0, u_end, du_rk4=0.05, check_every=1,
+                        eps_switch=1e-2, sources=None, precision=FP64, mass=1.0, n_mu=18,
+                        measure=MEASURE_ENERGY, **params):
+        """One distribution in an expanding universe (kx_solve_expanding): f is
+        a CUDA float64 tensor [n] on the comoving grid q, updated in place."""
+        q = _np(q)
+        hu_a, hl_a = _np(np.atleast_1d(hu)), _np(np.atleast_1d(ln_H))
+        desc = GridDesc(q.size, q.ctypes.data, 1.0, mass, n_mu, measure, 0, precision, 0)
+        ex = Expansion(hl_a.size, hu_a.ctypes.data, hl_a.ctypes.data, float(u0), float(u_end),
+                       float(du_rk4), int(check_every), float(eps_switch))
+        src, ns, keep = self._sources(sources, 1, q.size)
+        par = self.params(**params)
+        res = ExpansionResult()
+        rc = self.lib.kx_solve_expanding(self.h, ctypes.byref(desc), float(sigma), src, ctypes.byref(ex),
+                                         ctypes.byref(par), _dptr(f), ctypes.byref(res))
+        del keep
+        if rc in (EINVAL, ENOMEM, ECUDA, ETIMEOUT, ENOTSUP):
+            raise self.error(rc, "kx_solve_expanding")
+        return res.as_dict()
 
     def launch_count(self) -> int:
         return int(self.lib.kx_launch_count(self.h))

@@ -261,7 +261,7 @@ static void kx_free_kernel(kx_kernel *k) {
     void *ptrs[] = {k->d_p, k->d_E, k->d_dp, k->d_dE, k->d_h, k->d_pair, k->d_W64,
                     k->d_om64, k->d_jl, k->d_vt, k->d_W32, k->d_pk, k->d_roff, k->d_rtask,
                     k->d_task, k->d_bins, k->d_Sg, k->d_lel, k->d_lseg, k->d_lsw,
-                    k->d_lorder, k->d_Mtile};
+                    k->d_lorder, k->d_Mtile, k->d_vt_all, k->d_pos};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     delete k;
@@ -280,7 +280,32 @@ static int kx_dev_alloc(kx_ctx *ctx, T **p, size_t count, long long *bytes) {
     return KX_OK;
 }
 
+// Grid of Appendix A at scale factor a (host, FP64, no FMA): p = q/a,
+// E = sqrt(p^2 + m^2), trapezoid widths Dq, Dp = Dq/a, dE = p Dp/E, h = p^2 Dp.
+static void kx_grid_host(kx_kernel *k, const double *q, double a, double mass) {
+    const int n = k->n;
+    k->p.resize(n); k->E.resize(n); k->dp.resize(n); k->dE.resize(n); k->h.resize(n);
+    for (int i = 0; i < n; ++i) {
+        double dq;
+        if (i == 0) dq = (q[1] - q[0]) / 2.0;
+        else if (i == n - 1) dq = (q[n - 1] - q[n - 2]) / 2.0;
+        else dq = (q[i + 1] - q[i - 1]) / 2.0;
+        k->p[i] = q[i] / a;
+        k->E[i] = sqrt(k->p[i] * k->p[i] + mass * mass);
+        k->dp[i] = dq / a;
+        k->dE[i] = k->p[i] * k->dp[i] / k->E[i];
+        k->h[i] = k->p[i] * k->p[i] * k->dp[i];
+    }
+}
+
+static int kx_build_kernel_ex(kx_ctx *ctx, const kx_grid_desc *d, kx_kernel **out, bool rescalable);
+
 extern "C" int kx_build_kernel(kx_ctx *ctx, const kx_grid_desc *d, kx_kernel **out) {
+    return kx_build_kernel_ex(ctx, d, out, false);
+}
+
+// rescalable: a kernel rebuilt in place at other scale factors (kx_kernel_rescale)
+static int kx_build_kernel_ex(kx_ctx *ctx, const kx_grid_desc *d, kx_kernel **out, bool rescalable) {
     kx_nvtx range_("kx_build_kernel");
     if (!ctx || !d || !out) return KX_EINVAL;
     *out = nullptr;
@@ -321,20 +346,10 @@ extern "C" int kx_build_kernel(kx_ctx *ctx, const kx_grid_desc *d, kx_kernel **o
     k->mass = d->mass;
     k->P = (long long)n * (n + 1) / 2;
     k->bytes = 0;
+    k->rescalable = rescalable;
     // grid (Appendix A; trapezoid widths in q)
     k->q.assign(d->q, d->q + n);
-    k->p.resize(n); k->E.resize(n); k->dp.resize(n); k->dE.resize(n); k->h.resize(n);
-    for (int i = 0; i < n; ++i) {
-        double dq;
-        if (i == 0) dq = (d->q[1] - d->q[0]) / 2.0;
-        else if (i == n - 1) dq = (d->q[n - 1] - d->q[n - 2]) / 2.0;
-        else dq = (d->q[i + 1] - d->q[i - 1]) / 2.0;
-        k->p[i] = d->q[i] / d->a;
-        k->E[i] = sqrt(k->p[i] * k->p[i] + d->mass * d->mass);
-        k->dp[i] = dq / d->a;
-        k->dE[i] = k->p[i] * k->dp[i] / k->E[i];
-        k->h[i] = k->p[i] * k->p[i] * k->dp[i];
-    }
+    kx_grid_host(k, d->q, d->a, d->mass);
     std::vector<uint32_t> pair;
     pair.reserve(k->P);
     for (int a = 0; a < n; ++a)
@@ -395,7 +410,7 @@ extern "C" int kx_build_kernel(kx_ctx *ctx, const kx_grid_desc *d, kx_kernel **o
     KX_CHK("upload pairs", cudaMemcpyAsync(k->d_pair, pair.data(), sizeof(uint32_t) * k->P, cudaMemcpyHostToDevice, s));
     if (d_vt_all)
         KX_CHK("upload vectors", cudaMemcpyAsync(d_vt_all, vt.data(), sizeof(uint32_t) * k->V, cudaMemcpyHostToDevice, s));
-    kx_gl_nodes gl;
+    kx_gl_nodes &gl = k->gl;
     memset(&gl, 0, sizeof(gl));
     if (k->n_mu > 0) kx_gauss_legendre(k->n_mu, &gl);
     KX_CHK("event", cudaEventCreate(&e0));
@@ -406,7 +421,7 @@ extern "C" int kx_build_kernel(kx_ctx *ctx, const kx_grid_desc *d, kx_kernel **o
     KX_CHK("build", kx_launch_build_fp64(k, gl, s));
     if (k->precision == KX_FP32) {
         // rows compacted to the vectors inside the kinematic support
-        KX_CHK("support", kx_launch_keep_scan(k, d_vt_all, k->V, d_pos, d_rcnt, s));
+        KX_CHK("support", kx_launch_keep_scan(k, d_vt_all, k->V, d_pos, d_rcnt, s, rescalable));
         std::vector<int> rcnt(n);
         KX_CHK("copy", cudaMemcpyAsync(rcnt.data(), d_rcnt, sizeof(int) * n, cudaMemcpyDeviceToHost, s));
         KX_CHK("sync", cudaStreamSynchronize(s));
@@ -491,8 +506,13 @@ extern "C" int kx_build_kernel(kx_ctx *ctx, const kx_grid_desc *d, kx_kernel **o
     k->build_ms = ms;
     k->nnz = (long long)cnt;
     cudaFree(d_cnt);
-    cudaFree(d_vt_all);
-    cudaFree(d_pos);
+    if (rescalable) {   // kept for the rebuilds at other scale factors
+        k->d_vt_all = d_vt_all;
+        k->d_pos = d_pos;
+    } else {
+        cudaFree(d_vt_all);
+        cudaFree(d_pos);
+    }
     cudaFree(d_rcnt);
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
@@ -512,7 +532,7 @@ extern "C" int kx_build_kernel(kx_ctx *ctx, const kx_grid_desc *d, kx_kernel **o
         k->stream_bytes = (long long)((k->nis + 255) / 256) * std::min(4, k->nsubI) * 1024 * 8 *
                               (k->KBG + (k->cheb_K ? k->KBL : 0)) +
                           (k->cheb_K ? 0 : k->nlel * 8 + k->nseg * 8);
-    if (k->precision != KX_FP64) {
+    if (k->precision != KX_FP64 && !rescalable) {
         // the FP32 and batched paths read only their own tables
         cudaFree(k->d_W64); k->d_W64 = nullptr;
         cudaFree(k->d_om64); k->d_om64 = nullptr;
@@ -680,8 +700,11 @@ static int kx_check_params(kx_ctx *ctx, const kx_solve_params *p) {
 }
 
 // Normalised source shapes and per-instance source descriptors.
+// hw: the weights that normalise the shapes (sum_j hw_j shape_j = 1); the
+// kernel's h when null (the expanding universe passes the comoving q^2 Dq).
 static int kx_sources_host(kx_ctx *ctx, const kx_kernel *k, int B, const kx_source *src, int nsets,
-                           std::vector<kx_src_dev> &sd, std::vector<double> &shapes) {
+                           std::vector<kx_src_dev> &sd, std::vector<double> &shapes,
+                           const double *hw = nullptr) {
     sd.assign(B, kx_src_dev());
     shapes.clear();
     const int n = k->n;
@@ -700,7 +723,7 @@ static int kx_sources_host(kx_ctx *ctx, const kx_kernel *k, int B, const kx_sour
             for (int j = 0; j < n; ++j) {
                 double v = S.shape[(size_t)r * n + j];
                 if (!(v >= 0) || !isfinite(v)) return kx_set_error(ctx, KX_EINVAL, "source shape must be >= 0");
-                norm += k->h[j] * v;
+                norm += (hw ? hw[j] : k->h[j]) * v;
             }
             if (!(norm > 0) || !(S.tau[r] > 0))
                 return kx_set_error(ctx, KX_EINVAL, "source shape must have positive weight, tau > 0");
@@ -735,10 +758,10 @@ struct kx_run {
 static int kx_setup_run(kx_ctx *ctx, const kx_kernel *k, int B, const double *sigma,
                         const kx_source *src, int nsets, const kx_solve_params *par,
                         const double *t0, const double *h0, double *f_dev, bool own_f,
-                        kx_run *run, double **f_used) {
+                        kx_run *run, double **f_used, const double *src_weights = nullptr) {
     std::vector<kx_src_dev> sd;
     std::vector<double> shapes;
-    int rc = kx_sources_host(ctx, k, B, src, nsets, sd, shapes);
+    int rc = kx_sources_host(ctx, k, B, src, nsets, sd, shapes, src_weights);
     if (rc) return rc;
     kx_solve_layout L = kx_layout_solve(k, B, (int)(shapes.size() / k->n) + 1, own_f);
     if ((rc = kx_arena_reserve(ctx, L.total)) != KX_OK) return rc;
@@ -760,6 +783,7 @@ static int kx_setup_run(kx_ctx *ctx, const kx_kernel *k, int B, const double *si
     sv.fixed = par->fixed_step;
     sv.check_every = par->check_every;
     sv.project = par->project;
+    sv.hscale = 1.0;
     run->mb = (double *)(base + L.mb);
     *f_used = sv.f;
     std::vector<kx_inst_state> st(B);
@@ -967,6 +991,185 @@ extern "C" int kx_solve_host(kx_ctx *ctx, const kx_kernel *k, int B, const doubl
     KX_CUDA_TRY(ctx, cudaMemcpyAsync(f_host, f, sizeof(double) * B * k->n, cudaMemcpyDeviceToHost, s));
     KX_CUDA_TRY(ctx, cudaStreamSynchronize(s));
     return rc2;
+}
+
+// ------------------------------------------------------ expanding universe
+// Rebuilds a rescalable kernel in place at scale factor a (stream ordered):
+// host grid, upload, FP64 tables, and for the FP32 path the uncompacted FP32
+// tables (every vector kept, so the layout does not depend on the support).
+static int kx_kernel_rescale(kx_ctx *ctx, kx_kernel *k, double a) {
+    cudaStream_t s = ctx->stream;
+    const int n = k->n;
+    kx_grid_host(k, k->q.data(), a, k->mass);
+    k->a = a;
+    KX_CUDA_TRY(ctx, cudaMemcpyAsync(k->d_p, k->p.data(), sizeof(double) * n, cudaMemcpyHostToDevice, s));
+    KX_CUDA_TRY(ctx, cudaMemcpyAsync(k->d_E, k->E.data(), sizeof(double) * n, cudaMemcpyHostToDevice, s));
+    KX_CUDA_TRY(ctx, cudaMemcpyAsync(k->d_dp, k->dp.data(), sizeof(double) * n, cudaMemcpyHostToDevice, s));
+    KX_CUDA_TRY(ctx, cudaMemcpyAsync(k->d_dE, k->dE.data(), sizeof(double) * n, cudaMemcpyHostToDevice, s));
+    KX_CUDA_TRY(ctx, cudaMemcpyAsync(k->d_h, k->h.data(), sizeof(double) * n, cudaMemcpyHostToDevice, s));
+    KX_CUDA_TRY(ctx, kx_launch_build_fp64(k, k->gl, s));
+    ctx->launches += 1;
+    if (k->precision == KX_FP32) {
+        KX_CUDA_TRY(ctx, kx_launch_pack_fp32(k, k->d_vt_all, k->V, k->d_pos, s));
+        ctx->launches += 1;
+    }
+    return KX_OK;
+}
+
+// H(u) = exp of the piecewise-linear interpolation of ln H (linear
+// extrapolation beyond the table; constant for a single point)
+static double kx_hubble(const kx_expansion *ex, double u) {
+    if (ex->n_h == 1) return exp(ex->ln_H[0]);
+    int k = 0;
+    while (k + 2 < ex->n_h && u > ex->u[k + 1]) ++k;
+    const double sl = (ex->ln_H[k + 1] - ex->ln_H[k]) / (ex->u[k + 1] - ex->u[k]);
+    return exp(ex->ln_H[k] + sl * (u - ex->u[k]));
+}
+
+extern "C" int kx_solve_expanding(kx_ctx *ctx, const kx_grid_desc *grid, double sigma, const kx_source *src,
+                                  const kx_expansion *ex, const kx_solve_params *par, double *f_dev,
+                                  kx_expansion_result *res) {
+    kx_nvtx range_("kx_solve_expanding");
+    if (!ctx || !grid || !ex || !f_dev) return kx_set_error(ctx, KX_EINVAL, "null argument");
+    int rc = kx_check_params(ctx, par);
+    if (rc) return rc;
+    if (grid->precision != KX_FP64 && grid->precision != KX_FP32)
+        return kx_set_error(ctx, KX_ENOTSUP, "expanding universe: FP64 and FP32 paths");
+    if (grid->stats != 0 || grid->loss_terms != 0)
+        return kx_set_error(ctx, KX_ENOTSUP, "expanding universe: dilute statistics, exact loss");
+    if (ex->n_h < 1 || !ex->ln_H || (ex->n_h > 1 && !ex->u) || !(ex->du_rk4 > 0) || ex->check_every < 1 ||
+        !(ex->eps_switch >= 0) || !(ex->u_end >= ex->u0) || !isfinite(ex->u0) || !isfinite(ex->u_end))
+        return kx_set_error(ctx, KX_EINVAL, "bad expansion description");
+    for (int j = 0; j < ex->n_h; ++j) {
+        if (!isfinite(ex->ln_H[j])) return kx_set_error(ctx, KX_EINVAL, "ln H must be finite");
+        if (j && !(ex->u[j] > ex->u[j - 1])) return kx_set_error(ctx, KX_EINVAL, "u table must ascend");
+    }
+    if (!(sigma > 0) || !isfinite(sigma)) return kx_set_error(ctx, KX_EINVAL, "sigma must be finite and > 0");
+    KX_CUDA_TRY(ctx, cudaSetDevice(ctx->device));
+    kx_grid_desc d = *grid;
+    d.a = exp(ex->u0);
+    kx_kernel *k = nullptr;
+    if ((rc = kx_build_kernel_ex(ctx, &d, &k, true)) != KX_OK) return rc;
+    struct Guard {
+        kx_kernel *k;
+        double *nu;
+        ~Guard() {
+            if (nu) cudaFree(nu);
+            kx_kernel_release(k);
+        }
+    } guard{k, nullptr};
+    const int n = k->n;
+    // comoving weights q^2 Dq (the h of a = 1) normalise the source shapes
+    std::vector<double> hc(n);
+    for (int i = 0; i < n; ++i) {
+        const double dq = i == 0 ? (grid->q[1] - grid->q[0]) / 2.0
+                                 : (i == n - 1 ? (grid->q[n - 1] - grid->q[n - 2]) / 2.0
+                                               : (grid->q[i + 1] - grid->q[i - 1]) / 2.0);
+        hc[i] = grid->q[i] * grid->q[i] * dq;
+    }
+    kx_solve_params pp = *par;
+    pp.t0 = ex->u0;
+    pp.t_end = ex->u_end;
+    pp.fixed_step = 0;
+    pp.l1_tol = 0.0;
+    pp.check_every = 0;
+    pp.project = 1;
+    kx_run r;
+    double *f = nullptr;
+    if ((rc = kx_setup_run(ctx, k, 1, &sigma, src, src ? 1 : 0, &pp, nullptr, nullptr, f_dev, false, &r, &f,
+                           hc.data())))
+        return rc;
+    if (cudaMalloc(&guard.nu, sizeof(double) * n) != cudaSuccess) {
+        cudaGetLastError();
+        return kx_set_error(ctx, KX_ENOMEM, "expanding universe: scratch allocation failed");
+    }
+    cudaStream_t s = ctx->stream;
+    const double M2 = kx_M2(k->mass, sigma);
+    std::vector<double> nu(n), fh(n);
+    long long rk4 = 0, checks = 0;
+    double gh = 0.0, u_switch = NAN;
+    // Gamma_2->2 / H at u: the number-weighted loss rate of the operator at a(u)
+    auto gamma_over_H = [&](double u, bool *over) -> int {
+        int e = kx_kernel_rescale(ctx, k, exp(u));
+        if (e) return e;
+        KX_CUDA_TRY(ctx, kx_launch_loss_rate64(k, f, guard.nu, s));
+        ctx->launches += 1;
+        KX_CUDA_TRY(ctx, cudaMemcpyAsync(nu.data(), guard.nu, sizeof(double) * n, cudaMemcpyDeviceToHost, s));
+        KX_CUDA_TRY(ctx, cudaMemcpyAsync(fh.data(), f, sizeof(double) * n, cudaMemcpyDeviceToHost, s));
+        KX_CUDA_TRY(ctx, cudaStreamSynchronize(s));
+        double num = 0.0, den = 0.0;
+        for (int i = 0; i < n; ++i) {
+            num += k->h[i] * fh[i] * nu[i];
+            den += k->h[i] * fh[i];
+        }
+        gh = den > 0.0 ? M2 * num / den / kx_hubble(ex, u) : 0.0;
+        ++checks;
+        *over = gh > ex->eps_switch;
+        return KX_OK;
+    };
+    // regime 1: the sources alone, RK4 on fixed intervals of u
+    double u = ex->u0;
+    bool sw = false;
+    if ((rc = gamma_over_H(u, &sw))) return rc;
+    if (sw) u_switch = u;
+    while (!sw && u < ex->u_end) {
+        // step k spans [u0 + k du, u0 + (k + 1) du], the last one clipped at u_end
+        double dd = ex->du_rk4;
+        u = ex->u0 + (double)rk4 * ex->du_rk4;
+        if (u + dd >= ex->u_end) dd = ex->u_end - u;
+        const double u1 = u + 0.5 * dd, u2 = u + dd;
+        KX_CUDA_TRY(ctx, kx_launch_rk4_sources(k, f, r.sv.src, r.sv.shapes, u, dd, 1.0 / kx_hubble(ex, u),
+                                               1.0 / kx_hubble(ex, u1), 1.0 / kx_hubble(ex, u2), s));
+        ctx->launches += 1;
+        u = (u + dd >= ex->u_end) ? ex->u_end : u + dd;
+        ++rk4;
+        if (rk4 % ex->check_every == 0) {
+            if ((rc = gamma_over_H(u, &sw))) return rc;
+            if (sw) u_switch = u;
+        }
+    }
+    // regime 2: adaptive Heun in u with the collisions, the kernel rebuilt at
+    // the scale factor of each evaluation
+    kx_inst_state st;
+    KX_CUDA_TRY(ctx, cudaMemcpyAsync(&st, r.sv.st, sizeof(st), cudaMemcpyDeviceToHost, s));
+    KX_CUDA_TRY(ctx, cudaStreamSynchronize(s));
+    st.t = u;
+    st.done = !(sw && u < ex->u_end);
+    KX_CUDA_TRY(ctx, cudaMemcpyAsync(r.sv.st, &st, sizeof(st), cudaMemcpyHostToDevice, s));
+    const double h_max = par->h_max > 0 ? par->h_max : INFINITY;
+    const auto t_start = std::chrono::steady_clock::now();
+    while (!st.done) {
+        double htry = st.h;
+        if (htry > h_max) htry = h_max;
+        if (htry < par->h_min) htry = par->h_min;
+        if (st.t + htry >= st.t_end) htry = st.t_end - st.t;
+        const double u1 = st.t, u2 = st.t + htry;
+        for (int stage = 1; stage <= 2; ++stage) {
+            const double us = stage == 1 ? u1 : u2;
+            if ((rc = kx_kernel_rescale(ctx, k, exp(us)))) return rc;
+            double *fin = stage == 1 ? r.sv.f : r.sv.fp;
+            KX_CUDA_TRY(ctx, kx_launch_prep(k, 1, fin, r.v, r.sv.st, s));
+            KX_CUDA_TRY(ctx, kx_launch_contract(k, 1, fin, r.v, r.sv.st, stage, s));
+            r.sv.hscale = 1.0 / kx_hubble(ex, us);
+            KX_CUDA_TRY(ctx, kx_launch_stage(k, 1, r.v, r.sv, stage, s));
+            ctx->launches += 3;
+        }
+        KX_CUDA_TRY(ctx, cudaMemcpyAsync(&st, r.sv.st, sizeof(st), cudaMemcpyDeviceToHost, s));
+        KX_CUDA_TRY(ctx, cudaStreamSynchronize(s));
+        if (std::chrono::duration<double>(std::chrono::steady_clock::now() - t_start).count() > 3600.0)
+            return kx_set_error(ctx, KX_ETIMEOUT, "expanding universe: wall-clock limit");
+    }
+    kx_result out;
+    int worst = kx_collect(ctx, k, 1, r, &out, nullptr, nullptr, 0.0);
+    if (res) {
+        res->r = out;
+        res->r.t = st.t > u ? st.t : u;
+        res->u_switch = u_switch;
+        res->gamma_over_H = gh;
+        res->rk4_steps = rk4;
+        res->checks = checks;
+    }
+    return worst;
 }
 
 extern "C" int kx_mb_fit(kx_ctx *ctx, const kx_kernel *k, int B, const double *f_dev, double *out) {

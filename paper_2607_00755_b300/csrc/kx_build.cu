@@ -120,9 +120,11 @@ cudaError_t kx_launch_build_fp64(const kx_kernel *k, const kx_gl_nodes &gl, cuda
 // list, one block per row i: pos[i][v] = index of vector v among row i's
 // vectors with an element inside the support (W != 0), or -1; cnt[i] = their
 // number.  Block-wide exclusive scan in tiles of blockDim vectors.
+// keep_all: every vector kept (pos[i][v] = v), for kernels rebuilt at other
+// scale factors, whose layout must not depend on the support.
 __global__ void k_keep_scan(int N, long long P, int V, const uint32_t *__restrict__ vt,
                             const double *__restrict__ W64, int *__restrict__ pos,
-                            int *__restrict__ cnt) {
+                            int *__restrict__ cnt, int keep_all) {
     __shared__ int s_warp[32];
     __shared__ int s_base;
     const int i = blockIdx.x, tid = threadIdx.x, lane = tid & 31, w = tid >> 5, nw = blockDim.x >> 5;
@@ -131,7 +133,8 @@ __global__ void k_keep_scan(int N, long long P, int V, const uint32_t *__restric
     for (int v0 = 0; v0 < V; v0 += blockDim.x) {
         const int v = v0 + tid;
         int keep = 0;
-        if (v < V) {
+        if (v < V && keep_all) keep = 1;
+        else if (v < V) {
             const uint32_t t = vt[v];
             const int n = t & 0xffff, m0 = t >> 16;
             const long long base = (long long)i * P + kx_pair_base(n, N);
@@ -163,8 +166,8 @@ __global__ void k_keep_scan(int N, long long P, int V, const uint32_t *__restric
 }
 
 cudaError_t kx_launch_keep_scan(const kx_kernel *k, const uint32_t *d_vt_all, int V, int *d_pos,
-                                int *d_cnt, cudaStream_t s) {
-    k_keep_scan<<<k->n, 1024, 0, s>>>(k->n, k->P, V, d_vt_all, k->d_W64, d_pos, d_cnt);
+                                int *d_cnt, cudaStream_t s, bool keep_all) {
+    k_keep_scan<<<k->n, 1024, 0, s>>>(k->n, k->P, V, d_vt_all, k->d_W64, d_pos, d_cnt, keep_all ? 1 : 0);
     return cudaGetLastError();
 }
 

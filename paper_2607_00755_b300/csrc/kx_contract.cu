@@ -1637,6 +1637,75 @@ cudaError_t kx_launch_finalize(const kx_kernel *k, int B, const double *f, const
     return cudaGetLastError();
 }
 
+// ------------------------------------------------------ expanding universe
+// One RK4 step of df/du = S(u)/H(u) for one instance (the collisions are off
+// in this regime; the right-hand side does not depend on f):
+//   f_i += d/6 (k1_i i0 + 2 k2_i i1 + 2 k3_i i1 + k4_i i2),
+// k1 = S(u), k2 = k3 = S(u + d/2), k4 = S(u + d), i = 1/H at those points, S
+// from the normalised source shapes and the envelopes rate_k exp(-(u - u_on,k)/tau_k).
+__global__ void k_rk4_sources(int n, double *__restrict__ f, const kx_src_dev *__restrict__ src,
+                              const double *__restrict__ shapes, double u, double d, double i0, double i1,
+                              double i2) {
+    const int i = threadIdx.x;
+    __shared__ double s_env[3][KX_MAX_SRC];
+    const kx_src_dev &sd = src[0];
+    if (i < 3 * KX_MAX_SRC) {
+        const int c = i / KX_MAX_SRC, k = i % KX_MAX_SRC;
+        const double uu = c == 0 ? u : (c == 1 ? u + 0.5 * d : u + d);
+        double e = 0.0;
+        if (k < sd.n_src && uu >= sd.t_on[k]) e = sd.rate[k] * kx_exp(-(uu - sd.t_on[k]) / sd.tau[k]);
+        s_env[c][k] = e;
+    }
+    __syncthreads();
+    if (i >= n) return;
+    double k1 = 0.0, k2 = 0.0, k4 = 0.0;
+    for (int k = 0; k < sd.n_src; ++k) {
+        const double sh = shapes[sd.shape_off + (long long)k * n + i];
+        k1 += s_env[0][k] * sh;
+        k2 += s_env[1][k] * sh;
+        k4 += s_env[2][k] * sh;
+    }
+    const double k3 = k2;
+    f[i] = f[i] + d / 6.0 * (((k1 * i0 + 2.0 * (k2 * i1)) + 2.0 * (k3 * i1)) + k4 * i2);
+}
+
+cudaError_t kx_launch_rk4_sources(const kx_kernel *k, double *f, const kx_src_dev *src, const double *shapes,
+                                  double u, double d, double i0, double i1, double i2, cudaStream_t s) {
+    k_rk4_sources<<<1, kx_fin_threads(k->n), 0, s>>>(k->n, f, src, shapes, u, d, i0, i1, i2);
+    return cudaGetLastError();
+}
+
+// Loss rate of every row from the FP64 tables: nu_i = sum_{n<=m} S_inm f_t,
+// f_t = exp((1 - omega) l_jL + omega l_jL+1), l = ln max(f, 1e-300); one block
+// per row, fixed-order block reduction.  (The regime switch of the expanding
+// universe weighs it: Gamma_2->2 = |M|^2 sum h f nu / sum h f.)
+__global__ void k_loss_rate64(int n, long long P, const double *__restrict__ W, const double *__restrict__ om,
+                              const uint16_t *__restrict__ jl, const double *__restrict__ f,
+                              double *__restrict__ nu) {
+    __shared__ double s_l[KX_MAX_N];
+    __shared__ double red[32];
+    const int i = blockIdx.x;
+    for (int t = threadIdx.x; t < n; t += blockDim.x) s_l[t] = log(f[t] > KX_LOG_FLOOR ? f[t] : KX_LOG_FLOOR);
+    __syncthreads();
+    double acc = 0.0;
+    for (long long p = threadIdx.x; p < P; p += blockDim.x) {
+        const double w = W[(long long)i * P + p];
+        if (w != 0.0) {
+            const int j = jl[(long long)i * P + p];
+            const double o = om[(long long)i * P + p];
+            acc += w * exp((1.0 - o) * s_l[j] + o * s_l[j + 1]);
+        }
+    }
+    double v[1] = {acc};
+    kx_block_sum<1>(v, red);
+    if (threadIdx.x == 0) nu[i] = v[0];
+}
+
+cudaError_t kx_launch_loss_rate64(const kx_kernel *k, const double *f, double *nu, cudaStream_t s) {
+    k_loss_rate64<<<k->n, 256, 0, s>>>(k->n, k->P, k->d_W64, k->d_om64, k->d_jl, f, nu);
+    return cudaGetLastError();
+}
+
 // ------------------------------------------------------------ MB fit -----
 // Moment-matched discrete Maxwell-Boltzmann: T solves <E>_MB(T) = sum h E f /
 // sum h f (safeguarded Newton in u = ln T inside [ln 1e-12, ln 1e12]; <E>(T) is
@@ -1853,7 +1922,8 @@ __device__ __forceinline__ void kx_stage_body(int b, int n, int chunks, int path
 #pragma unroll
     for (int k = 0; k < KX_MAX_SRC; ++k)
         if (k < n_src) Si += s_env[k] * shp[k];
-    const double kv = in ? C + Si : 0.0;
+    double kv = in ? C + Si : 0.0;
+    if (sv.hscale != 1.0) kv *= sv.hscale;   // d/du = (C + S) / H (expanding universe)
     if (stage == 1) {
         const double fpi = f0 + htry * kv;
         // one reduction for both flags (2 = non-finite, 1 = negative) and for

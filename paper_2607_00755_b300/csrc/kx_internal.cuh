@@ -82,6 +82,12 @@ struct kx_kernel {
     long long bytes;
     long long stream_bytes;   // table bytes one contraction launch reads
     double build_ms;
+    // rescalable kernels (expanding universe): rebuilt in place for each scale
+    // factor; FP64 tables kept, FP32 tables keep every vector (layout fixed)
+    bool rescalable;
+    kx_gl_nodes gl;
+    uint32_t *d_vt_all;  // [V] global vector list (n | m0 << 16)
+    int *d_pos;          // [n][V] vector positions in the rows (identity)
 };
 
 // Per-instance integration state (device resident).
@@ -196,7 +202,7 @@ void kx_carve_views(const kx_kernel *k, int B, void *base, kx_batch_views *v);
 
 cudaError_t kx_launch_build_fp64(const kx_kernel *k, const kx_gl_nodes &gl, cudaStream_t s);
 cudaError_t kx_launch_keep_scan(const kx_kernel *k, const uint32_t *d_vt_all, int V, int *d_pos,
-                                int *d_cnt, cudaStream_t s);
+                                int *d_cnt, cudaStream_t s, bool keep_all = false);
 cudaError_t kx_launch_pack_fp32(const kx_kernel *k, const uint32_t *d_vt_all, int V,
                                 const int *d_pos, cudaStream_t s);
 cudaError_t kx_launch_count_nnz(const kx_kernel *k, unsigned long long *d_count, cudaStream_t s);
@@ -230,6 +236,7 @@ struct kx_step_views {
     double rtol, atol, h_min, h_max, l1_tol;
     long long max_attempts;
     int fixed, check_every, project;
+    double hscale;      // right-hand side factor: 1 (static box), 1/H (expanding universe, d/du)
 };
 cudaError_t kx_launch_stage(const kx_kernel *k, int B, const kx_batch_views &v,
                             const kx_step_views &sv, int stage, cudaStream_t s, bool pdl = false);
@@ -237,6 +244,14 @@ cudaError_t kx_launch_stage(const kx_kernel *k, int B, const kx_batch_views &v,
 // st (nullable) gives each instance's last in-solve temperature as the start.
 cudaError_t kx_launch_mbfit(const kx_kernel *k, int nb, const double *f, double *out3,
                             cudaStream_t s, const kx_inst_state *st = nullptr, const int *idx = nullptr);
+
+// expanding universe: one RK4 step on the sources only (one instance, block of n
+// threads): f += d/6 (k1 i0 + 2 k2 i1 + 2 k3 i1 + k4 i2), k = S(u), S(u1), S(u1),
+// S(u2), i = 1/H at u, u1 = u + d/2, u2 = u + d
+cudaError_t kx_launch_rk4_sources(const kx_kernel *k, double *f, const kx_src_dev *src, const double *shapes,
+                                  double u, double d, double i0, double i1, double i2, cudaStream_t s);
+// expanding universe: loss rate nu_i = sum_{n<=m} S_inm f_t of each row from the FP64 tables
+cudaError_t kx_launch_loss_rate64(const kx_kernel *k, const double *f, double *nu, cudaStream_t s);
 
 // bounded-wait self-check: *out = 1 if a wait on an mbarrier nothing arrives
 // on gave up after `cycles` SM clock cycles

@@ -225,6 +225,7 @@ static int kx_make_group(kx_server *srv, const Request &r, Group **out) {
     sv.fixed = p.fixed_step;
     sv.check_every = p.check_every;
     sv.project = p.project;
+    sv.hscale = 1.0;
     cudaError_t e = cudaStreamCreateWithFlags(&g->stream, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&g->ev, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaMallocHost((void **)&g->h_st, sizeof(kx_inst_state) * cap);

@@ -62,7 +62,8 @@ def test_struct_layouts_match_header(tmp_path):
     import paper_2607_00755_b300 as kx
     structs = {"kx_grid_desc": kx.GridDesc, "kx_solve_params": kx.SolveParams, "kx_diag": kx.Diag,
                "kx_result": kx.Result, "kx_source": kx.Source, "kx_server_config": kx.ServerConfig,
-               "kx_server_stats": kx.ServerStats}
+               "kx_server_stats": kx.ServerStats, "kx_expansion": kx.Expansion,
+               "kx_expansion_result": kx.ExpansionResult}
     lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "kx.h"', "int main(void) {"]
     for cname, cls in structs.items():
         lines.append(f'printf("{cname} %zu\\n", sizeof({cname}));')

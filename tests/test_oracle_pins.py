@@ -550,3 +550,88 @@ def test_chebyshev_loss_within_its_bound_and_converges(N):
         C, G, L, B = oracle.collision_chebyshev(q, W, f, 32)
         if np.max(B / L0) < 1e-15:
             assert np.max(np.abs(L - L0) / L0) < 1e-13
+
+
+# ------------------------------------------------------ expanding universe ---
+def _rd_source(q, u_on=0.0, tau=0.3, rate=2e-2):
+    return dict(shape=ki.lognormal_bumps(q, (0.5,), (0.3,), (1.0,))[None], rate=np.array([rate]),
+                tau=np.array([tau]), t_on=np.array([u_on]))
+
+
+def test_expanding_rk4_regime_is_fourth_order():
+    """Sources only (the switch never fires): f(u_end) against the closed-form
+    integral of S(u)/H(u) for H = exp(-2u) (radiation domination) and an
+    exponential envelope; the error falls ~16x per halving of du."""
+    q = ki.log_grid(16, 1e-3, 10.0)
+    f0 = 1e-3 * ki.bimodal(np.random.default_rng(2), q)
+    src = _rd_source(q)
+    g1 = oracle.grid(q)   # a = 1: the comoving weights q^2 Dq
+    s = src["shape"][0] / np.sum(g1["h"] * src["shape"][0])
+    alpha, beta = -1.0 / 0.3 + 2.0, 0.0
+    integral = (np.exp(alpha * 1.0) - 1.0) * np.exp(beta) / alpha
+    exact = f0 + 2e-2 * s * integral
+    errs = []
+    for du in (0.1, 0.05, 0.025):
+        f, r = oracle.solve_expanding(q, f0, 1.0, hu=[0.0, 1.0], hlnH=[0.0, -2.0], u0=0.0, u_end=1.0,
+                                      du_rk4=du, eps_switch=np.inf, sources=src)
+        assert np.isnan(r["u_switch"]) and r["steps"] == 0 and r["rk4_steps"] == round(1.0 / du)
+        errs.append(np.max(np.abs(f - exact)) / np.max(exact))
+    assert errs[0] / errs[1] > 12 and errs[1] / errs[2] > 12, errs
+    assert errs[2] < 1e-8
+
+
+def test_expanding_collisions_conserve_comoving_number():
+    """Collisions only (switch at u0): the comoving number sum q^2 Dq f stays
+    at its initial value to rounding while a grows (the projection zeroes the
+    number moment at every a)."""
+    q = ki.log_grid(14, 1e-3, 10.0)
+    f0 = 1e-3 * ki.bimodal(np.random.default_rng(3), q)
+    hc = oracle.grid(q)["h"]
+    f, r = oracle.solve_expanding(q, f0, oracle.M2_from_sigma(1.0, 40.0), hu=[0.0, 1.0],
+                                  hlnH=[0.0, -2.0], u0=0.0, u_end=0.3, eps_switch=0.0, h0=1e-3)
+    assert r["u_switch"] == 0.0 and r["rk4_steps"] == 0 and r["steps"] > 10 and r["status"] == 0
+    assert abs(np.sum(hc * f) / np.sum(hc * f0) - 1) < 1e-13
+
+
+def test_expanding_heun_regime_against_an_independent_integrator():
+    """The Heun regime against scipy's DOP853 (tight tolerances) on the same
+    right-hand side (C_proj of the kernel at a = e^u plus the source, over
+    H(u)), assembled here from the pinned primitives."""
+    from scipy.integrate import solve_ivp
+    q = ki.log_grid(12, 1e-3, 10.0)
+    f0 = 1e-3 * ki.bimodal(np.random.default_rng(4), q)
+    src = _rd_source(q, tau=0.5)
+    M2 = oracle.M2_from_sigma(1.0, 60.0)
+    hc = oracle.grid(q)["h"]
+    s = src["shape"][0] / np.sum(hc * src["shape"][0])
+
+    def rhs(u, f):
+        a = np.exp(u)
+        g = oracle.grid(q, a=a)
+        W = oracle.kernel_tensor(q, a=a)
+        C = oracle.collision_tensor(q, W, f, a=a) * M2
+        Cp, _ = oracle.project(g["E"], g["h"], f, C)
+        return (Cp + 2e-2 * np.exp(-u / 0.5) * s) / np.exp(-2.0 * u)
+
+    ref = solve_ivp(rhs, (0.0, 0.25), f0, method="DOP853", rtol=1e-11, atol=1e-16).y[:, -1]
+    f, r = oracle.solve_expanding(q, f0, M2, hu=[0.0, 1.0], hlnH=[0.0, -2.0], u0=0.0, u_end=0.25,
+                                  eps_switch=0.0, sources=src, h0=1e-4, rtol=1e-9, atol=1e-18)
+    assert r["status"] == 0 and r["u"] == 0.25
+    assert np.max(np.abs(f - ref)) / np.max(ref) < 1e-6
+
+
+def test_expanding_switch_rule():
+    """eps_switch = 0 switches at u0 without RK4 steps; a finite threshold
+    switches at the first check with Gamma/H above it."""
+    q = ki.log_grid(16, 1e-3, 10.0)
+    f0 = 1e-3 * ki.bimodal(np.random.default_rng(5), q)
+    src = _rd_source(q)
+    M2 = oracle.M2_from_sigma(1.0, 40.0)
+    _, r0 = oracle.solve_expanding(q, f0, M2, hu=[0.0, 1.0], hlnH=[0.0, -2.0], u0=0.0, u_end=0.05,
+                                   eps_switch=0.0, sources=src)
+    assert r0["u_switch"] == 0.0 and r0["rk4_steps"] == 0
+    _, r1 = oracle.solve_expanding(q, f0, oracle.M2_from_sigma(1.0, 80.0), hu=[0.0, 1.0],
+                                   hlnH=[0.0, -2.0], u0=0.0, u_end=0.3, du_rk4=0.02, check_every=2,
+                                   eps_switch=1e-2, sources=src)
+    assert 0.0 < r1["u_switch"] < 0.3 and r1["gamma_over_H"] > 1e-2
+    assert r1["rk4_steps"] == round(r1["u_switch"] / 0.02) and r1["checks"] == r1["rk4_steps"] // 2 + 1
