@@ -243,6 +243,22 @@ int kx_solve_host(kx_ctx *ctx, const kx_kernel *k, int batch, const double *sigm
                   const kx_source *src, int n_src_sets, const kx_solve_params *par,
                   double *f_host, kx_result *res_host);
 
+/* ----------------------------------------------------------- uneven batch */
+/* Integrates G batches on G different grids (an uneven batch: G <= 8
+ * KX_SPLIT_TF32 kernels, kernel g with B[g] instances of sigma[g] (host
+ * [B[g]]) and distributions f_dev[g] (device [B[g]][n_g], updated in place))
+ * as one sequence of grouped launches: per Heun stage one gain-GEMM launch and
+ * one Chebyshev-loss-GEMM launch over the work items of all G kernels, the
+ * exact loss per kernel (all instances, or the Chebyshev path's flagged ones),
+ * and one stage launch over all instances; eight attempts per captured CUDA
+ * graph.  Each instance's arithmetic is that of kx_solve on its own kernel
+ * (results are bit-identical).  par as for kx_solve (no sources, adaptive
+ * steps); res[g] host [B[g]] (may be NULL).  KX_ENOTSUP for other precisions
+ * or fixed steps. */
+int kx_solve_grouped(kx_ctx *ctx, int G, const kx_kernel *const *kernels, const int *batch,
+                     const double *const *sigma_host, const kx_solve_params *par, double *const *f_dev,
+                     kx_result *const *res_host);
+
 /* ------------------------------------------------------ expanding universe */
 /* Hubble rate and the two regimes of the integration in u = ln a (Sec. 4,
  * eq. numerical_evolution_loga; Sec. 4.2).  The paper's H(a) comes from

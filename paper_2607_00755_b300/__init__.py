@@ -29,7 +29,7 @@ EXPORTS = (
     "kx_time_contractions", "kx_time_collision",
     "kx_collision_noalloc", "kx_server_start", "kx_submit", "kx_poll", "kx_server_get_stats",
     "kx_server_stop", "kx_math_check", "kx_wait_check", "kx_set_stream_variant", "kx_get_stream_variant",
-    "kx_source_higgs_decay", "kx_source_condensate", "kx_solve_expanding",
+    "kx_source_higgs_decay", "kx_source_condensate", "kx_solve_expanding", "kx_solve_grouped",
 )
 
 
@@ -152,6 +152,7 @@ def load_library(path: str = LIB_PATH):
         "kx_get_stream_variant": (i, [vp, i, i, vp, vp]),
         "kx_source_higgs_decay": (i, [i, vp, d, d, d, d, d, d, vp, vp]),
         "kx_source_condensate": (i, [i, vp, d, d, d, d, d, vp, vp]),
+        "kx_solve_grouped": (i, [vp, i, vp, vp, vp, ctypes.POINTER(SolveParams), vp, vp]),
         "kx_solve_expanding": (i, [vp, ctypes.POINTER(GridDesc), d, vp, ctypes.POINTER(Expansion),
                                    ctypes.POINTER(SolveParams), vp, ctypes.POINTER(ExpansionResult)]),
         "kx_launch_count": (ctypes.c_longlong, [vp]),
@@ -333,6 +334,25 @@ class Context:
         if rc in (EINVAL, ENOMEM, ECUDA, ETIMEOUT, ENOTSUP):
             raise self.error(rc, "kx_step")
         return [r.as_dict() for r in res]
+
+    def solve_grouped(self, kernels, fs, sigmas, **params):
+        """Uneven batch (kx_solve_grouped): kernels[g] with the CUDA float64
+        tensor fs[g] [B_g, n_g] (in place) and sigmas[g] [B_g]; returns one list
+        of result dicts per group."""
+        G = len(kernels)
+        Bs = [f.shape[0] for f in fs]
+        sig = [_np(np.broadcast_to(np.asarray(s_, dtype=np.float64), (b,))) for s_, b in zip(sigmas, Bs)]
+        karr = (ctypes.c_void_p * G)(*[k.h for k in kernels])
+        barr = (ctypes.c_int * G)(*Bs)
+        sarr = (ctypes.c_void_p * G)(*[x.ctypes.data for x in sig])
+        farr = (ctypes.c_void_p * G)(*[f.data_ptr() for f in fs])
+        res = [(Result * b)() for b in Bs]
+        rarr = (ctypes.c_void_p * G)(*[ctypes.addressof(r) for r in res])
+        par = self.params(**params)
+        rc = self.lib.kx_solve_grouped(self.h, G, karr, barr, sarr, ctypes.byref(par), farr, rarr)
+        if rc in (EINVAL, ENOMEM, ECUDA, ETIMEOUT, ENOTSUP):
+            raise self.error(rc, "kx_solve_grouped")
+        return [[x.as_dict() for x in r] for r in res]
 
     def solve_expanding(self, q, f, sigma, hu, ln_H, u0, u_end, du_rk4=0.05, check_every=1,
                         eps_switch=1e-2, sources=None, precision=FP64, mass=1.0, n_mu=18,

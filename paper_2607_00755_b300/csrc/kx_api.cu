@@ -755,17 +755,22 @@ struct kx_run {
     double *mb;
 };
 
+// offset: the run's place in the context arena (several runs side by side:
+// the grouped solve); the arena must already hold offset + the run's bytes
+// when offset > 0.
 static int kx_setup_run(kx_ctx *ctx, const kx_kernel *k, int B, const double *sigma,
                         const kx_source *src, int nsets, const kx_solve_params *par,
                         const double *t0, const double *h0, double *f_dev, bool own_f,
-                        kx_run *run, double **f_used, const double *src_weights = nullptr) {
+                        kx_run *run, double **f_used, const double *src_weights = nullptr,
+                        size_t offset = 0) {
     std::vector<kx_src_dev> sd;
     std::vector<double> shapes;
     int rc = kx_sources_host(ctx, k, B, src, nsets, sd, shapes, src_weights);
     if (rc) return rc;
     kx_solve_layout L = kx_layout_solve(k, B, (int)(shapes.size() / k->n) + 1, own_f);
-    if ((rc = kx_arena_reserve(ctx, L.total)) != KX_OK) return rc;
-    char *base = (char *)ctx->d_arena;
+    if (offset == 0 && (rc = kx_arena_reserve(ctx, L.total)) != KX_OK) return rc;
+    if (offset + L.total > ctx->arena_bytes) return kx_set_error(ctx, KX_ENOMEM, "arena too small for the run");
+    char *base = (char *)ctx->d_arena + offset;
     kx_carve_views(k, B, base + L.views, &run->v);
     kx_step_views &sv = run->sv;
     sv.f = own_f ? (double *)(base + L.f) : f_dev;
@@ -991,6 +996,119 @@ extern "C" int kx_solve_host(kx_ctx *ctx, const kx_kernel *k, int B, const doubl
     KX_CUDA_TRY(ctx, cudaMemcpyAsync(f_host, f, sizeof(double) * B * k->n, cudaMemcpyDeviceToHost, s));
     KX_CUDA_TRY(ctx, cudaStreamSynchronize(s));
     return rc2;
+}
+
+// ------------------------------------------------------ uneven batch
+// Device-resident integration of G batches on different grids (split-TF32
+// kernels) as one sequence of grouped launches: per Heun stage one gain-GEMM
+// launch and one loss-GEMM launch over the work items of all G kernels, the
+// exact loss per kernel (Chebyshev path: the flagged instances only), and one
+// stage launch over all instances; A attempts per captured graph.
+extern "C" int kx_solve_grouped(kx_ctx *ctx, int G, const kx_kernel *const *ks, const int *B,
+                                const double *const *sigma, const kx_solve_params *par, double *const *f_dev,
+                                kx_result *const *res) {
+    kx_nvtx range_("kx_solve_grouped");
+    if (!ctx || G < 1 || G > 8 || !ks || !B || !sigma || !f_dev) return kx_set_error(ctx, KX_EINVAL, "bad arguments");
+    int rc = kx_check_params(ctx, par);
+    if (rc) return rc;
+    if (par->fixed_step) return kx_set_error(ctx, KX_ENOTSUP, "grouped solve: adaptive steps only");
+    for (int g = 0; g < G; ++g) {
+        if ((rc = kx_check_batch(ctx, ks[g], B[g], sigma[g])) != KX_OK) return rc;
+        if (!f_dev[g]) return kx_set_error(ctx, KX_EINVAL, "null f");
+        if (ks[g]->precision != KX_SPLIT_TF32)
+            return kx_set_error(ctx, KX_ENOTSUP, "grouped solve: KX_SPLIT_TF32 kernels");
+    }
+    KX_CUDA_TRY(ctx, cudaSetDevice(ctx->device));
+    // one arena region per group
+    std::vector<size_t> off(G + 1, 0);
+    for (int g = 0; g < G; ++g) off[g + 1] = off[g] + kx_align(kx_layout_solve(ks[g], B[g], 1, false).total);
+    if ((rc = kx_arena_reserve(ctx, off[G])) != KX_OK) return rc;
+    std::vector<kx_run> runs(G);
+    for (int g = 0; g < G; ++g) {
+        double *f = nullptr;
+        // (the first region sits at offset 0: reserved above, so no reallocation)
+        if ((rc = kx_setup_run(ctx, ks[g], B[g], sigma[g], nullptr, 0, par, nullptr, nullptr, f_dev[g], false,
+                               &runs[g], &f, nullptr, off[g])))
+            return rc;
+    }
+    cudaStream_t s = ctx->stream;
+    std::vector<const kx_batch_views *> vs(G);
+    std::vector<const kx_step_views *> svs(G);
+    std::vector<const kx_inst_state *> sts(G);
+    for (int g = 0; g < G; ++g) {
+        vs[g] = &runs[g].v;
+        svs[g] = &runs[g].sv;
+        sts[g] = runs[g].sv.st;
+        KX_CUDA_TRY(ctx, kx_launch_prep(ks[g], B[g], runs[g].sv.f, runs[g].v, runs[g].sv.st, s));
+        ctx->launches += 1;
+    }
+    // one timeout flag for the grouped launches, seen by every group's stage
+    int *d_err = runs[0].v.err;
+    for (int g = 1; g < G; ++g) runs[g].v.err = d_err;
+    auto attempt = [&](cudaStream_t cs) -> cudaError_t {
+        cudaError_t e = cudaSuccess;
+        for (int stage = 1; stage <= 2 && e == cudaSuccess; ++stage) {
+            // the contraction's input: f (stage 1) or the predictor f_p (stage 2),
+            // prepared by the previous stage kernel
+            e = kx_launch_batch_contract_grouped(G, ks, B, vs.data(), sts.data(), stage, d_err, cs);
+            if (e == cudaSuccess) e = kx_launch_stage_grouped(G, ks, B, vs.data(), svs.data(), stage, cs);
+        }
+        return e;
+    };
+    const int A = 8;   // attempts per graph
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    cudaStream_t cap = nullptr;
+    cudaError_t e = cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+        for (int a = 0; a < A && e == cudaSuccess; ++a) e = attempt(cap);
+        cudaError_t e2 = cudaStreamEndCapture(cap, &graph);
+        if (e == cudaSuccess) e = e2;
+    }
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&exec, graph, 0);
+    if (cap) cudaStreamDestroy(cap);
+    if (e != cudaSuccess) {
+        if (graph) cudaGraphDestroy(graph);
+        return kx_set_error(ctx, KX_ECUDA, std::string("grouped graph capture: ") + cudaGetErrorString(e));
+    }
+    int Btot = 0;
+    for (int g = 0; g < G; ++g) Btot += B[g];
+    if ((rc = kx_pinned_reserve(ctx, sizeof(kx_inst_state) * (size_t)Btot)) != KX_OK) {
+        cudaGraphExecDestroy(exec);
+        cudaGraphDestroy(graph);
+        return rc;
+    }
+    kx_inst_state *h_st = (kx_inst_state *)ctx->h_pinned;
+    const auto t_start = std::chrono::steady_clock::now();
+    const long long max_launch = (long long)par->max_attempts / A + 2;
+    for (long long launched = 0; e == cudaSuccess && launched < max_launch;) {
+        e = cudaGraphLaunch(exec, s);
+        ++launched;
+        ctx->launches += (long long)A * (2 * (2 + G) + 2);
+        for (int g = 0, o = 0; g < G && e == cudaSuccess; o += B[g], ++g)
+            e = cudaMemcpyAsync(h_st + o, runs[g].sv.st, sizeof(kx_inst_state) * B[g], cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        bool all = true;
+        for (int b = 0; b < Btot; ++b) all &= h_st[b].done != 0;
+        if (all) break;
+        if (std::chrono::duration<double>(std::chrono::steady_clock::now() - t_start).count() > 3600.0) {
+            rc = KX_ETIMEOUT;
+            break;
+        }
+    }
+    cudaStreamSynchronize(s);
+    cudaGraphExecDestroy(exec);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) return kx_set_error(ctx, KX_ECUDA, std::string("grouped solve: ") + cudaGetErrorString(e));
+    const double latency = std::chrono::duration<double>(std::chrono::steady_clock::now() - t_start).count();
+    int worst = KX_OK;
+    for (int g = 0; g < G; ++g) {
+        int w = kx_collect(ctx, ks[g], B[g], runs[g], res ? res[g] : nullptr, nullptr, nullptr, latency);
+        if (w != KX_OK && worst == KX_OK) worst = w;
+    }
+    if (rc) return kx_set_error(ctx, rc, "grouped solve: wall-clock limit");
+    return worst;
 }
 
 // ------------------------------------------------------ expanding universe

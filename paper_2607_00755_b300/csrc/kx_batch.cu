@@ -141,6 +141,26 @@ __device__ __forceinline__ void kx_mbar_arrive(uint32_t bar) {
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
 }
 
+// One GEMM of a (grouped) launch: its operands, output and shape; its work
+// items are item0 .. item0 + MTb NTi chunks - 1 of the launch.
+#define KX_MAX_GROUPS 8
+struct kx_sg_problem {
+    const float *At, *Bt;
+    float *out;
+    const float *fT;
+    long long P;
+    int n, KB, KC, chunks, MTb, NTi, nsubI, Bpad, nis, item0;
+};
+struct kx_sg_list {
+    kx_sg_problem p[KX_MAX_GROUPS];
+    int np, items;
+};
+__device__ __forceinline__ int kx_sg_find(const kx_sg_list &L, int w) {
+    int g = 0;
+    while (g + 1 < L.np && w >= L.p[g + 1].item0) ++g;
+    return g;
+}
+
 // Shared-memory plan of a split GEMM: S stages of A (hi, lo: 2 x 8 KB) and B
 // (hi, lo: 2 x nsb x 4 KB, nsb = 64-row i tiles of the widest i tile); for the
 // gain with n <= 256 also the f' block of the item's 128 instances (fs[n][128],
@@ -152,7 +172,7 @@ __host__ __device__ inline kx_sg_plan kx_sg_plan_for(bool gen, int n, int nsubI)
     kx_sg_plan pl;
     pl.nsb = nsubI < 4 ? nsubI : 4;
     pl.stage = 2 * KX_ATILE * 4 + 2 * pl.nsb * KX_BTILE * 4;
-    pl.fs = (gen && n <= 256) ? 128 * n * 4 : 0;
+    pl.fs = (gen && n <= 256) ? 128 * n * 4 : 0;   // (n, nsubI: the largest of a grouped launch)
     const int budget = 227 * 1024 - 256;
     pl.S = (budget - pl.fs) / pl.stage;
     if (pl.S > 4) pl.S = 4;
@@ -177,12 +197,8 @@ __device__ __forceinline__ void kx_pair_decode(long long p, int N, int &n, int &
 }
 template <bool GEN>
 __global__ void __launch_bounds__(KX_SG_THREADS, 1)
-    k_split_gemm(const float *__restrict__ At, const float *__restrict__ Bt, float *__restrict__ out,
-                 const float *__restrict__ fT, long long P, int n,
-                 int KB, int KC, int chunks, int MTb, int NTi, int nsubI, int Bpad, int nis, int ncols,
-                 int *err) {
+    k_split_gemm(const kx_sg_list L, const kx_sg_plan pl, int ncols, int *err) {
     extern __shared__ __align__(1024) unsigned char kx_gsm[];
-    const kx_sg_plan pl = kx_sg_plan_for(GEN, n, nsubI);
     const int S = pl.S;
     float *fs = reinterpret_cast<float *>(kx_gsm + S * pl.stage);   // f' block (GEN, n <= 256)
     uint64_t *bars = reinterpret_cast<uint64_t *>(kx_gsm + S * pl.stage + pl.fs);
@@ -224,7 +240,7 @@ __global__ void __launch_bounds__(KX_SG_THREADS, 1)
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const uint32_t tmem = *tslot;
-    const int items = MTb * NTi * chunks;
+    const int items = L.items;
     const int half = ncols >> 1;   // columns of one accumulator
     int fissued = 0;               // f' blocks requested (tid 0) / waited for (producers)
     if (warp == 13) {
@@ -232,9 +248,12 @@ __global__ void __launch_bounds__(KX_SG_THREADS, 1)
         if (lane == 0) {
             int it = 0;
             for (int w = blockIdx.x; w < items && !*abort; w += gridDim.x) {
-                const int c = w % chunks, nt = (w / chunks) % NTi, mt = w / (chunks * NTi);
-                const int kb0 = c * KC, kb1 = min(KB, kb0 + KC);
-                const uint32_t bbytes = (uint32_t)(pl.nsb * KX_BTILE * 4);
+                const kx_sg_problem &pb = L.p[kx_sg_find(L, w)];
+                const int wl = w - pb.item0, KB = pb.KB;
+                const int c = wl % pb.chunks, nt = (wl / pb.chunks) % pb.NTi, mt = wl / (pb.chunks * pb.NTi);
+                const int kb0 = c * pb.KC, kb1 = min(KB, kb0 + pb.KC);
+                const int nsbp = min(4, pb.nsubI);   // the problem's 64-row i tiles per i tile
+                const uint32_t bbytes = (uint32_t)(nsbp * KX_BTILE * 4);
                 bool ok = true;
                 for (int kb = kb0; kb < kb1; ++kb, ++it) {
                     const int q = it % S, round = it / S;
@@ -245,11 +264,11 @@ __global__ void __launch_bounds__(KX_SG_THREADS, 1)
                     unsigned char *sa = kx_gsm + (size_t)q * pl.stage, *sb = sa + 2 * KX_ATILE * 4;
                     const uint32_t bar = full0 + 8 * q;
                     kx_mbar_expect_tx(bar, (GEN ? 0u : 2u * KX_ATILE * 4) + 2 * bbytes);
-                    const float *bsrc = Bt + ((size_t)nt * KB + kb) * 2 * pl.nsb * KX_BTILE;
+                    const float *bsrc = pb.Bt + ((size_t)nt * KB + kb) * 2 * nsbp * KX_BTILE;
                     kx_bulk_g2s(kx_smem_u32(sb), bsrc, bbytes, bar);
-                    kx_bulk_g2s(kx_smem_u32(sb + bbytes), bsrc + pl.nsb * KX_BTILE, bbytes, bar);
+                    kx_bulk_g2s(kx_smem_u32(sb + pl.nsb * KX_BTILE * 4), bsrc + nsbp * KX_BTILE, bbytes, bar);
                     if (!GEN) {
-                        const float *asrc = At + ((size_t)mt * KB + kb) * 2 * KX_ATILE;
+                        const float *asrc = pb.At + ((size_t)mt * KB + kb) * 2 * KX_ATILE;
                         kx_bulk_g2s(kx_smem_u32(sa), asrc, KX_ATILE * 4, bar);
                         kx_bulk_g2s(kx_smem_u32(sa + KX_ATILE * 4), asrc + KX_ATILE, KX_ATILE * 4, bar);
                     }
@@ -265,9 +284,12 @@ __global__ void __launch_bounds__(KX_SG_THREADS, 1)
             int it = 0;
             const int row = tid & 127, ph = (tid >> 7) * 8;   // instance row in the tile, first pair
             for (int w = blockIdx.x; w < items && !*abort; w += gridDim.x) {
-                const int c = w % chunks, mt = w / (chunks * NTi);
-                const int kb0 = c * KC, kb1 = min(KB, kb0 + KC);
-                const float *fblk = fT + (size_t)mt * n * 128;   // this instance tile's f' [n][128]
+                const kx_sg_problem &pb = L.p[kx_sg_find(L, w)];
+                const int wl = w - pb.item0, n = pb.n;
+                const long long P = pb.P;
+                const int c = wl % pb.chunks, mt = wl / (pb.chunks * pb.NTi);
+                const int kb0 = c * pb.KC, kb1 = min(pb.KB, kb0 + pb.KC);
+                const float *fblk = pb.fT + (size_t)mt * n * 128;   // this instance tile's f' [n][128]
                 bool ok = true;
                 if (fsm) {
                     // the item's f' block, once every generating warp is done with
@@ -354,9 +376,11 @@ __global__ void __launch_bounds__(KX_SG_THREADS, 1)
         if (lane == 0) {
             int it = 0, li = 0;
             for (int w = blockIdx.x; w < items && !*abort; w += gridDim.x, ++li) {
-                const int c = w % chunks, nt = (w / chunks) % NTi;
-                const int kb0 = c * KC, kb1 = min(KB, kb0 + KC);
-                const int Ni = min(KX_GN, nis - nt * KX_GN);
+                const kx_sg_problem &pb = L.p[kx_sg_find(L, w)];
+                const int wl = w - pb.item0;
+                const int c = wl % pb.chunks, nt = (wl / pb.chunks) % pb.NTi;
+                const int kb0 = c * pb.KC, kb1 = min(pb.KB, kb0 + pb.KC);
+                const int Ni = min(KX_GN, pb.nis - nt * KX_GN);
                 const int buf = li & 1, use = li >> 1;
                 if (use > 0 && !kx_wait_role(acce0 + 8 * buf, (use - 1) & 1, abort, err)) break;
                 asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
@@ -393,7 +417,9 @@ __global__ void __launch_bounds__(KX_SG_THREADS, 1)
         const int qtr = warp & 3;   // tensor-memory lane quarter this warp may read
         int li = 0;
         for (int w = blockIdx.x; w < items; w += gridDim.x, ++li) {
-            const int c = w % chunks, nt = (w / chunks) % NTi, mt = w / (chunks * NTi);
+            const kx_sg_problem &pb = L.p[kx_sg_find(L, w)];
+            const int wl = w - pb.item0, nis = pb.nis;
+            const int c = wl % pb.chunks, nt = (wl / pb.chunks) % pb.NTi, mt = wl / (pb.chunks * pb.NTi);
             const int Ni = min(KX_GN, nis - nt * KX_GN);
             const int buf = li & 1, use = li >> 1;
             int ok = 1;
@@ -402,11 +428,11 @@ __global__ void __launch_bounds__(KX_SG_THREADS, 1)
             if (!ok) break;
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
             const int b = mt * 128 + qtr * 32 + lane;
-            float *dst = out + ((size_t)c * Bpad + b) * nis + (size_t)nt * KX_GN;
+            float *dst = pb.out + ((size_t)c * pb.Bpad + b) * nis + (size_t)nt * KX_GN;
             for (int c0 = 0; c0 < Ni; c0 += 16) {
                 float t[16];
                 kx_tmem_ld16(tmem + ((uint32_t)(qtr * 32) << 16) + (uint32_t)(buf * half + c0), t);
-                if (b < Bpad) {
+                if (b < pb.Bpad) {
 #pragma unroll
                     for (int q = 0; q < 16; q += 4)
                         *reinterpret_cast<float4 *>(dst + c0 + q) = make_float4(t[q], t[q + 1], t[q + 2], t[q + 3]);
@@ -660,28 +686,57 @@ static int kx_sg_grid(int items) {
     return std::max(1, std::min(items, sms));
 }
 
-cudaError_t kx_launch_batch_contract(const kx_kernel *k, int B, const kx_batch_views &v,
-                                     const kx_inst_state *st, int stage, int *d_err,
-                                     cudaStream_t s) {
-    const int MTb = v.Bpad / 128, NTi = (k->nis + KX_GN - 1) / KX_GN;
-    int ncols = 32;   // two accumulators of up to 256 columns (the widest i tile)
-    while (ncols < 2 * std::min(KX_GN, k->nis)) ncols <<= 1;
-    // gain: out = Gs [gsk][Bpad][nis]
-    int items = MTb * NTi * k->gsk;
-    k_split_gemm<true><<<kx_sg_grid(items), KX_SG_THREADS, kx_sg_plan_for(true, k->n, k->nsubI).smem, s>>>(
-        nullptr, k->d_Sg, v.Gs, v.fT, k->P, k->n, k->KBG, KX_GAIN_KC, k->gsk, MTb, NTi, k->nsubI,
-        v.Bpad, k->nis, ncols, d_err);
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
-    if (k->cheb_K) {
-        // loss: out = Lp [lsk][Bpad][nis]
-        items = MTb * NTi * k->lsk;
-        k_split_gemm<false><<<kx_sg_grid(items), KX_SG_THREADS, kx_sg_plan_for(false, k->n, k->nsubI).smem, s>>>(
-            v.yt, k->d_Mtile, v.Lp, nullptr, 0, k->n, k->KBL, KX_LOSS_KC, k->lsk, MTb, NTi, k->nsubI,
-            v.Bpad, k->nis, ncols, d_err);
-        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+// The gain (GEN) or Chebyshev-loss GEMM problem of one kernel and batch.
+static kx_sg_problem kx_sg_problem_for(bool gen, const kx_kernel *k, const kx_batch_views &v, int item0) {
+    kx_sg_problem pb;
+    pb.At = gen ? nullptr : v.yt;
+    pb.Bt = gen ? k->d_Sg : k->d_Mtile;
+    pb.out = gen ? v.Gs : v.Lp;
+    pb.fT = v.fT;
+    pb.P = k->P;
+    pb.n = k->n;
+    pb.KB = gen ? k->KBG : k->KBL;
+    pb.KC = gen ? KX_GAIN_KC : KX_LOSS_KC;
+    pb.chunks = gen ? k->gsk : k->lsk;
+    pb.MTb = v.Bpad / 128;
+    pb.NTi = (k->nis + KX_GN - 1) / KX_GN;
+    pb.nsubI = k->nsubI;
+    pb.Bpad = v.Bpad;
+    pb.nis = k->nis;
+    pb.item0 = item0;
+    return pb;
+}
+
+// One launch of the gain (GEN) or loss GEMM over the problems of G kernels.
+static cudaError_t kx_launch_split_gemm(bool gen, int G, const kx_kernel *const *ks, const kx_batch_views *const *vs,
+                                        int *d_err, cudaStream_t s) {
+    kx_sg_list L;
+    L.np = 0;
+    int items = 0, nmax = 0, nsmax = 0, wmax = 0;
+    for (int g = 0; g < G; ++g) {
+        if (!gen && !ks[g]->cheb_K) continue;
+        kx_sg_problem pb = kx_sg_problem_for(gen, ks[g], *vs[g], items);
+        L.p[L.np++] = pb;
+        items += pb.MTb * pb.NTi * pb.chunks;
+        nmax = std::max(nmax, pb.n);
+        nsmax = std::max(nsmax, pb.nsubI);
+        wmax = std::max(wmax, std::min(KX_GN, pb.nis));
     }
-    // the exact loss: every instance, or (Chebyshev loss) the flagged ones
+    if (!L.np) return cudaSuccess;
+    L.items = items;
+    int ncols = 32;   // two accumulators of the widest i tile
+    while (ncols < 2 * wmax) ncols <<= 1;
+    const kx_sg_plan pl = kx_sg_plan_for(gen, nmax, nsmax);
+    if (gen)
+        k_split_gemm<true><<<kx_sg_grid(items), KX_SG_THREADS, pl.smem, s>>>(L, pl, ncols, d_err);
+    else
+        k_split_gemm<false><<<kx_sg_grid(items), KX_SG_THREADS, pl.smem, s>>>(L, pl, ncols, d_err);
+    return cudaGetLastError();
+}
+
+// The exact loss kernel (all instances, or the Chebyshev path's flagged ones).
+static cudaError_t kx_launch_batch_loss(const kx_kernel *k, int B, const kx_batch_views &v,
+                                        const kx_inst_state *st, int stage, cudaStream_t s) {
     const kx_loss_shape sh = kx_loss_shape_for(k->n);
     const int per = 32 * sh.ipl;
     dim3 g2((B + per - 1) / per, k->n);
@@ -697,6 +752,27 @@ cudaError_t kx_launch_batch_contract(const kx_kernel *k, int B, const kx_batch_v
         k_batch_loss<1, 32><<<g2, 1024, smem, s>>>(k->n, B, v.B, k->d_lel, k->d_lseg, k->d_lsw, k->d_lorder,
                                                    v.td, v.fmax, v.partial, st, stage, flags);
     return cudaGetLastError();
+}
+
+cudaError_t kx_launch_batch_contract(const kx_kernel *k, int B, const kx_batch_views &v,
+                                     const kx_inst_state *st, int stage, int *d_err,
+                                     cudaStream_t s) {
+    const kx_batch_views *vp = &v;
+    cudaError_t e = kx_launch_split_gemm(true, 1, &k, &vp, d_err, s);
+    if (e == cudaSuccess && k->cheb_K) e = kx_launch_split_gemm(false, 1, &k, &vp, d_err, s);
+    if (e == cudaSuccess) e = kx_launch_batch_loss(k, B, v, st, stage, s);
+    return e;
+}
+
+// Grouped contraction of G kernels (the uneven batch): one gain-GEMM launch
+// and one loss-GEMM launch over all their work items; the exact loss per kernel.
+cudaError_t kx_launch_batch_contract_grouped(int G, const kx_kernel *const *ks, const int *B,
+                                             const kx_batch_views *const *vs, const kx_inst_state *const *sts,
+                                             int stage, int *d_err, cudaStream_t s) {
+    cudaError_t e = kx_launch_split_gemm(true, G, ks, vs, d_err, s);
+    if (e == cudaSuccess) e = kx_launch_split_gemm(false, G, ks, vs, d_err, s);
+    for (int g = 0; g < G && e == cudaSuccess; ++g) e = kx_launch_batch_loss(ks[g], B[g], *vs[g], sts[g], stage, s);
+    return e;
 }
 
 // ------------------------------------------------------ host table build

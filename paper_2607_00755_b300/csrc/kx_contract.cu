@@ -2114,6 +2114,58 @@ __global__ void __launch_bounds__(KX_FIN_THREADS)
     kx_stage_body<Q>(blockIdx.x, n, chunks, PATH >= 0 ? PATH : path, E, h, v, sv, stage, max_attempts, smem);
 }
 
+// Grouped stage (the uneven batch): block b of the launch is instance b - b0_g
+// of group g (b0_g = the instances of the groups before g); every group's
+// instances run the same stage body with its own grid, tables and state.
+// Threads beyond a group's grid points take no part (the block sums and
+// maxima add zeros, so results equal the per-group launch bit for bit).
+#define KX_MAX_GROUPS_STAGE 8
+struct kx_stage_group {
+    int n, chunks, path, b0;
+    const double *E, *h;
+    kx_batch_views v;
+    kx_step_views sv;
+};
+struct kx_stage_groups {
+    kx_stage_group g[KX_MAX_GROUPS_STAGE];
+    int G;
+};
+
+__global__ void __launch_bounds__(KX_FIN_THREADS) k_stage_grouped(const kx_stage_groups G, int stage) {
+    __shared__ double smem[5 * KX_FIN_THREADS + 8];
+    kx_pdl_trigger();
+    int g = 0;
+    while (g + 1 < G.G && (int)blockIdx.x >= G.g[g + 1].b0) ++g;
+    const kx_stage_group &q = G.g[g];
+    kx_stage_body<false>((int)blockIdx.x - q.b0, q.n, q.chunks, q.path, q.E, q.h, q.v, q.sv, stage,
+                         q.sv.max_attempts, smem);
+}
+
+cudaError_t kx_launch_stage_grouped(int G, const kx_kernel *const *ks, const int *B,
+                                    const kx_batch_views *const *vs, const kx_step_views *const *svs, int stage,
+                                    cudaStream_t s) {
+    if (G < 1 || G > KX_MAX_GROUPS_STAGE) return cudaErrorInvalidValue;
+    kx_stage_groups L;
+    L.G = G;
+    int b0 = 0, nmax = 0;
+    for (int g = 0; g < G; ++g) {
+        if (ks[g]->stats) return cudaErrorInvalidValue;   // (quantum statistics: per-group stage only)
+        kx_stage_group &q = L.g[g];
+        q.n = ks[g]->n;
+        q.chunks = vs[g]->chunks;
+        q.path = ks[g]->precision;
+        q.b0 = b0;
+        q.E = ks[g]->d_E;
+        q.h = ks[g]->d_h;
+        q.v = *vs[g];
+        q.sv = *svs[g];
+        b0 += B[g];
+        nmax = std::max(nmax, ks[g]->n);
+    }
+    k_stage_grouped<<<b0, kx_fin_threads(nmax), 0, s>>>(L, stage);
+    return cudaGetLastError();
+}
+
 cudaError_t kx_launch_stage(const kx_kernel *k, int B, const kx_batch_views &v,
                             const kx_step_views &sv, int stage, cudaStream_t s, bool pdl) {
     auto *fn = k->precision != KX_FP32 ? k_stage<-1>

@@ -263,3 +263,13 @@ void kx_split_geometry(kx_kernel *k);   // GEMM shapes of the batched path from 
 cudaError_t kx_launch_batch_contract(const kx_kernel *k, int B, const kx_batch_views &v,
                                      const kx_inst_state *st, int stage, int *d_err, cudaStream_t s);
 void kx_batch_prepare();   // one-time kernel attribute setup (outside stream capture)
+// grouped (uneven batch) contraction of G split-path kernels: one gain-GEMM and
+// one loss-GEMM launch over all their work items, the exact loss per kernel
+cudaError_t kx_launch_batch_contract_grouped(int G, const kx_kernel *const *ks, const int *B,
+                                             const kx_batch_views *const *vs, const kx_inst_state *const *sts,
+                                             int stage, int *d_err, cudaStream_t s);
+// grouped stage: one launch over the instances of G kernels (block = instance,
+// threads = the largest grid of the group rounded up to whole warps)
+cudaError_t kx_launch_stage_grouped(int G, const kx_kernel *const *ks, const int *B,
+                                    const kx_batch_views *const *vs, const kx_step_views *const *svs, int stage,
+                                    cudaStream_t s);

@@ -271,3 +271,36 @@ def test_chebyshev_option_is_validated(env):
         with pytest.raises(kx.KxError) as ei:
             ctx.build_kernel(q, precision=prec, loss_terms=K)
         assert ei.value.code == code
+
+
+# ------------------------------------------------- uneven batch, grouped ---
+@pytest.mark.parametrize("loss_terms", [0, 16])
+def test_grouped_solve_equals_per_grid_solves(env, loss_terms):
+    """The uneven batch as one sequence of grouped launches (three grids, two
+    with more than one 128-instance tile, one with two i tiles): every
+    instance bit-identical to kx_solve on its own kernel, and sampled
+    instances of every grid within the mixed bound of the oracle's solve."""
+    kx, ctx, torch = env
+    rng = np.random.default_rng(90 + loss_terms)
+    sizes, Bs = (24, 40, 260), (130, 3, 2)
+    grids = [ki.log_grid(n, 1e-3, 1e2) for n in sizes]
+    f0 = [ki.batch_bimodal(rng, q, B) for q, B in zip(grids, Bs)]
+    sig = [10.0 ** rng.uniform(-1, 0.5, B) for B in Bs]
+    ks = [ctx.build_kernel(q, precision=kx.SPLIT_TF32, loss_terms=loss_terms) for q in grids]
+    par = dict(t_end=0.5, h0=1e-3, rtol=1e-6, atol=1e-12, l1_tol=0.0)
+    fd = [torch.as_tensor(f, device="cuda") for f in f0]
+    res = ctx.solve_grouped(ks, fd, sig, **par)
+    for g in range(3):
+        fa = torch.as_tensor(f0[g], device="cuda")
+        ra = ctx.solve(ks[g], fa, sig[g], **par)
+        np.testing.assert_array_equal(fd[g].cpu().numpy(), fa.cpu().numpy())
+        for b in range(Bs[g]):
+            assert res[g][b]["status"] == 0 and res[g][b]["steps"] == ra[b]["steps"]
+        W = oracle.kernel_tensor(grids[g]) if sizes[g] < 200 else None
+        if W is not None:
+            b = Bs[g] - 1
+            fo, ro = oracle.solve(grids[g], W, f0[g][b], oracle.M2_from_sigma(1.0, sig[g][b]), **par)
+            err = np.max(np.abs(fd[g].cpu().numpy()[b] - fo)) / np.max(fo)
+            assert err <= 1e-4, (g, err)
+    for k in ks:
+        k.release()
