@@ -148,6 +148,8 @@ size_t kx_views_bytes(const kx_kernel *k, int B) {
     s += kx_align(sizeof(float2) * B * n);           // td
     s += kx_align(kx_partial_bytes(k) * B * kx_partial_slots(k)); // partial
     s += kx_align(sizeof(double) * B);               // rfmax
+    s += kx_align(sizeof(double) * B);               // fsc
+    s += kx_align(sizeof(float) * B * 5 * KX_FIT_W); // fitp
     s += kx_align(sizeof(float4) * B);               // fit
     s += kx_align(sizeof(int) * B);                  // flags
     s += kx_align(sizeof(double) * B);               // M2
@@ -180,6 +182,8 @@ void kx_carve_views(const kx_kernel *k, int B, void *base, kx_batch_views *v) {
     v->td = (float2 *)p; p += kx_align(sizeof(float2) * B * n);
     v->partial = (double2 *)p; p += kx_align(kx_partial_bytes(k) * B * kx_partial_slots(k));
     v->rfmax = (double *)p; p += kx_align(sizeof(double) * B);
+    v->fsc = (double *)p; p += kx_align(sizeof(double) * B);
+    v->fitp = (float *)p; p += kx_align(sizeof(float) * B * 5 * KX_FIT_W);
     v->fit = (float4 *)p; p += kx_align(sizeof(float4) * B);
     v->flags = (int *)p; p += kx_align(sizeof(int) * B);
     v->M2 = (double *)p; p += kx_align(sizeof(double) * B);

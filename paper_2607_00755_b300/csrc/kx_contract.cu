@@ -419,14 +419,141 @@ struct kx_prep_pre {
     float Kf, hf;   // K and h_i as floats
     float4 lines;   // v.fit[b]
     bool have;
+    float2 next;    // FP32 dilute path, KX_LINE_NEXT: the line of the previous prep's fit
+    const double4_32a *ltab;   // log2 table (a shared-memory copy), or null: the global one
 };
 // idle: run by every thread just before the barrier that publishes 1/f_max and
 // log2 f_max, while threads 0 and 32 compute them (the other warps wait there)
-template <bool Q = false, typename Idle = kx_noop>
+// Line of the reference fit from its 5 block sums (sum w, w K, w K^2, w g, w K g):
+// weighted least squares, slope 0 when the spread of K is below 1% of its rms.
+__device__ __forceinline__ float2 kx_solve_line(const float *t) {
+    float slope = 0.f, icpt = 0.f;
+    if (t[0] > 0.f) {
+        const float det = t[0] * t[2] - t[1] * t[1];
+        if (det > 1e-4f * t[0] * t[2]) slope = (t[0] * t[4] - t[1] * t[3]) / det;
+        icpt = (t[3] - slope * t[1]) / t[0];
+    }
+    return make_float2(icpt, slope);
+}
+
+// The line of the previous prep's fit, from its per-warp partial sums
+// v.fitp[b][k][w] (k = the 5 sums, all KX_FIT_W slots, fixed order).
+__device__ __forceinline__ float2 kx_fit_line(const kx_batch_views &v, int b) {
+    float t[5];
+    const float *p = v.fitp + (size_t)b * 5 * KX_FIT_W;
+#pragma unroll
+    for (int k = 0; k < 5; ++k) {
+        float x = p[k * KX_FIT_W];
+        for (int w = 1; w < KX_FIT_W; ++w) x += p[k * KX_FIT_W + w];
+        t[k] = x;
+    }
+    return kx_solve_line(t);
+}
+
+// FP32 path (dilute) tables of one instance, block-wide (thread = grid point):
+//   l2'_j = log2(max(f_j, floor)) - e, 2^e the power of two of f_max (f_max =
+//          2^e m, 1 <= m < 2): the tables' scale (the elements' 2^(l2'_n + l2'_m)
+//          stay below 4; C_raw = M2 2^(2e) sum ...), exact in FP64;
+//   delta_j = log2 f_j - (a + b K_j), K = E - E_0: the deviation from a line
+//          in E, fitted to the absolute log2 f by least squares with weights
+//          h f 2^-e.  Any line cancels exactly in the elements' exponent
+//          differences (energy conservation, energy-linear interpolation); the
+//          fit only keeps the deviations small.
+// tl[j] = (l2'_j, delta_j); the contraction forms D_j = delta_(j+1) - delta_j
+// itself.  The line: KX_LINE_FIT a fit of this f (a new instance; one block
+// reduction); KX_LINE_NEXT the fit of the previous prep's f (pre.next, made
+// by the caller from the per-warp partials); KX_LINE_SAME the line of the
+// current tables (a re-prep of the same f builds the same tables).  This f's
+// fit sums are left as per-warp partials (v.fitp) for the next prep, so no
+// barrier closes the prep.  Also f_max, 2^-e, 2^e and the line used (v.fit.xy).
+template <typename Idle>
+__device__ __forceinline__ int kx_prep_block_f32(int n, double x, double Ei, double hi, double E0,
+                                                 const kx_batch_views &v, int b, unsigned long long key_in,
+                                                 int line_mode, Idle idle, const kx_prep_pre &pre) {
+    __shared__ unsigned long long s_key[32];
+    __shared__ float s_fit[5 * 32];
+    const int i = threadIdx.x, lane = i & 31, warp = i >> 5;
+    const bool in = i < n;
+    const bool nf = in && !isfinite(x);
+    idle();
+    int ex = 0;
+    double frx = 0.0;
+    if (in && !nf) kx_log2_parts(x > KX_LOG_FLOOR ? x : KX_LOG_FLOOR, ex, frx, pre.ltab ? pre.ltab : g_kx_log2_tab);
+    const unsigned long long key =
+        key_in != KX_KEY_NONE
+            ? key_in
+            : kx_block_max_key(nf ? KX_KEY_NONFINITE : (unsigned long long)__double_as_longlong(fabs(x)), s_key);
+    const int bad = key == KX_KEY_NONFINITE;
+    const double fm = bad ? INFINITY : __longlong_as_double((long long)key);
+    const bool ok = fm > 0.0 && !bad;
+    // the power of two of max(f_max, floor): 2^e and 2^-e exactly (bit patterns)
+    const unsigned long long kb = (unsigned long long)__double_as_longlong(fm > KX_LOG_FLOOR ? fm : KX_LOG_FLOOR);
+    const int e = ok ? (int)((kb >> 52) & 0x7ff) - 1023 : 0;
+    const double sc = __longlong_as_double((long long)(e + 1023) << 52);
+    const double rsc = __longlong_as_double((long long)(1023 - e) << 52);
+    const double K = pre.have ? pre.K : (in ? Ei - E0 : 0.0);
+    const float Kf = pre.have ? pre.Kf : (float)K;
+    const double l2a = (in && ok) ? (double)ex + frx : 0.0;            // log2 f
+    const double l2s = (in && ok) ? (double)(ex - e) + frx : -2000.0;  // log2 f - e
+    const float w = (in && ok && x > 0.0) ? (pre.have ? pre.hf : (float)hi) * (float)(x * rsc) : 0.f;
+    const float g = (float)l2a;
+    float sf[5] = {w, w * Kf, w * Kf * Kf, w * g, w * Kf * g};
+#pragma unroll
+    for (int k = 0; k < 5; ++k)
+#pragma unroll
+        for (int off = 16; off; off >>= 1) sf[k] += __shfl_xor_sync(0xffffffffu, sf[k], off);
+    float2 line;
+    if (line_mode == KX_LINE_FIT) {
+        if (lane == 0)
+#pragma unroll
+            for (int k = 0; k < 5; ++k) s_fit[k * 32 + warp] = sf[k];
+        __syncthreads();
+        float t[5];
+        const int nw = blockDim.x >> 5;
+#pragma unroll
+        for (int k = 0; k < 5; ++k) {
+            float y = s_fit[k * 32];
+            for (int w2 = 1; w2 < nw; ++w2) y += s_fit[k * 32 + w2];
+            t[k] = y;
+        }
+        line = kx_solve_line(t);
+    } else if (line_mode == KX_LINE_NEXT) {
+        line = pre.next;
+    } else {
+        const float4 cur = pre.have ? pre.lines : v.fit[b];
+        line = make_float2(cur.x, cur.y);
+    }
+    const double del = (in && ok) ? l2a - ((double)line.x + (double)line.y * K) : 0.0;
+    float2 *tl = v.tl + (long long)b * (n + 4);
+    if (in) tl[i] = make_float2((float)l2s, (float)del);
+    if (i < 4) tl[n + i] = make_float2(-2000.f, 0.f);
+    // every slot is written (zeros past the block's warps), whatever the block size
+    float *fp = v.fitp + (size_t)b * 5 * KX_FIT_W;
+    if (lane == 0 && warp < KX_FIT_W)
+#pragma unroll
+        for (int k = 0; k < 5; ++k) fp[k * KX_FIT_W + warp] = sf[k];
+    if (i == 0)
+        for (int w2 = (int)(blockDim.x >> 5); w2 < KX_FIT_W; ++w2)
+#pragma unroll
+            for (int k = 0; k < 5; ++k) fp[k * KX_FIT_W + w2] = 0.f;
+    if (i == 0) {
+        v.fmax[b] = fm;
+        v.rfmax[b] = ok ? rsc : 0.0;
+        v.fsc[b] = ok ? sc : 0.0;
+        v.fit[b] = make_float4(line.x, line.y, 0.f, 0.f);
+    }
+    return bad;
+}
+
+// F32: the FP32 dilute branch may be taken (false in the kernels of the other paths)
+template <bool Q = false, typename Idle = kx_noop, bool F32 = true>
 __device__ __forceinline__ int kx_prep_block(int n, int path, double x, double Ei, double hi, double E0,
                              const kx_batch_views &v, int b, double *smem,
                              unsigned long long key_in = KX_KEY_NONE, int line_mode = KX_LINE_FIT,
-                             Idle idle = Idle(), kx_prep_pre pre = kx_prep_pre{0.0, 0.f, 0.f, {}, false}) {
+                             Idle idle = Idle(), kx_prep_pre pre = kx_prep_pre{0.0, 0.f, 0.f, {}, false, {}, nullptr}) {
+    if constexpr (!Q && F32) {
+        if (path == KX_FP32) return kx_prep_block_f32(n, x, Ei, hi, E0, v, b, key_in, line_mode, idle, pre);
+    }
     __shared__ unsigned long long s_key[32];
     __shared__ float s_fit[5 * 32];
     __shared__ double s_scale[3];   // exponent and fraction of log2 f_max, 1 / f_max
@@ -464,6 +591,7 @@ __device__ __forceinline__ int kx_prep_block(int n, int path, double x, double E
         const double rfm = (fm > 0.0 && !bad) ? 1.0 / fm : 0.0;
         v.fmax[b] = fm;
         v.rfmax[b] = rfm;
+        v.fsc[b] = fm;   // the tables' scale
         s_scale[2] = rfm;
     }
     if (threadIdx.x == tlog) {
@@ -877,9 +1005,17 @@ __device__ __forceinline__ bool kx_stream_tables(int n, int B, int b0, const flo
         const int b = b0 + bb;
         for (int t = threadIdx.x; t < n + 4; t += blockDim.x)
             s_l[bb][t] = act[bb] ? tl[(long long)b * (n + 4) + t] : make_float2(-2000.f, 0.f);
+        // (delta_j - D_j, D_j), D_j = delta_(j+1) - delta_j (0 at the last point)
         if constexpr (WITH_D)
-            for (int t = threadIdx.x; t < n; t += blockDim.x)
-                s_d[bb][t] = act[bb] ? td[(long long)b * n + t] : make_float2(0.f, 0.f);
+            for (int t = threadIdx.x; t < n; t += blockDim.x) {
+                float2 d = make_float2(0.f, 0.f);
+                if (act[bb]) {
+                    const float2 a0 = tl[(long long)b * (n + 4) + t], a1 = tl[(long long)b * (n + 4) + t + 1];
+                    const float D = t + 1 < n ? a1.y - a0.y : 0.f;
+                    d = make_float2(a0.y - D, D);
+                }
+                s_d[bb][t] = d;
+            }
     }
     return true;
 }
@@ -1463,6 +1599,10 @@ __device__ __forceinline__ kx_row_out kx_combine_project(int n, int chunks, int 
                                          double *sm) {
     const int i = threadIdx.x, T = blockDim.x;
     const double fm = v.fmax[b], rfm = v.rfmax[b], M2 = v.M2[b];
+    // FP32 path: the tables' scale (C_raw = M2 scale^2 sum); xi = |f| / scale
+    // with the support threshold eps_supp f_max / scale (xi's scale cancels in
+    // the projection); the other paths: scale = f_max
+    const double fsc = path == KX_FP32 ? v.fsc[b] : fm;
     double G = 0.0, L = 0.0;
     if (i < n && path == KX_FP32) {
         // double-float task partials (hi, lo), four independent double-float
@@ -1537,7 +1677,7 @@ __device__ __forceinline__ kx_row_out kx_combine_project(int n, int chunks, int 
     double Craw;
     // FP32 path: G holds sum S (f_n f_m - f_i f_t) / f_max^2; the FP64 and batched
     // paths hold the gain G and the loss rate L
-    if (path == KX_FP32) Craw = M2 * (fm * fm * G);
+    if (path == KX_FP32) Craw = M2 * (fsc * fsc * G);
     else Craw = M2 * (G - fi * L);
     if (i >= n) Craw = 0.0;
     kx_row_out r;
@@ -1549,7 +1689,8 @@ __device__ __forceinline__ kx_row_out kx_combine_project(int n, int chunks, int 
     double xi = 0.0;
     if (i < n && fm > 0.0) {
         double q = fabs(fi) * rfm;
-        xi = q > KX_EPS_SUPP ? q : 0.0;
+        const double thr = path == KX_FP32 ? KX_EPS_SUPP * (fm * rfm) : KX_EPS_SUPP;
+        xi = q > thr ? q : 0.0;
     }
     const double hxi = hi * xi, hEx = hxi * Ei, hC = hi * Craw;
     const double s[5] = {hxi, hEx, hEx * Ei, hC, hC * Ei};
@@ -1819,13 +1960,15 @@ cudaError_t kx_launch_mbfit(const kx_kernel *k, int nb, const double *f, double 
 //          reject, next h, MB stopping test, prep(next f).
 // One instance's stage in one block (thread = grid point; smem: 5 blockDim.x +
 // 8 doubles).  Every exit is block-uniform.
-template <bool Q>
+template <bool Q, bool F32 = true>
 __device__ __forceinline__ void kx_stage_body(int b, int n, int chunks, int path, const double *__restrict__ E,
                               const double *__restrict__ h, kx_batch_views v,
                               kx_step_views sv, int stage, long long max_attempts,
                               double *smem) {
     __shared__ unsigned long long s_keys[3 * 32];
     __shared__ double s_env[KX_MAX_SRC];
+    __shared__ float2 s_next;   // FP32 dilute path: the line of the previous prep's fit
+    __shared__ double4_32a s_ltab[F32 ? 256 : 1];   // FP32 dilute path: the log2 table
     const int i = threadIdx.x;
     const bool in = i < n;
     // The grid and the source rows do not change while a graph of attempts
@@ -1837,6 +1980,12 @@ __device__ __forceinline__ void kx_stage_body(int b, int n, int chunks, int path
     pre.Kf = (float)pre.K;
     pre.hf = (float)hi;
     pre.have = path == KX_FP32;
+    pre.ltab = nullptr;
+    if constexpr (F32 && !Q) {
+        // the log2 table is constant: copied before the wait for the predecessor
+        for (int t = threadIdx.x; t < 256; t += blockDim.x) s_ltab[t] = g_kx_log2_tab[t];
+        pre.ltab = s_ltab;   // (read by the prep, after the barriers that follow)
+    }
     const kx_src_dev &src = sv.src[b];
     const int n_src = src.n_src;
     double shp[KX_MAX_SRC];
@@ -1856,7 +2005,8 @@ __device__ __forceinline__ void kx_stage_body(int b, int n, int chunks, int path
     // bit 2: a contraction's bounded device wait expired (checked, and the
     // instance stopped, before flag_in is used as the non-finite flag)
     const int flag_in = v.flags[b] | (*v.err ? 4 : 0);
-    pre.lines = path == KX_FP32 ? v.fit[b] : make_float4(0.f, 0.f, 0.f, 0.f);
+    // (the quantum path's lines; the dilute FP32 path takes its line from s_next)
+    pre.lines = (Q && path == KX_FP32) ? v.fit[b] : make_float4(0.f, 0.f, 0.f, 0.f);
     // Every thread takes its copy of the instance state here, before the first
     // block barrier: thread 0 rewrites the state at the end of the stage, and a
     // warp that read it after that write could disagree with the others on
@@ -1871,6 +2021,10 @@ __device__ __forceinline__ void kx_stage_body(int b, int n, int chunks, int path
     const bool envw = wid == lastw && lane < n_src;   // the lanes that own the envelopes
     const int env_ok = st->env_ok;
     const double env_t = st->env_t, env_mine = envw ? st->env[lane] : 0.0;
+    // the line for this stage's prep, from the previous prep's per-warp fit sums,
+    // on the last warp (a warp without grid points when the launch adds one);
+    // published by the barriers before the prep
+    if (!Q && path == KX_FP32 && wid == lastw && lane == 0) s_next = kx_fit_line(v, b);
     // the row combine and the projection first: their loads do not wait for
     // the state (a finished instance computes them in vain and writes nothing)
     const double fcur = stage == 1 ? f0 : fpv;
@@ -1974,7 +2128,9 @@ __device__ __forceinline__ void kx_stage_body(int b, int n, int chunks, int path
                 }
             }
         };
-        int bad2 = kx_prep_block<Q>(n, path, in ? fpi : 0.0, Ei, hi, E0, v, b, smem, keys[1], KX_LINE_NEXT, idle, pre);
+        pre.next = s_next;
+        int bad2 = kx_prep_block<Q, decltype(idle), F32>(n, path, in ? fpi : 0.0, Ei, hi, E0, v, b, smem, keys[1],
+                                                         KX_LINE_NEXT, idle, pre);
         if (threadIdx.x == 0) v.flags[b] = bad2;
         return;
     }
@@ -2096,8 +2252,9 @@ __device__ __forceinline__ void kx_stage_body(int b, int n, int chunks, int path
             }
         }
     };
-    int bad2 = kx_prep_block<Q>(n, path, in ? fnew : 0.0, Ei, hi, E0, v, b, smem, accept ? keys[1] : keys[2],
-                                KX_LINE_NEXT, idle, pre);
+    pre.next = s_next;
+    int bad2 = kx_prep_block<Q, decltype(idle), F32>(n, path, in ? fnew : 0.0, Ei, hi, E0, v, b, smem,
+                                                     accept ? keys[1] : keys[2], KX_LINE_NEXT, idle, pre);
     if (threadIdx.x == 0) v.flags[b] = bad2;
 }
 
@@ -2111,7 +2268,8 @@ __global__ void __launch_bounds__(KX_FIN_THREADS)
             kx_batch_views v, kx_step_views sv, int stage, long long max_attempts) {
     __shared__ double smem[5 * KX_FIN_THREADS + 8];
     kx_pdl_trigger();   // (the body waits for the predecessor after its constant loads)
-    kx_stage_body<Q>(blockIdx.x, n, chunks, PATH >= 0 ? PATH : path, E, h, v, sv, stage, max_attempts, smem);
+    kx_stage_body<Q, PATH == KX_FP32>(blockIdx.x, n, chunks, PATH >= 0 ? PATH : path, E, h, v, sv, stage,
+                                      max_attempts, smem);
 }
 
 // Grouped stage (the uneven batch): block b of the launch is instance b - b0_g
@@ -2137,8 +2295,8 @@ __global__ void __launch_bounds__(KX_FIN_THREADS) k_stage_grouped(const kx_stage
     int g = 0;
     while (g + 1 < G.G && (int)blockIdx.x >= G.g[g + 1].b0) ++g;
     const kx_stage_group &q = G.g[g];
-    kx_stage_body<false>((int)blockIdx.x - q.b0, q.n, q.chunks, q.path, q.E, q.h, q.v, q.sv, stage,
-                         q.sv.max_attempts, smem);
+    kx_stage_body<false, false>((int)blockIdx.x - q.b0, q.n, q.chunks, q.path, q.E, q.h, q.v, q.sv, stage,
+                                q.sv.max_attempts, smem);
 }
 
 cudaError_t kx_launch_stage_grouped(int G, const kx_kernel *const *ks, const int *B,
@@ -2170,7 +2328,11 @@ cudaError_t kx_launch_stage(const kx_kernel *k, int B, const kx_batch_views &v,
                             const kx_step_views &sv, int stage, cudaStream_t s, bool pdl) {
     auto *fn = k->precision != KX_FP32 ? k_stage<-1>
                                        : (k->stats ? k_stage<KX_FP32, true> : k_stage<KX_FP32>);
-    return kx_launch_ex(fn, dim3(B), dim3(kx_fin_threads(k->n)), 0, s, pdl, k->n, v.chunks,
+    // the FP32 path's stage takes one more warp, without grid points: it makes
+    // the source envelopes and the fit line off the points' critical path
+    int threads = kx_fin_threads(k->n);
+    if (k->precision == KX_FP32 && threads + 32 <= KX_FIN_THREADS) threads += 32;
+    return kx_launch_ex(fn, dim3(B), dim3(threads), 0, s, pdl, k->n, v.chunks,
                         (int)k->precision, (const double *)k->d_E, (const double *)k->d_h, v, sv,
                         stage, sv.max_attempts);
 }

@@ -23,6 +23,7 @@
 #define KX_T32 256            // threads per FP32 contraction block
 #define KX_BINS 2368          // equal-work bins of the FP32 contraction (148 SMs x 16 warps)
 #define KX_FIN_THREADS 512    // finalize / stage kernels: one block per instance, thread = grid point
+#define KX_FIT_W 17           // per-warp partial slots of the FP32 path's line fit (up to 17 warps)
 #define KX_WAIT_CYCLES_MAX (4ll << 30)   // longest bounded device wait (the kernels' own limit, ~2 s)
 
 struct kx_gl_nodes {
@@ -162,7 +163,9 @@ struct kx_batch_views {
                            // (1: the whole GPU; the server shares it among its groups)
     double2 *partial;      // [B][n][chunks]  (FP32 path: float2 (hi, lo) task partials, [B][chunks])
     const int2 *rtask;     // FP32 path: [n] (first partial slot i, tasks) per row; slot k at k n + i
-    double *rfmax;         // [B]          1 / f_max
+    double *rfmax;         // [B]          1 / scale of the tables (FP32 dilute path: 2^-e, f_max = 2^e m)
+    double *fsc;           // [B]          scale of the FP32 path's tables: 2^e (dilute) or f_max (quantum)
+    float *fitp;           // [B][5][KX_FIT_W] FP32 dilute path: per-warp partial sums of the line fit
     float4 *fit;           // [B]          FP32 path: reference lines (icpt, slope) of the current
                            //              tables and of the fit of their f
     int *flags;            // [B] non-finite flags

@@ -21,14 +21,17 @@
 
 // log2(x) = e + frac for normal x > 0: e the unbiased exponent, frac =
 // log2(m) for the significand m in [1, 2) (frac in [0, 1], absolute error
-// ~1e-17).  Callers pass x >= 1e-300 (normal, positive, finite).
-__device__ __forceinline__ void kx_log2_parts(double x, int &e, double &frac) {
+// ~1e-17).  Callers pass x >= 1e-300 (normal, positive, finite).  tab: the
+// table, or a copy of it in shared memory (the stage kernels take one before
+// they wait for their predecessor, so the lookup is not an L2 round trip).
+__device__ __forceinline__ void kx_log2_parts(double x, int &e, double &frac,
+                                              const double4_32a *tab = g_kx_log2_tab) {
     const long long bits = __double_as_longlong(x);
     e = (int)((bits >> 52) & 0x7ff) - 1023;
     const long long mb = bits & 0x000fffffffffffffLL;
     const int k = (int)(mb >> 44);
     const double m = __longlong_as_double(mb | 0x3ff0000000000000LL);
-    const double4_32a t = g_kx_log2_tab[k];
+    const double4_32a t = tab[k];
     // r = (m - F)/F: m - F is exact (Sterbenz), 0 <= r < 1/256 (r = 0 at m = F,
     // so log2 of a power of two is exact)
     const double r = (m - t.x) * t.y;
