@@ -133,9 +133,14 @@ __device__ __forceinline__ void kx_block_sum(double (&v)[K], double *smem) {
 // A column costs nw + 5 FP64 adds on one warp, against 10 per value for a
 // per-warp butterfly (FP64 is a reduced-rate pipe here).  sm holds K*T + K
 // doubles; returns after the barrier that publishes the totals.
+// tv: the caller's promise that threads tv .. T - 1 hold +0.0 in every column
+// (a multiple of 32, default T): only the first tv / 32 warps add, and they
+// skip those zeros (x + 0.0 == x, so the totals do not change).
 template <int K>
-__device__ __forceinline__ void kx_block_cols(const double (&v)[K], double *sm) {
-    const int T = blockDim.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = T >> 5;
+__device__ __forceinline__ void kx_block_cols(const double (&v)[K], double *sm, int tv = 0) {
+    const int T = blockDim.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    if (tv <= 0 || tv > T) tv = T;
+    const int nw = tv >> 5;
 #pragma unroll
     for (int k = 0; k < K; ++k) sm[k * T + tid] = v[k];
     __syncthreads();
@@ -144,7 +149,7 @@ __device__ __forceinline__ void kx_block_cols(const double (&v)[K], double *sm) 
         const int k2 = k + nw;
         const bool two = k2 < K;
         double x = sm[k * T + lane], y = two ? sm[k2 * T + lane] : 0.0;
-        for (int j = lane + 32; j < T; j += 32) {
+        for (int j = lane + 32; j < tv; j += 32) {
             x += sm[k * T + j];
             if (two) y += sm[k2 * T + j];
         }
@@ -163,8 +168,8 @@ __device__ __forceinline__ void kx_block_cols(const double (&v)[K], double *sm) 
 
 // Block sums of K doubles via kx_block_cols; all threads receive them.
 template <int K>
-__device__ __forceinline__ void kx_block_sum_t(double (&v)[K], double *sm) {
-    kx_block_cols<K>(v, sm);
+__device__ __forceinline__ void kx_block_sum_t(double (&v)[K], double *sm, int tv = 0) {
+    kx_block_cols<K>(v, sm, tv);
 #pragma unroll
     for (int k = 0; k < K; ++k) v[k] = sm[K * blockDim.x + k];
     __syncthreads();
@@ -493,9 +498,14 @@ __device__ __forceinline__ int kx_prep_block_f32(int n, double x, double Ei, dou
     const double rsc = __longlong_as_double((long long)(1023 - e) << 52);
     const double K = pre.have ? pre.K : (in ? Ei - E0 : 0.0);
     const float Kf = pre.have ? pre.Kf : (float)K;
-    const double l2a = (in && ok) ? (double)ex + frx : 0.0;            // log2 f
-    const double l2s = (in && ok) ? (double)(ex - e) + frx : -2000.0;  // log2 f - e
-    const float w = (in && ok && x > 0.0) ? (pre.have ? pre.hf : (float)hi) * (float)(x * rsc) : 0.f;
+    // (threads past n skip the FP64 arithmetic, a whole warp when the launch adds one)
+    double l2a = 0.0, l2s = -2000.0;   // log2 f, log2 f - e
+    float w = 0.f;
+    if (in && ok) {
+        l2a = (double)ex + frx;
+        l2s = (double)(ex - e) + frx;
+        if (x > 0.0) w = (pre.have ? pre.hf : (float)hi) * (float)(x * rsc);
+    }
     const float g = (float)l2a;
     float sf[5] = {w, w * Kf, w * Kf * Kf, w * g, w * Kf * g};
 #pragma unroll
@@ -523,9 +533,11 @@ __device__ __forceinline__ int kx_prep_block_f32(int n, double x, double Ei, dou
         const float4 cur = pre.have ? pre.lines : v.fit[b];
         line = make_float2(cur.x, cur.y);
     }
-    const double del = (in && ok) ? l2a - ((double)line.x + (double)line.y * K) : 0.0;
     float2 *tl = v.tl + (long long)b * (n + 4);
-    if (in) tl[i] = make_float2((float)l2s, (float)del);
+    if (in) {
+        const double del = ok ? l2a - ((double)line.x + (double)line.y * K) : 0.0;
+        tl[i] = make_float2((float)l2s, (float)del);
+    }
     if (i < 4) tl[n + i] = make_float2(-2000.f, 0.f);
     // every slot is written (zeros past the block's warps), whatever the block size
     float *fp = v.fitp + (size_t)b * 5 * KX_FIT_W;
@@ -1674,12 +1686,18 @@ __device__ __forceinline__ kx_row_out kx_combine_project(int n, int chunks, int 
             L += x.y;
         }
     }
-    double Craw;
+    // The FP64 pipe runs at a small fraction of the FP32 rate on this part, and
+    // a warp's FP64 instructions occupy its sub-partition's pipe whether or not
+    // its lanes hold grid points: threads past n (a whole warp when the launch
+    // adds one) skip the FP64 arithmetic below on a warp-uniform branch.
+    const bool wpts = (i & ~31) < n;   // this warp holds grid points
+    double Craw = 0.0;
     // FP32 path: G holds sum S (f_n f_m - f_i f_t) / f_max^2; the FP64 and batched
     // paths hold the gain G and the loss rate L
-    if (path == KX_FP32) Craw = M2 * (fsc * fsc * G);
-    else Craw = M2 * (G - fi * L);
-    if (i >= n) Craw = 0.0;
+    if (i < n) {
+        if (path == KX_FP32) Craw = M2 * (fsc * fsc * G);
+        else Craw = M2 * (G - fi * L);
+    }
     kx_row_out r;
     r.Craw = Craw;
     r.Cproj = Craw;
@@ -1692,13 +1710,21 @@ __device__ __forceinline__ kx_row_out kx_combine_project(int n, int chunks, int 
         const double thr = path == KX_FP32 ? KX_EPS_SUPP * (fm * rfm) : KX_EPS_SUPP;
         xi = q > thr ? q : 0.0;
     }
-    const double hxi = hi * xi, hEx = hxi * Ei, hC = hi * Craw;
-    const double s[5] = {hxi, hEx, hEx * Ei, hC, hC * Ei};
-    // five block sums (column form); one thread solves the 2x2 system
-    kx_block_cols<5>(s, sm);
-    {
-        // every thread solves the 2x2 system from the five sums (the same
-        // arithmetic everywhere; no broadcast barrier).  sm[5T .. 5T + 4] is not
+    double s[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
+    if (wpts) {
+        const double hxi = hi * xi, hEx = hxi * Ei, hC = hi * Craw;
+        s[0] = hxi;
+        s[1] = hEx;
+        s[2] = hEx * Ei;
+        s[3] = hC;
+        s[4] = hC * Ei;
+    }
+    // five block sums (column form) over the warps that hold grid points
+    kx_block_cols<5>(s, sm, (n + 31) & ~31);
+    if (wpts) {
+        // every thread of those warps solves the 2x2 system from the five sums
+        // (the same arithmetic everywhere; no broadcast barrier); a thread past n
+        // has xi = 0 and keeps C_proj = C_raw = 0.  sm[5T .. 5T + 4] is not
         // written again before the block's next barrier.
         const double *t = sm + 5 * T;
         const double t0 = t[0], t1 = t[1], t2 = t[2], t3 = t[3], t4 = t[4];
@@ -1715,8 +1741,8 @@ __device__ __forceinline__ kx_row_out kx_combine_project(int n, int chunks, int 
         r.alpha = al;
         r.beta = be;
         r.singular = sg;
+        r.Cproj = Craw - xi * (al + be * Ei);
     }
-    r.Cproj = Craw - xi * (r.alpha + r.beta * Ei);
     return r;
 }
 
@@ -1861,8 +1887,13 @@ __device__ __forceinline__ void kx_mb_fit_block(int n, double fi, double Ei, dou
     const int T = blockDim.x;
     const bool lead = threadIdx.x == 0;
     double *ctl = sm + 4 * T;   // [0] N0, [1] 1/T, [2] stop, [3] ebar
-    const double s0[2] = {in ? hi * fi : 0.0, in ? hi * Ei * fi : 0.0};
-    kx_block_cols<2>(s0, sm);
+    const int tv = (n + 31) & ~31;   // the threads that hold grid points, by warps
+    double s0[2] = {0.0, 0.0};
+    if (in) {
+        s0[0] = hi * fi;
+        s0[1] = hi * Ei * fi;
+    }
+    kx_block_cols<2>(s0, sm, tv);
     double u = 0.0, lo = log(1e-12), hi_u = log(1e12), ebar = 0.0, Tc = 0.0;
     if (lead) {
         const double N0 = sm[2 * T];
@@ -1888,9 +1919,14 @@ __device__ __forceinline__ void kx_mb_fit_block(int n, double fi, double Ei, dou
     }
     for (int it = 0; it < 200; ++it) {
         const double beta = ctl[1];
-        const double wgt = in ? hi * kx_exp(-(Ei - E0) * beta) : 0.0;
-        const double s[3] = {wgt, wgt * Ei, wgt * Ei * Ei};
-        kx_block_cols<3>(s, sm);
+        double s[3] = {0.0, 0.0, 0.0};
+        if (in) {
+            const double wgt = hi * kx_exp(-(Ei - E0) * beta);
+            s[0] = wgt;
+            s[1] = wgt * Ei;
+            s[2] = s[1] * Ei;
+        }
+        kx_block_cols<3>(s, sm, tv);
         if (lead) {
             // g = <E> - ebar = gs / s0 and Var(E) = vs / s0^2, so the Newton step
             // in u = ln T, -g T / Var(E), is -gs s0 T / vs (one division)
@@ -1912,12 +1948,16 @@ __device__ __forceinline__ void kx_mb_fit_block(int n, double fi, double Ei, dou
     }
     // final weights at T = exp(u): f_MB = N0 w / sum h w, L1 = sum h |f - f_MB| / N0
     const double beta = ctl[1];
-    const double w = in ? kx_exp(-(Ei - E0) * beta) : 0.0;
-    double s1[1] = {in ? hi * w : 0.0};
-    kx_block_sum_t<1>(s1, sm);
-    const double fmb = N0 * w / s1[0];
-    double s2[1] = {in ? hi * fabs(fi - fmb) : 0.0};
-    kx_block_sum_t<1>(s2, sm);
+    double w = 0.0;
+    double s1[1] = {0.0};
+    if (in) {
+        w = kx_exp(-(Ei - E0) * beta);
+        s1[0] = hi * w;
+    }
+    kx_block_sum_t<1>(s1, sm, tv);
+    double s2[1] = {0.0};
+    if (in) s2[0] = hi * fabs(fi - N0 * w / s1[0]);
+    kx_block_sum_t<1>(s2, sm, tv);
     out[0] = 1.0 / beta;
     out[1] = log(N0 / s1[0]) + E0 * beta;
     out[2] = s2[0] / N0;
@@ -2072,14 +2112,18 @@ __device__ __forceinline__ void kx_stage_body(int b, int n, int chunks, int path
     if (envw) s_env[lane] = (env_ok && env_t == tS) ? env_mine : envelope(tS);
     const double C = sv.project ? r.Cproj : r.Craw;
     __syncthreads();   // publishes s_env
-    double Si = 0.0;
+    // (threads past n skip the FP64 arithmetic: they hold kv = 0 and f = 0)
+    double kv = 0.0;
+    if (in) {
+        double Si = 0.0;
 #pragma unroll
-    for (int k = 0; k < KX_MAX_SRC; ++k)
-        if (k < n_src) Si += s_env[k] * shp[k];
-    double kv = in ? C + Si : 0.0;
-    if (sv.hscale != 1.0) kv *= sv.hscale;   // d/du = (C + S) / H (expanding universe)
+        for (int k = 0; k < KX_MAX_SRC; ++k)
+            if (k < n_src) Si += s_env[k] * shp[k];
+        kv = C + Si;
+        if (sv.hscale != 1.0) kv *= sv.hscale;   // d/du = (C + S) / H (expanding universe)
+    }
     if (stage == 1) {
-        const double fpi = f0 + htry * kv;
+        const double fpi = in ? f0 + htry * kv : 0.0;
         // one reduction for both flags (2 = non-finite, 1 = negative) and for
         // max |f_p| of the next prep
         unsigned long long keys[2] = {
@@ -2137,7 +2181,7 @@ __device__ __forceinline__ void kx_stage_body(int b, int n, int chunks, int path
     // stage 2: one reduction for the flags and the error norm (keys ordered
     // non-finite > negative > the bits of err >= 0), and for max |f_c| and
     // max |f| (the next prep takes the one the step decision keeps)
-    const double fci = f0 + 0.5 * htry * (k1v + kv);
+    const double fci = in ? f0 + 0.5 * htry * (k1v + kv) : 0.0;
     // The error ratio only decides acceptance and scales h.  On the FP32 path,
     // whose C carries FP32 rounding (~1e-7 relative) anyway, it is divided in
     // FP32 from the FP64 difference and scale (an FP64 division is a long chain
