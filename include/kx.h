@@ -453,13 +453,20 @@ int kx_source_condensate(int n, const double *q, double a, double mass, double m
                          double gamma_n, double *shape, double *rate);
 
 /* ----------------------------------------------------------- diagnostics */
-/* Self-check of the library's own table-driven FP64 log2 and exp (the stage
- * kernels use them for the per-point log of f, the source envelopes and the
- * Maxwell-Boltzmann fit; they have no counterpart in the paper).  For n
- * arguments x_dev (device, n doubles), writes out_dev[2i] = the library's
- * value and out_dev[2i+1] = CUDA's log2 (which = 0) or exp (which = 1) of
- * x_dev[i].  log2 takes x >= 1e-300.  Enqueues on the context's stream.
- * KX_EINVAL for bad arguments, KX_ECUDA if the launch fails. */
+/* Self-check of the library's own arithmetic helpers (the stage kernels use
+ * them for the per-point log of f, the source envelopes, the Maxwell-Boltzmann
+ * fit and the FP32 path's integer-pipe conversions; they have no counterpart
+ * in the paper).  For n arguments x_dev (device, n doubles), writes
+ * out_dev[2i] = the library's value and out_dev[2i+1] = CUDA's value, for
+ *   which = 0: the table-driven FP64 log2 (x >= 1e-300);
+ *   which = 1: the FP64 exp;
+ *   which = 2: the double-float log2 of the FP32 path's tables, e + hi + lo
+ *              (positive normal x);
+ *   which = 3: double -> float rounding on the integer pipe (as a double;
+ *              the library flushes results below 2^-126 to zero);
+ *   which = 4: float -> double on the integer pipe, of the float nearest x.
+ * Enqueues on the context's stream.  KX_EINVAL for bad arguments, KX_ECUDA
+ * if the launch fails. */
 int kx_math_check(kx_ctx *ctx, int which, int n, const double *x_dev, double *out_dev);
 
 /* Self-check of the bounded device waits (no counterpart in the paper): every
@@ -477,8 +484,11 @@ int kx_wait_check(kx_ctx *ctx, long long cycles, int *expired_host);
  * choice (which is otherwise timed once per (device, n, batch) before the
  * first launch): 0 = one instance per pass, 1 = two per pass (batch >= 2),
  * 2 = four per pass, bulk-copy staged (n > 160, batch >= 4), 3 = four per
- * pass, register pipeline (batch >= 4); -1 forgets the
- * pinned or tuned choice.  The pin applies to whole-GPU launches and to the
+ * pass, register pipeline (batch >= 4), 4 = the whole batch per pass with
+ * every warp's share of the tables staged in shared memory before the
+ * contraction waits for its predecessor (batch <= 4; used where the kernel's
+ * bins fit in shared memory and the launch has the whole GPU, else the
+ * default rule applies); -1 forgets the pinned or tuned choice.  The pin applies to whole-GPU launches and to the
  * serving groups' launches on a share of the GPU alike (the autotuner keys its
  * choice by that share as well).  All variants give bit-identical results; this is
  * for reproducible timing and for tests.  KX_EINVAL for a variant that does

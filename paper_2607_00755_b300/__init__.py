@@ -424,7 +424,7 @@ class Context:
         return out
 
     def set_stream_variant(self, n, batch, variant):
-        """Pin (0, 1, 2) or forget (-1) the streaming variant for (n, batch)."""
+        """Pin (0 .. 4) or forget (-1) the streaming variant for (n, batch)."""
         rc = self.lib.kx_set_stream_variant(self.h, int(n), int(batch), int(variant))
         if rc:
             raise self.error(rc, "kx_set_stream_variant")
@@ -439,8 +439,9 @@ class Context:
         return var.value, bool(tun.value)
 
     def math_check(self, which, x):
-        """(library value, CUDA value) of log2 (which=0) or exp (which=1) of x
-        (a CUDA float64 tensor); returns a [n, 2] tensor."""
+        """(library value, CUDA value) of x (a CUDA float64 tensor) for the
+        helper `which` (0 log2, 1 exp, 2 double-float log2, 3 double -> float,
+        4 float -> double of the float nearest x); returns a [n, 2] tensor."""
         import torch
         out = torch.empty((x.numel(), 2), dtype=torch.float64, device=x.device)
         rc = self.lib.kx_math_check(self.h, int(which), x.numel(), _dptr(x), _dptr(out))

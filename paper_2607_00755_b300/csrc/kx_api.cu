@@ -459,6 +459,12 @@ static int kx_build_kernel_ex(kx_ctx *ctx, const kx_grid_desc *d, kx_kernel **ou
             }
         }
         bins[KX_BINS] = (int)task.size();
+        k->bin_units = 0;
+        for (int b = 0; b < KX_BINS; ++b) {
+            int nu = 0;
+            for (int t = bins[b]; t < bins[b + 1]; ++t) nu += task[t].z - task[t].y;
+            k->bin_units = std::max(k->bin_units, nu);
+        }
         // partial slots: MT per row (the largest task count, rounded up to
         // even), slot k of row i at k n + i: a row's slots sit at a fixed
         // stride and the rows of one slot index are adjacent (coalesced reads
@@ -891,26 +897,91 @@ static int kx_solve_run(kx_ctx *ctx, const kx_kernel *k, int B, const kx_run &r,
     const auto t_start = std::chrono::steady_clock::now();
     KX_CUDA_TRY(ctx, kx_launch_prep(k, B, r.sv.f, r.v, r.sv.st, s));
     ctx->launches += 1;
-    if (kx_tune_contraction(k, B, r.sv.f, r.v, r.sv.st, s, &ctx->launches))
+    // The FP32 path's streaming variant: tuned here, on this solve's own
+    // attempt graphs (one captured per candidate, replayed in turn on real
+    // attempts, the fastest kept), when the size has no choice yet.  The
+    // variants give the same bits, so the trajectory does not depend on the
+    // order of the replays.  A stand-in predecessor does not rank them the way
+    // the stages between contractions do.
+    int cand[8], nc = 0;
+    if (!kx_stream_is_tuned(k, B, r.v.grid_div)) nc = kx_stream_candidate_list(k, B, r.v.grid_div, cand);
+    if (nc <= 1 && kx_tune_contraction(k, B, r.sv.f, r.v, r.sv.st, s, &ctx->launches))
         return kx_set_error(ctx, KX_ECUDA, "contraction autotuning failed");
     if (kx_fault("deverr")) KX_CUDA_TRY(ctx, cudaMemsetAsync(r.v.err, 0x01, 1, s));   // as in kx_collision
     const int G = 16;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
-    cudaStream_t cap = nullptr;
     int rc = KX_OK;
     if ((rc = kx_pinned_reserve(ctx, 2 * sizeof(kx_inst_state) * (size_t)B)) != KX_OK) return rc;
     kx_inst_state *h_st = (kx_inst_state *)ctx->h_pinned;
-    cudaError_t e = cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking);
-    if (e == cudaSuccess) e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
-    if (e == cudaSuccess) {
-        for (int a = 0; a < G && e == cudaSuccess; ++a) e = kx_enqueue_attempt(k, B, r, cap, a == 0);
-        cudaError_t e2 = cudaStreamEndCapture(cap, &graph);
-        if (e == cudaSuccess) e = e2;
+    auto capture = [&](cudaGraph_t *gr, cudaGraphExec_t *ex) -> cudaError_t {
+        cudaStream_t cap = nullptr;
+        cudaError_t x = cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking);
+        if (x == cudaSuccess) x = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+        if (x == cudaSuccess) {
+            for (int a = 0; a < G && x == cudaSuccess; ++a) x = kx_enqueue_attempt(k, B, r, cap, a == 0);
+            cudaError_t x2 = cudaStreamEndCapture(cap, gr);
+            if (x == cudaSuccess) x = x2;
+        }
+        if (x == cudaSuccess) x = cudaGraphInstantiate(ex, *gr, 0);
+        if (cap) cudaStreamDestroy(cap);
+        return x;
+    };
+    long long launched = 0;
+    cudaError_t e = cudaSuccess;
+    if (nc > 1) {
+        cudaGraph_t gs[8] = {};
+        cudaGraphExec_t xs[8] = {};
+        const int rounds = 3;   // the first replays warm the graphs up (not timed)
+        cudaEvent_t te[3][8][2] = {};
+        for (int c = 0; c < nc && e == cudaSuccess; ++c) {
+            kx_stream_pin(k, B, r.v.grid_div, cand[c]);
+            e = capture(&gs[c], &xs[c]);
+        }
+        for (int rd = 0; rd < rounds && e == cudaSuccess; ++rd)
+            for (int c = 0; c < nc && e == cudaSuccess; ++c) {
+                if (rd > 0) {
+                    e = cudaEventCreate(&te[rd][c][0]);
+                    if (e == cudaSuccess) e = cudaEventCreate(&te[rd][c][1]);
+                    if (e == cudaSuccess) e = cudaEventRecord(te[rd][c][0], s);
+                }
+                if (e == cudaSuccess) e = cudaGraphLaunch(xs[c], s);
+                if (e == cudaSuccess && rd > 0) e = cudaEventRecord(te[rd][c][1], s);
+                ++launched;
+                ctx->launches += 4LL * G;
+            }
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        int best = 0;
+        float best_ms = 0.f;
+        for (int c = 0; c < nc && e == cudaSuccess; ++c) {
+            float ms = 0.f;
+            for (int rd = 1; rd < rounds && e == cudaSuccess; ++rd) {
+                float t = 0.f;
+                e = cudaEventElapsedTime(&t, te[rd][c][0], te[rd][c][1]);
+                if (rd == 1 || t < ms) ms = t;
+            }
+            if (e == cudaSuccess && (c == 0 || ms < best_ms)) {
+                best_ms = ms;
+                best = c;
+            }
+        }
+        for (int rd = 0; rd < rounds; ++rd)
+            for (int c = 0; c < nc; ++c)
+                for (int q = 0; q < 2; ++q)
+                    if (te[rd][c][q]) cudaEventDestroy(te[rd][c][q]);
+        kx_stream_pin(k, B, r.v.grid_div, cand[best]);
+        for (int c = 0; c < nc; ++c) {
+            if (c == best) continue;
+            if (xs[c]) cudaGraphExecDestroy(xs[c]);
+            if (gs[c]) cudaGraphDestroy(gs[c]);
+        }
+        graph = gs[best];
+        exec = xs[best];
+    } else {
+        e = capture(&graph, &exec);
     }
-    if (e == cudaSuccess) e = cudaGraphInstantiate(&exec, graph, 0);
-    if (cap) cudaStreamDestroy(cap);
     if (e != cudaSuccess) {
+        if (exec) cudaGraphExecDestroy(exec);
         if (graph) cudaGraphDestroy(graph);
         return kx_set_error(ctx, KX_ECUDA, std::string("graph capture: ") + cudaGetErrorString(e));
     }
@@ -921,7 +992,6 @@ static int kx_solve_run(kx_ctx *ctx, const kx_kernel *k, int B, const kx_run &r,
     const long long max_launch = (long long)par->max_attempts / G + 2;
     const double wall_limit = 600.0;
     const bool fault_timeout = kx_fault("timeout");
-    long long launched = 0;
     auto launch_one = [&](int slot) -> cudaError_t {
         cudaError_t x = cudaGraphLaunch(exec, s);
         if (x == cudaSuccess)

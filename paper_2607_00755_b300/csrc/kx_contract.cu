@@ -12,14 +12,18 @@
 
 #include <map>
 #include <mutex>
+#include <set>
 #include <tuple>
 
 #include "kx_internal.cuh"
 
 __device__ double4_32a g_kx_log2_tab[256];
 __device__ double2 g_kx_exp2_tab[64];
+// the same table for the double-float log2: (1/F hi, lo; log2 F hi, lo) as floats
+__device__ float4 g_kx_log2_tab_f[256];
 
 #include "kx_math.cuh"
+#include "kx_lean.cuh"
 #include "kx_ptx.cuh"
 
 // Tables of kx_math.cuh, computed in long double on the host and copied to the
@@ -31,12 +35,15 @@ static cudaError_t kx_math_tables_init(int dev) {
     if (dev < 0 || dev >= 128) return cudaErrorInvalidDevice;
     if (ready[dev]) return cudaSuccess;
     double4_32a lt[256];
+    float4 ltf[256];
     double2 et[64];
     for (int k = 0; k < 256; ++k) {
         const long double F = 1.0L + (long double)k / 256.0L;   // exact in double
-        const long double l = log2l(F);
+        const long double l = log2l(F), rF = 1.0L / F;
         const double hi = (double)l;
-        lt[k] = make_double4_32a((double)F, (double)(1.0L / F), hi, (double)(l - (long double)hi));
+        lt[k] = make_double4_32a((double)F, (double)rF, hi, (double)(l - (long double)hi));
+        const float rh = (float)rF, lh = (float)l;
+        ltf[k] = make_float4(rh, (float)(rF - (long double)rh), lh, (float)(l - (long double)lh));
     }
     for (int j = 0; j < 64; ++j) {
         const long double t = exp2l((long double)j / 64.0L);
@@ -45,6 +52,7 @@ static cudaError_t kx_math_tables_init(int dev) {
     }
     cudaError_t e = cudaMemcpyToSymbol(g_kx_log2_tab, lt, sizeof(lt));
     if (e == cudaSuccess) e = cudaMemcpyToSymbol(g_kx_exp2_tab, et, sizeof(et));
+    if (e == cudaSuccess) e = cudaMemcpyToSymbol(g_kx_log2_tab_f, ltf, sizeof(ltf));
     if (e == cudaSuccess) ready[dev] = true;
     return e;
 }
@@ -56,14 +64,30 @@ __global__ void k_math_check(int which, int n, const double *__restrict__ x, dou
     if (which == 0) {
         out[2 * t] = kx_log2(v);
         out[2 * t + 1] = log2(v);
-    } else {
+    } else if (which == 1) {
         out[2 * t] = kx_exp(v);
         out[2 * t + 1] = exp(v);
+    } else if (which == 2) {
+        // double-float log2: e + hi + lo (FP64 sum of the exact parts)
+        int e;
+        kx_df fr;
+        kx_log2_df(v, e, fr, g_kx_log2_tab_f);
+        out[2 * t] = ((double)e + (double)fr.hi) + (double)fr.lo;
+        out[2 * t + 1] = log2(v);
+    } else if (which == 3) {
+        // double -> float on the integer pipe against CUDA's conversion
+        out[2 * t] = (double)kx_d2f(v);
+        out[2 * t + 1] = (double)__double2float_rn(v);
+    } else {
+        // float -> double on the integer pipe (the float nearest v) against CUDA's
+        const float f = __double2float_rn(v);
+        out[2 * t] = kx_f2d(f);
+        out[2 * t + 1] = (double)f;
     }
 }
 
 extern "C" int kx_math_check(kx_ctx *ctx, int which, int n, const double *x_dev, double *out_dev) {
-    if (!ctx || (which != 0 && which != 1) || n < 1 || !x_dev || !out_dev) return KX_EINVAL;
+    if (!ctx || which < 0 || which > 4 || n < 1 || !x_dev || !out_dev) return KX_EINVAL;
     if (cudaSetDevice(ctx->device) != cudaSuccess) return KX_ECUDA;
     k_math_check<<<(n + 255) / 256, 256, 0, ctx->stream>>>(which, n, x_dev, out_dev);
     return cudaGetLastError() == cudaSuccess ? KX_OK : KX_ECUDA;
@@ -420,12 +444,12 @@ struct kx_noop {
 // stored reference lines, when the caller has them already (the stage kernel
 // loads them early); have = false: the prep makes them itself.
 struct kx_prep_pre {
-    double K;       // E_i - E_0
-    float Kf, hf;   // K and h_i as floats
-    float4 lines;   // v.fit[b]
+    double K;           // E_i - E_0
+    float Kf, Kl, hf;   // K as a double-float (Kf, Kl) and h_i as a float
+    float4 lines;       // v.fit[b]
     bool have;
-    float2 next;    // FP32 dilute path, KX_LINE_NEXT: the line of the previous prep's fit
-    const double4_32a *ltab;   // log2 table (a shared-memory copy), or null: the global one
+    float2 next;        // FP32 dilute path, KX_LINE_NEXT: the line of the previous prep's fit
+    const float4 *ltabf;   // the double-float log2 table (a shared-memory copy), or null: the global one
 };
 // idle: run by every thread just before the barrier that publishes 1/f_max and
 // log2 f_max, while threads 0 and 32 compute them (the other warps wait there)
@@ -458,14 +482,18 @@ __device__ __forceinline__ float2 kx_fit_line(const kx_batch_views &v, int b) {
 // FP32 path (dilute) tables of one instance, block-wide (thread = grid point):
 //   l2'_j = log2(max(f_j, floor)) - e, 2^e the power of two of f_max (f_max =
 //          2^e m, 1 <= m < 2): the tables' scale (the elements' 2^(l2'_n + l2'_m)
-//          stay below 4; C_raw = M2 2^(2e) sum ...), exact in FP64;
+//          stay below 4; C_raw = M2 2^(2e) sum ...);
 //   delta_j = log2 f_j - (a + b K_j), K = E - E_0: the deviation from a line
 //          in E, fitted to the absolute log2 f by least squares with weights
 //          h f 2^-e.  Any line cancels exactly in the elements' exponent
 //          differences (energy conservation, energy-linear interpolation); the
 //          fit only keeps the deviations small.
-// tl[j] = (l2'_j, delta_j); the contraction forms D_j = delta_(j+1) - delta_j
-// itself.  The line: KX_LINE_FIT a fit of this f (a new instance; one block
+// tl[j] = (l2'_j, delta_j) as floats; the contraction forms D_j = delta_(j+1) -
+// delta_j itself.  log2 f and delta are made in double-float arithmetic on the
+// FP32 pipe (kx_log2_df: absolute error about 2e-14, far below the floats'
+// rounding of the stored values); the scale, the tests of f and the
+// conversions work on bit patterns, so the prep issues no FP64 arithmetic.
+// The line: KX_LINE_FIT a fit of this f (a new instance; one block
 // reduction); KX_LINE_NEXT the fit of the previous prep's f (pre.next, made
 // by the caller from the per-warp partials); KX_LINE_SAME the line of the
 // current tables (a re-prep of the same f builds the same tables).  This f's
@@ -479,34 +507,45 @@ __device__ __forceinline__ int kx_prep_block_f32(int n, double x, double Ei, dou
     __shared__ float s_fit[5 * 32];
     const int i = threadIdx.x, lane = i & 31, warp = i >> 5;
     const bool in = i < n;
-    const bool nf = in && !isfinite(x);
+    const bool nf = in && kx_nonfinite(x);
     idle();
+    // log2 of max(f, floor) before f_max is known (x >= 0 here: as signed bit
+    // patterns, values order like the numbers and -0.0 is below the floor)
     int ex = 0;
-    double frx = 0.0;
-    if (in && !nf) kx_log2_parts(x > KX_LOG_FLOOR ? x : KX_LOG_FLOOR, ex, frx, pre.ltab ? pre.ltab : g_kx_log2_tab);
+    kx_df frx = {0.f, 0.f};
+    const bool above = (long long)kx_bits(x) > (long long)kx_bits(KX_LOG_FLOOR);
+    if (in && !nf) kx_log2_df(above ? x : KX_LOG_FLOOR, ex, frx, pre.ltabf ? pre.ltabf : g_kx_log2_tab_f);
     const unsigned long long key =
-        key_in != KX_KEY_NONE
-            ? key_in
-            : kx_block_max_key(nf ? KX_KEY_NONFINITE : (unsigned long long)__double_as_longlong(fabs(x)), s_key);
+        key_in != KX_KEY_NONE ? key_in : kx_block_max_key(nf ? KX_KEY_NONFINITE : kx_abs_bits(x), s_key);
     const int bad = key == KX_KEY_NONFINITE;
     const double fm = bad ? INFINITY : __longlong_as_double((long long)key);
-    const bool ok = fm > 0.0 && !bad;
+    const bool ok = key != 0ull && !bad;   // f_max > 0
     // the power of two of max(f_max, floor): 2^e and 2^-e exactly (bit patterns)
-    const unsigned long long kb = (unsigned long long)__double_as_longlong(fm > KX_LOG_FLOOR ? fm : KX_LOG_FLOOR);
+    const unsigned long long kfl = kx_bits(KX_LOG_FLOOR);
+    const unsigned long long kb = key > kfl ? key : kfl;
     const int e = ok ? (int)((kb >> 52) & 0x7ff) - 1023 : 0;
     const double sc = __longlong_as_double((long long)(e + 1023) << 52);
     const double rsc = __longlong_as_double((long long)(1023 - e) << 52);
-    const double K = pre.have ? pre.K : (in ? Ei - E0 : 0.0);
-    const float Kf = pre.have ? pre.Kf : (float)K;
-    // (threads past n skip the FP64 arithmetic, a whole warp when the launch adds one)
-    double l2a = 0.0, l2s = -2000.0;   // log2 f, log2 f - e
-    float w = 0.f;
-    if (in && ok) {
-        l2a = (double)ex + frx;
-        l2s = (double)(ex - e) + frx;
-        if (x > 0.0) w = (pre.have ? pre.hf : (float)hi) * (float)(x * rsc);
+    kx_df Kd;
+    if (pre.have) {
+        Kd = kx_df{pre.Kf, pre.Kl};
+    } else {
+        Kd = in ? kx_df_of(Ei - E0) : kx_df{0.f, 0.f};
     }
-    const float g = (float)l2a;
+    const float Kf = Kd.hi;
+    // log2 f and log2 f - e (double-float), and the fit weight h f 2^-e
+    kx_df l2a = {0.f, 0.f};
+    float l2s = -2000.f, w = 0.f;
+    if (in && ok) {
+        float s0, e0;
+        kx_two_sum((float)ex, frx.hi, s0, e0);
+        l2a = kx_fast_two_sum(s0, __fadd_rn(e0, frx.lo));
+        float s1, e1;
+        kx_two_sum((float)(ex - e), frx.hi, s1, e1);
+        l2s = __fadd_rn(s1, __fadd_rn(e1, frx.lo));
+        if ((long long)kx_bits(x) > 0) w = (pre.have ? pre.hf : (float)hi) * kx_d2f_pow2(x, -e);
+    }
+    const float g = l2a.hi;
     float sf[5] = {w, w * Kf, w * Kf * Kf, w * g, w * Kf * g};
 #pragma unroll
     for (int k = 0; k < 5; ++k)
@@ -535,8 +574,13 @@ __device__ __forceinline__ int kx_prep_block_f32(int n, double x, double Ei, dou
     }
     float2 *tl = v.tl + (long long)b * (n + 4);
     if (in) {
-        const double del = ok ? l2a - ((double)line.x + (double)line.y * K) : 0.0;
-        tl[i] = make_float2((float)l2s, (float)del);
+        float del = 0.f;
+        if (ok) {
+            // delta = log2 f - (a + b K) in double-float
+            const kx_df ln = kx_df_add(kx_df{line.x, 0.f}, kx_df_mul(kx_df{line.y, 0.f}, Kd));
+            del = kx_df_round(kx_df_add(l2a, kx_df_neg(ln)));
+        }
+        tl[i] = make_float2(l2s, del);
     }
     if (i < 4) tl[n + i] = make_float2(-2000.f, 0.f);
     // every slot is written (zeros past the block's warps), whatever the block size
@@ -562,7 +606,7 @@ template <bool Q = false, typename Idle = kx_noop, bool F32 = true>
 __device__ __forceinline__ int kx_prep_block(int n, int path, double x, double Ei, double hi, double E0,
                              const kx_batch_views &v, int b, double *smem,
                              unsigned long long key_in = KX_KEY_NONE, int line_mode = KX_LINE_FIT,
-                             Idle idle = Idle(), kx_prep_pre pre = kx_prep_pre{0.0, 0.f, 0.f, {}, false, {}, nullptr}) {
+                             Idle idle = Idle(), kx_prep_pre pre = kx_prep_pre{0.0, 0.f, 0.f, 0.f, {}, false, {}, nullptr}) {
     if constexpr (!Q && F32) {
         if (path == KX_FP32) return kx_prep_block_f32(n, x, Ei, hi, E0, v, b, key_in, line_mode, idle, pre);
     }
@@ -864,13 +908,6 @@ __device__ __forceinline__ float kx_bracket_term(float a, float d) {
     return fabsf(d) < 0.25f ? nearv : farv;
 }
 
-// Error-free sum of two floats (Knuth's TwoSum): s + e == a + b exactly.
-__device__ __forceinline__ void kx_two_sum(float a, float b, float &s, float &e) {
-    s = a + b;
-    const float bv = s - a;
-    e = (a - (s - bv)) + (b - bv);
-}
-
 // (hi, lo) += x in double-float arithmetic (about 44 significant bits).
 __device__ __forceinline__ void kx_df_add(float &hi, float &lo, float x) {
     float s, e;
@@ -1005,6 +1042,44 @@ __device__ __forceinline__ bool kx_stream_tables(int n, int B, int b0, const flo
                                                  float2 (*s_l)[KX_MAX_N + 4],
                                                  float2 (*s_d)[KX_MAX_N], bool *act) {
     bool any = false;
+    if (n + 4 <= (int)blockDim.x) {
+        // one entry per thread: the table loads are issued together with the
+        // state loads (one round trip after the wait for the predecessor, not
+        // two); an inactive instance's loads are discarded
+        const int t = threadIdx.x;
+        float2 x0[BP], x1[BP];
+#pragma unroll
+        for (int bb = 0; bb < BP; ++bb) {
+            const int b = b0 + bb;
+            x0[bb] = x1[bb] = make_float2(-2000.f, 0.f);
+            if (b < B && t < n + 4) {
+                x0[bb] = tl[(long long)b * (n + 4) + t];
+                if (WITH_D && t + 1 < n) x1[bb] = tl[(long long)b * (n + 4) + t + 1];
+            }
+        }
+#pragma unroll
+        for (int bb = 0; bb < BP; ++bb) {
+            const int b = b0 + bb;
+            act[bb] = b < B && !(st && (st[b].done || (stage == 2 && st[b].skip2)));
+            any |= act[bb];
+        }
+        if (!any) return false;
+#pragma unroll
+        for (int bb = 0; bb < BP; ++bb) {
+            if (t < n + 4) s_l[bb][t] = act[bb] ? x0[bb] : make_float2(-2000.f, 0.f);
+            if constexpr (WITH_D)
+                if (t < n) {
+                    // (delta_j - D_j, D_j), D_j = delta_(j+1) - delta_j (0 at the last point)
+                    float2 d = make_float2(0.f, 0.f);
+                    if (act[bb]) {
+                        const float D = t + 1 < n ? x1[bb].y - x0[bb].y : 0.f;
+                        d = make_float2(x0[bb].y - D, D);
+                    }
+                    s_d[bb][t] = d;
+                }
+        }
+        return true;
+    }
 #pragma unroll
     for (int bb = 0; bb < BP; ++bb) {
         int b = b0 + bb;
@@ -1330,6 +1405,130 @@ __global__ void __launch_bounds__(KX_T32, VPL == 4 ? 2 : 3)
     }
 }
 
+// Staged-share streaming contraction: every warp copies ALL of its bins' units
+// (W, packed (j_L, omega), (n, m0) words; KX_STAGE_BYTES(VPL) each) into its
+// own part of shared memory with bulk copies issued before the wait for the
+// predecessor kernel: the tables are constant, so their L2/DRAM latency and
+// the dependent bin -> task -> row-offset walk overlap the previous Heun stage,
+// and after the wait a warp only loads the instances' (l2, delta) tables and
+// computes.  KX_TP threads per block (one bin per warp when the grid covers
+// the KX_BINS bins in one wave); BP instances per pass.  The arithmetic per
+// unit, the order of the unit sums and the task partials are those of the
+// other streaming kernels (kx_vector_terms, kx_task_partial), so the results
+// are bit-identical to theirs.  Shared memory: KX_TP/32 warps x umax units
+// (umax >= the units of the warp's bins, checked by the host).  The warp's
+// copies complete one mbarrier (bounded wait; on expiry *err is set and the
+// warp waits once more for its copies before it exits).
+#define KX_TP 512
+#define KX_P_UMAX 8   // unit descriptors per warp
+template <int BP, int VPL>
+__global__ void __launch_bounds__(KX_TP, 1)
+    k_stream32p(int n, const int *__restrict__ bins, const int4 *__restrict__ task,
+                const int *__restrict__ roff, int B,
+                const uint32_t *__restrict__ vt, const float4 *__restrict__ W,
+                const uint4 *__restrict__ PK, const float2 *__restrict__ tl,
+                const float2 *__restrict__ td, float2 *__restrict__ partial, int pstride,
+                const kx_inst_state *__restrict__ st, int stage, int umax, int *__restrict__ err) {
+    extern __shared__ __align__(128) unsigned char s_units[];   // [warp][umax][KX_STAGE_BYTES]
+    __shared__ float2 s_l[BP][KX_MAX_N + 4];   // (l2_j, delta_j)
+    __shared__ float2 s_d[BP][KX_MAX_N];       // (delta_j - D_j, D_j)
+    __shared__ __align__(8) unsigned long long s_bar[KX_TP / 32];
+    __shared__ int4 s_ud[KX_TP / 32][KX_P_UMAX];   // per unit: (row, slot, first of its task, last of its task)
+    __shared__ int s_cnt[KX_TP / 32];
+    kx_pdl_trigger();
+    constexpr int UNIT = 32 * VPL, SB = KX_STAGE_BYTES(VPL);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, wpb = blockDim.x >> 5;
+    const uint32_t bar = kx_smem_u32(&s_bar[warp]);
+    unsigned char *mine = s_units + (size_t)warp * umax * SB;
+    if (lane == 0) {
+        kx_mbar_init(bar, 1);
+        kx_fence_mbar_init();
+        // this warp's bins (vb, vb + stride, ...) and their units, in order; the
+        // copies of all of them complete the one mbarrier.  The host launches
+        // this kernel only when every warp's units fit (umax); a warp that
+        // finds more reports it through *err instead of dropping them silently.
+        const int stride = gridDim.x * wpb;
+        const int cap = umax < KX_P_UMAX ? umax : KX_P_UMAX;
+        int cnt = 0;
+        bool over = false;
+        for (int vb = blockIdx.x * wpb + warp; vb < KX_BINS; vb += stride) {
+            const int t1 = __ldg(bins + vb + 1);
+            for (int t = __ldg(bins + vb); t < t1; ++t) {
+                const int4 d = __ldg(task + t);
+                for (int c = d.y; c < d.z; ++c) {
+                    if (cnt < cap) s_ud[warp][cnt++] = make_int4(d.x, d.w, c == d.y, c + 1 == d.z);
+                    else over = true;
+                }
+            }
+        }
+        if (over) atomicExch(err, 1);
+        s_cnt[warp] = cnt;
+        kx_mbar_expect_tx(bar, (uint32_t)(cnt * SB));
+        // the copies, in the same walk order (the same units, as counted)
+        int u = 0;
+        for (int vb = blockIdx.x * wpb + warp; vb < KX_BINS && u < cnt; vb += stride) {
+            const int t1 = __ldg(bins + vb + 1);
+            for (int t = __ldg(bins + vb); t < t1 && u < cnt; ++t) {
+                const int4 d = __ldg(task + t);
+                const int rb = __ldg(roff + d.x);
+                for (int c = d.y; c < d.z && u < cnt; ++c, ++u) {
+                    const int v0 = rb + c * UNIT;
+                    unsigned char *dst = mine + (size_t)u * SB;
+                    kx_bulk_g2s(kx_smem_u32(dst), W + v0, UNIT * 16u, bar);
+                    kx_bulk_g2s(kx_smem_u32(dst + UNIT * 16), PK + v0, UNIT * 16u, bar);
+                    kx_bulk_g2s(kx_smem_u32(dst + UNIT * 32), vt + v0, UNIT * 4u, bar);
+                }
+            }
+        }
+    }
+    __syncthreads();   // (mbarrier initialised, unit list published)
+    const int cnt = s_cnt[warp];
+    kx_pdl_wait();
+    const int b0 = blockIdx.y * BP;
+    bool act[BP];
+    const bool any = kx_stream_tables<BP>(n, B, b0, tl, td, st, stage, s_l, s_d, act);
+    __syncthreads();
+    // this warp's copies (issued long ago: normally complete)
+    bool ok = cnt == 0 || kx_mbar_wait(bar, 0);
+    if (!ok) {
+        if (lane == 0) atomicExch(err, 1);
+        kx_mbar_wait(bar, 0);   // let the copies land (bounded) before the block exits
+        return;
+    }
+    if (!any) return;
+    const int rot = (lane >> 2) & 3;
+    const int so[4] = {rot, (1 + rot) & 3, (2 + rot) & 3, (3 + rot) & 3};
+    float hi[BP], lo[BP], di[BP];
+#pragma unroll
+    for (int bb = 0; bb < BP; ++bb) hi[bb] = lo[bb] = di[bb] = 0.f;
+    for (int u = 0; u < cnt; ++u) {
+        const int4 d = s_ud[warp][u];
+        if (d.z) {
+#pragma unroll
+            for (int bb = 0; bb < BP; ++bb) {
+                hi[bb] = 0.f;
+                lo[bb] = 0.f;
+                di[bb] = s_l[bb][d.x].y;
+            }
+        }
+        const unsigned char *src = mine + (size_t)u * SB;
+        const float4 *sW = reinterpret_cast<const float4 *>(src);
+        const uint4 *sP = reinterpret_cast<const uint4 *>(src + UNIT * 16);
+        const uint32_t *sV = reinterpret_cast<const uint32_t *>(src + UNIT * 32);
+        float acc[BP];
+#pragma unroll
+        for (int bb = 0; bb < BP; ++bb) acc[bb] = 0.f;
+#pragma unroll
+        for (int e = 0; e < VPL; ++e) {
+            const int vl = e * 32 + lane;
+            kx_vector_terms<BP>(sW[vl], sP[vl], sV[vl], s_l, s_d, di, so, acc);
+        }
+#pragma unroll
+        for (int bb = 0; bb < BP; ++bb) kx_df_add(hi[bb], lo[bb], acc[bb]);
+        if (d.w) kx_task_partial<BP>(hi, lo, act, lane, b0, pstride, d.y, partial);
+    }
+}
+
 int kx_chunks_per_row(const kx_kernel *k) {
     if (k->precision == KX_SPLIT_TF32) return 1;
     if (k->precision == KX_FP64) return (int)((k->P + KX_CH64 - 1) / KX_CH64);
@@ -1346,12 +1545,25 @@ static cudaError_t kx_stream_attr() {
     return cudaFuncSetAttribute(k_stream32<BP, VPL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 KX_STREAM_SMEM(VPL, KX_T32 / 32));
 }
+// dynamic shared memory of the staged-share variant, at most (with its static
+// tables, up to 35 KB for four instances, within the 227 KB of a block)
+#define KX_P_SMEM_MAX (188 * 1024)
+template <int BP, int VPL>
+static cudaError_t kx_stream_p_attr() {
+    return cudaFuncSetAttribute(k_stream32p<BP, VPL>, cudaFuncAttributeMaxDynamicSharedMemorySize, KX_P_SMEM_MAX);
+}
 
 cudaError_t kx_contract_prepare() {
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaError_t e = kx_math_tables_init(dev);
     if (e == cudaSuccess) e = kx_stream_attr<4, 4>();
+    if (e == cudaSuccess) e = kx_stream_p_attr<1, 2>();
+    if (e == cudaSuccess) e = kx_stream_p_attr<2, 2>();
+    if (e == cudaSuccess) e = kx_stream_p_attr<4, 2>();
+    if (e == cudaSuccess) e = kx_stream_p_attr<1, 4>();
+    if (e == cudaSuccess) e = kx_stream_p_attr<2, 4>();
+    if (e == cudaSuccess) e = kx_stream_p_attr<4, 4>();
     if (e != cudaSuccess) return e;
     if (g_sms) return cudaSuccess;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -1412,10 +1624,42 @@ static cudaError_t kx_launch_stream_r(const kx_kernel *k, int B, const kx_batch_
                         (const float4 *)v.tq, (const float *)v.tlam, (const double *)v.fmax, v.eta);
 }
 
+// The staged-share variant (4): one bin per warp in a single wave of KX_TP
+// blocks, every warp's units in shared memory; BP = the batch (1, 2, or 4 for
+// three or four instances).  Offered for one instance group, a whole-GPU grid
+// and bins that fit.
+static size_t kx_stream_p_smem(const kx_kernel *k) {
+    return (size_t)(KX_TP / 32) * (size_t)k->bin_units * KX_STAGE_BYTES(k->vpl);
+}
+static bool kx_stream_p_ok(const kx_kernel *k, int B, int grid_div) {
+    return k->precision == KX_FP32 && !k->stats && B >= 1 && B <= 4 && grid_div <= 1 && k->bin_units >= 1 &&
+           k->bin_units <= KX_P_UMAX && kx_stream_p_smem(k) <= KX_P_SMEM_MAX;
+}
+template <int BP, int VPL>
+static cudaError_t kx_launch_stream_p(const kx_kernel *k, int B, const kx_batch_views &v,
+                                      const kx_inst_state *st, int stage, cudaStream_t s, bool pdl) {
+    const int wpb = KX_TP / 32;
+    dim3 grid((KX_BINS + wpb - 1) / wpb, (B + BP - 1) / BP);
+    return kx_launch_ex(k_stream32p<BP, VPL>, grid, dim3(KX_TP), kx_stream_p_smem(k), s, pdl, k->n,
+                        (const int *)k->d_bins, (const int4 *)k->d_task, (const int *)k->d_roff, B,
+                        (const uint32_t *)k->d_vt, reinterpret_cast<const float4 *>(k->d_W32),
+                        reinterpret_cast<const uint4 *>(k->d_pk), (const float2 *)v.tl, (const float2 *)v.td,
+                        reinterpret_cast<float2 *>(v.partial), v.chunks, st, stage, k->bin_units, v.err);
+}
+template <int VPL>
+static cudaError_t kx_launch_stream_pb(const kx_kernel *k, int B, const kx_batch_views &v,
+                                       const kx_inst_state *st, int stage, cudaStream_t s, bool pdl) {
+    if (B == 1) return kx_launch_stream_p<1, VPL>(k, B, v, st, stage, s, pdl);
+    if (B == 2) return kx_launch_stream_p<2, VPL>(k, B, v, st, stage, s, pdl);
+    return kx_launch_stream_p<4, VPL>(k, B, v, st, stage, s, pdl);
+}
+
 // ------------------------------------------------------------ autotuner
 // Streaming variants of the FP32 path: 0 = register pipeline, one instance per
 // pass; 1 = register pipeline, two per pass; 2 = bulk-copy staged, four per pass
-// (units of 128 vectors only); 3 = register pipeline, four per pass.  All give bit-identical results (shared
+// (units of 128 vectors only); 3 = register pipeline, four per pass; 4 = every
+// warp's whole share staged before the wait (batches of up to four, one
+// wave).  All give bit-identical results (shared
 // arithmetic, the kernel's fixed bins), so the choice is purely a matter of
 // speed: it is timed once per (device, grid size, batch) on the caller's own
 // prepared inputs and kept for the process.
@@ -1424,14 +1668,18 @@ static std::mutex g_tune_mu;
 // launched on a fraction of the GPU (the server's shared graphs) can rank the
 // variants differently from a whole-GPU launch
 static std::map<std::tuple<int, int, int, int>, int> g_tuned;
+// the keys whose choice a solve's in-place tuning made or the caller pinned
+// (a solve re-tunes a choice the stand-in timing made)
+static std::set<std::tuple<int, int, int, int>> g_tuned_firm;
 static int kx_gd(int grid_div) { return grid_div > 1 ? grid_div : 1; }
 
-static void kx_stream_candidates(const kx_kernel *k, int B, int *cand, int *nc) {
+static void kx_stream_candidates(const kx_kernel *k, int B, int grid_div, int *cand, int *nc) {
     *nc = 0;
     cand[(*nc)++] = 0;
     if (B >= 2) cand[(*nc)++] = 1;
     if (k->vpl == 4 && B >= 4) cand[(*nc)++] = 2;
     if (B >= 4) cand[(*nc)++] = 3;
+    if (kx_stream_p_ok(k, B, grid_div)) cand[(*nc)++] = 4;
 }
 
 // The rule used before a size is tuned (measured on this part): two per pass on
@@ -1456,6 +1704,13 @@ static cudaError_t kx_stream_launch(int variant, const kx_kernel *k, int B, cons
     if (k->stats)
         return k->vpl == 2 ? kx_launch_stream_r<1, 2, true>(k, B, v, st, stage, s, pdl)
                            : kx_launch_stream_r<1, 4, true>(k, B, v, st, stage, s, pdl);
+    if (variant == 4) {
+        // (pinned but not eligible here, e.g. a shared grid: the default rule)
+        if (kx_stream_p_ok(k, B, v.grid_div))
+            return k->vpl == 2 ? kx_launch_stream_pb<2>(k, B, v, st, stage, s, pdl)
+                               : kx_launch_stream_pb<4>(k, B, v, st, stage, s, pdl);
+        variant = kx_stream_default(k, B);
+    }
     if (k->vpl == 2) {
         if (variant == 3) return kx_launch_stream_r<4, 2>(k, B, v, st, stage, s, pdl);
         return variant == 1 ? kx_launch_stream_r<2, 2>(k, B, v, st, stage, s, pdl)
@@ -1498,8 +1753,8 @@ int kx_tune_contraction(const kx_kernel *k, int B, const double *f, const kx_bat
         std::lock_guard<std::mutex> lock(g_tune_mu);
         if (g_tuned.count(key)) return 0;
     }
-    int cand[4], nc = 0;
-    kx_stream_candidates(k, B, cand, &nc);
+    int cand[5], nc = 0;
+    kx_stream_candidates(k, B, v.grid_div, cand, &nc);
     int best = kx_stream_default(k, B);
     if (nc > 1) {
         const int R = 6;
@@ -1548,6 +1803,29 @@ int kx_tune_contraction(const kx_kernel *k, int B, const double *f, const kx_bat
     return 0;
 }
 
+// In-place tuning (the solve): the candidates for a launch, whether its key
+// has a choice already, and pinning one.
+int kx_stream_candidate_list(const kx_kernel *k, int B, int grid_div, int *cand) {
+    if (k->precision != KX_FP32 || k->stats) return 0;
+    int nc = 0;
+    kx_stream_candidates(k, B, grid_div, cand, &nc);
+    return nc;
+}
+bool kx_stream_is_tuned(const kx_kernel *k, int B, int grid_div) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    return g_tuned_firm.count(std::make_tuple(dev, k->n, B, kx_gd(grid_div))) != 0;
+}
+void kx_stream_pin(const kx_kernel *k, int B, int grid_div, int variant) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    const auto key = std::make_tuple(dev, k->n, B, kx_gd(grid_div));
+    g_tuned[key] = variant;
+    g_tuned_firm.insert(key);
+}
+
 extern "C" int kx_get_stream_variant(kx_ctx *ctx, int n, int batch, int *variant, int *tuned) {
     if (!ctx || !variant || n < 4 || n > KX_MAX_N || batch < 1) return KX_EINVAL;
     kx_kernel probe;
@@ -1561,17 +1839,23 @@ extern "C" int kx_get_stream_variant(kx_ctx *ctx, int n, int batch, int *variant
 }
 
 extern "C" int kx_set_stream_variant(kx_ctx *ctx, int n, int batch, int variant) {
-    if (!ctx || n < 4 || n > KX_MAX_N || batch < 1 || variant < -1 || variant > 3) return KX_EINVAL;
+    if (!ctx || n < 4 || n > KX_MAX_N || batch < 1 || variant < -1 || variant > 4) return KX_EINVAL;
     const int vpl = n <= 160 ? 2 : 4;
     if (variant == 1 && batch < 2) return KX_EINVAL;
     if (variant == 2 && (vpl != 4 || batch < 4)) return KX_EINVAL;
     if (variant == 3 && batch < 4) return KX_EINVAL;
+    if (variant == 4 && batch > 4) return KX_EINVAL;
     // pinned (or forgotten) for every grid share
     std::lock_guard<std::mutex> lock(g_tune_mu);
     for (int gd = 1; gd <= 16; ++gd) {
         const auto key = std::make_tuple(ctx->device, n, batch, gd);
-        if (variant < 0) g_tuned.erase(key);
-        else g_tuned[key] = variant;
+        if (variant < 0) {
+            g_tuned.erase(key);
+            g_tuned_firm.erase(key);
+        } else {
+            g_tuned[key] = variant;
+            g_tuned_firm.insert(key);
+        }
     }
     return KX_OK;
 }
@@ -1603,58 +1887,17 @@ struct kx_row_out {
     int singular;
 };
 
-// sm: at least 5 * blockDim.x + 8 doubles; the caller passes a block barrier
-// before it writes sm[5 blockDim.x .. + 4] again (the projection sums, read by
-// every thread).
+// The FP64 and batched (split TF32) paths; the FP32 path has its own
+// (kx_combine_project_f32).  sm: at least 5 * blockDim.x + 8 doubles; the
+// caller passes a block barrier before it writes sm[5 blockDim.x .. + 4] again
+// (the projection sums, read by every thread).
 __device__ __forceinline__ kx_row_out kx_combine_project(int n, int chunks, int path, int b, double fi, double Ei,
                                          double hi, const kx_batch_views &v, int project,
                                          double *sm) {
     const int i = threadIdx.x, T = blockDim.x;
     const double fm = v.fmax[b], rfm = v.rfmax[b], M2 = v.M2[b];
-    // FP32 path: the tables' scale (C_raw = M2 scale^2 sum); xi = |f| / scale
-    // with the support threshold eps_supp f_max / scale (xi's scale cancels in
-    // the projection); the other paths: scale = f_max
-    const double fsc = path == KX_FP32 ? v.fsc[b] : fm;
     double G = 0.0, L = 0.0;
-    if (i < n && path == KX_FP32) {
-        // double-float task partials (hi, lo), four independent double-float
-        // sums (slot k mod 4) combined in a fixed order.  Row i's slots are
-        // i + k n, k = 0 .. MT - 1, of instance b (MT = chunks / n): consecutive
-        // rows are adjacent, so each load is coalesced across the warp; the
-        // first rt.y of them are written by the row's tasks (the addresses do
-        // not wait for the task count, which only masks the sums).
-        const int MT = chunks / n;
-        const float2 *pp = reinterpret_cast<const float2 *>(v.partial) + (long long)b * chunks + i;
-        const int ntask = v.rtask[i].y;
-        float h0 = 0.f, l0 = 0.f, h1 = 0.f, l1 = 0.f, h2 = 0.f, l2 = 0.f, h3 = 0.f, l3 = 0.f;
-        // batches of 24 slots: the loads of a batch are in flight together
-        for (int c0 = 0; c0 < MT; c0 += 24) {
-            float2 x[24];
-            const float2 *q = pp + (long long)c0 * n;
-#pragma unroll
-            for (int j = 0; j < 24; ++j, q += n) x[j] = c0 + j < MT ? *q : make_float2(0.f, 0.f);
-#pragma unroll
-            for (int j = 0; j < 24; j += 4) {
-                const int s0 = c0 + j;   // slots s0 .. s0 + 3; those >= ntask hold no task
-                const bool p0 = s0 >= ntask, p1 = s0 + 1 >= ntask, p2 = s0 + 2 >= ntask, p3 = s0 + 3 >= ntask;
-                kx_df_add(h0, l0, p0 ? 0.f : x[j].x);
-                l0 += p0 ? 0.f : x[j].y;
-                kx_df_add(h1, l1, p1 ? 0.f : x[j + 1].x);
-                l1 += p1 ? 0.f : x[j + 1].y;
-                kx_df_add(h2, l2, p2 ? 0.f : x[j + 2].x);
-                l2 += p2 ? 0.f : x[j + 2].y;
-                kx_df_add(h3, l3, p3 ? 0.f : x[j + 3].x);
-                l3 += p3 ? 0.f : x[j + 3].y;
-            }
-        }
-        kx_df_add(h0, l0, h1);
-        l0 += l1;
-        kx_df_add(h2, l2, h3);
-        l2 += l3;
-        kx_df_add(h0, l0, h2);
-        l0 += l2;
-        G = (double)h0 + (double)l0;
-    } else if (i < n && path == KX_SPLIT_TF32) {
+    if (i < n && path == KX_SPLIT_TF32) {
         // the gain GEMM's k chunks in order (f' units); the loss from the
         // Chebyshev GEMM's chunks, or the exact loss kernel's row sum (x f_max)
         // (double-float sums of the FP32 chunk partials: exact TwoSum, FP64 at the end)
@@ -1691,13 +1934,8 @@ __device__ __forceinline__ kx_row_out kx_combine_project(int n, int chunks, int 
     // its lanes hold grid points: threads past n (a whole warp when the launch
     // adds one) skip the FP64 arithmetic below on a warp-uniform branch.
     const bool wpts = (i & ~31) < n;   // this warp holds grid points
-    double Craw = 0.0;
-    // FP32 path: G holds sum S (f_n f_m - f_i f_t) / f_max^2; the FP64 and batched
-    // paths hold the gain G and the loss rate L
-    if (i < n) {
-        if (path == KX_FP32) Craw = M2 * (fsc * fsc * G);
-        else Craw = M2 * (G - fi * L);
-    }
+    double Craw = 0.0;   // G holds the gain and L the loss rate
+    if (i < n) Craw = M2 * (G - fi * L);
     kx_row_out r;
     r.Craw = Craw;
     r.Cproj = Craw;
@@ -1706,9 +1944,8 @@ __device__ __forceinline__ kx_row_out kx_combine_project(int n, int chunks, int 
     if (!project) return r;
     double xi = 0.0;
     if (i < n && fm > 0.0) {
-        double q = fabs(fi) * rfm;
-        const double thr = path == KX_FP32 ? KX_EPS_SUPP * (fm * rfm) : KX_EPS_SUPP;
-        xi = q > thr ? q : 0.0;
+        const double q = fabs(fi) * rfm;
+        xi = q > KX_EPS_SUPP ? q : 0.0;
     }
     double s[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
     if (wpts) {
@@ -1742,6 +1979,184 @@ __device__ __forceinline__ kx_row_out kx_combine_project(int n, int chunks, int 
         r.beta = be;
         r.singular = sg;
         r.Cproj = Craw - xi * (al + be * Ei);
+    }
+    return r;
+}
+
+// ---------------------------------------- FP32 path: combine + projection
+// Per-point constants of the FP32 path's projection (the stage kernels make
+// them before they wait for their predecessor).
+struct kx_pt32 {
+    double E, h, hE, hE2;   // E_i, h_i, h_i E_i, h_i E_i^2 (0 past n)
+};
+__device__ __forceinline__ kx_pt32 kx_pt32_make(bool in, double Ei, double hi) {
+    kx_pt32 p;
+    p.E = in ? Ei : 0.0;
+    p.h = in ? hi : 0.0;
+    p.hE = p.h * p.E;
+    p.hE2 = p.hE * p.E;
+    return p;
+}
+
+// 1/x for a positive normal double x: a float reciprocal of x's significand
+// (integer-pipe conversions) refined by two Newton-Raphson steps
+// r <- r + r (1 - x r), each squaring the relative error (2^-24 -> 2^-48 ->
+// the FP64 rounding): four FP64 operations.
+__device__ __forceinline__ double kx_rcp_newton(double x) {
+    const int ex = (int)((kx_bits(x) >> 52) & 0x7ff) - 1023;
+    const float m = kx_d2f_pow2(x, -ex);   // in [1, 2]
+    double r = kx_ldexp_bits(kx_f2d(1.f / m), -ex);
+    r = fma(r, fma(-x, r, 1.0), r);
+    r = fma(r, fma(-x, r, 1.0), r);
+    return r;
+}
+
+// Column sums of K doubles over the first tv threads (tv a multiple of 32, at
+// most blockDim.x; the other threads hold zeros), two columns per warp: lanes
+// 0-15 of warp w add column 2w and lanes 16-31 column 2w + 1, each lane over
+// rows l, l + 16, ... (fixed order), then a four-level shuffle tree in the
+// half-warp.  Against one column per warp this halves the FP64 adds of the
+// busiest sub-partition when K > number of warps.  sm holds K*T + K doubles
+// (T = blockDim.x); the totals are at sm[K*T + k] after the closing barrier.
+template <int K>
+__device__ __forceinline__ void kx_block_cols2(const double (&v)[K], double *sm, int tv) {
+    const int T = blockDim.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = T >> 5;
+#pragma unroll
+    for (int k = 0; k < K; ++k) sm[k * T + tid] = v[k];
+    __syncthreads();
+    const int l = lane & 15;
+    // column pairs (2w, 2w + 1), (2w + 2 nw, ...): a block with fewer than K/2
+    // warps takes several pairs per warp
+    for (int k0 = 2 * warp; k0 < K; k0 += 2 * nw) {
+        const int k = k0 + (lane >> 4);
+        double x = 0.0;
+        if (k < K) {
+            x = sm[k * T + l];
+            for (int j = l + 16; j < tv; j += 16) x += sm[k * T + j];
+        }
+#pragma unroll
+        for (int off = 8; off; off >>= 1) x += __shfl_xor_sync(0xffffffffu, x, off);
+        if (l == 0 && k < K) sm[K * T + k] = x;
+    }
+    __syncthreads();
+}
+
+// Row combine and projection of the FP32 path (block threads = grid points;
+// threads past n return zeros).  G_i, the row sum of the task partials in
+// double-float, holds sum S (f_n f_m - f_i f_t) / 4^e (2^e the tables' scale),
+// so C_raw,i = c G_i with c = |M|^2 4^e (exponent arithmetic).  The
+// projection of Appendix B in FP64, as on the other paths:
+//   xi_i = |f_i| / 2^e (exact scaling) where above eps_supp f_max / 2^e
+//     (the threshold test in FP32: it only cuts off negligible points);
+//   A = (sum h xi, sum h E xi, sum h E^2 xi), R = (sum h C, sum h E C);
+//   (alpha, beta) = A^-1 R, singular when det A <= 1e-14 A00 A22;
+//   C_proj = C_raw - xi (alpha + beta E).
+// Its FP64 instruction count is cut where exactness does not need it: the
+// scalings and tests work on bit patterns, 1/det is a Newton refinement of a
+// float reciprocal, and the column sums take two columns per warp.
+// RAW: C_raw is returned as well (the diagnostics).  sm: as kx_combine_project.
+template <bool RAW>
+__device__ __forceinline__ kx_row_out kx_combine_project_f32(int n, int chunks, int b, double fi, const kx_pt32 &pt,
+                                                             const kx_batch_views &v, int project, double *sm) {
+    const int i = threadIdx.x, T = blockDim.x;
+    const bool wpts = (i & ~31) < n;   // this warp holds grid points
+    kx_df G = {0.f, 0.f};
+    if (i < n) {
+        // double-float task partials (hi, lo), four independent double-float
+        // sums (slot k mod 4) combined in a fixed order.  Row i's slots are
+        // i + k n, k = 0 .. MT - 1, of instance b (MT = chunks / n): consecutive
+        // rows are adjacent, so each load is coalesced across the warp; the
+        // first rt.y of them are written by the row's tasks (the addresses do
+        // not wait for the task count, which only masks the sums).
+        const int MT = chunks / n;
+        const float2 *pp = reinterpret_cast<const float2 *>(v.partial) + (long long)b * chunks + i;
+        const int ntask = v.rtask[i].y;
+        float h0 = 0.f, l0 = 0.f, h1 = 0.f, l1 = 0.f, h2 = 0.f, l2 = 0.f, h3 = 0.f, l3 = 0.f;
+        // batches of 24 slots: the loads of a batch are in flight together
+        for (int c0 = 0; c0 < MT; c0 += 24) {
+            float2 x[24];
+            const float2 *q = pp + (long long)c0 * n;
+#pragma unroll
+            for (int j = 0; j < 24; ++j, q += n) x[j] = c0 + j < MT ? *q : make_float2(0.f, 0.f);
+#pragma unroll
+            for (int j = 0; j < 24; j += 4) {
+                const int s0 = c0 + j;   // slots s0 .. s0 + 3; those >= ntask hold no task
+                const bool p0 = s0 >= ntask, p1 = s0 + 1 >= ntask, p2 = s0 + 2 >= ntask, p3 = s0 + 3 >= ntask;
+                kx_df_add(h0, l0, p0 ? 0.f : x[j].x);
+                l0 += p0 ? 0.f : x[j].y;
+                kx_df_add(h1, l1, p1 ? 0.f : x[j + 1].x);
+                l1 += p1 ? 0.f : x[j + 1].y;
+                kx_df_add(h2, l2, p2 ? 0.f : x[j + 2].x);
+                l2 += p2 ? 0.f : x[j + 2].y;
+                kx_df_add(h3, l3, p3 ? 0.f : x[j + 3].x);
+                l3 += p3 ? 0.f : x[j + 3].y;
+            }
+        }
+        kx_df_add(h0, l0, h1);
+        l0 += l1;
+        kx_df_add(h2, l2, h3);
+        l2 += l3;
+        kx_df_add(h0, l0, h2);
+        l0 += l2;
+        G = kx_fast_two_sum(h0, l0);
+    }
+    // the tables' scale: 2^e on the dilute path (0: f = 0, no tables), f_max
+    // with quantum statistics; c = |M|^2 scale^2.  (xi uses 2^e, e the
+    // scale's exponent, in both cases: its scale cancels in the projection,
+    // and the threshold scales with it.)
+    const double fsc = v.fsc[b];
+    const bool sok = kx_bits(fsc) != 0ull;
+    const bool pow2 = (kx_bits(fsc) & 0x000fffffffffffffull) == 0ull;
+    const int e = sok ? (int)((kx_bits(fsc) >> 52) & 0x7ff) - 1023 : 0;
+    kx_row_out r;
+    r.Craw = r.Cproj = 0.0;
+    r.alpha = r.beta = 0.0;
+    r.singular = 0;
+    double s[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
+    double xi = 0.0;
+    if (wpts) {
+        const double c = !sok ? 0.0 : (pow2 ? kx_ldexp_bits(v.M2[b], 2 * e) : v.M2[b] * (fsc * fsc));
+        if (i < n) r.Craw = c * kx_df_to_double(G);
+        if (i < n && sok && project) {
+            // xi = |f| 2^-e (values below 2^-60 are far below the threshold)
+            const unsigned long long ab = kx_abs_bits(fi);
+            if ((int)(ab >> 52) - e > 1023 - 60) {
+                const float thr = (float)KX_EPS_SUPP * kx_d2f_pow2(v.fmax[b], -e);
+                const double q = __longlong_as_double((long long)(ab - ((unsigned long long)(long long)e << 52)));
+                xi = kx_d2f(q) > thr ? q : 0.0;
+            }
+        }
+        s[0] = pt.h * xi;
+        s[1] = pt.hE * xi;
+        s[2] = pt.hE2 * xi;
+        s[3] = pt.h * r.Craw;
+        s[4] = pt.hE * r.Craw;
+    }
+    r.Cproj = r.Craw;
+    if (!project) return r;
+    kx_block_cols2<5>(s, sm, (n + 31) & ~31);
+    if (wpts) {
+        // every thread of those warps solves the 2x2 system from the five sums
+        // (the same arithmetic everywhere; no broadcast barrier).  sm[5T .. 5T + 4]
+        // is not written again before the block's next barrier.
+        const double *t = sm + 5 * T;
+        const double t0 = t[0], t1 = t[1], t2 = t[2], t3 = t[3], t4 = t[4];
+        const double p02 = t0 * t2;
+        const double det = fma(-t1, t1, p02);
+        double al = 0.0, be = 0.0;
+        // det > 1e-14 t0 t2 (a positive guard: compare order keys)
+        const int sg = !(kx_order_key(det) > kx_order_key(KX_DET_GUARD * p02)) || (long long)kx_bits(p02) <= 0;
+        if (!sg) {
+            const double rd = kx_rcp_newton(det);
+            al = fma(t3, t2, -t4 * t1) * rd;
+            be = fma(t4, t0, -t3 * t1) * rd;
+        }
+        r.singular = sg;
+        if (RAW) {
+            r.alpha = al;
+            r.beta = be;
+        }
+        if (i < n) r.Cproj = fma(-xi, fma(be, pt.E, al), r.Craw);
     }
     return r;
 }
@@ -1786,7 +2201,13 @@ __global__ void __launch_bounds__(KX_FIN_THREADS)
     // a contraction whose bounded device wait expired left partials unfilled:
     // its C is NaN and the diagnostics say KX_ETIMEOUT
     const int timed_out = *v.err;
-    kx_row_out r = kx_combine_project(n, chunks, path, b, fi, Ei, hi, v, project, smem);
+    kx_row_out r;
+    if (path == KX_FP32) {
+        const kx_pt32 pt = kx_pt32_make(i < n, Ei, hi);
+        r = kx_combine_project_f32<true>(n, chunks, b, fi, pt, v, project, smem);
+    } else {
+        r = kx_combine_project(n, chunks, path, b, fi, Ei, hi, v, project, smem);
+    }
     if (i < n) Cout[(long long)b * n + i] = timed_out ? __longlong_as_double(0x7ff8000000000000ll)
                                                       : (project ? r.Cproj : r.Craw);
     __syncthreads();   // every thread has read the projection sums (sm[5T ..])
@@ -2000,6 +2421,18 @@ cudaError_t kx_launch_mbfit(const kx_kernel *k, int nb, const double *f, double 
 //          reject, next h, MB stopping test, prep(next f).
 // One instance's stage in one block (thread = grid point; smem: 5 blockDim.x +
 // 8 doubles).  Every exit is block-uniform.
+//
+// The last warp of the block is the scalar warp: it makes the attempt's step
+// size and times, the source envelopes, the FP32 path's fit line, and (stage
+// 2) the step-size controller and the new state, while the other warps wait
+// for their loads or build the tables; the FP32 path's launch gives it no grid
+// points (one warp more than the points need), so that this work runs beside
+// the points' work.  On the FP32 path (the F32 kernels) the points' own
+// arithmetic keeps to a few FP64 operations (kx_lean.cuh: every FP64
+// instruction of a warp holds its sub-partition's FP64 unit for about 64
+// cycles): the combine and projection of kx_combine_project_f32, the tests
+// of f on bit patterns, the error ratio in FP32 from one FP64 difference, and
+// the FP64 sums of the Heun update itself.
 template <bool Q, bool F32 = true>
 __device__ __forceinline__ void kx_stage_body(int b, int n, int chunks, int path, const double *__restrict__ E,
                               const double *__restrict__ h, kx_batch_views v,
@@ -2007,24 +2440,35 @@ __device__ __forceinline__ void kx_stage_body(int b, int n, int chunks, int path
                               double *smem) {
     __shared__ unsigned long long s_keys[3 * 32];
     __shared__ double s_env[KX_MAX_SRC];
+    __shared__ double s_h[2];   // this attempt's h_try; stage 2: the time an accepted step reaches
+    __shared__ int s_fl[3];     // stage 2: that time >= t_end; an MB check is due then; t >= t_end
     __shared__ float2 s_next;   // FP32 dilute path: the line of the previous prep's fit
-    __shared__ double4_32a s_ltab[F32 ? 256 : 1];   // FP32 dilute path: the log2 table
+    __shared__ float4 s_ltab[F32 ? 256 : 1];   // FP32 dilute path: the double-float log2 table
     const int i = threadIdx.x;
     const bool in = i < n;
-    // The grid and the source rows do not change while a graph of attempts
-    // runs: their loads are issued before the wait for the predecessor kernel
-    // (programmatic dependent launch), so that they overlap its tail.
+    const int lane = i & 31, wid = i >> 5, lastw = (blockDim.x >> 5) - 1;
+    const bool sw = wid == lastw;   // the scalar warp
+    // The grid, the source rows and the per-point constants do not change while
+    // a graph of attempts runs: they are loaded and made before the wait for
+    // the predecessor kernel (programmatic dependent launch), overlapping its
+    // tail.
     const double Ei = in ? E[i] : 0.0, hi = in ? h[i] : 0.0, E0 = E[0];
     kx_prep_pre pre;
     pre.K = in ? Ei - E0 : 0.0;
     pre.Kf = (float)pre.K;
+    pre.Kl = (float)(pre.K - (double)pre.Kf);
     pre.hf = (float)hi;
     pre.have = path == KX_FP32;
-    pre.ltab = nullptr;
-    if constexpr (F32 && !Q) {
-        // the log2 table is constant: copied before the wait for the predecessor
-        for (int t = threadIdx.x; t < 256; t += blockDim.x) s_ltab[t] = g_kx_log2_tab[t];
-        pre.ltab = s_ltab;   // (read by the prep, after the barriers that follow)
+    pre.ltabf = nullptr;
+    kx_pt32 pt = {};
+    if constexpr (F32) {
+        pt = kx_pt32_make(in, Ei, hi);
+        if constexpr (!Q) {
+            for (int t = threadIdx.x; t < 256; t += blockDim.x) s_ltab[t] = g_kx_log2_tab_f[t];
+            pre.ltabf = s_ltab;   // (read by the prep, after the barriers that follow)
+        }
+        // (the values are made here, not after the wait)
+        asm volatile("" ::"d"(pt.hE), "d"(pt.hE2), "f"(pre.Kl), "f"(pre.hf), "f"(pre.Kf));
     }
     const kx_src_dev &src = sv.src[b];
     const int n_src = src.n_src;
@@ -2048,27 +2492,74 @@ __device__ __forceinline__ void kx_stage_body(int b, int n, int chunks, int path
     // (the quantum path's lines; the dilute FP32 path takes its line from s_next)
     pre.lines = (Q && path == KX_FP32) ? v.fit[b] : make_float4(0.f, 0.f, 0.f, 0.f);
     // Every thread takes its copy of the instance state here, before the first
-    // block barrier: thread 0 rewrites the state at the end of the stage, and a
-    // warp that read it after that write could disagree with the others on
-    // block-uniform decisions (the MB check, which holds barriers).  (Thread 0's
-    // early write of h_try and last in stage 1 is read only by stage 2.)
+    // block barrier: the scalar warp rewrites the state at the end of the
+    // stage, and a warp that read it after that write could disagree with the
+    // others on block-uniform decisions (the MB check, which holds barriers).
+    // (The scalar warp's early write of h_try and last in stage 1 is read only
+    // by stage 2.)
     const int done0 = st->done, skip2_0 = st->skip2;
     const double t = st->t, t_end = st->t_end, h_state = st->h, h_try_state = st->h_try;
     const int last_state = st->last;
     const long long steps0 = st->steps, rejects0 = st->rejects;
     const double l1_0 = st->l1, T0 = st->T, lnz0 = st->lnz;
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, lastw = (blockDim.x >> 5) - 1;
-    const bool envw = wid == lastw && lane < n_src;   // the lanes that own the envelopes
+    const bool envw = sw && lane < n_src;   // the lanes that own the envelopes
     const int env_ok = st->env_ok;
     const double env_t = st->env_t, env_mine = envw ? st->env[lane] : 0.0;
-    // the line for this stage's prep, from the previous prep's per-warp fit sums,
-    // on the last warp (a warp without grid points when the launch adds one);
-    // published by the barriers before the prep
-    if (!Q && path == KX_FP32 && wid == lastw && lane == 0) s_next = kx_fit_line(v, b);
-    // the row combine and the projection first: their loads do not wait for
-    // the state (a finished instance computes them in vain and writes nothing)
+    auto envelope = [&](double tt) {
+        return tt >= src.t_on[lane] ? src.rate[lane] * kx_exp(-(tt - src.t_on[lane]) / src.tau[lane]) : 0.0;
+    };
+    const bool live = !done0 && !(flag_in & 4) && !(stage == 2 && skip2_0);
+    if (sw && live) {
+        // the scalar warp, while the point warps wait for their partial sums:
+        // this attempt's h_try (stage 1: the state's h clamped to [h_min, h_max]
+        // and to t_end), the envelopes at this stage's time, and the times and
+        // flags of an accepted stage-2 step
+        double htry;
+        if (stage == 1) {
+            htry = h_state;
+            if (!sv.fixed) {
+                if (htry > sv.h_max) htry = sv.h_max;
+                if (htry < sv.h_min) htry = sv.h_min;
+            }
+            int last = 0;
+            if (t + htry >= t_end) {
+                htry = t_end - t;
+                last = 1;
+            }
+            if (lane == 0) {
+                st->h_try = htry;
+                st->last = last;
+            }
+        } else {
+            htry = h_try_state;
+        }
+        // source envelopes at this stage's time: the previous stage kernel made
+        // them for this time (during an idle wait of its prep), else (a new
+        // state) they are made here
+        const double tS = stage == 1 ? t : t + htry;
+        if (envw) s_env[lane] = (env_ok && env_t == tS) ? env_mine : envelope(tS);
+        if (lane == 0) {
+            s_h[0] = htry;
+            if (stage == 2) {
+                const double tn = last_state ? t_end : t + htry;
+                s_h[1] = tn;
+                s_fl[0] = tn >= t_end;
+                s_fl[1] = sv.check_every > 0 && sv.l1_tol > 0.0 && tn >= src.t_off;
+                s_fl[2] = t >= t_end;
+            }
+            // the line for this stage's prep, from the previous prep's per-warp fit sums
+            if (!Q && path == KX_FP32) s_next = kx_fit_line(v, b);
+        }
+    }
+    // the row combine and the projection: their loads do not wait for the state
+    // (a finished instance computes them in vain and writes nothing)
     const double fcur = stage == 1 ? f0 : fpv;
-    kx_row_out r = kx_combine_project(n, chunks, path, b, fcur, Ei, hi, v, sv.project, smem);
+    kx_row_out r;
+    if constexpr (F32) {
+        r = kx_combine_project_f32<false>(n, chunks, b, fcur, pt, v, sv.project, smem);
+    } else {
+        r = kx_combine_project(n, chunks, path, b, fcur, Ei, hi, v, sv.project, smem);
+    }
     if (done0) return;
     if (flag_in & 4) {   // its partials are incomplete: stop the instance, report it
         __syncthreads();
@@ -2083,52 +2574,33 @@ __device__ __forceinline__ void kx_stage_body(int b, int n, int chunks, int path
         if (threadIdx.x == 0) st->skip2 = 0;
         return;
     }
-    double htry;
-    if (stage == 1) {
-        htry = h_state;
-        if (!sv.fixed) {
-            if (htry > sv.h_max) htry = sv.h_max;
-            if (htry < sv.h_min) htry = sv.h_min;
-        }
-        int last = 0;
-        if (t + htry >= t_end) {
-            htry = t_end - t;
-            last = 1;
-        }
-        if (threadIdx.x == 0) {
-            st->h_try = htry;
-            st->last = last;
-        }
-    } else {
-        htry = h_try_state;
-    }
-    // source envelopes at this stage's time, one per source on the last warp:
-    // the previous stage kernel made them for this time (during an idle wait of
-    // its prep), else (a new state) they are made here
-    auto envelope = [&](double tt) {
-        return tt >= src.t_on[lane] ? src.rate[lane] * kx_exp(-(tt - src.t_on[lane]) / src.tau[lane]) : 0.0;
-    };
-    const double tS = stage == 1 ? t : t + htry;
-    if (envw) s_env[lane] = (env_ok && env_t == tS) ? env_mine : envelope(tS);
     const double C = sv.project ? r.Cproj : r.Craw;
-    __syncthreads();   // publishes s_env
-    // (threads past n skip the FP64 arithmetic: they hold kv = 0 and f = 0)
+    __syncthreads();   // publishes s_env, s_h, s_fl, s_next
+    const double htry = s_h[0];
     double kv = 0.0;
     if (in) {
-        double Si = 0.0;
+        if constexpr (F32) {
+            kv = C;
 #pragma unroll
-        for (int k = 0; k < KX_MAX_SRC; ++k)
-            if (k < n_src) Si += s_env[k] * shp[k];
-        kv = C + Si;
-        if (sv.hscale != 1.0) kv *= sv.hscale;   // d/du = (C + S) / H (expanding universe)
+            for (int k = 0; k < KX_MAX_SRC; ++k)
+                if (k < n_src) kv = fma(s_env[k], shp[k], kv);
+        } else {
+            double Si = 0.0;
+#pragma unroll
+            for (int k = 0; k < KX_MAX_SRC; ++k)
+                if (k < n_src) Si += s_env[k] * shp[k];
+            kv = C + Si;
+        }
+        // d/du = (C + S) / H in the expanding universe (hscale = 1/H), else 1
+        if (kx_bits(sv.hscale) != 0x3ff0000000000000ull) kv *= sv.hscale;
     }
     if (stage == 1) {
-        const double fpi = in ? f0 + htry * kv : 0.0;
+        const double fpi = in ? fma(htry, kv, f0) : 0.0;
         // one reduction for both flags (2 = non-finite, 1 = negative) and for
         // max |f_p| of the next prep
         unsigned long long keys[2] = {
-            (in && !isfinite(fpi)) || flag_in ? 2ull : ((in && fpi < 0.0) ? 1ull : 0ull),
-            (in && isfinite(fpi)) ? (unsigned long long)__double_as_longlong(fabs(fpi)) : 0ull};
+            ((in && kx_nonfinite(fpi)) || flag_in) ? 2ull : ((in && kx_negative(fpi)) ? 1ull : 0ull),
+            (in && !kx_nonfinite(fpi)) ? kx_abs_bits(fpi) : 0ull};
         kx_block_max_keys<2>(keys, s_keys);
         const unsigned long long key = keys[0];
         if (key == 2ull) {
@@ -2181,24 +2653,40 @@ __device__ __forceinline__ void kx_stage_body(int b, int n, int chunks, int path
     // stage 2: one reduction for the flags and the error norm (keys ordered
     // non-finite > negative > the bits of err >= 0), and for max |f_c| and
     // max |f| (the next prep takes the one the step decision keeps)
-    const double fci = in ? f0 + 0.5 * htry * (k1v + kv) : 0.0;
-    // The error ratio only decides acceptance and scales h.  On the FP32 path,
-    // whose C carries FP32 rounding (~1e-7 relative) anyway, it is divided in
-    // FP32 from the FP64 difference and scale (an FP64 division is a long chain
-    // of FP64 operations on this part); the plain FP64 path divides in FP64.
-    double e = 0.0;
+    double fci = 0.0, e = 0.0;
     if (in) {
-        const double num = fabs(fci - fpv), den = sv.atol + sv.rtol * fabs(fci);
-        e = path == KX_FP32 ? (double)((float)num / (float)den) : num / den;
+        if constexpr (F32) {
+            // h/2 exactly (exponent arithmetic).  The error norm in FP64: the
+            // point passes when |f_c - f_p| <= atol + rtol |f_c|, an exact
+            // comparison of non-negative bit patterns; the ratio itself, which
+            // only scales the next h, is divided in FP32 (both terms scaled by
+            // the same power of two first) and then held on the right side of 1
+            fci = fma(kx_ldexp_bits(htry, -1), k1v + kv, f0);
+            const unsigned long long nb = kx_abs_bits(fci - fpv);
+            const double den = fma(sv.rtol, __longlong_as_double((long long)kx_abs_bits(fci)), sv.atol);
+            const unsigned long long db = kx_bits(den);
+            if (db == 0ull) {
+                e = nb == 0ull ? __longlong_as_double(0x7ff8000000000000ll) : INFINITY;   // 0/0 fails, as x/0
+            } else {
+                const int sh = 1023 - (int)(db >> 52);
+                const float ratio = kx_d2f_pow2(__longlong_as_double((long long)nb), sh) / kx_d2f_pow2(den, sh);
+                unsigned long long eb = kx_bits(kx_f2d(ratio));
+                if (nb > db) eb = eb > 0x3ff0000000000000ull ? eb : 0x3ff0000000000001ull;
+                else eb = eb < 0x3ff0000000000000ull ? eb : 0x3ff0000000000000ull;
+                e = __longlong_as_double((long long)eb);
+            }
+        } else {
+            fci = f0 + 0.5 * htry * (k1v + kv);
+            e = fabs(fci - fpv) / (sv.atol + sv.rtol * fabs(fci));
+        }
     }
     const unsigned long long kneg = KX_KEY_NONFINITE - 1ull;   // bits of +inf
     unsigned long long key;
-    if ((in && !isfinite(fci)) || flag_in) key = KX_KEY_NONFINITE;
-    else if (in && fci < 0.0) key = kneg;
-    else key = (unsigned long long)__double_as_longlong(e);
-    unsigned long long keys[3] = {
-        key, (in && isfinite(fci)) ? (unsigned long long)__double_as_longlong(fabs(fci)) : 0ull,
-        in ? (unsigned long long)__double_as_longlong(fabs(f0)) : 0ull};
+    if ((in && kx_nonfinite(fci)) || flag_in) key = KX_KEY_NONFINITE;
+    else if (in && kx_negative(fci)) key = kneg;
+    else key = kx_bits(e);
+    unsigned long long keys[3] = {key, (in && !kx_nonfinite(fci)) ? kx_abs_bits(fci) : 0ull,
+                                  in ? kx_abs_bits(f0) : 0ull};
     kx_block_max_keys<3>(keys, s_keys);
     key = keys[0];
     if (key == KX_KEY_NONFINITE) {
@@ -2218,20 +2706,17 @@ __device__ __forceinline__ void kx_stage_body(int b, int n, int chunks, int path
         }
         return;
     }
+    // err >= 0 (or NaN) as bits: err <= 1 is an integer comparison
     const double err = neg ? INFINITY : __longlong_as_double((long long)key);
-    const int accept = sv.fixed ? 1 : (!neg && err <= 1.0);
-    double tn = t;
-    if (accept) {
-        if (in) fb[i] = fci;
-        tn = last_state ? t_end : t + htry;
-    }
+    const int accept = sv.fixed ? 1 : (!neg && key <= 0x3ff0000000000000ull);
+    const double tn = accept ? s_h[1] : t;
+    if (accept && in) fb[i] = fci;
     const double fnew = accept ? fci : f0;
-    long long steps = steps0 + (accept ? 1 : 0);
-    long long rejects = rejects0 + (accept ? 0 : 1);
+    const long long steps = steps0 + (accept ? 1 : 0);
+    const long long rejects = rejects0 + (accept ? 0 : 1);
     int done = 0, converged = 0;
     double fit[3] = {l1_0, T0, lnz0};
-    if (accept && sv.check_every > 0 && sv.l1_tol > 0.0 && steps % sv.check_every == 0 &&
-        tn >= src.t_off) {
+    if (accept && s_fl[1] && steps % sv.check_every == 0) {
         double o[3];
         kx_mb_fit_block(n, in ? fnew : 0.0, Ei, hi, E0, T0, o, smem);
         fit[0] = o[2];
@@ -2244,14 +2729,16 @@ __device__ __forceinline__ void kx_stage_body(int b, int n, int chunks, int path
     }
     int status = KX_OK;
     if (!done) {
-        if (tn >= t_end) done = 1;
-        else if (steps + rejects >= max_attempts) {
+        if (accept ? s_fl[0] : s_fl[2]) {
+            done = 1;
+        } else if (steps + rejects >= max_attempts) {
             done = 1;
             status = KX_ENOCONV;
         }
     }
-    if (threadIdx.x == 0) {
-        // step-size controller (one thread: only the state keeps h)
+    if (sw && lane == 0) {
+        // step-size controller and the new state (the scalar warp: only the
+        // state keeps h)
         double hnext;
         if (sv.fixed) {
             hnext = htry;
@@ -2259,11 +2746,11 @@ __device__ __forceinline__ void kx_stage_body(int b, int n, int chunks, int path
             hnext = 0.5 * htry;
         } else if (path == KX_FP32) {
             // the same factor in FP32 (err came from an FP32 ratio)
-            const float ef = (float)err;
+            const float ef = kx_d2f(err);
             float fac = ef > 0.f ? 0.9f * rsqrtf(ef) : 5.f;
             if (fac > 5.f) fac = 5.f;
             if (fac < 0.2f) fac = 0.2f;
-            hnext = htry * (double)fac;
+            hnext = htry * kx_f2d(fac);
         } else {
             double fac = err > 0.0 ? 0.9 / sqrt(err) : 5.0;
             if (fac > 5.0) fac = 5.0;

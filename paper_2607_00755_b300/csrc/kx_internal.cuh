@@ -59,6 +59,7 @@ struct kx_kernel {
     long long Vt;        // kept vectors, all rows
     int vpl;             // vectors per lane of a unit
     int ntask;           // streaming tasks
+    int bin_units;       // the most units in one bin (sizes the staged variant's shared memory)
     int tslots;          // partial slots per instance: n x MT, MT = largest row task count rounded up to even
     // batched (split TF32) tables: the GEMMs take the instances as rows and the
     // grid points i as columns (64-row operand tiles of i, 16-wide k blocks)
@@ -219,6 +220,13 @@ cudaError_t kx_launch_prep(const kx_kernel *k, int B, const double *f, const kx_
 // Adds the launches it made to *launches.  0 on success, -1 on a CUDA error.
 int kx_tune_contraction(const kx_kernel *k, int B, const double *f, const kx_batch_views &v,
                         const kx_inst_state *st, cudaStream_t s, long long *launches);
+// The solve tunes in place instead (its own attempt graphs, one per candidate,
+// timed on real attempts): the candidate variants of a launch (0 or 1: nothing
+// to choose), whether its (device, n, batch, grid share) has a choice, and
+// pinning one for later launches and captures.
+int kx_stream_candidate_list(const kx_kernel *k, int B, int grid_div, int *cand);
+bool kx_stream_is_tuned(const kx_kernel *k, int B, int grid_div);
+void kx_stream_pin(const kx_kernel *k, int B, int grid_div, int variant);
 // pdl: launch with programmatic stream serialization where the kernel supports
 // it (the FP32 streaming contraction and the stage kernel wait for their
 // predecessor inside; other kernels launch in full stream order).

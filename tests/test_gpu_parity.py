@@ -285,6 +285,19 @@ def test_streaming_variants_are_bitwise_identical(ctx, kx, N):
         ctx.set_stream_variant(N, 1, 1)
     with pytest.raises(kx.KxError):
         ctx.set_stream_variant(N, 3, 3)
+    with pytest.raises(kx.KxError):
+        ctx.set_stream_variant(N, 8, 4)
+    # the staged-share variant (batches of up to four): the same bits as the
+    # register pipeline and as the batch of eight, instance by instance
+    for Bs in (1, 2, 3, 4):
+        got = []
+        for var in (0, 4):
+            ctx.set_stream_variant(N, Bs, var)
+            C, _ = ctx.collision(k, dev(f[:Bs]), sig[:Bs])
+            got.append(C.cpu().numpy())
+            ctx.set_stream_variant(N, Bs, -1)
+        np.testing.assert_array_equal(got[1], got[0])
+        np.testing.assert_array_equal(got[1], out[0][:Bs])
     k.release()
 
 
@@ -473,6 +486,48 @@ def test_table_log2_exp_against_cuda_and_libm(ctx, kx):
     assert out[-1, 0] == np.inf and out[-2, 0] == 0.0 and out[y.size - 9, 0] == 1.0
     nan = ctx.math_check(1, torch.as_tensor(np.array([np.nan]), device="cuda")).cpu().numpy()
     assert np.isnan(nan[0, 0])
+
+
+def test_lean_log2_and_conversions(ctx, kx):
+    """The FP32 path's integer-pipe conversions and double-float log2 against
+    numpy: float -> double exact for every class of float; double -> float
+    round-to-nearest-even bit for bit in the float normal range (ties, the
+    carry into the exponent, overflow to inf), zero below 2^-126; log2 of a
+    normal double to 3e-14 absolute (plus the FP64 rounding of the check's
+    own sum)."""
+    import torch
+    rng = np.random.default_rng(5)
+    x = np.concatenate([10.0 ** rng.uniform(-300, 300, 20000), 1.0 + rng.uniform(0, 1, 4000),
+                        1.0 + np.arange(256) / 256.0, np.nextafter(1.0 + np.arange(1, 257) / 256.0, 0.0),
+                        2.0 ** np.arange(-1000, 1000, 13.0), [1.0, 2.0, 0.5, 1e-300, 1.7e308]])
+    out = ctx.math_check(2, torch.as_tensor(x, device="cuda")).cpu().numpy()
+    ref = np.log2(x)
+    assert np.all(np.abs(out[:, 0] - ref) <= 3e-14 + 2 * np.spacing(np.abs(ref))), \
+        np.max(np.abs(out[:, 0] - ref))
+    # double -> float: random doubles in the float range, exact ties, the largest float
+    f = rng.uniform(-1, 1, 20000) * 10.0 ** rng.uniform(-37, 38, 20000)
+    f = f[np.abs(f) >= 2.0 ** -125]   # (the library flushes below the float normal range)
+    base = np.float32(rng.uniform(1, 2, 2000)).astype(np.float64)
+    ties = base + np.spacing(np.float32(base)).astype(np.float64) / 2   # halfway between floats
+    big = np.array([3.4028234663852886e38, 3.4028235677973366e38, 3.5e38, -3.5e38, np.inf, -np.inf, 0.0, -0.0])
+    y = np.concatenate([f, ties, -ties, big])
+    out = ctx.math_check(3, torch.as_tensor(y, device="cuda")).cpu().numpy()
+    with np.errstate(over="ignore"):
+        want = y.astype(np.float32).astype(np.float64)
+    assert np.array_equal(out[:, 0], want)
+    assert np.array_equal(np.signbit(out[:, 0]), np.signbit(want))
+    tiny = np.array([1e-39, -1e-39, 1e-45, 2.0 ** -127, 1e-300])
+    out = ctx.math_check(3, torch.as_tensor(tiny, device="cuda")).cpu().numpy()
+    assert np.all(out[:, 0] == 0.0) and np.array_equal(np.signbit(out[:, 0]), np.signbit(tiny))
+    nan = ctx.math_check(3, torch.as_tensor(np.array([np.nan]), device="cuda")).cpu().numpy()
+    assert np.isnan(nan[0, 0])
+    # float -> double: normals, subnormals, zeros, infinities
+    z = np.concatenate([f, [1e-38, 1e-40, -1e-40, 1.4e-45, -1.4e-45, 2.0 ** -140, 0.0, -0.0, np.inf, -np.inf,
+                            3.4e38]])
+    out = ctx.math_check(4, torch.as_tensor(z, device="cuda")).cpu().numpy()
+    assert np.array_equal(out[:, 0], out[:, 1])
+    assert np.array_equal(np.signbit(out[:, 0]), np.signbit(out[:, 1]))
+    assert np.array_equal(out[:, 0], z.astype(np.float32).astype(np.float64))
 
 
 # ----------------------------------------------- the bench workload itself ---
