@@ -33,21 +33,67 @@ import kx_inputs as ki  # noqa: E402
 METRIC = "collision-term evals/s & solves/s vs plain FP64 path; p50/p99 solve latency"
 UNIT = "evals/s"
 L2_FLUSH_BYTES = 512 << 20     # > 126 MB L2
-# DRAM bytes (read + write) per launch from one ncu capture of the current kernels
-# (profiles/k_stream32r_n128_batch4.md, profiles/k_stream32r_single_n384_n512.md); None
-# whenever those kernels have changed since the capture.
-NCU_TRAFFIC = {"stream_n128_b4": 6.783232e6, "stream_n384": 172.422656e6,
-               "stream_n512": 406.062848e6 + 0.040448e6}
+CSRC = os.path.join(ROOT, "paper_2607_00755_b300", "csrc")
+# DRAM bytes (read + write) per launch from one-pass ncu captures
+# (dram__bytes_read.sum + dram__bytes_write.sum) of the named kernel, with the
+# sha1 of the CUDA source file it was built from at capture time.  A capture
+# is used only while the live kernel has the same name and algorithmic bytes
+# and its source file is unchanged; otherwise the line's traffic is null and
+# says why.
+NCU_TRAFFIC = {
+    "stream_n128_b4": {"kernel": "k_stream32r<1,2>", "stream_bytes": None, "file": "kx_contract.cu",
+                       "sha1": None, "bytes": None},
+    "stream_n384": {"kernel": "k_stream32r<1,4>", "stream_bytes": None, "file": "kx_contract.cu",
+                    "sha1": None, "bytes": None},
+    "stream_n512": {"kernel": "k_stream32r<1,4>", "stream_bytes": None, "file": "kx_contract.cu",
+                    "sha1": None, "bytes": None},
+    "stage_n128_b4": {"kernel": "k_stage<1,0>", "stream_bytes": None, "file": "kx_contract.cu",
+                      "sha1": None, "bytes": None},
+}
+
+
+def source_sha1(name):
+    import hashlib
+    try:
+        with open(os.path.join(CSRC, name), "rb") as fh:
+            return hashlib.sha1(fh.read()).hexdigest()
+    except OSError:
+        return None
+
+
+def traffic_for(key, kernel, stream_bytes=None):
+    """(bytes per launch or None, note) for a kernel from its ncu capture."""
+    cap = NCU_TRAFFIC.get(key)
+    if not cap or cap["bytes"] is None:
+        return None, "no ncu capture of this kernel"
+    if not kernel.startswith(cap["kernel"]):
+        return None, f"the capture is of {cap['kernel']}, the run uses {kernel}"
+    if cap["stream_bytes"] is not None and stream_bytes is not None and cap["stream_bytes"] != stream_bytes:
+        return None, "the kernel's tables changed since the capture"
+    if source_sha1(cap["file"]) != cap["sha1"]:
+        return None, f"{cap['file']} changed since the capture"
+    return cap["bytes"], "one ncu capture (dram__bytes_read.sum + dram__bytes_write.sum)"
 
 
 def stream_kernel_name(ctx, n, batch):
     """Name of the FP32 streaming kernel the contraction of (n, batch) uses."""
     var, tuned = ctx.stream_variant(n, batch)
     vpl = 2 if n <= 160 else 4
+    if var == 4:
+        per = 1 if batch == 1 else (2 if batch == 2 else 4)
+        return f"k_stream32p<{per},{vpl}> (whole share staged, {'tuned' if tuned else 'default rule'})"
     per = {0: 1, 1: 2, 2: 4, 3: 4}[var]
     name = f"k_stream32<4,4> (bulk-copy staged)" if var == 2 else f"k_stream32r<{per},{vpl}>"
     return f"{name} ({per} instance{'s' if per > 1 else ''} per pass, {'tuned' if tuned else 'default rule'})"
+
+
 SOLVE = dict(t_end=1e5, h0=1e-3, rtol=1e-6, l1_tol=1e-3, check_every=10, max_attempts=2_000_000)
+# FP64 operations the method does per grid point in one Heun stage (FMA = 2):
+# C_raw = |M|^2 G (1), xi (1), the five projection moments (5 products, 5 sums),
+# the correction xi (alpha + beta E) (2 FMA = 4), the sources (2 FMA = 4),
+# k = C + S (1), and the update: stage 1 f + h k (2); stage 2 f + h/2 (k1 + k2)
+# (3) and the error ratio |f_c - f_p| / (atol + rtol |f_c|) (4).
+STAGE_FLOP_PER_POINT = {1: 23, 2: 28}
 
 
 def peaks():
@@ -189,21 +235,41 @@ def run_contraction_only(args):
     return 0
 
 
+def tf32_peak():
+    """TF32 dense peak: the measured bf16 figure times the nominal TF32/BF16
+    ratio (1.1 / 2.25 PFLOP/s)."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            p = json.load(fh)
+        return float(p["bf16_tflops"]) * 1.1 / 2.25, "measured bf16 x nominal tf32/bf16"
+    except Exception:
+        return 1800.0 * 1.1 / 2.25, "fallback bf16 x nominal tf32/bf16"
+
+
 def measure_batched(ctx, kx, torch, flush, iters=5, check_sample=4):
     """Batched configuration: B = 512 seeded bimodal distributions sharing one
     N = 192 kernel (q in [1e-3, 1e2]); projected C per instance through
-    kx_collision, split-TF32 tensor-core path vs the plain FP64 path on the same
-    inputs.  Returns the line and the first `check_sample` instances' outputs
-    (compared with the FP64 oracle in the CPU-baseline leg)."""
+    kx_collision on the split-TF32 tensor-core path, with the exact loss and
+    with the loss as a Chebyshev GEMM (K = 16), against the plain FP64 path on
+    the same inputs.  Useful FLOP of one batch: the gain GEMM 2 P N B over the
+    P = N (N + 1) / 2 symmetric pairs, and the Chebyshev loss GEMM 2 N (N K) B;
+    split TF32 issues three products for each.  Returns the line and the first
+    `check_sample` instances' outputs (compared with the FP64 oracle in the
+    CPU-baseline leg)."""
     c = ki.config3()
     q, f, B = c["q"], c["f"], c["f"].shape[0]
+    n = q.size
     stream = torch.cuda.current_stream()
     fd = torch.as_tensor(f, device="cuda")
     out = {}
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     Cs = {}
-    for name, prec, reps in (("split_tf32", kx.SPLIT_TF32, iters), ("fp64", kx.FP64, 2)):
-        k = ctx.build_kernel(q, precision=prec)
+    peak, peak_src = tf32_peak()
+    P = n * (n + 1) // 2
+    for name, prec, lt, reps in (("split_tf32_exact_loss", kx.SPLIT_TF32, 0, iters),
+                                 ("split_tf32_cheb16_loss", kx.SPLIT_TF32, 16, iters),
+                                 ("fp64", kx.FP64, 0, 2)):
+        k = ctx.build_kernel(q, precision=prec, loss_terms=lt) if lt else ctx.build_kernel(q, precision=prec)
         C, _ = ctx.collision(k, fd, c["sigma"])
         tot = 0.0
         for _ in range(reps):
@@ -214,12 +280,27 @@ def measure_batched(ctx, kx, torch, flush, iters=5, check_sample=4):
             e1.synchronize()
             tot += e0.elapsed_time(e1)
         Cs[name] = C[:check_sample].cpu().numpy()
-        out[name] = {"evals_per_s": B * reps / (tot / 1e3), "ms_per_batch": tot / reps}
+        ms = tot / reps
+        row = {"evals_per_s": B * reps / (tot / 1e3), "ms_per_batch": ms}
+        if prec == kx.SPLIT_TF32:
+            gain = 2.0 * P * n * B
+            loss = 2.0 * n * (n * lt) * B if lt else 0.0
+            useful = gain + loss
+            row.update({"useful_gflop": useful / 1e9, "useful_tflops": useful / (ms * 1e-3) / 1e12,
+                        "issued_tflops_split3": 3 * useful / (ms * 1e-3) / 1e12,
+                        "frac_of_tf32_peak_issued": 3 * useful / (ms * 1e-3) / 1e12 / peak,
+                        "tf32_peak_tflops": peak, "peak_source": peak_src,
+                        "note": "whole kx_collision call (prep, both GEMMs or the exact loss, "
+                                "row combine and projection), cold L2"})
+        out[name] = row
         k.release()
     line = {"workload": "B=512 distributions sharing one N=192 kernel, q in [1e-3,1e2], "
                         "projected C (kx_collision)",
-            "split_tf32": out["split_tf32"], "fp64_path": out["fp64"],
-            "speedup_vs_fp64": out["split_tf32"]["evals_per_s"] / out["fp64"]["evals_per_s"],
+            "split_tf32": out["split_tf32_exact_loss"],
+            "split_tf32_cheb16": out["split_tf32_cheb16_loss"],
+            "fp64_path": out["fp64"],
+            "speedup_vs_fp64": out["split_tf32_exact_loss"]["evals_per_s"] / out["fp64"]["evals_per_s"],
+            "speedup_vs_fp64_cheb16": out["split_tf32_cheb16_loss"]["evals_per_s"] / out["fp64"]["evals_per_s"],
             "max_rel_err_vs_oracle": None, "oracle_sample": f"{check_sample} instances"}
     check = {"q": q, "f": f[:check_sample], "sigma": c["sigma"][:check_sample], "C": Cs}
     return line, check
@@ -355,10 +436,41 @@ def measure_uneven(ctx, kx, t_end=5.0, fp64_per_size=4):
         out[name] = {"instances": len(tickets), "completed": ok, "seconds": dt,
                      "solves_per_s": ok / dt, "evals_per_s": evals / dt, "evals": evals,
                      "kernel_build_s": t_build}
+    # the same 1024 instances as one sequence of grouped launches (kx_solve_grouped:
+    # per Heun stage one gain-GEMM, one loss launch and one stage launch over all
+    # five grids, captured in a graph of attempts), exact loss and Chebyshev K = 16
+    import torch
+    sizes = (64, 96, 128, 192, 256)
+    grouped = {}
+    for lt in (0, 16):
+        ks = [ctx.build_kernel(c["grids"][n], precision=kx.SPLIT_TF32, loss_terms=lt) for n in sizes]
+        idx = [np.nonzero(c["ns"] == n)[0] for n in sizes]
+        fs = [torch.as_tensor(np.stack([c["f"][i] for i in ii]), device="cuda") for ii in idx]
+        sg = [c["sigma"][ii] for ii in idx]
+        gp = dict(par, t_end=t_end, h0=1e-3)
+        ctx.solve_grouped(ks, [f.clone() for f in fs], sg, **dict(gp, t_end=1e-3))   # warm
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        res = ctx.solve_grouped(ks, fs, sg, **gp)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        done = sum(1 for r in res for x in r if x["status"] == 0)
+        evals = sum(x["evals"] for r in res for x in r)
+        grouped["cheb16" if lt else "exact_loss"] = {
+            "instances": len(c["ns"]), "completed": done, "seconds": dt, "solves_per_s": done / dt,
+            "evals_per_s": evals / dt, "evals": evals}
+        for k in ks:
+            k.release()
     return {"workload": "1024 instances, N uniform over {64,96,128,192,256}, sigma logU[1e-3,1], "
                         f"no sources, each integrated to t={t_end}; all admitted at once",
             "split_tf32": out["split_tf32"], "fp64_path_sample": out["fp64"],
-            "speedup_vs_fp64_evals": out["split_tf32"]["evals_per_s"] / out["fp64"]["evals_per_s"]}
+            "speedup_vs_fp64_evals": out["split_tf32"]["evals_per_s"] / out["fp64"]["evals_per_s"],
+            "grouped_launch": grouped,
+            "grouped_speedup_vs_fp64_evals": {k2: v2["evals_per_s"] / out["fp64"]["evals_per_s"]
+                                              for k2, v2 in grouped.items()},
+            "note": "split_tf32: the solve server (one group and captured graph per grid, groups "
+                    "on concurrent streams); grouped_launch: kx_solve_grouped, one launch per "
+                    "phase over all grids; fp64_path_sample: the server on the plain FP64 path"}
 
 
 def serve_stream(kx, ctx, reqs, precision, budget=96 << 30, slots=2, phases=("run",)):
@@ -369,6 +481,7 @@ def serve_stream(kx, ctx, reqs, precision, budget=96 << 30, slots=2, phases=("ru
                     precision=precision, **par)
     res = {}
     for phase in phases:
+        srv.reset_latency()   # this phase's latency quantiles only
         s0 = srv.stats()
         t0 = time.perf_counter()
         tickets = []
@@ -380,7 +493,7 @@ def serve_stream(kx, ctx, reqs, precision, budget=96 << 30, slots=2, phases=("ru
                                        t_end=1e5, h0=1e-3), r["n"]))
         lat, ok, conv = [], 0, 0
         for t, n in tickets:
-            rc, _, rr = srv.poll(t, n, timeout=1800.0)
+            rc, _, rr = srv.poll(t, n, timeout=3600.0)
             if rc == kx.OK:
                 ok += 1
                 conv += int(rr["converged"])
@@ -389,22 +502,32 @@ def serve_stream(kx, ctx, reqs, precision, budget=96 << 30, slots=2, phases=("ru
         s1 = srv.stats()
         res[phase] = {"requests": len(reqs), "completed": ok, "converged": conv,
                       "failed": len(reqs) - ok, "seconds": dt, "solves_per_s": ok / dt,
+                      "converged_solves_per_s": conv / dt,
                       "evals_per_s": (s1["evals"] - s0["evals"]) / dt,
                       "p50_latency_s": float(np.percentile(lat, 50)) if lat else None,
                       "p99_latency_s": float(np.percentile(lat, 99)) if lat else None,
+                      # the server's split of this phase's latencies into the wait
+                      # for a slot (submit to admission) and the service (admission
+                      # to result)
+                      "p50_queue_wait_s": s1["p50_wait_s"], "p99_queue_wait_s": s1["p99_wait_s"],
+                      "p50_service_s": s1["p50_service_s"], "p99_service_s": s1["p99_service_s"],
+                      "ticks_shared": s1["ticks_shared"] - s0["ticks_shared"],
+                      "ticks_whole": s1["ticks_whole"] - s0["ticks_whole"],
                       "kernels_built": s1["kernels_built"] - s0["kernels_built"],
                       "kernel_cache_hits": s1["kernel_cache_hits"] - s0["kernel_cache_hits"]}
     srv.stop()
     return res
 
 
-def measure_serving(ctx, kx, requests=100, fp64_requests=8):
+def measure_serving(ctx, kx, requests=200, fp64_requests=16):
     """Serving: a seeded Poisson stream (mean 200 req/s) of full solves with
     N ~ U{64..384}, sigma ~ logU[1e-2, 10], random initial and source bumps,
     submitted at their arrival times.  FP32 path: kernel tensors built on demand
     (cold), then the same stream with every kernel cached (warm).  The plain FP64
     path and the FP32 path also serve the stream's first `fp64_requests` requests
-    (same inputs, cold) for the speedup."""
+    (same inputs, cold) for the speedup.  The configured stream has 2000
+    requests; `requests` takes its first ones (the default keeps the bench within
+    minutes; --requests 2000 serves all of them)."""
     reqs = ki.config5()[:requests]
     out = serve_stream(kx, ctx, reqs, kx.FP32, phases=("cold", "warm"))
     sub = reqs[:fp64_requests]
@@ -414,10 +537,16 @@ def measure_serving(ctx, kx, requests=100, fp64_requests=8):
     out["same_inputs_fp64_path"] = b
     out["speedup_vs_fp64_solves_per_s"] = (a["solves_per_s"] / b["solves_per_s"]
                                            if b["solves_per_s"] > 0 else None)
-    out["workload"] = (f"{requests} requests of a Poisson stream (200 req/s), N ~ U{{64..384}}, "
-                       "sigma logU[1e-2,10], two random source bumps each, full solves to "
-                       "L1<=1e-3 after the sources are off; FP32 path, 2 slots per kernel group; "
-                       f"FP32 vs FP64 path on the first {fp64_requests} requests")
+    out["speedup_vs_fp64_converged_solves_per_s"] = (a["converged_solves_per_s"] / b["converged_solves_per_s"]
+                                                     if b["converged_solves_per_s"] > 0 else None)
+    out["workload"] = (f"first {requests} of the 2000-request Poisson stream (200 req/s), "
+                       "N ~ U{64..384}, sigma logU[1e-2,10], two random source bumps each, full "
+                       "solves to L1<=1e-3 after the sources are off (t_end = 1e5); FP32 path, 2 "
+                       f"slots per kernel group; FP32 vs FP64 path on the first {fp64_requests} "
+                       "requests")
+    if requests < 2000:
+        out["prefix_reason"] = ("the full 2000-request stream takes several minutes per phase; "
+                                "bench.py --only serving --requests 2000 serves all of it")
     return out
 
 
@@ -464,10 +593,14 @@ def main():
     ap.add_argument("--rotate", type=int, default=0,
                     help="--only contraction: time R kernels of the grid back to back in rotation")
     ap.add_argument("--variant", type=int, default=-1,
-                    help="FP32: pin the streaming variant (0..3) instead of tuning it")
-    ap.add_argument("--requests", type=int, default=100)
+                    help="FP32: pin the streaming variant (0..4) instead of tuning it")
+    ap.add_argument("--requests", type=int, default=200,
+                    help="serving: the first R requests of the 2000-request stream")
     ap.add_argument("--no-serving", action="store_true",
                     help="skip the uneven-batch and serving measurements")
+    ap.add_argument("--paper-runtime", action="store_true",
+                    help="also re-time the paper's own runtime figure (one evaluation vs N, "
+                         "Bose-Einstein factors; context only)")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -578,27 +711,59 @@ def main():
         fp64 = {"value": ev64 / (t64 / 1e3), "unit": UNIT, "ms_per_step": t64 / args.fp64_steps,
                 "solves_per_s": B * args.fp64_steps / (t64 / 1e3)}
 
-    # ---- roofline of the dominant kernel (FP32 contraction) --------------------
+    # ---- rooflines of the step's two kernels, timed live --------------------
+    # kx_profile_attempts runs real Heun attempts of the workload with CUDA
+    # events between the contraction and the stage kernels (plain stream order:
+    # each time includes the kernel's launch and its wait on the predecessor),
+    # the FP64 and ex2 peaks come from the library's throughput kernels in this
+    # run (FP64: FMA = 2 flops)
     hbm, src_peak = peaks()
+    fp64_peak, ex2_peak = ctx.measure_peaks()
     kk = ctx.build_kernel(q, precision=kx.FP32)
-    fdev = torch.as_tensor(f0, device="cuda")
-    ms_cold = ctx.time_contraction(kk, fdev, iters=30, flush_bytes=L2_FLUSH_BYTES)
-    ms_warm = ctx.time_contraction(kk, fdev, iters=30, flush_bytes=0)
-    # algorithmic bytes: the compacted tables one launch streams (36 B per kept
-    # 4-element vector + task table), read once for all instances
-    alg_bytes = kk.info()["stream_bytes"]
+    fprof = torch.as_tensor(f0, device="cuda")
+    prof = ctx.profile_attempts(kk, fprof, sig, sources=src, attempts=400, **par)
+    info = kk.info()
+    alg_bytes = info["stream_bytes"]
+    kname = stream_kernel_name(ctx, 128, B)
+    us_k = 0.5 * (prof["contraction_1_us"] + prof["contraction_2_us"])
+    us_s = 0.5 * (prof["stage_1_us"] + prof["stage_2_us"])
+    ms_cold = ctx.time_contraction(kk, torch.as_tensor(f0, device="cuda"), iters=30,
+                                   flush_bytes=L2_FLUSH_BYTES)
     kk.release()
-    achieved = alg_bytes / (ms_cold * 1e-3) / 1e9
-    roof = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
-            "frac": achieved / hbm, "traffic": NCU_TRAFFIC["stream_n128_b4"],
-            "kernel": f"N=128, 4 instances: {stream_kernel_name(ctx, 128, B)}",
-            "algorithmic_bytes_per_launch": alg_bytes, "avg_launch_ms_cold_l2": ms_cold,
-            "avg_launch_ms_warm_l2": ms_warm, "peak_source": src_peak,
-            "note": "the collision contraction of the step; by device time the per-instance "
-                    "stage kernel (k_stage<1>: FP64 chains and block reductions on one block per "
-                    "instance, 4 SMs) is the larger share (~57 %, profiles/launch_list_config2_"
-                    "n128_step.md, profiles/k_stage_config2_n128.md); both are latency bound at "
-                    "N = 128 with 4 instances (tables 6.8 MB, L2-resident in the solve)"}
+    n = q.size
+    # contraction: the method's one exponential per kept element and instance (the
+    # interpolated f_t); the kernel evaluates two ex2 per element (the
+    # 2^a (1 - 2^d) form)
+    elem = info["nonzero_elements"] * B
+    tr_k, tr_k_note = traffic_for("stream_n128_b4", kname.split(" ")[0], alg_bytes)
+    roof_k = {"bound": "alu", "pipe": "MUFU (ex2)", "achieved": elem / (us_k * 1e-6) / 1e12,
+              "peak": ex2_peak / 1e12, "unit": "Tex2/s", "frac": elem / (us_k * 1e-6) / ex2_peak,
+              "traffic": tr_k, "traffic_note": tr_k_note,
+              "kernel": f"N=128, {B} instances: {kname}", "elements_per_launch": elem,
+              "avg_launch_us": us_k, "avg_launch_ms_isolated_cold_l2": ms_cold,
+              "algorithmic_bytes_per_launch": alg_bytes,
+              "l2_resident": "the tables (%.1f MB) stay in the 126 MB L2 during the solve" % (alg_bytes / 1e6),
+              "issued_frac": 2 * elem / (us_k * 1e-6) / ex2_peak,
+              "note": "latency and issue bound at this size: each warp streams 2-3 units of its "
+                      "bins after loading the instance tables written by the previous stage"}
+    flop_s = B * n * 0.5 * (STAGE_FLOP_PER_POINT[1] + STAGE_FLOP_PER_POINT[2])
+    tr_s, tr_s_note = traffic_for("stage_n128_b4", "k_stage<1,0>")
+    roof_s = {"bound": "alu", "pipe": "FP64", "achieved": flop_s / (us_s * 1e-6) / 1e9,
+              "peak": fp64_peak / 1e9, "unit": "GFLOP/s", "frac": flop_s / (us_s * 1e-6) / fp64_peak,
+              "traffic": tr_s, "traffic_note": tr_s_note,
+              "kernel": f"k_stage<1,0>: one block per instance ({B} blocks), row combine, projection, "
+                        "Heun stage, MB check, next tables",
+              "flop_per_launch": flop_s, "avg_launch_us": us_s,
+              "frac_of_the_sms_it_occupies": flop_s / (us_s * 1e-6) / (fp64_peak * B / 148.0),
+              "note": "latency bound: a dependent chain of FP64 operations and block reductions "
+                      "per instance on one SM each"}
+    dominant = "stage" if us_s >= us_k else "contraction"
+    roof = dict(roof_s if dominant == "stage" else roof_k)
+    roof["dominant"] = (f"{dominant}: {max(us_s, us_k):.2f} us of the {us_s + us_k:.2f} us of the "
+                        "two kernels per Heun stage (kx_profile_attempts, 400 attempts)")
+    roof["peak_source"] = "measured in this run (the library's DFMA / ex2 throughput kernels)"
+    roof_other = roof_k if dominant == "stage" else roof_s
+    roof_other["peak_source"] = roof["peak_source"]
     # streaming single-instance rooflines at N=384 and N=512 (tables 172 MB
     # and 406 MB, both > L2): several kernels of the same grid whose
     # contractions run back to back in rotation, so that each launch streams
@@ -615,9 +780,11 @@ def main():
         for kr in ks:
             kr.release()
         gbs = nb / (ms_pdl * 1e-3) / 1e9
+        kn = stream_kernel_name(ctx, n, 1)
+        tr, tr_note = traffic_for(f"stream_n{n}", kn.split(" ")[0], nb)
         return {"bound": "hbm", "achieved": gbs, "peak": hbm, "unit": "GB/s", "frac": gbs / hbm,
-                "traffic": NCU_TRAFFIC.get(f"stream_n{n}"),
-                "kernel": f"N={n}, single instance: {stream_kernel_name(ctx, n, 1)}",
+                "traffic": tr, "traffic_note": tr_note, "peak_source": src_peak,
+                "kernel": f"N={n}, single instance: {kn}",
                 "algorithmic_bytes_per_launch": nb, "avg_launch_ms": ms_pdl,
                 "timing": f"{rotate} kernels of the grid ({rotate} x {nb / 1e6:.0f} MB tables) in "
                           f"rotation, {10 * rotate} launches back to back between CUDA events, "
@@ -634,7 +801,8 @@ def main():
 
     config1 = measure_config1(ctx, kx, torch) if rank == 0 else None
     batched, batched_check = measure_batched(ctx, kx, torch, flush) if rank == 0 else (None, None)
-    runtime, runtime_check = measure_paper_runtime(ctx, kx, torch) if rank == 0 else (None, None)
+    runtime, runtime_check = (measure_paper_runtime(ctx, kx, torch)
+                              if rank == 0 and args.paper_runtime else (None, None))
     uneven = measure_uneven(ctx, kx) if rank == 0 and not args.no_serving else None
     serving = (measure_serving(ctx, kx, requests=args.requests)
                if rank == 0 and not args.no_serving else None)
@@ -663,7 +831,8 @@ def main():
                                   "evals": int(results[b]["evals"]), "t": results[b]["t"],
                                   "l1_to_mb": results[b]["l1_to_mb"]}
                                  for b in range(min(B, len(results)))],
-                "roofline": roof, "roofline_streaming_n384": roof384,
+                "roofline": roof, "roofline_other_kernel": roof_other,
+                "roofline_streaming_n384": roof384,
                 "roofline_streaming_n512": roof512,
                 "fixed_steps_n32": config1,
                 "batched_n192_b512": batched,

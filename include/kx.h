@@ -365,6 +365,10 @@ int kx_submit(kx_server *srv, const kx_grid_desc *grid, double sigma, const kx_s
 int kx_poll(kx_server *srv, kx_ticket ticket, double timeout_s, double *f_out_host,
             kx_result *res);
 int kx_server_get_stats(kx_server *srv, kx_server_stats *out);
+/* Starts a new sample for the latency quantiles of kx_server_get_stats (the
+ * requests completed from now on); the counters stay cumulative.  KX_EINVAL
+ * for a null server. */
+int kx_server_reset_latency(kx_server *srv);
 /* Finish the requests in flight, stop the worker and free the server. */
 void kx_server_stop(kx_server *srv);
 
@@ -453,6 +457,27 @@ int kx_source_condensate(int n, const double *q, double a, double mass, double m
                          double gamma_n, double *shape, double *rate);
 
 /* ----------------------------------------------------------- diagnostics */
+/* ALU throughput of the device (a diagnostic for rooflines, no counterpart in
+ * the paper): times a grid of 8 blocks per SM running independent chains of
+ * FP64 fused multiply-adds and of ex2.approx (the special-function unit) and
+ * writes the best of three runs: *fp64_flops (FMA = 2 flops, per second) and
+ * *ex2_per_s (host pointers).  Synchronises the context's stream.  KX_EINVAL
+ * for null arguments, KX_ECUDA on a CUDA error. */
+int kx_measure_peaks(kx_ctx *ctx, double *fp64_flops, double *ex2_per_s);
+
+/* Per-kernel timing of the solve's attempts (a diagnostic, no counterpart in
+ * the paper): sets up a solve of the B instances of f_dev exactly as kx_solve
+ * does (same arguments), prepares f and runs `attempts` (1 .. 100000) real
+ * Heun attempts whose four kernels (contraction, stage 1, contraction, stage
+ * 2) are launched in plain stream order with CUDA events between them, then
+ * writes to us[0..3] (host) the average microseconds of each of the four.
+ * Without the programmatic overlap of the solve's graphs each time includes
+ * the kernel's launch and its wait on its predecessor's tail.  f_dev is
+ * advanced by the attempts (pass a copy).  Synchronises the context's stream.
+ * KX_EINVAL for bad arguments, KX_ECUDA on a CUDA error. */
+int kx_profile_attempts(kx_ctx *ctx, const kx_kernel *k, int B, const double *sigma, const kx_source *src,
+                        int nsets, const kx_solve_params *par, double *f_dev, int attempts, double *us);
+
 /* Self-check of the library's own arithmetic helpers (the stage kernels use
  * them for the per-point log of f, the source envelopes, the Maxwell-Boltzmann
  * fit and the FP32 path's integer-pipe conversions; they have no counterpart

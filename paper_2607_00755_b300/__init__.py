@@ -28,7 +28,7 @@ EXPORTS = (
     "kx_solve", "kx_solve_host", "kx_mb_fit", "kx_launch_count", "kx_time_contraction",
     "kx_time_contractions", "kx_time_collision",
     "kx_collision_noalloc", "kx_server_start", "kx_submit", "kx_poll", "kx_server_get_stats",
-    "kx_server_stop", "kx_math_check", "kx_wait_check", "kx_set_stream_variant", "kx_get_stream_variant",
+    "kx_server_stop", "kx_math_check", "kx_profile_attempts", "kx_measure_peaks", "kx_server_reset_latency", "kx_wait_check", "kx_set_stream_variant", "kx_get_stream_variant",
     "kx_source_higgs_decay", "kx_source_condensate", "kx_solve_expanding", "kx_solve_grouped",
 )
 
@@ -147,6 +147,9 @@ def load_library(path: str = LIB_PATH):
         "kx_solve_host": (i, [vp, vp, i, vp, vp, i, ctypes.POINTER(SolveParams), vp, vp]),
         "kx_mb_fit": (i, [vp, vp, i, vp, vp]),
         "kx_math_check": (i, [vp, i, i, vp, vp]),
+        "kx_profile_attempts": (i, [vp, vp, i, vp, vp, i, vp, vp, i, vp]),
+        "kx_measure_peaks": (i, [vp, vp, vp]),
+        "kx_server_reset_latency": (i, [vp]),
         "kx_wait_check": (i, [vp, ctypes.c_longlong, vp]),
         "kx_set_stream_variant": (i, [vp, i, i, i]),
         "kx_get_stream_variant": (i, [vp, i, i, vp, vp]),
@@ -304,6 +307,33 @@ class Context:
         if rc in (EINVAL, ENOMEM, ECUDA, ETIMEOUT, ENOTSUP):
             raise self.error(rc, "kx_solve")
         return [r.as_dict() for r in res]
+
+    def measure_peaks(self):
+        """(FP64 flop/s, ex2/s) of the device from the library's throughput kernels."""
+        a, b = ctypes.c_double(0.0), ctypes.c_double(0.0)
+        rc = self.lib.kx_measure_peaks(self.h, ctypes.byref(a), ctypes.byref(b))
+        if rc:
+            raise self.error(rc, "kx_measure_peaks")
+        return a.value, b.value
+
+    def profile_attempts(self, kernel, f, sigma, sources=None, attempts=200, **params):
+        """Average device microseconds of the four kernels of a Heun attempt
+        (contraction 1, stage 1, contraction 2, stage 2), launched in plain
+        stream order with CUDA events between them; f (CUDA float64 [B, n]) is
+        advanced by the attempts."""
+        f2 = f if f.dim() == 2 else f.view(1, -1)
+        B = f2.shape[0]
+        sig = _np(np.broadcast_to(np.asarray(sigma, dtype=np.float64), (B,)))
+        src, ns, keep = self._sources(sources, B, kernel.n)
+        par = self.params(**params)
+        us = (ctypes.c_double * 4)()
+        rc = self.lib.kx_profile_attempts(self.h, kernel.h, B, _ptr(sig), src, ns, ctypes.byref(par),
+                                          _dptr(f2), int(attempts), us)
+        del keep
+        if rc:
+            raise self.error(rc, "kx_profile_attempts")
+        return {"contraction_1_us": us[0], "stage_1_us": us[1], "contraction_2_us": us[2],
+                "stage_2_us": us[3]}
 
     def solve_host(self, kernel, f, sigma, sources=None, **params):
         """Host-buffer variant: f numpy [B, n] copied in and out inside the call."""
@@ -527,6 +557,12 @@ class Server:
         st = ServerStats()
         self.lib.kx_server_get_stats(self.h, ctypes.byref(st))
         return st.as_dict()
+
+    def reset_latency(self):
+        """New sample for the latency quantiles (requests completed from now on)."""
+        rc = self.lib.kx_server_reset_latency(self.h)
+        if rc:
+            raise KxError(rc, "kx_server_reset_latency")
 
     def stop(self):
         if getattr(self, "h", None):

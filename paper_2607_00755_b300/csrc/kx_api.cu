@@ -1049,6 +1049,56 @@ extern "C" int kx_solve(kx_ctx *ctx, const kx_kernel *k, int B, const double *si
     return kx_solve_run(ctx, k, B, r, par, res);
 }
 
+extern "C" int kx_profile_attempts(kx_ctx *ctx, const kx_kernel *k, int B, const double *sigma,
+                                   const kx_source *src, int nsets, const kx_solve_params *par, double *f_dev,
+                                   int attempts, double *us) {
+    kx_nvtx range_("kx_profile_attempts");
+    int rc = kx_check_batch(ctx, k, B, sigma);
+    if (rc) return rc;
+    if ((rc = kx_check_params(ctx, par)) != KX_OK) return rc;
+    if (!f_dev || !us || attempts < 1 || attempts > 100000)
+        return kx_set_error(ctx, KX_EINVAL, "bad arguments");
+    KX_CUDA_TRY(ctx, cudaSetDevice(ctx->device));
+    kx_run r;
+    double *f = nullptr;
+    if ((rc = kx_setup_run(ctx, k, B, sigma, src, nsets, par, nullptr, nullptr, f_dev, false, &r, &f)))
+        return rc;
+    cudaStream_t s = ctx->stream;
+    KX_CUDA_TRY(ctx, kx_launch_prep(k, B, r.sv.f, r.v, r.sv.st, s));
+    ctx->launches += 1;
+    // events between the attempts' four kernels, each launched in plain stream
+    // order (no programmatic overlap): event j..j+1 brackets one kernel
+    std::vector<cudaEvent_t> ev((size_t)attempts * 4 + 1, nullptr);
+    cudaError_t e = cudaSuccess;
+    for (size_t j = 0; j < ev.size() && e == cudaSuccess; ++j) e = cudaEventCreate(&ev[j]);
+    if (e == cudaSuccess) e = cudaEventRecord(ev[0], s);
+    for (int a = 0; a < attempts && e == cudaSuccess; ++a) {
+        cudaEvent_t *q = ev.data() + (size_t)a * 4;
+        e = kx_launch_contract(k, B, r.sv.f, r.v, r.sv.st, 1, s, false);
+        if (e == cudaSuccess) e = cudaEventRecord(q[1], s);
+        if (e == cudaSuccess) e = kx_launch_stage(k, B, r.v, r.sv, 1, s, false);
+        if (e == cudaSuccess) e = cudaEventRecord(q[2], s);
+        if (e == cudaSuccess) e = kx_launch_contract(k, B, r.sv.fp, r.v, r.sv.st, 2, s, false);
+        if (e == cudaSuccess) e = cudaEventRecord(q[3], s);
+        if (e == cudaSuccess) e = kx_launch_stage(k, B, r.v, r.sv, 2, s, false);
+        if (e == cudaSuccess) e = cudaEventRecord(q[4], s);
+        ctx->launches += 4;
+    }
+    if (e == cudaSuccess) e = cudaEventSynchronize(ev.back());
+    double sum[4] = {0.0, 0.0, 0.0, 0.0};
+    for (int a = 0; a < attempts && e == cudaSuccess; ++a)
+        for (int j = 0; j < 4 && e == cudaSuccess; ++j) {
+            float ms = 0.f;
+            e = cudaEventElapsedTime(&ms, ev[(size_t)a * 4 + j], ev[(size_t)a * 4 + j + 1]);
+            sum[j] += ms;
+        }
+    for (auto x : ev)
+        if (x) cudaEventDestroy(x);
+    if (e != cudaSuccess) return kx_set_error(ctx, KX_ECUDA, std::string("profile: ") + cudaGetErrorString(e));
+    for (int j = 0; j < 4; ++j) us[j] = 1e3 * sum[j] / attempts;
+    return KX_OK;
+}
+
 extern "C" int kx_solve_host(kx_ctx *ctx, const kx_kernel *k, int B, const double *sigma,
                              const kx_source *src, int nsets, const kx_solve_params *par,
                              double *f_host, kx_result *res) {

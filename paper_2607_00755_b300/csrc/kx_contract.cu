@@ -93,6 +93,78 @@ extern "C" int kx_math_check(kx_ctx *ctx, int which, int n, const double *x_dev,
     return cudaGetLastError() == cudaSuccess ? KX_OK : KX_ECUDA;
 }
 
+// ALU throughput probes (the denominators of the bench's ALU rooflines):
+// every thread runs 8 independent chains of R dependent DFMA (FP64 pipe) or
+// ex2.approx (MUFU) operations; the host times a grid of 8 blocks per SM.
+#define KX_PEAK_R 2048
+__global__ void k_peak_dfma(double a, double b, double *out) {
+    double x[8];
+#pragma unroll
+    for (int c = 0; c < 8; ++c) x[c] = 1.0 + 1e-9 * (threadIdx.x + c);
+#pragma unroll 1
+    for (int r = 0; r < KX_PEAK_R; ++r)
+#pragma unroll
+        for (int c = 0; c < 8; ++c) x[c] = fma(x[c], a, b);
+    double s = 0.0;
+#pragma unroll
+    for (int c = 0; c < 8; ++c) s += x[c];
+    if (s == 12345.678) out[0] = s;   // (keeps the chains live; never true for these inputs)
+}
+__global__ void k_peak_ex2(float *out) {
+    float x[8];
+#pragma unroll
+    for (int c = 0; c < 8; ++c) x[c] = 1e-3f * (float)c + 1e-7f * (float)threadIdx.x;
+#pragma unroll 1
+    for (int r = 0; r < KX_PEAK_R; ++r)
+#pragma unroll
+        for (int c = 0; c < 8; ++c) {
+            float y;
+            asm volatile("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x[c]));
+            x[c] = -0.5f * y;
+        }
+    float s = 0.f;
+#pragma unroll
+    for (int c = 0; c < 8; ++c) s += x[c];
+    if (s == 12345.678f) out[0] = s;
+}
+
+extern "C" int kx_measure_peaks(kx_ctx *ctx, double *fp64_flops, double *ex2_per_s) {
+    if (!ctx || !fp64_flops || !ex2_per_s) return KX_EINVAL;
+    if (cudaSetDevice(ctx->device) != cudaSuccess) return KX_ECUDA;
+    int sms = 0;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ctx->device);
+    const int blocks = 8 * (sms > 0 ? sms : 148), threads = 256;
+    const double ops = (double)blocks * threads * KX_PEAK_R * 8;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaError_t e = cudaEventCreate(&e0);
+    if (e == cudaSuccess) e = cudaEventCreate(&e1);
+    float best_d = 0.f, best_x = 0.f;
+    for (int rep = 0; rep < 3 && e == cudaSuccess; ++rep) {
+        float ms = 0.f;
+        e = cudaEventRecord(e0, ctx->stream);
+        if (e == cudaSuccess) k_peak_dfma<<<blocks, threads, 0, ctx->stream>>>(0.9999999, 1e-9, nullptr);
+        if (e == cudaSuccess) e = cudaGetLastError();
+        if (e == cudaSuccess) e = cudaEventRecord(e1, ctx->stream);
+        if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+        if (e == cudaSuccess && (rep == 0 || ms < best_d)) best_d = ms;
+        if (e == cudaSuccess) e = cudaEventRecord(e0, ctx->stream);
+        if (e == cudaSuccess) k_peak_ex2<<<blocks, threads, 0, ctx->stream>>>(nullptr);
+        if (e == cudaSuccess) e = cudaGetLastError();
+        if (e == cudaSuccess) e = cudaEventRecord(e1, ctx->stream);
+        if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+        if (e == cudaSuccess && (rep == 0 || ms < best_x)) best_x = ms;
+    }
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    ctx->launches += 6;
+    if (e != cudaSuccess || best_d <= 0.f || best_x <= 0.f) return KX_ECUDA;
+    *fp64_flops = 2.0 * ops / (best_d * 1e-3);   // an FMA is two flops
+    *ex2_per_s = ops / (best_x * 1e-3);
+    return KX_OK;
+}
+
 // Bounded-wait self-check: one thread initialises an mbarrier that expects one
 // arrival, never arrives on it, and waits for its phase with the given cycle
 // limit; *out = 1 if the wait gave up (the expected result), 0 if it completed.

@@ -678,6 +678,15 @@ extern "C" int kx_server_get_stats(kx_server *srv, kx_server_stats *out) {
     return KX_OK;
 }
 
+extern "C" int kx_server_reset_latency(kx_server *srv) {
+    if (!srv) return KX_EINVAL;
+    std::lock_guard<std::mutex> lock(srv->mu);
+    srv->lat.clear();
+    srv->wait.clear();
+    srv->service.clear();
+    return KX_OK;
+}
+
 extern "C" void kx_server_stop(kx_server *srv) {
     if (!srv) return;
     {
