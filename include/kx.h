@@ -457,6 +457,24 @@ int kx_source_condensate(int n, const double *q, double a, double mass, double m
                          double gamma_n, double *shape, double *rate);
 
 /* ----------------------------------------------------------- diagnostics */
+/* Bounds-checked build (no counterpart in the paper): libkx_check.so is this
+ * library compiled with -DKX_CHECK.  Its contraction and loss kernels test
+ * their table, bracket, task and slot indices against the arrays' lengths;
+ * a failed test records the first failing site and index (and a count) and
+ * uses index 0 instead, so that no access leaves its array.  kx_check_status
+ * reports *checked = 1 in that build (0 in libkx.so, whose records stay 0),
+ * the failures since the last reset, and the first failure's site and index
+ * (reset != 0 clears the records after reading them).  Synchronises the
+ * context's stream.  KX_EINVAL for null arguments, KX_ECUDA on a CUDA error. */
+int kx_check_status(kx_ctx *ctx, int reset, int *checked, long long *failures, int *first_site,
+                    long long *first_index);
+/* Passes `index` through the same check with the bound `limit` (>= 0) in a
+ * one-thread kernel and writes its result to *result (host): index when
+ * 0 <= index < limit, else 0 and a recorded failure in the checked build;
+ * index in the normal build.  No memory is addressed with the index.
+ * KX_EINVAL for bad arguments, KX_ECUDA on a CUDA error. */
+int kx_check_probe(kx_ctx *ctx, int index, int limit, int *result);
+
 /* ALU throughput of the device (a diagnostic for rooflines, no counterpart in
  * the paper): times a grid of 8 blocks per SM running independent chains of
  * FP64 fused multiply-adds and of ex2.approx (the special-function unit) and

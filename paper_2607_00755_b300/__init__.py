@@ -28,7 +28,7 @@ EXPORTS = (
     "kx_solve", "kx_solve_host", "kx_mb_fit", "kx_launch_count", "kx_time_contraction",
     "kx_time_contractions", "kx_time_collision",
     "kx_collision_noalloc", "kx_server_start", "kx_submit", "kx_poll", "kx_server_get_stats",
-    "kx_server_stop", "kx_math_check", "kx_profile_attempts", "kx_measure_peaks", "kx_server_reset_latency", "kx_wait_check", "kx_set_stream_variant", "kx_get_stream_variant",
+    "kx_server_stop", "kx_math_check", "kx_profile_attempts", "kx_measure_peaks", "kx_server_reset_latency", "kx_check_status", "kx_check_probe", "kx_wait_check", "kx_set_stream_variant", "kx_get_stream_variant",
     "kx_source_higgs_decay", "kx_source_condensate", "kx_solve_expanding", "kx_solve_grouped",
 )
 
@@ -117,6 +117,13 @@ class ServerStats(ctypes.Structure):
 
 
 _lib = None
+_libs = {}
+LIB_CHECK_PATH = os.path.join(_HERE, "libkx_check.so")
+
+
+def load_checked_library():
+    """Load libkx_check.so, the bounds-checked build (kx_check_status)."""
+    return _open_library(LIB_CHECK_PATH)
 
 
 def load_library(path: str = LIB_PATH):
@@ -124,8 +131,16 @@ def load_library(path: str = LIB_PATH):
     global _lib
     if _lib is not None:
         return _lib
+    _lib = _open_library(path)
+    return _lib
+
+
+def _open_library(path: str):
+    if path in _libs:
+        return _libs[path]
     if not os.path.exists(path):
-        raise RuntimeError(f"libkx.so not built at {path}; run python -m paper_2607_00755_b300.build")
+        raise RuntimeError(f"{os.path.basename(path)} not built at {path}; "
+                           "run python -m paper_2607_00755_b300.build")
     lib = ctypes.CDLL(path)
     i, vp, d = ctypes.c_int, ctypes.c_void_p, ctypes.c_double
     sig = {
@@ -150,6 +165,8 @@ def load_library(path: str = LIB_PATH):
         "kx_profile_attempts": (i, [vp, vp, i, vp, vp, i, vp, vp, i, vp]),
         "kx_measure_peaks": (i, [vp, vp, vp]),
         "kx_server_reset_latency": (i, [vp]),
+        "kx_check_status": (i, [vp, i, vp, vp, vp, vp]),
+        "kx_check_probe": (i, [vp, i, i, vp]),
         "kx_wait_check": (i, [vp, ctypes.c_longlong, vp]),
         "kx_set_stream_variant": (i, [vp, i, i, i]),
         "kx_get_stream_variant": (i, [vp, i, i, vp, vp]),
@@ -173,7 +190,7 @@ def load_library(path: str = LIB_PATH):
         fn = getattr(lib, name)
         fn.restype = res
         fn.argtypes = args
-    _lib = lib
+    _libs[path] = lib
     return lib
 
 
@@ -203,9 +220,9 @@ def _dptr(t):
 class Context:
     """kx_ctx bound to a CUDA device and a torch stream."""
 
-    def __init__(self, device: int = 0, stream=None):
+    def __init__(self, device: int = 0, stream=None, lib=None):
         import torch
-        self.lib = load_library()
+        self.lib = lib if lib is not None else load_library()
         self.device = device
         if stream is None:
             stream = torch.cuda.current_stream(device)
@@ -307,6 +324,25 @@ class Context:
         if rc in (EINVAL, ENOMEM, ECUDA, ETIMEOUT, ENOTSUP):
             raise self.error(rc, "kx_solve")
         return [r.as_dict() for r in res]
+
+    def check_status(self, reset=False):
+        """Bounds-check record (kx_check_status): checked build?, failures,
+        first failing site and index."""
+        c, nf, site, idx = ctypes.c_int(0), ctypes.c_longlong(0), ctypes.c_int(0), ctypes.c_longlong(0)
+        rc = self.lib.kx_check_status(self.h, int(bool(reset)), ctypes.byref(c), ctypes.byref(nf),
+                                      ctypes.byref(site), ctypes.byref(idx))
+        if rc:
+            raise self.error(rc, "kx_check_status")
+        return {"checked": bool(c.value), "failures": nf.value, "first_site": site.value,
+                "first_index": idx.value}
+
+    def check_probe(self, index, limit):
+        """Result of passing index through the bounds check with the given limit."""
+        r = ctypes.c_int(0)
+        rc = self.lib.kx_check_probe(self.h, int(index), int(limit), ctypes.byref(r))
+        if rc:
+            raise self.error(rc, "kx_check_probe")
+        return r.value
 
     def measure_peaks(self):
         """(FP64 flop/s, ex2/s) of the device from the library's throughput kernels."""

@@ -1099,6 +1099,36 @@ extern "C" int kx_profile_attempts(kx_ctx *ctx, const kx_kernel *k, int B, const
     return KX_OK;
 }
 
+extern "C" int kx_check_status(kx_ctx *ctx, int reset, int *checked, long long *failures, int *first_site,
+                               long long *first_index) {
+    if (!ctx || !checked || !failures || !first_site || !first_index) return KX_EINVAL;
+    KX_CUDA_TRY(ctx, cudaSetDevice(ctx->device));
+    KX_CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
+    unsigned int a[3] = {0u, 0u, 0u}, b[3] = {0u, 0u, 0u};
+    if (kx_chk_read_contract(a, reset != 0) || kx_chk_read_batch(b, reset != 0))
+        return kx_set_error(ctx, KX_ECUDA, "check record");
+    *checked = KX_CHECKED;
+    *failures = (long long)a[0] + (long long)b[0];
+    const unsigned int *first = a[0] ? a : b;
+    *first_site = (int)first[1];
+    *first_index = (long long)(int)first[2];
+    return KX_OK;
+}
+
+extern "C" int kx_check_probe(kx_ctx *ctx, int index, int limit, int *result) {
+    if (!ctx || !result || limit < 0) return KX_EINVAL;
+    KX_CUDA_TRY(ctx, cudaSetDevice(ctx->device));
+    int *d = nullptr;
+    KX_CUDA_TRY(ctx, cudaMalloc(&d, sizeof(int)));
+    cudaError_t e = kx_launch_chk_probe(index, limit, d, ctx->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(result, d, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    cudaFree(d);
+    ctx->launches += 1;
+    if (e != cudaSuccess) return kx_set_error(ctx, KX_ECUDA, std::string("check probe: ") + cudaGetErrorString(e));
+    return KX_OK;
+}
+
 extern "C" int kx_solve_host(kx_ctx *ctx, const kx_kernel *k, int B, const double *sigma,
                              const kx_source *src, int nsets, const kx_solve_params *par,
                              double *f_host, kx_result *res) {

@@ -314,8 +314,13 @@ __global__ void __launch_bounds__(KX_SG_THREADS, 1)
                     // one another)
                     const long long pq = (long long)kb * 16 + ph + (lane & 7);
                     int dn = 0, dm = 0;
-                    if (pq < P) kx_pair_decode(pq, n, dn, dm);
-                    else dn = -1;   // padding: the product is dropped (dm = 0 keeps the load in range)
+                    if (pq < P) {
+                        kx_pair_decode(pq, n, dn, dm);
+                        dn = KX_IDX(dn, n, KX_SITE_GAIN_PAIR);
+                        dm = KX_IDX(dm, n, KX_SITE_GAIN_PAIR);
+                    } else {
+                        dn = -1;   // padding: the product is dropped (dm = 0 keeps the load in range)
+                    }
                     if (round > 0) {
                         int r = 1;
                         if (lane == 0) r = kx_wait_role(empty0 + 8 * q, (round - 1) & 1, abort, err);
@@ -491,7 +496,7 @@ __global__ void __launch_bounds__(WARPS * 32, (WARPS <= 16 && IPL <= 2) ? 2 : 1)
                  const int2 *__restrict__ lseg, const int *__restrict__ lsw,
                  const int *__restrict__ lorder, const float2 *__restrict__ td,
                  const double *__restrict__ fmax, double2 *__restrict__ partial,
-                 const kx_inst_state *__restrict__ st, int stage, const int *__restrict__ cflag) {
+                 const kx_inst_state *__restrict__ st, int stage, const int *__restrict__ cflag, int nel) {
     // [n][32][IPL] (l2_j, D_j) table; after the loss loop the same space holds
     // the cross-warp reduction [2][WARPS][32 IPL] doubles
     extern __shared__ __align__(16) float2 kx_ltab[];
@@ -510,8 +515,9 @@ __global__ void __launch_bounds__(WARPS * 32, (WARPS <= 16 && IPL <= 2) ? 2 : 1)
         any |= act[s];
     }
     if (!__syncthreads_or(any)) return;
-    const int i = lorder[blockIdx.y];
+    const int i = KX_IDX(lorder[blockIdx.y], n, KX_SITE_LOSS_ROW);
     float hi[IPL], lo[IPL];
+    (void)nel;
 #pragma unroll
     for (int s = 0; s < IPL; ++s) hi[s] = lo[s] = 0.f;
     {
@@ -544,8 +550,8 @@ __global__ void __launch_bounds__(WARPS * 32, (WARPS <= 16 && IPL <= 2) ? 2 : 1)
         if (g < gend) {
             dsc = __ldg(lseg + g);
             const int c = dsc.y & 255;
-            if (lane < c) el0 = __ldg(lel + dsc.x + lane);
-            if (lane + 32 < c) el1 = __ldg(lel + dsc.x + 32 + lane);
+            if (lane < c) el0 = __ldg(lel + KX_IDX(dsc.x + lane, nel, KX_SITE_LOSS_ELEM));
+            if (lane + 32 < c) el1 = __ldg(lel + KX_IDX(dsc.x + 32 + lane, nel, KX_SITE_LOSS_ELEM));
         }
         if (g + 1 < gend) dn = __ldg(lseg + g + 1);
         for (; g < gend; ++g) {
@@ -554,13 +560,13 @@ __global__ void __launch_bounds__(WARPS * 32, (WARPS <= 16 && IPL <= 2) ? 2 : 1)
             float2 en0 = make_float2(0.f, 0.f), en1 = en0;
             if (g + 1 < gend) {
                 const int c = dn.y & 255;
-                if (lane < c) en0 = __ldg(lel + dn.x + lane);
-                if (lane + 32 < c) en1 = __ldg(lel + dn.x + 32 + lane);
+                if (lane < c) en0 = __ldg(lel + KX_IDX(dn.x + lane, nel, KX_SITE_LOSS_ELEM));
+                if (lane + 32 < c) en1 = __ldg(lel + KX_IDX(dn.x + 32 + lane, nel, KX_SITE_LOSS_ELEM));
             }
             s_el[warp][lane] = el0;
             s_el[warp][32 + lane] = el1;
             __syncwarp();
-            const int j = dsc.y >> 8, c4 = dsc.y & 255;   // count, a multiple of 4
+            const int j = KX_IDX(dsc.y >> 8, n, KX_SITE_LOSS_BRACKET), c4 = dsc.y & 255;   // count, a multiple of 4
             float2 t[IPL];
             if constexpr (IPL == 1) {
                 t[0] = kx_ltab[j * 32 + lane];
@@ -744,13 +750,16 @@ static cudaError_t kx_launch_batch_loss(const kx_kernel *k, int B, const kx_batc
     const int *flags = k->cheb_K ? v.cflag : nullptr;
     if (sh.ipl == 2 && sh.warps == 16)
         k_batch_loss<2, 16><<<g2, 512, smem, s>>>(k->n, B, v.B, k->d_lel, k->d_lseg, k->d_lsw, k->d_lorder,
-                                                  v.td, v.fmax, v.partial, st, stage, flags);
+                                                  v.td, v.fmax, v.partial, st, stage, flags,
+                                                  (int)k->nlel);
     else if (sh.ipl == 2)
         k_batch_loss<2, 32><<<g2, 1024, smem, s>>>(k->n, B, v.B, k->d_lel, k->d_lseg, k->d_lsw, k->d_lorder,
-                                                   v.td, v.fmax, v.partial, st, stage, flags);
+                                                   v.td, v.fmax, v.partial, st, stage, flags,
+                                                  (int)k->nlel);
     else
         k_batch_loss<1, 32><<<g2, 1024, smem, s>>>(k->n, B, v.B, k->d_lel, k->d_lseg, k->d_lsw, k->d_lorder,
-                                                   v.td, v.fmax, v.partial, st, stage, flags);
+                                                   v.td, v.fmax, v.partial, st, stage, flags,
+                                                  (int)k->nlel);
     return cudaGetLastError();
 }
 
@@ -971,3 +980,5 @@ int kx_batch_build_tables(kx_ctx *ctx, kx_kernel *k) {
         return kx_set_error(ctx, KX_ECUDA, "batched build: table upload failed");
     return KX_OK;
 }
+
+int kx_chk_read_batch(unsigned int *out, bool reset) { return kx_chk_read(out, reset); }

@@ -165,6 +165,18 @@ extern "C" int kx_measure_peaks(kx_ctx *ctx, double *fp64_flops, double *ex2_per
     return KX_OK;
 }
 
+// KX_CHECK: this unit's failure record, and a probe kernel that passes one
+// index through the check (in the normal build it only copies the index; no
+// memory is addressed with it either way)
+int kx_chk_read_contract(unsigned int *out, bool reset) { return kx_chk_read(out, reset); }
+__global__ void k_chk_probe(int index, int limit, int *out) {
+    if (threadIdx.x == 0 && blockIdx.x == 0) out[0] = KX_IDX(index, limit, KX_SITE_PROBE);
+}
+cudaError_t kx_launch_chk_probe(int index, int limit, int *out, cudaStream_t s) {
+    k_chk_probe<<<1, 32, 0, s>>>(index, limit, out);
+    return cudaGetLastError();
+}
+
 // Bounded-wait self-check: one thread initialises an mbarrier that expects one
 // arrival, never arrives on it, and waits for its phase with the given cycle
 // limit; *out = 1 if the wait gave up (the expected result), 0 if it completed.
@@ -902,8 +914,8 @@ __global__ void __launch_bounds__(KX_T64)
             double w = W[base + pidx];
             if (w != 0.0) {
                 uint32_t pr = pair[pidx];
-                int nn = pr & 0xffff, mm = pr >> 16;
-                int j = jl[base + pidx];
+                int nn = KX_IDX(pr & 0xffff, n, KX_SITE_F64_PAIR), mm = KX_IDX(pr >> 16, n, KX_SITE_F64_PAIR);
+                int j = KX_IDX(jl[base + pidx], n - 1, KX_SITE_F64_BRACKET);
                 double o = om[base + pidx];
                 const double ft = exp((1.0 - o) * s_l[j] + o * s_l[j + 1]);
                 if (eta == 0) {
@@ -992,22 +1004,25 @@ __device__ __forceinline__ void kx_df_add(float &hi, float &lo, float x) {
 // acc[bb] += sum_q W_q [f_n f_m - f_i f_t] / f_max^2 in the bracket form.  The
 // same code serves both streaming kernels, so an instance's result does not
 // depend on which of them ran.
+// (nl = n + 4, nd = n: the tables' lengths, used by the KX_CHECK build only)
 template <int BP>
 __device__ __forceinline__ void kx_vector_terms(const float4 wv, const uint4 pv, const uint32_t nvw,
                                                 const float2 (*s_l)[KX_MAX_N + 4],
                                                 const float2 (*s_d)[KX_MAX_N], const float *di,
-                                                const int *so, float *acc) {
-    const int nn = nvw & 0xffff, m0 = nvw >> 16;
+                                                const int *so, float *acc, int nl, int nd) {
+    const int nn = KX_IDX(nvw & 0xffff, nl, KX_SITE_TAB_N), m0 = nvw >> 16;
     const float wk[4] = {wv.x, wv.y, wv.z, wv.w};
     const uint32_t pw[4] = {pv.x, pv.y, pv.z, pv.w};
+    (void)nl;
+    (void)nd;
 #pragma unroll
     for (int bb = 0; bb < BP; ++bb) {
         const float2 ln = s_l[bb][nn];
         const float cn = di[bb] - ln.y;
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
-            const float2 lm = s_l[bb][m0 + so[q]];
-            const float2 dj = s_d[bb][pw[q] >> 23];
+            const float2 lm = s_l[bb][KX_IDX(m0 + so[q], nl, KX_SITE_TAB_M)];
+            const float2 dj = s_d[bb][KX_IDX(pw[q] >> 23, nd, KX_SITE_BRACKET)];
             const float a = ln.x + lm.x;
             // delta_t = (delta_j - D_j) + (1 + omega) D_j
             const float d = (cn + fmaf(kx_one_plus_omega(pw[q]), dj.y, dj.x)) - lm.y;
@@ -1029,8 +1044,10 @@ __device__ __forceinline__ void kx_vector_terms_q(const float4 wv, const uint4 p
                                                   const float2 (*s_l)[KX_MAX_N + 4],
                                                   const float4 (*s_q)[KX_MAX_N], const float *di,
                                                   const float *lami, const float *efm,
-                                                  const int *so, float *acc) {
-    const int nn = nvw & 0xffff, m0 = nvw >> 16;
+                                                  const int *so, float *acc, int nl, int nd) {
+    const int nn = KX_IDX(nvw & 0xffff, nl, KX_SITE_TAB_N), m0 = nvw >> 16;
+    (void)nl;
+    (void)nd;
     const float wk[4] = {wv.x, wv.y, wv.z, wv.w};
     const uint32_t pw[4] = {pv.x, pv.y, pv.z, pv.w};
 #pragma unroll
@@ -1040,8 +1057,8 @@ __device__ __forceinline__ void kx_vector_terms_q(const float4 wv, const uint4 p
         const float an = ln.x + lami[bb];
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
-            const float2 lm = s_l[bb][m0 + so[q]];
-            const float4 dj = s_q[bb][pw[q] >> 23];
+            const float2 lm = s_l[bb][KX_IDX(m0 + so[q], nl, KX_SITE_TAB_M)];
+            const float4 dj = s_q[bb][KX_IDX(pw[q] >> 23, nd, KX_SITE_BRACKET)];
             const float opo = kx_one_plus_omega(pw[q]);
             const float et = fmaf(opo, dj.y, dj.x);   // eps_t
             const float lt = fmaf(opo, dj.w, dj.z);   // l2_t
@@ -1092,7 +1109,8 @@ __device__ __forceinline__ void kx_task_partial(const float *hi, const float *lo
             h = sm;
             l = (l + l2) + e;
         }
-        if (lane == 0 && act[bb]) partial[(long long)(b0 + bb) * pstride + tslot] = make_float2(h, l);
+        if (lane == 0 && act[bb])
+            partial[(long long)(b0 + bb) * pstride + KX_IDX(tslot, pstride, KX_SITE_SLOT)] = make_float2(h, l);
     }
 }
 
@@ -1193,7 +1211,7 @@ __global__ void __launch_bounds__(KX_T32)
                 const float2 *__restrict__ td, float2 *__restrict__ partial, int pstride,
                 const kx_inst_state *__restrict__ st, int stage,
                 const float4 *__restrict__ tq, const float *__restrict__ tlam,
-                const double *__restrict__ fmax, int eta) {
+                const double *__restrict__ fmax, int eta, const kx_lim lim) {
     __shared__ float2 s_l[BP][KX_MAX_N + 4];   // (l2_j, delta_j)
     __shared__ float2 s_d[Q ? 1 : BP][Q ? 1 : KX_MAX_N];   // (delta_j - D_j, D_j), D_j = delta_{j+1} - delta_j
     __shared__ float4 s_q[Q ? BP : 1][Q ? KX_MAX_N : 1];   // quantum: (eps_j - De_j, De_j, l2_j - Dl_j, Dl_j)
@@ -1208,22 +1226,23 @@ __global__ void __launch_bounds__(KX_T32)
     uint4 pk[VPL];
     uint32_t nv[VPL];
     auto first_unit = [&](int t) {
-        const int4 d = __ldg(task + t);
+        const int4 d = __ldg(task + KX_IDX(t, lim.ntask, KX_SITE_TASK));
         kx_unit u;
-        u.i = d.x;
+        u.i = KX_IDX(d.x, n, KX_SITE_TASK);
         u.c = d.y;
         u.cend = d.z;
         u.slot = d.w;
-        u.rb = __ldg(roff + d.x);
+        u.rb = __ldg(roff + u.i);
         return u;
     };
     auto load_unit = [&](const kx_unit &u) {
         const int v0 = u.rb + u.c * (32 * VPL) + lane;
 #pragma unroll
         for (int e = 0; e < VPL; ++e) {
-            w[e] = kx_ld_stream(W + v0 + e * 32);
-            pk[e] = kx_ld_stream(PK + v0 + e * 32);
-            nv[e] = __ldg(vt + v0 + e * 32);
+            const int vi = KX_IDX(v0 + e * 32, lim.Vt, KX_SITE_VECTOR);
+            w[e] = kx_ld_stream(W + vi);
+            pk[e] = kx_ld_stream(PK + vi);
+            nv[e] = __ldg(vt + vi);
         }
     };
     // equal-work bins of tasks, taken by the warps in a fixed order
@@ -1300,10 +1319,10 @@ __global__ void __launch_bounds__(KX_T32)
             if constexpr (Q) {
 #pragma unroll
                 for (int e = 0; e < VPL; ++e)
-                    kx_vector_terms_q<BP>(wc[e], pc[e], nc[e], s_l, s_q, di, lami, efm, so, acc);
+                    kx_vector_terms_q<BP>(wc[e], pc[e], nc[e], s_l, s_q, di, lami, efm, so, acc, n + 4, n);
             } else {
 #pragma unroll
-                for (int e = 0; e < VPL; ++e) kx_vector_terms<BP>(wc[e], pc[e], nc[e], s_l, s_d, di, so, acc);
+                for (int e = 0; e < VPL; ++e) kx_vector_terms<BP>(wc[e], pc[e], nc[e], s_l, s_d, di, so, acc, n + 4, n);
             }
 #pragma unroll
             for (int bb = 0; bb < BP; ++bb) kx_df_add(hi[bb], lo[bb], acc[bb]);
@@ -1337,7 +1356,7 @@ __global__ void __launch_bounds__(KX_T32, VPL == 4 ? 2 : 3)
                const uint32_t *__restrict__ vt, const float4 *__restrict__ W,
                const uint4 *__restrict__ PK, const float2 *__restrict__ tl,
                const float2 *__restrict__ td, float2 *__restrict__ partial, int pstride,
-               const kx_inst_state *__restrict__ st, int stage, int *__restrict__ err) {
+               const kx_inst_state *__restrict__ st, int stage, int *__restrict__ err, const kx_lim lim) {
     extern __shared__ __align__(128) unsigned char s_ring[];   // [warp][2 stages][KX_STAGE_BYTES]
     __shared__ float2 s_l[BP][KX_MAX_N + 4];   // (l2_j, delta_j)
     __shared__ float2 s_d[BP][KX_MAX_N];       // (delta_j - D_j, D_j), D_j = delta_{j+1} - delta_j
@@ -1367,20 +1386,21 @@ __global__ void __launch_bounds__(KX_T32, VPL == 4 ? 2 : 3)
     uint32_t pending = 0u;   // bit sg: a copy into stage sg is in flight
 
     auto first_unit = [&](int t) {
-        const int4 d = __ldg(task + t);
+        const int4 d = __ldg(task + KX_IDX(t, lim.ntask, KX_SITE_TASK));
         kx_unit u;
-        u.i = d.x;
+        u.i = KX_IDX(d.x, n, KX_SITE_TASK);
         u.c = d.y;
         u.cend = d.z;
         u.slot = d.w;
-        u.rb = __ldg(roff + d.x);
+        u.rb = __ldg(roff + u.i);
         return u;
     };
     // lane 0: copy unit u's tables into stage sg (rows are whole units of 64
     // vectors, so every copy is full and 16-byte aligned)
     auto issue = [&](const kx_unit &u, int sg) {
         if (lane == 0) {
-            const int v0 = u.rb + u.c * UNIT;
+            const int v1 = u.rb + u.c * UNIT, vc = KX_IDX(v1 + UNIT - 1, lim.Vt, KX_SITE_VECTOR);
+            const int v0 = vc == v1 + UNIT - 1 ? v1 : 0;   // (KX_CHECK: an out-of-range unit reads unit 0)
             unsigned char *dst = ring + sg * SB;
             const uint32_t b = sg ? bar1 : bar0;
             kx_fence_proxy_async();
@@ -1455,7 +1475,7 @@ __global__ void __launch_bounds__(KX_T32, VPL == 4 ? 2 : 3)
 #pragma unroll
             for (int e = 0; e < VPL; ++e) {
                 const int vl = e * 32 + lane;
-                kx_vector_terms<BP>(sW[vl], sP[vl], sV[vl], s_l, s_d, di, so, acc);
+                kx_vector_terms<BP>(sW[vl], sP[vl], sV[vl], s_l, s_d, di, so, acc, n + 4, n);
             }
 #pragma unroll
             for (int bb = 0; bb < BP; ++bb) kx_df_add(hi[bb], lo[bb], acc[bb]);
@@ -1500,7 +1520,8 @@ __global__ void __launch_bounds__(KX_TP, 1)
                 const uint32_t *__restrict__ vt, const float4 *__restrict__ W,
                 const uint4 *__restrict__ PK, const float2 *__restrict__ tl,
                 const float2 *__restrict__ td, float2 *__restrict__ partial, int pstride,
-                const kx_inst_state *__restrict__ st, int stage, int umax, int *__restrict__ err) {
+                const kx_inst_state *__restrict__ st, int stage, int umax, int *__restrict__ err,
+                const kx_lim lim) {
     extern __shared__ __align__(128) unsigned char s_units[];   // [warp][umax][KX_STAGE_BYTES]
     __shared__ float2 s_l[BP][KX_MAX_N + 4];   // (l2_j, delta_j)
     __shared__ float2 s_d[BP][KX_MAX_N];       // (delta_j - D_j, D_j)
@@ -1526,7 +1547,7 @@ __global__ void __launch_bounds__(KX_TP, 1)
         for (int vb = blockIdx.x * wpb + warp; vb < KX_BINS; vb += stride) {
             const int t1 = __ldg(bins + vb + 1);
             for (int t = __ldg(bins + vb); t < t1; ++t) {
-                const int4 d = __ldg(task + t);
+                const int4 d = __ldg(task + KX_IDX(t, lim.ntask, KX_SITE_TASK));
                 for (int c = d.y; c < d.z; ++c) {
                     if (cnt < cap) s_ud[warp][cnt++] = make_int4(d.x, d.w, c == d.y, c + 1 == d.z);
                     else over = true;
@@ -1541,10 +1562,11 @@ __global__ void __launch_bounds__(KX_TP, 1)
         for (int vb = blockIdx.x * wpb + warp; vb < KX_BINS && u < cnt; vb += stride) {
             const int t1 = __ldg(bins + vb + 1);
             for (int t = __ldg(bins + vb); t < t1 && u < cnt; ++t) {
-                const int4 d = __ldg(task + t);
-                const int rb = __ldg(roff + d.x);
+                const int4 d = __ldg(task + KX_IDX(t, lim.ntask, KX_SITE_TASK));
+                const int rb = __ldg(roff + KX_IDX(d.x, n, KX_SITE_TASK));
                 for (int c = d.y; c < d.z && u < cnt; ++c, ++u) {
-                    const int v0 = rb + c * UNIT;
+                    const int v1 = rb + c * UNIT, vc = KX_IDX(v1 + UNIT - 1, lim.Vt, KX_SITE_VECTOR);
+                    const int v0 = vc == v1 + UNIT - 1 ? v1 : 0;
                     unsigned char *dst = mine + (size_t)u * SB;
                     kx_bulk_g2s(kx_smem_u32(dst), W + v0, UNIT * 16u, bar);
                     kx_bulk_g2s(kx_smem_u32(dst + UNIT * 16), PK + v0, UNIT * 16u, bar);
@@ -1593,7 +1615,7 @@ __global__ void __launch_bounds__(KX_TP, 1)
 #pragma unroll
         for (int e = 0; e < VPL; ++e) {
             const int vl = e * 32 + lane;
-            kx_vector_terms<BP>(sW[vl], sP[vl], sV[vl], s_l, s_d, di, so, acc);
+            kx_vector_terms<BP>(sW[vl], sP[vl], sV[vl], s_l, s_d, di, so, acc, n + 4, n);
         }
 #pragma unroll
         for (int bb = 0; bb < BP; ++bb) kx_df_add(hi[bb], lo[bb], acc[bb]);
@@ -1673,7 +1695,7 @@ static cudaError_t kx_launch_stream(const kx_kernel *k, int B, const kx_batch_vi
     return kx_launch_ex(k_stream32<BP, VPL>, grid, dim3(KX_T32), smem, s, pdl, k->n,
                         (const int *)k->d_bins, (const int4 *)k->d_task, (const int *)k->d_roff, B,
                         (const uint32_t *)k->d_vt, W, PK, (const float2 *)v.tl, (const float2 *)v.td,
-                        reinterpret_cast<float2 *>(v.partial), v.chunks, st, stage, v.err);
+                        reinterpret_cast<float2 *>(v.partial), v.chunks, st, stage, v.err, kx_lim{k->ntask, k->Vt});
 }
 
 template <int BP, int VPL, bool Q = false>
@@ -1693,7 +1715,8 @@ static cudaError_t kx_launch_stream_r(const kx_kernel *k, int B, const kx_batch_
                         (const uint32_t *)k->d_vt, reinterpret_cast<const float4 *>(k->d_W32),
                         reinterpret_cast<const uint4 *>(k->d_pk), (const float2 *)v.tl,
                         (const float2 *)v.td, reinterpret_cast<float2 *>(v.partial), v.chunks, st, stage,
-                        (const float4 *)v.tq, (const float *)v.tlam, (const double *)v.fmax, v.eta);
+                        (const float4 *)v.tq, (const float *)v.tlam, (const double *)v.fmax, v.eta,
+                        kx_lim{k->ntask, k->Vt});
 }
 
 // The staged-share variant (4): one bin per warp in a single wave of KX_TP
@@ -1716,7 +1739,8 @@ static cudaError_t kx_launch_stream_p(const kx_kernel *k, int B, const kx_batch_
                         (const int *)k->d_bins, (const int4 *)k->d_task, (const int *)k->d_roff, B,
                         (const uint32_t *)k->d_vt, reinterpret_cast<const float4 *>(k->d_W32),
                         reinterpret_cast<const uint4 *>(k->d_pk), (const float2 *)v.tl, (const float2 *)v.td,
-                        reinterpret_cast<float2 *>(v.partial), v.chunks, st, stage, k->bin_units, v.err);
+                        reinterpret_cast<float2 *>(v.partial), v.chunks, st, stage, k->bin_units, v.err,
+                        kx_lim{k->ntask, k->Vt});
 }
 template <int VPL>
 static cudaError_t kx_launch_stream_pb(const kx_kernel *k, int B, const kx_batch_views &v,

@@ -26,6 +26,67 @@
 #define KX_FIT_W 17           // per-warp partial slots of the FP32 path's line fit (up to 17 warps)
 #define KX_WAIT_CYCLES_MAX (4ll << 30)   // longest bounded device wait (the kernels' own limit, ~2 s)
 
+// ---------------------------------------------------------------- KX_CHECK
+// Bounds-checked build (compiled with -DKX_CHECK; libkx_check.so): the hot
+// kernels pass their table, bracket, task, bin and slot indices through
+// KX_IDX(i, limit, site), which in that build tests 0 <= i < limit and, when
+// it fails, records the site and the index (the first failure of the
+// translation unit, and a count) and returns 0 instead, so that the access
+// stays inside its array and the kernel runs to its end.  In the normal build
+// KX_IDX(i, limit, site) is i and the limits are not used.  Sites:
+#define KX_SITE_TAB_N 1       // FP32 streaming: the n-row of the (l2, delta) table
+#define KX_SITE_TAB_M 2       // FP32 streaming: the m-row of the (l2, delta) table
+#define KX_SITE_BRACKET 3     // FP32 streaming: bracket j of (delta - D, D)
+#define KX_SITE_TASK 4        // FP32 streaming: task index
+#define KX_SITE_VECTOR 5      // FP32 streaming: kept-vector index of a unit
+#define KX_SITE_SLOT 6        // FP32 streaming / row combine: partial slot
+#define KX_SITE_F64_BRACKET 7 // FP64 contraction: bracket j, j + 1 of the log table
+#define KX_SITE_F64_PAIR 8    // FP64 contraction: pair (n, m)
+#define KX_SITE_LOSS_ELEM 9   // batched exact loss: a segment's element range
+#define KX_SITE_LOSS_BRACKET 10   // batched exact loss: bracket j of a segment
+#define KX_SITE_LOSS_ROW 11   // batched exact loss: row i
+#define KX_SITE_GAIN_PAIR 12  // batched gain GEMM: decoded pair (n, m)
+#define KX_SITE_BIN 13        // FP32 streaming: bin index
+#define KX_SITE_PROBE 99      // kx_check_probe
+#ifdef KX_CHECK
+static __device__ unsigned int kx_chk_state[3];   // failures, first site, first index (this unit)
+__device__ __forceinline__ int kx_chk_idx(long long i, long long lim, int site) {
+    if (i >= 0 && i < lim) return (int)i;
+    if (atomicAdd(&kx_chk_state[0], 1u) == 0u) {
+        kx_chk_state[1] = (unsigned)site;
+        kx_chk_state[2] = (unsigned)i;
+    }
+    return 0;
+}
+#define KX_IDX(i, lim, site) kx_chk_idx((long long)(i), (long long)(lim), (site))
+// failures, first site and index of this translation unit; reset = clear them
+static inline int kx_chk_read(unsigned int *out, bool reset) {
+    cudaError_t e = cudaMemcpyFromSymbol(out, kx_chk_state, sizeof(unsigned int) * 3);
+    if (e == cudaSuccess && reset) {
+        const unsigned int z[3] = {0u, 0u, 0u};
+        e = cudaMemcpyToSymbol(kx_chk_state, z, sizeof(z));
+    }
+    return e == cudaSuccess ? 0 : -1;
+}
+#define KX_CHECKED 1
+#else
+#define KX_IDX(i, lim, site) (i)
+static inline int kx_chk_read(unsigned int *out, bool) {
+    out[0] = out[1] = out[2] = 0u;
+    return 0;
+}
+#define KX_CHECKED 0
+#endif
+// each translation unit with checked kernels defines its reader
+int kx_chk_read_contract(unsigned int *out, bool reset);
+int kx_chk_read_batch(unsigned int *out, bool reset);
+cudaError_t kx_launch_chk_probe(int index, int limit, int *out, cudaStream_t s);
+// limits of the FP32 streaming kernels' indices (KX_CHECK)
+struct kx_lim {
+    int ntask;
+    long long Vt;
+};
+
 struct kx_gl_nodes {
     double x[KX_MAX_NMU];
     double w[KX_MAX_NMU];
