@@ -291,7 +291,8 @@ def measure_batched(ctx, kx, torch, flush, iters=5, check_sample=4):
                         "frac_of_tf32_peak_issued": 3 * useful / (ms * 1e-3) / 1e12 / peak,
                         "tf32_peak_tflops": peak, "peak_source": peak_src,
                         "note": "whole kx_collision call (prep, both GEMMs or the exact loss, "
-                                "row combine and projection), cold L2"})
+                                "row combine and projection), cold L2",
+                        "launch_choices": ctx.split_tuning(k, B)})
         out[name] = row
         k.release()
     line = {"workload": "B=512 distributions sharing one N=192 kernel, q in [1e-3,1e2], "
@@ -581,7 +582,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--fp64-steps", type=int, default=1)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--only", default="", choices=["", "contraction", "step", "uneven", "serving"],
+    ap.add_argument("--only", default="", choices=["", "contraction", "step", "uneven", "serving", "batched"],
                     help="contraction: time the contraction kernel alone; step: run the "
                          "workload's steps only (no baselines), for profiling")
     ap.add_argument("--n", type=int, default=384)
@@ -609,12 +610,16 @@ def main():
         return run_reference(args, rank)
     if args.only == "contraction":
         return run_contraction_only(args)
-    if args.only in ("uneven", "serving"):
+    if args.only in ("uneven", "serving", "batched"):
         import torch
         import paper_2607_00755_b300 as kx
         ctx = kx.Context(0)
-        r = measure_uneven(ctx, kx) if args.only == "uneven" else measure_serving(
-            ctx, kx, requests=args.requests)
+        if args.only == "batched":
+            flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
+            r = measure_batched(ctx, kx, torch, flush)[0]
+        else:
+            r = measure_uneven(ctx, kx) if args.only == "uneven" else measure_serving(
+                ctx, kx, requests=args.requests)
         print(json.dumps(r), flush=True)
         ctx.close()
         return 0

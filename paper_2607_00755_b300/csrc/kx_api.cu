@@ -907,6 +907,12 @@ static int kx_solve_run(kx_ctx *ctx, const kx_kernel *k, int B, const kx_run &r,
     if (!kx_stream_is_tuned(k, B, r.v.grid_div)) nc = kx_stream_candidate_list(k, B, r.v.grid_div, cand);
     if (nc <= 1 && kx_tune_contraction(k, B, r.sv.f, r.v, r.sv.st, s, &ctx->launches))
         return kx_set_error(ctx, KX_ECUDA, "contraction autotuning failed");
+    if (k->precision == KX_SPLIT_TF32) {
+        // one contraction outside the capture: the split path tunes its launch
+        // choices on first use (the graph's first attempt recomputes it)
+        KX_CUDA_TRY(ctx, kx_launch_contract(k, B, r.sv.f, r.v, r.sv.st, 1, s, false));
+        ctx->launches += 3;
+    }
     if (kx_fault("deverr")) KX_CUDA_TRY(ctx, cudaMemsetAsync(r.v.err, 0x01, 1, s));   // as in kx_collision
     const int G = 16;
     cudaGraph_t graph = nullptr;
@@ -1210,6 +1216,9 @@ extern "C" int kx_solve_grouped(kx_ctx *ctx, int G, const kx_kernel *const *ks, 
         return e;
     };
     const int A = 8;   // attempts per graph
+    // one contraction outside the capture: the split path tunes its launch
+    // choices on first use (the graph's first attempt recomputes it)
+    KX_CUDA_TRY(ctx, kx_launch_batch_contract_grouped(G, ks, B, vs.data(), sts.data(), 1, d_err, s));
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
     cudaStream_t cap = nullptr;

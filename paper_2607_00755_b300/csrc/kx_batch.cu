@@ -15,6 +15,11 @@
 #include <cstring>
 #include <vector>
 
+#include <map>
+#include <mutex>
+#include <tuple>
+#include <vector>
+
 #include "kx_internal.cuh"
 
 #define KX_ATILE (128 * KX_TILE_K)   // floats per A tile: 128 rows x 16 k
@@ -168,14 +173,18 @@ __device__ __forceinline__ int kx_sg_find(const kx_sg_list &L, int w) {
 struct kx_sg_plan {
     int S, nsb, stage, fs, smem;
 };
-__host__ __device__ inline kx_sg_plan kx_sg_plan_for(bool gen, int n, int nsubI) {
+// req_S: the ring depth wanted (0: as many stages as fit, at most 4); use_fs:
+// stage the f' block when it fits (0: the generating warps read global memory).
+// Neither changes a result: the k chunks and their order are fixed.
+__host__ __device__ inline kx_sg_plan kx_sg_plan_for(bool gen, int n, int nsubI, int req_S = 0, int use_fs = 1) {
     kx_sg_plan pl;
     pl.nsb = nsubI < 4 ? nsubI : 4;
     pl.stage = 2 * KX_ATILE * 4 + 2 * pl.nsb * KX_BTILE * 4;
-    pl.fs = (gen && n <= 256) ? 128 * n * 4 : 0;   // (n, nsubI: the largest of a grouped launch)
+    pl.fs = (gen && n <= 256 && use_fs) ? 128 * n * 4 : 0;   // (n, nsubI: the largest of a grouped launch)
     const int budget = 227 * 1024 - 256;
     pl.S = (budget - pl.fs) / pl.stage;
     if (pl.S > 4) pl.S = 4;
+    if (req_S > 0 && req_S < pl.S) pl.S = req_S;
     pl.smem = pl.S * pl.stage + pl.fs + 256;
     return pl;
 }
@@ -663,6 +672,8 @@ static kx_loss_shape kx_loss_shape_for(int n) {
     if (n <= 400) return {2, 32};
     return {1, 32};
 }
+// (the warps per block fix the kernel's segment tables; the instances per lane
+// can be tuned: an instance's sums do not depend on them)
 // dynamic shared memory: the table, or the reduction if that is larger
 static size_t kx_loss_smem(int n, kx_loss_shape sh) {
     return std::max((size_t)n, (size_t)sh.warps) * 32 * sh.ipl * sizeof(float2);
@@ -677,7 +688,118 @@ void kx_batch_prepare() {
                          (int)kx_loss_smem(400, {2, 32}));
     cudaFuncSetAttribute(k_batch_loss<1, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)kx_loss_smem(KX_MAX_N, {1, 32}));
+    cudaFuncSetAttribute(k_batch_loss<1, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)kx_loss_smem(200, {1, 16}));
     cudaGetLastError();
+}
+
+// ------------------------------------------------------------ split tuner
+// The split path's result-neutral launch choices: the GEMM ring depth and the
+// f' staging (per launch shape: gain or loss, the widest grid, its i tiles,
+// the work items), and the exact loss kernel's instances per lane (per grid
+// and batch).  Each is timed on the launch's own operands the first time the
+// shape is launched outside a stream capture (the GEMMs and the loss kernel
+// rewrite their partials with the same values, so the repeats are harmless)
+// and kept for the process; under capture the default rule is used.
+struct kx_sg_choice {
+    int S, fs;
+};
+static std::mutex g_sg_mu;
+static std::map<std::tuple<int, int, int, int, int>, kx_sg_choice> g_sg_tuned;   // (dev, gen, n, nsubI, items)
+static std::map<std::tuple<int, int, int>, int> g_loss_tuned;                     // (dev, n, B) -> ipl
+static bool g_split_tuning = true;
+
+static bool kx_capturing(cudaStream_t s) {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(s, &cs) != cudaSuccess) {
+        cudaGetLastError();
+        return true;
+    }
+    return cs != cudaStreamCaptureStatusNone;
+}
+
+// best (min over 3 repeats after one warm launch) of the candidates; launch(c)
+// enqueues candidate c on s
+template <typename F>
+static int kx_time_candidates(int nc, cudaStream_t s, F launch) {
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+        if (e0) cudaEventDestroy(e0);
+        cudaGetLastError();
+        return 0;
+    }
+    int best = 0;
+    float best_ms = 0.f;
+    for (int c = 0; c < nc; ++c) {
+        float ms_c = 0.f;
+        cudaError_t e = launch(c);
+        for (int r = 0; r < 3 && e == cudaSuccess; ++r) {
+            float ms = 0.f;
+            e = cudaEventRecord(e0, s);
+            if (e == cudaSuccess) e = launch(c);
+            if (e == cudaSuccess) e = cudaEventRecord(e1, s);
+            if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+            if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+            if (e == cudaSuccess && (r == 0 || ms < ms_c)) ms_c = ms;
+        }
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            continue;
+        }
+        if (c == 0 || ms_c < best_ms) {
+            best_ms = ms_c;
+            best = c;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    return best;
+}
+
+extern "C" int kx_set_split_tuning(int enabled) {
+    std::lock_guard<std::mutex> lock(g_sg_mu);
+    g_split_tuning = enabled != 0;
+    if (!g_split_tuning) {
+        g_sg_tuned.clear();
+        g_loss_tuned.clear();
+    }
+    return KX_OK;
+}
+
+extern "C" int kx_get_split_tuning(const kx_kernel *k, int B, int *gain_S, int *gain_fs, int *loss_S,
+                                   int *loss_ipl, int *tuned) {
+    if (!k || B < 1 || !gain_S || !gain_fs || !loss_S || !loss_ipl || !tuned) return KX_EINVAL;
+    if (k->precision != KX_SPLIT_TF32) return KX_ENOTSUP;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    const int Bpad = (B + 127) / 128 * 128;
+    const int NTi = (k->nis + KX_GN - 1) / KX_GN;
+    const int ig = Bpad / 128 * NTi * k->gsk, il = Bpad / 128 * NTi * k->lsk;
+    std::lock_guard<std::mutex> lock(g_sg_mu);
+    *tuned = 0;
+    const kx_sg_plan dg = kx_sg_plan_for(true, k->n, k->nsubI), dl = kx_sg_plan_for(false, k->n, k->nsubI);
+    *gain_S = dg.S;
+    *gain_fs = dg.fs > 0;
+    *loss_S = k->cheb_K ? dl.S : 0;
+    *loss_ipl = kx_loss_shape_for(k->n).ipl;
+    auto ig_it = g_sg_tuned.find(std::make_tuple(dev, 1, k->n, k->nsubI, ig));
+    if (ig_it != g_sg_tuned.end()) {
+        const kx_sg_plan p = kx_sg_plan_for(true, k->n, k->nsubI, ig_it->second.S, ig_it->second.fs);
+        *gain_S = p.S;
+        *gain_fs = p.fs > 0;
+        *tuned |= 1;
+    }
+    auto il_it = g_sg_tuned.find(std::make_tuple(dev, 0, k->n, k->nsubI, il));
+    if (k->cheb_K && il_it != g_sg_tuned.end()) {
+        *loss_S = kx_sg_plan_for(false, k->n, k->nsubI, il_it->second.S, 0).S;
+        *tuned |= 2;
+    }
+    auto lo_it = g_loss_tuned.find(std::make_tuple(dev, k->n, B));
+    if (lo_it != g_loss_tuned.end()) {
+        *loss_ipl = lo_it->second;
+        *tuned |= 4;
+    }
+    return KX_OK;
 }
 
 // Persistent grid of a split GEMM: one CTA per SM, at most one per work item.
@@ -732,35 +854,90 @@ static cudaError_t kx_launch_split_gemm(bool gen, int G, const kx_kernel *const 
     L.items = items;
     int ncols = 32;   // two accumulators of the widest i tile
     while (ncols < 2 * wmax) ncols <<= 1;
-    const kx_sg_plan pl = kx_sg_plan_for(gen, nmax, nsmax);
-    if (gen)
-        k_split_gemm<true><<<kx_sg_grid(items), KX_SG_THREADS, pl.smem, s>>>(L, pl, ncols, d_err);
-    else
-        k_split_gemm<false><<<kx_sg_grid(items), KX_SG_THREADS, pl.smem, s>>>(L, pl, ncols, d_err);
-    return cudaGetLastError();
+    auto launch = [&](const kx_sg_plan &pl) {
+        if (gen)
+            k_split_gemm<true><<<kx_sg_grid(items), KX_SG_THREADS, pl.smem, s>>>(L, pl, ncols, d_err);
+        else
+            k_split_gemm<false><<<kx_sg_grid(items), KX_SG_THREADS, pl.smem, s>>>(L, pl, ncols, d_err);
+        return cudaGetLastError();
+    };
+    int dev = 0;
+    cudaGetDevice(&dev);
+    const auto key = std::make_tuple(dev, gen ? 1 : 0, nmax, nsmax, items);
+    kx_sg_choice ch = {0, 1};
+    bool tune = false;
+    {
+        std::lock_guard<std::mutex> lock(g_sg_mu);
+        auto it = g_sg_tuned.find(key);
+        if (it != g_sg_tuned.end()) ch = it->second;
+        else tune = g_split_tuning;
+    }
+    if (tune && !kx_capturing(s)) {
+        // ring depths 2 .. the most that fit, with and without the f' stage
+        std::vector<kx_sg_choice> cand;
+        for (int fs = (gen && nmax <= 256) ? 1 : 0; fs >= 0; --fs) {
+            const int smax = kx_sg_plan_for(gen, nmax, nsmax, 0, fs).S;
+            for (int S = smax; S >= 2; --S) cand.push_back({S, fs});
+        }
+        if (!cand.empty()) {
+            const int best = kx_time_candidates((int)cand.size(), s, [&](int c) {
+                return launch(kx_sg_plan_for(gen, nmax, nsmax, cand[c].S, cand[c].fs));
+            });
+            ch = cand[best];
+        }
+        std::lock_guard<std::mutex> lock(g_sg_mu);
+        g_sg_tuned[key] = ch;
+    }
+    return launch(kx_sg_plan_for(gen, nmax, nsmax, ch.S, ch.fs));
 }
 
 // The exact loss kernel (all instances, or the Chebyshev path's flagged ones).
 static cudaError_t kx_launch_batch_loss(const kx_kernel *k, int B, const kx_batch_views &v,
                                         const kx_inst_state *st, int stage, cudaStream_t s) {
-    const kx_loss_shape sh = kx_loss_shape_for(k->n);
-    const int per = 32 * sh.ipl;
-    dim3 g2((B + per - 1) / per, k->n);
-    const size_t smem = kx_loss_smem(k->n, sh);
     const int *flags = k->cheb_K ? v.cflag : nullptr;
-    if (sh.ipl == 2 && sh.warps == 16)
-        k_batch_loss<2, 16><<<g2, 512, smem, s>>>(k->n, B, v.B, k->d_lel, k->d_lseg, k->d_lsw, k->d_lorder,
-                                                  v.td, v.fmax, v.partial, st, stage, flags,
-                                                  (int)k->nlel);
-    else if (sh.ipl == 2)
-        k_batch_loss<2, 32><<<g2, 1024, smem, s>>>(k->n, B, v.B, k->d_lel, k->d_lseg, k->d_lsw, k->d_lorder,
-                                                   v.td, v.fmax, v.partial, st, stage, flags,
-                                                  (int)k->nlel);
-    else
-        k_batch_loss<1, 32><<<g2, 1024, smem, s>>>(k->n, B, v.B, k->d_lel, k->d_lseg, k->d_lsw, k->d_lorder,
-                                                   v.td, v.fmax, v.partial, st, stage, flags,
-                                                  (int)k->nlel);
-    return cudaGetLastError();
+    auto launch = [&](kx_loss_shape sh) {
+        const int per = 32 * sh.ipl;
+        dim3 g2((B + per - 1) / per, k->n);
+        const size_t smem = kx_loss_smem(k->n, sh);
+        if (sh.ipl == 2 && sh.warps == 16)
+            k_batch_loss<2, 16><<<g2, 512, smem, s>>>(k->n, B, v.B, k->d_lel, k->d_lseg, k->d_lsw, k->d_lorder,
+                                                      v.td, v.fmax, v.partial, st, stage, flags, (int)k->nlel);
+        else if (sh.warps == 16)
+            k_batch_loss<1, 16><<<g2, 512, smem, s>>>(k->n, B, v.B, k->d_lel, k->d_lseg, k->d_lsw, k->d_lorder,
+                                                      v.td, v.fmax, v.partial, st, stage, flags, (int)k->nlel);
+        else if (sh.ipl == 2)
+            k_batch_loss<2, 32><<<g2, 1024, smem, s>>>(k->n, B, v.B, k->d_lel, k->d_lseg, k->d_lsw, k->d_lorder,
+                                                       v.td, v.fmax, v.partial, st, stage, flags, (int)k->nlel);
+        else
+            k_batch_loss<1, 32><<<g2, 1024, smem, s>>>(k->n, B, v.B, k->d_lel, k->d_lseg, k->d_lsw, k->d_lorder,
+                                                       v.td, v.fmax, v.partial, st, stage, flags, (int)k->nlel);
+        return cudaGetLastError();
+    };
+    kx_loss_shape sh = kx_loss_shape_for(k->n);
+    // (the Chebyshev path runs the exact loss only for flagged instances: not tuned)
+    if (!k->cheb_K) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        const auto key = std::make_tuple(dev, k->n, B);
+        bool tune = false;
+        {
+            std::lock_guard<std::mutex> lock(g_sg_mu);
+            auto it = g_loss_tuned.find(key);
+            if (it != g_loss_tuned.end()) sh.ipl = it->second;
+            else tune = g_split_tuning;
+        }
+        if (tune && !kx_capturing(s)) {
+            // the rule's shape and the other instances-per-lane count (two
+            // instances per lane with 32 warps fit only up to n = 400)
+            const kx_loss_shape c2[2] = {sh, {3 - sh.ipl, sh.warps}};
+            const int nc = (sh.ipl == 1 && sh.warps == 32) ? 1 : 2;
+            const int best = kx_time_candidates(nc, s, [&](int c) { return launch(c2[c]); });
+            sh.ipl = c2[best].ipl;
+            std::lock_guard<std::mutex> lock(g_sg_mu);
+            g_loss_tuned[key] = sh.ipl;
+        }
+    }
+    return launch(sh);
 }
 
 cudaError_t kx_launch_batch_contract(const kx_kernel *k, int B, const kx_batch_views &v,

@@ -304,3 +304,31 @@ def test_grouped_solve_equals_per_grid_solves(env, loss_terms):
             assert err <= 1e-4, (g, err)
     for k in ks:
         k.release()
+
+
+@pytest.mark.parametrize("N,B", [(96, 200), (260, 40)])
+def test_split_tuning_is_result_neutral(env, N, B):
+    """The split path's timed launch choices (GEMM ring depth, f' staging,
+    instances per lane of the exact loss) change no bit of C: the result with
+    the default rule, on the call that times the choices, and with the chosen
+    ones are identical, for the exact and the Chebyshev loss; the choices are
+    recorded as timed."""
+    kx, ctx, torch = env
+    q = ki.log_grid(N, 1e-3, 1e2)
+    f = ki.batch_bimodal(np.random.default_rng(70 + N), q, B)
+    sig = 10.0 ** np.random.default_rng(71).uniform(-1, 1, B)
+    fd = torch.as_tensor(f, device="cuda")
+    for lt in (0, 16):
+        k = ctx.build_kernel(q, precision=kx.SPLIT_TF32, loss_terms=lt)
+        ctx.set_split_tuning(False)
+        C0 = ctx.collision(k, fd, sig)[0].cpu().numpy()
+        assert ctx.split_tuning(k, B)["tuned"] == 0
+        ctx.set_split_tuning(True)
+        C1 = ctx.collision(k, fd, sig)[0].cpu().numpy()
+        C2 = ctx.collision(k, fd, sig)[0].cpu().numpy()
+        np.testing.assert_array_equal(C1, C0)
+        np.testing.assert_array_equal(C2, C0)
+        t = ctx.split_tuning(k, B)
+        assert t["tuned"] & 1 and t["gain_S"] >= 2
+        assert (t["tuned"] & 2) if lt else (t["tuned"] & 4)
+        k.release()
