@@ -123,6 +123,14 @@ typedef struct {
     int fixed_step;         /* 1: constant h = h0, always accept, negative stage -> KX_ENEG */
     int check_every;        /* MB test every k accepted steps */
     int project;            /* 1: use the projected operator (Appendix B) */
+    int chains;             /* kx_solve / kx_solve_host only (no counterpart in the paper):
+                               0 = the library's rule: on the FP32 path a batch of 2..4
+                               instances runs as concurrent chains, one per instance (its
+                               own state, captured graph of attempts and stream), which
+                               overlap one another's kernel dependency gaps; else one
+                               batch; 1 = one batch; 2 = one chain per instance (batches of
+                               up to 8, any path).  The results are the same bits either
+                               way: an instance's arithmetic does not depend on its batch. */
 } kx_solve_params;
 
 /* Projection diagnostics (Appendix B: eq. app_epsilon_definition and

@@ -49,7 +49,7 @@ class SolveParams(ctypes.Structure):
                 ("rtol", ctypes.c_double), ("atol", ctypes.c_double), ("h_min", ctypes.c_double),
                 ("h_max", ctypes.c_double), ("l1_tol", ctypes.c_double),
                 ("max_attempts", ctypes.c_int), ("fixed_step", ctypes.c_int),
-                ("check_every", ctypes.c_int), ("project", ctypes.c_int)]
+                ("check_every", ctypes.c_int), ("project", ctypes.c_int), ("chains", ctypes.c_int)]
 
 
 class Diag(ctypes.Structure):
@@ -308,7 +308,8 @@ class Context:
     @staticmethod
     def params(**kw):
         p = dict(t0=0.0, t_end=1.0, h0=1e-3, rtol=1e-6, atol=1e-12, h_min=0.0, h_max=0.0,
-                 l1_tol=0.0, max_attempts=1_000_000, fixed_step=0, check_every=10, project=1)
+                 l1_tol=0.0, max_attempts=1_000_000, fixed_step=0, check_every=10, project=1,
+                 chains=0)
         p.update(kw)
         return SolveParams(**{k: p[k] for k, _ in SolveParams._fields_})
 

@@ -706,6 +706,7 @@ static int kx_check_params(kx_ctx *ctx, const kx_solve_params *p) {
         return kx_set_error(ctx, KX_EINVAL, "rtol/atol must be >= 0, not both 0");
     if (!(p->h0 > 0)) return kx_set_error(ctx, KX_EINVAL, "h0 must be > 0");
     if (p->max_attempts < 1) return kx_set_error(ctx, KX_EINVAL, "max_attempts must be >= 1");
+    if (p->chains < 0 || p->chains > 2) return kx_set_error(ctx, KX_EINVAL, "chains must be 0, 1 or 2");
     return KX_OK;
 }
 
@@ -891,10 +892,12 @@ extern "C" int kx_step(kx_ctx *ctx, const kx_kernel *k, int B, const double *sig
 
 // Device-resident integration: G attempts per captured graph; the host keeps
 // one graph in flight ahead of the status word it reads (bounded wall time).
-static int kx_solve_run(kx_ctx *ctx, const kx_kernel *k, int B, const kx_run &r,
-                        const kx_solve_params *par, kx_result *res) {
-    cudaStream_t s = ctx->stream;
-    const auto t_start = std::chrono::steady_clock::now();
+// Prepares a run's graph of G attempts on stream s: f's tables, the FP32
+// streaming variant (tuned in place when the size has no choice yet), the
+// split path's launch choices, then the capture.  *launched: graph replays the
+// tuning made (real attempts of this run).
+static int kx_run_prepare(kx_ctx *ctx, const kx_kernel *k, int B, const kx_run &r, cudaStream_t s, int G,
+                          cudaGraph_t *graph_out, cudaGraphExec_t *exec_out, long long *launched) {
     KX_CUDA_TRY(ctx, kx_launch_prep(k, B, r.sv.f, r.v, r.sv.st, s));
     ctx->launches += 1;
     // The FP32 path's streaming variant: tuned here, on this solve's own
@@ -914,12 +917,8 @@ static int kx_solve_run(kx_ctx *ctx, const kx_kernel *k, int B, const kx_run &r,
         ctx->launches += 3;
     }
     if (kx_fault("deverr")) KX_CUDA_TRY(ctx, cudaMemsetAsync(r.v.err, 0x01, 1, s));   // as in kx_collision
-    const int G = 16;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
-    int rc = KX_OK;
-    if ((rc = kx_pinned_reserve(ctx, 2 * sizeof(kx_inst_state) * (size_t)B)) != KX_OK) return rc;
-    kx_inst_state *h_st = (kx_inst_state *)ctx->h_pinned;
     auto capture = [&](cudaGraph_t *gr, cudaGraphExec_t *ex) -> cudaError_t {
         cudaStream_t cap = nullptr;
         cudaError_t x = cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking);
@@ -933,7 +932,6 @@ static int kx_solve_run(kx_ctx *ctx, const kx_kernel *k, int B, const kx_run &r,
         if (cap) cudaStreamDestroy(cap);
         return x;
     };
-    long long launched = 0;
     cudaError_t e = cudaSuccess;
     if (nc > 1) {
         cudaGraph_t gs[8] = {};
@@ -953,7 +951,7 @@ static int kx_solve_run(kx_ctx *ctx, const kx_kernel *k, int B, const kx_run &r,
                 }
                 if (e == cudaSuccess) e = cudaGraphLaunch(xs[c], s);
                 if (e == cudaSuccess && rd > 0) e = cudaEventRecord(te[rd][c][1], s);
-                ++launched;
+                ++*launched;
                 ctx->launches += 4LL * G;
             }
         if (e == cudaSuccess) e = cudaStreamSynchronize(s);
@@ -991,6 +989,24 @@ static int kx_solve_run(kx_ctx *ctx, const kx_kernel *k, int B, const kx_run &r,
         if (graph) cudaGraphDestroy(graph);
         return kx_set_error(ctx, KX_ECUDA, std::string("graph capture: ") + cudaGetErrorString(e));
     }
+    *graph_out = graph;
+    *exec_out = exec;
+    return KX_OK;
+}
+
+static int kx_solve_run(kx_ctx *ctx, const kx_kernel *k, int B, const kx_run &r,
+                        const kx_solve_params *par, kx_result *res) {
+    cudaStream_t s = ctx->stream;
+    const auto t_start = std::chrono::steady_clock::now();
+    const int G = 16;
+    int rc = KX_OK;
+    if ((rc = kx_pinned_reserve(ctx, 2 * sizeof(kx_inst_state) * (size_t)B)) != KX_OK) return rc;
+    kx_inst_state *h_st = (kx_inst_state *)ctx->h_pinned;
+    long long launched = 0;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    if ((rc = kx_run_prepare(ctx, k, B, r, s, G, &graph, &exec, &launched)) != KX_OK) return rc;
+    cudaError_t e = cudaSuccess;
     // two status buffers / events: graph g+1 runs while the host reads graph g's status
     cudaEvent_t ev[2] = {nullptr, nullptr};
     cudaEventCreateWithFlags(&ev[0], cudaEventDisableTiming);
@@ -1039,6 +1055,131 @@ static int kx_solve_run(kx_ctx *ctx, const kx_kernel *k, int B, const kx_run &r,
     return worst;
 }
 
+// Whether kx_solve runs a batch as concurrent per-instance chains (the
+// chains field of kx_solve_params).
+#define KX_CHAINS_MAX 8
+static bool kx_use_chains(const kx_kernel *k, int B, const kx_solve_params *par) {
+    if (par->chains == 1 || B < 2) return false;
+    if (par->chains == 2) return B <= KX_CHAINS_MAX;
+    return k->precision == KX_FP32 && B <= 4;
+}
+
+// A small batch as concurrent chains: every instance its own run (arena
+// region, state, captured graph of G attempts) on its own stream, each graph
+// relaunched as its chain's status arrives (two in flight per chain).  The
+// chains' kernels fill one another's dependency gaps: at N = 128 an attempt
+// of a batch is a chain of four latency-bound kernels.  An instance's
+// arithmetic does not depend on the batch it is launched with, so the results
+// are those of the single-batch solve bit for bit.  f_dev: device [B][n] (in
+// place); arena_base: the arena offset of the first chain's region.
+static int kx_solve_chains(kx_ctx *ctx, const kx_kernel *k, int B, const double *sigma, const kx_source *src,
+                           int nsets, const kx_solve_params *par, double *f_dev, kx_result *res,
+                           size_t arena_base = 0) {
+    const auto t_start = std::chrono::steady_clock::now();
+    const int n = k->n, G = 16;
+    int rc = KX_OK;
+    const size_t per = kx_align(kx_layout_solve(k, 1, KX_MAX_SRC + 1, false).total);
+    if ((rc = kx_arena_reserve(ctx, arena_base + per * B)) != KX_OK) return rc;
+    std::vector<kx_run> runs(B);
+    for (int b = 0; b < B; ++b) {
+        double *f = nullptr;
+        const kx_source *sb = src ? src + (nsets == B ? b : 0) : nullptr;
+        // (the arena is reserved above: the region at offset 0 does not move it)
+        if ((rc = kx_setup_run(ctx, k, 1, sigma + b, sb, sb ? 1 : 0, par, nullptr, nullptr, f_dev + (size_t)b * n,
+                               false, &runs[b], &f, nullptr, arena_base + per * b)))
+            return rc;
+    }
+    if ((rc = kx_pinned_reserve(ctx, 2 * sizeof(kx_inst_state) * (size_t)B)) != KX_OK) return rc;
+    kx_inst_state *h_st = (kx_inst_state *)ctx->h_pinned;
+    std::vector<cudaStream_t> cs(B, nullptr);
+    std::vector<cudaGraph_t> graph(B, nullptr);
+    std::vector<cudaGraphExec_t> exec(B, nullptr);
+    std::vector<cudaEvent_t> ev(2 * B, nullptr);
+    std::vector<long long> launched(B, 0), g(B, 0);
+    std::vector<int> done(B, 0);
+    std::vector<double> lat(B, 0.0);
+    cudaEvent_t fork = nullptr;
+    cudaError_t e = cudaEventCreateWithFlags(&fork, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventRecord(fork, ctx->stream);   // after the runs' uploads
+    for (int b = 0; b < B && e == cudaSuccess; ++b) {
+        e = cudaStreamCreateWithFlags(&cs[b], cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(cs[b], fork, 0);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ev[2 * b], cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ev[2 * b + 1], cudaEventDisableTiming);
+    }
+    // (the first chain tunes the streaming variant in place if its size has no
+    // choice yet; the others find it)
+    for (int b = 0; b < B && e == cudaSuccess && rc == KX_OK; ++b)
+        rc = kx_run_prepare(ctx, k, 1, runs[b], cs[b], G, &graph[b], &exec[b], &launched[b]);
+    const long long max_launch = (long long)par->max_attempts / G + 2;
+    const double wall_limit = 600.0;
+    const bool fault_timeout = kx_fault("timeout");
+    auto launch_one = [&](int b, int slot) -> cudaError_t {
+        cudaError_t x = cudaGraphLaunch(exec[b], cs[b]);
+        if (x == cudaSuccess)
+            x = cudaMemcpyAsync(h_st + 2 * (size_t)b + slot, runs[b].sv.st, sizeof(kx_inst_state),
+                                cudaMemcpyDeviceToHost, cs[b]);
+        if (x == cudaSuccess) x = cudaEventRecord(ev[2 * b + slot], cs[b]);
+        ++launched[b];
+        ctx->launches += 4LL * G;
+        return x;
+    };
+    for (int b = 0; b < B && e == cudaSuccess && rc == KX_OK; ++b) {
+        e = launch_one(b, 0);
+        if (e == cudaSuccess && launched[b] < max_launch) e = launch_one(b, 1);
+    }
+    int remaining = B;
+    while (remaining > 0 && e == cudaSuccess && rc == KX_OK) {
+        bool progressed = false;
+        for (int b = 0; b < B && e == cudaSuccess; ++b) {
+            if (done[b]) continue;
+            const int slot = (int)(g[b] & 1);
+            const cudaError_t q = cudaEventQuery(ev[2 * b + slot]);
+            if (q == cudaErrorNotReady) continue;
+            if (q != cudaSuccess) {
+                e = q;
+                break;
+            }
+            progressed = true;
+            if (h_st[2 * (size_t)b + slot].done || launched[b] >= max_launch) {
+                done[b] = 1;
+                --remaining;
+                lat[b] = std::chrono::duration<double>(std::chrono::steady_clock::now() - t_start).count();
+                continue;
+            }
+            e = launch_one(b, slot);
+            ++g[b];
+        }
+        if (!progressed && e == cudaSuccess) {
+            if (fault_timeout) rc = KX_ETIMEOUT;
+            const double el = std::chrono::duration<double>(std::chrono::steady_clock::now() - t_start).count();
+            if (el > wall_limit) rc = KX_ETIMEOUT;
+            std::this_thread::yield();
+        }
+    }
+    for (int b = 0; b < B; ++b)
+        if (cs[b]) cudaStreamSynchronize(cs[b]);
+    for (int b = 0; b < B; ++b) {
+        if (exec[b]) cudaGraphExecDestroy(exec[b]);
+        if (graph[b]) cudaGraphDestroy(graph[b]);
+        if (cs[b]) cudaStreamDestroy(cs[b]);
+    }
+    for (auto x : ev)
+        if (x) cudaEventDestroy(x);
+    if (fork) cudaEventDestroy(fork);
+    if (rc != KX_OK && rc != KX_ETIMEOUT) return rc;
+    if (e != cudaSuccess) return kx_set_error(ctx, KX_ECUDA, std::string("solve chains: ") + cudaGetErrorString(e));
+    int worst = KX_OK;
+    for (int b = 0; b < B; ++b) {
+        const int w = kx_collect(ctx, k, 1, runs[b], res ? res + b : nullptr, nullptr, nullptr,
+                                 lat[b] > 0.0 ? lat[b]
+                                              : std::chrono::duration<double>(std::chrono::steady_clock::now() - t_start).count());
+        if (w != KX_OK && worst == KX_OK) worst = w;
+    }
+    if (rc) return rc;
+    return worst;
+}
+
 extern "C" int kx_solve(kx_ctx *ctx, const kx_kernel *k, int B, const double *sigma,
                         const kx_source *src, int nsets, const kx_solve_params *par, double *f_dev,
                         kx_result *res) {
@@ -1048,6 +1189,7 @@ extern "C" int kx_solve(kx_ctx *ctx, const kx_kernel *k, int B, const double *si
     if ((rc = kx_check_params(ctx, par)) != KX_OK) return rc;
     if (!f_dev) return kx_set_error(ctx, KX_EINVAL, "null f");
     KX_CUDA_TRY(ctx, cudaSetDevice(ctx->device));
+    if (kx_use_chains(k, B, par)) return kx_solve_chains(ctx, k, B, sigma, src, nsets, par, f_dev, res);
     kx_run r;
     double *f = nullptr;
     if ((rc = kx_setup_run(ctx, k, B, sigma, src, nsets, par, nullptr, nullptr, f_dev, false, &r, &f)))
@@ -1144,6 +1286,21 @@ extern "C" int kx_solve_host(kx_ctx *ctx, const kx_kernel *k, int B, const doubl
     if ((rc = kx_check_params(ctx, par)) != KX_OK) return rc;
     if (!f_host) return kx_set_error(ctx, KX_EINVAL, "null f");
     KX_CUDA_TRY(ctx, cudaSetDevice(ctx->device));
+    if (kx_use_chains(k, B, par)) {
+        // f at the start of the arena, the chains' regions after it
+        const size_t fb = kx_align(sizeof(double) * B * k->n);
+        const size_t per = kx_align(kx_layout_solve(k, 1, KX_MAX_SRC + 1, false).total);
+        if ((rc = kx_arena_reserve(ctx, fb + per * B)) != KX_OK) return rc;
+        double *f = (double *)ctx->d_arena;
+        cudaStream_t s = ctx->stream;
+        KX_CUDA_TRY(ctx, cudaMemcpyAsync(f, f_host, sizeof(double) * B * k->n, cudaMemcpyHostToDevice, s));
+        if (kx_fault("nan")) KX_CUDA_TRY(ctx, cudaMemsetAsync(f, 0xff, sizeof(double), s));   // f[0][0] = NaN
+        int rc2 = kx_solve_chains(ctx, k, B, sigma, src, nsets, par, f, res, fb);
+        if (rc2 == KX_ECUDA || rc2 == KX_ETIMEOUT || rc2 == KX_ENOMEM || rc2 == KX_EINVAL) return rc2;
+        KX_CUDA_TRY(ctx, cudaMemcpyAsync(f_host, f, sizeof(double) * B * k->n, cudaMemcpyDeviceToHost, s));
+        KX_CUDA_TRY(ctx, cudaStreamSynchronize(s));
+        return rc2;
+    }
     kx_run r;
     double *f = nullptr;
     if ((rc = kx_setup_run(ctx, k, B, sigma, src, nsets, par, nullptr, nullptr, nullptr, true, &r, &f)))

@@ -442,6 +442,40 @@ def test_solve_batch_of_sigmas_matches_individual(ctx, kx):
         np.testing.assert_array_equal(fh, fb.cpu().numpy())
 
 
+@pytest.mark.parametrize("precision", [0, 1])
+def test_concurrent_chains_equal_one_batch(ctx, kx, precision):
+    """kx_solve's concurrent per-instance chains (the rule's choice for small
+    FP32 batches, chains = 2 forces them on any path) give the bits of the
+    one-batch solve (chains = 1): f, steps, rejects, evaluations and the MB
+    fit of every instance, with per-instance sources, on device and host
+    buffers alike; invalid chain settings are refused."""
+    q = ki.log_grid(40, 1e-3, 10.0)
+    B = 3
+    f0 = ki.batch_bimodal(np.random.default_rng(66), q, B)
+    sig = np.array([0.3, 1.0, 4.0])
+    rng = np.random.default_rng(67)
+    srcs = [dict(shape=np.stack([ki.lognormal_bumps(q, (c,), (0.3,), (1.0,)) for c in (0.05, 2.0)]),
+                 rate=rng.uniform(0.01, 0.05, 2), tau=np.array([1.0, 1.0]), t_on=np.array([0.0, 1.0]))
+            for _ in range(B)]
+    par = dict(t_end=4.0, h0=1e-3, rtol=1e-6, atol=1e-12, l1_tol=1e-3, check_every=5)
+    k = ctx.build_kernel(q, precision=precision)
+    out = {}
+    for ch in (1, 0, 2):
+        fd = dev(f0)
+        res = ctx.solve(k, fd, sig, sources=srcs, chains=ch, **par)
+        out[ch] = (fd.cpu().numpy(), res)
+    fh, rh = ctx.solve_host(k, f0, sig, sources=srcs, chains=2, **par)
+    out["host"] = (fh, rh)
+    for key in (0, 2, "host"):
+        np.testing.assert_array_equal(out[key][0], out[1][0])
+        for a, b in zip(out[key][1], out[1][1]):
+            for fld in ("steps", "rejects", "evals", "status", "converged", "t", "h", "T_mb", "l1_to_mb"):
+                assert a[fld] == b[fld], (key, fld, a[fld], b[fld])
+    with pytest.raises(kx.KxError):
+        ctx.solve(k, dev(f0), sig, chains=3, **par)
+    k.release()
+
+
 def test_mb_fit_matches_oracle(ctx, kx):
     N = 64
     q = ki.log_grid(N, 1e-3, 10.0)
