@@ -203,6 +203,7 @@ void kx_carve_views(const kx_kernel *k, int B, void *base, kx_batch_views *v) {
     v->tlam = nullptr;
     v->eta = k->stats;
     v->grid_div = 1;
+    v->tune_tag = 0;
     if (k->precision == KX_FP32 && k->stats) {
         v->tq = (float4 *)p; p += kx_align(sizeof(float4) * B * n);
         v->tlam = (float *)p; p += kx_align(sizeof(float) * B * n);
@@ -892,12 +893,30 @@ extern "C" int kx_step(kx_ctx *ctx, const kx_kernel *k, int B, const double *sig
 
 // Device-resident integration: G attempts per captured graph; the host keeps
 // one graph in flight ahead of the status word it reads (bounded wall time).
+// A captured graph of G attempts of run r.
+static cudaError_t kx_capture_attempts(const kx_kernel *k, int B, const kx_run &r, int G, cudaGraph_t *gr,
+                                       cudaGraphExec_t *ex) {
+    cudaStream_t cap = nullptr;
+    cudaError_t x = cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking);
+    if (x == cudaSuccess) x = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+    if (x == cudaSuccess) {
+        for (int a = 0; a < G && x == cudaSuccess; ++a) x = kx_enqueue_attempt(k, B, r, cap, a == 0);
+        cudaError_t x2 = cudaStreamEndCapture(cap, gr);
+        if (x == cudaSuccess) x = x2;
+    }
+    if (x == cudaSuccess) x = cudaGraphInstantiate(ex, *gr, 0);
+    if (cap) cudaStreamDestroy(cap);
+    return x;
+}
+
 // Prepares a run's graph of G attempts on stream s: f's tables, the FP32
-// streaming variant (tuned in place when the size has no choice yet), the
-// split path's launch choices, then the capture.  *launched: graph replays the
-// tuning made (real attempts of this run).
+// streaming variant (tuned in place when the size has no choice yet, unless
+// tune is false), the split path's launch choices, then the capture (not when
+// capture is false: the caller captures).  *launched: graph replays the tuning
+// made (real attempts of this run).
 static int kx_run_prepare(kx_ctx *ctx, const kx_kernel *k, int B, const kx_run &r, cudaStream_t s, int G,
-                          cudaGraph_t *graph_out, cudaGraphExec_t *exec_out, long long *launched) {
+                          cudaGraph_t *graph_out, cudaGraphExec_t *exec_out, long long *launched,
+                          bool tune = true, bool capture_graph = true) {
     KX_CUDA_TRY(ctx, kx_launch_prep(k, B, r.sv.f, r.v, r.sv.st, s));
     ctx->launches += 1;
     // The FP32 path's streaming variant: tuned here, on this solve's own
@@ -907,8 +926,9 @@ static int kx_run_prepare(kx_ctx *ctx, const kx_kernel *k, int B, const kx_run &
     // order of the replays.  A stand-in predecessor does not rank them the way
     // the stages between contractions do.
     int cand[8], nc = 0;
-    if (!kx_stream_is_tuned(k, B, r.v.grid_div)) nc = kx_stream_candidate_list(k, B, r.v.grid_div, cand);
-    if (nc <= 1 && kx_tune_contraction(k, B, r.sv.f, r.v, r.sv.st, s, &ctx->launches))
+    if (tune && !kx_stream_is_tuned(k, B, r.v.grid_div, r.v.tune_tag))
+        nc = kx_stream_candidate_list(k, B, r.v.grid_div, cand);
+    if (tune && nc <= 1 && kx_tune_contraction(k, B, r.sv.f, r.v, r.sv.st, s, &ctx->launches))
         return kx_set_error(ctx, KX_ECUDA, "contraction autotuning failed");
     if (k->precision == KX_SPLIT_TF32) {
         // one contraction outside the capture: the split path tunes its launch
@@ -917,21 +937,10 @@ static int kx_run_prepare(kx_ctx *ctx, const kx_kernel *k, int B, const kx_run &
         ctx->launches += 3;
     }
     if (kx_fault("deverr")) KX_CUDA_TRY(ctx, cudaMemsetAsync(r.v.err, 0x01, 1, s));   // as in kx_collision
+    if (!capture_graph) return KX_OK;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
-    auto capture = [&](cudaGraph_t *gr, cudaGraphExec_t *ex) -> cudaError_t {
-        cudaStream_t cap = nullptr;
-        cudaError_t x = cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking);
-        if (x == cudaSuccess) x = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
-        if (x == cudaSuccess) {
-            for (int a = 0; a < G && x == cudaSuccess; ++a) x = kx_enqueue_attempt(k, B, r, cap, a == 0);
-            cudaError_t x2 = cudaStreamEndCapture(cap, gr);
-            if (x == cudaSuccess) x = x2;
-        }
-        if (x == cudaSuccess) x = cudaGraphInstantiate(ex, *gr, 0);
-        if (cap) cudaStreamDestroy(cap);
-        return x;
-    };
+    auto capture = [&](cudaGraph_t *gr, cudaGraphExec_t *ex) { return kx_capture_attempts(k, B, r, G, gr, ex); };
     cudaError_t e = cudaSuccess;
     if (nc > 1) {
         cudaGraph_t gs[8] = {};
@@ -939,7 +948,7 @@ static int kx_run_prepare(kx_ctx *ctx, const kx_kernel *k, int B, const kx_run &
         const int rounds = 3;   // the first replays warm the graphs up (not timed)
         cudaEvent_t te[3][8][2] = {};
         for (int c = 0; c < nc && e == cudaSuccess; ++c) {
-            kx_stream_pin(k, B, r.v.grid_div, cand[c]);
+            kx_stream_pin(k, B, r.v.grid_div, r.v.tune_tag, cand[c]);
             e = capture(&gs[c], &xs[c]);
         }
         for (int rd = 0; rd < rounds && e == cudaSuccess; ++rd)
@@ -973,7 +982,7 @@ static int kx_run_prepare(kx_ctx *ctx, const kx_kernel *k, int B, const kx_run &
             for (int c = 0; c < nc; ++c)
                 for (int q = 0; q < 2; ++q)
                     if (te[rd][c][q]) cudaEventDestroy(te[rd][c][q]);
-        kx_stream_pin(k, B, r.v.grid_div, cand[best]);
+        kx_stream_pin(k, B, r.v.grid_div, r.v.tune_tag, cand[best]);
         for (int c = 0; c < nc; ++c) {
             if (c == best) continue;
             if (xs[c]) cudaGraphExecDestroy(xs[c]);
@@ -1107,10 +1116,86 @@ static int kx_solve_chains(kx_ctx *ctx, const kx_kernel *k, int B, const double 
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ev[2 * b], cudaEventDisableTiming);
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ev[2 * b + 1], cudaEventDisableTiming);
     }
-    // (the first chain tunes the streaming variant in place if its size has no
-    // choice yet; the others find it)
+    // The streaming variant of chain launches has its own tuning key (the
+    // chains share the GPU): when it has no choice yet, every candidate's
+    // graphs of all chains are replayed together, in turn, and timed from the
+    // first chain's start to the last chain's end; the fastest candidate's
+    // graphs are kept.
+    for (int b = 0; b < B; ++b) runs[b].v.tune_tag = B;
+    int cand[8], nc = 0;
+    if (!kx_stream_is_tuned(k, 1, 1, B)) nc = kx_stream_candidate_list(k, 1, 1, cand);
     for (int b = 0; b < B && e == cudaSuccess && rc == KX_OK; ++b)
-        rc = kx_run_prepare(ctx, k, 1, runs[b], cs[b], G, &graph[b], &exec[b], &launched[b]);
+        rc = kx_run_prepare(ctx, k, 1, runs[b], cs[b], G, &graph[b], &exec[b], &launched[b], nc <= 1, nc <= 1);
+    if (nc > 1 && e == cudaSuccess && rc == KX_OK) {
+        std::vector<cudaGraph_t> gx((size_t)nc * B, nullptr);
+        std::vector<cudaGraphExec_t> xx((size_t)nc * B, nullptr);
+        for (int c = 0; c < nc && e == cudaSuccess; ++c) {
+            kx_stream_pin(k, 1, 1, B, cand[c]);
+            for (int b = 0; b < B && e == cudaSuccess; ++b)
+                e = kx_capture_attempts(k, 1, runs[b], G, &gx[(size_t)c * B + b], &xx[(size_t)c * B + b]);
+        }
+        const int rounds = 3;   // (the first round warms the graphs up: not timed)
+        std::vector<cudaEvent_t> t0((size_t)rounds * nc, nullptr), t1((size_t)rounds * nc, nullptr);
+        cudaEvent_t done_b = nullptr;
+        cudaStream_t ts = nullptr;
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&done_b, cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&ts, cudaStreamNonBlocking);
+        for (size_t j = 0; j < t0.size() && e == cudaSuccess; ++j) {
+            e = cudaEventCreate(&t0[j]);
+            if (e == cudaSuccess) e = cudaEventCreate(&t1[j]);
+        }
+        for (int b = 0; b < B && e == cudaSuccess; ++b) {   // after every chain's preparation
+            e = cudaEventRecord(done_b, cs[b]);
+            if (e == cudaSuccess) e = cudaStreamWaitEvent(ts, done_b, 0);
+        }
+        for (int rd = 0; rd < rounds && e == cudaSuccess; ++rd)
+            for (int c = 0; c < nc && e == cudaSuccess; ++c) {
+                const size_t j = (size_t)rd * nc + c;
+                e = cudaEventRecord(t0[j], ts);
+                for (int b = 0; b < B && e == cudaSuccess; ++b) {
+                    e = cudaStreamWaitEvent(cs[b], t0[j], 0);
+                    if (e == cudaSuccess) e = cudaGraphLaunch(xx[(size_t)c * B + b], cs[b]);
+                    if (e == cudaSuccess) e = cudaEventRecord(done_b, cs[b]);
+                    if (e == cudaSuccess) e = cudaStreamWaitEvent(ts, done_b, 0);
+                    ++launched[b];
+                    ctx->launches += 4LL * G;
+                }
+                if (e == cudaSuccess) e = cudaEventRecord(t1[j], ts);
+            }
+        if (e == cudaSuccess) e = cudaStreamSynchronize(ts);
+        int best = 0;
+        float best_ms = 0.f;
+        for (int c = 0; c < nc && e == cudaSuccess; ++c) {
+            float ms = 0.f;
+            for (int rd = 1; rd < rounds && e == cudaSuccess; ++rd) {
+                float t = 0.f;
+                e = cudaEventElapsedTime(&t, t0[(size_t)rd * nc + c], t1[(size_t)rd * nc + c]);
+                if (rd == 1 || t < ms) ms = t;
+            }
+            if (e == cudaSuccess && (c == 0 || ms < best_ms)) {
+                best_ms = ms;
+                best = c;
+            }
+        }
+        for (size_t j = 0; j < t0.size(); ++j) {
+            if (t0[j]) cudaEventDestroy(t0[j]);
+            if (t1[j]) cudaEventDestroy(t1[j]);
+        }
+        if (done_b) cudaEventDestroy(done_b);
+        if (ts) cudaStreamDestroy(ts);
+        if (e == cudaSuccess) kx_stream_pin(k, 1, 1, B, cand[best]);
+        for (int c = 0; c < nc; ++c)
+            for (int b = 0; b < B; ++b) {
+                const size_t j = (size_t)c * B + b;
+                if (c == best && e == cudaSuccess) {
+                    graph[b] = gx[j];
+                    exec[b] = xx[j];
+                } else {
+                    if (xx[j]) cudaGraphExecDestroy(xx[j]);
+                    if (gx[j]) cudaGraphDestroy(gx[j]);
+                }
+            }
+    }
     const long long max_launch = (long long)par->max_attempts / G + 2;
     const double wall_limit = 600.0;
     const bool fault_timeout = kx_fault("timeout");

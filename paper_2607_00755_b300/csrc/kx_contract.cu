@@ -1767,7 +1767,7 @@ static std::map<std::tuple<int, int, int, int>, int> g_tuned;
 // the keys whose choice a solve's in-place tuning made or the caller pinned
 // (a solve re-tunes a choice the stand-in timing made)
 static std::set<std::tuple<int, int, int, int>> g_tuned_firm;
-static int kx_gd(int grid_div) { return grid_div > 1 ? grid_div : 1; }
+static int kx_gd(int grid_div, int tag = 0) { return (grid_div > 1 ? grid_div : 1) + 1000 * tag; }
 
 static void kx_stream_candidates(const kx_kernel *k, int B, int grid_div, int *cand, int *nc) {
     *nc = 0;
@@ -1785,11 +1785,11 @@ static int kx_stream_default(const kx_kernel *k, int B) {
     return B >= 4 ? 2 : (B >= 2 ? 1 : 0);
 }
 
-static int kx_stream_variant(const kx_kernel *k, int B, int grid_div) {
+static int kx_stream_variant(const kx_kernel *k, int B, int grid_div, int tag) {
     int dev = 0;
     cudaGetDevice(&dev);
     std::lock_guard<std::mutex> lock(g_tune_mu);
-    auto it = g_tuned.find(std::make_tuple(dev, k->n, B, kx_gd(grid_div)));
+    auto it = g_tuned.find(std::make_tuple(dev, k->n, B, kx_gd(grid_div, tag)));
     return it != g_tuned.end() ? it->second : kx_stream_default(k, B);
 }
 
@@ -1844,7 +1844,7 @@ int kx_tune_contraction(const kx_kernel *k, int B, const double *f, const kx_bat
     if (k->precision != KX_FP32 || k->stats) return 0;   // quantum statistics: one variant
     int dev = 0;
     cudaGetDevice(&dev);
-    const auto key = std::make_tuple(dev, k->n, B, kx_gd(v.grid_div));
+    const auto key = std::make_tuple(dev, k->n, B, kx_gd(v.grid_div, v.tune_tag));
     {
         std::lock_guard<std::mutex> lock(g_tune_mu);
         if (g_tuned.count(key)) return 0;
@@ -1907,17 +1907,17 @@ int kx_stream_candidate_list(const kx_kernel *k, int B, int grid_div, int *cand)
     kx_stream_candidates(k, B, grid_div, cand, &nc);
     return nc;
 }
-bool kx_stream_is_tuned(const kx_kernel *k, int B, int grid_div) {
+bool kx_stream_is_tuned(const kx_kernel *k, int B, int grid_div, int tag) {
     int dev = 0;
     cudaGetDevice(&dev);
     std::lock_guard<std::mutex> lock(g_tune_mu);
-    return g_tuned_firm.count(std::make_tuple(dev, k->n, B, kx_gd(grid_div))) != 0;
+    return g_tuned_firm.count(std::make_tuple(dev, k->n, B, kx_gd(grid_div, tag))) != 0;
 }
-void kx_stream_pin(const kx_kernel *k, int B, int grid_div, int variant) {
+void kx_stream_pin(const kx_kernel *k, int B, int grid_div, int tag, int variant) {
     int dev = 0;
     cudaGetDevice(&dev);
     std::lock_guard<std::mutex> lock(g_tune_mu);
-    const auto key = std::make_tuple(dev, k->n, B, kx_gd(grid_div));
+    const auto key = std::make_tuple(dev, k->n, B, kx_gd(grid_div, tag));
     g_tuned[key] = variant;
     g_tuned_firm.insert(key);
 }
@@ -1941,18 +1941,19 @@ extern "C" int kx_set_stream_variant(kx_ctx *ctx, int n, int batch, int variant)
     if (variant == 2 && (vpl != 4 || batch < 4)) return KX_EINVAL;
     if (variant == 3 && batch < 4) return KX_EINVAL;
     if (variant == 4 && batch > 4) return KX_EINVAL;
-    // pinned (or forgotten) for every grid share
+    // pinned (or forgotten) for every grid share and solve-chain count
     std::lock_guard<std::mutex> lock(g_tune_mu);
-    for (int gd = 1; gd <= 16; ++gd) {
-        const auto key = std::make_tuple(ctx->device, n, batch, gd);
-        if (variant < 0) {
-            g_tuned.erase(key);
-            g_tuned_firm.erase(key);
-        } else {
-            g_tuned[key] = variant;
-            g_tuned_firm.insert(key);
+    for (int tag = 0; tag <= 8; ++tag)
+        for (int gd = 1; gd <= 16; ++gd) {
+            const auto key = std::make_tuple(ctx->device, n, batch, kx_gd(gd, tag));
+            if (variant < 0) {
+                g_tuned.erase(key);
+                g_tuned_firm.erase(key);
+            } else {
+                g_tuned[key] = variant;
+                g_tuned_firm.insert(key);
+            }
         }
-    }
     return KX_OK;
 }
 
@@ -1969,7 +1970,7 @@ cudaError_t kx_launch_contract(const kx_kernel *k, int B, const double *f, const
     // the variant tuned for this size and batch (or the default rule)
     // (only the streaming kernels wait for their predecessor: the other paths'
     // contractions always launch in full stream order)
-    return kx_stream_launch(kx_stream_variant(k, B, v.grid_div), k, B, v, st, stage, s, pdl);
+    return kx_stream_launch(kx_stream_variant(k, B, v.grid_div, v.tune_tag), k, B, v, st, stage, s, pdl);
 }
 
 // ---------------------------------------------------- row combine + projection

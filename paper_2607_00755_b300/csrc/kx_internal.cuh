@@ -222,6 +222,8 @@ struct kx_batch_views {
     float *tlam;           // FP32 path with quantum statistics: [B][n] lambda_j = log2(1 + eta f_j)
     int eta;               // quantum statistics of the kernel: 0 dilute, +1 BE, -1 FD
     int grid_div;          // FP32 streaming launches use 1/grid_div of the resident blocks
+    int tune_tag;          // FP32 streaming variant choice: 0, or the number of concurrent
+                           // solve chains the launch runs beside (a separate tuning key)
                            // (1: the whole GPU; the server shares it among its groups)
     double2 *partial;      // [B][n][chunks]  (FP32 path: float2 (hi, lo) task partials, [B][chunks])
     const int2 *rtask;     // FP32 path: [n] (first partial slot i, tasks) per row; slot k at k n + i
@@ -286,8 +288,8 @@ int kx_tune_contraction(const kx_kernel *k, int B, const double *f, const kx_bat
 // to choose), whether its (device, n, batch, grid share) has a choice, and
 // pinning one for later launches and captures.
 int kx_stream_candidate_list(const kx_kernel *k, int B, int grid_div, int *cand);
-bool kx_stream_is_tuned(const kx_kernel *k, int B, int grid_div);
-void kx_stream_pin(const kx_kernel *k, int B, int grid_div, int variant);
+bool kx_stream_is_tuned(const kx_kernel *k, int B, int grid_div, int tag);
+void kx_stream_pin(const kx_kernel *k, int B, int grid_div, int tag, int variant);
 // pdl: launch with programmatic stream serialization where the kernel supports
 // it (the FP32 streaming contraction and the stage kernel wait for their
 // predecessor inside; other kernels launch in full stream order).
