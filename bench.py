@@ -41,14 +41,14 @@ CSRC = os.path.join(ROOT, "paper_2607_00755_b300", "csrc")
 # and its source file is unchanged; otherwise the line's traffic is null and
 # says why.
 NCU_TRAFFIC = {
-    "stream_n128_b4": {"kernel": "k_stream32r<1,2>", "stream_bytes": None, "file": "kx_contract.cu",
-                       "sha1": None, "bytes": None},
-    "stream_n384": {"kernel": "k_stream32r<1,4>", "stream_bytes": None, "file": "kx_contract.cu",
-                    "sha1": None, "bytes": None},
-    "stream_n512": {"kernel": "k_stream32r<1,4>", "stream_bytes": None, "file": "kx_contract.cu",
-                    "sha1": None, "bytes": None},
-    "stage_n128_b4": {"kernel": "k_stage<1,0>", "stream_bytes": None, "file": "kx_contract.cu",
-                      "sha1": None, "bytes": None},
+    "stream_n128_b1": {"kernel": "k_stream32r<1,2>", "stream_bytes": 6755176, "file": "kx_contract.cu",
+                       "sha1": "5cc2a5762c13b70f75dbcadda59c8902d6ac4a28", "bytes": 6769920.0},
+    "stream_n384": {"kernel": "k_stream32r<1,4>", "stream_bytes": 172449208, "file": "kx_contract.cu",
+                    "sha1": "5cc2a5762c13b70f75dbcadda59c8902d6ac4a28", "bytes": 172478976.0 + 2655232.0},
+    "stream_n512": {"kernel": "k_stream32r<1,4>", "stream_bytes": 406086712, "file": "kx_contract.cu",
+                    "sha1": "5cc2a5762c13b70f75dbcadda59c8902d6ac4a28", "bytes": 406124544.0 + 2694400.0},
+    "stage_n128_b1": {"kernel": "k_stage<1,0>", "stream_bytes": None, "file": "kx_contract.cu",
+                      "sha1": "5cc2a5762c13b70f75dbcadda59c8902d6ac4a28", "bytes": 0.5 * (124672.0 + 122368.0)},
 }
 
 
@@ -203,14 +203,14 @@ def run_reference(args, rank):
 
 
 def run_contraction_only(args):
-    """Contraction kernel alone on an n-point grid (q in [1e-3, 1e2]) for
+    """Contraction kernel alone on an n-point grid (q in [1e-3, qmax]) for
     `batch` seeded bimodal distributions: cold L2 before every launch, or with
     --rotate R, R kernels of the grid whose contractions run back to back in
     rotation (each launch reads its tables from HBM when R x tables > L2)."""
     import torch
     import paper_2607_00755_b300 as kx
     ctx = kx.Context(0)
-    q = ki.log_grid(args.n, 1e-3, 1e2)
+    q = ki.log_grid(args.n, 1e-3, args.qmax)
     prec = {"fp32": kx.FP32, "fp64": kx.FP64, "split": kx.SPLIT_TF32}[args.precision]
     ks = [ctx.build_kernel(q, precision=prec) for _ in range(max(1, args.rotate))]
     k = ks[0]
@@ -586,6 +586,8 @@ def main():
                     help="contraction: time the contraction kernel alone; step: run the "
                          "workload's steps only (no baselines), for profiling")
     ap.add_argument("--n", type=int, default=384)
+    ap.add_argument("--qmax", type=float, default=1e2,
+                    help="--only contraction: the grid's largest q/m (the N=128 workload uses 10)")
     ap.add_argument("--batch", type=int, default=1)
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64", "split"])
     ap.add_argument("--iters", type=int, default=20)
@@ -599,6 +601,8 @@ def main():
                     help="serving: the first R requests of the 2000-request stream")
     ap.add_argument("--no-serving", action="store_true",
                     help="skip the uneven-batch and serving measurements")
+    ap.add_argument("--no-split-tuning", action="store_true",
+                    help="split path: the default launch choices, not timed ones (for profiling)")
     ap.add_argument("--paper-runtime", action="store_true",
                     help="also re-time the paper's own runtime figure (one evaluation vs N, "
                          "Bose-Einstein factors; context only)")
@@ -614,6 +618,8 @@ def main():
         import torch
         import paper_2607_00755_b300 as kx
         ctx = kx.Context(0)
+        if args.no_split_tuning:
+            ctx.set_split_tuning(False)
         if args.only == "batched":
             flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
             r = measure_batched(ctx, kx, torch, flush)[0]
@@ -717,19 +723,22 @@ def main():
                 "solves_per_s": B * args.fp64_steps / (t64 / 1e3)}
 
     # ---- rooflines of the step's two kernels, timed live --------------------
-    # kx_profile_attempts runs real Heun attempts of the workload with CUDA
-    # events between the contraction and the stage kernels (plain stream order:
-    # each time includes the kernel's launch and its wait on the predecessor),
-    # the FP64 and ex2 peaks come from the library's throughput kernels in this
-    # run (FP64: FMA = 2 flops)
+    # The solve runs the four instances as concurrent chains (one instance per
+    # launch).  kx_profile_attempts runs real Heun attempts of one chain (the
+    # longest, sigma = 0.1) with CUDA events between its contraction and stage
+    # kernels (plain stream order: each time includes the kernel's launch and
+    # its wait on the predecessor, and no other chain runs beside it); the FP64
+    # and ex2 peaks come from the library's throughput kernels in this run
+    # (FP64: FMA = 2 flops)
     hbm, src_peak = peaks()
     fp64_peak, ex2_peak = ctx.measure_peaks()
     kk = ctx.build_kernel(q, precision=kx.FP32)
-    fprof = torch.as_tensor(f0, device="cuda")
-    prof = ctx.profile_attempts(kk, fprof, sig, sources=src, attempts=400, **par)
+    Bp = 1
+    fprof = torch.as_tensor(f0[:Bp], device="cuda")
+    prof = ctx.profile_attempts(kk, fprof, sig[:Bp], sources=src, attempts=400, **par)
     info = kk.info()
     alg_bytes = info["stream_bytes"]
-    kname = stream_kernel_name(ctx, 128, B)
+    kname = stream_kernel_name(ctx, 128, Bp)
     us_k = 0.5 * (prof["contraction_1_us"] + prof["contraction_2_us"])
     us_s = 0.5 * (prof["stage_1_us"] + prof["stage_2_us"])
     ms_cold = ctx.time_contraction(kk, torch.as_tensor(f0, device="cuda"), iters=30,
@@ -739,33 +748,33 @@ def main():
     # contraction: the method's one exponential per kept element and instance (the
     # interpolated f_t); the kernel evaluates two ex2 per element (the
     # 2^a (1 - 2^d) form)
-    elem = info["nonzero_elements"] * B
-    tr_k, tr_k_note = traffic_for("stream_n128_b4", kname.split(" ")[0], alg_bytes)
+    elem = info["nonzero_elements"] * Bp
+    tr_k, tr_k_note = traffic_for("stream_n128_b1", kname.split(" ")[0], alg_bytes)
     roof_k = {"bound": "alu", "pipe": "MUFU (ex2)", "achieved": elem / (us_k * 1e-6) / 1e12,
               "peak": ex2_peak / 1e12, "unit": "Tex2/s", "frac": elem / (us_k * 1e-6) / ex2_peak,
               "traffic": tr_k, "traffic_note": tr_k_note,
-              "kernel": f"N=128, {B} instances: {kname}", "elements_per_launch": elem,
+              "kernel": f"N=128, one chain (1 instance): {kname}", "elements_per_launch": elem,
               "avg_launch_us": us_k, "avg_launch_ms_isolated_cold_l2": ms_cold,
               "algorithmic_bytes_per_launch": alg_bytes,
               "l2_resident": "the tables (%.1f MB) stay in the 126 MB L2 during the solve" % (alg_bytes / 1e6),
               "issued_frac": 2 * elem / (us_k * 1e-6) / ex2_peak,
               "note": "latency and issue bound at this size: each warp streams 2-3 units of its "
                       "bins after loading the instance tables written by the previous stage"}
-    flop_s = B * n * 0.5 * (STAGE_FLOP_PER_POINT[1] + STAGE_FLOP_PER_POINT[2])
-    tr_s, tr_s_note = traffic_for("stage_n128_b4", "k_stage<1,0>")
+    flop_s = Bp * n * 0.5 * (STAGE_FLOP_PER_POINT[1] + STAGE_FLOP_PER_POINT[2])
+    tr_s, tr_s_note = traffic_for("stage_n128_b1", "k_stage<1,0>")
     roof_s = {"bound": "alu", "pipe": "FP64", "achieved": flop_s / (us_s * 1e-6) / 1e9,
               "peak": fp64_peak / 1e9, "unit": "GFLOP/s", "frac": flop_s / (us_s * 1e-6) / fp64_peak,
               "traffic": tr_s, "traffic_note": tr_s_note,
-              "kernel": f"k_stage<1,0>: one block per instance ({B} blocks), row combine, projection, "
-                        "Heun stage, MB check, next tables",
+              "kernel": "k_stage<1,0>: one block per instance (one chain: 1 block), row combine, "
+                        "projection, Heun stage, MB check, next tables",
               "flop_per_launch": flop_s, "avg_launch_us": us_s,
-              "frac_of_the_sms_it_occupies": flop_s / (us_s * 1e-6) / (fp64_peak * B / 148.0),
+              "frac_of_the_sms_it_occupies": flop_s / (us_s * 1e-6) / (fp64_peak * Bp / 148.0),
               "note": "latency bound: a dependent chain of FP64 operations and block reductions "
                       "per instance on one SM each"}
     dominant = "stage" if us_s >= us_k else "contraction"
     roof = dict(roof_s if dominant == "stage" else roof_k)
     roof["dominant"] = (f"{dominant}: {max(us_s, us_k):.2f} us of the {us_s + us_k:.2f} us of the "
-                        "two kernels per Heun stage (kx_profile_attempts, 400 attempts)")
+                        "two kernels per Heun stage of one chain (kx_profile_attempts, 400 attempts)")
     roof["peak_source"] = "measured in this run (the library's DFMA / ex2 throughput kernels)"
     roof_other = roof_k if dominant == "stage" else roof_s
     roof_other["peak_source"] = roof["peak_source"]
