@@ -265,6 +265,10 @@ def measure_batched(ctx, kx, torch, flush, iters=5, check_sample=4):
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     Cs = {}
     peak, peak_src = tf32_peak()
+    # the raw tcgen05 kind::tf32 issue rate at this N tile (library microbenchmark),
+    # at the SM clock's maximum, for context beside the contract's peak
+    fpc, cyc = ctx.measure_mma_rate(0, n)
+    mma_rate = fpc * 148 * 2.032e9 / 1e12
     P = n * (n + 1) // 2
     for name, prec, lt, reps in (("split_tf32_exact_loss", kx.SPLIT_TF32, 0, iters),
                                  ("split_tf32_cheb16_loss", kx.SPLIT_TF32, 16, iters),
@@ -290,6 +294,11 @@ def measure_batched(ctx, kx, torch, flush, iters=5, check_sample=4):
                         "issued_tflops_split3": 3 * useful / (ms * 1e-3) / 1e12,
                         "frac_of_tf32_peak_issued": 3 * useful / (ms * 1e-3) / 1e12 / peak,
                         "tf32_peak_tflops": peak, "peak_source": peak_src,
+                        "tf32_mma_issue_rate_tflops": mma_rate,
+                        "frac_of_mma_issue_rate": 3 * useful / (ms * 1e-3) / 1e12 / mma_rate,
+                        "mma_issue_rate_note": (f"tcgen05.mma kind::tf32 M=128 N={n} K=8 back to back from "
+                                                f"shared memory: {cyc:.1f} cycles each, {fpc:.0f} FLOP/clk/SM, "
+                                                "x 148 SMs x 2.032 GHz"),
                         "note": "whole kx_collision call (prep, both GEMMs or the exact loss, "
                                 "row combine and projection), cold L2",
                         "launch_choices": ctx.split_tuning(k, B)})

@@ -507,6 +507,15 @@ int kx_check_probe(kx_ctx *ctx, int index, int limit, int *result);
  * for null arguments, KX_ECUDA on a CUDA error. */
 int kx_measure_peaks(kx_ctx *ctx, double *fp64_flops, double *ex2_per_s);
 
+/* Tensor-core issue rate (a diagnostic for the batched path's roofline, no
+ * counterpart in the paper): one thread per SM issues 4096 tcgen05.mma of
+ * M = 128, N = n (16 .. 256, a multiple of 16), K = 8 with TF32 operands (kind
+ * 0) or K = 16 with BF16 operands (kind 1) from shared-memory tiles into tensor
+ * memory and waits for them; writes the FLOP per clock per SM and the cycles
+ * per MMA (host pointers).  Synchronises the context's stream.  KX_EINVAL for
+ * bad arguments, KX_ECUDA on a CUDA error or an expired wait. */
+int kx_measure_mma_rate(kx_ctx *ctx, int kind, int n, double *flop_per_clk_sm, double *cycles_per_mma);
+
 /* Per-kernel timing of the solve's attempts (a diagnostic, no counterpart in
  * the paper): sets up a solve of the B instances of f_dev exactly as kx_solve
  * does (same arguments), prepares f and runs `attempts` (1 .. 100000) real

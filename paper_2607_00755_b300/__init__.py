@@ -28,7 +28,7 @@ EXPORTS = (
     "kx_solve", "kx_solve_host", "kx_mb_fit", "kx_launch_count", "kx_time_contraction",
     "kx_time_contractions", "kx_time_collision",
     "kx_collision_noalloc", "kx_server_start", "kx_submit", "kx_poll", "kx_server_get_stats",
-    "kx_server_stop", "kx_math_check", "kx_profile_attempts", "kx_measure_peaks", "kx_server_reset_latency", "kx_check_status", "kx_check_probe", "kx_set_split_tuning", "kx_get_split_tuning", "kx_wait_check", "kx_set_stream_variant", "kx_get_stream_variant",
+    "kx_server_stop", "kx_math_check", "kx_profile_attempts", "kx_measure_peaks", "kx_measure_mma_rate", "kx_server_reset_latency", "kx_check_status", "kx_check_probe", "kx_set_split_tuning", "kx_get_split_tuning", "kx_wait_check", "kx_set_stream_variant", "kx_get_stream_variant",
     "kx_source_higgs_decay", "kx_source_condensate", "kx_solve_expanding", "kx_solve_grouped",
 )
 
@@ -164,6 +164,7 @@ def _open_library(path: str):
         "kx_math_check": (i, [vp, i, i, vp, vp]),
         "kx_profile_attempts": (i, [vp, vp, i, vp, vp, i, vp, vp, i, vp]),
         "kx_measure_peaks": (i, [vp, vp, vp]),
+        "kx_measure_mma_rate": (i, [vp, i, i, vp, vp]),
         "kx_server_reset_latency": (i, [vp]),
         "kx_check_status": (i, [vp, i, vp, vp, vp, vp]),
         "kx_check_probe": (i, [vp, i, i, vp]),
@@ -359,6 +360,15 @@ class Context:
         if rc:
             raise self.error(rc, "kx_check_probe")
         return r.value
+
+    def measure_mma_rate(self, kind, n):
+        """(FLOP per clock per SM, cycles per MMA) of tcgen05.mma M=128, N=n: kind 0
+        TF32 (K = 8), kind 1 BF16 (K = 16)."""
+        a, b = ctypes.c_double(0.0), ctypes.c_double(0.0)
+        rc = self.lib.kx_measure_mma_rate(self.h, int(kind), int(n), ctypes.byref(a), ctypes.byref(b))
+        if rc:
+            raise self.error(rc, "kx_measure_mma_rate")
+        return a.value, b.value
 
     def measure_peaks(self):
         """(FP64 flop/s, ex2/s) of the device from the library's throughput kernels."""

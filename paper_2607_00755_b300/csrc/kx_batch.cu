@@ -693,6 +693,85 @@ void kx_batch_prepare() {
     cudaGetLastError();
 }
 
+// ------------------------------------------------------------ MMA issue rate
+// One thread per CTA (one CTA per SM) issues R MMAs of M = 128, N = n, K = 8
+// (kind::tf32) or 16 (kind::f16, bf16 operands) from zero tiles in shared memory
+// (the GEMMs' no-swizzle K-major layout) into a tensor-memory accumulator, commits
+// and waits (bounded); cycles of CTA 0 go to out[0], whether the wait completed to
+// out[1].
+template <int KIND>
+__global__ void __launch_bounds__(128, 1) k_mma_rate(int n, int R, long long *out) {
+    __shared__ __align__(1024) unsigned char sm[128 * 64 + 256 * 64];
+    __shared__ __align__(8) unsigned long long bar;
+    __shared__ uint32_t tslot;
+    const int tid = threadIdx.x, warp = tid >> 5;
+    for (int i = tid; i < (int)sizeof(sm) / 4; i += blockDim.x) reinterpret_cast<uint32_t *>(sm)[i] = 0u;
+    if (tid == 0) {
+        kx_mbar_init(kx_smem_u32(&bar), 1);
+        kx_fence_mbar_init();
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 256;" ::"r"(kx_smem_u32(&tslot))
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    kx_fence_proxy_async();
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = tslot;
+    if (tid == 0) {
+        const uint32_t a = kx_smem_u32(sm), b = kx_smem_u32(sm + 128 * 64);
+        // D F32; A, B tf32 (2, kind::tf32) or bf16 (1, kind::f16); K-major; N >> 3, M >> 4
+        const uint32_t fmt = KIND == 0 ? 2u : 1u;
+        const uint32_t id = (1u << 4) | (fmt << 7) | (fmt << 10) | ((uint32_t)(n >> 3) << 17) | (8u << 24);
+        const long long t0 = clock64();
+        for (int r = 0; r < R; ++r) {
+            const uint32_t acc = r > 0 ? 1u : 0u;
+            if (KIND == 0)
+                kx_mma_tf32(tmem, kx_desc(a, 128, 512), kx_desc(b, 128, 512), id, acc);
+            else
+                asm volatile("{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+                             "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem),
+                             "l"(kx_desc(a, 128, 512)), "l"(kx_desc(b, 128, 512)), "r"(id), "r"(acc)
+                             : "memory");
+        }
+        kx_mma_commit(kx_smem_u32(&bar));
+        const bool ok = kx_mbar_wait(kx_smem_u32(&bar), 0);
+        const long long t1 = clock64();
+        if (blockIdx.x == 0) {
+            out[0] = t1 - t0;
+            out[1] = ok ? 1 : 0;
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 256;" ::"r"(tmem) : "memory");
+}
+
+extern "C" int kx_measure_mma_rate(kx_ctx *ctx, int kind, int n, double *flop_per_clk_sm, double *cycles_per_mma) {
+    if (!ctx || (kind != 0 && kind != 1) || n < 16 || n > 256 || n % 16 || !flop_per_clk_sm || !cycles_per_mma)
+        return KX_EINVAL;
+    if (cudaSetDevice(ctx->device) != cudaSuccess) return KX_ECUDA;
+    int sms = 0;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ctx->device);
+    long long *d = nullptr, h[2] = {0, 0};
+    if (cudaMalloc(&d, sizeof(h)) != cudaSuccess) return KX_ENOMEM;
+    const int R = 4096;
+    if (kind == 0) k_mma_rate<0><<<sms > 0 ? sms : 148, 128, 0, ctx->stream>>>(n, R, d);
+    else k_mma_rate<1><<<sms > 0 ? sms : 148, 128, 0, ctx->stream>>>(n, R, d);
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaMemcpyAsync(h, d, sizeof(h), cudaMemcpyDeviceToHost, ctx->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    cudaFree(d);
+    ctx->launches += 1;
+    if (e != cudaSuccess || !h[1] || h[0] <= 0) return KX_ECUDA;
+    *cycles_per_mma = (double)h[0] / R;
+    *flop_per_clk_sm = 2.0 * 128 * n * (kind == 0 ? 8 : 16) / *cycles_per_mma;
+    return KX_OK;
+}
+
 // ------------------------------------------------------------ split tuner
 // The split path's result-neutral launch choices: the GEMM ring depth and the
 // f' staging (per launch shape: gain or loss, the widest grid, its i tiles,

@@ -69,3 +69,29 @@ def test_time_collision_output_is_the_collision(env, precision, stats):
         assert 0.0 < ms < 1e3
         np.testing.assert_array_equal(C.cpu().numpy(), ref.cpu().numpy())
     k.release()
+
+
+def test_diagnostic_rates_and_attempt_profile(env):
+    """kx_measure_peaks (FP64 and ex2 throughput), kx_measure_mma_rate (tcgen05
+    issue rate) and kx_profile_attempts (per-kernel times of real attempts):
+    plausible positive figures, TF32 and BF16 MMAs of one shape take the same
+    cycles (the same operand bytes), the profiled attempts advance f as a solve
+    does, and bad arguments are refused."""
+    kx, ctx, torch = env
+    fp64, ex2 = ctx.measure_peaks()
+    assert 1e11 < fp64 < 1e14 and 1e12 < ex2 < 1e14
+    f32c, c32 = ctx.measure_mma_rate(0, 128)
+    f16c, c16 = ctx.measure_mma_rate(1, 128)
+    assert 500.0 < f32c < 50000.0 and abs(f16c / f32c - 2.0) < 0.2 and abs(c16 / c32 - 1.0) < 0.1
+    with pytest.raises(kx.KxError):
+        ctx.measure_mma_rate(0, 100)
+    q = ki.log_grid(32, 1e-3, 10.0)
+    f0 = ki.batch_bimodal(np.random.default_rng(9), q, 2)
+    k = ctx.build_kernel(q, precision=kx.FP32)
+    fd = torch.as_tensor(f0, device="cuda")
+    prof = ctx.profile_attempts(k, fd, [1.0, 2.0], attempts=20, t_end=1.0, h0=1e-3)
+    assert all(0.0 < v < 1e5 for v in prof.values()) and len(prof) == 4
+    assert not np.array_equal(fd.cpu().numpy(), f0)
+    with pytest.raises(kx.KxError):
+        ctx.profile_attempts(k, fd, [1.0, 2.0], attempts=0, t_end=1.0, h0=1e-3)
+    k.release()
