@@ -407,6 +407,36 @@ def measure_config1(ctx, kx, torch, reps=5):
     return out
 
 
+def measure_grouped(ctx, kx, c, par, t_end, forms=(0, 16)):
+    """The uneven batch as one sequence of grouped launches (kx_solve_grouped:
+    per Heun stage one gain-GEMM launch, one loss launch (Chebyshev GEMM, or the
+    grids' exact loss kernels side by side) and one stage launch over all five
+    grids, captured in a graph of attempts), exact loss and Chebyshev K = 16."""
+    import torch
+    sizes = (64, 96, 128, 192, 256)
+    grouped = {}
+    for lt in forms:
+        ks = [ctx.build_kernel(c["grids"][n], precision=kx.SPLIT_TF32, loss_terms=lt) for n in sizes]
+        idx = [np.nonzero(c["ns"] == n)[0] for n in sizes]
+        fs = [torch.as_tensor(np.stack([c["f"][i] for i in ii]), device="cuda") for ii in idx]
+        sg = [c["sigma"][ii] for ii in idx]
+        gp = dict(par, t_end=t_end, h0=1e-3)
+        ctx.solve_grouped(ks, [f.clone() for f in fs], sg, **dict(gp, t_end=1e-3))   # warm
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        res = ctx.solve_grouped(ks, fs, sg, **gp)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        done = sum(1 for r in res for x in r if x["status"] == 0)
+        evals = sum(x["evals"] for r in res for x in r)
+        grouped["cheb16" if lt else "exact_loss"] = {
+            "instances": len(c["ns"]), "completed": done, "seconds": dt, "solves_per_s": done / dt,
+            "evals_per_s": evals / dt, "evals": evals}
+        for k in ks:
+            k.release()
+    return grouped
+
+
 def measure_uneven(ctx, kx, t_end=5.0, fp64_per_size=4):
     """Uneven batch: 1024 instances with N uniform over {64, 96, 128, 192, 256},
     sigma log-uniform over [1e-3, 1], 5 shared kernel tensors, all admitted at once
@@ -446,31 +476,7 @@ def measure_uneven(ctx, kx, t_end=5.0, fp64_per_size=4):
         out[name] = {"instances": len(tickets), "completed": ok, "seconds": dt,
                      "solves_per_s": ok / dt, "evals_per_s": evals / dt, "evals": evals,
                      "kernel_build_s": t_build}
-    # the same 1024 instances as one sequence of grouped launches (kx_solve_grouped:
-    # per Heun stage one gain-GEMM, one loss launch and one stage launch over all
-    # five grids, captured in a graph of attempts), exact loss and Chebyshev K = 16
-    import torch
-    sizes = (64, 96, 128, 192, 256)
-    grouped = {}
-    for lt in (0, 16):
-        ks = [ctx.build_kernel(c["grids"][n], precision=kx.SPLIT_TF32, loss_terms=lt) for n in sizes]
-        idx = [np.nonzero(c["ns"] == n)[0] for n in sizes]
-        fs = [torch.as_tensor(np.stack([c["f"][i] for i in ii]), device="cuda") for ii in idx]
-        sg = [c["sigma"][ii] for ii in idx]
-        gp = dict(par, t_end=t_end, h0=1e-3)
-        ctx.solve_grouped(ks, [f.clone() for f in fs], sg, **dict(gp, t_end=1e-3))   # warm
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        res = ctx.solve_grouped(ks, fs, sg, **gp)
-        torch.cuda.synchronize()
-        dt = time.perf_counter() - t0
-        done = sum(1 for r in res for x in r if x["status"] == 0)
-        evals = sum(x["evals"] for r in res for x in r)
-        grouped["cheb16" if lt else "exact_loss"] = {
-            "instances": len(c["ns"]), "completed": done, "seconds": dt, "solves_per_s": done / dt,
-            "evals_per_s": evals / dt, "evals": evals}
-        for k in ks:
-            k.release()
+    grouped = measure_grouped(ctx, kx, c, par, t_end)
     return {"workload": "1024 instances, N uniform over {64,96,128,192,256}, sigma logU[1e-3,1], "
                         f"no sources, each integrated to t={t_end}; all admitted at once",
             "split_tf32": out["split_tf32"], "fp64_path_sample": out["fp64"],
@@ -591,7 +597,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--fp64-steps", type=int, default=1)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--only", default="", choices=["", "contraction", "step", "uneven", "serving", "batched"],
+    ap.add_argument("--only", default="", choices=["", "contraction", "step", "uneven", "serving", "batched",
+                                                   "grouped"],
                     help="contraction: time the contraction kernel alone; step: run the "
                          "workload's steps only (no baselines), for profiling")
     ap.add_argument("--n", type=int, default=384)
@@ -623,7 +630,7 @@ def main():
         return run_reference(args, rank)
     if args.only == "contraction":
         return run_contraction_only(args)
-    if args.only in ("uneven", "serving", "batched"):
+    if args.only in ("uneven", "serving", "batched", "grouped"):
         import torch
         import paper_2607_00755_b300 as kx
         ctx = kx.Context(0)
@@ -632,6 +639,9 @@ def main():
         if args.only == "batched":
             flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
             r = measure_batched(ctx, kx, torch, flush)[0]
+        elif args.only == "grouped":
+            r = measure_grouped(ctx, kx, ki.config4(), dict(rtol=1e-6, atol=1e-12, l1_tol=0.0, check_every=10,
+                                                            max_attempts=1_000_000), 5.0)
         else:
             r = measure_uneven(ctx, kx) if args.only == "uneven" else measure_serving(
                 ctx, kx, requests=args.requests)

@@ -1447,12 +1447,31 @@ extern "C" int kx_solve_grouped(kx_ctx *ctx, int G, const kx_kernel *const *ks, 
     // one timeout flag for the grouped launches, seen by every group's stage
     int *d_err = runs[0].v.err;
     for (int g = 1; g < G; ++g) runs[g].v.err = d_err;
+    // side streams and events: the grids' exact loss kernels run side by side
+    // (forked and joined inside the captured graph)
+    struct side_t {
+        std::vector<cudaStream_t> st;
+        std::vector<cudaEvent_t> ev;
+        ~side_t() {
+            for (auto x : st)
+                if (x) cudaStreamDestroy(x);
+            for (auto x : ev)
+                if (x) cudaEventDestroy(x);
+        }
+    } side;
+    if (G > 1) {
+        side.st.assign(G, nullptr);
+        side.ev.assign(G + 1, nullptr);
+        for (int g = 0; g < G; ++g) KX_CUDA_TRY(ctx, cudaStreamCreateWithFlags(&side.st[g], cudaStreamNonBlocking));
+        for (int g = 0; g <= G; ++g) KX_CUDA_TRY(ctx, cudaEventCreateWithFlags(&side.ev[g], cudaEventDisableTiming));
+    }
     auto attempt = [&](cudaStream_t cs) -> cudaError_t {
         cudaError_t e = cudaSuccess;
         for (int stage = 1; stage <= 2 && e == cudaSuccess; ++stage) {
             // the contraction's input: f (stage 1) or the predictor f_p (stage 2),
             // prepared by the previous stage kernel
-            e = kx_launch_batch_contract_grouped(G, ks, B, vs.data(), sts.data(), stage, d_err, cs);
+            e = kx_launch_batch_contract_grouped(G, ks, B, vs.data(), sts.data(), stage, d_err, cs,
+                                                 G > 1 ? side.st.data() : nullptr, G > 1 ? side.ev.data() : nullptr);
             if (e == cudaSuccess) e = kx_launch_stage_grouped(G, ks, B, vs.data(), svs.data(), stage, cs);
         }
         return e;

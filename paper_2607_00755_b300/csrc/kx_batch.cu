@@ -1033,10 +1033,23 @@ cudaError_t kx_launch_batch_contract(const kx_kernel *k, int B, const kx_batch_v
 // and one loss-GEMM launch over all their work items; the exact loss per kernel.
 cudaError_t kx_launch_batch_contract_grouped(int G, const kx_kernel *const *ks, const int *B,
                                              const kx_batch_views *const *vs, const kx_inst_state *const *sts,
-                                             int stage, int *d_err, cudaStream_t s) {
+                                             int stage, int *d_err, cudaStream_t s, const cudaStream_t *side,
+                                             const cudaEvent_t *ev) {
     cudaError_t e = kx_launch_split_gemm(true, G, ks, vs, d_err, s);
     if (e == cudaSuccess) e = kx_launch_split_gemm(false, G, ks, vs, d_err, s);
-    for (int g = 0; g < G && e == cudaSuccess; ++g) e = kx_launch_batch_loss(ks[g], B[g], *vs[g], sts[g], stage, s);
+    if (!side || !ev) {
+        for (int g = 0; g < G && e == cudaSuccess; ++g) e = kx_launch_batch_loss(ks[g], B[g], *vs[g], sts[g], stage, s);
+        return e;
+    }
+    // the exact loss kernels of the G grids side by side: forked from s after the
+    // GEMMs (ev[0]) onto the side streams and joined back (ev[1 + g])
+    if (e == cudaSuccess) e = cudaEventRecord(ev[0], s);
+    for (int g = 0; g < G && e == cudaSuccess; ++g) {
+        e = cudaStreamWaitEvent(side[g], ev[0], 0);
+        if (e == cudaSuccess) e = kx_launch_batch_loss(ks[g], B[g], *vs[g], sts[g], stage, side[g]);
+        if (e == cudaSuccess) e = cudaEventRecord(ev[1 + g], side[g]);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(s, ev[1 + g], 0);
+    }
     return e;
 }
 

@@ -341,7 +341,8 @@ void kx_batch_prepare();   // one-time kernel attribute setup (outside stream ca
 // one loss-GEMM launch over all their work items, the exact loss per kernel
 cudaError_t kx_launch_batch_contract_grouped(int G, const kx_kernel *const *ks, const int *B,
                                              const kx_batch_views *const *vs, const kx_inst_state *const *sts,
-                                             int stage, int *d_err, cudaStream_t s);
+                                             int stage, int *d_err, cudaStream_t s, const cudaStream_t *side = nullptr,
+                                             const cudaEvent_t *ev = nullptr);
 // grouped stage: one launch over the instances of G kernels (block = instance,
 // threads = the largest grid of the group rounded up to whole warps)
 cudaError_t kx_launch_stage_grouped(int G, const kx_kernel *const *ks, const int *B,
