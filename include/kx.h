@@ -466,20 +466,26 @@ int kx_source_condensate(int n, const double *q, double a, double mass, double m
 
 /* ----------------------------------------------------------- diagnostics */
 /* The split-TF32 path's launch choices (no counterpart in the paper): the
- * gain and Chebyshev-loss GEMMs' ring depth and f' staging, per launch shape,
- * and the exact loss kernel's instances per lane, per (n, batch).  None of
+ * gain and Chebyshev-loss GEMMs' ring depth and f' staging, the gain's A
+ * operand (the generated f'_n f'_m tile) in tensor or shared memory, per
+ * launch shape, and the exact loss kernel's instances per lane, per
+ * (n, batch).  None of
  * them changes a result; each is timed on the launch's own operands the first
  * time the shape is launched outside a stream capture and kept for the
  * process.  kx_set_split_tuning(0) switches the timing off and forgets the
  * choices (the default rule applies), 1 switches it on.  kx_get_split_tuning
  * reports the choices a whole-batch launch of kernel k with B instances uses:
  * *gain_S, *gain_fs (1: f' staged), *loss_S (0 without the Chebyshev loss),
- * *loss_ipl, and *tuned (bit 0 gain, bit 1 Chebyshev loss, bit 2 exact loss:
- * timed rather than the rule).  KX_EINVAL for bad arguments, KX_ENOTSUP for a
- * kernel of another path. */
+ * *loss_ipl, *tuned (bit 0 gain, bit 1 Chebyshev loss, bit 2 exact loss:
+ * timed rather than the rule) and *gain_atm (1: A in tensor memory).
+ * kx_set_gain_operand(where) restricts the gain's A operand for later
+ * launches (and forgets the timed GEMM choices): 0 either (the default; the
+ * rule takes tensor memory), 1 shared memory only, 2 tensor memory only.
+ * KX_EINVAL for bad arguments, KX_ENOTSUP for a kernel of another path. */
 int kx_set_split_tuning(int enabled);
+int kx_set_gain_operand(int where);
 int kx_get_split_tuning(const kx_kernel *k, int B, int *gain_S, int *gain_fs, int *loss_S, int *loss_ipl,
-                        int *tuned);
+                        int *tuned, int *gain_atm);
 
 /* Bounds-checked build (no counterpart in the paper): libkx_check.so is this
  * library compiled with -DKX_CHECK.  Its contraction and loss kernels test

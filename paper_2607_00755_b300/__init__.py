@@ -28,7 +28,7 @@ EXPORTS = (
     "kx_solve", "kx_solve_host", "kx_mb_fit", "kx_launch_count", "kx_time_contraction",
     "kx_time_contractions", "kx_time_collision",
     "kx_collision_noalloc", "kx_server_start", "kx_submit", "kx_poll", "kx_server_get_stats",
-    "kx_server_stop", "kx_math_check", "kx_profile_attempts", "kx_measure_peaks", "kx_measure_mma_rate", "kx_server_reset_latency", "kx_check_status", "kx_check_probe", "kx_set_split_tuning", "kx_get_split_tuning", "kx_wait_check", "kx_set_stream_variant", "kx_get_stream_variant",
+    "kx_server_stop", "kx_math_check", "kx_profile_attempts", "kx_measure_peaks", "kx_measure_mma_rate", "kx_server_reset_latency", "kx_check_status", "kx_check_probe", "kx_set_split_tuning", "kx_set_gain_operand", "kx_get_split_tuning", "kx_wait_check", "kx_set_stream_variant", "kx_get_stream_variant",
     "kx_source_higgs_decay", "kx_source_condensate", "kx_solve_expanding", "kx_solve_grouped",
 )
 
@@ -169,7 +169,8 @@ def _open_library(path: str):
         "kx_check_status": (i, [vp, i, vp, vp, vp, vp]),
         "kx_check_probe": (i, [vp, i, i, vp]),
         "kx_set_split_tuning": (i, [i]),
-        "kx_get_split_tuning": (i, [vp, i, vp, vp, vp, vp, vp]),
+        "kx_get_split_tuning": (i, [vp, i, vp, vp, vp, vp, vp, vp]),
+        "kx_set_gain_operand": (i, [i]),
         "kx_wait_check": (i, [vp, ctypes.c_longlong, vp]),
         "kx_set_stream_variant": (i, [vp, i, i, i]),
         "kx_get_stream_variant": (i, [vp, i, i, vp, vp]),
@@ -335,12 +336,19 @@ class Context:
 
     def split_tuning(self, kernel, batch):
         """The split path's launch choices for kernel and batch (kx_get_split_tuning)."""
-        v = [ctypes.c_int(0) for _ in range(5)]
+        v = [ctypes.c_int(0) for _ in range(6)]
         rc = self.lib.kx_get_split_tuning(kernel.h, int(batch), *[ctypes.byref(x) for x in v])
         if rc:
             raise self.error(rc, "kx_get_split_tuning")
         return {"gain_S": v[0].value, "gain_fs": v[1].value, "loss_S": v[2].value, "loss_ipl": v[3].value,
-                "tuned": v[4].value}
+                "tuned": v[4].value, "gain_atm": v[5].value}
+
+    def set_gain_operand(self, where):
+        """Where the split path's gain GEMM keeps its generated A operand
+        (kx_set_gain_operand): "any", "shared" or "tensor"."""
+        rc = self.lib.kx_set_gain_operand({"any": 0, "shared": 1, "tensor": 2}[where])
+        if rc:
+            raise self.error(rc, "kx_set_gain_operand")
 
     def check_status(self, reset=False):
         """Bounds-check record (kx_check_status): checked build?, failures,

@@ -53,6 +53,24 @@ __device__ __forceinline__ void kx_mma_tf32(uint32_t tmem, uint64_t a, uint64_t 
         "l"(a), "l"(b), "r"(idesc), "r"(accumulate)
         : "memory");
 }
+// The same MMA with the A operand (M rows x 8 TF32 of k, row m in lane m, k in
+// consecutive columns) read from tensor memory at column address ta.
+__device__ __forceinline__ void kx_mma_tf32_at(uint32_t tmem, uint32_t ta, uint64_t b, uint32_t idesc,
+                                               uint32_t accumulate) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::tf32 [%0], [%1], %2, %3, p;\n\t}" ::"r"(tmem),
+        "r"(ta), "l"(b), "r"(idesc), "r"(accumulate)
+        : "memory");
+}
+// Eight consecutive 32-bit columns of this thread's lane (the warp's lane
+// quarter) from registers; completion is awaited with tcgen05.wait::st.
+__device__ __forceinline__ void kx_tmem_st8(uint32_t taddr, const uint32_t *v) {
+    asm volatile("tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};" ::"r"(taddr), "r"(v[0]),
+                 "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(v[4]), "r"(v[5]), "r"(v[6]), "r"(v[7])
+                 : "memory");
+}
 __device__ __forceinline__ void kx_mma_commit(uint32_t bar) {
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
                  : "memory");
@@ -166,26 +184,85 @@ __device__ __forceinline__ int kx_sg_find(const kx_sg_list &L, int w) {
     return g;
 }
 
-// Shared-memory plan of a split GEMM: S stages of A (hi, lo: 2 x 8 KB) and B
-// (hi, lo: 2 x nsb x 4 KB, nsb = 64-row i tiles of the widest i tile); for the
-// gain with n <= 256 also the f' block of the item's 128 instances (fs[n][128],
-// one bulk copy) that the generating warps read instead of global memory.
+// Shared- and tensor-memory plan of a split GEMM.  Shared memory: S stages of
+// B (hi, lo: 2 x nsb x 4 KB, nsb = 64-row i tiles of the widest i tile), plus A
+// (hi, lo: 2 x 8 KB) unless A sits in tensor memory; for the gain with n <= 256
+// also the f' block of the item's 128 instances (fs[n][128], one bulk copy)
+// that the generating warps read instead of global memory.  Tensor memory
+// (ncols columns): nbuf accumulators of up to `half` columns at columns
+// 0 and half, and with atm (the gain only) the S stages of the generated A
+// operand, 32 columns each (16 k of hi, 16 of lo; lane = instance row), stage
+// q at column a0 + (q / 2) a2 + (q % 2) 32.
+// The epilogue's staging rows (ew = 32 or 16 columns, 0: none): each epilogue
+// warp passes its 32 rows x ew accumulator columns through shared memory
+// (rows padded to ew + 4 floats) so that its global stores are whole row
+// segments of ew floats, eight or four lanes per row, instead of one 16-byte
+// piece per lane in 32 rows.
 struct kx_sg_plan {
-    int S, nsb, stage, fs, smem;
+    int S, nsb, stage, aoff, fs, eb, ew, smem, atm, ncols, half, nbuf, a0, a2;
 };
-// req_S: the ring depth wanted (0: as many stages as fit, at most 4); use_fs:
-// stage the f' block when it fits (0: the generating warps read global memory).
-// Neither changes a result: the k chunks and their order are fixed.
-__host__ __device__ inline kx_sg_plan kx_sg_plan_for(bool gen, int n, int nsubI, int req_S = 0, int use_fs = 1) {
+__host__ __device__ __forceinline__ int kx_sg_acol(const kx_sg_plan &pl, int q) {
+    return pl.a0 + (q >> 1) * pl.a2 + (q & 1) * 32;
+}
+// wmax: the widest i tile (columns of an accumulator); req_S: the ring depth
+// wanted (0: as many stages as fit, at most 4); use_fs: stage the f' block when
+// it fits (0: the generating warps read global memory); req_atm: the gain's A
+// operand in tensor memory (1, the default) or in shared memory (0).  None of
+// them changes a result: the k chunks, their order and the MMAs are fixed.
+__host__ __device__ inline kx_sg_plan kx_sg_plan_for(bool gen, int n, int nsubI, int wmax, int req_S = 0,
+                                                     int use_fs = 1, int req_atm = 1) {
     kx_sg_plan pl;
+    pl.atm = gen && req_atm ? 1 : 0;
     pl.nsb = nsubI < 4 ? nsubI : 4;
-    pl.stage = 2 * KX_ATILE * 4 + 2 * pl.nsb * KX_BTILE * 4;
+    pl.aoff = pl.atm ? 0 : 2 * KX_ATILE * 4;
+    pl.stage = pl.aoff + 2 * pl.nsb * KX_BTILE * 4;
     pl.fs = (gen && n <= 256 && use_fs) ? 128 * n * 4 : 0;   // (n, nsubI: the largest of a grouped launch)
     const int budget = 227 * 1024 - 256;
-    pl.S = (budget - pl.fs) / pl.stage;
+    int sfull = (budget - pl.fs) / pl.stage;
+    if (sfull > 4) sfull = 4;
+    // the widest epilogue staging that keeps min(sfull, 3) stages
+    pl.eb = 0;
+    pl.ew = 0;
+    for (int w = 32; w >= 16; w -= 16) {
+        const int eb = 4 * 32 * (w + 4) * 4;
+        const int need = sfull < 3 ? sfull : 3;
+        if ((budget - pl.fs - eb) / pl.stage >= need) {
+            pl.eb = eb;
+            pl.ew = w;
+            break;
+        }
+    }
+    pl.S = (budget - pl.fs - pl.eb) / pl.stage;
     if (pl.S > 4) pl.S = 4;
     if (req_S > 0 && req_S < pl.S) pl.S = req_S;
-    pl.smem = pl.S * pl.stage + pl.fs + 256;
+    pl.smem = pl.S * pl.stage + pl.fs + pl.eb + 256;
+    pl.a0 = 0;
+    pl.a2 = 64;
+    int p2 = 32;   // accumulator width: the widest i tile, rounded up to a power of two
+    while (p2 < wmax) p2 <<= 1;
+    pl.nbuf = 2;
+    pl.half = p2;
+    if (!pl.atm) {
+        pl.ncols = 2 * p2;
+    } else if (2 * p2 + 32 * pl.S <= 512) {
+        // two accumulators, then the A stages
+        pl.a0 = 2 * p2;
+        pl.ncols = 32;
+        while (pl.ncols < 2 * p2 + 32 * pl.S) pl.ncols <<= 1;
+    } else if (wmax <= 192) {
+        // accumulators at 0 and 256; the A stages in the 64 columns after each
+        pl.ncols = 512;
+        pl.half = 256;
+        pl.a0 = 192;
+        pl.a2 = 256;
+    } else {
+        // one accumulator of 256 columns (its epilogue does not overlap the next
+        // item's MMAs), the A stages after it
+        pl.ncols = 512;
+        pl.nbuf = 1;
+        pl.half = 256;
+        pl.a0 = 256;
+    }
     return pl;
 }
 
@@ -206,11 +283,12 @@ __device__ __forceinline__ void kx_pair_decode(long long p, int N, int &n, int &
 }
 template <bool GEN>
 __global__ void __launch_bounds__(KX_SG_THREADS, 1)
-    k_split_gemm(const kx_sg_list L, const kx_sg_plan pl, int ncols, int *err) {
+    k_split_gemm(const kx_sg_list L, const kx_sg_plan pl, int *err) {
     extern __shared__ __align__(1024) unsigned char kx_gsm[];
     const int S = pl.S;
     float *fs = reinterpret_cast<float *>(kx_gsm + S * pl.stage);   // f' block (GEN, n <= 256)
-    uint64_t *bars = reinterpret_cast<uint64_t *>(kx_gsm + S * pl.stage + pl.fs);
+    float *ebuf = reinterpret_cast<float *>(kx_gsm + S * pl.stage + pl.fs);   // epilogue staging rows
+    uint64_t *bars = reinterpret_cast<uint64_t *>(kx_gsm + S * pl.stage + pl.fs + pl.eb);
     // bars: full[4] empty[4] accf[2] acce[2] fbar fsfree
     uint32_t *tslot = reinterpret_cast<uint32_t *>(bars + 14);
     volatile int *abort = reinterpret_cast<volatile int *>(tslot + 1);
@@ -241,7 +319,7 @@ __global__ void __launch_bounds__(KX_SG_THREADS, 1)
     }
     if (warp == 8) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(kx_smem_u32(tslot)),
-                     "r"(ncols)
+                     "r"(pl.ncols)
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
@@ -250,7 +328,8 @@ __global__ void __launch_bounds__(KX_SG_THREADS, 1)
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const uint32_t tmem = *tslot;
     const int items = L.items;
-    const int half = ncols >> 1;   // columns of one accumulator
+    const int half = pl.half, nbuf = pl.nbuf;   // accumulator columns, accumulators
+    const bool atm = GEN && pl.atm;               // the generated A operand in tensor memory
     int fissued = 0;               // f' blocks requested (tid 0) / waited for (producers)
     if (warp == 13) {
         // ---- bulk copies: B (hi, lo) and, for the loss, A (hi, lo) of each stage
@@ -270,7 +349,7 @@ __global__ void __launch_bounds__(KX_SG_THREADS, 1)
                         ok = false;
                         break;
                     }
-                    unsigned char *sa = kx_gsm + (size_t)q * pl.stage, *sb = sa + 2 * KX_ATILE * 4;
+                    unsigned char *sa = kx_gsm + (size_t)q * pl.stage, *sb = sa + pl.aoff;
                     const uint32_t bar = full0 + 8 * q;
                     kx_mbar_expect_tx(bar, (GEN ? 0u : 2u * KX_ATILE * 4) + 2 * bbytes);
                     const float *bsrc = pb.Bt + ((size_t)nt * KB + kb) * 2 * nsbp * KX_BTILE;
@@ -316,19 +395,32 @@ __global__ void __launch_bounds__(KX_SG_THREADS, 1)
                     ++fissued;
                     if (!r) break;
                 }
+                // (cn, cm): this warp's first pair of the current k block, decoded
+                // once per item and then walked forward 16 pairs per block (row n
+                // holds the pairs m = n .. N - 1)
+                int cn = n - 1, cm = n;   // (past the last pair)
+                if ((long long)kb0 * 16 + ph < P) kx_pair_decode((long long)kb0 * 16 + ph, n, cn, cm);
                 for (int kb = kb0; kb < kb1; ++kb, ++it) {
                     const int q = it % S, round = it / S;
-                    // lanes 0-7 decode this warp's eight pairs of the block
-                    // (independent of each other, so the loads below do not wait on
-                    // one another)
-                    const long long pq = (long long)kb * 16 + ph + (lane & 7);
-                    int dn = 0, dm = 0;
-                    if (pq < P) {
-                        kx_pair_decode(pq, n, dn, dm);
-                        dn = KX_IDX(dn, n, KX_SITE_GAIN_PAIR);
-                        dm = KX_IDX(dm, n, KX_SITE_GAIN_PAIR);
-                    } else {
-                        dn = -1;   // padding: the product is dropped (dm = 0 keeps the load in range)
+                    // this warp's eight consecutive pairs of the block (the same in
+                    // every lane); padding pairs past P get nn = -1 (the product is
+                    // dropped; mm = 0 keeps the load in range)
+                    const long long pq0 = (long long)kb * 16 + ph;
+                    int nn[8], mm[8];
+                    {
+                        int a = cn, c = cm;
+#pragma unroll
+                        for (int e = 0; e < 8; ++e) {
+                            const bool in = pq0 + e < P;
+                            nn[e] = in ? KX_IDX(a, n, KX_SITE_GAIN_PAIR) : -1;
+                            mm[e] = in ? KX_IDX(c, n, KX_SITE_GAIN_PAIR) : 0;
+                            if (++c == n) c = ++a;
+                        }
+                        cm += 16;
+                        while (cm >= n && cn < n - 1) {
+                            cm -= n - cn - 1;
+                            ++cn;
+                        }
                     }
                     if (round > 0) {
                         int r = 1;
@@ -338,6 +430,8 @@ __global__ void __launch_bounds__(KX_SG_THREADS, 1)
                             ok = false;
                             break;
                         }
+                        // the MMAs that read this stage are complete (their commit)
+                        if (atm) asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
                     }
                     float *ah = reinterpret_cast<float *>(kx_gsm + (size_t)q * pl.stage), *al = ah + KX_ATILE;
                     // (the source is chosen outside the unrolled loop, so that its
@@ -346,34 +440,49 @@ __global__ void __launch_bounds__(KX_SG_THREADS, 1)
                     if (fsm) {
 #pragma unroll
                         for (int e = 0; e < 8; ++e) {
-                            const int nn = __shfl_sync(0xffffffffu, dn, e), mm = __shfl_sync(0xffffffffu, dm, e);
-                            const float v = fs[max(nn, 0) * 128 + row] * fs[mm * 128 + row];
-                            y[e] = nn >= 0 ? v : 0.f;
+                            const float v = fs[max(nn[e], 0) * 128 + row] * fs[mm[e] * 128 + row];
+                            y[e] = nn[e] >= 0 ? v : 0.f;
                         }
                     } else {
 #pragma unroll
                         for (int e = 0; e < 8; ++e) {
-                            const int nn = __shfl_sync(0xffffffffu, dn, e), mm = __shfl_sync(0xffffffffu, dm, e);
-                            const float v = __ldg(fblk + (size_t)max(nn, 0) * 128 + row) * __ldg(fblk + (size_t)mm * 128 + row);
-                            y[e] = nn >= 0 ? v : 0.f;
+                            const float v = __ldg(fblk + (size_t)max(nn[e], 0) * 128 + row) *
+                                            __ldg(fblk + (size_t)mm[e] * 128 + row);
+                            y[e] = nn[e] >= 0 ? v : 0.f;
                         }
                     }
+                    if (atm) {
+                        // this lane's row of the stage: columns ph .. ph + 7 (hi) and
+                        // 16 + ph .. (lo) of the warp's lane quarter
+                        uint32_t h[8], l[8];
 #pragma unroll
-                    for (int q4 = 0; q4 < 8; q4 += 4) {
-                        float h[4], l[4];
-#pragma unroll
-                        for (int e = 0; e < 4; ++e) {
-                            uint32_t hb;
-                            asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(hb) : "f"(y[q4 + e]));
-                            h[e] = __uint_as_float(hb);
-                            l[e] = y[q4 + e] - h[e];
+                        for (int e = 0; e < 8; ++e) {
+                            asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(h[e]) : "f"(y[e]));
+                            l[e] = __float_as_uint(y[e] - __uint_as_float(h[e]));
                         }
-                        const int off = kx_tile_offset(row, ph + q4);
-                        *reinterpret_cast<float4 *>(ah + off) = make_float4(h[0], h[1], h[2], h[3]);
-                        *reinterpret_cast<float4 *>(al + off) = make_float4(l[0], l[1], l[2], l[3]);
+                        const uint32_t ta = tmem + ((uint32_t)(row & ~31) << 16) + (uint32_t)(kx_sg_acol(pl, q) + ph);
+                        kx_tmem_st8(ta, h);
+                        kx_tmem_st8(ta + 16u, l);
+                        asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+                        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+                    } else {
+#pragma unroll
+                        for (int q4 = 0; q4 < 8; q4 += 4) {
+                            float h[4], l[4];
+#pragma unroll
+                            for (int e = 0; e < 4; ++e) {
+                                uint32_t hb;
+                                asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(hb) : "f"(y[q4 + e]));
+                                h[e] = __uint_as_float(hb);
+                                l[e] = y[q4 + e] - h[e];
+                            }
+                            const int off = kx_tile_offset(row, ph + q4);
+                            *reinterpret_cast<float4 *>(ah + off) = make_float4(h[0], h[1], h[2], h[3]);
+                            *reinterpret_cast<float4 *>(al + off) = make_float4(l[0], l[1], l[2], l[3]);
+                        }
+                        // generic-proxy writes become visible to the tensor core (async proxy)
+                        kx_fence_proxy_async();
                     }
-                    // generic-proxy writes become visible to the tensor core (async proxy)
-                    kx_fence_proxy_async();
                     __syncwarp();
                     if (lane == 0) kx_mbar_arrive(full0 + 8 * q);
                 }
@@ -395,7 +504,7 @@ __global__ void __launch_bounds__(KX_SG_THREADS, 1)
                 const int c = wl % pb.chunks, nt = (wl / pb.chunks) % pb.NTi;
                 const int kb0 = c * pb.KC, kb1 = min(pb.KB, kb0 + pb.KC);
                 const int Ni = min(KX_GN, pb.nis - nt * KX_GN);
-                const int buf = li & 1, use = li >> 1;
+                const int buf = li % nbuf, use = li / nbuf;
                 if (use > 0 && !kx_wait_role(acce0 + 8 * buf, (use - 1) & 1, abort, err)) break;
                 asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
                 const uint32_t d = tmem + (uint32_t)(buf * half);
@@ -410,14 +519,25 @@ __global__ void __launch_bounds__(KX_SG_THREADS, 1)
                     seen[q] = round + 1;
                     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
                     const uint32_t aH = kx_smem_u32(kx_gsm + (size_t)q * pl.stage), aL = aH + KX_ATILE * 4;
-                    const uint32_t bH = aH + 2 * KX_ATILE * 4, bL = bH + pl.nsb * KX_BTILE * 4;
+                    const uint32_t bH = aH + pl.aoff, bL = bH + pl.nsb * KX_BTILE * 4;
+                    if (atm) {
+                        const uint32_t tH = tmem + (uint32_t)kx_sg_acol(pl, q), tL = tH + 16u;
 #pragma unroll
-                    for (int step = 0; step < KX_TILE_K / 8; ++step) {
-                        const uint32_t o = 256u * step;   // 8 TF32 = two 16-byte core-matrix columns
-                        kx_mma_tf32(d, kx_desc(aH + o, 128, 512), kx_desc(bH + o, 128, 512), idesc,
-                                    (kb > kb0 || step) ? 1u : 0u);
-                        kx_mma_tf32(d, kx_desc(aH + o, 128, 512), kx_desc(bL + o, 128, 512), idesc, 1u);
-                        kx_mma_tf32(d, kx_desc(aL + o, 128, 512), kx_desc(bH + o, 128, 512), idesc, 1u);
+                        for (int step = 0; step < KX_TILE_K / 8; ++step) {
+                            const uint32_t o = 256u * step, c = 8u * step;   // 8 TF32 of k
+                            kx_mma_tf32_at(d, tH + c, kx_desc(bH + o, 128, 512), idesc, (kb > kb0 || step) ? 1u : 0u);
+                            kx_mma_tf32_at(d, tH + c, kx_desc(bL + o, 128, 512), idesc, 1u);
+                            kx_mma_tf32_at(d, tL + c, kx_desc(bH + o, 128, 512), idesc, 1u);
+                        }
+                    } else {
+#pragma unroll
+                        for (int step = 0; step < KX_TILE_K / 8; ++step) {
+                            const uint32_t o = 256u * step;   // 8 TF32 = two 16-byte core-matrix columns
+                            kx_mma_tf32(d, kx_desc(aH + o, 128, 512), kx_desc(bH + o, 128, 512), idesc,
+                                        (kb > kb0 || step) ? 1u : 0u);
+                            kx_mma_tf32(d, kx_desc(aH + o, 128, 512), kx_desc(bL + o, 128, 512), idesc, 1u);
+                            kx_mma_tf32(d, kx_desc(aL + o, 128, 512), kx_desc(bH + o, 128, 512), idesc, 1u);
+                        }
                     }
                     kx_mma_commit(empty0 + 8 * q);
                     *lastc = it + 1;
@@ -435,21 +555,53 @@ __global__ void __launch_bounds__(KX_SG_THREADS, 1)
             const int wl = w - pb.item0, nis = pb.nis;
             const int c = wl % pb.chunks, nt = (wl / pb.chunks) % pb.NTi, mt = wl / (pb.chunks * pb.NTi);
             const int Ni = min(KX_GN, nis - nt * KX_GN);
-            const int buf = li & 1, use = li >> 1;
+            const int buf = li % nbuf, use = li / nbuf;
             int ok = 1;
             if (lane == 0) ok = kx_wait_role(accf0 + 8 * buf, use & 1, abort, err);
             ok = __shfl_sync(0xffffffffu, ok, 0);
             if (!ok) break;
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
             const int b = mt * 128 + qtr * 32 + lane;
-            float *dst = pb.out + ((size_t)c * pb.Bpad + b) * nis + (size_t)nt * KX_GN;
-            for (int c0 = 0; c0 < Ni; c0 += 16) {
-                float t[16];
-                kx_tmem_ld16(tmem + ((uint32_t)(qtr * 32) << 16) + (uint32_t)(buf * half + c0), t);
-                if (b < pb.Bpad) {
+            const uint32_t tl = tmem + ((uint32_t)(qtr * 32) << 16) + (uint32_t)(buf * half);
+            const int ew = pl.ew;
+            if (ew) {
+                // lane l: row l's ew columns into its staging row (columns up to
+                // Ni rounded up to ew, all inside the accumulator); then lanes
+                // (l / k, l % k), k = ew / 4 lanes per row, store float4 pieces of
+                // 32 / k rows per instruction (rows are whole ew-float segments)
+                float *wb = ebuf + (warp - 9) * 32 * (ew + 4);
+                const int k = ew >> 2, rpi = 32 / k, rr = lane / k, pp = lane % k;
+                float *dst0 = pb.out + ((size_t)c * pb.Bpad + (size_t)mt * 128 + qtr * 32) * nis + (size_t)nt * KX_GN;
+                for (int c0 = 0; c0 < Ni; c0 += ew) {
+                    float t[16];
+                    for (int h = 0; h < ew; h += 16) {
+                        kx_tmem_ld16(tl + (uint32_t)(c0 + h), t);
 #pragma unroll
-                    for (int q = 0; q < 16; q += 4)
-                        *reinterpret_cast<float4 *>(dst + c0 + q) = make_float4(t[q], t[q + 1], t[q + 2], t[q + 3]);
+                        for (int q = 0; q < 16; q += 4)
+                            *reinterpret_cast<float4 *>(wb + lane * (ew + 4) + h + q) =
+                                make_float4(t[q], t[q + 1], t[q + 2], t[q + 3]);
+                    }
+                    __syncwarp();
+                    for (int r0 = 0; r0 < 32; r0 += rpi) {
+                        const int r = r0 + rr;
+                        const float4 x = *reinterpret_cast<const float4 *>(wb + r * (ew + 4) + 4 * pp);
+                        // (Ni is a multiple of 16: a piece lies wholly inside the tile or
+                        // wholly past it; the columns past Ni are read, not stored)
+                        if (mt * 128 + qtr * 32 + r < pb.Bpad && c0 + 4 * pp < Ni)
+                            *reinterpret_cast<float4 *>(dst0 + (size_t)r * nis + c0 + 4 * pp) = x;
+                    }
+                    __syncwarp();
+                }
+            } else {
+                float *dst = pb.out + ((size_t)c * pb.Bpad + b) * nis + (size_t)nt * KX_GN;
+                for (int c0 = 0; c0 < Ni; c0 += 16) {
+                    float t[16];
+                    kx_tmem_ld16(tl + (uint32_t)c0, t);
+                    if (b < pb.Bpad) {
+#pragma unroll
+                        for (int q = 0; q < 16; q += 4)
+                            *reinterpret_cast<float4 *>(dst + c0 + q) = make_float4(t[q], t[q + 1], t[q + 2], t[q + 3]);
+                    }
                 }
             }
             asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -473,7 +625,7 @@ __global__ void __launch_bounds__(KX_SG_THREADS, 1)
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     if (warp == 8)
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(ncols) : "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(pl.ncols) : "memory");
 }
 
 // ------------------------------------------------------------- exact loss
@@ -781,12 +933,13 @@ extern "C" int kx_measure_mma_rate(kx_ctx *ctx, int kind, int n, double *flop_pe
 // rewrite their partials with the same values, so the repeats are harmless)
 // and kept for the process; under capture the default rule is used.
 struct kx_sg_choice {
-    int S, fs;
+    int S, fs, atm;
 };
 static std::mutex g_sg_mu;
 static std::map<std::tuple<int, int, int, int, int>, kx_sg_choice> g_sg_tuned;   // (dev, gen, n, nsubI, items)
 static std::map<std::tuple<int, int, int>, int> g_loss_tuned;                     // (dev, n, B) -> ipl
 static bool g_split_tuning = true;
+static int g_gain_operand = 0;   // 0: either (timed; default tensor memory), 1: shared memory, 2: tensor memory
 
 static bool kx_capturing(cudaStream_t s) {
     cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
@@ -845,32 +998,45 @@ extern "C" int kx_set_split_tuning(int enabled) {
     return KX_OK;
 }
 
+extern "C" int kx_set_gain_operand(int where) {
+    if (where < 0 || where > 2) return KX_EINVAL;
+    std::lock_guard<std::mutex> lock(g_sg_mu);
+    if (where != g_gain_operand) g_sg_tuned.clear();
+    g_gain_operand = where;
+    return KX_OK;
+}
+
 extern "C" int kx_get_split_tuning(const kx_kernel *k, int B, int *gain_S, int *gain_fs, int *loss_S,
-                                   int *loss_ipl, int *tuned) {
-    if (!k || B < 1 || !gain_S || !gain_fs || !loss_S || !loss_ipl || !tuned) return KX_EINVAL;
+                                   int *loss_ipl, int *tuned, int *gain_atm) {
+    if (!k || B < 1 || !gain_S || !gain_fs || !loss_S || !loss_ipl || !tuned || !gain_atm) return KX_EINVAL;
     if (k->precision != KX_SPLIT_TF32) return KX_ENOTSUP;
     int dev = 0;
     cudaGetDevice(&dev);
     const int Bpad = (B + 127) / 128 * 128;
     const int NTi = (k->nis + KX_GN - 1) / KX_GN;
     const int ig = Bpad / 128 * NTi * k->gsk, il = Bpad / 128 * NTi * k->lsk;
+    const int wmax = std::min(KX_GN, k->nis);
     std::lock_guard<std::mutex> lock(g_sg_mu);
     *tuned = 0;
-    const kx_sg_plan dg = kx_sg_plan_for(true, k->n, k->nsubI), dl = kx_sg_plan_for(false, k->n, k->nsubI);
+    const kx_sg_plan dg = kx_sg_plan_for(true, k->n, k->nsubI, wmax, 0, 1, g_gain_operand != 1),
+                     dl = kx_sg_plan_for(false, k->n, k->nsubI, wmax);
     *gain_S = dg.S;
     *gain_fs = dg.fs > 0;
+    *gain_atm = dg.atm;
     *loss_S = k->cheb_K ? dl.S : 0;
     *loss_ipl = kx_loss_shape_for(k->n).ipl;
     auto ig_it = g_sg_tuned.find(std::make_tuple(dev, 1, k->n, k->nsubI, ig));
     if (ig_it != g_sg_tuned.end()) {
-        const kx_sg_plan p = kx_sg_plan_for(true, k->n, k->nsubI, ig_it->second.S, ig_it->second.fs);
+        const kx_sg_choice &c = ig_it->second;
+        const kx_sg_plan p = kx_sg_plan_for(true, k->n, k->nsubI, wmax, c.S, c.fs, c.atm);
         *gain_S = p.S;
         *gain_fs = p.fs > 0;
+        *gain_atm = p.atm;
         *tuned |= 1;
     }
     auto il_it = g_sg_tuned.find(std::make_tuple(dev, 0, k->n, k->nsubI, il));
     if (k->cheb_K && il_it != g_sg_tuned.end()) {
-        *loss_S = kx_sg_plan_for(false, k->n, k->nsubI, il_it->second.S, 0).S;
+        *loss_S = kx_sg_plan_for(false, k->n, k->nsubI, wmax, il_it->second.S, 0).S;
         *tuned |= 2;
     }
     auto lo_it = g_loss_tuned.find(std::make_tuple(dev, k->n, B));
@@ -931,43 +1097,46 @@ static cudaError_t kx_launch_split_gemm(bool gen, int G, const kx_kernel *const 
     }
     if (!L.np) return cudaSuccess;
     L.items = items;
-    int ncols = 32;   // two accumulators of the widest i tile
-    while (ncols < 2 * wmax) ncols <<= 1;
     auto launch = [&](const kx_sg_plan &pl) {
         if (gen)
-            k_split_gemm<true><<<kx_sg_grid(items), KX_SG_THREADS, pl.smem, s>>>(L, pl, ncols, d_err);
+            k_split_gemm<true><<<kx_sg_grid(items), KX_SG_THREADS, pl.smem, s>>>(L, pl, d_err);
         else
-            k_split_gemm<false><<<kx_sg_grid(items), KX_SG_THREADS, pl.smem, s>>>(L, pl, ncols, d_err);
+            k_split_gemm<false><<<kx_sg_grid(items), KX_SG_THREADS, pl.smem, s>>>(L, pl, d_err);
         return cudaGetLastError();
     };
     int dev = 0;
     cudaGetDevice(&dev);
     const auto key = std::make_tuple(dev, gen ? 1 : 0, nmax, nsmax, items);
-    kx_sg_choice ch = {0, 1};
     bool tune = false;
+    int operand = 0;
+    kx_sg_choice ch;
     {
         std::lock_guard<std::mutex> lock(g_sg_mu);
+        operand = g_gain_operand;
+        ch = {0, 1, operand != 1};
         auto it = g_sg_tuned.find(key);
         if (it != g_sg_tuned.end()) ch = it->second;
         else tune = g_split_tuning;
     }
     if (tune && !kx_capturing(s)) {
-        // ring depths 2 .. the most that fit, with and without the f' stage
+        // the gain's A operand in tensor or shared memory (as allowed), ring
+        // depths 2 .. the most that fit, with and without the f' stage
         std::vector<kx_sg_choice> cand;
-        for (int fs = (gen && nmax <= 256) ? 1 : 0; fs >= 0; --fs) {
-            const int smax = kx_sg_plan_for(gen, nmax, nsmax, 0, fs).S;
-            for (int S = smax; S >= 2; --S) cand.push_back({S, fs});
-        }
+        for (int atm = (gen && operand != 1) ? 1 : 0; atm >= (operand == 2 ? 1 : 0); --atm)
+            for (int fs = (gen && nmax <= 256) ? 1 : 0; fs >= 0; --fs) {
+                const int smax = kx_sg_plan_for(gen, nmax, nsmax, wmax, 0, fs, atm).S;
+                for (int S = smax; S >= 2; --S) cand.push_back({S, fs, atm});
+            }
         if (!cand.empty()) {
             const int best = kx_time_candidates((int)cand.size(), s, [&](int c) {
-                return launch(kx_sg_plan_for(gen, nmax, nsmax, cand[c].S, cand[c].fs));
+                return launch(kx_sg_plan_for(gen, nmax, nsmax, wmax, cand[c].S, cand[c].fs, cand[c].atm));
             });
             ch = cand[best];
         }
         std::lock_guard<std::mutex> lock(g_sg_mu);
         g_sg_tuned[key] = ch;
     }
-    return launch(kx_sg_plan_for(gen, nmax, nsmax, ch.S, ch.fs));
+    return launch(kx_sg_plan_for(gen, nmax, nsmax, wmax, ch.S, ch.fs, ch.atm));
 }
 
 // The exact loss kernel (all instances, or the Chebyshev path's flagged ones).

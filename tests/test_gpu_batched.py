@@ -332,3 +332,35 @@ def test_split_tuning_is_result_neutral(env, N, B):
         assert t["tuned"] & 1 and t["gain_S"] >= 2
         assert (t["tuned"] & 2) if lt else (t["tuned"] & 4)
         k.release()
+
+
+@pytest.mark.parametrize("N", [60, 100, 192, 256, 300])
+def test_gain_operand_placement_is_result_neutral(env, N):
+    """The gain GEMM's generated A operand (f'_n f'_m, hi and lo) read by the
+    MMAs from tensor memory or from shared memory: the same MMAs in the same
+    order, so C is bit-identical; N spans the tensor-memory layouts (two
+    accumulators and the A stages after them, A stages in the gaps after two
+    256-column accumulators, one accumulator) and two i tiles (N = 300)."""
+    kx, ctx, torch = env
+    q = ki.log_grid(N, 1e-3, 1e2)
+    B = 150
+    f = ki.batch_bimodal(np.random.default_rng(90 + N), q, B)
+    sig = 10.0 ** np.random.default_rng(91).uniform(-1, 1, B)
+    fd = torch.as_tensor(f, device="cuda")
+    k = ctx.build_kernel(q, precision=kx.SPLIT_TF32)
+    ctx.set_split_tuning(False)
+    out = {}
+    try:
+        for where in ("shared", "tensor"):
+            ctx.set_gain_operand(where)
+            out[where] = ctx.collision(k, fd, sig)[0].cpu().numpy()
+            assert ctx.split_tuning(k, B)["gain_atm"] == (where == "tensor")
+    finally:
+        ctx.set_gain_operand("any")
+        ctx.set_split_tuning(True)
+    np.testing.assert_array_equal(out["tensor"], out["shared"])
+    if N <= 192:
+        Co = oracle_rows(q, f[:2], sig[:2], 1)
+        err = np.max(np.abs(out["tensor"][:2] - Co)) / np.max(np.abs(Co))
+        assert err <= TOL, err
+    k.release()
