@@ -64,12 +64,19 @@ __device__ __forceinline__ void kx_mma_tf32_at(uint32_t tmem, uint32_t ta, uint6
         "r"(ta), "l"(b), "r"(idesc), "r"(accumulate)
         : "memory");
 }
-// Eight consecutive 32-bit columns of this thread's lane (the warp's lane
+// C (4 or 8) consecutive 32-bit columns of this thread's lane (the warp's lane
 // quarter) from registers; completion is awaited with tcgen05.wait::st.
-__device__ __forceinline__ void kx_tmem_st8(uint32_t taddr, const uint32_t *v) {
-    asm volatile("tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};" ::"r"(taddr), "r"(v[0]),
-                 "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(v[4]), "r"(v[5]), "r"(v[6]), "r"(v[7])
-                 : "memory");
+template <int C>
+__device__ __forceinline__ void kx_tmem_st(uint32_t taddr, const uint32_t *v) {
+    static_assert(C == 4 || C == 8, "4 or 8 columns");
+    if constexpr (C == 8)
+        asm volatile("tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};" ::"r"(taddr),
+                     "r"(v[0]), "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(v[4]), "r"(v[5]), "r"(v[6]), "r"(v[7])
+                     : "memory");
+    else
+        asm volatile("tcgen05.st.sync.aligned.32x32b.x4.b32 [%0], {%1,%2,%3,%4};" ::"r"(taddr), "r"(v[0]),
+                     "r"(v[1]), "r"(v[2]), "r"(v[3])
+                     : "memory");
 }
 __device__ __forceinline__ void kx_mma_commit(uint32_t bar) {
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
@@ -128,29 +135,39 @@ __device__ __forceinline__ unsigned long long kx_fma2(unsigned long long a, unsi
 // MMA) accumulate in FP32 in tensor memory.  The k chunks are fixed by the
 // kernel (not by the batch), so an instance's sums do not depend on the batch.
 // A work item is (instance tile, i tile, chunk); the CTAs take them round
-// robin (persistent, one CTA per SM).  Roles: warp 13 (one lane) issues the
-// bulk copies of each stage of an S-stage ring, warps 0-7 generate the gain's
-// A operand into the same stage (two warps per 32 instance rows, eight pairs
-// each; full barrier: the copy bytes plus one arrival per generating warp;
-// empty barrier: the MMAs' commit), warp 8 lane 0 issues the MMAs into one of
-// two accumulators, warps 9-12 read the previous item's accumulator
-// (tensor-memory lane quarter = warp % 4) and store its partials while the
-// next item's MMAs run.  Operand tiles of one (i tile, k block) are
+// robin (persistent, one CTA per SM).  Roles (G = KX_SG_GW): warps 0 .. G-1
+// generate the gain's A operand of each stage of an S-stage ring (G/4 warps
+// per 32 instance rows, 16/(G/4) pairs each), warp G lane 0 issues the MMAs
+// into one of two accumulators, warps G+1 .. G+4 read the previous item's
+// accumulator (tensor-memory lane quarter = warp % 4) and store its partials
+// while the next item's MMAs run, warp G+5 (one lane) issues the bulk copies
+// of each stage (full barrier: the copy bytes plus one arrival per generating
+// warp; empty barrier: the MMAs' commit).  Operand tiles of one (i tile, k block) are
 // contiguous per hi/lo part, so a stage takes two (gain) or four (loss) copies.  Every wait is bounded: on
 // expiry the CTA sets *err and every role stops; copies and MMAs in flight get
 // a bounded wait before shared and tensor memory are released.
 #define KX_GN 256                                             // i columns per tile
 #define KX_GSTAGE (2 * KX_ATILE * 4 + 2 * 4 * KX_BTILE * 4)   // A hi/lo 16 KB + B hi/lo 32 KB
-#define KX_SG_THREADS 448   // warps 0-7 generate A (gain), 8 MMA, 9-12 epilogue, 13 bulk copies
-#define KX_GAIN_KC 32   // k blocks per chunk of the gain GEMM (a work item)
+#define KX_SG_GW 8                        // generating warps (gain), a multiple of 4 dividing 64
+#define KX_SG_PPW (64 / KX_SG_GW)         // pairs of a k block per generating warp
+#define KX_SG_MMAW KX_SG_GW               // the MMA warp
+#define KX_SG_EPIW (KX_SG_GW + 1)         // the first of the four epilogue warps
+#define KX_SG_CPYW (KX_SG_GW + 5)         // the bulk-copy warp
+#define KX_SG_THREADS ((KX_SG_GW + 6) * 32)
+#define KX_GAIN_KC 32   // k blocks per chunk of the gain GEMM (a work item; at most 32: one per lane)
 #define KX_LOSS_KC 8    // k blocks per chunk of the loss GEMM
 
 // A bounded mbarrier wait that also gives up when another role of the CTA has
 // given up (abort != 0); on its own expiry it raises abort and *err.
-__device__ __forceinline__ bool kx_wait_role(uint32_t bar, uint32_t parity, volatile int *abort, int *err) {
+// nap_ns > 0: sleep that long between tests (for roles whose waits are long
+// and not on the critical path, so that they leave the issue slots to the
+// generating and MMA warps).
+__device__ __forceinline__ bool kx_wait_role(uint32_t bar, uint32_t parity, volatile int *abort, int *err,
+                                             unsigned nap_ns = 0u) {
     const long long t0 = clock64();
     for (;;) {
         if (kx_mbar_try_wait(bar, parity)) return true;
+        if (nap_ns) __nanosleep(nap_ns);
         if (*abort) return false;
         if (clock64() - t0 > KX_WAIT_CYCLES) {
             *abort = 1;
@@ -199,7 +216,7 @@ __device__ __forceinline__ int kx_sg_find(const kx_sg_list &L, int w) {
 // segments of ew floats, eight or four lanes per row, instead of one 16-byte
 // piece per lane in 32 rows.
 struct kx_sg_plan {
-    int S, nsb, stage, aoff, fs, eb, ew, smem, atm, ncols, half, nbuf, a0, a2;
+    int S, nsb, stage, aoff, fs, pt, eb, ew, smem, atm, ncols, half, nbuf, a0, a2;
 };
 __host__ __device__ __forceinline__ int kx_sg_acol(const kx_sg_plan &pl, int q) {
     return pl.a0 + (q >> 1) * pl.a2 + (q & 1) * 32;
@@ -217,7 +234,8 @@ __host__ __device__ inline kx_sg_plan kx_sg_plan_for(bool gen, int n, int nsubI,
     pl.aoff = pl.atm ? 0 : 2 * KX_ATILE * 4;
     pl.stage = pl.aoff + 2 * pl.nsb * KX_BTILE * 4;
     pl.fs = (gen && n <= 256 && use_fs) ? 128 * n * 4 : 0;   // (n, nsubI: the largest of a grouped launch)
-    const int budget = 227 * 1024 - 256;
+    pl.pt = gen ? KX_SG_GW * KX_GAIN_KC * KX_SG_PPW * 4 : 0;    // the generating warps' pair lists
+    const int budget = 227 * 1024 - 256 - pl.pt;
     int sfull = (budget - pl.fs) / pl.stage;
     if (sfull > 4) sfull = 4;
     // the widest epilogue staging that keeps min(sfull, 3) stages
@@ -235,7 +253,7 @@ __host__ __device__ inline kx_sg_plan kx_sg_plan_for(bool gen, int n, int nsubI,
     pl.S = (budget - pl.fs - pl.eb) / pl.stage;
     if (pl.S > 4) pl.S = 4;
     if (req_S > 0 && req_S < pl.S) pl.S = req_S;
-    pl.smem = pl.S * pl.stage + pl.fs + pl.eb + 256;
+    pl.smem = pl.S * pl.stage + pl.fs + pl.pt + pl.eb + 256;
     pl.a0 = 0;
     pl.a2 = 64;
     int p2 = 32;   // accumulator width: the widest i tile, rounded up to a power of two
@@ -287,8 +305,11 @@ __global__ void __launch_bounds__(KX_SG_THREADS, 1)
     extern __shared__ __align__(1024) unsigned char kx_gsm[];
     const int S = pl.S;
     float *fs = reinterpret_cast<float *>(kx_gsm + S * pl.stage);   // f' block (GEN, n <= 256)
-    float *ebuf = reinterpret_cast<float *>(kx_gsm + S * pl.stage + pl.fs);   // epilogue staging rows
-    uint64_t *bars = reinterpret_cast<uint64_t *>(kx_gsm + S * pl.stage + pl.fs + pl.eb);
+    // the generating warps' pair lists (GEN): warp w's (n | m << 16) of its PPW
+    // pairs of each k block of the current item
+    uint32_t *ptab = reinterpret_cast<uint32_t *>(kx_gsm + S * pl.stage + pl.fs);
+    float *ebuf = reinterpret_cast<float *>(kx_gsm + S * pl.stage + pl.fs + pl.pt);   // epilogue staging rows
+    uint64_t *bars = reinterpret_cast<uint64_t *>(kx_gsm + S * pl.stage + pl.fs + pl.pt + pl.eb);
     // bars: full[4] empty[4] accf[2] acce[2] fbar fsfree
     uint32_t *tslot = reinterpret_cast<uint32_t *>(bars + 14);
     volatile int *abort = reinterpret_cast<volatile int *>(tslot + 1);
@@ -302,7 +323,7 @@ __global__ void __launch_bounds__(KX_SG_THREADS, 1)
     const bool fsm = GEN && pl.fs > 0;
     if (tid == 0) {
         for (int q = 0; q < S; ++q) {
-            kx_mbar_init(full0 + 8 * q, GEN ? 9 : 1);   // GEN: the copy arrival + eight generating warps
+            kx_mbar_init(full0 + 8 * q, GEN ? 1 + KX_SG_GW : 1);   // GEN: the copy arrival + the generating warps
             kx_mbar_init(empty0 + 8 * q, 1);
             issued[q] = 0;
             seen[q] = 0;
@@ -312,12 +333,12 @@ __global__ void __launch_bounds__(KX_SG_THREADS, 1)
             kx_mbar_init(acce0 + 8 * q, 4);   // one arrival per epilogue warp
         }
         kx_mbar_init(fbar, 1);
-        kx_mbar_init(fsfree, 8);   // one arrival per generating warp
+        kx_mbar_init(fsfree, KX_SG_GW);   // one arrival per generating warp
         *lastc = 0;
         *abort = 0;
         kx_fence_mbar_init();
     }
-    if (warp == 8) {
+    if (warp == KX_SG_MMAW) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(kx_smem_u32(tslot)),
                      "r"(pl.ncols)
                      : "memory");
@@ -331,7 +352,7 @@ __global__ void __launch_bounds__(KX_SG_THREADS, 1)
     const int half = pl.half, nbuf = pl.nbuf;   // accumulator columns, accumulators
     const bool atm = GEN && pl.atm;               // the generated A operand in tensor memory
     int fissued = 0;               // f' blocks requested (tid 0) / waited for (producers)
-    if (warp == 13) {
+    if (warp == KX_SG_CPYW) {
         // ---- bulk copies: B (hi, lo) and, for the loss, A (hi, lo) of each stage
         if (lane == 0) {
             int it = 0;
@@ -345,7 +366,7 @@ __global__ void __launch_bounds__(KX_SG_THREADS, 1)
                 bool ok = true;
                 for (int kb = kb0; kb < kb1; ++kb, ++it) {
                     const int q = it % S, round = it / S;
-                    if (round > 0 && !kx_wait_role(empty0 + 8 * q, (round - 1) & 1, abort, err)) {
+                    if (round > 0 && !kx_wait_role(empty0 + 8 * q, (round - 1) & 1, abort, err, 64u)) {
                         ok = false;
                         break;
                     }
@@ -365,12 +386,12 @@ __global__ void __launch_bounds__(KX_SG_THREADS, 1)
                 if (!ok) break;
             }
         }
-    } else if (warp < 8) {
+    } else if (warp < KX_SG_GW) {
         // ---- the gain's A operand: row r = f'_n f'_m of instance b for the 16
-        // pairs of each k block (warp w: rows 32 (w % 4) .., pairs 8 (w / 4) ..)
+        // pairs of each k block (warp w: rows 32 (w % 4) .., pairs PPW (w / 4) ..)
         if (GEN) {
             int it = 0;
-            const int row = tid & 127, ph = (tid >> 7) * 8;   // instance row in the tile, first pair
+            const int row = tid & 127, ph = (tid >> 7) * KX_SG_PPW;   // instance row in the tile, first pair
             for (int w = blockIdx.x; w < items && !*abort; w += gridDim.x) {
                 const kx_sg_problem &pb = L.p[kx_sg_find(L, w)];
                 const int wl = w - pb.item0, n = pb.n;
@@ -395,33 +416,57 @@ __global__ void __launch_bounds__(KX_SG_THREADS, 1)
                     ++fissued;
                     if (!r) break;
                 }
-                // (cn, cm): this warp's first pair of the current k block, decoded
-                // once per item and then walked forward 16 pairs per block (row n
-                // holds the pairs m = n .. N - 1)
-                int cn = n - 1, cm = n;   // (past the last pair)
-                if ((long long)kb0 * 16 + ph < P) kx_pair_decode((long long)kb0 * 16 + ph, n, cn, cm);
-                for (int kb = kb0; kb < kb1; ++kb, ++it) {
-                    const int q = it % S, round = it / S;
-                    // this warp's eight consecutive pairs of the block (the same in
-                    // every lane); padding pairs past P get nn = -1 (the product is
-                    // dropped; mm = 0 keeps the load in range)
-                    const long long pq0 = (long long)kb * 16 + ph;
-                    int nn[8], mm[8];
-                    {
-                        int a = cn, c = cm;
+                // this warp's pair list of the item: lane j decodes the first of the
+                // warp's PPW pairs of k block kb0 + j and steps on to the others
+                // (row a holds the pairs m = a .. N - 1; after (a, N - 1) comes
+                // (a + 1, a + 1)); padding pairs past P are 0xffff
+                uint32_t *wpt = ptab + warp * (KX_GAIN_KC * KX_SG_PPW);
+                if (lane < kb1 - kb0) {
+                    const long long p0 = (long long)(kb0 + lane) * 16 + ph;
+                    int a = n - 1, c = n;
+                    if (p0 < P) kx_pair_decode(p0, n, a, c);
 #pragma unroll
-                        for (int e = 0; e < 8; ++e) {
-                            const bool in = pq0 + e < P;
-                            nn[e] = in ? KX_IDX(a, n, KX_SITE_GAIN_PAIR) : -1;
-                            mm[e] = in ? KX_IDX(c, n, KX_SITE_GAIN_PAIR) : 0;
-                            if (++c == n) c = ++a;
-                        }
-                        cm += 16;
-                        while (cm >= n && cn < n - 1) {
-                            cm -= n - cn - 1;
-                            ++cn;
+                    for (int e = 0; e < KX_SG_PPW; ++e) {
+                        wpt[lane * KX_SG_PPW + e] = p0 + e < P ? (uint32_t)a | ((uint32_t)c << 16) : 0xffffu;
+                        if (++c == n) c = ++a;
+                    }
+                }
+                __syncwarp();
+                // y = f'_n f'_m of this lane's row for the warp's PPW pairs of k block
+                // kb (the pairs are the same in every lane; padding pairs give 0)
+                auto gen_y = [&](int kb, float *y) {
+                    int nn[KX_SG_PPW], mm[KX_SG_PPW];
+                    const uint4 *wq = reinterpret_cast<const uint4 *>(wpt + (kb - kb0) * KX_SG_PPW);
+#pragma unroll
+                    for (int e4 = 0; e4 < KX_SG_PPW / 4; ++e4) {
+                        const uint4 w4 = wq[e4];
+                        const uint32_t wv[4] = {w4.x, w4.y, w4.z, w4.w};
+#pragma unroll
+                        for (int e = 0; e < 4; ++e) {
+                            const bool in = wv[e] != 0xffffu;
+                            nn[4 * e4 + e] = in ? KX_IDX((int)(wv[e] & 0xffffu), n, KX_SITE_GAIN_PAIR) : -1;
+                            mm[4 * e4 + e] = in ? KX_IDX((int)(wv[e] >> 16), n, KX_SITE_GAIN_PAIR) : 0;
                         }
                     }
+                    // (the source is chosen outside the unrolled loops, so that the
+                    // loads are issued back to back)
+                    if (fsm) {
+#pragma unroll
+                        for (int e = 0; e < KX_SG_PPW; ++e) {
+                            const float v = fs[max(nn[e], 0) * 128 + row] * fs[mm[e] * 128 + row];
+                            y[e] = nn[e] >= 0 ? v : 0.f;
+                        }
+                    } else {
+#pragma unroll
+                        for (int e = 0; e < KX_SG_PPW; ++e) {
+                            const float v = __ldg(fblk + (size_t)max(nn[e], 0) * 128 + row) *
+                                            __ldg(fblk + (size_t)mm[e] * 128 + row);
+                            y[e] = nn[e] >= 0 ? v : 0.f;
+                        }
+                    }
+                };
+                for (int kb = kb0; kb < kb1; ++kb, ++it) {
+                    const int q = it % S, round = it / S;
                     if (round > 0) {
                         int r = 1;
                         if (lane == 0) r = kx_wait_role(empty0 + 8 * q, (round - 1) & 1, abort, err);
@@ -434,40 +479,25 @@ __global__ void __launch_bounds__(KX_SG_THREADS, 1)
                         if (atm) asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
                     }
                     float *ah = reinterpret_cast<float *>(kx_gsm + (size_t)q * pl.stage), *al = ah + KX_ATILE;
-                    // (the source is chosen outside the unrolled loop, so that its
-                    // 32 loads are issued back to back)
-                    float y[8];
-                    if (fsm) {
-#pragma unroll
-                        for (int e = 0; e < 8; ++e) {
-                            const float v = fs[max(nn[e], 0) * 128 + row] * fs[mm[e] * 128 + row];
-                            y[e] = nn[e] >= 0 ? v : 0.f;
-                        }
-                    } else {
-#pragma unroll
-                        for (int e = 0; e < 8; ++e) {
-                            const float v = __ldg(fblk + (size_t)max(nn[e], 0) * 128 + row) *
-                                            __ldg(fblk + (size_t)mm[e] * 128 + row);
-                            y[e] = nn[e] >= 0 ? v : 0.f;
-                        }
-                    }
+                    float y[KX_SG_PPW];
+                    gen_y(kb, y);
                     if (atm) {
-                        // this lane's row of the stage: columns ph .. ph + 7 (hi) and
-                        // 16 + ph .. (lo) of the warp's lane quarter
-                        uint32_t h[8], l[8];
+                        // this lane's row of the stage: columns ph .. ph + PPW - 1 (hi)
+                        // and 16 + ph .. (lo) of the warp's lane quarter
+                        uint32_t h[KX_SG_PPW], l[KX_SG_PPW];
 #pragma unroll
-                        for (int e = 0; e < 8; ++e) {
+                        for (int e = 0; e < KX_SG_PPW; ++e) {
                             asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(h[e]) : "f"(y[e]));
                             l[e] = __float_as_uint(y[e] - __uint_as_float(h[e]));
                         }
                         const uint32_t ta = tmem + ((uint32_t)(row & ~31) << 16) + (uint32_t)(kx_sg_acol(pl, q) + ph);
-                        kx_tmem_st8(ta, h);
-                        kx_tmem_st8(ta + 16u, l);
+                        kx_tmem_st<KX_SG_PPW>(ta, h);
+                        kx_tmem_st<KX_SG_PPW>(ta + 16u, l);
                         asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
                         asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
                     } else {
 #pragma unroll
-                        for (int q4 = 0; q4 < 8; q4 += 4) {
+                        for (int q4 = 0; q4 < KX_SG_PPW; q4 += 4) {
                             float h[4], l[4];
 #pragma unroll
                             for (int e = 0; e < 4; ++e) {
@@ -494,7 +524,7 @@ __global__ void __launch_bounds__(KX_SG_THREADS, 1)
                 }
             }
         }
-    } else if (warp == 8) {
+    } else if (warp == KX_SG_MMAW) {
         // ---- MMA issue
         if (lane == 0) {
             int it = 0, li = 0;
@@ -557,7 +587,7 @@ __global__ void __launch_bounds__(KX_SG_THREADS, 1)
             const int Ni = min(KX_GN, nis - nt * KX_GN);
             const int buf = li % nbuf, use = li / nbuf;
             int ok = 1;
-            if (lane == 0) ok = kx_wait_role(accf0 + 8 * buf, use & 1, abort, err);
+            if (lane == 0) ok = kx_wait_role(accf0 + 8 * buf, use & 1, abort, err, 256u);
             ok = __shfl_sync(0xffffffffu, ok, 0);
             if (!ok) break;
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
@@ -569,7 +599,7 @@ __global__ void __launch_bounds__(KX_SG_THREADS, 1)
                 // Ni rounded up to ew, all inside the accumulator); then lanes
                 // (l / k, l % k), k = ew / 4 lanes per row, store float4 pieces of
                 // 32 / k rows per instruction (rows are whole ew-float segments)
-                float *wb = ebuf + (warp - 9) * 32 * (ew + 4);
+                float *wb = ebuf + (warp - KX_SG_EPIW) * 32 * (ew + 4);
                 const int k = ew >> 2, rpi = 32 / k, rr = lane / k, pp = lane % k;
                 float *dst0 = pb.out + ((size_t)c * pb.Bpad + (size_t)mt * 128 + qtr * 32) * nis + (size_t)nt * KX_GN;
                 for (int c0 = 0; c0 < Ni; c0 += ew) {
@@ -624,7 +654,7 @@ __global__ void __launch_bounds__(KX_SG_THREADS, 1)
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    if (warp == 8)
+    if (warp == KX_SG_MMAW)
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(pl.ncols) : "memory");
 }
 
