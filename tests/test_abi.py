@@ -53,6 +53,10 @@ def test_strerror_and_error_paths_without_gpu(lib):
     assert lib.kx_create(None, 0, None) == -1
     assert lib.kx_build_kernel(None, None, None) == -1
     assert lib.kx_collision(None, None, 1, None, None, None, 1, None) == -1
+    # the gain-operand setting is host state only: out-of-range values are
+    # rejected, 0 (either placement, the default) is accepted
+    assert lib.kx_set_gain_operand(3) == -1 and lib.kx_set_gain_operand(-1) == -1
+    assert lib.kx_set_gain_operand(0) == 0
 
 
 def test_struct_layouts_match_header(tmp_path):
