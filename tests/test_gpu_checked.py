@@ -112,3 +112,34 @@ def test_checked_build_solve_no_failed_check(env):
         assert x["status"] == 0 and x["steps"] == y["steps"] and x["rejects"] == y["rejects"]
     np.testing.assert_array_equal(fa.cpu().numpy(), fb.cpu().numpy())
     assert ctx.check_status(reset=True)["failures"] == 0
+
+
+@pytest.mark.parametrize("loss_terms", [0, 16])
+def test_checked_build_grouped_solve_no_failed_check(env, loss_terms):
+    """A short grouped solve of three grids on the split path through the
+    checked build (the gain GEMM's pair lists, the grids' exact loss kernels
+    forked onto side streams, or the Chebyshev loss GEMM, the grouped stage):
+    results bit-identical to the normal build and no failed check."""
+    kx, ctx, torch = env
+    rng = np.random.default_rng(120 + loss_terms)
+    sizes, Bs = (24, 40, 100), (130, 3, 5)
+    grids = [ki.log_grid(n, 1e-3, 1e2) for n in sizes]
+    f0 = [ki.batch_bimodal(rng, q, B) for q, B in zip(grids, Bs)]
+    sig = [10.0 ** rng.uniform(-1, 0.5, B) for B in Bs]
+    par = dict(t_end=0.2, h0=1e-3, rtol=1e-6, atol=1e-12, l1_tol=0.0)
+    ctx.check_status(reset=True)
+    out = []
+    plain = kx.Context(0)
+    for cx in (ctx, plain):
+        ks = [cx.build_kernel(q, precision=kx.SPLIT_TF32, loss_terms=loss_terms) for q in grids]
+        fd = [torch.as_tensor(f, device="cuda") for f in f0]
+        res = cx.solve_grouped(ks, fd, sig, **par)
+        out.append(([f.cpu().numpy() for f in fd], [[(x["status"], x["steps"], x["rejects"]) for x in r] for r in res]))
+        for k in ks:
+            k.release()
+    plain.close()
+    for g in range(len(sizes)):
+        np.testing.assert_array_equal(out[0][0][g], out[1][0][g])
+    assert out[0][1] == out[1][1]
+    assert all(s == 0 for r in out[0][1] for s, _, _ in r)
+    assert ctx.check_status(reset=True)["failures"] == 0
