@@ -529,6 +529,9 @@ def serve_stream(kx, ctx, reqs, precision, budget=96 << 30, slots=2, phases=("ru
                       "p50_service_s": s1["p50_service_s"], "p99_service_s": s1["p99_service_s"],
                       "ticks_shared": s1["ticks_shared"] - s0["ticks_shared"],
                       "ticks_whole": s1["ticks_whole"] - s0["ticks_whole"],
+                      # the completed solves' table bytes (one pass per evaluation)
+                      # per second: an upper bound of the algorithmic HBM read rate
+                      "stream_gbs": (s1["stream_bytes"] - s0["stream_bytes"]) / dt / 1e9,
                       "kernels_built": s1["kernels_built"] - s0["kernels_built"],
                       "kernel_cache_hits": s1["kernel_cache_hits"] - s0["kernel_cache_hits"]}
     srv.stop()
@@ -551,6 +554,15 @@ def measure_serving(ctx, kx, requests=200, fp64_requests=16):
     b = serve_stream(kx, ctx, sub, kx.FP64)["run"]
     out["same_inputs_fp32"] = a
     out["same_inputs_fp64_path"] = b
+    hbm, src = peaks()
+    if "warm" in out:
+        w = out["warm"]["stream_gbs"]
+        out["roofline"] = {"bound": "hbm", "achieved": w, "peak": hbm, "unit": "GB/s", "frac": w / hbm,
+                           "phase": "warm", "peak_source": src,
+                           "note": "the completed solves' evaluations x their kernel's streamed table "
+                                   "bytes per second: an upper bound of the algorithmic reads (the two "
+                                   "slots of a group share a pass; tables of the smaller grids can stay "
+                                   "in the 126 MB L2), so the fraction is an upper bound too"}
     out["speedup_vs_fp64_solves_per_s"] = (a["solves_per_s"] / b["solves_per_s"]
                                            if b["solves_per_s"] > 0 else None)
     out["speedup_vs_fp64_converged_solves_per_s"] = (a["converged_solves_per_s"] / b["converged_solves_per_s"]

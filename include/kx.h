@@ -356,6 +356,11 @@ typedef struct {
     long long ticks_whole;        /* group graph launches on the whole GPU */
     double p99_wait_s;            /* submit -> admitted */
     double p50_service_s, p99_service_s;   /* admitted -> result available */
+    long long stream_bytes;       /* sum over the completed solves of evaluations x the
+                                     kernel's stream_bytes: the table bytes the solves'
+                                     contractions stream when each runs alone (the two
+                                     slots of a group share one pass; small tables can
+                                     stay in L2), an upper bound of the algorithmic reads */
 } kx_server_stats;
 
 /* Start a server on the context's device (the context's stream is not used).

@@ -110,7 +110,8 @@ class ServerStats(ctypes.Structure):
                [(k, ctypes.c_double) for k in ("p50_latency_s", "p99_latency_s", "mean_latency_s",
                                                "p50_wait_s")] + \
                [(k, ctypes.c_longlong) for k in ("evals", "converged", "ticks_shared", "ticks_whole")] + \
-               [(k, ctypes.c_double) for k in ("p99_wait_s", "p50_service_s", "p99_service_s")]
+               [(k, ctypes.c_double) for k in ("p99_wait_s", "p50_service_s", "p99_service_s")] + \
+               [("stream_bytes", ctypes.c_longlong)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

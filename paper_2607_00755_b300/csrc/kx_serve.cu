@@ -369,6 +369,7 @@ static void kx_complete(kx_server *srv, Group *g) {
         srv->service.push_back(r->t_done - r->t_admit);
         srv->stats.active--;
         srv->stats.evals += st.evals;
+        srv->stats.stream_bytes += st.evals * g->k->stream_bytes;
         srv->lat.push_back(o.latency_s);
         g->slot[s] = nullptr;
         g->active--;
