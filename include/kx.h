@@ -84,8 +84,8 @@ typedef struct {
     int measure;      /* KX_MEASURE_ENERGY | KX_MEASURE_LITERAL */
     int stats;        /* 0 = dilute f3 f4 - f1 f2 (eq. Lambda dilute); +1 Bose-Einstein, -1
                          Fermi-Dirac: the factor of eq. Lambda_quantum per element, f_t from the
-                         log interpolation of f (FP64 and FP32 paths; KX_SPLIT_TF32 ->
-                         KX_ENOTSUP) */
+                         log interpolation of f (every path; KX_SPLIT_TF32 with the exact
+                         loss only: loss_terms != 0 -> KX_ENOTSUP) */
     int precision;    /* KX_FP64 | KX_FP32 | KX_SPLIT_TF32 */
     int loss_terms;   /* KX_SPLIT_TF32 only (else must be 0): 0 = exact loss (one exp2 per element
                          and instance); 8, 16 or 32 = the loss rate as a second tensor-core GEMM

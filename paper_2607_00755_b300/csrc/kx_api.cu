@@ -168,6 +168,7 @@ size_t kx_views_bytes(const kx_kernel *k, int B) {
             s += kx_align(sizeof(float) * Bpad * (size_t)k->lsk * k->nis);   // Lp
             s += kx_align(sizeof(int) * B);                                   // cflag
         }
+        if (k->stats) s += kx_align(sizeof(double) * B * n);                  // qsum
     }
     return s;
 }
@@ -194,6 +195,7 @@ void kx_carve_views(const kx_kernel *k, int B, void *base, kx_batch_views *v) {
     v->fT = v->Gs = nullptr;
     v->yt = v->Lp = nullptr;
     v->cflag = nullptr;
+    v->qsum = nullptr;
     v->cheb_K = k->cheb_K;
     v->KBL = k->KBL;
     v->gsk = k->gsk;
@@ -218,6 +220,10 @@ void kx_carve_views(const kx_kernel *k, int B, void *base, kx_batch_views *v) {
             v->yt = (float *)p; p += kx_align(sizeof(float) * Bpad * (size_t)k->KBL * 16 * 2);
             v->Lp = (float *)p; p += kx_align(sizeof(float) * Bpad * (size_t)k->lsk * k->nis);
             v->cflag = (int *)p; p += kx_align(sizeof(int) * B);
+        }
+        if (k->stats) {
+            v->qsum = (double *)p;
+            p += kx_align(sizeof(double) * B * n);
         }
     }
 }
@@ -265,7 +271,7 @@ static void kx_free_kernel(kx_kernel *k) {
     cudaSetDevice(k->device);
     void *ptrs[] = {k->d_p, k->d_E, k->d_dp, k->d_dE, k->d_h, k->d_pair, k->d_W64,
                     k->d_om64, k->d_jl, k->d_vt, k->d_W32, k->d_pk, k->d_roff, k->d_rtask,
-                    k->d_task, k->d_bins, k->d_Sg, k->d_lel, k->d_lseg, k->d_lsw,
+                    k->d_task, k->d_bins, k->d_Sg, k->d_lel, k->d_lnm, k->d_lseg, k->d_lsw,
                     k->d_lorder, k->d_Mtile, k->d_vt_all, k->d_pos};
     for (void *p : ptrs)
         if (p) cudaFree(p);
@@ -322,8 +328,8 @@ static int kx_build_kernel_ex(kx_ctx *ctx, const kx_grid_desc *d, kx_kernel **ou
     if (d->measure != KX_MEASURE_ENERGY && d->measure != KX_MEASURE_LITERAL)
         return kx_set_error(ctx, KX_EINVAL, "unknown measure");
     if (d->stats < -1 || d->stats > 1) return kx_set_error(ctx, KX_EINVAL, "stats in {-1, 0, +1}");
-    if (d->stats != 0 && d->precision == KX_SPLIT_TF32)
-        return kx_set_error(ctx, KX_ENOTSUP, "quantum statistics: FP64 and FP32 paths only");
+    if (d->stats != 0 && d->precision == KX_SPLIT_TF32 && d->loss_terms != 0)
+        return kx_set_error(ctx, KX_ENOTSUP, "quantum statistics on the split path: exact loss only");
     if (d->loss_terms != 0 && d->precision != KX_SPLIT_TF32)
         return kx_set_error(ctx, KX_ENOTSUP, "the Chebyshev loss GEMM: KX_SPLIT_TF32 path only");
     if (d->loss_terms != 0 && d->loss_terms != 8 && d->loss_terms != 16 && d->loss_terms != 32)

@@ -841,6 +841,140 @@ __global__ void __launch_bounds__(WARPS * 32, (WARPS <= 16 && IPL <= 2) ? 2 : 1)
     }
 }
 
+// The exact loss with quantum statistics (eq. Lambda_quantum).  With
+// eta = +1 (BE) or -1 (FD) an element's factor
+//   f_n f_m (1 + eta f_i)(1 + eta f~) - f_i f~ (1 + eta f_n)(1 + eta f_m)
+// sums over a row to (1 + eta f_i) G_i - f_i L_i - eta f_i P_i + eta Q_i
+// (eta^2 = 1), with G_i = sum S f_n f_m (the gain GEMM), L_i = sum S f~,
+// P_i = sum S f~ (f_n + f_m) and Q_i = sum S f~ f_n f_m.  This kernel makes
+// L, P and Q of each (instance, row): the dilute kernel's segments and
+// per-element exponent, and per element the pair's f'_n, f'_m (f' = f / f_max,
+// from the gain's f' block) read from a shared-memory table by the pair
+// indices of the element (d_lnm).  One instance per lane, WARPS warps (the
+// loss list's warp split); the FP32 sums flush into double-float accumulators
+// every 64 or more elements, FP64 across warps.  Output: partial[b][i] =
+// (f_max^2 P', f_max L'), qsum[b][i] = f_max^3 Q' (primes: f' units).
+template <int WARPS>
+__global__ void __launch_bounds__(WARPS * 32, 1)
+    k_batch_loss_q(int n, int B, int tds, const float2 *__restrict__ lel, const uint32_t *__restrict__ lnm,
+                   const int2 *__restrict__ lseg, const int *__restrict__ lsw, const int *__restrict__ lorder,
+                   const float2 *__restrict__ td, const float *__restrict__ fT, const double *__restrict__ fmax,
+                   double2 *__restrict__ partial, double *__restrict__ qsum,
+                   const kx_inst_state *__restrict__ st, int stage, int nel) {
+    // [n][32] (l2_j, D_j), then [n][32] f'_j; after the loop the same space holds
+    // the cross-warp reduction [3][WARPS][32] doubles
+    extern __shared__ __align__(16) float2 kx_ltab[];
+    float *ftab = reinterpret_cast<float *>(kx_ltab + (size_t)n * 32);
+    __shared__ __align__(16) float2 s_el[WARPS][KX_SEG];
+    __shared__ __align__(16) uint32_t s_nm[WARPS][KX_SEG];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int b = blockIdx.x * 32 + lane;
+    const bool act = b < B && !(st && (st[b].done || (stage == 2 && st[b].skip2)));
+    if (!__syncthreads_or(act)) return;
+    const int i = KX_IDX(lorder[blockIdx.y], n, KX_SITE_LOSS_ROW);
+    const float *fb = fT + (size_t)(b >> 7) * n * 128 + (b & 127);
+    for (int j = warp; j < n; j += WARPS) {
+        kx_ltab[j * 32 + lane] = act ? td[(size_t)j * tds + b] : make_float2(-2000.f, 0.f);
+        ftab[j * 32 + lane] = act ? fb[(size_t)j * 128] : 0.f;
+    }
+    __syncthreads();
+    float hl = 0.f, ll = 0.f, hp = 0.f, lp = 0.f, hq = 0.f, lq = 0.f;
+    {
+        const int gend = lsw[i * WARPS + warp + 1];
+        int g = lsw[i * WARPS + warp];
+        float aL[4] = {0.f, 0.f, 0.f, 0.f}, aP[4] = {0.f, 0.f, 0.f, 0.f}, aQ[4] = {0.f, 0.f, 0.f, 0.f};
+        int na = 0;
+        for (; g < gend; ++g) {
+            const int2 dsc = __ldg(lseg + g);
+            const int c = dsc.y & 255;
+            float2 el0 = make_float2(0.f, 0.f), el1 = el0;
+            uint32_t nm0 = 0u, nm1 = 0u;
+            if (lane < c) {
+                const int x = KX_IDX(dsc.x + lane, nel, KX_SITE_LOSS_ELEM);
+                el0 = __ldg(lel + x);
+                nm0 = __ldg(lnm + x);
+            }
+            if (lane + 32 < c) {
+                const int x = KX_IDX(dsc.x + 32 + lane, nel, KX_SITE_LOSS_ELEM);
+                el1 = __ldg(lel + x);
+                nm1 = __ldg(lnm + x);
+            }
+            s_el[warp][lane] = el0;
+            s_el[warp][32 + lane] = el1;
+            s_nm[warp][lane] = nm0;
+            s_nm[warp][32 + lane] = nm1;
+            __syncwarp();
+            const int j = KX_IDX(dsc.y >> 8, n, KX_SITE_LOSS_BRACKET), c4 = c;   // a multiple of 4
+            const float2 t = kx_ltab[j * 32 + lane];
+            const float4 *pe = reinterpret_cast<const float4 *>(s_el[warp]);
+            const uint4 *pn = reinterpret_cast<const uint4 *>(s_nm[warp]);
+            for (int e4 = 0; e4 < c4; e4 += 4, pe += 2, ++pn) {
+                // elements e4 .. e4 + 3: (S_0, S_1, omega_0, omega_1), (S_2, S_3, omega_2, omega_3)
+                const float4 x01 = pe[0], x23 = pe[1];
+                const uint4 w4 = *pn;
+                const float S[4] = {x01.x, x01.y, x23.x, x23.y}, om[4] = {x01.z, x01.w, x23.z, x23.w};
+                const uint32_t nm[4] = {w4.x, w4.y, w4.z, w4.w};
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const float ft = kx_ex2f(fmaf(om[u], t.y, t.x));
+                    const int a = KX_IDX((int)(nm[u] & 0xffffu), n, KX_SITE_LOSS_PAIR);
+                    const int m = KX_IDX((int)(nm[u] >> 16), n, KX_SITE_LOSS_PAIR);
+                    const float fn = ftab[a * 32 + lane], fm = ftab[m * 32 + lane];
+                    const float w = S[u] * ft;
+                    aL[u] = fmaf(S[u], ft, aL[u]);
+                    aP[u] = fmaf(w, fn + fm, aP[u]);
+                    aQ[u] = fmaf(w, fn * fm, aQ[u]);
+                }
+            }
+            na += c4;
+            if (na >= KX_SEG) {
+                float sm, er;
+                kx_two_sum_f(hl, (aL[0] + aL[1]) + (aL[2] + aL[3]), sm, er);
+                hl = sm;
+                ll += er;
+                kx_two_sum_f(hp, (aP[0] + aP[1]) + (aP[2] + aP[3]), sm, er);
+                hp = sm;
+                lp += er;
+                kx_two_sum_f(hq, (aQ[0] + aQ[1]) + (aQ[2] + aQ[3]), sm, er);
+                hq = sm;
+                lq += er;
+#pragma unroll
+                for (int u = 0; u < 4; ++u) aL[u] = aP[u] = aQ[u] = 0.f;
+                na = 0;
+            }
+            __syncwarp();   // the slots are refilled next segment
+        }
+        float sm, er;
+        kx_two_sum_f(hl, (aL[0] + aL[1]) + (aL[2] + aL[3]), sm, er);
+        hl = sm;
+        ll += er;
+        kx_two_sum_f(hp, (aP[0] + aP[1]) + (aP[2] + aP[3]), sm, er);
+        hp = sm;
+        lp += er;
+        kx_two_sum_f(hq, (aQ[0] + aQ[1]) + (aQ[2] + aQ[3]), sm, er);
+        hq = sm;
+        lq += er;
+    }
+    __syncthreads();   // every warp is done with the tables
+    double *red = reinterpret_cast<double *>(kx_ltab);   // [3][WARPS][32]
+    red[(0 * WARPS + warp) * 32 + lane] = (double)hl + (double)ll;
+    red[(1 * WARPS + warp) * 32 + lane] = (double)hp + (double)lp;
+    red[(2 * WARPS + warp) * 32 + lane] = (double)hq + (double)lq;
+    __syncthreads();
+    if (warp == 0 && act) {
+        double L = 0.0, P = 0.0, Q = 0.0;
+#pragma unroll
+        for (int w = 0; w < WARPS; ++w) {
+            L += red[(0 * WARPS + w) * 32 + lane];
+            P += red[(1 * WARPS + w) * 32 + lane];
+            Q += red[(2 * WARPS + w) * 32 + lane];
+        }
+        const double fm = fmax[b];
+        partial[(size_t)b * n + i] = make_double2(fm * fm * P, fm * L);
+        qsum[(size_t)b * n + i] = fm * fm * fm * Q;
+    }
+}
+
 // Loss-kernel shape for an n-point grid: two instances per lane while the
 // table (n x 32 x 2 float2) leaves room for two 16-warp blocks per SM or, up to
 // n = 400, for one 32-warp block; one instance per lane (32 warps) above that.
@@ -860,6 +994,10 @@ static kx_loss_shape kx_loss_shape_for(int n) {
 static size_t kx_loss_smem(int n, kx_loss_shape sh) {
     return std::max((size_t)n, (size_t)sh.warps) * 32 * sh.ipl * sizeof(float2);
 }
+// quantum statistics: the (l2, D) and f' tables, or the three reductions
+static size_t kx_loss_q_smem(int n, int warps) {
+    return std::max((size_t)n * 32 * (sizeof(float2) + sizeof(float)), (size_t)3 * warps * 32 * sizeof(double));
+}
 
 void kx_batch_prepare() {
     cudaFuncSetAttribute(k_split_gemm<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
@@ -872,6 +1010,10 @@ void kx_batch_prepare() {
                          (int)kx_loss_smem(KX_MAX_N, {1, 32}));
     cudaFuncSetAttribute(k_batch_loss<1, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)kx_loss_smem(200, {1, 16}));
+    cudaFuncSetAttribute(k_batch_loss_q<16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)kx_loss_q_smem(KX_MAX_N, 16));
+    cudaFuncSetAttribute(k_batch_loss_q<32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)kx_loss_q_smem(KX_MAX_N, 32));
     cudaGetLastError();
 }
 
@@ -1172,6 +1314,21 @@ static cudaError_t kx_launch_split_gemm(bool gen, int G, const kx_kernel *const 
 // The exact loss kernel (all instances, or the Chebyshev path's flagged ones).
 static cudaError_t kx_launch_batch_loss(const kx_kernel *k, int B, const kx_batch_views &v,
                                         const kx_inst_state *st, int stage, cudaStream_t s) {
+    if (k->stats) {
+        // quantum statistics: L, P and Q, one instance per lane (the loss list's warps)
+        const int warps = kx_loss_shape_for(k->n).warps;
+        dim3 g2((B + 31) / 32, k->n);
+        const size_t smem = kx_loss_q_smem(k->n, warps);
+        if (warps == 16)
+            k_batch_loss_q<16><<<g2, 512, smem, s>>>(k->n, B, v.B, k->d_lel, k->d_lnm, k->d_lseg, k->d_lsw,
+                                                     k->d_lorder, v.td, v.fT, v.fmax, v.partial, v.qsum, st,
+                                                     stage, (int)k->nlel);
+        else
+            k_batch_loss_q<32><<<g2, 1024, smem, s>>>(k->n, B, v.B, k->d_lel, k->d_lnm, k->d_lseg, k->d_lsw,
+                                                      k->d_lorder, v.td, v.fT, v.fmax, v.partial, v.qsum, st,
+                                                      stage, (int)k->nlel);
+        return cudaGetLastError();
+    }
     const int *flags = k->cheb_K ? v.cflag : nullptr;
     auto launch = [&](kx_loss_shape sh) {
         const int per = 32 * sh.ipl;
@@ -1320,6 +1477,7 @@ int kx_batch_build_tables(kx_ctx *ctx, kx_kernel *k) {
             Sg[bt_index(i, p, k->KBG, 1)] = wl;
         }
     std::vector<float2> lel;
+    std::vector<uint32_t> lnm;   // quantum statistics: the elements' pairs
     std::vector<int2> lseg;
     const int WARPS = kx_loss_shape_for(n).warps;
     std::vector<int> lsw((size_t)n * WARPS + 1, 0), rlen(n, 0);
@@ -1328,6 +1486,7 @@ int kx_batch_build_tables(kx_ctx *ctx, kx_kernel *k) {
     struct El {
         int j;
         float w, om;
+        uint32_t nm;   // the element's pair n | m << 16
     };
     std::vector<El> row;
     std::vector<std::pair<size_t, size_t>> seg;
@@ -1339,7 +1498,7 @@ int kx_batch_build_tables(kx_ctx *ctx, kx_kernel *k) {
         for (int a = 0; a < n; ++a) {
             for (int b = a; b < n; ++b) {
                 const size_t e = (size_t)i * P + base[a] + (b - a);
-                if (W[e] != 0.0) row.push_back({(int)jl[e], (float)W[e], (float)om[e]});
+                if (W[e] != 0.0) row.push_back({(int)jl[e], (float)W[e], (float)om[e], (uint32_t)a | ((uint32_t)b << 16)});
             }
         }
         std::stable_sort(row.begin(), row.end(), [](const El &x, const El &y) { return x.j < y.j; });
@@ -1376,6 +1535,9 @@ int kx_batch_build_tables(kx_ctx *ctx, kx_kernel *k) {
                     lel.push_back(make_float2(v0 ? row[p0 + e].w : 0.f, v1 ? row[p0 + e + 1].w : 0.f));
                     lel.push_back(make_float2(v0 ? row[p0 + e].om : 0.f, v1 ? row[p0 + e + 1].om : 0.f));
                 }
+                // the pairs in element order (c4 words: lnm and lel share the segments' offsets)
+                if (k->stats)
+                    for (size_t e = 0; e < (size_t)c4; ++e) lnm.push_back(p0 + e < p1 ? row[p0 + e].nm : 0u);
             }
         }
         rlen[i] = (int)row.size();
@@ -1446,6 +1608,18 @@ int kx_batch_build_tables(kx_ctx *ctx, kx_kernel *k) {
         cudaMemcpy(k->d_lsw, lsw.data(), sizeof(int) * lsw.size(), cudaMemcpyHostToDevice) != cudaSuccess ||
         cudaMemcpy(k->d_lorder, lorder.data(), sizeof(int) * lorder.size(), cudaMemcpyHostToDevice) != cudaSuccess)
         return kx_set_error(ctx, KX_ECUDA, "batched build: table upload failed");
+    if (k->stats) {
+        if (lnm.empty()) lnm.push_back(0u);
+        if (lnm.size() != lel.size() && !(lel.size() == 1 && lnm.size() == 1))
+            return kx_set_error(ctx, KX_ECUDA, "batched build: pair list out of step with the loss list");
+        if (cudaMalloc(&k->d_lnm, sizeof(uint32_t) * lnm.size()) != cudaSuccess) {
+            cudaGetLastError();
+            return kx_set_error(ctx, KX_ENOMEM, "batched build: allocation failed");
+        }
+        k->bytes += (long long)(sizeof(uint32_t) * lnm.size());
+        if (cudaMemcpy(k->d_lnm, lnm.data(), sizeof(uint32_t) * lnm.size(), cudaMemcpyHostToDevice) != cudaSuccess)
+            return kx_set_error(ctx, KX_ECUDA, "batched build: table upload failed");
+    }
     return KX_OK;
 }
 

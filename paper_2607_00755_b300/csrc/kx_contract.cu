@@ -1993,7 +1993,7 @@ __device__ __forceinline__ kx_row_out kx_combine_project(int n, int chunks, int 
                                          double *sm) {
     const int i = threadIdx.x, T = blockDim.x;
     const double fm = v.fmax[b], rfm = v.rfmax[b], M2 = v.M2[b];
-    double G = 0.0, L = 0.0;
+    double G = 0.0, L = 0.0, X = 0.0;   // X: the quantum terms - eta f_i P_i + eta Q_i
     if (i < n && path == KX_SPLIT_TF32) {
         // the gain GEMM's k chunks in order (f' units); the loss from the
         // Chebyshev GEMM's chunks, or the exact loss kernel's row sum (x f_max)
@@ -2018,6 +2018,14 @@ __device__ __forceinline__ kx_row_out kx_combine_project(int n, int chunks, int 
         } else {
             L = v.partial[(long long)b * n + i].y;
         }
+        if (v.eta) {
+            // quantum statistics (eq. Lambda_quantum): the row is
+            // (1 + eta f_i) G - f_i L - eta f_i P + eta Q
+            const double eta = (double)v.eta;
+            const double P = v.partial[(long long)b * n + i].x, Q = v.qsum[(long long)b * n + i];
+            G *= 1.0 + eta * fi;
+            X = eta * (Q - fi * P);
+        }
     } else if (i < n) {
         const double2 *pp = v.partial + ((long long)b * n + i) * chunks;
         for (int c = 0; c < chunks; ++c) {
@@ -2032,7 +2040,7 @@ __device__ __forceinline__ kx_row_out kx_combine_project(int n, int chunks, int 
     // adds one) skip the FP64 arithmetic below on a warp-uniform branch.
     const bool wpts = (i & ~31) < n;   // this warp holds grid points
     double Craw = 0.0;   // G holds the gain and L the loss rate
-    if (i < n) Craw = M2 * (G - fi * L);
+    if (i < n) Craw = v.eta ? M2 * ((G - fi * L) + X) : M2 * (G - fi * L);
     kx_row_out r;
     r.Craw = Craw;
     r.Cproj = Craw;

@@ -47,6 +47,7 @@
 #define KX_SITE_LOSS_ROW 11   // batched exact loss: row i
 #define KX_SITE_GAIN_PAIR 12  // batched gain GEMM: decoded pair (n, m)
 #define KX_SITE_BIN 13        // FP32 streaming: bin index
+#define KX_SITE_LOSS_PAIR 14  // batched exact loss with quantum statistics: an element's (n, m)
 #define KX_SITE_PROBE 99      // kx_check_probe
 #ifdef KX_CHECK
 static __device__ unsigned int kx_chk_state[3];   // failures, first site, first index (this unit)
@@ -131,6 +132,8 @@ struct kx_kernel {
     float *d_Sg;         // [nsubI][KBG][hi, lo][1024]: S_ip as TF32 hi/lo operand tiles
     float2 *d_lel;       // per row i: nonzero (S_inm, omega) sorted by j_L, element pairs as
                          // (S_0, S_1), (omega_0, omega_1)
+    uint32_t *d_lnm;     // quantum statistics: per loss element (same order and padding as the
+                         // elements of d_lel) its pair n | m << 16 (padding: 0)
     int2 *d_lseg;        // segments of <= 64 elements of one j_L: (first element, j_L << 8 | count)
     int *d_lsw;          // [n * warps + 1] first segment of each (row, loss-kernel warp)
     int *d_lorder;       // [n] rows by element count, longest first
@@ -242,6 +245,8 @@ struct kx_batch_views {
     float *yt;             // Chebyshev loss: [Bpad/64][KBL][hi, lo][1024] coefficient operand tiles
     float *Lp;             // Chebyshev loss: [lsk][Bpad][nis] FP32 loss partials per k chunk
     int *cflag;            // Chebyshev loss: [B] 1 = an instance bracket beyond the truncation bound
+    double *qsum;          // split path with quantum statistics: [B][n] Q_i = sum S f~ f_n f_m (the
+                           // loss kernel's third row sum; P_i = sum S f~ (f_n + f_m) goes to partial.x)
     int cheb_K, KBL;       // Chebyshev loss: terms (0: exact loss), k blocks of the coefficient tiles
     int gsk, lsk, nis;     // split path: k chunks of the gain and loss GEMMs, partial row length
     int *err;              // tensor-core stage timeout flag (bounded waits)

@@ -364,3 +364,81 @@ def test_gain_operand_placement_is_result_neutral(env, N):
         err = np.max(np.abs(out["tensor"][:2] - Co)) / np.max(np.abs(Co))
         assert err <= TOL, err
     k.release()
+
+
+@pytest.mark.parametrize("eta", [1, -1])
+@pytest.mark.parametrize("N,B", [(24, 3), (40, 70), (100, 33)])
+def test_quantum_statistics_split_path_matches_oracle(env, eta, N, B):
+    """The split path with the Bose-Einstein / Fermi-Dirac factor (eq.
+    Lambda_quantum): the gain GEMM times (1 + eta f_i) plus the exact loss
+    kernel's three row sums (sum S f~, sum S f~ (f_n + f_m), sum S f~ f_n f_m);
+    C raw and projected within the mixed-precision bound of the oracle on
+    bimodal f of occupations of order one, instances bit-identical alone and in
+    the batch, the equilibrium of the statistics near its fixed point, and the
+    Chebyshev loss refused with these factors."""
+    kx, ctx, torch = env
+    q = ki.log_grid(N, 1e-2, 20.0)
+    g = oracle.grid(q)
+    W = oracle.kernel_tensor(q)
+    f = 0.8 * ki.batch_bimodal(np.random.default_rng(140 + N + eta), q, B)
+    sig = np.random.default_rng(141).uniform(0.3, 3.0, B)
+    k = ctx.build_kernel(q, precision=kx.SPLIT_TF32, stats=eta)
+    fd = torch.as_tensor(f, device="cuda")
+    picks = sorted({0, B // 2, B - 1})
+    for project in (0, 1):
+        C = ctx.collision(k, fd, sig, project=bool(project))[0].cpu().numpy()
+        for b in picks:
+            Co = oracle.collision_tensor_stats(q, W, f[b], eta) * oracle.M2_from_sigma(1.0, sig[b])
+            if project:
+                Co, _ = oracle.project(g["E"], g["h"], f[b], Co)
+            err = np.max(np.abs(C[b] - Co)) / np.max(np.abs(Co))
+            assert err <= TOL, (project, b, err)
+        if project:
+            b = picks[-1]
+            C1 = ctx.collision(k, torch.as_tensor(f[b:b + 1], device="cuda"), sig[b:b + 1], project=True)[0]
+            np.testing.assert_array_equal(C1.cpu().numpy()[0], C[b])
+    feq = 1.0 / (np.exp((g["E"] - 0.6) / 0.7) - eta)
+    C = ctx.collision(k, torch.as_tensor(feq[None], device="cuda"), np.array([1.0]), project=False)[0]
+    Co = oracle.collision_tensor_stats(q, W, feq, eta) * oracle.M2_from_sigma(1.0, 1.0)
+    _, G, _ = oracle.collision_tensor(q, W, feq, parts=True)
+    # the row's four sums ((1 + eta f) G, f L, f P, Q) are each up to (1 + f_max)^2
+    # times the dilute gain and carry their own FP32 rounding before they cancel
+    scale = oracle.M2_from_sigma(1.0, 1.0) * np.max(G) * (1.0 + np.max(np.abs(feq))) ** 2
+    assert np.max(np.abs(C.cpu().numpy()[0] - Co)) <= 1e-5 * scale
+    k.release()
+    with pytest.raises(kx.KxError):
+        ctx.build_kernel(q, precision=kx.SPLIT_TF32, stats=eta, loss_terms=16)
+
+
+@pytest.mark.parametrize("eta", [1, -1])
+def test_quantum_statistics_split_path_fixed_step_solve(env, eta):
+    """Twenty fixed Heun steps with Bose-Einstein (Fermi-Dirac: f scaled below
+    one) factors on the split path against the same steps taken with the
+    oracle's operator and projection; number and energy conserved to the
+    mixed-precision bound."""
+    kx, ctx, torch = env
+    c = ki.config1()
+    q, f0 = c["q"], c["f0"] * (1.0 if eta == 1 else 0.5)
+    g = oracle.grid(q)
+    W = oracle.kernel_tensor(q)
+    M2 = oracle.M2_from_sigma(1.0, c["sigma"])
+    h, steps = c["h"], 20
+
+    def rhs(f):
+        return oracle.project(g["E"], g["h"], f, oracle.collision_tensor_stats(q, W, f, eta) * M2)[0]
+
+    fo = f0.copy()
+    for _ in range(steps):
+        k1 = rhs(fo)
+        fp = fo + h * k1
+        fo = fo + 0.5 * h * (k1 + rhs(fp))
+    k = ctx.build_kernel(q, precision=kx.SPLIT_TF32, stats=eta)
+    fd = torch.as_tensor(f0[None], device="cuda")
+    res = ctx.solve(k, fd, c["sigma"], t_end=steps * h, h0=h, fixed_step=1)
+    f = fd.cpu().numpy()[0]
+    assert res[0]["status"] == 0 and res[0]["steps"] == steps
+    err = np.max(np.abs(f - fo)) / np.max(np.abs(fo))
+    assert err <= TOL, err
+    for w in (g["h"], g["h"] * g["E"]):
+        assert abs(np.sum(w * f) / np.sum(w * f0) - 1) < 1e-7
+    k.release()

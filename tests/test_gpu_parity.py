@@ -134,7 +134,7 @@ def test_build_rejects_bad_grids(ctx, kx):
     with pytest.raises(kx.KxError):
         ctx.build_kernel(ki.log_grid(16, 1e-3, 10.0), mass=0.0)
     with pytest.raises(kx.KxError) as ei:
-        ctx.build_kernel(ki.log_grid(16, 1e-3, 10.0), stats=1, precision=kx.SPLIT_TF32)
+        ctx.build_kernel(ki.log_grid(16, 1e-3, 10.0), stats=1, precision=kx.SPLIT_TF32, loss_terms=16)
     assert ei.value.code == kx.ENOTSUP
     with pytest.raises(kx.KxError):
         ctx.build_kernel(ki.log_grid(16, 1e-3, 10.0), stats=2)
