@@ -270,10 +270,11 @@ def measure_batched(ctx, kx, torch, flush, iters=5, check_sample=4):
     fpc, cyc = ctx.measure_mma_rate(0, n)
     mma_rate = fpc * 148 * 2.032e9 / 1e12
     P = n * (n + 1) // 2
-    for name, prec, lt, reps in (("split_tf32_exact_loss", kx.SPLIT_TF32, 0, iters),
-                                 ("split_tf32_cheb16_loss", kx.SPLIT_TF32, 16, iters),
-                                 ("fp64", kx.FP64, 0, 2)):
-        k = ctx.build_kernel(q, precision=prec, loss_terms=lt) if lt else ctx.build_kernel(q, precision=prec)
+    for name, prec, lt, reps, eta in (("split_tf32_exact_loss", kx.SPLIT_TF32, 0, iters, 0),
+                                      ("split_tf32_cheb16_loss", kx.SPLIT_TF32, 16, iters, 0),
+                                      ("split_tf32_bose_einstein", kx.SPLIT_TF32, 0, iters, 1),
+                                      ("fp64", kx.FP64, 0, 2, 0)):
+        k = ctx.build_kernel(q, precision=prec, loss_terms=lt, stats=eta)
         C, _ = ctx.collision(k, fd, c["sigma"])
         tot = 0.0
         for _ in range(reps):
@@ -308,6 +309,9 @@ def measure_batched(ctx, kx, torch, flush, iters=5, check_sample=4):
                         "projected C (kx_collision)",
             "split_tf32": out["split_tf32_exact_loss"],
             "split_tf32_cheb16": out["split_tf32_cheb16_loss"],
+            # the same batch with Bose-Einstein factors (eq. Lambda_quantum): the gain
+            # GEMM and the exact loss kernel's three row sums
+            "split_tf32_bose_einstein": out["split_tf32_bose_einstein"],
             "fp64_path": out["fp64"],
             "speedup_vs_fp64": out["split_tf32_exact_loss"]["evals_per_s"] / out["fp64"]["evals_per_s"],
             "speedup_vs_fp64_cheb16": out["split_tf32_cheb16_loss"]["evals_per_s"] / out["fp64"]["evals_per_s"],
@@ -361,10 +365,12 @@ def oracle_errors(batched_check, runtime_check):
         g = oracle.grid(q)
         err = {name: 0.0 for name in batched_check["C"]}
         for b in range(f.shape[0]):
-            Co = oracle.collision_tensor(q, W, f[b]) * oracle.M2_from_sigma(1.0, sig[b])
-            Co, _ = oracle.project(g["E"], g["h"], f[b], Co)
+            M2 = oracle.M2_from_sigma(1.0, sig[b])
+            Co, _ = oracle.project(g["E"], g["h"], f[b], oracle.collision_tensor(q, W, f[b]) * M2)
+            Cq, _ = oracle.project(g["E"], g["h"], f[b], oracle.collision_tensor_stats(q, W, f[b], 1) * M2)
             for name, C in batched_check["C"].items():
-                err[name] = max(err[name], float(np.max(np.abs(C[b] - Co)) / np.max(np.abs(Co))))
+                ref = Cq if name.endswith("bose_einstein") else Co
+                err[name] = max(err[name], float(np.max(np.abs(C[b] - ref)) / np.max(np.abs(ref))))
         out["batched"] = err
     for item in runtime_check or []:
         q, f = item["q"], item["f"]
