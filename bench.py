@@ -175,6 +175,17 @@ def oracle_sample(c, B, seconds: float):
     return evals, dt, oracle.num_threads()
 
 
+def cpu_model():
+    try:
+        with open("/proc/cpuinfo") as fh:
+            for line in fh:
+                if line.startswith("model name"):
+                    return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return None
+
+
 def run_reference(args, rank):
     """Reference arm: the FP64 CPU oracle on this host's cores (rank 0 only)."""
     if rank != 0:
@@ -861,9 +872,15 @@ def main():
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         e, t, cores = oracle_sample(c, B, 12.0)
+        # the same sample on one thread, and the host's CPU model
+        import oracle
+        oracle.set_threads(1)
+        e1, t1, _ = oracle_sample(c, B, 4.0)
+        oracle.set_threads(cores)
         cpu = {"value": e / t, "unit": UNIT, "cores": cores, "kind": "oracle",
                "sample": f"{e} RHS evaluations (tensor-form C + projection + sources) of the "
-                         f"N=128 workload's first Heun attempts in {t:.1f} s"}
+                         f"N=128 workload's first Heun attempts in {t:.1f} s",
+               "single_thread_value": e1 / t1, "cpu_model": cpu_model()}
         errs = oracle_errors(batched_check, runtime_check)
         if batched is not None:
             batched["max_rel_err_vs_oracle"] = errs.get("batched")
