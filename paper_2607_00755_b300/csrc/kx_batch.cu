@@ -854,35 +854,60 @@ __global__ void __launch_bounds__(WARPS * 32, (WARPS <= 16 && IPL <= 2) ? 2 : 1)
 // loss list's warp split); the FP32 sums flush into double-float accumulators
 // every 64 or more elements, FP64 across warps.  Output: partial[b][i] =
 // (f_max^2 P', f_max L'), qsum[b][i] = f_max^3 Q' (primes: f' units).
-template <int WARPS>
+template <int IPL, int WARPS>
 __global__ void __launch_bounds__(WARPS * 32, 1)
     k_batch_loss_q(int n, int B, int tds, const float2 *__restrict__ lel, const uint32_t *__restrict__ lnm,
                    const int2 *__restrict__ lseg, const int *__restrict__ lsw, const int *__restrict__ lorder,
                    const float2 *__restrict__ td, const float *__restrict__ fT, const double *__restrict__ fmax,
                    double2 *__restrict__ partial, double *__restrict__ qsum,
                    const kx_inst_state *__restrict__ st, int stage, int nel) {
-    // [n][32] (l2_j, D_j), then [n][32] f'_j; after the loop the same space holds
-    // the cross-warp reduction [3][WARPS][32] doubles
+    // IPL = 1: [n][32] (l2_j, D_j) and [n][32] f'_j; IPL = 2 (two instances per
+    // lane, packed f32x2 arithmetic): [n][32] (l2, l2', D, D') and [n][32] (f', f'').
+    // After the loop the same space holds the reduction [3][WARPS][32 IPL] doubles.
     extern __shared__ __align__(16) float2 kx_ltab[];
-    float *ftab = reinterpret_cast<float *>(kx_ltab + (size_t)n * 32);
+    float *ftab = reinterpret_cast<float *>(kx_ltab + (size_t)n * 32 * IPL);
     __shared__ __align__(16) float2 s_el[WARPS][KX_SEG];
     __shared__ __align__(16) uint32_t s_nm[WARPS][KX_SEG];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int b = blockIdx.x * 32 + lane;
-    const bool act = b < B && !(st && (st[b].done || (stage == 2 && st[b].skip2)));
-    if (!__syncthreads_or(act)) return;
+    int b[IPL];
+    bool act[IPL];
+    bool any = false;
+#pragma unroll
+    for (int s = 0; s < IPL; ++s) {
+        b[s] = blockIdx.x * (32 * IPL) + s * 32 + lane;
+        act[s] = b[s] < B && !(st && (st[b[s]].done || (stage == 2 && st[b[s]].skip2)));
+        any |= act[s];
+    }
+    if (!__syncthreads_or(any)) return;
     const int i = KX_IDX(lorder[blockIdx.y], n, KX_SITE_LOSS_ROW);
-    const float *fb = fT + (size_t)(b >> 7) * n * 128 + (b & 127);
     for (int j = warp; j < n; j += WARPS) {
-        kx_ltab[j * 32 + lane] = act ? td[(size_t)j * tds + b] : make_float2(-2000.f, 0.f);
-        ftab[j * 32 + lane] = act ? fb[(size_t)j * 128] : 0.f;
+        float2 t[IPL];
+        float fv[IPL];
+#pragma unroll
+        for (int s = 0; s < IPL; ++s) {
+            t[s] = act[s] ? td[(size_t)j * tds + b[s]] : make_float2(-2000.f, 0.f);
+            fv[s] = act[s] ? fT[((size_t)(b[s] >> 7) * n + j) * 128 + (b[s] & 127)] : 0.f;
+        }
+        if constexpr (IPL == 1) {
+            kx_ltab[j * 32 + lane] = t[0];
+            ftab[j * 32 + lane] = fv[0];
+        } else {
+            reinterpret_cast<float4 *>(kx_ltab)[j * 32 + lane] = make_float4(t[0].x, t[1].x, t[0].y, t[1].y);
+            reinterpret_cast<float2 *>(ftab)[j * 32 + lane] = make_float2(fv[0], fv[1]);
+        }
     }
     __syncthreads();
-    float hl = 0.f, ll = 0.f, hp = 0.f, lp = 0.f, hq = 0.f, lq = 0.f;
+    // per instance slot: double-float accumulators of L, P and Q
+    float hl[IPL], ll[IPL], hp[IPL], lp[IPL], hq[IPL], lq[IPL];
+#pragma unroll
+    for (int s = 0; s < IPL; ++s) hl[s] = ll[s] = hp[s] = lp[s] = hq[s] = lq[s] = 0.f;
     {
         const int gend = lsw[i * WARPS + warp + 1];
         int g = lsw[i * WARPS + warp];
-        float aL[4] = {0.f, 0.f, 0.f, 0.f}, aP[4] = {0.f, 0.f, 0.f, 0.f}, aQ[4] = {0.f, 0.f, 0.f, 0.f};
+        // FP32 sums of elements 0..3 of each four, per slot (IPL = 2: packed pairs)
+        unsigned long long aL[4], aP[4], aQ[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) aL[u] = aP[u] = aQ[u] = 0ull;
         int na = 0;
         for (; g < gend; ++g) {
             const int2 dsc = __ldg(lseg + g);
@@ -905,7 +930,17 @@ __global__ void __launch_bounds__(WARPS * 32, 1)
             s_nm[warp][32 + lane] = nm1;
             __syncwarp();
             const int j = KX_IDX(dsc.y >> 8, n, KX_SITE_LOSS_BRACKET), c4 = c;   // a multiple of 4
-            const float2 t = kx_ltab[j * 32 + lane];
+            // (l2, D) of the slots: scalar (IPL = 1) or packed pairs (IPL = 2)
+            unsigned long long tL, tD;
+            if constexpr (IPL == 1) {
+                const float2 t = kx_ltab[j * 32 + lane];
+                tL = kx_pk2(t.x, 0.f);
+                tD = kx_pk2(t.y, 0.f);
+            } else {
+                const float4 t = reinterpret_cast<const float4 *>(kx_ltab)[j * 32 + lane];
+                tL = kx_pk2(t.x, t.y);
+                tD = kx_pk2(t.z, t.w);
+            }
             const float4 *pe = reinterpret_cast<const float4 *>(s_el[warp]);
             const uint4 *pn = reinterpret_cast<const uint4 *>(s_nm[warp]);
             for (int e4 = 0; e4 < c4; e4 += 4, pe += 2, ++pn) {
@@ -916,62 +951,107 @@ __global__ void __launch_bounds__(WARPS * 32, 1)
                 const uint32_t nm[4] = {w4.x, w4.y, w4.z, w4.w};
 #pragma unroll
                 for (int u = 0; u < 4; ++u) {
-                    const float ft = kx_ex2f(fmaf(om[u], t.y, t.x));
                     const int a = KX_IDX((int)(nm[u] & 0xffffu), n, KX_SITE_LOSS_PAIR);
                     const int m = KX_IDX((int)(nm[u] >> 16), n, KX_SITE_LOSS_PAIR);
-                    const float fn = ftab[a * 32 + lane], fm = ftab[m * 32 + lane];
-                    const float w = S[u] * ft;
-                    aL[u] = fmaf(S[u], ft, aL[u]);
-                    aP[u] = fmaf(w, fn + fm, aP[u]);
-                    aQ[u] = fmaf(w, fn * fm, aQ[u]);
+                    if constexpr (IPL == 1) {
+                        const float ft = kx_ex2f(fmaf(om[u], kx_upk2(tD).x, kx_upk2(tL).x));
+                        const float fn = ftab[a * 32 + lane], fm = ftab[m * 32 + lane];
+                        const float w = S[u] * ft;
+                        const float2 A = kx_upk2(aL[u]), Pq = kx_upk2(aP[u]), Qq = kx_upk2(aQ[u]);
+                        aL[u] = kx_pk2(fmaf(S[u], ft, A.x), 0.f);
+                        aP[u] = kx_pk2(fmaf(w, fn + fm, Pq.x), 0.f);
+                        aQ[u] = kx_pk2(fmaf(w, fn * fm, Qq.x), 0.f);
+                    } else {
+                        // both slots at once: per lane the scalar operations (round to
+                        // nearest, no flush) of the IPL = 1 form
+                        const float2 e = kx_upk2(kx_fma2(kx_pk2(om[u], om[u]), tD, tL));
+                        const unsigned long long ft = kx_pk2(kx_ex2f(e.x), kx_ex2f(e.y));
+                        const unsigned long long S2 = kx_pk2(S[u], S[u]), z = 0ull;
+                        const unsigned long long fn = reinterpret_cast<const unsigned long long *>(ftab)[a * 32 + lane];
+                        const unsigned long long fm = reinterpret_cast<const unsigned long long *>(ftab)[m * 32 + lane];
+                        const unsigned long long w = kx_fma2(S2, ft, z);                   // S f~
+                        const unsigned long long sum = kx_fma2(fn, kx_pk2(1.f, 1.f), fm);  // f_n + f_m
+                        const unsigned long long prd = kx_fma2(fn, fm, z);                 // f_n f_m
+                        aL[u] = kx_fma2(S2, ft, aL[u]);
+                        aP[u] = kx_fma2(w, sum, aP[u]);
+                        aQ[u] = kx_fma2(w, prd, aQ[u]);
+                    }
                 }
             }
             na += c4;
-            if (na >= KX_SEG) {
-                float sm, er;
-                kx_two_sum_f(hl, (aL[0] + aL[1]) + (aL[2] + aL[3]), sm, er);
-                hl = sm;
-                ll += er;
-                kx_two_sum_f(hp, (aP[0] + aP[1]) + (aP[2] + aP[3]), sm, er);
-                hp = sm;
-                lp += er;
-                kx_two_sum_f(hq, (aQ[0] + aQ[1]) + (aQ[2] + aQ[3]), sm, er);
-                hq = sm;
-                lq += er;
+            const bool flush = na >= KX_SEG;
+            if (flush) {
+                const float2 L0 = kx_upk2(aL[0]), L1 = kx_upk2(aL[1]), L2 = kx_upk2(aL[2]), L3 = kx_upk2(aL[3]);
+                const float2 P0 = kx_upk2(aP[0]), P1 = kx_upk2(aP[1]), P2 = kx_upk2(aP[2]), P3 = kx_upk2(aP[3]);
+                const float2 Q0 = kx_upk2(aQ[0]), Q1 = kx_upk2(aQ[1]), Q2 = kx_upk2(aQ[2]), Q3 = kx_upk2(aQ[3]);
+                const float sL[2] = {(L0.x + L1.x) + (L2.x + L3.x), (L0.y + L1.y) + (L2.y + L3.y)};
+                const float sP[2] = {(P0.x + P1.x) + (P2.x + P3.x), (P0.y + P1.y) + (P2.y + P3.y)};
+                const float sQ[2] = {(Q0.x + Q1.x) + (Q2.x + Q3.x), (Q0.y + Q1.y) + (Q2.y + Q3.y)};
 #pragma unroll
-                for (int u = 0; u < 4; ++u) aL[u] = aP[u] = aQ[u] = 0.f;
+                for (int s = 0; s < IPL; ++s) {
+                    float sm, er;
+                    kx_two_sum_f(hl[s], sL[s], sm, er);
+                    hl[s] = sm;
+                    ll[s] += er;
+                    kx_two_sum_f(hp[s], sP[s], sm, er);
+                    hp[s] = sm;
+                    lp[s] += er;
+                    kx_two_sum_f(hq[s], sQ[s], sm, er);
+                    hq[s] = sm;
+                    lq[s] += er;
+                }
+#pragma unroll
+                for (int u = 0; u < 4; ++u) aL[u] = aP[u] = aQ[u] = 0ull;
                 na = 0;
             }
             __syncwarp();   // the slots are refilled next segment
         }
-        float sm, er;
-        kx_two_sum_f(hl, (aL[0] + aL[1]) + (aL[2] + aL[3]), sm, er);
-        hl = sm;
-        ll += er;
-        kx_two_sum_f(hp, (aP[0] + aP[1]) + (aP[2] + aP[3]), sm, er);
-        hp = sm;
-        lp += er;
-        kx_two_sum_f(hq, (aQ[0] + aQ[1]) + (aQ[2] + aQ[3]), sm, er);
-        hq = sm;
-        lq += er;
+        {
+            const float2 L0 = kx_upk2(aL[0]), L1 = kx_upk2(aL[1]), L2 = kx_upk2(aL[2]), L3 = kx_upk2(aL[3]);
+            const float2 P0 = kx_upk2(aP[0]), P1 = kx_upk2(aP[1]), P2 = kx_upk2(aP[2]), P3 = kx_upk2(aP[3]);
+            const float2 Q0 = kx_upk2(aQ[0]), Q1 = kx_upk2(aQ[1]), Q2 = kx_upk2(aQ[2]), Q3 = kx_upk2(aQ[3]);
+            const float sL[2] = {(L0.x + L1.x) + (L2.x + L3.x), (L0.y + L1.y) + (L2.y + L3.y)};
+            const float sP[2] = {(P0.x + P1.x) + (P2.x + P3.x), (P0.y + P1.y) + (P2.y + P3.y)};
+            const float sQ[2] = {(Q0.x + Q1.x) + (Q2.x + Q3.x), (Q0.y + Q1.y) + (Q2.y + Q3.y)};
+#pragma unroll
+            for (int s = 0; s < IPL; ++s) {
+                float sm, er;
+                kx_two_sum_f(hl[s], sL[s], sm, er);
+                hl[s] = sm;
+                ll[s] += er;
+                kx_two_sum_f(hp[s], sP[s], sm, er);
+                hp[s] = sm;
+                lp[s] += er;
+                kx_two_sum_f(hq[s], sQ[s], sm, er);
+                hq[s] = sm;
+                lq[s] += er;
+            }
+        }
     }
     __syncthreads();   // every warp is done with the tables
-    double *red = reinterpret_cast<double *>(kx_ltab);   // [3][WARPS][32]
-    red[(0 * WARPS + warp) * 32 + lane] = (double)hl + (double)ll;
-    red[(1 * WARPS + warp) * 32 + lane] = (double)hp + (double)lp;
-    red[(2 * WARPS + warp) * 32 + lane] = (double)hq + (double)lq;
-    __syncthreads();
-    if (warp == 0 && act) {
-        double L = 0.0, P = 0.0, Q = 0.0;
+    double *red = reinterpret_cast<double *>(kx_ltab);   // [3][WARPS][32 IPL]
 #pragma unroll
-        for (int w = 0; w < WARPS; ++w) {
-            L += red[(0 * WARPS + w) * 32 + lane];
-            P += red[(1 * WARPS + w) * 32 + lane];
-            Q += red[(2 * WARPS + w) * 32 + lane];
+    for (int s = 0; s < IPL; ++s) {
+        red[((0 * WARPS + warp) * IPL + s) * 32 + lane] = (double)hl[s] + (double)ll[s];
+        red[((1 * WARPS + warp) * IPL + s) * 32 + lane] = (double)hp[s] + (double)lp[s];
+        red[((2 * WARPS + warp) * IPL + s) * 32 + lane] = (double)hq[s] + (double)lq[s];
+    }
+    __syncthreads();
+    if (warp < IPL) {
+        const int s = warp;   // warp s finishes instance slot s
+        const int bb = blockIdx.x * (32 * IPL) + s * 32 + lane;
+        if (bb < B && !(st && (st[bb].done || (stage == 2 && st[bb].skip2)))) {
+            double L = 0.0, P = 0.0, Q = 0.0;
+#pragma unroll
+            for (int w = 0; w < WARPS; ++w) {
+                L += red[((0 * WARPS + w) * IPL + s) * 32 + lane];
+                P += red[((1 * WARPS + w) * IPL + s) * 32 + lane];
+                Q += red[((2 * WARPS + w) * IPL + s) * 32 + lane];
+            }
+            const double fm = fmax[bb];
+            partial[(size_t)bb * n + i] = make_double2(fm * fm * P, fm * L);
+            qsum[(size_t)bb * n + i] = fm * fm * fm * Q;
         }
-        const double fm = fmax[b];
-        partial[(size_t)b * n + i] = make_double2(fm * fm * P, fm * L);
-        qsum[(size_t)b * n + i] = fm * fm * fm * Q;
     }
 }
 
@@ -994,9 +1074,12 @@ static kx_loss_shape kx_loss_shape_for(int n) {
 static size_t kx_loss_smem(int n, kx_loss_shape sh) {
     return std::max((size_t)n, (size_t)sh.warps) * 32 * sh.ipl * sizeof(float2);
 }
-// quantum statistics: the (l2, D) and f' tables, or the three reductions
-static size_t kx_loss_q_smem(int n, int warps) {
-    return std::max((size_t)n * 32 * (sizeof(float2) + sizeof(float)), (size_t)3 * warps * 32 * sizeof(double));
+// quantum statistics: the (l2, D) and f' tables, or the three reductions; two
+// instances per lane while the tables fit (n <= 256), else one
+static int kx_loss_q_ipl(int n) { return n <= 256 ? 2 : 1; }
+static size_t kx_loss_q_smem(int n, int warps, int ipl) {
+    return std::max((size_t)n * 32 * ipl * (sizeof(float2) + sizeof(float)),
+                    (size_t)3 * warps * 32 * ipl * sizeof(double));
 }
 
 void kx_batch_prepare() {
@@ -1010,10 +1093,14 @@ void kx_batch_prepare() {
                          (int)kx_loss_smem(KX_MAX_N, {1, 32}));
     cudaFuncSetAttribute(k_batch_loss<1, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)kx_loss_smem(200, {1, 16}));
-    cudaFuncSetAttribute(k_batch_loss_q<16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)kx_loss_q_smem(KX_MAX_N, 16));
-    cudaFuncSetAttribute(k_batch_loss_q<32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)kx_loss_q_smem(KX_MAX_N, 32));
+    cudaFuncSetAttribute(k_batch_loss_q<1, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)kx_loss_q_smem(KX_MAX_N, 16, 1));
+    cudaFuncSetAttribute(k_batch_loss_q<1, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)kx_loss_q_smem(KX_MAX_N, 32, 1));
+    cudaFuncSetAttribute(k_batch_loss_q<2, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)kx_loss_q_smem(256, 16, 2));
+    cudaFuncSetAttribute(k_batch_loss_q<2, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)kx_loss_q_smem(256, 32, 2));
     cudaGetLastError();
 }
 
@@ -1315,18 +1402,20 @@ static cudaError_t kx_launch_split_gemm(bool gen, int G, const kx_kernel *const 
 static cudaError_t kx_launch_batch_loss(const kx_kernel *k, int B, const kx_batch_views &v,
                                         const kx_inst_state *st, int stage, cudaStream_t s) {
     if (k->stats) {
-        // quantum statistics: L, P and Q, one instance per lane (the loss list's warps)
-        const int warps = kx_loss_shape_for(k->n).warps;
-        dim3 g2((B + 31) / 32, k->n);
-        const size_t smem = kx_loss_q_smem(k->n, warps);
-        if (warps == 16)
-            k_batch_loss_q<16><<<g2, 512, smem, s>>>(k->n, B, v.B, k->d_lel, k->d_lnm, k->d_lseg, k->d_lsw,
-                                                     k->d_lorder, v.td, v.fT, v.fmax, v.partial, v.qsum, st,
-                                                     stage, (int)k->nlel);
-        else
-            k_batch_loss_q<32><<<g2, 1024, smem, s>>>(k->n, B, v.B, k->d_lel, k->d_lnm, k->d_lseg, k->d_lsw,
-                                                      k->d_lorder, v.td, v.fT, v.fmax, v.partial, v.qsum, st,
-                                                      stage, (int)k->nlel);
+        // quantum statistics: L, P and Q (the loss list's warps; instances per
+        // lane by n alone, so that an instance's sums do not depend on the batch)
+        const int warps = kx_loss_shape_for(k->n).warps, ipl = kx_loss_q_ipl(k->n);
+        dim3 g2((B + 32 * ipl - 1) / (32 * ipl), k->n);
+        const size_t smem = kx_loss_q_smem(k->n, warps, ipl);
+#define KX_LQ(I, W)                                                                                             \
+    k_batch_loss_q<I, W><<<g2, W * 32, smem, s>>>(k->n, B, v.B, k->d_lel, k->d_lnm, k->d_lseg, k->d_lsw,        \
+                                                  k->d_lorder, v.td, v.fT, v.fmax, v.partial, v.qsum, st, stage, \
+                                                  (int)k->nlel)
+        if (ipl == 2 && warps == 16) KX_LQ(2, 16);
+        else if (ipl == 2) KX_LQ(2, 32);
+        else if (warps == 16) KX_LQ(1, 16);
+        else KX_LQ(1, 32);
+#undef KX_LQ
         return cudaGetLastError();
     }
     const int *flags = k->cheb_K ? v.cflag : nullptr;

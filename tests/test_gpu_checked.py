@@ -143,3 +143,27 @@ def test_checked_build_grouped_solve_no_failed_check(env, loss_terms):
     assert out[0][1] == out[1][1]
     assert all(s == 0 for r in out[0][1] for s, _, _ in r)
     assert ctx.check_status(reset=True)["failures"] == 0
+
+
+@pytest.mark.parametrize("N", [24, 100])
+def test_checked_build_quantum_split_no_failed_check(env, N):
+    """The split path with Bose-Einstein factors (the quantum loss kernel's
+    element, bracket and pair indices checked) through the checked build:
+    within the path's tolerance of the oracle and no failed check."""
+    kx, ctx, torch = env
+    q = ki.log_grid(N, 1e-2, 20.0)
+    B = 4
+    f = 0.8 * ki.batch_bimodal(np.random.default_rng(150 + N), q, B)
+    sig = np.array([0.5, 1.0, 2.0, 4.0])
+    W = oracle.kernel_tensor(q)
+    g = oracle.grid(q)
+    ctx.check_status(reset=True)
+    k = ctx.build_kernel(q, precision=kx.SPLIT_TF32, stats=1)
+    C, _ = ctx.collision(k, torch.as_tensor(f, device="cuda"), sig)
+    C = C.cpu().numpy()
+    k.release()
+    for b in range(B):
+        Co = oracle.collision_tensor_stats(q, W, f[b], 1) * oracle.M2_from_sigma(1.0, sig[b])
+        Co, _ = oracle.project(g["E"], g["h"], f[b], Co)
+        assert np.max(np.abs(C[b] - Co)) / np.max(np.abs(Co)) <= 1e-5
+    assert ctx.check_status(reset=True)["failures"] == 0
