@@ -155,6 +155,9 @@ __device__ __forceinline__ unsigned long long kx_fma2(unsigned long long a, unsi
 #define KX_SG_CPYW (KX_SG_GW + 5)         // the bulk-copy warp
 #define KX_SG_THREADS ((KX_SG_GW + 6) * 32)
 #define KX_GAIN_KC 32   // k blocks per chunk of the gain GEMM (a work item; at most 32: one per lane)
+static_assert(KX_GAIN_KC <= 32, "a generating warp builds its pair list with one lane per k block");
+static_assert(KX_SG_GW % 4 == 0 && 64 % KX_SG_GW == 0 && KX_SG_PPW % 4 == 0,
+              "generating warps: whole lane quarters, pairs per warp a multiple of 4");
 #define KX_LOSS_KC 8    // k blocks per chunk of the loss GEMM
 
 // A bounded mbarrier wait that also gives up when another role of the CTA has
