@@ -2943,7 +2943,9 @@ cudaError_t kx_launch_stage_grouped(int G, const kx_kernel *const *ks, const int
     L.G = G;
     int b0 = 0, nmax = 0;
     for (int g = 0; g < G; ++g) {
-        if (ks[g]->stats) return cudaErrorInvalidValue;   // (quantum statistics: per-group stage only)
+        // (the grouped body has no FP32 quantum tables; the split path's quantum
+        // factors live in its contraction and row combine)
+        if (ks[g]->stats && ks[g]->precision == KX_FP32) return cudaErrorInvalidValue;
         kx_stage_group &q = L.g[g];
         q.n = ks[g]->n;
         q.chunks = vs[g]->chunks;

@@ -442,3 +442,26 @@ def test_quantum_statistics_split_path_fixed_step_solve(env, eta):
     for w in (g["h"], g["h"] * g["E"]):
         assert abs(np.sum(w * f) / np.sum(w * f0) - 1) < 1e-7
     k.release()
+
+
+def test_grouped_solve_with_quantum_statistics_equals_per_grid_solves(env):
+    """Two grids with Bose-Einstein factors in one grouped solve: every
+    instance bit-identical to kx_solve on its own kernel."""
+    kx, ctx, torch = env
+    rng = np.random.default_rng(160)
+    sizes, Bs = (24, 40), (5, 3)
+    grids = [ki.log_grid(n, 1e-2, 20.0) for n in sizes]
+    f0 = [0.8 * ki.batch_bimodal(rng, q, B) for q, B in zip(grids, Bs)]
+    sig = [10.0 ** rng.uniform(-1, 0.5, B) for B in Bs]
+    ks = [ctx.build_kernel(q, precision=kx.SPLIT_TF32, stats=1) for q in grids]
+    par = dict(t_end=0.3, h0=1e-3, rtol=1e-6, atol=1e-12, l1_tol=0.0)
+    fd = [torch.as_tensor(f, device="cuda") for f in f0]
+    res = ctx.solve_grouped(ks, fd, sig, **par)
+    for g in range(len(sizes)):
+        fa = torch.as_tensor(f0[g], device="cuda")
+        ra = ctx.solve(ks[g], fa, sig[g], **par)
+        np.testing.assert_array_equal(fd[g].cpu().numpy(), fa.cpu().numpy())
+        for b in range(Bs[g]):
+            assert res[g][b]["status"] == 0 and res[g][b]["steps"] == ra[b]["steps"]
+    for k in ks:
+        k.release()
