@@ -2897,9 +2897,11 @@ __device__ __forceinline__ void kx_stage_body(int b, int n, int chunks, int path
 // PATH >= 0: an instantiation for that path alone (the FP32 path's, which holds
 // only its own prep: a smaller kernel, and a register allocation that the
 // other paths' code does not move); PATH = -1: the path is the argument.
-// Q: the FP32 path with quantum statistics.
+// Q: the FP32 path with quantum statistics.  The other paths' instantiations
+// ask for one resident block per SM (minimum blocks 1): without it the compiler
+// held them to 64 registers and spilled; the FP32 path's keeps its allocation.
 template <int PATH, bool Q = false>
-__global__ void __launch_bounds__(KX_FIN_THREADS)
+__global__ void __launch_bounds__(KX_FIN_THREADS, PATH == KX_FP32 ? 0 : 1)
     k_stage(int n, int chunks, int path, const double *__restrict__ E, const double *__restrict__ h,
             kx_batch_views v, kx_step_views sv, int stage, long long max_attempts) {
     __shared__ double smem[5 * KX_FIN_THREADS + 8];
@@ -2964,8 +2966,9 @@ cudaError_t kx_launch_stage_grouped(int G, const kx_kernel *const *ks, const int
 
 cudaError_t kx_launch_stage(const kx_kernel *k, int B, const kx_batch_views &v,
                             const kx_step_views &sv, int stage, cudaStream_t s, bool pdl) {
-    auto *fn = k->precision != KX_FP32 ? k_stage<-1>
-                                       : (k->stats ? k_stage<KX_FP32, true> : k_stage<KX_FP32>);
+    auto *fn = k->precision == KX_SPLIT_TF32 ? k_stage<KX_SPLIT_TF32>
+               : k->precision != KX_FP32   ? k_stage<-1>
+                                           : (k->stats ? k_stage<KX_FP32, true> : k_stage<KX_FP32>);
     // the FP32 path's stage takes one more warp, without grid points: it makes
     // the source envelopes and the fit line off the points' critical path
     int threads = kx_fin_threads(k->n);
