@@ -635,3 +635,19 @@ def test_expanding_switch_rule():
                                    eps_switch=1e-2, sources=src)
     assert 0.0 < r1["u_switch"] < 0.3 and r1["gamma_over_H"] > 1e-2
     assert r1["rk4_steps"] == round(r1["u_switch"] / 0.02) and r1["checks"] == r1["rk4_steps"] // 2 + 1
+
+
+@pytest.mark.parametrize("N", [96, 256])
+def test_projection_correction_small_on_the_paper_workload(N):
+    """The paper reports (Sec. 5, its runtime workload: the two-bump f of eq.
+    benchmark_two_bump, m = 1, a = 1, q in [1e-3, 1e2], N_mu = 18, BE factors)
+    that the pointwise moment-fixing correction stays below one percent of
+    max |C_raw|.  The oracle's correction on that input, under the energy
+    measure (reading A1): below 1 %, with and without the quantum factor."""
+    q = ki.log_grid(N, 1e-3, 1e2)
+    f = ki.paper_two_bump(q)
+    g = oracle.grid(q)
+    W = oracle.kernel_tensor(q)
+    for C in (oracle.collision_tensor_stats(q, W, f, 1), oracle.collision_tensor(q, W, f)):
+        Cp, _ = oracle.project(g["E"], g["h"], f, C)
+        assert np.max(np.abs(Cp - C)) < 1e-2 * np.max(np.abs(C))
