@@ -129,10 +129,12 @@ __device__ __forceinline__ unsigned long long kx_fma2(unsigned long long a, unsi
 //               (the Chebyshev expansion of f_t, eq. app_log_interp).
 // f' = f / f_max.  The B operand (S or M: rows i, K-major) is a kernel table
 // in 64-row TF32 hi/lo tiles, staged by bulk copies; the A operand is the
-// per-call coefficient tiles (loss, bulk copies) or is generated in shared
-// memory by four producer warps from f' and the pair table (gain: f'_n f'_m in
-// FP32, split into TF32 hi + lo).  Products hi*hi + hi*lo + lo*hi (K = 8 per
-// MMA) accumulate in FP32 in tensor memory.  The k chunks are fixed by the
+// per-call coefficient tiles (loss, bulk copies) or is generated by the
+// generating warps from the staged f' block and their pair lists (gain:
+// f'_n f'_m in FP32, split into TF32 hi + lo) and stored into tensor memory
+// (tcgen05.st; the MMAs read A from there) or into the stage's shared memory.
+// Products hi*hi + hi*lo + lo*hi (K = 8 per MMA) accumulate in FP32 in tensor
+// memory.  The k chunks are fixed by the
 // kernel (not by the batch), so an instance's sums do not depend on the batch.
 // A work item is (instance tile, i tile, chunk); the CTAs take them round
 // robin (persistent, one CTA per SM).  Roles (G = KX_SG_GW): warps 0 .. G-1
@@ -147,7 +149,6 @@ __device__ __forceinline__ unsigned long long kx_fma2(unsigned long long a, unsi
 // expiry the CTA sets *err and every role stops; copies and MMAs in flight get
 // a bounded wait before shared and tensor memory are released.
 #define KX_GN 256                                             // i columns per tile
-#define KX_GSTAGE (2 * KX_ATILE * 4 + 2 * 4 * KX_BTILE * 4)   // A hi/lo 16 KB + B hi/lo 32 KB
 #define KX_SG_GW 8                        // generating warps (gain), a multiple of 4 dividing 64
 #define KX_SG_PPW (64 / KX_SG_GW)         // pairs of a k block per generating warp
 #define KX_SG_MMAW KX_SG_GW               // the MMA warp
