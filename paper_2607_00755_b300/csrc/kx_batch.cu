@@ -140,7 +140,8 @@ __device__ __forceinline__ unsigned long long kx_fma2(unsigned long long a, unsi
 // robin (persistent, one CTA per SM).  Roles (G = KX_SG_GW): warps 0 .. G-1
 // generate the gain's A operand of each stage of an S-stage ring (G/4 warps
 // per 32 instance rows, 16/(G/4) pairs each), warp G lane 0 issues the MMAs
-// into one of two accumulators, warps G+1 .. G+4 read the previous item's
+// into one of two accumulators (one where the tensor-memory columns do not
+// hold two and the A stages), warps G+1 .. G+4 read the previous item's
 // accumulator (tensor-memory lane quarter = warp % 4) and store its partials
 // while the next item's MMAs run, warp G+5 (one lane) issues the bulk copies
 // of each stage (full barrier: the copy bytes plus one arrival per generating
